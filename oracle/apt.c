@@ -1,0 +1,479 @@
+/*
+ * Oracle: p-bit Gibbs sweeps, adaptive parallel tempering with replica
+ * exchange and isoenergetic cluster moves, the adaptive beta ladder and the
+ * pilot-run histograms.  TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Parallel tempering is written the usual way: replicas ("buffers") stay
+ * where they are and an accepted swap exchanges their temperatures, which
+ * is the same Markov chain as exchanging the states (Algorithm S2, "swap the
+ * p-bit states").  buf_of[r][a] names the buffer that holds temperature r
+ * with ICM label a; temp_of[b] is its inverse.
+ */
+#include <limits.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "oracle.h"
+#include "oracle_internal.h"
+
+/* ---------------- shared sampler pieces ---------------- */
+
+/* Threshold table of one temperature over I in [-Imax, Imax]. */
+static uint32_t *make_table(double beta, int64_t Imax) {
+  uint32_t *t = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(2 * Imax + 1));
+  if (!t) return NULL;
+  for (int64_t I = -Imax; I <= Imax; ++I) t[I + Imax] = or_pbit_threshold(beta, I);
+  return t;
+}
+
+/* Random initial state (Algorithm S2 "Initialize all replicas to random
+ * states"): +1 iff the init half-word is below 2^15. */
+static void init_spins(const or_lat *L, int B, int8_t *spin, uint64_t seed, uint32_t ent,
+                       uint32_t tag) {
+  for (int b = 0; b < B; ++b) {
+    for (int lin = 0; lin < L->N; ++lin) {
+      int c = or_colour(L, lin);
+      uint32_t ctr[4] = {(uint32_t)(lin >> 1), 0u, ((uint32_t)c << 16) | (uint32_t)(b >> 3),
+                         (ent << 8) | tag};
+      uint32_t x[4];
+      or_philox(ctr, seed, x);
+      spin[(size_t)b * L->N + lin] = (or_half(x, b & 7) < 0x8000u) ? 1 : -1;
+    }
+  }
+}
+
+/* One Monte Carlo sweep (every spin of every buffer updated once) in the
+ * graph-coloured order of Algorithm S2's p-computer: all colour-0 sites,
+ * then all colour-1 sites.  Each update solves Eq. synapse for I and
+ * Eq. neuron through the threshold of the buffer's temperature. */
+static void gibbs_sweep(const or_lat *L, const int8_t *J, const int8_t *h, int64_t Imax,
+                        int B, int8_t *spin, const int32_t *temp_of, uint32_t *const *tab,
+                        uint64_t seed, uint32_t ent, uint32_t s, uint32_t tag_main,
+                        uint32_t tag_ref) {
+  for (int c = 0; c < 2; ++c) {
+    for (int b = 0; b < B; ++b) {
+      int8_t *sb = spin + (size_t)b * L->N;
+      const uint32_t *T = tab[temp_of[b]];
+      for (int lin = 0; lin < L->N; ++lin) {
+        if (or_colour(L, lin) != c) continue;
+        int64_t I = or_field(L, J, h, sb, lin);
+        uint32_t u = or_uniform32(seed, (uint32_t)(lin >> 1), s,
+                                  ((uint32_t)c << 16) | (uint32_t)(b >> 3), ent, tag_main,
+                                  tag_ref, b & 7);
+        sb[lin] = (u < T[I + Imax]) ? 1 : -1;
+      }
+    }
+  }
+}
+
+/* ---------------- APT ---------------- */
+typedef struct {
+  or_lat L;
+  int8_t *J, *h;
+  int T, A, B;
+  double *beta;
+  int64_t Imax;
+  uint32_t **tab;
+  int32_t *temp_of, *buf_of;
+  int8_t *spin;
+  int64_t *E;
+  uint32_t ent;
+  int64_t best_E, best_sweep, hit_sweep, target;
+  int32_t best_buf;
+  int8_t *best_spin;
+  int64_t *att, *acc;
+  int64_t icm[3];
+  int32_t *queue;
+  uint8_t *inC;
+} apt_entry;
+
+struct or_apt {
+  int n;
+  apt_entry *e;
+  uint64_t seed;
+  int64_t sweeps_done, swaps_done;
+};
+
+static void entry_free(apt_entry *e) {
+  if (e->tab)
+    for (int t = 0; t < e->T; ++t) free(e->tab[t]);
+  free(e->tab);
+  free(e->J); free(e->h); free(e->beta); free(e->temp_of); free(e->buf_of);
+  free(e->spin); free(e->E); free(e->best_spin); free(e->att); free(e->acc);
+  free(e->queue); free(e->inC);
+  or_lat_free(&e->L);
+}
+
+void or_apt_destroy(or_apt *a) {
+  if (!a) return;
+  for (int i = 0; i < a->n; ++i) entry_free(&a->e[i]);
+  free(a->e);
+  free(a);
+}
+
+int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *periodic,
+                  const int8_t *J, const int8_t *h, const int32_t *n_temps,
+                  const double *betas, int n_labels, uint64_t seed, uint32_t entry0) {
+  *out = NULL;
+  if (n_inst < 1 || n_labels < 1 || n_labels > 2) return -1;
+  or_apt *a = (or_apt *)calloc(1, sizeof(or_apt));
+  if (!a) return -2;
+  a->n = n_inst;
+  a->seed = seed;
+  a->e = (apt_entry *)calloc((size_t)n_inst, sizeof(apt_entry));
+  if (!a->e) { free(a); return -2; }
+  size_t joff = 0, boff = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    apt_entry *e = &a->e[i];
+    int rc = or_lat_init(&e->L, dims + 3 * i, periodic ? periodic + 3 * i : NULL);
+    if (rc) { or_apt_destroy(a); return rc; }
+    int N = e->L.N;
+    e->T = n_temps[i];
+    e->A = n_labels;
+    e->B = e->T * e->A;
+    if (e->T < 1) { or_apt_destroy(a); return -1; }
+    e->ent = entry0 + (uint32_t)i;
+    e->J = (int8_t *)malloc((size_t)3 * N);
+    memcpy(e->J, J + 3 * joff, (size_t)3 * N);
+    if (h) {
+      e->h = (int8_t *)malloc((size_t)N);
+      memcpy(e->h, h + joff, (size_t)N);
+    }
+    e->beta = (double *)malloc(sizeof(double) * e->T);
+    memcpy(e->beta, betas + boff, sizeof(double) * e->T);
+    for (int t = 1; t < e->T; ++t)
+      if (!(e->beta[t] > e->beta[t - 1])) { or_apt_destroy(a); return -1; }
+    e->Imax = or_field_bound(&e->L, e->J, e->h);
+    e->tab = (uint32_t **)calloc((size_t)e->T, sizeof(uint32_t *));
+    for (int t = 0; t < e->T; ++t) e->tab[t] = make_table(e->beta[t], e->Imax);
+    e->temp_of = (int32_t *)malloc(sizeof(int32_t) * e->B);
+    e->buf_of = (int32_t *)malloc(sizeof(int32_t) * e->B);
+    for (int b = 0; b < e->B; ++b) {
+      e->temp_of[b] = b / e->A;     /* buffer b starts at temperature b / A */
+      e->buf_of[b] = b;             /* with label b % A */
+    }
+    e->spin = (int8_t *)malloc((size_t)e->B * N);
+    e->E = (int64_t *)malloc(sizeof(int64_t) * e->B);
+    e->best_spin = (int8_t *)malloc((size_t)N);
+    e->att = (int64_t *)calloc((size_t)(e->T > 1 ? e->T - 1 : 1) * e->A, sizeof(int64_t));
+    e->acc = (int64_t *)calloc((size_t)(e->T > 1 ? e->T - 1 : 1) * e->A, sizeof(int64_t));
+    e->queue = (int32_t *)malloc(sizeof(int32_t) * N);
+    e->inC = (uint8_t *)malloc((size_t)N);
+    e->best_E = INT64_MAX;
+    e->best_sweep = -1;
+    e->best_buf = -1;
+    e->hit_sweep = -1;
+    e->target = INT64_MIN;
+    init_spins(&e->L, e->B, e->spin, seed, e->ent, OR_TAG_APT_INIT);
+    for (int b = 0; b < e->B; ++b)
+      e->E[b] = or_energy_lat(&e->L, e->J, e->h, e->spin + (size_t)b * N);
+    joff += (size_t)N;
+    boff += (size_t)e->T;
+  }
+  *out = a;
+  return 0;
+}
+
+/* Minimum-energy selection (Algorithm S2 output; the paper keeps the
+ * minimum-energy replica at every swap): lowest buffer index on ties, strict
+ * improvement only. */
+static void best_update(apt_entry *e, int64_t sweeps) {
+  int bmin = 0;
+  for (int b = 1; b < e->B; ++b)
+    if (e->E[b] < e->E[bmin]) bmin = b;
+  if (e->E[bmin] < e->best_E) {
+    e->best_E = e->E[bmin];
+    e->best_sweep = sweeps;
+    e->best_buf = bmin;
+    memcpy(e->best_spin, e->spin + (size_t)bmin * e->L.N, (size_t)e->L.N);
+  }
+  if (e->hit_sweep < 0 && e->best_E <= e->target) e->hit_sweep = sweeps;
+}
+
+/* Core of ICMop on two configurations; x = the pair's Philox block.
+ * Returns 0 (no mismatch), 1 (cluster flipped in both) or 2 (one whole
+ * replica flipped); *size = cluster size. */
+static int icm_core(const or_lat *L, int8_t *sa, int8_t *sb, const uint32_t x[4],
+                    int32_t *queue, uint8_t *inC, int64_t *size_out) {
+  int N = L->N;
+  int64_t nminus = 0;
+  for (int lin = 0; lin < N; ++lin) nminus += (sa[lin] != sb[lin]);
+  *size_out = 0;
+  if (nminus == 0) return 0;
+  int64_t k = (int64_t)(((uint64_t)x[0] * (uint64_t)nminus) >> 32);
+  int seed_site = -1;
+  int64_t cnt = 0;
+  for (int c = 0; c < 2 && seed_site < 0; ++c)
+    for (int lin = 0; lin < N; ++lin) {
+      if (or_colour(L, lin) != c || sa[lin] == sb[lin]) continue;
+      if (cnt == k) { seed_site = lin; break; }
+      ++cnt;
+    }
+  memset(inC, 0, (size_t)N);
+  int head = 0, tail = 0;
+  queue[tail++] = seed_site;
+  inC[seed_site] = 1;
+  while (head < tail) {
+    int v = queue[head++];
+    for (int dir = 0; dir < 6; ++dir) {
+      int n = L->nb[6 * v + dir];
+      if (n < 0 || inC[n] || sa[n] == sb[n]) continue;
+      inC[n] = 1;
+      queue[tail++] = n;
+    }
+  }
+  *size_out = tail;
+  if (2 * (int64_t)tail > (int64_t)N) {
+    int8_t *sf = (x[1] & 1u) ? sb : sa;
+    for (int lin = 0; lin < N; ++lin) sf[lin] = (int8_t)-sf[lin];
+    return 2;
+  }
+  for (int q = 0; q < tail; ++q) {
+    int v = queue[q];
+    sa[v] = (int8_t)-sa[v];
+    sb[v] = (int8_t)-sb[v];
+  }
+  return 1;
+}
+
+/* ICMop of Algorithm S2 on buffers (ba, bb) at attempt t, temperature r:
+ * overlap q_i = s_i^a s_i^b; a uniformly chosen site with q = -1 (the k-th
+ * in canonical order: colour 0 by increasing lin, then colour 1, with
+ * k = floor(x0 n_minus / 2^32)) seeds the cluster = its connected component
+ * of {q = -1} on the lattice graph.  If the cluster holds more than half of
+ * all spins, one of the two replicas (x1 bit 0: 0 -> a, 1 -> b) is flipped
+ * entirely; otherwise the cluster is flipped in both. */
+static void icm_op(apt_entry *e, uint64_t seed, int ba, int bb, uint32_t r, uint32_t t,
+                   uint32_t p) {
+  int N = e->L.N;
+  int8_t *sa = e->spin + (size_t)ba * N, *sb = e->spin + (size_t)bb * N;
+  uint32_t ctr[4] = {r, t, p, (e->ent << 8) | OR_TAG_ICM}, x[4];
+  or_philox(ctr, seed, x);
+  int64_t size;
+  int br = icm_core(&e->L, sa, sb, x, e->queue, e->inC, &size);
+  e->icm[br]++;
+  if (br == 0) return;
+  e->E[ba] = or_energy_lat(&e->L, e->J, e->h, sa);
+  e->E[bb] = or_energy_lat(&e->L, e->J, e->h, sb);
+}
+
+int or_icm_apply(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb,
+                 uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p,
+                 int64_t *cluster_size) {
+  or_lat L;
+  int rc = or_lat_init(&L, dims, periodic);
+  if (rc) return rc;
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * L.N);
+  uint8_t *inC = (uint8_t *)malloc((size_t)L.N);
+  uint32_t ctr[4] = {r, t, p, (entry << 8) | OR_TAG_ICM}, x[4];
+  or_philox(ctr, seed, x);
+  int br = icm_core(&L, sa, sb, x, queue, inC, cluster_size);
+  free(queue); free(inC);
+  or_lat_free(&L);
+  return br;
+}
+
+/* Replica exchange at attempt t (0-based): even t pairs (0,1),(2,3),...
+ * (the paper's odd-numbered attempt), odd t pairs (1,2),(3,4),...; within
+ * each pair every label decides on its own with
+ * p_swap = min(1, exp(dbeta dE)), dE = E_{r+1} - E_r, dbeta = b_{r+1}-b_r. */
+static void swap_step(apt_entry *e, uint64_t seed, uint32_t t) {
+  for (int r = (int)(t & 1u); r + 1 < e->T; r += 2) {
+    for (int a = 0; a < e->A; ++a) {
+      int bA = e->buf_of[r * e->A + a], bB = e->buf_of[(r + 1) * e->A + a];
+      int64_t dE = e->E[bB] - e->E[bA];
+      uint32_t ctr[4] = {(uint32_t)r, t, (uint32_t)a, (e->ent << 8) | OR_TAG_SWAP}, x[4];
+      or_philox(ctr, seed, x);
+      int accept = (dE >= 0) || (x[0] < or_swap_threshold(e->beta[r + 1] - e->beta[r], dE));
+      e->att[r * e->A + a]++;
+      if (accept) {
+        e->acc[r * e->A + a]++;
+        e->buf_of[r * e->A + a] = bB;
+        e->buf_of[(r + 1) * e->A + a] = bA;
+        e->temp_of[bA] = r + 1;
+        e->temp_of[bB] = r;
+      }
+    }
+  }
+}
+
+int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int threads) {
+  if (!a || n_swaps < 0 || sweeps_per_swap < 1) return -1;
+  for (int i = 0; i < a->n; ++i) {
+    if (icm && a->e[i].A != 2) return -1;
+    if (icm && a->e[i].h) return -1; /* whole-replica flip needs h = 0 */
+  }
+  int64_t s0 = a->sweeps_done, t0 = a->swaps_done;
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < a->n; ++i) {
+    apt_entry *e = &a->e[i];
+    int64_t s = s0;
+    for (int64_t k = 0; k < n_swaps; ++k) {
+      uint32_t t = (uint32_t)(t0 + k);
+      for (int q = 0; q < sweeps_per_swap; ++q, ++s)
+        gibbs_sweep(&e->L, e->J, e->h, e->Imax, e->B, e->spin, e->temp_of, e->tab, a->seed,
+                    e->ent, (uint32_t)s, OR_TAG_APT_SWEEP, OR_TAG_APT_REFINE);
+      for (int b = 0; b < e->B; ++b)
+        e->E[b] = or_energy_lat(&e->L, e->J, e->h, e->spin + (size_t)b * e->L.N);
+      best_update(e, s);
+      if (icm) {
+        for (int r = 0; r < e->T; ++r)
+          icm_op(e, a->seed, e->buf_of[r * 2 + 0], e->buf_of[r * 2 + 1], (uint32_t)r, t, 0u);
+        best_update(e, s);
+      }
+      swap_step(e, a->seed, t);
+    }
+  }
+  (void)threads;
+  a->sweeps_done += n_swaps * sweeps_per_swap;
+  a->swaps_done += n_swaps;
+  return 0;
+}
+
+int or_apt_set_target(or_apt *a, int inst, int64_t e_target) {
+  if (!a || inst < 0 || inst >= a->n) return -1;
+  a->e[inst].target = e_target;
+  a->e[inst].hit_sweep = -1;
+  if (a->e[inst].best_E <= e_target) a->e[inst].hit_sweep = a->e[inst].best_sweep;
+  return 0;
+}
+
+int or_apt_state(const or_apt *a, int inst, int8_t *spins, int64_t *energies, int32_t *temp_of) {
+  if (!a || inst < 0 || inst >= a->n) return -1;
+  const apt_entry *e = &a->e[inst];
+  if (spins) memcpy(spins, e->spin, (size_t)e->B * e->L.N);
+  if (energies) memcpy(energies, e->E, sizeof(int64_t) * e->B);
+  if (temp_of) memcpy(temp_of, e->temp_of, sizeof(int32_t) * e->B);
+  return 0;
+}
+
+int or_apt_best(const or_apt *a, int inst, int64_t *E, int64_t *sweep, int32_t *buf,
+                int64_t *hit_sweep, int8_t *spins) {
+  if (!a || inst < 0 || inst >= a->n) return -1;
+  const apt_entry *e = &a->e[inst];
+  if (E) *E = e->best_E;
+  if (sweep) *sweep = e->best_sweep;
+  if (buf) *buf = e->best_buf;
+  if (hit_sweep) *hit_sweep = e->hit_sweep;
+  if (spins) memcpy(spins, e->best_spin, (size_t)e->L.N);
+  return 0;
+}
+
+int or_apt_stats(const or_apt *a, int inst, int64_t *att, int64_t *acc, int64_t *icm) {
+  if (!a || inst < 0 || inst >= a->n) return -1;
+  const apt_entry *e = &a->e[inst];
+  size_t np = (size_t)(e->T > 1 ? e->T - 1 : 0) * e->A;
+  if (att) memcpy(att, e->att, sizeof(int64_t) * np);
+  if (acc) memcpy(acc, e->acc, sizeof(int64_t) * np);
+  if (icm) memcpy(icm, e->icm, sizeof(e->icm));
+  return 0;
+}
+
+int64_t or_apt_sweeps(const or_apt *a) { return a ? a->sweeps_done : -1; }
+
+/* ---------------- adaptive ladder ---------------- */
+/* Preprocessing of Algorithm S2 (Methods, "APT details"): n_chains chains
+ * run `sweeps` sweeps at beta_t, warm-started from the previous step's
+ * states; each chain's energy variance comes from its last `tail`
+ * post-sweep energies; sigma_E is the square root of the chains' mean
+ * variance; beta_{t+1} = beta_t + alpha / sigma_E; stop at the first beta
+ * whose sigma_E < tol. */
+int or_adaptive_ladder(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+                       const int8_t *h, uint32_t entry, uint64_t seed, double beta0,
+                       double alpha, int n_chains, int sweeps, int tail, double tol,
+                       int max_len, double *beta_out, double *sigma_out, int *len_out) {
+  if (n_chains < 1 || sweeps < 1 || tail < 2 || tail > sweeps || max_len < 1 || !(beta0 > 0))
+    return -1;
+  or_lat L;
+  int rc = or_lat_init(&L, dims, periodic);
+  if (rc) return rc;
+  int N = L.N;
+  int64_t Imax = or_field_bound(&L, J, h);
+  int8_t *spin = (int8_t *)malloc((size_t)n_chains * N);
+  int32_t *temp_of = (int32_t *)calloc((size_t)n_chains, sizeof(int32_t));
+  int64_t *sE = (int64_t *)malloc(sizeof(int64_t) * n_chains);
+  int64_t *sE2 = (int64_t *)malloc(sizeof(int64_t) * n_chains);
+  init_spins(&L, n_chains, spin, seed, entry, OR_TAG_LAD_INIT);
+  double beta = beta0;
+  int len = 0, status = 1;
+  uint32_t s = 0;
+  while (len < max_len) {
+    uint32_t *tab = make_table(beta, Imax);
+    memset(sE, 0, sizeof(int64_t) * n_chains);
+    memset(sE2, 0, sizeof(int64_t) * n_chains);
+    for (int k = 0; k < sweeps; ++k, ++s) {
+      gibbs_sweep(&L, J, h, Imax, n_chains, spin, temp_of, &tab, seed, entry, s,
+                  OR_TAG_LAD_SWEEP, OR_TAG_LAD_REFINE);
+      if (k >= sweeps - tail) {
+        for (int b = 0; b < n_chains; ++b) {
+          int64_t E = or_energy_lat(&L, J, h, spin + (size_t)b * N);
+          sE[b] += E;
+          sE2[b] += E * E;
+        }
+      }
+    }
+    free(tab);
+    double mean_var = 0.0;
+    for (int b = 0; b < n_chains; ++b) {
+      int64_t num = (int64_t)tail * sE2[b] - sE[b] * sE[b];
+      mean_var += (double)num / ((double)tail * (double)(tail - 1));
+    }
+    mean_var /= (double)n_chains;
+    double sigma = sqrt(mean_var);
+    beta_out[len] = beta;
+    if (sigma_out) sigma_out[len] = sigma;
+    ++len;
+    if (sigma < tol) { status = 0; break; }
+    beta = beta + alpha / sigma;
+  }
+  *len_out = len;
+  free(spin); free(temp_of); free(sE); free(sE2);
+  or_lat_free(&L);
+  return status;
+}
+
+/* ---------------- pilot histograms ---------------- */
+int or_pilot_hist(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+                  const int8_t *h, uint32_t entry, uint64_t seed, int n_beta,
+                  const double *betas, int chains_per_beta, int sweeps, int burn,
+                  int n_bins, int64_t *counts) {
+  if (n_beta < 1 || chains_per_beta < 1 || sweeps < 1 || burn < 0 || burn >= sweeps ||
+      n_bins < 1)
+    return -1;
+  or_lat L;
+  int rc = or_lat_init(&L, dims, periodic);
+  if (rc) return rc;
+  int N = L.N, B = n_beta * chains_per_beta;
+  int64_t Imax = or_field_bound(&L, J, h);
+  int8_t *spin = (int8_t *)malloc((size_t)B * N);
+  int32_t *temp_of = (int32_t *)malloc(sizeof(int32_t) * B);
+  uint32_t **tab = (uint32_t **)malloc(sizeof(uint32_t *) * n_beta);
+  for (int b = 0; b < B; ++b) temp_of[b] = b / chains_per_beta;
+  for (int t = 0; t < n_beta; ++t) tab[t] = make_table(betas[t], Imax);
+  memset(counts, 0, sizeof(int64_t) * (size_t)n_beta * n_bins);
+  init_spins(&L, B, spin, seed, entry, OR_TAG_PIL_INIT);
+  int64_t span = 3 * (int64_t)N;
+  for (int s = 0; s < sweeps; ++s) {
+    gibbs_sweep(&L, J, h, Imax, B, spin, temp_of, tab, seed, entry, (uint32_t)s,
+                OR_TAG_PIL_SWEEP, OR_TAG_PIL_REFINE);
+    if (s < burn) continue;
+    for (int b = 0; b < B; ++b) {
+      int64_t E = or_energy_lat(&L, J, h, spin + (size_t)b * N);
+      int64_t num = (E + span) * n_bins;
+      int64_t bin = num < 0 ? 0 : num / span;
+      if (bin > n_bins - 1) bin = n_bins - 1;
+      counts[(size_t)temp_of[b] * n_bins + bin]++;
+    }
+  }
+  for (int t = 0; t < n_beta; ++t) free(tab[t]);
+  free(tab); free(spin); free(temp_of);
+  or_lat_free(&L);
+  return 0;
+}

@@ -1,0 +1,117 @@
+/*
+ * CPU oracle for the probabilistic-computer Monte Carlo of arXiv 2503.10302.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, slow, obviously-correct C that restates
+ * the paper's method step by step (p-bit / Gibbs updates, Eqs. synapse and
+ * neuron; the Edwards-Anderson energy, Eqs. EAmodel and ising_energy; the
+ * replica-exchange rule of Sec. "Comparison with Adaptive Parallel
+ * Tempering"; ICMop and the adaptive beta ladder of Algorithm S2; DT-SQA of
+ * Eq. S.3 and Algorithm S1).  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header,
+ * table or constant generator with the CUDA library.
+ *
+ * All functions return 0 on success and a negative value on invalid input.
+ *
+ * Randomness contract (both implementations follow it; each has its own
+ * Philox4x32-10 written from Salmon et al., SC'11):
+ *   key  = (seed & 0xffffffff, seed >> 32)
+ *   half v_i of a Philox output block x[0..3], i in 0..7:
+ *        (x[i >> 1] >> (16 * (i & 1))) & 0xffff
+ *   sampler replica ("buffer") b of problem entry e: group g = b >> 3,
+ *   nibble i = b & 7.  A site lin of colour c = (x+y+z)&1 has colour-local
+ *   index j = lin >> 1.
+ *   update uniform u (32 bits) at sweep s:
+ *        hi = v_i(Philox((j, s, (c<<16)|g, (e<<8)|TAG_MAIN)))
+ *        lo = v_i(Philox((j, s, (c<<16)|g, (e<<8)|TAG_REFINE)))
+ *        u  = (hi << 16) | lo;   sigma <- +1 iff u < T(beta, I)
+ *   initial spin: +1 iff v_i(Philox((j, 0, (c<<16)|g, (e<<8)|TAG_INIT))) < 0x8000
+ */
+#ifndef PCOMP_ORACLE_H
+#define PCOMP_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  OR_TAG_APT_INIT = 1, OR_TAG_APT_SWEEP = 2, OR_TAG_APT_REFINE = 3,
+  OR_TAG_SWAP = 4, OR_TAG_ICM = 5,
+  OR_TAG_LAD_INIT = 6, OR_TAG_LAD_SWEEP = 7, OR_TAG_LAD_REFINE = 8,
+  OR_TAG_PIL_INIT = 9, OR_TAG_PIL_SWEEP = 10, OR_TAG_PIL_REFINE = 11,
+  OR_TAG_SQA_INIT = 12, OR_TAG_SQA_SWEEP = 13, OR_TAG_SQA_REFINE = 14
+};
+
+/* Philox4x32-10 on one counter. */
+void or_philox(const uint32_t ctr[4], uint64_t seed, uint32_t out[4]);
+/* n counters [n][4] -> n blocks [n][4]. */
+void or_philox_many(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out);
+
+/* Acceptance thresholds (uint32, compared with a uniform 32-bit u). */
+uint32_t or_pbit_threshold(double beta, int64_t I);   /* floor(2^32 / (1+exp(-2 beta I))) */
+uint32_t or_swap_threshold(double dbeta, int64_t dE); /* floor(2^32 exp(dbeta dE)), dE < 0 */
+int32_t  or_jperp_q(double gamma, int P, double T);   /* round(2^16 J_perp) */
+uint32_t or_sqa_threshold(double beta_eff, int64_t I, int32_t jq, int n);
+
+/* Energy E = -sum_bonds J s s - sum h s of one configuration (int64). */
+int or_energy(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+              const int8_t *h, const int8_t *spin, int64_t *E_out);
+
+/* ---------------- adaptive parallel tempering (Algorithm S2) ---------------- */
+typedef struct or_apt or_apt;
+/* n_inst problems; dims/periodic [n][3]; J concatenated [sum N][3];
+   h concatenated [sum N] or NULL; n_temps[n]; betas concatenated. */
+int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *periodic,
+                  const int8_t *J, const int8_t *h, const int32_t *n_temps,
+                  const double *betas, int n_labels, uint64_t seed, uint32_t entry0);
+void or_apt_destroy(or_apt *a);
+/* n_swaps swap attempts, each preceded by sweeps_per_swap sweeps.
+   icm: 0 off, 1 on.  threads: OpenMP threads over problems (<=0: default). */
+int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int threads);
+int or_apt_set_target(or_apt *a, int inst, int64_t e_target);
+/* spins [B][N] in buffer order; energies [B]; temp index of each buffer [B]. */
+int or_apt_state(const or_apt *a, int inst, int8_t *spins, int64_t *energies, int32_t *temp_of);
+/* best energy, sweep count when found, buffer, target hit sweep (-1: never). */
+int or_apt_best(const or_apt *a, int inst, int64_t *E, int64_t *sweep, int32_t *buf,
+                int64_t *hit_sweep, int8_t *spins /* nullable [N] */);
+/* swap attempts / accepts [n_temps-1][n_labels]; icm counters [3]:
+   empty overlap, cluster flips, whole-replica flips. */
+int or_apt_stats(const or_apt *a, int inst, int64_t *att, int64_t *acc, int64_t *icm);
+int64_t or_apt_sweeps(const or_apt *a);
+/* One ICMop on two configurations (ctr = (r, t, p, (entry<<8)|TAG_ICM));
+   returns 0 no overlap mismatch, 1 cluster flipped in both, 2 one whole
+   replica flipped; *cluster_size = size of the grown cluster. */
+int or_icm_apply(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb,
+                 uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p,
+                 int64_t *cluster_size);
+
+/* ---------------- adaptive beta ladder (Algorithm S2 preprocessing) --------- */
+/* beta_out/sigma_out have room for max_len; *len_out = ladder length;
+   returns 1 (not 0) if max_len was reached before sigma_E < tol. */
+int or_adaptive_ladder(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+                       const int8_t *h, uint32_t entry, uint64_t seed, double beta0,
+                       double alpha, int n_chains, int sweeps, int tail, double tol,
+                       int max_len, double *beta_out, double *sigma_out, int *len_out);
+
+/* ---------------- pilot-run energy histograms ---------------- */
+/* counts [n_beta][n_bins]: post-sweep energies of sweeps burn..sweeps-1 of
+   chains_per_beta chains at each beta; bin = floor(n_bins (E+3N)/(3N)),
+   clamped to [0, n_bins-1] (E/N over [-3, 0]). */
+int or_pilot_hist(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+                  const int8_t *h, uint32_t entry, uint64_t seed, int n_beta,
+                  const double *betas, int chains_per_beta, int sweeps, int burn,
+                  int n_bins, int64_t *counts);
+
+/* ---------------- DT-SQA (Eq. S.3, Algorithm S1) ---------------- */
+/* R runs (global ids run0..run0+R-1) of P slices; E_out [R][P] final classical
+   slice energies; spins_out [R][P][N] or NULL. */
+int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+                  int P, double T, int n_sweeps, const double *gamma, int R,
+                  uint32_t run0, uint64_t seed, int64_t *E_out, int8_t *spins_out,
+                  int threads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

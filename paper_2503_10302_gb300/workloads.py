@@ -1,0 +1,131 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the CPU oracle.
+
+This module holds input generators only: the coupling realisations of the
+3D Edwards-Anderson +-J model (each J_ij drawn from {-1,+1} with equal
+probability on nearest-neighbour bonds of a periodic simple-cubic lattice),
+the geometric beta ladders and the linear transverse-field schedules that the
+workloads name, and the workload shapes themselves.  None of the method's
+arithmetic (sweeps, thresholds, swaps, cluster moves, energies, ladders) lives
+here; the random numbers the method itself draws come from each side's own
+Philox4x32-10.
+
+Coupling layout used everywhere: ``J[lin, d]`` is the coupling of the forward
+bond of site ``lin = x + Lx*(y + Ly*z)`` along axis d (0:+x, 1:+y, 2:+z),
+int8 in {-1,+1}; with periodic boundaries every site has all three.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+# seed streams for instance families (instance i of a family uses [family, i])
+SEED_INSTANCES = 1000
+SEED_TRAIN = 2000
+SEED_EVAL = 3000
+SEED_MIXED = 4000
+
+
+def ea_couplings(dims: Sequence[int], seed: int, index: int = 0) -> np.ndarray:
+    """+-J couplings for one periodic lattice, shape [N, 3], int8."""
+    lx, ly, lz = (int(v) for v in dims)
+    n = lx * ly * lz
+    rng = np.random.Generator(np.random.Philox(key=[seed, index]))
+    bits = rng.integers(0, 2, size=(n, 3), dtype=np.int8)
+    return (2 * bits - 1).astype(np.int8)
+
+
+def geometric_ladder(n_temps: int, beta_min: float = 0.2, beta_max: float = 3.0) -> np.ndarray:
+    """beta_r = beta_min * (beta_max/beta_min)**(r/(n-1)), r = 0..n-1."""
+    if n_temps == 1:
+        return np.array([beta_min], dtype=np.float64)
+    r = np.arange(n_temps, dtype=np.float64) / (n_temps - 1)
+    return beta_min * (beta_max / beta_min) ** r
+
+
+def linear_gamma_schedule(n_sweeps: int, gamma0: float = 3.0, gamma1: float = 1e-3) -> np.ndarray:
+    """Gamma_s = gamma0 + (gamma1 - gamma0) * s/(S-1), s = 0..S-1."""
+    if n_sweeps == 1:
+        return np.array([gamma0], dtype=np.float64)
+    s = np.arange(n_sweeps, dtype=np.float64)
+    return gamma0 + (gamma1 - gamma0) * s / (n_sweeps - 1)
+
+
+@dataclasses.dataclass
+class AptBatch:
+    """A batch of APT problems: one entry per instance."""
+    dims: np.ndarray          # [n, 3] int32
+    J: List[np.ndarray]       # per instance [N, 3] int8
+    betas: List[np.ndarray]   # per instance [n_temps] float64
+    n_labels: int
+
+    @property
+    def n(self) -> int:
+        return len(self.J)
+
+    def spins_per_sweep(self) -> int:
+        return int(sum(int(np.prod(d)) * len(b) * self.n_labels for d, b in zip(self.dims, self.betas)))
+
+
+def apt_single(L: int = 4, n_temps: int = 8, n_labels: int = 2, seed: int = SEED_INSTANCES,
+               index: int = 0) -> AptBatch:
+    """One periodic L^3 instance with a geometric 0.2-3.0 ladder."""
+    dims = np.array([[L, L, L]], dtype=np.int32)
+    return AptBatch(dims, [ea_couplings((L, L, L), seed, index)], [geometric_ladder(n_temps)], n_labels)
+
+
+def apt_uniform_batch(n_inst: int, L: int, n_temps: int, n_labels: int = 2,
+                      seed: int = SEED_INSTANCES) -> AptBatch:
+    dims = np.tile(np.array([L, L, L], dtype=np.int32), (n_inst, 1))
+    J = [ea_couplings((L, L, L), seed, i) for i in range(n_inst)]
+    return AptBatch(dims, J, [geometric_ladder(n_temps) for _ in range(n_inst)], n_labels)
+
+
+def apt_mixed_batch(n_inst: int = 256, sizes: Sequence[int] = (6, 8, 10, 12, 14, 16),
+                    temps: Tuple[int, int] = (24, 32), n_labels: int = 2,
+                    seed: int = SEED_MIXED) -> AptBatch:
+    """Mixed-size batch: L uniform over `sizes`, n_temps uniform over [temps]."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, 0xFFFF]))
+    Ls = rng.choice(np.asarray(sizes), size=n_inst)
+    nts = rng.integers(temps[0], temps[1] + 1, size=n_inst)
+    dims = np.stack([Ls, Ls, Ls], axis=1).astype(np.int32)
+    J = [ea_couplings((int(L),) * 3, seed, i) for i, L in enumerate(Ls)]
+    return AptBatch(dims, J, [geometric_ladder(int(t)) for t in nts], n_labels)
+
+
+@dataclasses.dataclass
+class SqaWorkload:
+    dims: Tuple[int, int, int]
+    J: np.ndarray            # [N, 3] int8
+    P: int                   # Trotter slices
+    R: int                   # independent runs
+    T: float                 # temperature
+    gamma: np.ndarray        # [S] float64
+
+    def flips_per_anneal(self) -> int:
+        return int(np.prod(self.dims)) * self.P * self.R * len(self.gamma)
+
+
+def sqa_workload(L: int = 8, P: int = 64, R: int = 256, T: float = 0.05, n_sweeps: int = 10000,
+                 gamma0: float = 3.0, gamma1: float = 1e-3, seed: int = SEED_INSTANCES,
+                 index: int = 0) -> SqaWorkload:
+    return SqaWorkload((L, L, L), ea_couplings((L, L, L), seed, index), P, R, T,
+                       linear_gamma_schedule(n_sweeps, gamma0, gamma1))
+
+
+def random_spins(n: int, seed: int) -> np.ndarray:
+    """+-1 int8 spins (used only for host-logic tests of energy routines)."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, 0xABCD]))
+    return (2 * rng.integers(0, 2, size=n, dtype=np.int8) - 1).astype(np.int8)
+
+
+def mlp_init(sizes: Sequence[int], seed: int) -> List[Tuple[np.ndarray, np.ndarray]]:
+    """He-uniform initial weights [out, in] and zero biases, float32."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, 0x4D4C50]))
+    params = []
+    for fan_in, fan_out in zip(sizes[:-1], sizes[1:]):
+        bound = np.sqrt(6.0 / fan_in)
+        W = rng.uniform(-bound, bound, size=(fan_out, fan_in)).astype(np.float32)
+        params.append((W, np.zeros(fan_out, dtype=np.float32)))
+    return params
