@@ -1,0 +1,204 @@
+/*
+ * pcomp: GB300 (sm_103a) probabilistic-computer Monte Carlo for 3D +-J
+ * Edwards-Anderson spin glasses, after arXiv 2503.10302 ("Pushing the
+ * Boundary of Quantum Advantage in Hard Combinatorial Optimization with
+ * Probabilistic Computers").
+ *
+ * C ABI.  Plain pointers and sizes only.  Unless a name ends in _dev, every
+ * pointer argument is a HOST pointer owned by the caller; the library never
+ * keeps a caller pointer after a call returns.  Device memory behind a
+ * context is owned by the context and freed by pc_destroy.  *_dev calls
+ * take DEVICE pointers owned by the caller, valid on the context's device,
+ * and enqueue work on the context's stream without synchronising.
+ *
+ * Every int-returning call returns PC_OK (0) or a negative PC_E* code and
+ * sets a thread-local message readable with pc_last_error().  No call
+ * aborts the process.  Kernels contain no unbounded waits.
+ *
+ * Lattices: dims = (Lx, Ly, Lz), site lin = x + Lx*(y + Ly*z), all three
+ * axes periodic, every dimension even, 2 <= Lx <= 16, Ly, Lz >= 2,
+ * N = Lx*Ly*Lz <= 4096.  Couplings J are int8 [N][3]: the forward bond of
+ * site lin along +x, +y, +z, each in {-1, +1} (Eq. EAmodel).  No field
+ * (h = 0) on this path.
+ *
+ * Randomness contract (shared with the CPU oracle, which has its own
+ * code): Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed;
+ * every draw is a counter (c0, c1, c2, c3) whose 8 16-bit halves feed 8
+ * spins of one "group" of 8 replicas (or 8 Trotter slices); a spin's
+ * 32-bit uniform is (main half << 16) | (refine half).  See the oracle's
+ * header and DESIGN notes for the exact counters.
+ */
+#ifndef PCOMP_H
+#define PCOMP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PC_OK 0
+#define PC_EINVAL (-1)   /* bad argument / unsupported shape */
+#define PC_ENOMEM (-2)   /* host or device allocation failed */
+#define PC_ECUDA (-3)    /* CUDA runtime error (message has the detail) */
+#define PC_ESTATE (-4)   /* call out of order (e.g. run before load) */
+#define PC_EDEVICE (-5)  /* a kernel reported a failed device-side check */
+
+typedef struct pc_ctx pc_ctx;
+
+/* Context on CUDA device `device` with Philox seed `seed`.  All launches go
+ * to the context's stream (a new non-blocking stream unless pc_set_stream
+ * names another). */
+int pc_create(pc_ctx **out, int device, uint64_t seed);
+void pc_destroy(pc_ctx *ctx);
+const char *pc_last_error(void);
+/* Use `stream` (a cudaStream_t, or NULL for the legacy default stream). */
+int pc_set_stream(pc_ctx *ctx, void *stream);
+int pc_synchronize(pc_ctx *ctx);
+int pc_device_sm_count(pc_ctx *ctx, int *sms);
+
+/* Device Philox4x32-10 on n host counters [n][4] -> host out [n][4] (the
+ * generator of the randomness contract; used to check it on the GPU). */
+int pc_philox(pc_ctx *ctx, int64_t n, const uint32_t *ctr, uint32_t *out);
+
+/* ------------------------------------------------------------------------
+ * Thresholds (host functions; the CUDA kernels read these tables).
+ * Eq. neuron gives P(s = +1) = (1 + tanh(beta I)) / 2 = 1/(1 + e^{-2 beta I});
+ * the threshold is floor(2^32 P) clamped to 2^32 - 1 and a spin becomes +1
+ * iff its 32-bit uniform is below it.
+ * ---------------------------------------------------------------------- */
+uint32_t pc_pbit_threshold(double beta, int I);
+/* Replica exchange (Sec. "Comparison with Adaptive Parallel Tempering"):
+ * p_swap = min(1, exp(dbeta dE)); threshold floor(2^32 exp(dbeta dE)) for
+ * dbeta dE < 0. */
+uint32_t pc_swap_threshold(double dbeta, int64_t dE);
+/* Eq. S.3 multiplied by P: J_perp = -(P T / 2) ln tanh(Gamma / (P T)),
+ * returned in Q16.16 (round to nearest). */
+int32_t pc_jperp_q(double gamma, int P, double T);
+
+/* ------------------------------------------------------------------------
+ * Adaptive parallel tempering with isoenergetic cluster moves
+ * (Algorithm S2; Methods "APT details").
+ * ---------------------------------------------------------------------- */
+/* Load a batch of n_inst problems: dims [n][3], J concatenated [sum N][3],
+ * n_temps [n], betas concatenated (strictly increasing per problem),
+ * n_labels in {1, 2} replicas per temperature (ICM needs 2), and
+ * n_temps * n_labels <= 64.  Problem i uses entry id entry0 + i in its
+ * Philox counters.  Builds the p-bit and swap tables, draws the random
+ * initial state (Algorithm S2 "Initialize all replicas to random states")
+ * and resets counters, best energies and statistics.  Replaces any batch
+ * loaded before. */
+int pc_apt_load(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
+                const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0);
+/* n_swaps swap attempts; each = sweeps_per_swap checkerboard sweeps of all
+ * replicas, replica energies, best-energy update, (icm != 0) one ICMop per
+ * temperature on its two labels and a second best update, then the
+ * neighbour swaps of that attempt's parity.  Resumable: state, counters and
+ * statistics carry over between calls.  Enqueued on the context stream. */
+int pc_apt_run(pc_ctx *ctx, int64_t n_swaps, int sweeps_per_swap, int icm);
+/* Sweeps and swap attempts done since pc_apt_load. */
+int pc_apt_progress(pc_ctx *ctx, int64_t *sweeps, int64_t *swaps);
+/* Target energy for time-to-target: the first sweep count at which the
+ * best energy is <= e_target is recorded as the hit sweep. */
+int pc_apt_set_target(pc_ctx *ctx, int inst, int64_t e_target);
+/* Replica spins [B][N] int8 +-1 (buffer order, lin order), energies [B],
+ * temperature index of each buffer [B]; any output may be NULL.
+ * B = n_temps * n_labels; buffer b starts at temperature b / n_labels with
+ * label b % n_labels and keeps its label. */
+int pc_apt_get_state(pc_ctx *ctx, int inst, int8_t *spins, int64_t *energies, int32_t *temp_of);
+/* Best energy seen at a measurement point, the sweep count then, the
+ * buffer, the hit sweep (-1 if the target was never reached), and the
+ * best state [N] (nullable). */
+int pc_apt_get_best(pc_ctx *ctx, int inst, int64_t *E, int64_t *sweep, int32_t *buf,
+                    int64_t *hit_sweep, int8_t *spins);
+/* Best energies [n_inst] and hit sweeps [n_inst] of all problems. */
+int pc_apt_get_best_all(pc_ctx *ctx, int64_t *E, int64_t *hit_sweep);
+/* Swap attempts / accepts [n_temps-1][n_labels]; icm [3] = (empty
+ * overlap, cluster flips, whole-replica flips). */
+int pc_apt_get_stats(pc_ctx *ctx, int inst, int64_t *att, int64_t *acc, int64_t *icm);
+/* The tables the kernels use: p-bit thresholds [n_temps][7] for I = 2c - 6,
+ * c = 0..6, and the swap table of pair (r, r+1): entry k = threshold for
+ * dE = -2k, k = 0..len-1 (entries past len are 0). */
+int pc_apt_get_pbit_table(pc_ctx *ctx, int inst, uint32_t *out);
+int pc_apt_get_swap_table(pc_ctx *ctx, int inst, int pair, uint32_t *out, int max_len, int *len);
+
+/* ------------------------------------------------------------------------
+ * Discrete-time simulated quantum annealing (Eq. S.3, Algorithm S1).
+ * ---------------------------------------------------------------------- */
+/* One instance (dims, J) with P Trotter slices (P a multiple of 16,
+ * N * P <= 262144), temperature T and the transverse-field schedule
+ * gamma[n_sweeps] (all > 0).  Builds J_perp (Q16.16) and the per-sweep
+ * threshold tables and uploads everything. */
+int pc_sqa_setup(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, double T,
+                 int n_sweeps, const double *gamma);
+/* Threshold table of sweep s: out[3][7] for n = s_{k-1} + s_{k+1} in
+ * {-2, 0, 2} and intra-slice field I = 2c - 6; *jq = J_perp in Q16.16. */
+int pc_sqa_get_table(pc_ctx *ctx, int sweep, uint32_t *out, int32_t *jq);
+/* Anneal R independent runs (global run ids run0 .. run0+R-1) from random
+ * states through the whole schedule.  Outputs (host, nullable): E_out
+ * [R][P] final classical slice energies (full J, no J_perp term), spins_out
+ * [R][P][N] final slice spins (lin order). */
+int pc_sqa_run(pc_ctx *ctx, int R, uint32_t run0, int64_t *E_out, int8_t *spins_out);
+/* Device-buffer variant: E_dev [R][P] int32 and best_dev [R][2] int32
+ * (minimum slice energy, its slice index; lowest index on ties). */
+int pc_sqa_run_dev(pc_ctx *ctx, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev);
+/* One call from host data to host results: setup + run + copy back. */
+int pc_sqa_anneal(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, double T,
+                  int n_sweeps, const double *gamma, int R, uint32_t run0, int64_t *E_out);
+
+/* ------------------------------------------------------------------------
+ * Adaptive beta ladder (Algorithm S2 preprocessing; Methods: beta_0 = 0.5,
+ * alpha = 1.25, 100 chains, 10^4 sweeps, variance from the last 10^3).
+ * ---------------------------------------------------------------------- */
+/* For each of n_inst instances (dims [n][3], J concatenated, Philox entry
+ * entry0 + i): n_chains chains sweep `sweeps` times at beta_t (warm start),
+ * sigma_E = sqrt(mean over chains of the unbiased variance of the last
+ * `tail` post-sweep energies), beta_{t+1} = beta_t + alpha / sigma_E, until
+ * sigma_E < tol.  Outputs [n][max_len] betas and sigmas, len [n], and
+ * converged [n] (0 if max_len was reached first). */
+int pc_adaptive_ladder(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
+                       uint32_t entry0, double beta0, double alpha, int n_chains, int sweeps,
+                       int tail, double tol, int max_len, double *beta_out, double *sigma_out,
+                       int32_t *len_out, int32_t *converged_out);
+/* Piecewise-linear resampling of a ladder to n points in normalised index,
+ * endpoints kept (host). */
+int pc_resample_ladder(const double *beta, int len, int n, double *out);
+
+/* ------------------------------------------------------------------------
+ * Learned ladder: pilot histograms, features and the MLP predictor.
+ * ---------------------------------------------------------------------- */
+/* Energy histograms of a short pilot run: for each instance, n_beta
+ * temperatures x chains_per_beta chains, post-sweep energies of sweeps
+ * burn..sweeps-1, bin = floor(n_bins (E + 3N) / (3N)) clamped to
+ * [0, n_bins-1].  counts [n][n_beta][n_bins]. */
+int pc_pilot_hist(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
+                  uint32_t entry0, int n_beta, const double *betas, int chains_per_beta,
+                  int sweeps, int burn, int n_bins, int64_t *counts);
+/* [cbrt(N)/16, fraction of J > 0, fraction of frustrated plaquettes]. */
+int pc_instance_features(const int32_t *dims, const int8_t *J, double *out3);
+
+/* MLP 259 -> 256 -> 256 -> 256 -> 32 (ReLU hidden), head
+ * beta_k = beta_min + sum_{m<=k} softplus(o_m), loss = mean (beta - y)^2,
+ * fp32 on the GPU, Adam.  W[l] is [out][in] row-major, b[l] is [out]. */
+typedef struct pc_mlp pc_mlp;
+int pc_mlp_create(pc_ctx *ctx, pc_mlp **out, const float *const *W, const float *const *b,
+                  float beta_min);
+void pc_mlp_destroy(pc_mlp *m);
+/* X [batch][259] -> beta [batch][32] (host). */
+int pc_mlp_forward(pc_mlp *m, int batch, const float *X, float *beta);
+/* Loss and gradients without updating (host outputs, [out][in] / [out]). */
+int pc_mlp_grads(pc_mlp *m, int batch, const float *X, const float *Y, float *loss,
+                 float *const *gW, float *const *gb);
+/* One Adam step (lr, b1 = 0.9, b2 = 0.999, eps = 1e-8) on a minibatch;
+ * *loss = loss before the step (nullable). */
+int pc_mlp_train_step(pc_mlp *m, int batch, const float *X, const float *Y, float lr,
+                      float *loss);
+/* Device-buffer training step: X_dev [batch][259], Y_dev [batch][32]. */
+int pc_mlp_train_step_dev(pc_mlp *m, int batch, const float *X_dev, const float *Y_dev,
+                          float lr, float *loss_dev);
+int pc_mlp_get_params(pc_mlp *m, float *const *W, float *const *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

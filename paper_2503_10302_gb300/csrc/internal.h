@@ -1,0 +1,52 @@
+// Host-side declarations shared by the C-ABI layer and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pcomp.h"
+
+namespace pc {
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define PC_CUDA_TRY(call)                                                          \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return ::pc::fail(PC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ---------------------------------------------------------------- lattice
+struct Lattice {
+  int L[3];
+  int N;
+};
+// jneg byte of every site: bit d set iff the coupling on direction d
+// (0:+x 1:-x 2:+y 3:-y 4:+z 5:-z) is -1.
+std::vector<uint8_t> pack_jneg(const Lattice &lat, const int8_t *J);
+int check_lattice(const int32_t *dims, const int8_t *J, Lattice *out);
+uint32_t recip32(uint32_t d);   // ceil(2^32 / d)
+
+// ---------------------------------------------------------------- DT-SQA
+struct SqaArgs {
+  int Lx, Ly, Lz, N, P, NB, S;
+  uint32_t mLx, mLy;       // reciprocals of Lx and Ly
+  uint32_t run0, k0, k1;
+  const uint8_t *jneg;     // [N]
+  const uint32_t *table;   // [S][24]: index c + 8 m
+  int32_t *E;              // [R][P]
+  int32_t *best;           // [R][2] (nullable)
+  int8_t *spins;           // [R][P][N] (nullable)
+};
+size_t sqa_smem_bytes(int N, int P);
+int sqa_launch(const SqaArgs &a, int R, cudaStream_t st);
+
+// ---------------------------------------------------------------- Philox check
+int philox_launch(const uint32_t *ctr, uint32_t *out, int64_t n, uint32_t k0, uint32_t k1,
+                  cudaStream_t st);
+
+}  // namespace pc

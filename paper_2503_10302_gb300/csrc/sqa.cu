@@ -1,0 +1,259 @@
+// Discrete-time simulated quantum annealing (Suzuki-Trotter mapping, Eq. S.3;
+// Algorithm S1) as one persistent CTA per independent run.
+//
+// Layout.  A run is the (d+1)-dimensional lattice of P slices of the 3D
+// lattice.  Its 4D checkerboard colour is c = (x + y + z + k) & 1, so at a
+// 3D site s of parity q the slices of colour c are k = 2m + (c ^ q).  Eight
+// consecutive m of one (colour, site) share a 32-bit word, one spin per
+// nibble (bit 0 = spin +1), block b = m >> 3.  Shared memory holds
+// W[c][b][s] for the whole run (N * P / 2 bytes).  With this packing
+//  - the six spatial neighbours of a word are the words of the other colour
+//    at the neighbouring sites with the SAME block: nibble-aligned, and the
+//    coupling J (common to all slices) is one mask per direction;
+//  - the two imaginary-time neighbours are the other colour's word at the
+//    same site and that word shifted by one nibble (carry from block b +- 1).
+// So one word yields 8 nibble-packed satisfied-bond counts (0..6) and 8
+// time-neighbour counts (0..2) with a handful of 32-bit ops, and one
+// Philox4x32-10 call supplies the 8 16-bit uniforms.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace {
+using namespace pcdev;
+
+// Site coordinates of a 3D site index.
+struct Site {
+  int s, x, y, z, q;
+  uint32_t jb;
+};
+
+__device__ __forceinline__ Site site_of(const pc::SqaArgs &a, int s, const uint8_t *jn) {
+  Site t;
+  t.s = s;
+  const int r = (int)fdiv((uint32_t)s, a.mLx);   // s / Lx
+  t.x = s - r * a.Lx;
+  t.z = (int)fdiv((uint32_t)r, a.mLy);           // r / Ly
+  t.y = r - t.z * a.Ly;
+  t.q = (t.x + t.y + t.z) & 1;
+  t.jb = jn[s];
+  return t;
+}
+
+// Neighbour of site t along direction d (0:+x 1:-x 2:+y 3:-y 4:+z 5:-z),
+// periodic boundaries.
+__device__ __forceinline__ int neighbour(const pc::SqaArgs &a, const Site &t, int d) {
+  const int LxLy = a.Lx * a.Ly;
+  switch (d) {
+    case 0: return (t.x + 1 == a.Lx) ? t.s - (a.Lx - 1) : t.s + 1;
+    case 1: return (t.x == 0) ? t.s + (a.Lx - 1) : t.s - 1;
+    case 2: return (t.y + 1 == a.Ly) ? t.s - (a.Ly - 1) * a.Lx : t.s + a.Lx;
+    case 3: return (t.y == 0) ? t.s + (a.Ly - 1) * a.Lx : t.s - a.Lx;
+    case 4: return (t.z + 1 == a.Lz) ? t.s - (a.Lz - 1) * LxLy : t.s + LxLy;
+    default: return (t.z == 0) ? t.s + (a.Lz - 1) * LxLy : t.s - LxLy;
+  }
+}
+
+// Nibble-packed counts, per block, of satisfied terms J_d s_nbr = +1 over
+// the six spatial directions (Eq. synapse with I = 2C - 6).  XOR with the
+// all-nibbles mask turns a neighbour spin into J_d s_nbr for J_d = -1.
+template <int NB>
+__device__ __forceinline__ void spatial_counts(const pc::SqaArgs &a, const uint32_t *Wo,
+                                               const Site &t, uint32_t (&C)[NB]) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b) C[b] = 0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    const int n = neighbour(a, t, d);
+    const uint32_t m = nib_mask((t.jb >> d) & 1u);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) C[b] += Wo[b * a.N + n] ^ m;
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(1024) sqa_kernel(const pc::SqaArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int N = a.N, P = a.P;
+  uint32_t *W = smem;                              // [2][NB][N]
+  uint32_t *tab = W + 2 * NB * N;                  // [2][24] full thresholds
+  uint32_t *tabh = tab + 48;                       // [2][24] high halves
+  int32_t *Eacc = reinterpret_cast<int32_t *>(tabh + 48);   // [P]
+  uint8_t *jn = reinterpret_cast<uint8_t *>(Eacc + P);      // [N]
+  const int run = blockIdx.x;
+  const uint32_t ent = a.run0 + (uint32_t)run;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const uint32_t k0 = a.k0, k1 = a.k1;
+
+  for (int i = tid; i < N; i += nt) jn[i] = a.jneg[i];
+  // Algorithm S1: all spins of all slices start random (+1 iff half < 2^15)
+  for (int idx = tid; idx < 2 * NB * N; idx += nt) {
+    const int s = idx % N, cb = idx / N, b = cb % NB, c = cb / NB;
+    const uint4 x = philox((uint32_t)s, 0u, ((uint32_t)c << 16) | (uint32_t)b,
+                           (ent << 8) | TAG_SQA_INIT, k0, k1);
+    uint32_t w = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w |= (half_lo(x, i) < 0x8000u) ? (1u << (4 * i)) : 0u;
+    W[idx] = w;
+  }
+  if (tid < 24) {
+    tab[tid] = a.table[tid];
+    tabh[tid] = a.table[tid] & 0xFFFF0000u;
+  }
+  __syncthreads();
+
+  for (int sw = 0; sw < a.S; ++sw) {
+    // the transverse coupling of this sweep lives in its threshold table;
+    // prefetch the next sweep's table into the other buffer
+    const uint32_t *T = tab + 24 * (sw & 1);
+    const uint32_t *Th = tabh + 24 * (sw & 1);
+    if (tid < 24 && sw + 1 < a.S) {
+      const uint32_t t = a.table[(size_t)(sw + 1) * 24 + tid];
+      tab[24 * ((sw + 1) & 1) + tid] = t;
+      tabh[24 * ((sw + 1) & 1) + tid] = t & 0xFFFF0000u;
+    }
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const uint32_t *Wo = W + (1 - c) * NB * N;
+      uint32_t *Wc = W + c * NB * N;
+      const uint32_t c2 = (uint32_t)c << 16;
+      for (int s = tid; s < N; s += nt) {
+        const Site t = site_of(a, s, jn);
+        const int e = c ^ t.q;   // slice parity of this word's nibbles
+        uint32_t C[NB], O[NB];
+        spatial_counts<NB>(a, Wo, t, C);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) O[b] = Wo[b * N + s];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          // time neighbours: slice k-1 and k+1 of the same site
+          const uint32_t T2 = e ? ((O[b] >> 4) | (O[(b + 1) % NB] << 28))
+                                : ((O[b] << 4) | (O[(b + NB - 1) % NB] >> 28));
+          const uint32_t M = O[b] + T2;
+          const uint32_t De = (C[b] & 0x0F0F0F0Fu) + ((M & 0x0F0F0F0Fu) << 3);
+          const uint32_t Do = ((C[b] >> 4) & 0x0F0F0F0Fu) + (((M >> 4) & 0x0F0F0F0Fu) << 3);
+          const uint4 x = philox((uint32_t)s, (uint32_t)sw, c2 | (uint32_t)b,
+                                 (ent << 8) | TAG_SQA_SWEEP, k0, k1);
+          bool tie = false;
+          uint32_t w = decide8(x, De, Do, Th, tie);
+          if (tie) {
+            const uint4 y = philox((uint32_t)s, (uint32_t)sw, c2 | (uint32_t)b,
+                                   (ent << 8) | TAG_SQA_REFINE, k0, k1);
+            w = refine8(w, x, y, De, Do, T);
+          }
+          Wc[b * N + s] = w;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // Algorithm S1: classical energy of every slice (full J, no J_perp).  Each
+  // bond has one endpoint with 3D parity 1, so E_k = 3N - 2 sum_{q(s)=1} sat.
+  for (int k = tid; k < P; k += nt) Eacc[k] = 0;
+  __syncthreads();
+  for (int c = 0; c < 2; ++c) {
+    const uint32_t *Wo = W + (1 - c) * NB * N;
+    const uint32_t *Wc = W + c * NB * N;
+    for (int s = tid; s < N; s += nt) {
+      const Site t = site_of(a, s, jn);
+      if (!t.q) continue;
+      const int e = c ^ 1;
+      uint32_t C[NB];
+      spatial_counts<NB>(a, Wo, t, C);
+      for (int b = 0; b < NB; ++b) {
+        const uint32_t w = Wc[b * N + s];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int ci = (C[b] >> (4 * i)) & 0xF;
+          const int sat = ((w >> (4 * i)) & 1u) ? ci : 6 - ci;
+          atomicAdd(&Eacc[2 * (8 * b + i) + e], sat);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < P; k += nt) {
+    Eacc[k] = 3 * N - 2 * Eacc[k];
+    a.E[(size_t)run * P + k] = Eacc[k];
+  }
+  __syncthreads();
+  if (a.best && tid == 0) {
+    int kb = 0;
+    for (int k = 1; k < P; ++k)
+      if (Eacc[k] < Eacc[kb]) kb = k;
+    a.best[2 * run] = Eacc[kb];
+    a.best[2 * run + 1] = kb;
+  }
+  if (a.spins) {
+    for (int idx = tid; idx < 2 * NB * N; idx += nt) {
+      const int s = idx % N, cb = idx / N, b = cb % NB, c = cb / NB;
+      const int r = (int)fdiv((uint32_t)s, a.mLx), x = s - r * a.Lx;
+      const int z = (int)fdiv((uint32_t)r, a.mLy), y = r - z * a.Ly;
+      const int e = c ^ ((x + y + z) & 1);
+      const uint32_t w = W[idx];
+      for (int i = 0; i < 8; ++i) {
+        const int k = 2 * (8 * b + i) + e;
+        a.spins[((size_t)run * P + k) * N + s] = ((w >> (4 * i)) & 1u) ? 1 : -1;
+      }
+    }
+  }
+}
+
+__global__ void philox_kernel(const uint32_t *ctr, uint32_t *out, int64_t n, uint32_t k0,
+                              uint32_t k1) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 x = philox(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+  out[4 * i] = x.x;
+  out[4 * i + 1] = x.y;
+  out[4 * i + 2] = x.z;
+  out[4 * i + 3] = x.w;
+}
+
+template <int NB>
+int launch_nb(const pc::SqaArgs &a, int R, cudaStream_t st) {
+  const size_t smem = pc::sqa_smem_bytes(a.N, a.P);
+  PC_CUDA_TRY(cudaFuncSetAttribute(sqa_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  int tpb = ((a.N + 31) / 32) * 32;
+  if (tpb > 1024) tpb = 1024;
+  sqa_kernel<NB><<<R, tpb, smem, st>>>(a);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+}  // namespace
+
+namespace pc {
+
+size_t sqa_smem_bytes(int N, int P) {
+  const int NB = P / 16;
+  return (size_t)2 * NB * N * 4 + 96 * 4 + (size_t)P * 4 + (size_t)N;
+}
+
+int sqa_launch(const SqaArgs &a, int R, cudaStream_t st) {
+  switch (a.NB) {
+    case 1: return launch_nb<1>(a, R, st);
+    case 2: return launch_nb<2>(a, R, st);
+    case 3: return launch_nb<3>(a, R, st);
+    case 4: return launch_nb<4>(a, R, st);
+    case 5: return launch_nb<5>(a, R, st);
+    case 6: return launch_nb<6>(a, R, st);
+    case 7: return launch_nb<7>(a, R, st);
+    case 8: return launch_nb<8>(a, R, st);
+    default: return fail(PC_EINVAL, "P must be 16 * k with 1 <= k <= 8");
+  }
+}
+
+int philox_launch(const uint32_t *ctr, uint32_t *out, int64_t n, uint32_t k0, uint32_t k1,
+                  cudaStream_t st) {
+  if (n <= 0) return PC_OK;
+  const int tpb = 256;
+  philox_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(ctr, out, n, k0, k1);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+}  // namespace pc

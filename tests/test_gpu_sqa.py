@@ -1,0 +1,102 @@
+"""DT-SQA on the GPU against the oracle: bit-exact energies and spins."""
+import numpy as np
+import pytest
+
+from paper_2503_10302_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2503_10302_gb300 import build, pcomp
+    build.build()
+    return pcomp
+
+
+def test_device_philox_equals_oracle(pc, orc):
+    rng = np.random.default_rng(3)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    for seed in (0, 0x123456789ABCDEF):
+        ctx = pc.Context(0, seed)
+        assert np.array_equal(pc.pc_philox(ctx.h, ctr), orc.philox(ctr, seed))
+        ctx.close()
+
+
+def test_sqa_tables_equal_oracle(pc, orc):
+    wl = W.sqa_workload(L=4, P=64, R=1, n_sweeps=57)
+    ctx = pc.Context(0, 1)
+    pc.pc_sqa_setup(ctx.h, wl.dims, wl.J, wl.P, wl.T, wl.gamma)
+    beta_eff = 1.0 / (wl.P * wl.T)
+    for s in (0, 1, 28, 56):
+        tab, jq = pc.pc_sqa_get_table(ctx.h, s)
+        assert jq == orc.jperp_q(wl.gamma[s], wl.P, wl.T)
+        for m, n in enumerate((-2, 0, 2)):
+            for c in range(7):
+                assert tab[m, c] == orc.sqa_threshold(beta_eff, 2 * c - 6, jq, n)
+    ctx.close()
+
+
+CASES = [
+    # dims, P, R, sweeps, seed
+    ((4, 4, 4), 16, 6, 40, 0),
+    ((8, 8, 8), 64, 3, 12, 5),
+    ((6, 4, 2), 32, 5, 30, 7),
+    ((2, 2, 2), 16, 4, 25, 9),
+    ((4, 6, 8), 48, 3, 15, 11),
+    ((10, 10, 10), 128, 2, 4, 13),
+]
+
+
+@pytest.mark.parametrize("dims,P,R,S,seed", CASES)
+def test_sqa_bit_exact(pc, orc, dims, P, R, S, seed):
+    J = W.ea_couplings(dims, W.SEED_INSTANCES, seed)
+    gamma = W.linear_gamma_schedule(S)
+    N = int(np.prod(dims))
+    run0 = 17 * seed
+    E_ref, s_ref = orc.sqa_anneal(dims, J, P, 0.05, gamma, R, run0=run0, seed=seed,
+                                  want_spins=True)
+    ctx = pc.Context(0, seed)
+    pc.pc_sqa_setup(ctx.h, dims, J, P, 0.05, gamma)
+    E, s = pc.pc_sqa_run(ctx.h, R, run0, P, N, want_spins=True)
+    ctx.close()
+    assert np.array_equal(s, s_ref)
+    assert np.array_equal(E, E_ref)
+
+
+def test_sqa_zero_sweeps_is_random_init(pc, orc):
+    dims, P = (4, 4, 4), 16
+    J = W.ea_couplings(dims, 1, 0)
+    E_ref, s_ref = orc.sqa_anneal(dims, J, P, 0.05, np.zeros(0), 3, seed=2, want_spins=True)
+    ctx = pc.Context(0, 2)
+    pc.pc_sqa_setup(ctx.h, dims, J, P, 0.05, np.zeros(0))
+    E, s = pc.pc_sqa_run(ctx.h, 3, 0, P, 64, want_spins=True)
+    assert np.array_equal(s, s_ref) and np.array_equal(E, E_ref)
+    ctx.close()
+
+
+def test_sqa_rejects_bad_shapes(pc):
+    ctx = pc.Context(0, 0)
+    J = W.ea_couplings((4, 4, 4), 1, 0)
+    for dims, P in (((4, 4, 4), 24), ((5, 4, 4), 16), ((4, 4, 4), 0), ((4, 4, 4), 144)):
+        with pytest.raises(pc.PcompError):
+            pc.pc_sqa_setup(ctx.h, dims, W.ea_couplings(dims, 1, 0), P, 0.05, np.ones(3))
+    with pytest.raises(pc.PcompError):
+        pc.pc_sqa_setup(ctx.h, (4, 4, 4), J, 16, 0.05, np.array([1.0, 0.0]))
+    ctx.close()
+
+
+def test_sqa_full_size_sampled_runs(pc, orc):
+    """The L=8, P=64, R=256, 1e4-sweep anneal in the bench's launch
+    configuration; runs 0, 137 and 255 re-computed by the oracle."""
+    wl = W.sqa_workload()
+    N = 512
+    ctx = pc.Context(0, 0)
+    pc.pc_sqa_setup(ctx.h, wl.dims, wl.J, wl.P, wl.T, wl.gamma)
+    E = pc.pc_sqa_run(ctx.h, wl.R, 0, wl.P, N)
+    ctx.close()
+    assert (E % 2 == (3 * N) % 2).all() and (E >= -3 * N).all()
+    picks = [0, 137, 255]
+    for r in picks:
+        E_ref = orc.sqa_anneal(wl.dims, wl.J, wl.P, wl.T, wl.gamma, 1, run0=r, seed=0)
+        assert np.array_equal(E[r], E_ref[0]), r
