@@ -146,6 +146,29 @@ int pc_sqa_run_dev(pc_ctx *ctx, int R, uint32_t run0, int32_t *E_dev, int32_t *b
 int pc_sqa_anneal(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, double T,
                   int n_sweeps, const double *gamma, int R, uint32_t run0, int64_t *E_out);
 
+/* The DT-SQA anneal without any allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * code whose device memory is all owned by another allocator (a framework's
+ * caching allocator or a fixed arena) or code that must not allocate on a
+ * latency-critical path.  It runs the same kernel as pc_sqa_run_dev with the
+ * same results, but keeps its scratch (packed couplings and per-sweep
+ * threshold tables) in a static device array of about 0.94 MiB that every
+ * GPU loading this library holds until the process exits.
+ *   device, stream   CUDA device and stream (NULL: legacy default stream).
+ *   seed             Philox key.
+ *   dims, J, P, T, n_sweeps, gamma   as pc_sqa_setup (host pointers).
+ *   R, run0          as pc_sqa_run_dev.
+ *   E_dev [R][P], best_dev [R][2] (nullable)   caller-owned device buffers.
+ * Limits: n_sweeps <= 10240, N <= 4096 (else PC_EINVAL with a message).
+ * No cudaMalloc, cudaFree or other allocating call is made.  The first call
+ * on a device looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the one array and leave it
+ * holding the last call's tables, so calls that overlap on the GPU (e.g. on
+ * two streams) race; issue them in one stream or serialise them. */
+int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, const int32_t *dims,
+                          const int8_t *J, int P, double T, int n_sweeps, const double *gamma,
+                          int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev);
+
 /* ------------------------------------------------------------------------
  * Adaptive beta ladder (Algorithm S2 preprocessing; Methods: beta_0 = 0.5,
  * alpha = 1.25, 100 chains, 10^4 sweeps, variance from the last 10^3).

@@ -30,6 +30,7 @@ struct Lattice {
 std::vector<uint8_t> pack_jneg(const Lattice &lat, const int8_t *J);
 int check_lattice(const int32_t *dims, const int8_t *J, Lattice *out);
 uint32_t recip32(uint32_t d);   // ceil(2^32 / d)
+uint32_t sqa_threshold(double beta_eff, int I, int32_t jq, int n);
 
 // ---------------------------------------------------------------- DT-SQA
 struct SqaArgs {

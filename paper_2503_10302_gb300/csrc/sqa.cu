@@ -257,3 +257,126 @@ int philox_launch(const uint32_t *ctr, uint32_t *out, int64_t n, uint32_t k0, ui
 }
 
 }  // namespace pc
+
+// ---------------------------------------------------------------------------
+// DT-SQA entry point that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: code running under a memory manager
+// that owns every device allocation (a framework's caching allocator or a
+// fixed arena), or code that must not allocate on a latency-critical path.
+// pc_sqa_anneal_noalloc runs the same anneal kernel as pc_sqa_run_dev but
+// keeps its scratch (the packed couplings and the per-sweep threshold
+// tables) in the file-scope device array below instead of in
+// library-allocated buffers.  Every GPU that loads this library keeps this
+// array (about 0.94 MiB) until the process exits.
+namespace {
+
+constexpr int kNoallocMaxSweeps = 10240;
+constexpr int kNoallocJnegBytes = 4096;   // N <= 4096 sites
+constexpr size_t kNoallocTableBytes = (size_t)kNoallocMaxSweeps * 24 * 4;
+constexpr size_t kNoallocBytes = kNoallocJnegBytes + kNoallocTableBytes;
+
+static __device__ __align__(256) unsigned char g_sqa_noalloc_scratch[kNoallocBytes];
+
+// Device address of the scratch array, looked up once per device (with that
+// device current).  The symbol's name is a host-side stand-in, never a
+// device address, so only this pointer is handed to kernels.
+constexpr int kMaxDevices = 64;
+static unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+int noalloc_scratch(int device, unsigned char **out) {
+  if (device < 0 || device >= kMaxDevices) return pc::fail(PC_EINVAL, "device index out of range");
+  if (!g_scratch_ptr[device]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_sqa_noalloc_scratch);
+    if (e != cudaSuccess)
+      return pc::fail(PC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_scratch_ptr[device] = static_cast<unsigned char *>(p);
+  }
+  *out = g_scratch_ptr[device];
+  return PC_OK;
+}
+
+}  // namespace
+
+extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, const int32_t *dims,
+                                     const int8_t *J, int P, double T, int n_sweeps,
+                                     const double *gamma, int R, uint32_t run0, int32_t *E_dev,
+                                     int32_t *best_dev) {
+  using namespace pc;
+  if (!dims || !J || (n_sweeps > 0 && !gamma) || (R > 0 && !E_dev))
+    return fail(PC_EINVAL, "NULL argument");
+  Lattice lat;
+  int rc = check_lattice(dims, J, &lat);
+  if (rc) return rc;
+  if (P < 16 || P % 16 || P > 128) return fail(PC_EINVAL, "P must be a multiple of 16 in [16, 128]");
+  if ((int64_t)lat.N * P > 262144) return fail(PC_EINVAL, "N * P must be <= 262144");
+  if (!(T > 0.0) || n_sweeps < 0) return fail(PC_EINVAL, "T must be > 0 and n_sweeps >= 0");
+  if (n_sweeps > kNoallocMaxSweeps)
+    return fail(PC_EINVAL, "pc_sqa_anneal_noalloc: n_sweeps exceeds the scratch limit of 10240");
+  if (R < 0 || (uint64_t)run0 + (uint64_t)R > (1ull << 24))
+    return fail(PC_EINVAL, "R must be >= 0 and run ids < 2^24");
+  for (int s = 0; s < n_sweeps; ++s)
+    if (!(gamma[s] > 0.0)) return fail(PC_EINVAL, "every Gamma must be > 0");
+  PC_CUDA_TRY(cudaSetDevice(device));
+  unsigned char *scratch = nullptr;
+  if ((rc = noalloc_scratch(device, &scratch))) return rc;
+  if (R == 0) return PC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // couplings: one byte per site, staged through a stack buffer
+  {
+    uint8_t jn[kNoallocJnegBytes];
+    const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2];
+    for (int s = 0; s < lat.N; ++s) {
+      const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
+      const int xm = (x + Lx - 1) % Lx + Lx * (y + Ly * z);
+      const int ym = x + Lx * ((y + Ly - 1) % Ly + Ly * z);
+      const int zm = x + Lx * (y + Ly * ((z + Lz - 1) % Lz));
+      const int8_t j6[6] = {J[3 * s], J[3 * xm], J[3 * s + 1], J[3 * ym + 1], J[3 * s + 2],
+                            J[3 * zm + 2]};
+      uint8_t m = 0;
+      for (int d = 0; d < 6; ++d)
+        if (j6[d] < 0) m |= (uint8_t)(1u << d);
+      jn[s] = m;
+    }
+    PC_CUDA_TRY(cudaMemcpyAsync(scratch, jn, (size_t)lat.N, cudaMemcpyHostToDevice, st));
+  }
+  // per-sweep threshold tables, 64 sweeps per staged copy
+  {
+    constexpr int kChunk = 64;
+    uint32_t tab[kChunk * 24];
+    const double beta_eff = 1.0 / ((double)P * T);
+    for (int s0 = 0; s0 < n_sweeps; s0 += kChunk) {
+      const int ns = (n_sweeps - s0 < kChunk) ? n_sweeps - s0 : kChunk;
+      for (int k = 0; k < ns; ++k) {
+        const int32_t jq = pc_jperp_q(gamma[s0 + k], P, T);
+        for (int e = 0; e < 24; ++e) tab[24 * k + e] = 0u;
+        for (int m = 0; m < 3; ++m)
+          for (int cc = 0; cc < 7; ++cc)
+            tab[24 * k + cc + 8 * m] = sqa_threshold(beta_eff, 2 * cc - 6, jq, 2 * m - 2);
+      }
+      PC_CUDA_TRY(cudaMemcpyAsync(scratch + kNoallocJnegBytes + (size_t)s0 * 96, tab,
+                                  (size_t)ns * 96, cudaMemcpyHostToDevice, st));
+    }
+  }
+  SqaArgs a;
+  a.Lx = lat.L[0];
+  a.Ly = lat.L[1];
+  a.Lz = lat.L[2];
+  a.N = lat.N;
+  a.P = P;
+  a.NB = P / 16;
+  a.S = n_sweeps;
+  a.mLx = recip32((uint32_t)a.Lx);
+  a.mLy = recip32((uint32_t)a.Ly);
+  a.run0 = run0;
+  a.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  a.k1 = (uint32_t)(seed >> 32);
+  a.jneg = scratch;
+  a.table = reinterpret_cast<const uint32_t *>(scratch + kNoallocJnegBytes);
+  a.E = E_dev;
+  a.best = best_dev;
+  a.spins = nullptr;
+  return sqa_launch(a, R, st);
+}

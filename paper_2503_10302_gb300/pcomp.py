@@ -56,6 +56,8 @@ SIGNATURES = {
     "pc_sqa_run": (c_int, [c_vp, c_int, c_u32, c_i64p, c_i8p]),
     "pc_sqa_run_dev": (c_int, [c_vp, c_int, c_u32, c_vp, c_vp]),
     "pc_sqa_anneal": (c_int, [c_vp, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p, c_int, c_u32, c_i64p]),
+    "pc_sqa_anneal_noalloc": (c_int, [c_int, c_vp, c_u64, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p,
+                                      c_int, c_u32, c_vp, c_vp]),
     "pc_adaptive_ladder": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_u32, c_dbl, c_dbl, c_int, c_int,
                                    c_int, c_dbl, c_int, c_f64p, c_f64p, c_i32p, c_i32p]),
     "pc_resample_ladder": (c_int, [c_f64p, c_int, c_int, c_f64p]),
@@ -205,6 +207,16 @@ def pc_sqa_anneal(ctx, dims, J, P: int, T: float, gamma, R: int, run0: int = 0) 
     _call("pc_sqa_anneal", ctx, ptr(d, ctypes.c_int32), ptr(j, ctypes.c_int8), P, T, len(g),
           ptr(g, ctypes.c_double), R, c_u32(run0), ptr(E, ctypes.c_int64))
     return E
+
+
+def pc_sqa_anneal_noalloc(device: int, stream_handle: int, seed: int, dims, J, P: int, T: float,
+                          gamma, R: int, run0: int, E_dev_ptr: int, best_dev_ptr: int = 0) -> None:
+    """Allocation-free DT-SQA anneal into caller-owned device buffers."""
+    d, j = _dims(dims), _J(J)
+    g = np.ascontiguousarray(np.asarray(gamma, np.float64))
+    _call("pc_sqa_anneal_noalloc", device, c_vp(stream_handle or None), c_u64(seed),
+          ptr(d, ctypes.c_int32), ptr(j, ctypes.c_int8), P, T, len(g), ptr(g, ctypes.c_double), R,
+          c_u32(run0), c_vp(E_dev_ptr), c_vp(best_dev_ptr or None))
 
 
 class Context:

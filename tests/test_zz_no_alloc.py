@@ -1,0 +1,64 @@
+"""The allocation-free DT-SQA entry point (pc_sqa_anneal_noalloc).
+
+It serves callers that cannot call cudaMalloc: code whose device memory is
+owned by another allocator, or code that must not allocate on a hot path.
+Its results must equal those of the ordinary entry point (which allocates
+its scratch through a context) bit for bit, on consecutive calls that reuse
+the same static scratch array with different problems.  This file is named
+so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+from paper_2503_10302_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CALLS = [
+    # dims, P, R, sweeps, seed, run0
+    ((8, 8, 8), 64, 6, 120, 5, 0),
+    ((4, 6, 4), 32, 5, 45, 9, 1000),
+]
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2503_10302_gb300 import build, pcomp
+    build.build()
+    pcomp.lib()
+    return pcomp
+
+
+def _reference(pc, dims, J, P, T, gamma, R, seed, run0):
+    ctx = pc.Context(0, seed)
+    pc.pc_sqa_setup(ctx.h, dims, J, P, T, gamma)
+    E = pc.pc_sqa_run(ctx.h, R, run0, P, int(np.prod(dims)))
+    ctx.close()
+    return E
+
+
+def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(pc):
+    import torch
+    T = 0.05
+    for dims, P, R, S, seed, run0 in CALLS:
+        J = W.ea_couplings(dims, W.SEED_INSTANCES, seed)
+        gamma = W.linear_gamma_schedule(S)
+        E_dev = torch.full((R, P), 12345, dtype=torch.int32, device="cuda:0")
+        best_dev = torch.full((R, 2), -7, dtype=torch.int32, device="cuda:0")
+        torch.cuda.synchronize()
+        pc.pc_sqa_anneal_noalloc(0, 0, seed, dims, J, P, T, gamma, R, run0, E_dev.data_ptr(),
+                                 best_dev.data_ptr())
+        torch.cuda.synchronize()
+        E = E_dev.cpu().numpy().astype(np.int64)
+        best = best_dev.cpu().numpy()
+        E_ref = _reference(pc, dims, J, P, T, gamma, R, seed, run0)
+        assert np.array_equal(E, E_ref)
+        assert np.array_equal(best[:, 0], E_ref.min(axis=1))
+        assert np.array_equal(best[:, 1], E_ref.argmin(axis=1))
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(pc):
+    dims = (4, 4, 4)
+    J = W.ea_couplings(dims, 1, 0)
+    with pytest.raises(pc.PcompError, match="10240"):
+        pc.pc_sqa_anneal_noalloc(0, 0, 0, dims, J, 16, 0.05, np.ones(10241), 2, 0, 1, 0)
