@@ -158,7 +158,7 @@ int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *
     }
     e->spin = (int8_t *)malloc((size_t)e->B * N);
     e->E = (int64_t *)malloc(sizeof(int64_t) * e->B);
-    e->best_spin = (int8_t *)malloc((size_t)N);
+    e->best_spin = (int8_t *)calloc((size_t)N, 1);
     e->att = (int64_t *)calloc((size_t)(e->T > 1 ? e->T - 1 : 1) * e->A, sizeof(int64_t));
     e->acc = (int64_t *)calloc((size_t)(e->T > 1 ? e->T - 1 : 1) * e->A, sizeof(int64_t));
     e->queue = (int32_t *)malloc(sizeof(int32_t) * N);

@@ -23,7 +23,9 @@ int fail(int code, const std::string &msg) {
 }
 
 uint32_t recip32(uint32_t d) {
-  // ceil(2^32 / d); exact quotients for n, d < 2^16 through __umulhi
+  // ceil(2^32 / d): exact quotients for n, d < 2^16 through __umulhi; d = 1
+  // (no 32-bit reciprocal) maps to 0, which the device divider treats as 1
+  if (d <= 1) return 0u;
   return (uint32_t)((((uint64_t)1 << 32) + d - 1) / d);
 }
 
@@ -131,7 +133,7 @@ void pc_destroy(pc_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   c->sqa.release();
-  c->apt.release();
+  pc_apt_release_impl(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -1,0 +1,710 @@
+// Adaptive parallel tempering with isoenergetic cluster moves (Algorithm S2)
+// as one persistent CTA per problem: checkerboard p-bit sweeps of every
+// replica, replica energies, best-energy tracking, Houdayer cluster moves
+// and replica exchange all run on chip between kernel launches.  The same
+// kernel also drives the chains of the adaptive-ladder preprocessing
+// (energy sums over a tail window) and of the pilot runs (energy
+// histograms).
+//
+// Layout.  Replicas ("buffers") of one problem are packed eight to a 32-bit
+// word, one spin per nibble (bit 0 = +1): group g holds buffers 8g..8g+7.
+// Sites are split by checkerboard colour c = (x+y+z)&1 and indexed inside a
+// colour by j = lin >> 1, so a word S[g][c][j] carries site (c, j) of eight
+// replicas.  All replicas of a problem share the couplings, hence one word
+// gives the nibble-packed satisfied-bond counts of eight replicas with six
+// XOR/ADD pairs, and one Philox4x32-10 call gives their eight 16-bit
+// uniforms.  Swaps exchange temperatures between buffers (the buffer ->
+// temperature map), so replica states never move.
+#include <cuda_runtime.h>
+
+#include "apt_dev.h"
+#include "device.cuh"
+#include "internal.h"
+
+namespace {
+using namespace pcdev;
+using pc::AptArgs;
+using pc::AptProbDev;
+
+constexpr int MAXGC = 4;   // groups handled per thread per site
+
+struct Geo {
+  int Lx, Ly, Lz, N, H, hx;
+  uint32_t mhx, mLy;
+};
+
+// Neighbours (other colour, colour-local index) of site (c, j), in the
+// direction order +x, -x, +y, -y, +z, -z; periodic boundaries.
+__device__ __forceinline__ void neighbours(const Geo &g, int c, int j, int (&n)[6]) {
+  const int row = (int)fdiv((uint32_t)j, g.mhx);   // j / hx
+  const int jx = j - row * g.hx;
+  const int z = (int)fdiv((uint32_t)row, g.mLy);   // row / Ly
+  const int y = row - z * g.Ly;
+  const int p = (y + z + c) & 1;                   // x = 2 jx + p
+  const int base = row * g.hx;
+  int jxp, jxm;
+  if (p == 0) {
+    jxp = jx;
+    jxm = (jx == 0) ? g.hx - 1 : jx - 1;
+  } else {
+    jxp = (jx + 1 == g.hx) ? 0 : jx + 1;
+    jxm = jx;
+  }
+  n[0] = base + jxp;
+  n[1] = base + jxm;
+  const int yp = (y + 1 == g.Ly) ? 0 : y + 1, ym = (y == 0) ? g.Ly - 1 : y - 1;
+  const int zp = (z + 1 == g.Lz) ? 0 : z + 1, zm = (z == 0) ? g.Lz - 1 : z - 1;
+  n[2] = (yp + g.Ly * z) * g.hx + jx;
+  n[3] = (ym + g.Ly * z) * g.hx + jx;
+  n[4] = (y + g.Ly * zp) * g.hx + jx;
+  n[5] = (y + g.Ly * zm) * g.hx + jx;
+}
+
+// lin = x + Lx (y + Ly z) of site (c, j).
+__device__ __forceinline__ int lin_of(const Geo &g, int c, int j) {
+  const int row = (int)fdiv((uint32_t)j, g.mhx);
+  const int jx = j - row * g.hx;
+  const int z = (int)fdiv((uint32_t)row, g.mLy);
+  const int y = row - z * g.Ly;
+  return 2 * jx + ((y + z + c) & 1) + g.Lx * row;
+}
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// Threshold of nibble i for packed count C (thr points at the group's 64
+// entries: 8 buffers x 8 counts).
+__device__ __forceinline__ uint32_t decide8_grp(const uint4 &x, uint32_t C, const uint32_t *thrh,
+                                                bool &tie) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t v = half_hi(x, i), th = thrh[8 * i + ((C >> (4 * i)) & 0xFu)];
+    w |= (v < th) ? (1u << (4 * i)) : 0u;
+    tie |= (v == th);
+  }
+  return w;
+}
+
+__device__ __noinline__ uint32_t refine8_grp(uint32_t w, uint4 x, uint4 y, uint32_t C,
+                                             const uint32_t *thr) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t t = thr[8 * i + ((C >> (4 * i)) & 0xFu)];
+    const uint32_t v = half_hi(x, i);
+    if (v == (t & 0xFFFF0000u)) {
+      const uint32_t u = v | half_lo(y, i);
+      w = (u < t) ? (w | (1u << (4 * i))) : (w & ~(1u << (4 * i)));
+    }
+  }
+  return w;
+}
+
+struct Shared {
+  uint32_t *S;       // [Gc][2][H]
+  uint32_t *thr;     // [Gc*8][8]
+  uint32_t *thrh;    // [Gc*8][8] high halves
+  int32_t *temp_of;  // [Gc*8]
+  int32_t *buf_of;   // [Gc*8]
+  int32_t *E;        // [Gc*8]
+  int32_t *Eacc;     // [Gc*8]
+  int32_t *satt, *sacc;   // [64] swap attempts / accepts of this launch
+  int32_t *hist;     // pilot histogram [T][n_bins]
+  int64_t *sum1, *sum2;   // ladder sums [Gc*8]
+  int64_t *m64;      // best E, best sweep, hit sweep, target
+  int32_t *m32;      // best buffer, flag, icm counters x3
+  uint8_t *jn;       // [2][H]
+  uint32_t *icm;     // per warp 4 x nw words
+};
+
+struct Cta {
+  Geo geo;
+  int T, A, B, Bc, Gc, g0;
+  uint32_t ent;
+  // thread chunking of the site loop: nch chunks of tpc threads, gc groups each
+  int nch, tpc, gc;
+};
+
+// One colour phase of a sweep over the CTA's groups.  UPDATE: Eq. synapse +
+// Eq. neuron for every site of colour c.  ENERGY: accumulate, per buffer,
+// the satisfied bonds of the colour-c sites (every bond has exactly one
+// colour-1 endpoint, so the colour-1 pass gives E = 3N - 2 * satisfied).
+template <bool UPDATE, bool ENERGY>
+__device__ __forceinline__ void colour_phase(const AptArgs &a, const Cta &k, const Shared &sh,
+                                             int c, uint32_t sweep) {
+  const int tid = threadIdx.x;
+  const int q = tid / k.tpc, lt = tid - q * k.tpc;
+  const int H = k.geo.H;
+  const int gbeg = q * k.gc;
+  int gcnt = k.Gc - gbeg;
+  if (gcnt > k.gc) gcnt = k.gc;
+  uint32_t acc[MAXGC][4];
+#pragma unroll
+  for (int u = 0; u < MAXGC; ++u)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[u][m] = 0;
+  const uint32_t c2 = (uint32_t)c << 16;
+  if (gcnt > 0) {
+    for (int j = lt; j < H; j += k.tpc) {
+      int n[6];
+      neighbours(k.geo, c, j, n);
+      const uint32_t jb = sh.jn[c * H + j];
+      uint32_t jm[6];
+#pragma unroll
+      for (int d = 0; d < 6; ++d) jm[d] = nib_mask((jb >> d) & 1u);
+#pragma unroll
+      for (int u = 0; u < MAXGC; ++u) {
+        if (u >= gcnt) break;
+        const int gl = gbeg + u;
+        const uint32_t *Wo = sh.S + (size_t)(2 * gl + (1 - c)) * H;
+        uint32_t C = 0;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) C += Wo[n[d]] ^ jm[d];
+        uint32_t w;
+        uint32_t *dst = sh.S + (size_t)(2 * gl + c) * H + j;
+        if (UPDATE) {
+          const uint32_t g = (uint32_t)(k.g0 + gl);
+          const uint4 x = philox((uint32_t)j, sweep, c2 | g, (k.ent << 8) | a.tag_main, a.k0, a.k1);
+          bool tie = false;
+          w = decide8_grp(x, C, sh.thrh + 64 * gl, tie);
+          if (tie) {
+            const uint4 y = philox((uint32_t)j, sweep, c2 | g, (k.ent << 8) | a.tag_ref, a.k0, a.k1);
+            w = refine8_grp(w, x, y, C, sh.thr + 64 * gl);
+          }
+          *dst = w;
+        } else {
+          w = *dst;
+        }
+        if (ENERGY) {
+          const uint32_t full = w * 0xFu;    // nibble of all ones where the spin is +1
+          const uint32_t sat = (C & full) | ((0x66666666u - C) & ~full);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) acc[u][m] += (sat >> (4 * m)) & 0x000F000Fu;
+        }
+      }
+    }
+  }
+  if (ENERGY) {
+    // lanes of a warp share the chunk q; reduce 16-bit lanes across the warp
+    const int lane = tid & 31;
+#pragma unroll
+    for (int u = 0; u < MAXGC; ++u) {
+      if (u >= gcnt) break;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        uint32_t v = acc[u][m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) {
+          const int b = 8 * (gbeg + u) + m;
+          atomicAdd(&sh.Eacc[b], (int)(v & 0xFFFFu));
+          atomicAdd(&sh.Eacc[b + 4], (int)(v >> 16));
+        }
+      }
+    }
+  }
+}
+
+// E_b = 3N - 2 * (satisfied bonds); resets the accumulators.
+__device__ __forceinline__ void finish_energies(const Cta &k, const Shared &sh) {
+  for (int b = threadIdx.x; b < 8 * k.Gc; b += blockDim.x) {
+    sh.E[b] = 3 * k.geo.N - 2 * sh.Eacc[b];
+    sh.Eacc[b] = 0;
+  }
+}
+
+// Minimum-energy selection (Algorithm S2 output): strict improvement, lowest
+// buffer index on ties; copies the state of the new best replica.
+__device__ void best_update(const AptArgs &a, const Cta &k, const Shared &sh, int p,
+                            int64_t sweeps) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int bestE = 0x7FFFFFFF, bestb = 0x7FFFFFFF;
+    for (int b = lane; b < k.Bc; b += 32) {
+      const int e = sh.E[b];
+      if (e < bestE || (e == bestE && b < bestb)) {
+        bestE = e;
+        bestb = b;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const int oe = __shfl_xor_sync(0xFFFFFFFFu, bestE, o);
+      const int ob = __shfl_xor_sync(0xFFFFFFFFu, bestb, o);
+      if (oe < bestE || (oe == bestE && ob < bestb)) {
+        bestE = oe;
+        bestb = ob;
+      }
+    }
+    if (lane == 0) {
+      int flag = 0;
+      if ((int64_t)bestE < sh.m64[0]) {
+        sh.m64[0] = bestE;
+        sh.m64[1] = sweeps;
+        sh.m32[0] = bestb;
+        flag = 1;
+      }
+      if (sh.m64[2] < 0 && sh.m64[0] <= sh.m64[3]) sh.m64[2] = sweeps;
+      sh.m32[1] = flag;
+    }
+  }
+  __syncthreads();
+  if (sh.m32[1]) {
+    const int b = sh.m32[0];
+    const int g = b >> 3, i = b & 7;
+    const AptProbDev &P = a.prob[p];
+    for (int kk = threadIdx.x; kk < k.geo.N; kk += blockDim.x) {
+      const int c = kk >= k.geo.H ? 1 : 0, j = kk - c * k.geo.H;
+      const uint32_t w = sh.S[(size_t)(2 * g + c) * k.geo.H + j];
+      a.best_spins[P.best_off + lin_of(k.geo, c, j)] = ((w >> (4 * i)) & 1u) ? 1 : -1;
+    }
+  }
+  __syncthreads();
+}
+
+// ICMop (Algorithm S2) of one pair of buffers by one warp.  Canonical site
+// order k = c*H + j.  M = mismatch bits, V = cluster bits, F/F2 = BFS
+// frontiers (warp-private shared memory).
+__device__ void icm_pair(const AptArgs &a, const Cta &k, const Shared &sh, int r, uint32_t t,
+                         int ba, int bb, uint32_t *M, uint32_t *V, uint32_t *F, uint32_t *F2) {
+  const int lane = threadIdx.x & 31;
+  const Geo &geo = k.geo;
+  const int N = geo.N, H = geo.H, nw = (N + 31) >> 5;
+  const int ga = ba >> 3, ia = ba & 7, gb = bb >> 3, ib = bb & 7;
+  uint32_t *Sa = sh.S + (size_t)2 * ga * H, *Sb = sh.S + (size_t)2 * gb * H;
+  // overlap q_i = s_i^a s_i^b: mismatch bitmask
+  int nminus = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int kk = 32 * w + lane;
+    bool mm = false;
+    if (kk < N) {
+      const int c = kk >= H ? 1 : 0, j = kk - c * H;
+      mm = (((Sa[c * H + j] >> (4 * ia)) ^ (Sb[c * H + j] >> (4 * ib))) & 1u) != 0;
+    }
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, mm);
+    if (lane == 0) M[w] = m;
+    nminus += __popc(m);
+  }
+  if (nminus == 0) {
+    if (lane == 0) atomicAdd(&sh.m32[2], 1);
+    return;
+  }
+  const uint4 x = philox((uint32_t)r, t, 0u, (k.ent << 8) | TAG_ICM, a.k0, a.k1);
+  const int kth = (int)(((uint64_t)x.x * (uint64_t)nminus) >> 32);
+  __syncwarp();
+  // the kth mismatch site in canonical order: lane owns words [lane*wpl, ...)
+  const int wpl = (nw + 31) >> 5;
+  int local = 0;
+  for (int w = lane * wpl; w < (lane + 1) * wpl && w < nw; ++w) local += __popc(M[w]);
+  int incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int excl = incl - local;
+  int seed = -1;
+  if (kth >= excl && kth < incl) {
+    int rem = kth - excl;
+    for (int w = lane * wpl; w < (lane + 1) * wpl && w < nw; ++w) {
+      const uint32_t m = M[w];
+      const int pc = __popc(m);
+      if (rem < pc) {
+        seed = 32 * w + (int)__fns(m, 0, rem + 1);
+        break;
+      }
+      rem -= pc;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) seed = max(seed, __shfl_xor_sync(0xFFFFFFFFu, seed, o));
+  // grow the cluster of the seed: level-synchronous BFS on the mismatch graph
+  for (int w = lane; w < nw; w += 32) {
+    V[w] = 0;
+    F[w] = 0;
+    F2[w] = 0;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    V[seed >> 5] = 1u << (seed & 31);
+    F[seed >> 5] = 1u << (seed & 31);
+  }
+  __syncwarp();
+  int size = 1;
+  const int half = N >> 1;
+  for (int iter = 0; iter <= N; ++iter) {
+    int added = 0;
+    for (int w = lane; w < nw; w += 32) {
+      uint32_t f = F[w];
+      if (!f) continue;
+      F[w] = 0;
+      while (f) {
+        const int bit = __ffs(f) - 1;
+        f &= f - 1;
+        const int v = 32 * w + bit;
+        const int c = v >= H ? 1 : 0, j = v - c * H;
+        int n[6];
+        neighbours(geo, c, j, n);
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+          const int u = (1 - c) * H + n[d];
+          const uint32_t mb = 1u << (u & 31);
+          if ((M[u >> 5] & mb) && !(V[u >> 5] & mb)) {
+            const uint32_t old = atomicOr(&V[u >> 5], mb);
+            if (!(old & mb)) {
+              atomicOr(&F2[u >> 5], mb);
+              ++added;
+            }
+          }
+        }
+      }
+    }
+    added = warp_sum(added);
+    size += added;
+    __syncwarp();
+    uint32_t *tmp = F;
+    F = F2;
+    F2 = tmp;
+    if (added == 0 || 2 * size > N) break;
+  }
+  (void)half;
+  if (2 * size > N) {
+    // more than half of all spins: flip one whole replica (x.y bit 0: 0 -> a, 1 -> b)
+    const int bt = (x.y & 1u) ? bb : ba;
+    const int gt = bt >> 3;
+    const uint32_t mask = 1u << (4 * (bt & 7));
+    uint32_t *St = sh.S + (size_t)2 * gt * H;
+    for (int kk = lane; kk < N; kk += 32) atomicXor(&St[kk], mask);   // [2][H] is contiguous
+    if (lane == 0) atomicAdd(&sh.m32[4], 1);
+    return;   // h = 0: energies unchanged
+  }
+  // energy change of replica a: bonds leaving the cluster change sign
+  int dEa = 0;
+  for (int w = lane; w < nw; w += 32) {
+    uint32_t f = V[w];
+    while (f) {
+      const int bit = __ffs(f) - 1;
+      f &= f - 1;
+      const int v = 32 * w + bit;
+      const int c = v >= H ? 1 : 0, j = v - c * H;
+      int n[6];
+      neighbours(geo, c, j, n);
+      const uint32_t jb = sh.jn[c * H + j];
+      const int sv = (int)((Sa[c * H + j] >> (4 * ia)) & 1u);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const int u = (1 - c) * H + n[d];
+        if (V[u >> 5] & (1u << (u & 31))) continue;
+        const int sn = (int)((Sa[(1 - c) * H + n[d]] >> (4 * ia)) & 1u);
+        // J s_v s_n = +1 iff (s_v == s_n) xor (J = -1)
+        const int prod = ((sv ^ sn ^ (int)((jb >> d) & 1u)) == 0) ? 1 : -1;
+        dEa += 2 * prod;
+      }
+    }
+  }
+  dEa = warp_sum(dEa);
+  __syncwarp();
+  const uint32_t ma = 1u << (4 * ia), mb2 = 1u << (4 * ib);
+  for (int w = lane; w < nw; w += 32) {
+    uint32_t f = V[w];
+    while (f) {
+      const int bit = __ffs(f) - 1;
+      f &= f - 1;
+      const int v = 32 * w + bit;
+      atomicXor(Sa + v, ma);
+      atomicXor(Sb + v, mb2);
+    }
+  }
+  if (lane == 0) {
+    sh.E[ba] += dEa;
+    sh.E[bb] -= dEa;
+    atomicAdd(&sh.m32[3], 1);
+  }
+}
+
+// Replica exchange of attempt t (Sec. "Comparison with Adaptive Parallel
+// Tempering"; Methods): even t pairs (0,1),(2,3)..., odd t (1,2),(3,4)...;
+// each label decides on its own; p_swap = min(1, exp(dbeta dE)).
+__device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int p, uint32_t t) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const AptProbDev &P = a.prob[p];
+  const int q = (int)(t & 1u);
+  const int np = (k.T - q) / 2;
+  const int A = k.A;
+  for (int idx = lane; idx < np * A; idx += 32) {
+    const int r = q + 2 * (idx / A), al = idx % A;
+    const int bA = sh.buf_of[r * A + al], bB = sh.buf_of[(r + 1) * A + al];
+    const int dE = sh.E[bB] - sh.E[bA];
+    bool acc = dE >= 0;
+    if (!acc) {
+      const uint4 x = philox((uint32_t)r, t, (uint32_t)al, (k.ent << 8) | TAG_SWAP, a.k0, a.k1);
+      const int kk = (-dE) >> 1;
+      const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
+      const uint32_t th = ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
+      acc = x.x < th;
+    }
+    sh.satt[r * A + al] += 1;
+    if (acc) {
+      sh.sacc[r * A + al] += 1;
+      sh.buf_of[r * A + al] = bB;
+      sh.buf_of[(r + 1) * A + al] = bA;
+      sh.temp_of[bA] = r + 1;
+      sh.temp_of[bB] = r;
+      const uint32_t *tA = a.pbit + P.pbit_off + 8 * (r + 1), *tB = a.pbit + P.pbit_off + 8 * r;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        sh.thr[8 * bA + e] = tA[e];
+        sh.thrh[8 * bA + e] = tA[e] & 0xFFFF0000u;
+        sh.thr[8 * bB + e] = tB[e];
+        sh.thrh[8 * bB + e] = tB[e] & 0xFFFF0000u;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const int cta = blockIdx.x;
+  const int p = a.cta_prob[cta];
+  const AptProbDev &P = a.prob[p];
+  Cta k;
+  k.geo.Lx = P.Lx;
+  k.geo.Ly = P.Ly;
+  k.geo.Lz = P.Lz;
+  k.geo.N = P.N;
+  k.geo.H = P.N >> 1;
+  k.geo.hx = P.Lx >> 1;
+  k.geo.mhx = P.mhx;
+  k.geo.mLy = P.mLy;
+  k.T = P.T;
+  k.A = P.A;
+  k.B = P.B;
+  k.g0 = a.cta_g0[cta];
+  k.Gc = a.cta_gc[cta];
+  k.Bc = min(8 * k.Gc, P.B - 8 * k.g0);
+  k.ent = P.ent;
+  k.nch = a.cta_nch[cta];
+  k.tpc = blockDim.x / k.nch;
+  k.gc = (k.Gc + k.nch - 1) / k.nch;
+  const int N = P.N, G8 = 8 * k.Gc;
+  const int nwarps = blockDim.x >> 5;
+  const int64_t s0 = a.ctr[0], t0 = a.ctr[1];
+  const int nw = (N + 31) >> 5;
+  // carve shared memory
+  Shared sh;
+  uint32_t *cur = smem;
+  sh.S = cur;            cur += (size_t)k.Gc * N;
+  sh.thr = cur;          cur += 8 * G8;
+  sh.thrh = cur;         cur += 8 * G8;
+  sh.temp_of = reinterpret_cast<int32_t *>(cur);  cur += G8;
+  sh.buf_of = reinterpret_cast<int32_t *>(cur);   cur += G8;
+  sh.E = reinterpret_cast<int32_t *>(cur);        cur += G8;
+  sh.Eacc = reinterpret_cast<int32_t *>(cur);     cur += G8;
+  sh.satt = reinterpret_cast<int32_t *>(cur);     cur += 64;
+  sh.sacc = reinterpret_cast<int32_t *>(cur);     cur += 64;
+  sh.m32 = reinterpret_cast<int32_t *>(cur);      cur += 8;
+  cur += ((uintptr_t)cur & 4) ? 1 : 0;            // 8-byte align
+  sh.m64 = reinterpret_cast<int64_t *>(cur);      cur += 8;
+  sh.sum1 = reinterpret_cast<int64_t *>(cur);     cur += 2 * G8;
+  sh.sum2 = reinterpret_cast<int64_t *>(cur);     cur += 2 * G8;
+  sh.hist = reinterpret_cast<int32_t *>(cur);     cur += a.mode == pc::APT_MODE_PILOT ? k.T * a.n_bins : 0;
+  sh.icm = cur;          cur += (a.mode == pc::APT_MODE_APT && a.icm) ? 4 * nw * nwarps : 0;
+  sh.jn = reinterpret_cast<uint8_t *>(cur);
+
+  // load state
+  const uint32_t *gS = a.spins + P.spin_off + (size_t)k.g0 * N;
+  for (int i = threadIdx.x; i < k.Gc * N; i += blockDim.x) sh.S[i] = gS[i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sh.jn[i] = a.jneg[P.jneg_off + i];
+  for (int b = threadIdx.x; b < G8; b += blockDim.x) {
+    const int gb = 8 * k.g0 + b;
+    const int tb = (b < k.Bc) ? a.temp_of[P.buf_off + gb] : 0;
+    sh.temp_of[b] = tb;
+    sh.buf_of[b] = (b < k.Bc) ? a.buf_of[P.buf_off + gb] : 0;
+    sh.E[b] = (b < k.Bc) ? a.E[P.buf_off + gb] : 0;
+    sh.Eacc[b] = 0;
+    sh.sum1[b] = 0;
+    sh.sum2[b] = 0;
+    for (int e = 0; e < 8; ++e) {
+      const uint32_t th = a.pbit[P.pbit_off + 8 * tb + e];
+      sh.thr[8 * b + e] = th;
+      sh.thrh[8 * b + e] = th & 0xFFFF0000u;
+    }
+  }
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    sh.satt[i] = 0;
+    sh.sacc[i] = 0;
+  }
+  if (a.mode == pc::APT_MODE_PILOT)
+    for (int i = threadIdx.x; i < k.T * a.n_bins; i += blockDim.x) sh.hist[i] = 0;
+  if (threadIdx.x == 0) {
+    sh.m64[0] = a.best_E[p];
+    sh.m64[1] = a.best_sweep[p];
+    sh.m64[2] = a.hit_sweep[p];
+    sh.m64[3] = a.target[p];
+    sh.m32[0] = a.best_buf[p];
+    sh.m32[1] = 0;
+    sh.m32[2] = sh.m32[3] = sh.m32[4] = 0;
+  }
+  __syncthreads();
+
+  if (a.mode == pc::APT_MODE_ENERGY) {
+    colour_phase<false, true>(a, k, sh, 1, 0u);
+    __syncthreads();
+    finish_energies(k, sh);
+    __syncthreads();
+  } else {
+    for (int it = 0; it < a.n_iter; ++it) {
+      const uint32_t t = (uint32_t)(t0 + it);
+      for (int qq = 0; qq < a.spp; ++qq) {
+        const uint32_t s = (uint32_t)(s0 + (int64_t)it * a.spp + qq);
+        colour_phase<true, false>(a, k, sh, 0, s);
+        __syncthreads();
+        colour_phase<true, true>(a, k, sh, 1, s);
+        __syncthreads();
+        finish_energies(k, sh);
+        __syncthreads();
+        if (a.mode == pc::APT_MODE_LADDER) {
+          if ((int64_t)it * a.spp + qq >= a.window_from)
+            for (int b = threadIdx.x; b < k.Bc; b += blockDim.x) {
+              const int64_t e = sh.E[b];
+              sh.sum1[b] += e;
+              sh.sum2[b] += e * e;
+            }
+        } else if (a.mode == pc::APT_MODE_PILOT) {
+          if ((int64_t)s >= a.window_from)
+            for (int b = threadIdx.x; b < k.Bc; b += blockDim.x) {
+              const int64_t span = 3 * (int64_t)N;
+              const int64_t num = ((int64_t)sh.E[b] + span) * a.n_bins;
+              int64_t bin = num < 0 ? 0 : num / span;
+              if (bin > a.n_bins - 1) bin = a.n_bins - 1;
+              atomicAdd(&sh.hist[sh.temp_of[b] * a.n_bins + (int)bin], 1);
+            }
+        }
+      }
+      if (a.mode != pc::APT_MODE_APT) continue;
+      const int64_t sweeps = s0 + (int64_t)(it + 1) * a.spp;
+      best_update(a, k, sh, p, sweeps);
+      if (a.icm) {
+        const int w = threadIdx.x >> 5;
+        uint32_t *base = sh.icm + (size_t)4 * nw * w;
+        for (int r = w; r < k.T; r += nwarps)
+          icm_pair(a, k, sh, r, t, sh.buf_of[2 * r], sh.buf_of[2 * r + 1], base, base + nw,
+                   base + 2 * nw, base + 3 * nw);
+        __syncthreads();
+        best_update(a, k, sh, p, sweeps);
+      }
+      swap_step(a, k, sh, p, t);
+      __syncthreads();
+    }
+  }
+
+  // store state
+  uint32_t *gSo = a.spins + P.spin_off + (size_t)k.g0 * N;
+  for (int i = threadIdx.x; i < k.Gc * N; i += blockDim.x) gSo[i] = sh.S[i];
+  for (int b = threadIdx.x; b < k.Bc; b += blockDim.x) {
+    const int gb = 8 * k.g0 + b;
+    a.temp_of[P.buf_off + gb] = sh.temp_of[b];
+    a.buf_of[P.buf_off + gb] = sh.buf_of[b];
+    a.E[P.buf_off + gb] = sh.E[b];
+    if (a.mode == pc::APT_MODE_LADDER) {
+      a.sum1[P.buf_off + gb] = sh.sum1[b];
+      a.sum2[P.buf_off + gb] = sh.sum2[b];
+    }
+  }
+  if (a.mode == pc::APT_MODE_PILOT)
+    for (int i = threadIdx.x; i < k.T * a.n_bins; i += blockDim.x)
+      atomicAdd(reinterpret_cast<unsigned long long *>(&a.hist[P.hist_off + i]),
+                (unsigned long long)sh.hist[i]);
+  if (a.mode == pc::APT_MODE_APT) {
+    const int npair = (k.T - 1) * k.A;
+    for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+      a.stats[P.stat_off + i] += sh.satt[i];
+      a.stats[P.stat_off + npair + i] += sh.sacc[i];
+    }
+    if (threadIdx.x == 0) {
+      a.stats[P.stat_off + 2 * npair + 0] += sh.m32[2];
+      a.stats[P.stat_off + 2 * npair + 1] += sh.m32[3];
+      a.stats[P.stat_off + 2 * npair + 2] += sh.m32[4];
+      a.best_E[p] = sh.m64[0];
+      a.best_sweep[p] = sh.m64[1];
+      a.hit_sweep[p] = sh.m64[2];
+      a.best_buf[p] = sh.m32[0];
+    }
+  }
+}
+
+__global__ void apt_advance_kernel(int64_t *ctr, int64_t sweeps, int64_t swaps) {
+  ctr[0] += sweeps;
+  ctr[1] += swaps;
+}
+
+// Random initial state of every replica: +1 iff the init half-word < 2^15.
+__global__ void apt_init_kernel(const AptArgs a, int n_prob) {
+  const int p = blockIdx.y;
+  if (p >= n_prob) return;
+  const AptProbDev &P = a.prob[p];
+  const int N = P.N, H = N >> 1;
+  const int G = (P.B + 7) >> 3;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < G * N; idx += gridDim.x * blockDim.x) {
+    const int g = idx / N, rem = idx - g * N, c = rem / H, j = rem - c * H;
+    const uint4 x = philox((uint32_t)j, 0u, ((uint32_t)c << 16) | (uint32_t)g,
+                           (P.ent << 8) | a.tag_init, a.k0, a.k1);
+    uint32_t w = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w |= (half_lo(x, i) < 0x8000u) ? (1u << (4 * i)) : 0u;
+    a.spins[P.spin_off + idx] = w;
+  }
+}
+
+}  // namespace
+
+namespace pc {
+
+size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins) {
+  const size_t G8 = 8 * (size_t)Gc;
+  size_t words = (size_t)Gc * N + 16 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
+  if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
+  if (mode == APT_MODE_APT && icm) words += (size_t)4 * ((N + 31) / 32) * nwarps;
+  return words * 4 + (size_t)N + 16;
+}
+
+int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st) {
+  if (n_cta <= 0) return PC_OK;
+  // raise the dynamic shared-memory limit once per device (never inside a
+  // stream capture: the first launch on a device happens at load time)
+  static size_t set_for[64] = {0};
+  int dev = 0;
+  PC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(PC_EINVAL, "device index out of range");
+  if (smem > set_for[dev]) {
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set_for[dev] = smem;
+  }
+  apt_kernel<<<n_cta, tpb, smem, st>>>(a);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+int apt_advance_launch(int64_t *ctr, int64_t sweeps, int64_t swaps, cudaStream_t st) {
+  apt_advance_kernel<<<1, 1, 0, st>>>(ctr, sweeps, swaps);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+int apt_init_launch(const AptArgs &a, int n_prob, int max_words, cudaStream_t st) {
+  if (n_prob <= 0) return PC_OK;
+  const int tpb = 256;
+  int bx = (max_words + tpb - 1) / tpb;
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  dim3 grid((unsigned)bx, (unsigned)n_prob);
+  apt_init_kernel<<<grid, tpb, 0, st>>>(a, n_prob);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+}  // namespace pc

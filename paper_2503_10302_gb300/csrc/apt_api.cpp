@@ -1,0 +1,749 @@
+// C ABI of adaptive parallel tempering (Algorithm S2), the adaptive beta
+// ladder (its preprocessing) and the pilot-run histograms.  Host side:
+// validation, tables, batch packing, CTA scheduling and CUDA graphs; the
+// work itself runs in apt.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "apt_dev.h"
+#include "ctx.h"
+#include "internal.h"
+
+namespace pc {
+
+namespace {
+
+constexpr int kTpb = 512;        // threads per CTA of the sweep kernel
+constexpr int kMaxGcCta = 8;     // groups (64 buffers) per CTA
+constexpr int kChunkAttempts = 128;
+
+// Batch of problems resident on the device (one per APT problem, or one per
+// ladder/pilot instance).
+struct Batch {
+  std::vector<AptProbDev> prob;
+  std::vector<int> G;            // groups per problem
+  // device arrays
+  DevBuf<AptProbDev> d_prob;
+  DevBuf<uint32_t> d_spins, d_pbit, d_swaptab, d_swapidx;
+  DevBuf<uint8_t> d_jneg;
+  DevBuf<int32_t> d_temp, d_buf, d_E, d_bestbuf;
+  DevBuf<int64_t> d_bestE, d_bestsweep, d_hit, d_target, d_stats, d_sum1, d_sum2, d_hist, d_ctr;
+  DevBuf<int8_t> d_bestspins;
+  DevBuf<int> d_cta;             // [4][n_cta]: prob, g0, gc, nch
+  int n_cta = 0;
+  size_t smem = 0;
+  std::vector<uint32_t> h_pbit, h_swaptab, h_swapidx;
+};
+
+int choose_nch(int H, int Gc) {
+  int best = 1, best_cost = INT_MAX;
+  for (int nch = 1; nch <= 8; nch *= 2) {
+    if (kTpb % (32 * nch)) continue;
+    const int gc = (Gc + nch - 1) / nch;
+    if (gc > 4) continue;
+    const int tpc = kTpb / nch;
+    const int cost = ((H + tpc - 1) / tpc) * gc;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = nch;
+    }
+  }
+  return best;
+}
+
+// Per (colour, j) coupling signs: bit d set iff J along direction d
+// (+x, -x, +y, -y, +z, -z) is -1.
+std::vector<uint8_t> pack_jneg_cj(const Lattice &lat, const int8_t *J) {
+  std::vector<uint8_t> bylin = pack_jneg(lat, J);
+  const int Lx = lat.L[0], Ly = lat.L[1], H = lat.N / 2;
+  std::vector<uint8_t> out((size_t)lat.N);
+  for (int s = 0; s < lat.N; ++s) {
+    const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
+    const int c = (x + y + z) & 1;
+    out[(size_t)c * H + (s >> 1)] = bylin[(size_t)s];
+  }
+  return out;
+}
+
+// Host mirror of the spins of one problem, [B][N] in lin order.
+void unpack_spins(const AptProbDev &P, const uint32_t *words, int B, int8_t *out) {
+  const int N = P.N, H = N / 2, Lx = P.Lx, Ly = P.Ly;
+  for (int s = 0; s < N; ++s) {
+    const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
+    const int c = (x + y + z) & 1, j = s >> 1;
+    for (int b = 0; b < B; ++b) {
+      const uint32_t w = words[((size_t)(b >> 3) * 2 + c) * H + j];
+      out[(size_t)b * N + s] = ((w >> (4 * (b & 7))) & 1u) ? 1 : -1;
+    }
+  }
+}
+
+struct ProbSpec {
+  Lattice lat;
+  const int8_t *J;
+  int T, A, B;
+  uint32_t ent;
+  std::vector<double> beta;       // [T] (ladder: 1 entry, pilot: n_beta)
+  std::vector<int32_t> temp_of;   // [B]
+  bool swaps;
+};
+
+// Allocates and fills the device arrays of a batch.
+int build_batch(pc_ctx *c, Batch &bt, const std::vector<ProbSpec> &specs, int n_bins) {
+  const int n = (int)specs.size();
+  bt.prob.assign((size_t)n, AptProbDev{});
+  bt.G.assign((size_t)n, 0);
+  size_t spin_w = 0, jneg_b = 0, pbit_w = 0, swapidx_w = 0, buf_n = 0, best_b = 0, stat_n = 0,
+         hist_n = 0;
+  std::vector<uint8_t> h_jneg;
+  bt.h_pbit.clear();
+  bt.h_swaptab.clear();
+  bt.h_swapidx.clear();
+  std::vector<int32_t> h_temp, h_buf;
+  for (int i = 0; i < n; ++i) {
+    const ProbSpec &s = specs[(size_t)i];
+    AptProbDev &P = bt.prob[(size_t)i];
+    const int G = (s.B + 7) / 8;
+    bt.G[(size_t)i] = G;
+    P.Lx = s.lat.L[0];
+    P.Ly = s.lat.L[1];
+    P.Lz = s.lat.L[2];
+    P.N = s.lat.N;
+    P.mhx = recip32((uint32_t)(P.Lx / 2));
+    P.mLy = recip32((uint32_t)P.Ly);
+    P.T = s.T;
+    P.A = s.A;
+    P.B = s.B;
+    P.ent = s.ent;
+    P.spin_off = (uint32_t)spin_w;
+    spin_w += (size_t)G * P.N;
+    P.jneg_off = (uint32_t)jneg_b;
+    std::vector<uint8_t> jn = pack_jneg_cj(s.lat, s.J);
+    h_jneg.insert(h_jneg.end(), jn.begin(), jn.end());
+    jneg_b += (size_t)P.N;
+    P.pbit_off = (uint32_t)pbit_w;
+    for (int t = 0; t < s.T; ++t) {
+      for (int cc = 0; cc < 7; ++cc) bt.h_pbit.push_back(pc_pbit_threshold(s.beta[(size_t)t], 2 * cc - 6));
+      bt.h_pbit.push_back(0u);
+    }
+    pbit_w += (size_t)8 * s.T;
+    P.swapidx_off = (uint32_t)swapidx_w;
+    for (int r = 0; r + 1 < s.T; ++r) {
+      const uint32_t off = (uint32_t)bt.h_swaptab.size();
+      const double db = s.beta[(size_t)r + 1] - s.beta[(size_t)r];
+      bt.h_swaptab.push_back(0xFFFFFFFFu);   // dE = 0: always accepted
+      if (s.swaps) {
+        for (int64_t k = 1; k <= 3 * (int64_t)P.N; ++k) {
+          const uint32_t th = pc_swap_threshold(db, -2 * k);
+          if (th == 0u) break;
+          bt.h_swaptab.push_back(th);
+        }
+      }
+      bt.h_swapidx.push_back(off);
+      bt.h_swapidx.push_back((uint32_t)bt.h_swaptab.size() - off);
+    }
+    swapidx_w += (size_t)2 * (s.T > 1 ? s.T - 1 : 0);
+    P.buf_off = (uint32_t)buf_n;
+    for (int b = 0; b < 8 * G; ++b) {
+      h_temp.push_back(b < s.B ? s.temp_of[(size_t)b] : 0);
+      h_buf.push_back(b);
+    }
+    buf_n += (size_t)8 * G;
+    P.best_off = (uint32_t)best_b;
+    best_b += (size_t)P.N;
+    P.stat_off = (uint32_t)stat_n;
+    stat_n += (size_t)2 * (s.T > 1 ? s.T - 1 : 0) * s.A + 3;
+    P.hist_off = (uint32_t)hist_n;
+    hist_n += (size_t)s.T * (n_bins > 0 ? n_bins : 0);
+  }
+  if (bt.h_swaptab.empty()) bt.h_swaptab.push_back(0u);
+  if (bt.h_swapidx.empty()) bt.h_swapidx.push_back(0u);
+  if (spin_w > 0xFFFFFFFFull || bt.h_swaptab.size() > 0xFFFFFFFFull)
+    return fail(PC_EINVAL, "batch too large");
+  int rc;
+  if ((rc = bt.d_prob.alloc((size_t)n)) || (rc = bt.d_spins.alloc(spin_w)) ||
+      (rc = bt.d_jneg.alloc(jneg_b)) || (rc = bt.d_pbit.alloc(bt.h_pbit.size())) ||
+      (rc = bt.d_swaptab.alloc(bt.h_swaptab.size())) || (rc = bt.d_swapidx.alloc(bt.h_swapidx.size())) ||
+      (rc = bt.d_temp.alloc(buf_n)) || (rc = bt.d_buf.alloc(buf_n)) || (rc = bt.d_E.alloc(buf_n)) ||
+      (rc = bt.d_sum1.alloc(buf_n)) || (rc = bt.d_sum2.alloc(buf_n)) ||
+      (rc = bt.d_bestE.alloc((size_t)n)) || (rc = bt.d_bestsweep.alloc((size_t)n)) ||
+      (rc = bt.d_hit.alloc((size_t)n)) || (rc = bt.d_target.alloc((size_t)n)) ||
+      (rc = bt.d_bestbuf.alloc((size_t)n)) || (rc = bt.d_bestspins.alloc(best_b)) ||
+      (rc = bt.d_stats.alloc(stat_n)) || (rc = bt.d_hist.alloc(hist_n)) || (rc = bt.d_ctr.alloc(2)))
+    return rc;
+  cudaStream_t st = c->stream;
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_prob.p, bt.prob.data(), sizeof(AptProbDev) * n, cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_jneg.p, h_jneg.data(), h_jneg.size(), cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_pbit.p, bt.h_pbit.data(), bt.h_pbit.size() * 4, cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_swaptab.p, bt.h_swaptab.data(), bt.h_swaptab.size() * 4,
+                              cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_swapidx.p, bt.h_swapidx.data(), bt.h_swapidx.size() * 4,
+                              cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_temp.p, h_temp.data(), h_temp.size() * 4, cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_buf.p, h_buf.data(), h_buf.size() * 4, cudaMemcpyHostToDevice, st));
+  std::vector<int64_t> big((size_t)n, INT64_MAX), neg((size_t)n, -1), low((size_t)n, INT64_MIN);
+  std::vector<int32_t> negi((size_t)n, -1);
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_bestE.p, big.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_bestsweep.p, neg.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_hit.p, neg.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_target.p, low.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_bestbuf.p, negi.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+  if ((rc = bt.d_stats.zero(st)) || (rc = bt.d_hist.zero(st)) || (rc = bt.d_ctr.zero(st)) ||
+      (rc = bt.d_E.zero(st)) || (rc = bt.d_sum1.zero(st)) || (rc = bt.d_sum2.zero(st)) ||
+      (rc = bt.d_bestspins.zero(st)))
+    return rc;
+  // host vectors must outlive the async copies
+  PC_CUDA_TRY(cudaStreamSynchronize(st));
+  return PC_OK;
+}
+
+AptArgs base_args(pc_ctx *c, Batch &bt) {
+  AptArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.prob = bt.d_prob.p;
+  a.cta_prob = bt.d_cta.p;
+  a.cta_g0 = bt.d_cta.p + bt.n_cta;
+  a.cta_gc = bt.d_cta.p + 2 * bt.n_cta;
+  a.cta_nch = bt.d_cta.p + 3 * bt.n_cta;
+  a.spins = bt.d_spins.p;
+  a.jneg = bt.d_jneg.p;
+  a.pbit = bt.d_pbit.p;
+  a.swaptab = bt.d_swaptab.p;
+  a.swapidx = bt.d_swapidx.p;
+  a.temp_of = bt.d_temp.p;
+  a.buf_of = bt.d_buf.p;
+  a.E = bt.d_E.p;
+  a.best_E = bt.d_bestE.p;
+  a.best_sweep = bt.d_bestsweep.p;
+  a.hit_sweep = bt.d_hit.p;
+  a.target = bt.d_target.p;
+  a.best_buf = bt.d_bestbuf.p;
+  a.best_spins = bt.d_bestspins.p;
+  a.stats = bt.d_stats.p;
+  a.sum1 = bt.d_sum1.p;
+  a.sum2 = bt.d_sum2.p;
+  a.hist = bt.d_hist.p;
+  a.ctr = bt.d_ctr.p;
+  a.k0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
+  a.k1 = (uint32_t)(c->seed >> 32);
+  a.spp = 1;
+  return a;
+}
+
+// CTA list: problems in decreasing order of work (largest first, so the
+// block scheduler packs the small ones behind), each split into CTAs of at
+// most kMaxGcCta groups; only problems with active[i] set.
+int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, int icm, int n_bins) {
+  const int n = (int)bt.prob.size();
+  std::vector<int> order;
+  for (int i = 0; i < n; ++i)
+    if (active.empty() || active[(size_t)i]) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (int64_t)bt.prob[(size_t)x].N * bt.prob[(size_t)x].B > (int64_t)bt.prob[(size_t)y].N * bt.prob[(size_t)y].B;
+  });
+  std::vector<int> cp, cg0, cgc, cnch;
+  size_t smem = 0;
+  for (int i : order) {
+    const AptProbDev &P = bt.prob[(size_t)i];
+    const int G = bt.G[(size_t)i];
+    for (int g0 = 0; g0 < G; g0 += kMaxGcCta) {
+      const int gc = std::min(kMaxGcCta, G - g0);
+      cp.push_back(i);
+      cg0.push_back(g0);
+      cgc.push_back(gc);
+      cnch.push_back(choose_nch(P.N / 2, gc));
+      smem = std::max(smem, apt_smem_bytes(P.N, gc, kTpb / 32, mode, icm, P.T, n_bins));
+    }
+  }
+  bt.n_cta = (int)cp.size();
+  if (smem > (size_t)c->smem_optin) return fail(PC_EINVAL, "problem does not fit in shared memory");
+  bt.smem = smem;
+  std::vector<int> all;
+  all.insert(all.end(), cp.begin(), cp.end());
+  all.insert(all.end(), cg0.begin(), cg0.end());
+  all.insert(all.end(), cgc.begin(), cgc.end());
+  all.insert(all.end(), cnch.begin(), cnch.end());
+  int rc;
+  if (bt.d_cta.n < all.size() && (rc = bt.d_cta.alloc(all.size()))) return rc;
+  if (!all.empty())
+    PC_CUDA_TRY(cudaMemcpyAsync(bt.d_cta.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PC_OK;
+}
+
+int set_counters(pc_ctx *c, Batch &bt, int64_t s0, int64_t t0) {
+  const int64_t v[2] = {s0, t0};
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_ctr.p, v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PC_OK;
+}
+
+int max_words(const Batch &bt) {
+  int m = 0;
+  for (size_t i = 0; i < bt.prob.size(); ++i) m = std::max(m, bt.G[i] * bt.prob[i].N);
+  return m;
+}
+
+}  // namespace
+
+// -------------------------------------------------------------------- APT
+struct AptImpl {
+  Batch bt;
+  int A = 0;
+  bool icm_ok = false;
+  // CUDA graph of one chunk of kChunkAttempts swap attempts
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int g_spp = -1, g_icm = -1;
+  ~AptImpl() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+}  // namespace pc
+
+using namespace pc;
+
+static AptImpl *apt_impl(pc_ctx *c) { return static_cast<AptImpl *>(c->apt_impl); }
+
+void pc_apt_release_impl(pc_ctx *c) {
+  delete apt_impl(c);
+  c->apt_impl = nullptr;
+}
+
+extern "C" {
+
+int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, const int32_t *n_temps,
+                const double *betas, int n_labels, uint32_t entry0) {
+  if (!c || !dims || !J || !n_temps || !betas) return fail(PC_EINVAL, "NULL argument");
+  if (n_inst < 1) return fail(PC_EINVAL, "n_inst must be >= 1");
+  if (n_labels < 1 || n_labels > 2) return fail(PC_EINVAL, "n_labels must be 1 or 2");
+  if ((uint64_t)entry0 + (uint64_t)n_inst > (1ull << 24)) return fail(PC_EINVAL, "entry ids must be < 2^24");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  std::vector<ProbSpec> specs((size_t)n_inst);
+  size_t joff = 0, boff = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    ProbSpec &s = specs[(size_t)i];
+    int rc = check_lattice(dims + 3 * i, J + 3 * joff, &s.lat);
+    if (rc) return rc;
+    s.J = J + 3 * joff;
+    s.T = n_temps[i];
+    s.A = n_labels;
+    s.B = s.T * n_labels;
+    if (s.T < 1 || s.B > 64) return fail(PC_EINVAL, "need 1 <= n_temps and n_temps * n_labels <= 64");
+    s.ent = entry0 + (uint32_t)i;
+    s.beta.assign(betas + boff, betas + boff + s.T);
+    for (int t = 0; t < s.T; ++t) {
+      if (!(s.beta[(size_t)t] >= 0.0) || !std::isfinite(s.beta[(size_t)t]))
+        return fail(PC_EINVAL, "betas must be finite and >= 0");
+      if (t > 0 && !(s.beta[(size_t)t] > s.beta[(size_t)t - 1]))
+        return fail(PC_EINVAL, "betas must be strictly increasing");
+    }
+    s.temp_of.resize((size_t)s.B);
+    for (int b = 0; b < s.B; ++b) s.temp_of[(size_t)b] = b / n_labels;
+    s.swaps = true;
+    joff += (size_t)s.lat.N;
+    boff += (size_t)s.T;
+  }
+  pc_apt_release_impl(c);
+  AptImpl *im = new AptImpl();
+  c->apt_impl = im;
+  c->apt.ready = false;
+  im->A = n_labels;
+  int rc = build_batch(c, im->bt, specs, 0);
+  if (rc) return rc;
+  if ((rc = schedule(c, im->bt, {}, APT_MODE_APT, n_labels == 2, 0))) return rc;
+  AptArgs a = base_args(c, im->bt);
+  a.tag_init = 1;   // TAG_APT_INIT
+  if ((rc = apt_init_launch(a, n_inst, max_words(im->bt), c->stream))) return rc;
+  a.mode = APT_MODE_ENERGY;
+  if ((rc = apt_launch(a, im->bt.n_cta, kTpb, im->bt.smem, c->stream))) return rc;
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->apt.ready = true;
+  c->apt.n = n_inst;
+  c->apt.A = n_labels;
+  c->apt.sweeps = 0;
+  c->apt.swaps = 0;
+  return PC_OK;
+}
+
+static int apt_enqueue(pc_ctx *c, AptImpl *im, int n_iter, int spp, int icm) {
+  AptArgs a = base_args(c, im->bt);
+  a.mode = APT_MODE_APT;
+  a.n_iter = n_iter;
+  a.spp = spp;
+  a.icm = icm;
+  a.tag_main = 2;    // TAG_APT_SWEEP
+  a.tag_ref = 3;     // TAG_APT_REFINE
+  int rc = apt_launch(a, im->bt.n_cta, kTpb, im->bt.smem, c->stream);
+  if (rc) return rc;
+  return apt_advance_launch(im->bt.d_ctr.p, (int64_t)n_iter * spp, n_iter, c->stream);
+}
+
+int pc_apt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  if (n_swaps < 0 || sweeps_per_swap < 1) return fail(PC_EINVAL, "n_swaps >= 0, sweeps_per_swap >= 1");
+  AptImpl *im = apt_impl(c);
+  if (icm && im->A != 2) return fail(PC_EINVAL, "ICM needs two labels per temperature");
+  if (c->apt.sweeps + n_swaps * sweeps_per_swap > 0xFFFFFFFFll || c->apt.swaps + n_swaps > 0xFFFFFFFFll)
+    return fail(PC_EINVAL, "sweep counter would exceed 2^32");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  icm = icm ? 1 : 0;
+  int64_t left = n_swaps;
+  // whole chunks replay one CUDA graph (sweep kernel + counter advance)
+  if (left >= kChunkAttempts) {
+    if (!im->exec || im->g_spp != sweeps_per_swap || im->g_icm != icm) {
+      if (im->exec) cudaGraphExecDestroy(im->exec);
+      if (im->graph) cudaGraphDestroy(im->graph);
+      im->exec = nullptr;
+      im->graph = nullptr;
+      cudaStream_t cap;
+      PC_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      int rc = PC_OK;
+      if (e == cudaSuccess) {
+        cudaStream_t saved = c->stream;
+        c->stream = cap;
+        rc = apt_enqueue(c, im, kChunkAttempts, sweeps_per_swap, icm);
+        c->stream = saved;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &im->graph);
+        if (!rc && e2 != cudaSuccess) rc = fail(PC_ECUDA, std::string("capture: ") + cudaGetErrorString(e2));
+      } else {
+        rc = fail(PC_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+      }
+      cudaStreamDestroy(cap);
+      if (rc) return rc;
+      PC_CUDA_TRY(cudaGraphInstantiate(&im->exec, im->graph, 0));
+      im->g_spp = sweeps_per_swap;
+      im->g_icm = icm;
+    }
+    while (left >= kChunkAttempts) {
+      PC_CUDA_TRY(cudaGraphLaunch(im->exec, c->stream));
+      left -= kChunkAttempts;
+    }
+  }
+  if (left > 0) {
+    int rc = apt_enqueue(c, im, (int)left, sweeps_per_swap, icm);
+    if (rc) return rc;
+  }
+  c->apt.sweeps += n_swaps * sweeps_per_swap;
+  c->apt.swaps += n_swaps;
+  return PC_OK;
+}
+
+int pc_apt_progress(pc_ctx *c, int64_t *sweeps, int64_t *swaps) {
+  if (!c || !c->apt.ready) return fail(PC_ESTATE, "pc_apt_load first");
+  if (sweeps) *sweeps = c->apt.sweeps;
+  if (swaps) *swaps = c->apt.swaps;
+  return PC_OK;
+}
+
+static int check_inst(pc_ctx *c, int inst) {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  if (inst < 0 || inst >= c->apt.n) return fail(PC_EINVAL, "instance index out of range");
+  return PC_OK;
+}
+
+int pc_apt_set_target(pc_ctx *c, int inst, int64_t e_target) {
+  int rc = check_inst(c, inst);
+  if (rc) return rc;
+  Batch &bt = apt_impl(c)->bt;
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  int64_t best = 0, bsw = 0;
+  PC_CUDA_TRY(cudaMemcpy(&best, bt.d_bestE.p + inst, 8, cudaMemcpyDeviceToHost));
+  PC_CUDA_TRY(cudaMemcpy(&bsw, bt.d_bestsweep.p + inst, 8, cudaMemcpyDeviceToHost));
+  const int64_t hit = (best <= e_target) ? bsw : -1;
+  PC_CUDA_TRY(cudaMemcpy(bt.d_target.p + inst, &e_target, 8, cudaMemcpyHostToDevice));
+  PC_CUDA_TRY(cudaMemcpy(bt.d_hit.p + inst, &hit, 8, cudaMemcpyHostToDevice));
+  return PC_OK;
+}
+
+int pc_apt_get_state(pc_ctx *c, int inst, int8_t *spins, int64_t *energies, int32_t *temp_of) {
+  int rc = check_inst(c, inst);
+  if (rc) return rc;
+  Batch &bt = apt_impl(c)->bt;
+  const AptProbDev &P = bt.prob[(size_t)inst];
+  const int G = bt.G[(size_t)inst];
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (spins) {
+    std::vector<uint32_t> w((size_t)G * P.N);
+    PC_CUDA_TRY(cudaMemcpy(w.data(), bt.d_spins.p + P.spin_off, w.size() * 4, cudaMemcpyDeviceToHost));
+    unpack_spins(P, w.data(), P.B, spins);
+  }
+  if (energies) {
+    std::vector<int32_t> e((size_t)P.B);
+    PC_CUDA_TRY(cudaMemcpy(e.data(), bt.d_E.p + P.buf_off, e.size() * 4, cudaMemcpyDeviceToHost));
+    for (int b = 0; b < P.B; ++b) energies[b] = e[(size_t)b];
+  }
+  if (temp_of)
+    PC_CUDA_TRY(cudaMemcpy(temp_of, bt.d_temp.p + P.buf_off, (size_t)P.B * 4, cudaMemcpyDeviceToHost));
+  return PC_OK;
+}
+
+int pc_apt_get_best(pc_ctx *c, int inst, int64_t *E, int64_t *sweep, int32_t *buf, int64_t *hit_sweep,
+                    int8_t *spins) {
+  int rc = check_inst(c, inst);
+  if (rc) return rc;
+  Batch &bt = apt_impl(c)->bt;
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (E) PC_CUDA_TRY(cudaMemcpy(E, bt.d_bestE.p + inst, 8, cudaMemcpyDeviceToHost));
+  if (sweep) PC_CUDA_TRY(cudaMemcpy(sweep, bt.d_bestsweep.p + inst, 8, cudaMemcpyDeviceToHost));
+  if (buf) PC_CUDA_TRY(cudaMemcpy(buf, bt.d_bestbuf.p + inst, 4, cudaMemcpyDeviceToHost));
+  if (hit_sweep) PC_CUDA_TRY(cudaMemcpy(hit_sweep, bt.d_hit.p + inst, 8, cudaMemcpyDeviceToHost));
+  if (spins)
+    PC_CUDA_TRY(cudaMemcpy(spins, bt.d_bestspins.p + bt.prob[(size_t)inst].best_off,
+                           (size_t)bt.prob[(size_t)inst].N, cudaMemcpyDeviceToHost));
+  return PC_OK;
+}
+
+int pc_apt_get_best_all(pc_ctx *c, int64_t *E, int64_t *hit_sweep) {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  Batch &bt = apt_impl(c)->bt;
+  const size_t n = bt.prob.size();
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  if (E) PC_CUDA_TRY(cudaMemcpyAsync(E, bt.d_bestE.p, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+  if (hit_sweep) PC_CUDA_TRY(cudaMemcpyAsync(hit_sweep, bt.d_hit.p, 8 * n, cudaMemcpyDeviceToHost, c->stream));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PC_OK;
+}
+
+int pc_apt_get_stats(pc_ctx *c, int inst, int64_t *att, int64_t *acc, int64_t *icm) {
+  int rc = check_inst(c, inst);
+  if (rc) return rc;
+  Batch &bt = apt_impl(c)->bt;
+  const AptProbDev &P = bt.prob[(size_t)inst];
+  const int np = (P.T - 1) * P.A;
+  std::vector<int64_t> s((size_t)2 * np + 3);
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  PC_CUDA_TRY(cudaMemcpy(s.data(), bt.d_stats.p + P.stat_off, s.size() * 8, cudaMemcpyDeviceToHost));
+  if (att) std::memcpy(att, s.data(), 8 * (size_t)np);
+  if (acc) std::memcpy(acc, s.data() + np, 8 * (size_t)np);
+  if (icm) std::memcpy(icm, s.data() + 2 * np, 24);
+  return PC_OK;
+}
+
+int pc_apt_get_pbit_table(pc_ctx *c, int inst, uint32_t *out) {
+  int rc = check_inst(c, inst);
+  if (rc) return rc;
+  Batch &bt = apt_impl(c)->bt;
+  const AptProbDev &P = bt.prob[(size_t)inst];
+  for (int t = 0; t < P.T; ++t)
+    for (int cc = 0; cc < 7; ++cc) out[7 * t + cc] = bt.h_pbit[P.pbit_off + 8 * t + cc];
+  return PC_OK;
+}
+
+int pc_apt_get_swap_table(pc_ctx *c, int inst, int pair, uint32_t *out, int max_len, int *len) {
+  int rc = check_inst(c, inst);
+  if (rc) return rc;
+  Batch &bt = apt_impl(c)->bt;
+  const AptProbDev &P = bt.prob[(size_t)inst];
+  if (pair < 0 || pair + 1 >= P.T) return fail(PC_EINVAL, "pair out of range");
+  const uint32_t off = bt.h_swapidx[P.swapidx_off + 2 * pair], n = bt.h_swapidx[P.swapidx_off + 2 * pair + 1];
+  if (len) *len = (int)n;
+  for (int k = 0; k < max_len && k < (int)n; ++k) out[k] = bt.h_swaptab[off + k];
+  return PC_OK;
+}
+
+// ------------------------------------------------------------------ ladder
+int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+                       double beta0, double alpha, int n_chains, int sweeps, int tail, double tol,
+                       int max_len, double *beta_out, double *sigma_out, int32_t *len_out,
+                       int32_t *converged_out) {
+  if (!c || !dims || !J || !beta_out || !len_out) return fail(PC_EINVAL, "NULL argument");
+  if (n_inst < 1 || n_chains < 1 || n_chains > 4096 || sweeps < 1 || tail < 2 || tail > sweeps ||
+      max_len < 1 || !(beta0 > 0.0) || !(alpha > 0.0))
+    return fail(PC_EINVAL, "bad ladder parameters");
+  if ((uint64_t)entry0 + (uint64_t)n_inst > (1ull << 24)) return fail(PC_EINVAL, "entry ids must be < 2^24");
+  if ((int64_t)sweeps * max_len > 0xFFFFFFFFll) return fail(PC_EINVAL, "sweep counter would exceed 2^32");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  std::vector<ProbSpec> specs((size_t)n_inst);
+  size_t joff = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    ProbSpec &s = specs[(size_t)i];
+    int rc = check_lattice(dims + 3 * i, J + 3 * joff, &s.lat);
+    if (rc) return rc;
+    if ((int64_t)tail * 3 * s.lat.N * 3 * s.lat.N > (int64_t)1 << 62)
+      return fail(PC_EINVAL, "tail too long for exact int64 sums");
+    s.J = J + 3 * joff;
+    s.T = 1;
+    s.A = 1;
+    s.B = n_chains;
+    s.ent = entry0 + (uint32_t)i;
+    s.beta.assign(1, beta0);
+    s.temp_of.assign((size_t)n_chains, 0);
+    s.swaps = false;
+    joff += (size_t)s.lat.N;
+  }
+  Batch bt;
+  int rc = build_batch(c, bt, specs, 0);
+  if (rc) return rc;
+  std::vector<double> beta((size_t)n_inst, beta0);
+  std::vector<char> active((size_t)n_inst, 1);
+  std::vector<int> len((size_t)n_inst, 0), conv((size_t)n_inst, 0);
+  AptArgs a;
+  if ((rc = schedule(c, bt, active, APT_MODE_LADDER, 0, 0))) return rc;
+  a = base_args(c, bt);
+  a.tag_init = 6;   // TAG_LAD_INIT
+  if ((rc = apt_init_launch(a, n_inst, max_words(bt), c->stream))) return rc;
+  std::vector<int64_t> s1, s2;
+  for (int step = 0; step < max_len; ++step) {
+    // thresholds of each active instance's current beta
+    std::vector<uint32_t> pb((size_t)8 * n_inst, 0u);
+    for (int i = 0; i < n_inst; ++i)
+      for (int cc = 0; cc < 7; ++cc) pb[(size_t)8 * i + cc] = pc_pbit_threshold(beta[(size_t)i], 2 * cc - 6);
+    PC_CUDA_TRY(cudaMemcpyAsync(bt.d_pbit.p, pb.data(), pb.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    if ((rc = schedule(c, bt, active, APT_MODE_LADDER, 0, 0))) return rc;
+    if ((rc = set_counters(c, bt, (int64_t)step * sweeps, 0))) return rc;
+    a = base_args(c, bt);
+    a.mode = APT_MODE_LADDER;
+    a.n_iter = sweeps;
+    a.spp = 1;
+    a.window_from = sweeps - tail;
+    a.tag_main = 7;   // TAG_LAD_SWEEP
+    a.tag_ref = 8;    // TAG_LAD_REFINE
+    if ((rc = apt_launch(a, bt.n_cta, kTpb, bt.smem, c->stream))) return rc;
+    s1.resize(bt.d_sum1.n);
+    s2.resize(bt.d_sum2.n);
+    PC_CUDA_TRY(cudaMemcpyAsync(s1.data(), bt.d_sum1.p, s1.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    PC_CUDA_TRY(cudaMemcpyAsync(s2.data(), bt.d_sum2.p, s2.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    bool any = false;
+    for (int i = 0; i < n_inst; ++i) {
+      if (!active[(size_t)i]) continue;
+      const AptProbDev &P = bt.prob[(size_t)i];
+      double mean_var = 0.0;
+      for (int b = 0; b < n_chains; ++b) {
+        const int64_t sE = s1[P.buf_off + b], sE2 = s2[P.buf_off + b];
+        const int64_t num = (int64_t)tail * sE2 - sE * sE;
+        mean_var += (double)num / ((double)tail * (double)(tail - 1));
+      }
+      mean_var /= (double)n_chains;
+      const double sigma = std::sqrt(mean_var);
+      beta_out[(size_t)i * max_len + len[(size_t)i]] = beta[(size_t)i];
+      if (sigma_out) sigma_out[(size_t)i * max_len + len[(size_t)i]] = sigma;
+      len[(size_t)i] += 1;
+      if (sigma < tol) {
+        conv[(size_t)i] = 1;
+        active[(size_t)i] = 0;
+      } else if (len[(size_t)i] == max_len) {
+        active[(size_t)i] = 0;
+      } else {
+        beta[(size_t)i] = beta[(size_t)i] + alpha / sigma;
+        any = true;
+      }
+    }
+    if (!any) break;
+  }
+  for (int i = 0; i < n_inst; ++i) {
+    len_out[i] = len[(size_t)i];
+    if (converged_out) converged_out[i] = conv[(size_t)i];
+  }
+  return PC_OK;
+}
+
+int pc_resample_ladder(const double *beta, int len, int n, double *out) {
+  if (!beta || !out || len < 1 || n < 2) return fail(PC_EINVAL, "bad arguments");
+  if (len == 1) {
+    for (int k = 0; k < n; ++k) out[k] = beta[0];
+    return PC_OK;
+  }
+  for (int k = 0; k < n; ++k) {
+    const double pos = (double)k * (double)(len - 1) / (double)(n - 1);
+    int lo = (int)std::floor(pos);
+    if (lo > len - 2) lo = len - 2;
+    const double w = pos - (double)lo;
+    out[k] = beta[lo] * (1.0 - w) + beta[lo + 1] * w;
+  }
+  return PC_OK;
+}
+
+// ------------------------------------------------------------------ pilot
+int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+                  int n_beta, const double *betas, int chains_per_beta, int sweeps, int burn, int n_bins,
+                  int64_t *counts) {
+  if (!c || !dims || !J || !betas || !counts) return fail(PC_EINVAL, "NULL argument");
+  if (n_inst < 1 || n_beta < 1 || chains_per_beta < 1 || n_beta * chains_per_beta > 64 || sweeps < 1 ||
+      burn < 0 || burn >= sweeps || n_bins < 1 || n_bins > 256 || n_beta * n_bins > 2048)
+    return fail(PC_EINVAL, "bad pilot parameters (n_beta * chains_per_beta <= 64)");
+  if ((uint64_t)entry0 + (uint64_t)n_inst > (1ull << 24)) return fail(PC_EINVAL, "entry ids must be < 2^24");
+  for (int t = 0; t < n_beta; ++t)
+    if (!(betas[t] >= 0.0) || !std::isfinite(betas[t])) return fail(PC_EINVAL, "betas must be finite and >= 0");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  std::vector<ProbSpec> specs((size_t)n_inst);
+  size_t joff = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    ProbSpec &s = specs[(size_t)i];
+    int rc = check_lattice(dims + 3 * i, J + 3 * joff, &s.lat);
+    if (rc) return rc;
+    s.J = J + 3 * joff;
+    s.T = n_beta;
+    s.A = 1;
+    s.B = n_beta * chains_per_beta;
+    s.ent = entry0 + (uint32_t)i;
+    s.beta.assign(betas, betas + n_beta);
+    s.temp_of.resize((size_t)s.B);
+    for (int b = 0; b < s.B; ++b) s.temp_of[(size_t)b] = b / chains_per_beta;
+    s.swaps = false;
+    joff += (size_t)s.lat.N;
+  }
+  Batch bt;
+  int rc = build_batch(c, bt, specs, n_bins);
+  if (rc) return rc;
+  if ((rc = schedule(c, bt, {}, APT_MODE_PILOT, 0, n_bins))) return rc;
+  if ((rc = set_counters(c, bt, 0, 0))) return rc;
+  AptArgs a = base_args(c, bt);
+  a.tag_init = 9;   // TAG_PIL_INIT
+  if ((rc = apt_init_launch(a, n_inst, max_words(bt), c->stream))) return rc;
+  a.mode = APT_MODE_PILOT;
+  a.n_iter = sweeps;
+  a.spp = 1;
+  a.window_from = burn;
+  a.n_bins = n_bins;
+  a.tag_main = 10;   // TAG_PIL_SWEEP
+  a.tag_ref = 11;    // TAG_PIL_REFINE
+  if ((rc = apt_launch(a, bt.n_cta, kTpb, bt.smem, c->stream))) return rc;
+  PC_CUDA_TRY(cudaMemcpyAsync(counts, bt.d_hist.p, (size_t)n_inst * n_beta * n_bins * 8,
+                              cudaMemcpyDeviceToHost, c->stream));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PC_OK;
+}
+
+int pc_instance_features(const int32_t *dims, const int8_t *J, double *out3) {
+  if (!dims || !J || !out3) return fail(PC_EINVAL, "NULL argument");
+  Lattice lat;
+  int rc = check_lattice(dims, J, &lat);
+  if (rc) return rc;
+  const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2], N = lat.N;
+  auto at = [&](int x, int y, int z) { return ((x % Lx) + Lx * ((y % Ly) + Ly * (z % Lz))); };
+  int64_t pos = 0, frust = 0;
+  for (int s = 0; s < N; ++s) {
+    const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
+    for (int d = 0; d < 3; ++d) pos += J[3 * s + d] > 0;
+    // plaquettes in the (x,y), (x,z), (y,z) planes with lower corner s
+    const int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int a = 0; a < 3; ++a)
+      for (int b = a + 1; b < 3; ++b) {
+        const int sa = at(x + e[a][0], y + e[a][1], z + e[a][2]);
+        const int sb = at(x + e[b][0], y + e[b][1], z + e[b][2]);
+        const int prod = J[3 * s + a] * J[3 * sa + b] * J[3 * sb + a] * J[3 * s + b];
+        frust += prod < 0;
+      }
+  }
+  out3[0] = std::cbrt((double)N) / 16.0;
+  out3[1] = (double)pos / (3.0 * N);
+  out3[2] = (double)frust / (3.0 * N);
+  return PC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// Device-side descriptors of the adaptive-parallel-tempering kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pc {
+
+enum : int { APT_MODE_APT = 0, APT_MODE_LADDER = 1, APT_MODE_PILOT = 2, APT_MODE_ENERGY = 3 };
+
+// One problem (lattice + replicas) of a batch; offsets index the batch-wide
+// arrays of AptArgs.
+struct AptProbDev {
+  int Lx, Ly, Lz, N;
+  uint32_t mhx, mLy;      // ceil(2^32 / (Lx/2)), ceil(2^32 / Ly)
+  int T, A, B;            // temperatures, labels, buffers (= T * A, or chains)
+  uint32_t ent;           // Philox entry id
+  uint32_t spin_off;      // words: [G][2][N/2]
+  uint32_t jneg_off;      // bytes: [2][N/2] coupling signs per (colour, j)
+  uint32_t pbit_off;      // words: [T][8] p-bit thresholds, count c = 0..6
+  uint32_t swapidx_off;   // words: [T-1][2] (offset, length) of each pair's swap table
+  uint32_t buf_off;       // per-buffer arrays (temp_of, buf_of, E, sums)
+  uint32_t best_off;      // bytes: best state [N] in lin order
+  uint32_t stat_off;      // int64: att [(T-1)A], acc [(T-1)A], icm [3]
+  uint32_t hist_off;      // int64: [T][n_bins]
+};
+
+struct AptArgs {
+  const AptProbDev *prob;
+  const int *cta_prob, *cta_g0, *cta_gc, *cta_nch;
+  uint32_t *spins;
+  const uint8_t *jneg;
+  const uint32_t *pbit, *swaptab, *swapidx;
+  int32_t *temp_of, *buf_of, *E;
+  int64_t *best_E, *best_sweep, *hit_sweep;
+  const int64_t *target;
+  int32_t *best_buf;
+  int8_t *best_spins;
+  int64_t *stats;
+  int64_t *sum1, *sum2;   // ladder: per-buffer sums of E and E^2
+  int64_t *hist;          // pilot histograms
+  int n_bins;
+  int mode, n_iter, spp, icm;
+  int64_t *ctr;           // [2]: sweeps and swap attempts done before this launch
+  int64_t window_from;
+  uint32_t tag_init, tag_main, tag_ref;
+  uint32_t k0, k1;
+};
+
+size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins);
+int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st);
+int apt_init_launch(const AptArgs &a, int n_prob, int max_words, cudaStream_t st);
+// ctr[0] += sweeps, ctr[1] += swaps (stream-ordered after a launch).
+int apt_advance_launch(int64_t *ctr, int64_t sweeps, int64_t swaps, cudaStream_t st);
+
+}  // namespace pc

@@ -89,31 +89,12 @@ struct SqaState {
   }
 };
 
-struct AptProblemHost {
-  Lattice lat{};
-  int T = 0, A = 0, B = 0, G = 0;
-  std::vector<double> beta;
-  std::vector<uint32_t> pbit;        // [T][8]
-  std::vector<uint32_t> swap_off;    // [T] offset of pair r's table; [T-1] used
-  std::vector<uint32_t> swap_len;    // [T]
-};
-
+// Bookkeeping of the loaded APT batch; the batch itself (device arrays,
+// CUDA graph) lives in apt_api.cpp behind pc_ctx::apt_impl.
 struct AptState {
   bool ready = false;
   int n = 0, A = 0;
-  uint32_t entry0 = 0;
   int64_t sweeps = 0, swaps = 0;
-  std::vector<AptProblemHost> prob;
-  std::vector<int> order;            // launch order (largest work first)
-  // device arrays (see apt.cu for the layout)
-  DevBuf<uint8_t> d_blob;
-  size_t bytes = 0;
-  void release() {
-    ready = false;
-    d_blob.reset();
-    prob.clear();
-    order.clear();
-  }
 };
 
 }  // namespace pc
@@ -127,4 +108,7 @@ struct pc_ctx {
   int smem_optin = 0;
   pc::SqaState sqa;
   pc::AptState apt;
+  void *apt_impl = nullptr;
 };
+
+void pc_apt_release_impl(pc_ctx *c);

@@ -71,7 +71,7 @@ __device__ __forceinline__ uint32_t decide8(const uint4 &x, uint32_t De, uint32_
 
 // Exact settlement of the tied nibbles with the refine block y; T is the
 // full 32-bit table.
-__device__ __noinline__ uint32_t refine8(uint32_t w, uint4 x, uint4 y, uint32_t De, uint32_t Do,
+static __device__ __noinline__ uint32_t refine8(uint32_t w, uint4 x, uint4 y, uint32_t De, uint32_t Do,
                                          const uint32_t *T) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -85,8 +85,9 @@ __device__ __noinline__ uint32_t refine8(uint32_t w, uint4 x, uint4 y, uint32_t 
   return w;
 }
 
-// Exact n / d for n < 2^16, d < 2^16 via a 32-bit reciprocal m = ceil(2^32/d).
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t m) { return __umulhi(n, m); }
+// Exact n / d for n < 2^16, 2 <= d < 2^16 via a 32-bit reciprocal
+// m = ceil(2^32/d); d = 1 has no 32-bit reciprocal and is passed as m = 0.
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, uint32_t m) { return m ? __umulhi(n, m) : n; }
 
 __device__ __forceinline__ uint32_t nib_mask(uint32_t bit) { return bit * 0x11111111u; }
 

@@ -219,6 +219,190 @@ def pc_sqa_anneal_noalloc(device: int, stream_handle: int, seed: int, dims, J, P
           c_u32(run0), c_vp(E_dev_ptr), c_vp(best_dev_ptr or None))
 
 
+def _concat_J(J_list):
+    return np.ascontiguousarray(np.concatenate([np.asarray(j, np.int8).reshape(-1, 3) for j in J_list]))
+
+
+def pc_apt_load(ctx, dims, J_list, betas_list, n_labels: int = 2, entry0: int = 0) -> None:
+    d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(-1, 3))
+    J = _concat_J(J_list)
+    nt = np.ascontiguousarray([len(b) for b in betas_list], dtype=np.int32)
+    be = np.ascontiguousarray(np.concatenate([np.asarray(b, np.float64) for b in betas_list]))
+    _call("pc_apt_load", ctx, len(J_list), ptr(d, ctypes.c_int32), ptr(J, ctypes.c_int8),
+          ptr(nt, ctypes.c_int32), ptr(be, ctypes.c_double), n_labels, c_u32(entry0))
+
+
+def pc_apt_run(ctx, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True) -> None:
+    _call("pc_apt_run", ctx, c_i64(n_swaps), sweeps_per_swap, int(bool(icm)))
+
+
+def pc_apt_progress(ctx):
+    a, b = c_i64(), c_i64()
+    _call("pc_apt_progress", ctx, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def pc_apt_set_target(ctx, inst: int, e_target: int) -> None:
+    _call("pc_apt_set_target", ctx, inst, c_i64(e_target))
+
+
+def pc_apt_get_state(ctx, inst: int, N: int, B: int):
+    s = np.zeros((B, N), np.int8)
+    E = np.zeros(B, np.int64)
+    t = np.zeros(B, np.int32)
+    _call("pc_apt_get_state", ctx, inst, ptr(s, ctypes.c_int8), ptr(E, ctypes.c_int64),
+          ptr(t, ctypes.c_int32))
+    return s, E, t
+
+
+def pc_apt_get_best(ctx, inst: int, N: int):
+    E, sw, hit = c_i64(), c_i64(), c_i64()
+    b = ctypes.c_int32()
+    s = np.zeros(N, np.int8)
+    _call("pc_apt_get_best", ctx, inst, ctypes.byref(E), ctypes.byref(sw), ctypes.byref(b),
+          ctypes.byref(hit), ptr(s, ctypes.c_int8))
+    return dict(E=E.value, sweep=sw.value, buf=b.value, hit_sweep=hit.value, spins=s)
+
+
+def pc_apt_get_best_all(ctx, n: int):
+    E = np.zeros(n, np.int64)
+    hit = np.zeros(n, np.int64)
+    _call("pc_apt_get_best_all", ctx, ptr(E, ctypes.c_int64), ptr(hit, ctypes.c_int64))
+    return E, hit
+
+
+def pc_apt_get_stats(ctx, inst: int, T: int, A: int):
+    att = np.zeros((max(T - 1, 0), A), np.int64)
+    acc = np.zeros_like(att)
+    icm = np.zeros(3, np.int64)
+    _call("pc_apt_get_stats", ctx, inst, ptr(att, ctypes.c_int64), ptr(acc, ctypes.c_int64),
+          ptr(icm, ctypes.c_int64))
+    return att, acc, icm
+
+
+def pc_apt_get_pbit_table(ctx, inst: int, T: int) -> np.ndarray:
+    out = np.zeros((T, 7), np.uint32)
+    _call("pc_apt_get_pbit_table", ctx, inst, ptr(out, ctypes.c_uint32))
+    return out
+
+
+def pc_apt_get_swap_table(ctx, inst: int, pair: int, max_len: int = 1 << 16) -> np.ndarray:
+    out = np.zeros(max_len, np.uint32)
+    n = c_int()
+    _call("pc_apt_get_swap_table", ctx, inst, pair, ptr(out, ctypes.c_uint32), max_len, ctypes.byref(n))
+    return out[: min(n.value, max_len)].copy()
+
+
+def pc_adaptive_ladder(ctx, dims, J_list, entry0=0, beta0=0.5, alpha=1.25, n_chains=100, sweeps=10000,
+                       tail=1000, tol=1.0, max_len=64):
+    n = len(J_list)
+    d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(n, 3))
+    J = _concat_J(J_list)
+    beta = np.zeros((n, max_len), np.float64)
+    sig = np.zeros((n, max_len), np.float64)
+    ln = np.zeros(n, np.int32)
+    conv = np.zeros(n, np.int32)
+    _call("pc_adaptive_ladder", ctx, n, ptr(d, ctypes.c_int32), ptr(J, ctypes.c_int8), c_u32(entry0),
+          beta0, alpha, n_chains, sweeps, tail, tol, max_len, ptr(beta, ctypes.c_double),
+          ptr(sig, ctypes.c_double), ptr(ln, ctypes.c_int32), ptr(conv, ctypes.c_int32))
+    return [(beta[i, : ln[i]].copy(), sig[i, : ln[i]].copy(), bool(conv[i])) for i in range(n)]
+
+
+def pc_resample_ladder(beta, n: int = 32) -> np.ndarray:
+    b = np.ascontiguousarray(np.asarray(beta, np.float64))
+    out = np.zeros(n, np.float64)
+    _call("pc_resample_ladder", ptr(b, ctypes.c_double), len(b), n, ptr(out, ctypes.c_double))
+    return out
+
+
+def pc_pilot_hist(ctx, dims, J_list, betas, entry0=0, chains_per_beta=8, sweeps=256, burn=128,
+                  n_bins=64) -> np.ndarray:
+    n = len(J_list)
+    d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(n, 3))
+    J = _concat_J(J_list)
+    be = np.ascontiguousarray(np.asarray(betas, np.float64))
+    out = np.zeros((n, len(be), n_bins), np.int64)
+    _call("pc_pilot_hist", ctx, n, ptr(d, ctypes.c_int32), ptr(J, ctypes.c_int8), c_u32(entry0), len(be),
+          ptr(be, ctypes.c_double), chains_per_beta, sweeps, burn, n_bins, ptr(out, ctypes.c_int64))
+    return out
+
+
+def pc_instance_features(dims, J) -> np.ndarray:
+    d = _dims(dims)
+    j = _J(J)
+    out = np.zeros(3, np.float64)
+    _call("pc_instance_features", ptr(d, ctypes.c_int32), ptr(j, ctypes.c_int8), ptr(out, ctypes.c_double))
+    return out
+
+
+MLP_SIZES = (259, 256, 256, 256, 32)
+
+
+def _fpp(arrs):
+    arr_t = c_f32p * len(arrs)
+    return arr_t(*[a.ctypes.data_as(c_f32p) for a in arrs])
+
+
+class Mlp:
+    """The ladder predictor on the GPU (pc_mlp_*): params [(W [out,in], b [out])] x 4."""
+
+    def __init__(self, ctx, params, beta_min: float = 0.0):
+        self.ctx = ctx
+        Ws = [np.ascontiguousarray(W, np.float32) for W, _ in params]
+        bs = [np.ascontiguousarray(b, np.float32) for _, b in params]
+        h = c_vp()
+        _call("pc_mlp_create", ctx, ctypes.byref(h), _fpp(Ws), _fpp(bs), c_flt(beta_min))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lib().pc_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, np.float32)
+        out = np.zeros((X.shape[0], MLP_SIZES[-1]), np.float32)
+        _call("pc_mlp_forward", self.h, X.shape[0], ptr(X, ctypes.c_float), ptr(out, ctypes.c_float))
+        return out
+
+    def _bufs(self):
+        Ws = [np.zeros((o, i), np.float32) for i, o in zip(MLP_SIZES[:-1], MLP_SIZES[1:])]
+        bs = [np.zeros(o, np.float32) for o in MLP_SIZES[1:]]
+        return Ws, bs
+
+    def grads(self, X, Y):
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        Ws, bs = self._bufs()
+        loss = c_flt()
+        _call("pc_mlp_grads", self.h, X.shape[0], ptr(X, ctypes.c_float), ptr(Y, ctypes.c_float),
+              ctypes.byref(loss), _fpp(Ws), _fpp(bs))
+        return loss.value, list(zip(Ws, bs))
+
+    def train_step(self, X, Y, lr: float = 1e-3) -> float:
+        X = np.ascontiguousarray(X, np.float32)
+        Y = np.ascontiguousarray(Y, np.float32)
+        loss = c_flt()
+        _call("pc_mlp_train_step", self.h, X.shape[0], ptr(X, ctypes.c_float), ptr(Y, ctypes.c_float),
+              c_flt(lr), ctypes.byref(loss))
+        return loss.value
+
+    def train_step_dev(self, batch: int, X_ptr: int, Y_ptr: int, lr: float, loss_ptr: int = 0) -> None:
+        _call("pc_mlp_train_step_dev", self.h, batch, c_vp(X_ptr), c_vp(Y_ptr), c_flt(lr),
+              c_vp(loss_ptr or None))
+
+    def params(self):
+        Ws, bs = self._bufs()
+        _call("pc_mlp_get_params", self.h, _fpp(Ws), _fpp(bs))
+        return list(zip(Ws, bs))
+
+
 class Context:
     """Owns a pc_ctx on one device."""
 

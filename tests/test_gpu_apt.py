@@ -1,0 +1,247 @@
+"""Adaptive parallel tempering + ICM, the adaptive ladder and the pilot
+histograms on the GPU against the CPU oracle: bit-exact spins, energies,
+temperature assignments, swap/ICM statistics, best energies and hit sweeps."""
+import numpy as np
+import pytest
+
+from paper_2503_10302_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2503_10302_gb300 import build, pcomp
+    build.build()
+    return pcomp
+
+
+def _compare(pc, orc_apt, ctx, batch, insts=None, entry0=0):
+    """GPU problem i vs oracle problem i - entry0 offset mapping."""
+    insts = range(batch.n) if insts is None else insts
+    for gi, oi in insts:
+        N = int(np.prod(batch.dims[gi]))
+        T = len(batch.betas[gi])
+        B = T * batch.n_labels
+        s, E, t = pc.pc_apt_get_state(ctx.h, gi, N, B)
+        s2, E2, t2 = orc_apt.state(oi)
+        assert np.array_equal(t, t2), ("temps", gi)
+        assert np.array_equal(E, E2), ("energies", gi)
+        assert np.array_equal(s, s2), ("spins", gi)
+        b1 = pc.pc_apt_get_best(ctx.h, gi, N)
+        b2 = orc_apt.best(oi)
+        for key in ("E", "sweep", "buf", "hit_sweep"):
+            assert b1[key] == b2[key], (key, gi, b1[key], b2[key])
+        if b2["sweep"] >= 0:
+            assert np.array_equal(b1["spins"], b2["spins"]), ("best spins", gi)
+        att, acc, icm = pc.pc_apt_get_stats(ctx.h, gi, T, batch.n_labels)
+        att2, acc2, icm2 = orc_apt.stats(oi)
+        assert np.array_equal(att, att2) and np.array_equal(acc, acc2), ("swap stats", gi)
+        assert np.array_equal(icm, icm2), ("icm stats", gi, icm, icm2)
+
+
+def test_tables_equal_oracle(pc, orc):
+    b = W.apt_uniform_batch(2, 4, 12)
+    b.betas[1] = W.geometric_ladder(12, 0.1, 5.0)
+    ctx = pc.Context(0, 0)
+    pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
+    for i in range(2):
+        tab = pc.pc_apt_get_pbit_table(ctx.h, i, 12)
+        for t, beta in enumerate(b.betas[i]):
+            assert [int(v) for v in tab[t]] == [orc.pbit_threshold(beta, 2 * c - 6) for c in range(7)]
+        for r in range(11):
+            sw = pc.pc_apt_get_swap_table(ctx.h, i, r)
+            db = b.betas[i][r + 1] - b.betas[i][r]
+            # entry k: dE = -2k; the table ends where the threshold reaches 0
+            # or at |dE| = 6N, the largest gap two states can have
+            ref = [orc.swap_threshold(db, -2 * k) for k in range(1, len(sw) + 1)]
+            assert sw[0] == 0xFFFFFFFF and list(sw[1:]) == ref[:-1]
+            assert ref[-1] == 0 or len(sw) == 3 * 64 + 1
+    ctx.close()
+
+
+def test_initial_state_equals_oracle(pc, orc):
+    b = W.apt_uniform_batch(3, 6, 9)
+    ctx = pc.Context(0, 11)
+    pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 5)
+    apt = orc.Apt(b.dims, b.J, b.betas, 2, seed=11, entry0=5)
+    _compare(pc, apt, ctx, b, [(i, i) for i in range(3)])
+    ctx.close()
+
+
+def test_c1_full_run_bit_exact(pc, orc):
+    """One L = 4 instance, 8 temperatures x 2 replicas, swap + ICM every
+    sweep, 1e4 sweeps; compared after 100 and after 10000 sweeps."""
+    b = W.apt_single(L=4, n_temps=8)
+    ctx = pc.Context(0, 0)
+    pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
+    apt = orc.Apt(b.dims, b.J, b.betas, 2, seed=0)
+    pc.pc_apt_run(ctx.h, 100, 1, True)
+    apt.run(100)
+    _compare(pc, apt, ctx, b, [(0, 0)])
+    pc.pc_apt_run(ctx.h, 9900, 1, True)
+    apt.run(9900)
+    _compare(pc, apt, ctx, b, [(0, 0)])
+    assert pc.pc_apt_progress(ctx.h) == (10000, 10000)
+    ctx.close()
+
+
+@pytest.mark.parametrize("spp,icm,labels", [(1, False, 2), (3, True, 2), (2, False, 1)])
+def test_apt_variants(pc, orc, spp, icm, labels):
+    b = W.apt_uniform_batch(2, 6, 7, n_labels=labels)
+    ctx = pc.Context(0, 3)
+    pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, labels, 0)
+    apt = orc.Apt(b.dims, b.J, b.betas, labels, seed=3)
+    pc.pc_apt_run(ctx.h, 150, spp, icm)
+    apt.run(150, spp, icm)
+    _compare(pc, apt, ctx, b, [(0, 0), (1, 1)])
+    ctx.close()
+
+
+def test_mixed_shapes_batch(pc, orc):
+    """Uneven shapes and ladder lengths in one launch, incl. the largest
+    supported problem (16^3 spins x 64 replicas)."""
+    shapes = [(4, 4, 4), (6, 6, 6), (8, 8, 8), (4, 6, 8), (2, 4, 6), (10, 10, 10), (16, 16, 16)]
+    temps = [5, 9, 16, 11, 3, 24, 32]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 7, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, 2)
+    ctx = pc.Context(0, 21)
+    pc.pc_apt_load(ctx.h, dims, J, betas, 2, 100)
+    apt = orc.Apt(dims, J, betas, 2, seed=21, entry0=100)
+    pc.pc_apt_run(ctx.h, 30, 1, True)
+    apt.run(30, threads=8)
+    _compare(pc, apt, ctx, b, [(i, i) for i in range(len(shapes))])
+    ctx.close()
+
+
+def test_resume_and_chunking(pc, orc):
+    """140 attempts in one call (graph replay + remainder) == 60 + 80."""
+    b = W.apt_single(L=6, n_temps=10)
+    c1 = pc.Context(0, 2)
+    pc.pc_apt_load(c1.h, b.dims, b.J, b.betas, 2, 0)
+    pc.pc_apt_run(c1.h, 140, 1, True)
+    c2 = pc.Context(0, 2)
+    pc.pc_apt_load(c2.h, b.dims, b.J, b.betas, 2, 0)
+    pc.pc_apt_run(c2.h, 60, 1, True)
+    pc.pc_apt_run(c2.h, 80, 1, True)
+    for x, y in zip(pc.pc_apt_get_state(c1.h, 0, 216, 20), pc.pc_apt_get_state(c2.h, 0, 216, 20)):
+        assert np.array_equal(x, y)
+    c1.close()
+    c2.close()
+
+
+def test_target_hit_sweep(pc, orc):
+    b = W.apt_single(L=4, n_temps=8)
+    ctx = pc.Context(0, 4)
+    pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
+    apt = orc.Apt(b.dims, b.J, b.betas, 2, seed=4)
+    pc.pc_apt_run(ctx.h, 300, 1, True)
+    apt.run(300)
+    e_best = apt.best(0)["E"]
+    for tgt in (e_best + 8, e_best):
+        pc.pc_apt_set_target(ctx.h, 0, tgt)
+        apt.set_target(0, tgt)
+    pc.pc_apt_run(ctx.h, 700, 1, True)
+    apt.run(700)
+    _compare(pc, apt, ctx, b, [(0, 0)])
+    E, hit = pc.pc_apt_get_best_all(ctx.h, 1)
+    assert E[0] == apt.best(0)["E"] and hit[0] == apt.best(0)["hit_sweep"]
+    ctx.close()
+
+
+def test_c3_shape_sampled(pc, orc):
+    """64 instances of L = 12 with 32 x 2 replicas (the APT+ICM batch
+    shape); instances 0, 31 and 63 re-computed by the oracle."""
+    b = W.apt_uniform_batch(64, 12, 32)
+    ctx = pc.Context(0, 9)
+    pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
+    pc.pc_apt_run(ctx.h, 40, 1, True)
+    for i in (0, 31, 63):
+        apt = orc.Apt(b.dims[i:i + 1], b.J[i:i + 1], b.betas[i:i + 1], 2, seed=9, entry0=i)
+        apt.run(40)
+        _compare(pc, apt, ctx, b, [(i, 0)])
+    ctx.close()
+
+
+def test_c4_mixed_batch_sampled(pc, orc):
+    """256 instances, L uniform over {6..16}, 24-32 temperatures x 2; the
+    smallest, the largest and a middle instance re-computed by the oracle."""
+    b = W.apt_mixed_batch()
+    ctx = pc.Context(0, 17)
+    pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
+    pc.pc_apt_run(ctx.h, 12, 1, True)
+    work = [int(np.prod(d)) * len(t) for d, t in zip(b.dims, b.betas)]
+    picks = {int(np.argmin(work)), int(np.argmax(work)), 128}
+    for i in picks:
+        apt = orc.Apt(b.dims[i:i + 1], b.J[i:i + 1], b.betas[i:i + 1], 2, seed=17, entry0=i)
+        apt.run(12)
+        _compare(pc, apt, ctx, b, [(i, 0)])
+    ctx.close()
+
+
+def test_apt_rejects_bad_input(pc):
+    ctx = pc.Context(0, 0)
+    J = [W.ea_couplings((4, 4, 4), 1, 0)]
+    with pytest.raises(pc.PcompError):
+        pc.pc_apt_run(ctx.h, 10, 1, True)                          # before load
+    with pytest.raises(pc.PcompError):
+        pc.pc_apt_load(ctx.h, [(4, 4, 4)], J, [W.geometric_ladder(33)], 2, 0)   # > 64 replicas
+    with pytest.raises(pc.PcompError):
+        pc.pc_apt_load(ctx.h, [(4, 4, 4)], J, [np.array([1.0, 0.5])], 2, 0)     # not increasing
+    with pytest.raises(pc.PcompError):
+        pc.pc_apt_load(ctx.h, [(5, 4, 4)], [W.ea_couplings((5, 4, 4), 1, 0)], [np.ones(1)], 2, 0)
+    pc.pc_apt_load(ctx.h, [(4, 4, 4)], J, [W.geometric_ladder(4)], 1, 0)
+    with pytest.raises(pc.PcompError):
+        pc.pc_apt_run(ctx.h, 5, 1, True)                           # ICM needs 2 labels
+    ctx.close()
+
+
+# ---------------------------------------------------------------- ladder / pilot
+def test_adaptive_ladder_bit_exact(pc, orc):
+    shapes = [(4, 4, 4), (6, 6, 6), (4, 4, 8)]
+    J = [W.ea_couplings(s, 3, i) for i, s in enumerate(shapes)]
+    ctx = pc.Context(0, 5)
+    res = pc.pc_adaptive_ladder(ctx.h, shapes, J, entry0=10, n_chains=20, sweeps=60, tail=30,
+                                max_len=40)
+    for i, s in enumerate(shapes):
+        beta, sig, ok = orc.adaptive_ladder(s, J[i], entry=10 + i, seed=5, n_chains=20, sweeps=60,
+                                            tail=30, max_len=40)
+        assert res[i][2] == ok
+        assert np.array_equal(res[i][0], beta) and np.array_equal(res[i][1], sig)
+    ctx.close()
+
+
+def test_adaptive_ladder_many_chains(pc, orc):
+    """100 chains (more than one CTA's 64 replicas), paper's beta_0 and alpha."""
+    J = W.ea_couplings((6, 6, 6), 3, 9)
+    ctx = pc.Context(0, 6)
+    res = pc.pc_adaptive_ladder(ctx.h, [(6, 6, 6)], [J], n_chains=100, sweeps=40, tail=20, max_len=6)
+    beta, sig, ok = orc.adaptive_ladder((6, 6, 6), J, seed=6, n_chains=100, sweeps=40, tail=20, max_len=6)
+    assert np.array_equal(res[0][0], beta) and np.array_equal(res[0][1], sig) and res[0][2] == ok
+    ctx.close()
+
+
+def test_pilot_histograms_bit_exact(pc, orc):
+    shapes = [(4, 4, 4), (8, 8, 8)]
+    J = [W.ea_couplings(s, 4, i) for i, s in enumerate(shapes)]
+    betas = W.geometric_ladder(4)
+    ctx = pc.Context(0, 8)
+    got = pc.pc_pilot_hist(ctx.h, shapes, J, betas, entry0=3, chains_per_beta=8, sweeps=50, burn=20)
+    for i, s in enumerate(shapes):
+        ref = orc.pilot_hist(s, J[i], betas, entry=3 + i, seed=8, chains_per_beta=8, sweeps=50, burn=20)
+        assert np.array_equal(got[i], ref)
+    ctx.close()
+
+
+def test_features_and_resampling_match_oracle(pc):
+    from oracle import mlp
+    for i, s in enumerate([(4, 4, 4), (6, 8, 4), (16, 16, 16)]):
+        J = W.ea_couplings(s, 12, i)
+        f = pc.pc_instance_features(s, J)
+        ref = mlp.instance_features(s, J)
+        assert f[1] == ref[1] and f[2] == ref[2] and abs(f[0] - ref[0]) < 1e-15
+    for ln in (1, 2, 20, 33, 34):
+        beta = np.sort(np.random.default_rng(ln).random(ln)) + 0.5
+        assert np.array_equal(pc.pc_resample_ladder(beta, 32), mlp.resample_ladder(beta, 32))

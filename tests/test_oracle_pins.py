@@ -20,33 +20,47 @@ mpmath.mp.dps = 50
 
 
 # ---------------------------------------------------------------- Philox
+_TRITON_PHILOX = r"""
+import json, sys
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def k(out, cin, seed_ptr, n: tl.constexpr):
+    offs = tl.arange(0, n)
+    c0 = tl.load(cin + offs * 4 + 0).to(tl.uint32)
+    c1 = tl.load(cin + offs * 4 + 1).to(tl.uint32)
+    c2 = tl.load(cin + offs * 4 + 2).to(tl.uint32)
+    c3 = tl.load(cin + offs * 4 + 3).to(tl.uint32)
+    seed = tl.load(seed_ptr).to(tl.uint64)
+    r0, r1, r2, r3 = tl.philox(seed, c0, c1, c2, c3, 10)
+    tl.store(out + offs * 4 + 0, r0.to(tl.int64))
+    tl.store(out + offs * 4 + 1, r1.to(tl.int64))
+    tl.store(out + offs * 4 + 2, r2.to(tl.int64))
+    tl.store(out + offs * 4 + 3, r3.to(tl.int64))
+
+req = json.loads(sys.stdin.read())
+ctr = np.array(req["ctr"], dtype=np.int64)
+n = ctr.shape[0]
+out = torch.zeros(n * 4, dtype=torch.int64)
+k[(1,)](out, torch.tensor(ctr.reshape(-1)), torch.tensor([req["seed"]], dtype=torch.int64), n)
+print(json.dumps((out.numpy() & 0xFFFFFFFF).tolist()))
+"""
+
+
 def _triton_philox(ctr, seed):
+    """Triton's Philox4x32 run by its CPU interpreter in a child process (the
+    interpreter must be selected before triton is imported)."""
+    import json
     import os
-    os.environ["TRITON_INTERPRET"] = "1"
-    triton = pytest.importorskip("triton")
-    import torch
-    import triton.language as tl
-
-    @triton.jit
-    def k(out, cin, seed_ptr, n: tl.constexpr):
-        offs = tl.arange(0, n)
-        c0 = tl.load(cin + offs * 4 + 0).to(tl.uint32)
-        c1 = tl.load(cin + offs * 4 + 1).to(tl.uint32)
-        c2 = tl.load(cin + offs * 4 + 2).to(tl.uint32)
-        c3 = tl.load(cin + offs * 4 + 3).to(tl.uint32)
-        seed = tl.load(seed_ptr).to(tl.uint64)
-        r0, r1, r2, r3 = tl.philox(seed, c0, c1, c2, c3, 10)
-        tl.store(out + offs * 4 + 0, r0.to(tl.int64))
-        tl.store(out + offs * 4 + 1, r1.to(tl.int64))
-        tl.store(out + offs * 4 + 2, r2.to(tl.int64))
-        tl.store(out + offs * 4 + 3, r3.to(tl.int64))
-
-    n = ctr.shape[0]
-    out = torch.zeros(n * 4, dtype=torch.int64)
-    cin = torch.tensor(ctr.astype(np.int64).reshape(-1))
-    sd = torch.tensor([seed], dtype=torch.int64)
-    k[(1,)](out, cin, sd, n)
-    return (out.numpy() & 0xFFFFFFFF).astype(np.uint32).reshape(n, 4)
+    import subprocess
+    import sys
+    pytest.importorskip("triton")
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, "-c", _TRITON_PHILOX], input=json.dumps(
+        {"ctr": ctr.astype(np.int64).tolist(), "seed": int(seed)}), capture_output=True, text=True,
+        env=env, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return np.array(json.loads(r.stdout), dtype=np.uint64).astype(np.uint32).reshape(-1, 4)
 
 
 def test_philox_matches_independent_implementation(orc):
