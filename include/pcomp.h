@@ -83,7 +83,7 @@ int32_t pc_jperp_q(double gamma, int P, double T);
 /* Load a batch of n_inst problems: dims [n][3], J concatenated [sum N][3],
  * n_temps [n], betas concatenated (strictly increasing per problem),
  * n_labels in {1, 2} replicas per temperature (ICM needs 2), and
- * n_temps * n_labels <= 64.  Problem i uses entry id entry0 + i in its
+ * 8 * ceil(n_temps / 8) * n_labels <= 64.  Problem i uses entry id entry0 + i in its
  * Philox counters.  Builds the p-bit and swap tables, draws the random
  * initial state (Algorithm S2 "Initialize all replicas to random states")
  * and resets counters, best energies and statistics.  Replaces any batch
@@ -101,13 +101,13 @@ int pc_apt_progress(pc_ctx *ctx, int64_t *sweeps, int64_t *swaps);
 /* Target energy for time-to-target: the first sweep count at which the
  * best energy is <= e_target is recorded as the hit sweep. */
 int pc_apt_set_target(pc_ctx *ctx, int inst, int64_t e_target);
-/* Replica spins [B][N] int8 +-1 (buffer order, lin order), energies [B],
- * temperature index of each buffer [B]; any output may be NULL.
- * B = n_temps * n_labels; buffer b starts at temperature b / n_labels with
- * label b % n_labels and keeps its label. */
+/* Replica spins [B][N] int8 +-1 (slot order, lin order), energies [B],
+ * temperature index of each slot [B]; any output may be NULL.
+ * B = n_temps * n_labels; slot b is temperature b / n_labels with label
+ * b % n_labels (accepted swaps exchange the replicas' states). */
 int pc_apt_get_state(pc_ctx *ctx, int inst, int8_t *spins, int64_t *energies, int32_t *temp_of);
 /* Best energy seen at a measurement point, the sweep count then, the
- * buffer, the hit sweep (-1 if the target was never reached), and the
+ * slot, the hit sweep (-1 if the target was never reached), and the
  * best state [N] (nullable). */
 int pc_apt_get_best(pc_ctx *ctx, int inst, int64_t *E, int64_t *sweep, int32_t *buf,
                     int64_t *hit_sweep, int8_t *spins);

@@ -3,11 +3,11 @@
  * exchange and isoenergetic cluster moves, the adaptive beta ladder and the
  * pilot-run histograms.  TEST INFRASTRUCTURE ONLY (see oracle.h).
  *
- * Parallel tempering is written the usual way: replicas ("buffers") stay
- * where they are and an accepted swap exchanges their temperatures, which
- * is the same Markov chain as exchanging the states (Algorithm S2, "swap the
- * p-bit states").  buf_of[r][a] names the buffer that holds temperature r
- * with ICM label a; temp_of[b] is its inverse.
+ * Replicas live in slots (temperature r, ICM label a), slot index
+ * r * A + a.  An accepted swap exchanges the p-bit states of the two slots
+ * (Algorithm S2, "swap the p-bit states").  Random numbers are keyed by the
+ * slot's replica id  rid(r, a) = a * Tp + r  with Tp = 8 * ceil(T / 8), so
+ * the eight replicas of one Philox call are eight temperatures of one label.
  */
 #include <limits.h>
 #include <math.h>
@@ -32,16 +32,17 @@ static uint32_t *make_table(double beta, int64_t Imax) {
 
 /* Random initial state (Algorithm S2 "Initialize all replicas to random
  * states"): +1 iff the init half-word is below 2^15. */
-static void init_spins(const or_lat *L, int B, int8_t *spin, uint64_t seed, uint32_t ent,
-                       uint32_t tag) {
+static void init_spins(const or_lat *L, int B, const int32_t *rid, int8_t *spin, uint64_t seed,
+                       uint32_t ent, uint32_t tag) {
   for (int b = 0; b < B; ++b) {
+    const int id = rid ? rid[b] : b;
     for (int lin = 0; lin < L->N; ++lin) {
       int c = or_colour(L, lin);
-      uint32_t ctr[4] = {(uint32_t)(lin >> 1), 0u, ((uint32_t)c << 16) | (uint32_t)(b >> 3),
+      uint32_t ctr[4] = {(uint32_t)(lin >> 1), 0u, ((uint32_t)c << 16) | (uint32_t)(id >> 3),
                          (ent << 8) | tag};
       uint32_t x[4];
       or_philox(ctr, seed, x);
-      spin[(size_t)b * L->N + lin] = (or_half(x, b & 7) < 0x8000u) ? 1 : -1;
+      spin[(size_t)b * L->N + lin] = (or_half(x, id & 7) < 0x8000u) ? 1 : -1;
     }
   }
 }
@@ -51,19 +52,20 @@ static void init_spins(const or_lat *L, int B, int8_t *spin, uint64_t seed, uint
  * then all colour-1 sites.  Each update solves Eq. synapse for I and
  * Eq. neuron through the threshold of the buffer's temperature. */
 static void gibbs_sweep(const or_lat *L, const int8_t *J, const int8_t *h, int64_t Imax,
-                        int B, int8_t *spin, const int32_t *temp_of, uint32_t *const *tab,
-                        uint64_t seed, uint32_t ent, uint32_t s, uint32_t tag_main,
-                        uint32_t tag_ref) {
+                        int B, const int32_t *rid, int8_t *spin, const int32_t *temp_of,
+                        uint32_t *const *tab, uint64_t seed, uint32_t ent, uint32_t s,
+                        uint32_t tag_main, uint32_t tag_ref) {
   for (int c = 0; c < 2; ++c) {
     for (int b = 0; b < B; ++b) {
       int8_t *sb = spin + (size_t)b * L->N;
       const uint32_t *T = tab[temp_of[b]];
+      const int id = rid ? rid[b] : b;
       for (int lin = 0; lin < L->N; ++lin) {
         if (or_colour(L, lin) != c) continue;
         int64_t I = or_field(L, J, h, sb, lin);
         uint32_t u = or_uniform32(seed, (uint32_t)(lin >> 1), s,
-                                  ((uint32_t)c << 16) | (uint32_t)(b >> 3), ent, tag_main,
-                                  tag_ref, b & 7);
+                                  ((uint32_t)c << 16) | (uint32_t)(id >> 3), ent, tag_main,
+                                  tag_ref, id & 7);
         sb[lin] = (u < T[I + Imax]) ? 1 : -1;
       }
     }
@@ -78,8 +80,9 @@ typedef struct {
   double *beta;
   int64_t Imax;
   uint32_t **tab;
-  int32_t *temp_of, *buf_of;
+  int32_t *temp_of, *rid;   /* per slot: temperature r, replica id a*Tp + r */
   int8_t *spin;
+  int8_t *tmp;
   int64_t *E;
   uint32_t ent;
   int64_t best_E, best_sweep, hit_sweep, target;
@@ -102,7 +105,7 @@ static void entry_free(apt_entry *e) {
   if (e->tab)
     for (int t = 0; t < e->T; ++t) free(e->tab[t]);
   free(e->tab);
-  free(e->J); free(e->h); free(e->beta); free(e->temp_of); free(e->buf_of);
+  free(e->J); free(e->h); free(e->beta); free(e->temp_of); free(e->rid); free(e->tmp);
   free(e->spin); free(e->E); free(e->best_spin); free(e->att); free(e->acc);
   free(e->queue); free(e->inC);
   or_lat_free(&e->L);
@@ -151,10 +154,12 @@ int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *
     e->tab = (uint32_t **)calloc((size_t)e->T, sizeof(uint32_t *));
     for (int t = 0; t < e->T; ++t) e->tab[t] = make_table(e->beta[t], e->Imax);
     e->temp_of = (int32_t *)malloc(sizeof(int32_t) * e->B);
-    e->buf_of = (int32_t *)malloc(sizeof(int32_t) * e->B);
+    e->rid = (int32_t *)malloc(sizeof(int32_t) * e->B);
+    e->tmp = (int8_t *)malloc((size_t)N);
+    const int Tp = 8 * ((e->T + 7) / 8);
     for (int b = 0; b < e->B; ++b) {
-      e->temp_of[b] = b / e->A;     /* buffer b starts at temperature b / A */
-      e->buf_of[b] = b;             /* with label b % A */
+      e->temp_of[b] = b / e->A;                      /* slot b = (r, a) = (b / A, b % A) */
+      e->rid[b] = (b % e->A) * Tp + b / e->A;
     }
     e->spin = (int8_t *)malloc((size_t)e->B * N);
     e->E = (int64_t *)malloc(sizeof(int64_t) * e->B);
@@ -168,7 +173,7 @@ int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *
     e->best_buf = -1;
     e->hit_sweep = -1;
     e->target = INT64_MIN;
-    init_spins(&e->L, e->B, e->spin, seed, e->ent, OR_TAG_APT_INIT);
+    init_spins(&e->L, e->B, e->rid, e->spin, seed, e->ent, OR_TAG_APT_INIT);
     for (int b = 0; b < e->B; ++b)
       e->E[b] = or_energy_lat(&e->L, e->J, e->h, e->spin + (size_t)b * N);
     joff += (size_t)N;
@@ -282,20 +287,25 @@ int or_icm_apply(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, i
  * each pair every label decides on its own with
  * p_swap = min(1, exp(dbeta dE)), dE = E_{r+1} - E_r, dbeta = b_{r+1}-b_r. */
 static void swap_step(apt_entry *e, uint64_t seed, uint32_t t) {
+  const int N = e->L.N;
   for (int r = (int)(t & 1u); r + 1 < e->T; r += 2) {
     for (int a = 0; a < e->A; ++a) {
-      int bA = e->buf_of[r * e->A + a], bB = e->buf_of[(r + 1) * e->A + a];
-      int64_t dE = e->E[bB] - e->E[bA];
+      const int sA = r * e->A + a, sB = (r + 1) * e->A + a;
+      int64_t dE = e->E[sB] - e->E[sA];
       uint32_t ctr[4] = {(uint32_t)r, t, (uint32_t)a, (e->ent << 8) | OR_TAG_SWAP}, x[4];
       or_philox(ctr, seed, x);
       int accept = (dE >= 0) || (x[0] < or_swap_threshold(e->beta[r + 1] - e->beta[r], dE));
       e->att[r * e->A + a]++;
       if (accept) {
+        /* swap the p-bit states (and energies) of the two replicas */
+        int8_t *pA = e->spin + (size_t)sA * N, *pB = e->spin + (size_t)sB * N;
+        memcpy(e->tmp, pA, (size_t)N);
+        memcpy(pA, pB, (size_t)N);
+        memcpy(pB, e->tmp, (size_t)N);
+        int64_t te = e->E[sA];
+        e->E[sA] = e->E[sB];
+        e->E[sB] = te;
         e->acc[r * e->A + a]++;
-        e->buf_of[r * e->A + a] = bB;
-        e->buf_of[(r + 1) * e->A + a] = bA;
-        e->temp_of[bA] = r + 1;
-        e->temp_of[bB] = r;
       }
     }
   }
@@ -318,14 +328,14 @@ int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int thr
     for (int64_t k = 0; k < n_swaps; ++k) {
       uint32_t t = (uint32_t)(t0 + k);
       for (int q = 0; q < sweeps_per_swap; ++q, ++s)
-        gibbs_sweep(&e->L, e->J, e->h, e->Imax, e->B, e->spin, e->temp_of, e->tab, a->seed,
+        gibbs_sweep(&e->L, e->J, e->h, e->Imax, e->B, e->rid, e->spin, e->temp_of, e->tab, a->seed,
                     e->ent, (uint32_t)s, OR_TAG_APT_SWEEP, OR_TAG_APT_REFINE);
       for (int b = 0; b < e->B; ++b)
         e->E[b] = or_energy_lat(&e->L, e->J, e->h, e->spin + (size_t)b * e->L.N);
       best_update(e, s);
       if (icm) {
         for (int r = 0; r < e->T; ++r)
-          icm_op(e, a->seed, e->buf_of[r * 2 + 0], e->buf_of[r * 2 + 1], (uint32_t)r, t, 0u);
+          icm_op(e, a->seed, 2 * r, 2 * r + 1, (uint32_t)r, t, 0u);
         best_update(e, s);
       }
       swap_step(e, a->seed, t);
@@ -400,7 +410,7 @@ int or_adaptive_ladder(const int32_t dims[3], const uint8_t periodic[3], const i
   int32_t *temp_of = (int32_t *)calloc((size_t)n_chains, sizeof(int32_t));
   int64_t *sE = (int64_t *)malloc(sizeof(int64_t) * n_chains);
   int64_t *sE2 = (int64_t *)malloc(sizeof(int64_t) * n_chains);
-  init_spins(&L, n_chains, spin, seed, entry, OR_TAG_LAD_INIT);
+  init_spins(&L, n_chains, NULL, spin, seed, entry, OR_TAG_LAD_INIT);
   double beta = beta0;
   int len = 0, status = 1;
   uint32_t s = 0;
@@ -409,7 +419,7 @@ int or_adaptive_ladder(const int32_t dims[3], const uint8_t periodic[3], const i
     memset(sE, 0, sizeof(int64_t) * n_chains);
     memset(sE2, 0, sizeof(int64_t) * n_chains);
     for (int k = 0; k < sweeps; ++k, ++s) {
-      gibbs_sweep(&L, J, h, Imax, n_chains, spin, temp_of, &tab, seed, entry, s,
+      gibbs_sweep(&L, J, h, Imax, n_chains, NULL, spin, temp_of, &tab, seed, entry, s,
                   OR_TAG_LAD_SWEEP, OR_TAG_LAD_REFINE);
       if (k >= sweeps - tail) {
         for (int b = 0; b < n_chains; ++b) {
@@ -458,10 +468,10 @@ int or_pilot_hist(const int32_t dims[3], const uint8_t periodic[3], const int8_t
   for (int b = 0; b < B; ++b) temp_of[b] = b / chains_per_beta;
   for (int t = 0; t < n_beta; ++t) tab[t] = make_table(betas[t], Imax);
   memset(counts, 0, sizeof(int64_t) * (size_t)n_beta * n_bins);
-  init_spins(&L, B, spin, seed, entry, OR_TAG_PIL_INIT);
+  init_spins(&L, B, NULL, spin, seed, entry, OR_TAG_PIL_INIT);
   int64_t span = 3 * (int64_t)N;
   for (int s = 0; s < sweeps; ++s) {
-    gibbs_sweep(&L, J, h, Imax, B, spin, temp_of, tab, seed, entry, (uint32_t)s,
+    gibbs_sweep(&L, J, h, Imax, B, NULL, spin, temp_of, tab, seed, entry, (uint32_t)s,
                 OR_TAG_PIL_SWEEP, OR_TAG_PIL_REFINE);
     if (s < burn) continue;
     for (int b = 0; b < B; ++b) {

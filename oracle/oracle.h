@@ -17,9 +17,10 @@
  *   key  = (seed & 0xffffffff, seed >> 32)
  *   half v_i of a Philox output block x[0..3], i in 0..7:
  *        (x[i >> 1] >> (16 * (i & 1))) & 0xffff
- *   sampler replica ("buffer") b of problem entry e: group g = b >> 3,
- *   nibble i = b & 7.  A site lin of colour c = (x+y+z)&1 has colour-local
- *   index j = lin >> 1.
+ *   sampler replica id b of problem entry e: group g = b >> 3, nibble
+ *   i = b & 7 (APT: the replica in slot (temperature r, label a) has id
+ *   a * Tp + r, Tp = 8 ceil(T/8); ladder and pilot chains: id = chain).
+ *   A site lin of colour c = (x+y+z)&1 has colour-local index j = lin >> 1.
  *   update uniform u (32 bits) at sweep s:
  *        hi = v_i(Philox((j, s, (c<<16)|g, (e<<8)|TAG_MAIN)))
  *        lo = v_i(Philox((j, s, (c<<16)|g, (e<<8)|TAG_REFINE)))
@@ -70,7 +71,8 @@ void or_apt_destroy(or_apt *a);
    icm: 0 off, 1 on.  threads: OpenMP threads over problems (<=0: default). */
 int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int threads);
 int or_apt_set_target(or_apt *a, int inst, int64_t e_target);
-/* spins [B][N] in buffer order; energies [B]; temp index of each buffer [B]. */
+/* spins [B][N] in slot order (slot r*A + a: temperature r, label a);
+   energies [B]; temperature index of each slot [B] (= slot / A). */
 int or_apt_state(const or_apt *a, int inst, int8_t *spins, int64_t *energies, int32_t *temp_of);
 /* best energy, sweep count when found, buffer, target hit sweep (-1: never). */
 int or_apt_best(const or_apt *a, int inst, int64_t *E, int64_t *sweep, int32_t *buf,

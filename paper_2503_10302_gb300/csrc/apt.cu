@@ -13,8 +13,14 @@
 // replicas.  All replicas of a problem share the couplings, hence one word
 // gives the nibble-packed satisfied-bond counts of eight replicas with six
 // XOR/ADD pairs, and one Philox4x32-10 call gives their eight 16-bit
-// uniforms.  Swaps exchange temperatures between buffers (the buffer ->
-// temperature map), so replica states never move.
+// uniforms.
+//
+// Replica slots are fixed: temperature r with ICM label a lives in buffer
+// a*Tp + r (Tp = 8 ceil(T/8)), so the two labels of temperature r sit in the
+// same nibble of groups h and h + G/2.  An accepted swap exchanges the two
+// replicas' states (Algorithm S2) with SWAR nibble swaps, and the overlap of
+// eight ICM pairs is one XOR of two words, which makes the cluster growth a
+// nibble-parallel flood fill over all pairs at once.
 #include <cuda_runtime.h>
 
 #include "apt_dev.h"
@@ -108,21 +114,28 @@ struct Shared {
   uint32_t *thr;     // [Gc*8][8]
   uint32_t *thrh;    // [Gc*8][8] high halves
   int32_t *temp_of;  // [Gc*8]
-  int32_t *buf_of;   // [Gc*8]
+  int32_t *buf_of;   // [Gc*8] (unused by the fixed-slot APT mode)
   int32_t *E;        // [Gc*8]
   int32_t *Eacc;     // [Gc*8]
   int32_t *satt, *sacc;   // [64] swap attempts / accepts of this launch
   int32_t *hist;     // pilot histogram [T][n_bins]
   int64_t *sum1, *sum2;   // ladder sums [Gc*8]
   int64_t *m64;      // best E, best sweep, hit sweep, target
-  int32_t *m32;      // best buffer, flag, icm counters x3
+  int32_t *m32;      // best buffer, flag, icm counters x3, any-swap flag
   uint8_t *jn;       // [2][H]
-  uint32_t *icm;     // per warp 4 x nw words
+  uint32_t *V;       // ICM cluster nibbles [G/2][2][H]
+  uint32_t *ikx;     // [64] per pair: Philox word 0, then k
+  int32_t *ibit;     // [64] per pair: replica choice bit
+  int32_t *inm;      // [64] per pair: mismatch count
+  int32_t *isz;      // [64] per pair: cluster size
+  uint32_t *imask;   // [3][8] per half-group: cluster-flip, whole-flip label 0, label 1
+  uint32_t *swm;     // [8] per group: in-group swap nibble mask; [8] cross-group flags
+  uint32_t *scan;    // [nwarps + 1][16] block-scan scratch
 };
 
 struct Cta {
   Geo geo;
-  int T, A, B, Bc, Gc, g0;
+  int T, Tp, A, B, Bc, Gc, g0;
   uint32_t ent;
   // thread chunking of the site loop: nch chunks of tpc threads, gc groups each
   int nch, tpc, gc;
@@ -217,25 +230,30 @@ __device__ __forceinline__ void finish_energies(const Cta &k, const Shared &sh) 
 }
 
 // Minimum-energy selection (Algorithm S2 output): strict improvement, lowest
-// buffer index on ties; copies the state of the new best replica.
+// slot index (r * A + a) on ties; copies the state of the new best replica.
 __device__ void best_update(const AptArgs &a, const Cta &k, const Shared &sh, int p,
                             int64_t sweeps) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    int bestE = 0x7FFFFFFF, bestb = 0x7FFFFFFF;
-    for (int b = lane; b < k.Bc; b += 32) {
-      const int e = sh.E[b];
-      if (e < bestE || (e == bestE && b < bestb)) {
+    int bestE = 0x7FFFFFFF, bests = 0x7FFFFFFF, bestb = 0;
+    for (int b = lane; b < 8 * k.Gc; b += 32) {
+      const int r = b % k.Tp, lab = b / k.Tp;
+      if (r >= k.T) continue;
+      const int e = sh.E[b], slot = r * k.A + lab;
+      if (e < bestE || (e == bestE && slot < bests)) {
         bestE = e;
+        bests = slot;
         bestb = b;
       }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const int oe = __shfl_xor_sync(0xFFFFFFFFu, bestE, o);
+      const int os = __shfl_xor_sync(0xFFFFFFFFu, bests, o);
       const int ob = __shfl_xor_sync(0xFFFFFFFFu, bestb, o);
-      if (oe < bestE || (oe == bestE && ob < bestb)) {
+      if (oe < bestE || (oe == bestE && os < bests)) {
         bestE = oe;
+        bests = os;
         bestb = ob;
       }
     }
@@ -265,202 +283,257 @@ __device__ void best_update(const AptArgs &a, const Cta &k, const Shared &sh, in
   __syncthreads();
 }
 
-// ICMop (Algorithm S2) of one pair of buffers by one warp.  Canonical site
-// order k = c*H + j.  M = mismatch bits, V = cluster bits, F/F2 = BFS
-// frontiers (warp-private shared memory).
-__device__ void icm_pair(const AptArgs &a, const Cta &k, const Shared &sh, int r, uint32_t t,
-                         int ba, int bb, uint32_t *M, uint32_t *V, uint32_t *F, uint32_t *F2) {
-  const int lane = threadIdx.x & 31;
-  const Geo &geo = k.geo;
-  const int N = geo.N, H = geo.H, nw = (N + 31) >> 5;
-  const int ga = ba >> 3, ia = ba & 7, gb = bb >> 3, ib = bb & 7;
-  uint32_t *Sa = sh.S + (size_t)2 * ga * H, *Sb = sh.S + (size_t)2 * gb * H;
-  // overlap q_i = s_i^a s_i^b: mismatch bitmask
-  int nminus = 0;
-  for (int w = 0; w < nw; ++w) {
-    const int kk = 32 * w + lane;
-    bool mm = false;
-    if (kk < N) {
-      const int c = kk >= H ? 1 : 0, j = kk - c * H;
-      mm = (((Sa[c * H + j] >> (4 * ia)) ^ (Sb[c * H + j] >> (4 * ib))) & 1u) != 0;
-    }
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, mm);
-    if (lane == 0) M[w] = m;
-    nminus += __popc(m);
-  }
-  if (nminus == 0) {
-    if (lane == 0) atomicAdd(&sh.m32[2], 1);
-    return;
-  }
-  const uint4 x = philox((uint32_t)r, t, 0u, (k.ent << 8) | TAG_ICM, a.k0, a.k1);
-  const int kth = (int)(((uint64_t)x.x * (uint64_t)nminus) >> 32);
-  __syncwarp();
-  // the kth mismatch site in canonical order: lane owns words [lane*wpl, ...)
-  const int wpl = (nw + 31) >> 5;
-  int local = 0;
-  for (int w = lane * wpl; w < (lane + 1) * wpl && w < nw; ++w) local += __popc(M[w]);
-  int incl = local;
+// Block-wide exclusive scan of 16 words of two 16-bit lanes each (lane
+// totals < 2^16).  Returns the exclusive prefix in ex[] and the block total
+// in tot[] (valid in every thread).
+__device__ __forceinline__ void block_scan16(const Shared &sh, const uint32_t (&v)[16],
+                                             uint32_t (&ex)[16], uint32_t (&tot)[16]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint32_t inc[16];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += v;
+  for (int q = 0; q < 16; ++q) {
+    uint32_t x = v[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    inc[q] = x;
+    if (lane == 31) sh.scan[16 * warp + q] = x;
   }
-  const int excl = incl - local;
-  int seed = -1;
-  if (kth >= excl && kth < incl) {
-    int rem = kth - excl;
-    for (int w = lane * wpl; w < (lane + 1) * wpl && w < nw; ++w) {
-      const uint32_t m = M[w];
-      const int pc = __popc(m);
-      if (rem < pc) {
-        seed = 32 * w + (int)__fns(m, 0, rem + 1);
-        break;
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      uint32_t x = lane < nwarps ? sh.scan[16 * lane + q] : 0u;
+      uint32_t y = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t z = __shfl_up_sync(0xFFFFFFFFu, y, o);
+        if (lane >= o) y += z;
       }
-      rem -= pc;
+      if (lane < nwarps) sh.scan[16 * lane + q] = y - x;   // exclusive warp offsets
+      if (lane == 31) sh.scan[16 * nwarps + q] = y;        // block total
     }
   }
+  __syncthreads();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) seed = max(seed, __shfl_xor_sync(0xFFFFFFFFu, seed, o));
-  // grow the cluster of the seed: level-synchronous BFS on the mismatch graph
-  for (int w = lane; w < nw; w += 32) {
-    V[w] = 0;
-    F[w] = 0;
-    F2[w] = 0;
+  for (int q = 0; q < 16; ++q) {
+    ex[q] = sh.scan[16 * warp + q] + inc[q] - v[q];
+    tot[q] = sh.scan[16 * nwarps + q];
   }
-  __syncwarp();
-  if (lane == 0) {
-    V[seed >> 5] = 1u << (seed & 31);
-    F[seed >> 5] = 1u << (seed & 31);
+  __syncthreads();
+}
+
+// ICMop of Algorithm S2 for every temperature at once.  Pair r = 8h + i is
+// nibble i of groups h (label 0) and h + Gh (label 1), so the overlap of
+// eight pairs is X = S[h] ^ S[h + Gh].  The seed of pair r is the k-th site
+// (canonical order c*H + j) with X set, k = floor(x0 n_minus / 2^32); its
+// cluster is grown by an in-place flood fill V <- V | (X & OR_nbr V),
+// alternating colours, until no pair's cluster changes.  Clusters larger
+// than N/2 flip one whole replica (x1 bit 0: label 0 or 1), smaller ones
+// flip in both replicas; then all energies are recomputed.
+__device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32_t t) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int N = k.geo.N, H = k.geo.H, Gh = k.Gc >> 1;
+  const uint32_t *S = sh.S;
+  uint32_t *V = sh.V;
+  if (tid < 8 * Gh) {
+    const int r = tid;
+    if (r < k.T) {
+      const uint4 x = philox((uint32_t)r, t, 0u, (k.ent << 8) | TAG_ICM, a.k0, a.k1);
+      sh.ikx[r] = x.x;
+      sh.ibit[r] = (int)(x.y & 1u);
+    }
+    sh.isz[r] = 0;
   }
-  __syncwarp();
-  int size = 1;
-  const int half = N >> 1;
-  for (int iter = 0; iter <= N; ++iter) {
-    int added = 0;
-    for (int w = lane; w < nw; w += 32) {
-      uint32_t f = F[w];
-      if (!f) continue;
-      F[w] = 0;
-      while (f) {
-        const int bit = __ffs(f) - 1;
-        f &= f - 1;
-        const int v = 32 * w + bit;
-        const int c = v >= H ? 1 : 0, j = v - c * H;
+  if (tid < 24) sh.imask[tid] = 0;
+  // (A) mismatch counts over this thread's contiguous canonical range
+  const int cr = (N + nt - 1) / nt, k0 = min(N, tid * cr), k1 = min(N, k0 + cr);
+  uint32_t cnt[16], ex[16], tot[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) cnt[q] = 0;
+  for (int kk = k0; kk < k1; ++kk) {
+    const int c = kk >= H ? 1 : 0, j = kk - c * H;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      if (h >= Gh) break;
+      const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
+      V[(2 * h + c) * H + j] = 0u;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) cnt[4 * h + m] += (x >> (4 * m)) & 0x000F000Fu;
+    }
+  }
+  block_scan16(sh, cnt, ex, tot);
+  // lane (h, m) low 16 bits: pair 8h + m; high 16 bits: pair 8h + m + 4
+  if (tid < 8 * Gh) {
+    const int r = tid, h = r >> 3, i = r & 7, q = 4 * h + (i & 3);
+    const int nm = (int)((tot[q] >> ((i >> 2) * 16)) & 0xFFFFu);
+    sh.inm[r] = nm;
+    if (r < k.T) sh.ikx[r] = (uint32_t)(((uint64_t)sh.ikx[r] * (uint64_t)nm) >> 32);
+  }
+  __syncthreads();
+  // seeds: the thread whose range holds the k-th mismatch of a pair plants it
+  for (int r = 0; r < k.T; ++r) {
+    const int h = r >> 3, i = r & 7, q = 4 * h + (i & 3), sh16 = (i >> 2) * 16;
+    const int nm = sh.inm[r];
+    if (nm == 0) continue;
+    const int kth = (int)sh.ikx[r];
+    const int lo = (int)((ex[q] >> sh16) & 0xFFFFu), n = (int)((cnt[q] >> sh16) & 0xFFFFu);
+    if (kth < lo || kth >= lo + n) continue;
+    int rem = kth - lo;
+    for (int kk = k0; kk < k1; ++kk) {
+      const int c = kk >= H ? 1 : 0, j = kk - c * H;
+      const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
+      if ((x >> (4 * i)) & 1u) {
+        if (rem == 0) {
+          V[(2 * h + c) * H + j] |= 1u << (4 * i);
+          break;
+        }
+        --rem;
+      }
+    }
+  }
+  __syncthreads();
+  // (B) flood fill, alternating colours in place
+  for (int it = 0; it < N; ++it) {
+    int changed = 0;
+    for (int c = 0; c < 2; ++c) {
+      for (int j = tid; j < H; j += nt) {
         int n[6];
-        neighbours(geo, c, j, n);
+        bool nb_ready = false;
 #pragma unroll
-        for (int d = 0; d < 6; ++d) {
-          const int u = (1 - c) * H + n[d];
-          const uint32_t mb = 1u << (u & 31);
-          if ((M[u >> 5] & mb) && !(V[u >> 5] & mb)) {
-            const uint32_t old = atomicOr(&V[u >> 5], mb);
-            if (!(old & mb)) {
-              atomicOr(&F2[u >> 5], mb);
-              ++added;
-            }
+        for (int h = 0; h < 4; ++h) {
+          if (h >= Gh) break;
+          const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
+          if (!x) continue;
+          if (!nb_ready) {
+            neighbours(k.geo, c, j, n);
+            nb_ready = true;
+          }
+          const uint32_t *Vo = V + (2 * h + (1 - c)) * H;
+          const uint32_t o = Vo[n[0]] | Vo[n[1]] | Vo[n[2]] | Vo[n[3]] | Vo[n[4]] | Vo[n[5]];
+          const uint32_t v = V[(2 * h + c) * H + j];
+          const uint32_t nv = v | (x & o);
+          if (nv != v) {
+            V[(2 * h + c) * H + j] = nv;
+            changed = 1;
           }
         }
       }
+      __syncthreads();
     }
-    added = warp_sum(added);
-    size += added;
-    __syncwarp();
-    uint32_t *tmp = F;
-    F = F2;
-    F2 = tmp;
-    if (added == 0 || 2 * size > N) break;
+    if (!__syncthreads_or(changed)) break;
   }
-  (void)half;
-  if (2 * size > N) {
-    // more than half of all spins: flip one whole replica (x.y bit 0: 0 -> a, 1 -> b)
-    const int bt = (x.y & 1u) ? bb : ba;
-    const int gt = bt >> 3;
-    const uint32_t mask = 1u << (4 * (bt & 7));
-    uint32_t *St = sh.S + (size_t)2 * gt * H;
-    for (int kk = lane; kk < N; kk += 32) atomicXor(&St[kk], mask);   // [2][H] is contiguous
-    if (lane == 0) atomicAdd(&sh.m32[4], 1);
-    return;   // h = 0: energies unchanged
-  }
-  // energy change of replica a: bonds leaving the cluster change sign
-  int dEa = 0;
-  for (int w = lane; w < nw; w += 32) {
-    uint32_t f = V[w];
-    while (f) {
-      const int bit = __ffs(f) - 1;
-      f &= f - 1;
-      const int v = 32 * w + bit;
-      const int c = v >= H ? 1 : 0, j = v - c * H;
-      int n[6];
-      neighbours(geo, c, j, n);
-      const uint32_t jb = sh.jn[c * H + j];
-      const int sv = (int)((Sa[c * H + j] >> (4 * ia)) & 1u);
+  // (C) cluster sizes
 #pragma unroll
-      for (int d = 0; d < 6; ++d) {
-        const int u = (1 - c) * H + n[d];
-        if (V[u >> 5] & (1u << (u & 31))) continue;
-        const int sn = (int)((Sa[(1 - c) * H + n[d]] >> (4 * ia)) & 1u);
-        // J s_v s_n = +1 iff (s_v == s_n) xor (J = -1)
-        const int prod = ((sv ^ sn ^ (int)((jb >> d) & 1u)) == 0) ? 1 : -1;
-        dEa += 2 * prod;
-      }
+  for (int q = 0; q < 16; ++q) cnt[q] = 0;
+  for (int kk = k0; kk < k1; ++kk) {
+    const int c = kk >= H ? 1 : 0, j = kk - c * H;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      if (h >= Gh) break;
+      const uint32_t v = V[(2 * h + c) * H + j];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) cnt[4 * h + m] += (v >> (4 * m)) & 0x000F000Fu;
     }
   }
-  dEa = warp_sum(dEa);
-  __syncwarp();
-  const uint32_t ma = 1u << (4 * ia), mb2 = 1u << (4 * ib);
-  for (int w = lane; w < nw; w += 32) {
-    uint32_t f = V[w];
-    while (f) {
-      const int bit = __ffs(f) - 1;
-      f &= f - 1;
-      const int v = 32 * w + bit;
-      atomicXor(Sa + v, ma);
-      atomicXor(Sb + v, mb2);
+  block_scan16(sh, cnt, ex, tot);
+  // (D) decisions
+  if (tid < k.T) {
+    const int r = tid, h = r >> 3, i = r & 7, q = 4 * h + (i & 3);
+    const int size = (int)((tot[q] >> ((i >> 2) * 16)) & 0xFFFFu);
+    const uint32_t bit = 1u << (4 * i);
+    if (sh.inm[r] == 0) {
+      atomicAdd(&sh.m32[2], 1);
+    } else if (2 * size > N) {
+      atomicOr(&sh.imask[8 + 8 * sh.ibit[r] + h], bit);   // whole replica of label ibit
+      atomicAdd(&sh.m32[4], 1);
+    } else {
+      atomicOr(&sh.imask[h], bit);                          // cluster, both replicas
+      atomicAdd(&sh.m32[3], 1);
     }
   }
-  if (lane == 0) {
-    sh.E[ba] += dEa;
-    sh.E[bb] -= dEa;
-    atomicAdd(&sh.m32[3], 1);
+  __syncthreads();
+  // (E) flips
+  for (int kk = tid; kk < N; kk += nt) {
+    const int c = kk >= H ? 1 : 0, j = kk - c * H;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      if (h >= Gh) break;
+      const uint32_t vv = V[(2 * h + c) * H + j] & sh.imask[h];
+      sh.S[(2 * h + c) * H + j] ^= vv | sh.imask[8 + h];
+      sh.S[(2 * (h + Gh) + c) * H + j] ^= vv | sh.imask[16 + h];
+    }
   }
+  __syncthreads();
+  // (F) energies after the moves
+  colour_phase<false, true>(a, k, sh, 1, 0u);
+  __syncthreads();
+  finish_energies(k, sh);
+  __syncthreads();
 }
 
 // Replica exchange of attempt t (Sec. "Comparison with Adaptive Parallel
 // Tempering"; Methods): even t pairs (0,1),(2,3)..., odd t (1,2),(3,4)...;
-// each label decides on its own; p_swap = min(1, exp(dbeta dE)).
+// each label decides on its own; p_swap = min(1, exp(dbeta dE)).  Accepted
+// pairs exchange their p-bit states (SWAR nibble swaps over all sites) and
+// energies.
 __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int p, uint32_t t) {
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
   const AptProbDev &P = a.prob[p];
-  const int q = (int)(t & 1u);
-  const int np = (k.T - q) / 2;
-  const int A = k.A;
-  for (int idx = lane; idx < np * A; idx += 32) {
-    const int r = q + 2 * (idx / A), al = idx % A;
-    const int bA = sh.buf_of[r * A + al], bB = sh.buf_of[(r + 1) * A + al];
-    const int dE = sh.E[bB] - sh.E[bA];
-    bool acc = dE >= 0;
-    if (!acc) {
-      const uint4 x = philox((uint32_t)r, t, (uint32_t)al, (k.ent << 8) | TAG_SWAP, a.k0, a.k1);
-      const int kk = (-dE) >> 1;
-      const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
-      const uint32_t th = ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
-      acc = x.x < th;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane < 16) sh.swm[lane] = 0;
+    __syncwarp();
+    const int q = (int)(t & 1u);
+    const int np = (k.T - q) / 2;
+    const int A = k.A;
+    int any = 0;
+    for (int idx = lane; idx < np * A; idx += 32) {
+      const int r = q + 2 * (idx / A), al = idx % A;
+      const int bA = al * k.Tp + r, bB = bA + 1;
+      const int dE = sh.E[bB] - sh.E[bA];
+      bool acc = dE >= 0;
+      if (!acc) {
+        const uint4 x = philox((uint32_t)r, t, (uint32_t)al, (k.ent << 8) | TAG_SWAP, a.k0, a.k1);
+        const int kk = (-dE) >> 1;
+        const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
+        const uint32_t th = ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
+        acc = x.x < th;
+      }
+      sh.satt[r * A + al] += 1;
+      if (acc) {
+        sh.sacc[r * A + al] += 1;
+        const int eA = sh.E[bA];
+        sh.E[bA] = sh.E[bB];
+        sh.E[bB] = eA;
+        if ((bA & 7) != 7) atomicOr(&sh.swm[bA >> 3], 1u << (4 * (bA & 7)));
+        else sh.swm[8 + (bA >> 3)] = 1u;
+        any = 1;
+      }
     }
-    sh.satt[r * A + al] += 1;
-    if (acc) {
-      sh.sacc[r * A + al] += 1;
-      sh.buf_of[r * A + al] = bB;
-      sh.buf_of[(r + 1) * A + al] = bA;
-      sh.temp_of[bA] = r + 1;
-      sh.temp_of[bB] = r;
-      const uint32_t *tA = a.pbit + P.pbit_off + 8 * (r + 1), *tB = a.pbit + P.pbit_off + 8 * r;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        sh.thr[8 * bA + e] = tA[e];
-        sh.thrh[8 * bA + e] = tA[e] & 0xFFFF0000u;
-        sh.thr[8 * bB + e] = tB[e];
-        sh.thrh[8 * bB + e] = tB[e] & 0xFFFF0000u;
+    any = __any_sync(0xFFFFFFFFu, any);
+    if (lane == 0) sh.m32[5] = any;
+  }
+  __syncthreads();
+  if (!sh.m32[5]) return;
+  const int H = k.geo.H, G = k.Gc;
+  for (int kk = threadIdx.x; kk < 2 * H; kk += blockDim.x) {
+    uint32_t *col = sh.S + kk;   // word (g, c, j) at col[g * 2H]
+    for (int g = 0; g < G; ++g) {
+      const uint32_t m = sh.swm[g];
+      if (m) {
+        uint32_t w = col[(size_t)g * 2 * H];
+        const uint32_t d = (w ^ (w >> 4)) & m;
+        col[(size_t)g * 2 * H] = w ^ (d | (d << 4));
+      }
+    }
+    for (int g = 0; g + 1 < G; ++g) {
+      if (sh.swm[8 + g]) {
+        uint32_t w0 = col[(size_t)g * 2 * H], w1 = col[(size_t)(g + 1) * 2 * H];
+        const uint32_t d = ((w0 >> 28) ^ w1) & 1u;
+        col[(size_t)g * 2 * H] = w0 ^ (d << 28);
+        col[(size_t)(g + 1) * 2 * H] = w1 ^ d;
       }
     }
   }
@@ -481,6 +554,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.geo.mhx = P.mhx;
   k.geo.mLy = P.mLy;
   k.T = P.T;
+  k.Tp = P.Tp;
   k.A = P.A;
   k.B = P.B;
   k.g0 = a.cta_g0[cta];
@@ -493,7 +567,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   const int N = P.N, G8 = 8 * k.Gc;
   const int nwarps = blockDim.x >> 5;
   const int64_t s0 = a.ctr[0], t0 = a.ctr[1];
-  const int nw = (N + 31) >> 5;
+  const bool icm = a.mode == pc::APT_MODE_APT && a.icm;
   // carve shared memory
   Shared sh;
   uint32_t *cur = smem;
@@ -512,7 +586,14 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.sum1 = reinterpret_cast<int64_t *>(cur);     cur += 2 * G8;
   sh.sum2 = reinterpret_cast<int64_t *>(cur);     cur += 2 * G8;
   sh.hist = reinterpret_cast<int32_t *>(cur);     cur += a.mode == pc::APT_MODE_PILOT ? k.T * a.n_bins : 0;
-  sh.icm = cur;          cur += (a.mode == pc::APT_MODE_APT && a.icm) ? 4 * nw * nwarps : 0;
+  sh.ikx = cur;                                   cur += 64;
+  sh.ibit = reinterpret_cast<int32_t *>(cur);     cur += 64;
+  sh.inm = reinterpret_cast<int32_t *>(cur);      cur += 64;
+  sh.isz = reinterpret_cast<int32_t *>(cur);      cur += 64;
+  sh.imask = cur;                                 cur += 24;
+  sh.swm = cur;                                   cur += 16;
+  sh.scan = cur;                                  cur += 16 * (nwarps + 1);
+  sh.V = cur;                                     cur += icm ? (size_t)(k.Gc / 2) * N : 0;
   sh.jn = reinterpret_cast<uint8_t *>(cur);
 
   // load state
@@ -588,13 +669,8 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
       if (a.mode != pc::APT_MODE_APT) continue;
       const int64_t sweeps = s0 + (int64_t)(it + 1) * a.spp;
       best_update(a, k, sh, p, sweeps);
-      if (a.icm) {
-        const int w = threadIdx.x >> 5;
-        uint32_t *base = sh.icm + (size_t)4 * nw * w;
-        for (int r = w; r < k.T; r += nwarps)
-          icm_pair(a, k, sh, r, t, sh.buf_of[2 * r], sh.buf_of[2 * r + 1], base, base + nw,
-                   base + 2 * nw, base + 3 * nw);
-        __syncthreads();
+      if (icm) {
+        icm_all(a, k, sh, t);
         best_update(a, k, sh, p, sweeps);
       }
       swap_step(a, k, sh, p, t);
@@ -667,8 +743,9 @@ namespace pc {
 size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins) {
   const size_t G8 = 8 * (size_t)Gc;
   size_t words = (size_t)Gc * N + 16 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
+  words += 4 * 64 + 24 + 16 + 16 * ((size_t)nwarps + 1);
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
-  if (mode == APT_MODE_APT && icm) words += (size_t)4 * ((N + 31) / 32) * nwarps;
+  if (mode == APT_MODE_APT && icm) words += (size_t)(Gc / 2) * N;
   return words * 4 + (size_t)N + 16;
 }
 

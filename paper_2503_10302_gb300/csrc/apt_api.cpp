@@ -87,7 +87,7 @@ void unpack_spins(const AptProbDev &P, const uint32_t *words, int B, int8_t *out
 struct ProbSpec {
   Lattice lat;
   const int8_t *J;
-  int T, A, B;
+  int T, Tp, A, B;
   uint32_t ent;
   std::vector<double> beta;       // [T] (ladder: 1 entry, pilot: n_beta)
   std::vector<int32_t> temp_of;   // [B]
@@ -118,6 +118,7 @@ int build_batch(pc_ctx *c, Batch &bt, const std::vector<ProbSpec> &specs, int n_
     P.mhx = recip32((uint32_t)(P.Lx / 2));
     P.mLy = recip32((uint32_t)P.Ly);
     P.T = s.T;
+    P.Tp = s.Tp;
     P.A = s.A;
     P.B = s.B;
     P.ent = s.ent;
@@ -336,8 +337,10 @@ int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, con
     s.J = J + 3 * joff;
     s.T = n_temps[i];
     s.A = n_labels;
-    s.B = s.T * n_labels;
-    if (s.T < 1 || s.B > 64) return fail(PC_EINVAL, "need 1 <= n_temps and n_temps * n_labels <= 64");
+    s.Tp = 8 * ((s.T + 7) / 8);
+    s.B = s.Tp * n_labels;     // replica of (r, a) in buffer a * Tp + r
+    if (s.T < 1 || s.B > 64)
+      return fail(PC_EINVAL, "need 1 <= n_temps and 8*ceil(n_temps/8) * n_labels <= 64");
     s.ent = entry0 + (uint32_t)i;
     s.beta.assign(betas + boff, betas + boff + s.T);
     for (int t = 0; t < s.T; ++t) {
@@ -347,7 +350,7 @@ int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, con
         return fail(PC_EINVAL, "betas must be strictly increasing");
     }
     s.temp_of.resize((size_t)s.B);
-    for (int b = 0; b < s.B; ++b) s.temp_of[(size_t)b] = b / n_labels;
+    for (int b = 0; b < s.B; ++b) s.temp_of[(size_t)b] = (b % s.Tp < s.T) ? b % s.Tp : 0;
     s.swaps = true;
     joff += (size_t)s.lat.N;
     boff += (size_t)s.T;
@@ -474,18 +477,24 @@ int pc_apt_get_state(pc_ctx *c, int inst, int8_t *spins, int64_t *energies, int3
   const int G = bt.G[(size_t)inst];
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int nslot = P.T * P.A;
   if (spins) {
     std::vector<uint32_t> w((size_t)G * P.N);
     PC_CUDA_TRY(cudaMemcpy(w.data(), bt.d_spins.p + P.spin_off, w.size() * 4, cudaMemcpyDeviceToHost));
-    unpack_spins(P, w.data(), P.B, spins);
+    std::vector<int8_t> all((size_t)P.B * P.N);
+    unpack_spins(P, w.data(), P.B, all.data());
+    for (int sl = 0; sl < nslot; ++sl) {
+      const int b = (sl % P.A) * P.Tp + sl / P.A;
+      std::memcpy(spins + (size_t)sl * P.N, all.data() + (size_t)b * P.N, (size_t)P.N);
+    }
   }
   if (energies) {
     std::vector<int32_t> e((size_t)P.B);
     PC_CUDA_TRY(cudaMemcpy(e.data(), bt.d_E.p + P.buf_off, e.size() * 4, cudaMemcpyDeviceToHost));
-    for (int b = 0; b < P.B; ++b) energies[b] = e[(size_t)b];
+    for (int sl = 0; sl < nslot; ++sl) energies[sl] = e[(size_t)((sl % P.A) * P.Tp + sl / P.A)];
   }
   if (temp_of)
-    PC_CUDA_TRY(cudaMemcpy(temp_of, bt.d_temp.p + P.buf_off, (size_t)P.B * 4, cudaMemcpyDeviceToHost));
+    for (int sl = 0; sl < nslot; ++sl) temp_of[sl] = sl / P.A;
   return PC_OK;
 }
 
@@ -498,7 +507,12 @@ int pc_apt_get_best(pc_ctx *c, int inst, int64_t *E, int64_t *sweep, int32_t *bu
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (E) PC_CUDA_TRY(cudaMemcpy(E, bt.d_bestE.p + inst, 8, cudaMemcpyDeviceToHost));
   if (sweep) PC_CUDA_TRY(cudaMemcpy(sweep, bt.d_bestsweep.p + inst, 8, cudaMemcpyDeviceToHost));
-  if (buf) PC_CUDA_TRY(cudaMemcpy(buf, bt.d_bestbuf.p + inst, 4, cudaMemcpyDeviceToHost));
+  if (buf) {
+    int32_t b = -1;
+    PC_CUDA_TRY(cudaMemcpy(&b, bt.d_bestbuf.p + inst, 4, cudaMemcpyDeviceToHost));
+    const AptProbDev &P = bt.prob[(size_t)inst];
+    *buf = (b < 0) ? -1 : (b % P.Tp) * P.A + b / P.Tp;   // slot index
+  }
   if (hit_sweep) PC_CUDA_TRY(cudaMemcpy(hit_sweep, bt.d_hit.p + inst, 8, cudaMemcpyDeviceToHost));
   if (spins)
     PC_CUDA_TRY(cudaMemcpy(spins, bt.d_bestspins.p + bt.prob[(size_t)inst].best_off,
@@ -577,6 +591,7 @@ int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t 
       return fail(PC_EINVAL, "tail too long for exact int64 sums");
     s.J = J + 3 * joff;
     s.T = 1;
+    s.Tp = 1;
     s.A = 1;
     s.B = n_chains;
     s.ent = entry0 + (uint32_t)i;
@@ -688,6 +703,7 @@ int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, u
     if (rc) return rc;
     s.J = J + 3 * joff;
     s.T = n_beta;
+    s.Tp = n_beta;
     s.A = 1;
     s.B = n_beta * chains_per_beta;
     s.ent = entry0 + (uint32_t)i;

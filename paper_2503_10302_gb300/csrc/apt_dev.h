@@ -13,7 +13,8 @@ enum : int { APT_MODE_APT = 0, APT_MODE_LADDER = 1, APT_MODE_PILOT = 2, APT_MODE
 struct AptProbDev {
   int Lx, Ly, Lz, N;
   uint32_t mhx, mLy;      // ceil(2^32 / (Lx/2)), ceil(2^32 / Ly)
-  int T, A, B;            // temperatures, labels, buffers (= T * A, or chains)
+  int T, Tp, A, B;        // temperatures, padded temperatures 8*ceil(T/8), labels,
+                          // buffers (APT: A * Tp; ladder / pilot: chains)
   uint32_t ent;           // Philox entry id
   uint32_t spin_off;      // words: [G][2][N/2]
   uint32_t jneg_off;      // bytes: [2][N/2] coupling signs per (colour, j)

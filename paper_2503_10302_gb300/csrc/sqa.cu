@@ -72,14 +72,113 @@ __device__ __forceinline__ void spatial_counts(const pc::SqaArgs &a, const uint3
   }
 }
 
+// Per-site constants of the sweep: neighbour indices and the coupling
+// signs.  With s_nbr in {0,1} per nibble, J s_nbr "satisfied" is s_nbr for
+// J = +1 and 1 - s_nbr for J = -1, so the packed count of satisfied terms is
+// C = K + sum_d eps_d W_d with eps_d = +-1 and K = 0x11111111 * #(J = -1):
+// six multiply-adds per word.
+struct SiteK {
+  int nb[6];
+  int eps[6];
+  uint32_t K;
+  int q;
+};
+
+__device__ __forceinline__ SiteK site_consts(const pc::SqaArgs &a, int s, const uint8_t *jn) {
+  const Site t = site_of(a, s, jn);
+  SiteK k;
+  k.q = t.q;
+  int nneg = 0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    k.nb[d] = neighbour(a, t, d);
+    const int neg = (t.jb >> d) & 1;
+    k.eps[d] = 1 - 2 * neg;
+    nneg += neg;
+  }
+  k.K = 0x11111111u * (uint32_t)nneg;
+  return k;
+}
+
+// Threshold tables in static shared memory, so that a byte of a packed
+// index word is directly an address offset: [2 sweeps][32 entries],
+// entry c + 8 m, high halves (Th) and full values (Tf).
+__shared__ __align__(16) uint32_t s_Th[2][32];
+__shared__ __align__(16) uint32_t s_Tf[2][32];
+
+// Eq. neuron for the 8 nibbles of one word.  Byte k of Dlo / Dhi is the
+// byte offset of the threshold of nibble 2k / 2k+1 in s_Th (index * 4 plus
+// 128 for the odd sweep's buffer).
+__device__ __forceinline__ uint32_t decide_word(const uint4 &x, uint32_t Dlo, uint32_t Dhi, bool &tie) {
+  uint32_t w = 0;
+  const char *base = reinterpret_cast<const char *>(&s_Th[0][0]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t off = __byte_perm((i & 1) ? Dhi : Dlo, 0u, 0x4440u + (uint32_t)(i >> 1));
+    const uint32_t th = *reinterpret_cast<const uint32_t *>(base + off);
+    const uint32_t xw = word_of(x, i >> 1);
+    const uint32_t v = (i & 1) ? (xw & 0xFFFF0000u) : (xw << 16);
+    w |= (v < th) ? (1u << (4 * i)) : 0u;
+    tie |= (v == th);
+  }
+  return w;
+}
+
+__device__ __noinline__ uint32_t settle_ties(uint32_t w, uint4 x, uint4 y, uint32_t Dlo, uint32_t Dhi) {
+  const char *base = reinterpret_cast<const char *>(&s_Tf[0][0]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t off = __byte_perm((i & 1) ? Dhi : Dlo, 0u, 0x4440u + (uint32_t)(i >> 1));
+    const uint32_t t = *reinterpret_cast<const uint32_t *>(base + off);
+    const uint32_t v = half_hi(x, i);
+    if (v == (t & 0xFFFF0000u)) {
+      const uint32_t u = v | half_lo(y, i);
+      w = (u < t) ? (w | (1u << (4 * i))) : (w & ~(1u << (4 * i)));
+    }
+  }
+  return w;
+}
+
+// All NB words of one (site, colour) in one sweep.
 template <int NB>
-__global__ void __launch_bounds__(1024) sqa_kernel(const pc::SqaArgs a) {
+__device__ __forceinline__ void update_site(const pc::SqaArgs &a, const uint32_t *Wo, uint32_t *Wc,
+                                            int s, const SiteK &k, int c, uint32_t sw,
+                                            uint32_t boff, uint32_t ent) {
+  const int N = a.N;
+  const int e = c ^ k.q;   // slice parity of this word's nibbles
+  const uint32_t c2 = (uint32_t)c << 16;
+#pragma unroll 1
+  for (int b = 0; b < NB; ++b) {
+    const int bp = (b + 1 == NB) ? 0 : b + 1, bm = (b == 0) ? NB - 1 : b - 1;
+    const uint32_t Ob = Wo[b * N + s];
+    const uint32_t On = Wo[(e ? bp : bm) * N + s];
+    uint32_t C = k.K;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) C += (uint32_t)k.eps[d] * Wo[b * N + k.nb[d]];
+    // time neighbours k-1, k+1: the other colour's word and that word
+    // shifted by one nibble (funnel shift through the adjacent block)
+    const uint32_t lo = e ? Ob : On;
+    const uint32_t hi = e ? On : Ob;
+    const uint32_t M = Ob + __funnelshift_r(lo, hi, e ? 4u : 28u);
+    const uint32_t Dlo = ((C & 0x0F0F0F0Fu) << 2) + ((M & 0x0F0F0F0Fu) << 5) + boff;
+    const uint32_t Dhi = (((C >> 4) & 0x0F0F0F0Fu) << 2) + (((M >> 4) & 0x0F0F0F0Fu) << 5) + boff;
+    const uint4 x = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_SWEEP, a.k0, a.k1);
+    bool tie = false;
+    uint32_t w = decide_word(x, Dlo, Dhi, tie);
+    if (tie) {
+      const uint4 y = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_REFINE, a.k0, a.k1);
+      w = settle_ties(w, x, y, Dlo, Dhi);
+    }
+    Wc[b * N + s] = w;
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(512, 2) sqa_kernel(const pc::SqaArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int N = a.N, P = a.P;
-  uint32_t *W = smem;                              // [2][NB][N]
-  uint32_t *tab = W + 2 * NB * N;                  // [2][24] full thresholds
-  uint32_t *tabh = tab + 48;                       // [2][24] high halves
-  int32_t *Eacc = reinterpret_cast<int32_t *>(tabh + 48);   // [P]
+  uint32_t *W = smem;                                       // [2][NB][N]
+  int32_t *Eacc = reinterpret_cast<int32_t *>(W + 2 * NB * N);   // [P]
   uint8_t *jn = reinterpret_cast<uint8_t *>(Eacc + P);      // [N]
   const int run = blockIdx.x;
   const uint32_t ent = a.run0 + (uint32_t)run;
@@ -97,52 +196,36 @@ __global__ void __launch_bounds__(1024) sqa_kernel(const pc::SqaArgs a) {
     for (int i = 0; i < 8; ++i) w |= (half_lo(x, i) < 0x8000u) ? (1u << (4 * i)) : 0u;
     W[idx] = w;
   }
-  if (tid < 24) {
-    tab[tid] = a.table[tid];
-    tabh[tid] = a.table[tid] & 0xFFFF0000u;
+  if (tid < 32) {
+    const uint32_t t = tid < 24 ? a.table[tid] : 0u;
+    s_Tf[0][tid] = t;
+    s_Th[0][tid] = t & 0xFFFF0000u;
   }
   __syncthreads();
+  // one site per thread (N <= blockDim): its constants stay in registers
+  const bool hoist = N <= nt;
+  SiteK kh;
+  if (hoist && tid < N) kh = site_consts(a, tid, jn);
 
   for (int sw = 0; sw < a.S; ++sw) {
     // the transverse coupling of this sweep lives in its threshold table;
     // prefetch the next sweep's table into the other buffer
-    const uint32_t *T = tab + 24 * (sw & 1);
-    const uint32_t *Th = tabh + 24 * (sw & 1);
-    if (tid < 24 && sw + 1 < a.S) {
-      const uint32_t t = a.table[(size_t)(sw + 1) * 24 + tid];
-      tab[24 * ((sw + 1) & 1) + tid] = t;
-      tabh[24 * ((sw + 1) & 1) + tid] = t & 0xFFFF0000u;
+    if (tid < 32 && sw + 1 < a.S) {
+      const uint32_t t = tid < 24 ? a.table[(size_t)(sw + 1) * 24 + tid] : 0u;
+      s_Tf[(sw + 1) & 1][tid] = t;
+      s_Th[(sw + 1) & 1][tid] = t & 0xFFFF0000u;
     }
+    const uint32_t boff = (sw & 1) ? 0x80808080u : 0u;
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const uint32_t *Wo = W + (1 - c) * NB * N;
       uint32_t *Wc = W + c * NB * N;
-      const uint32_t c2 = (uint32_t)c << 16;
-      for (int s = tid; s < N; s += nt) {
-        const Site t = site_of(a, s, jn);
-        const int e = c ^ t.q;   // slice parity of this word's nibbles
-        uint32_t C[NB], O[NB];
-        spatial_counts<NB>(a, Wo, t, C);
-#pragma unroll
-        for (int b = 0; b < NB; ++b) O[b] = Wo[b * N + s];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          // time neighbours: slice k-1 and k+1 of the same site
-          const uint32_t T2 = e ? ((O[b] >> 4) | (O[(b + 1) % NB] << 28))
-                                : ((O[b] << 4) | (O[(b + NB - 1) % NB] >> 28));
-          const uint32_t M = O[b] + T2;
-          const uint32_t De = (C[b] & 0x0F0F0F0Fu) + ((M & 0x0F0F0F0Fu) << 3);
-          const uint32_t Do = ((C[b] >> 4) & 0x0F0F0F0Fu) + (((M >> 4) & 0x0F0F0F0Fu) << 3);
-          const uint4 x = philox((uint32_t)s, (uint32_t)sw, c2 | (uint32_t)b,
-                                 (ent << 8) | TAG_SQA_SWEEP, k0, k1);
-          bool tie = false;
-          uint32_t w = decide8(x, De, Do, Th, tie);
-          if (tie) {
-            const uint4 y = philox((uint32_t)s, (uint32_t)sw, c2 | (uint32_t)b,
-                                   (ent << 8) | TAG_SQA_REFINE, k0, k1);
-            w = refine8(w, x, y, De, Do, T);
-          }
-          Wc[b * N + s] = w;
+      if (hoist) {
+        if (tid < N) update_site<NB>(a, Wo, Wc, tid, kh, c, (uint32_t)sw, boff, ent);
+      } else {
+        for (int s = tid; s < N; s += nt) {
+          const SiteK k = site_consts(a, s, jn);
+          update_site<NB>(a, Wo, Wc, s, k, c, (uint32_t)sw, boff, ent);
         }
       }
       __syncthreads();
@@ -218,7 +301,7 @@ int launch_nb(const pc::SqaArgs &a, int R, cudaStream_t st) {
   PC_CUDA_TRY(cudaFuncSetAttribute(sqa_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   int tpb = ((a.N + 31) / 32) * 32;
-  if (tpb > 1024) tpb = 1024;
+  if (tpb > 512) tpb = 512;
   sqa_kernel<NB><<<R, tpb, smem, st>>>(a);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
@@ -230,7 +313,7 @@ namespace pc {
 
 size_t sqa_smem_bytes(int N, int P) {
   const int NB = P / 16;
-  return (size_t)2 * NB * N * 4 + 96 * 4 + (size_t)P * 4 + (size_t)N;
+  return (size_t)2 * NB * N * 4 + (size_t)P * 4 + (size_t)N;
 }
 
 int sqa_launch(const SqaArgs &a, int R, cudaStream_t st) {
