@@ -104,10 +104,8 @@ class ClockSampler:
 
 
 def _dist():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2503_10302_gb300.dist import env_rank
+    return env_rank()
 
 
 def cpu_oracle_sample(target_s: float = 12.0):
@@ -194,9 +192,11 @@ def main() -> int:
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     run0 = rank * R
 
+    from paper_2503_10302_gb300.dist import max_over_ranks, run_ids
+
     def one_step(i):
         # every step anneals a fresh batch of R runs (new run ids -> new randomness)
-        pcomp.pc_sqa_run_dev(ctx.h, R, (i * world + rank) * R, E_dev.data_ptr(), best_dev.data_ptr())
+        pcomp.pc_sqa_run_dev(ctx.h, R, run_ids(i, rank, world, R), E_dev.data_ptr(), best_dev.data_ptr())
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
@@ -222,10 +222,7 @@ def main() -> int:
     clk = clocks.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     value = flips_step * args.steps * world / (total_ms * 1e6)
 
     # sanity of the timed work: energies are valid slice energies
@@ -244,10 +241,7 @@ def main() -> int:
     for i in range(e2e_steps):
         E_host = pcomp.pc_sqa_anneal(ctx.h, wl.dims, J_host, P, T, g_host, R, run0)
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     e2e_val = flips_step * e2e_steps * world / (e2e_s * 1e9)
     h2d = N + 24 * 4 * S        # coupling masks + per-sweep threshold tables
     d2h = R * P * 4             # final slice energies

@@ -142,6 +142,13 @@ int pc_sqa_run(pc_ctx *ctx, int R, uint32_t run0, int64_t *E_out, int8_t *spins_
 /* Device-buffer variant: E_dev [R][P] int32 and best_dev [R][2] int32
  * (minimum slice energy, its slice index; lowest index on ties). */
 int pc_sqa_run_dev(pc_ctx *ctx, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev);
+/* Self-test of the bounded waits of the time-sliced anneal schedule: runs
+ * two runs from their second chunk, so that no wait for a previous chunk
+ * can succeed; every wait gives up after 50 ms.  *status receives the
+ * status the host then reports (PC_EDEVICE when the waits gave up as they
+ * must); the context stays usable.  Needs a prior pc_sqa_setup with at
+ * least 2 sweeps. */
+int pc_sqa_selftest_wait(pc_ctx *ctx, int *status);
 /* One call from host data to host results: setup + run + copy back. */
 int pc_sqa_anneal(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, double T,
                   int n_sweeps, const double *gamma, int R, uint32_t run0, int64_t *E_out);

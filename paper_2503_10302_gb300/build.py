@@ -44,12 +44,13 @@ def _headers():
     return hs + [os.path.join(INCLUDE, "pcomp.h")]
 
 
-def _compile(src: str, cuda: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, cuda: str, verbose_ptxas: bool, build_dir: str = BUILD,
+             defines=()) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     if src.endswith(".cu"):
         cmd = [os.path.join(cuda, "bin", "nvcc"), *ARCH, "-O3", "-lineinfo", "-std=c++17",
-               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE, "-c", src,
-               "-o", obj]
+               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE,
+               *[f"-D{d}" for d in defines], "-c", src, "-o", obj]
         if verbose_ptxas:
             cmd[1:1] = ["-Xptxas", "-v"]
     else:
@@ -70,21 +71,24 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _sources() + _headers() + [__file__])
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose_ptxas: bool = False, so_path: str = SO,
+          build_dir: str = BUILD, defines=()) -> str:
+    """Compiles every source in csrc/ and links so_path.  `defines` are extra
+    -D tuning macros for the CUDA sources (the defaults are the tuned values)."""
+    if not force and so_path == SO and up_to_date():
         return SO
     cuda = _cuda_home()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, cuda, verbose_ptxas), srcs))
-    tmp = SO + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, cuda, verbose_ptxas, build_dir, defines), srcs))
+    tmp = so_path + f".tmp{os.getpid()}"
     cmd = [os.path.join(cuda, "bin", "nvcc"), *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, SO)
-    return SO
+    os.replace(tmp, so_path)
+    return so_path
 
 
 if __name__ == "__main__":

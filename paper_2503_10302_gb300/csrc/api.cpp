@@ -148,11 +148,13 @@ int pc_set_stream(pc_ctx *c, void *stream) {
   return PC_OK;
 }
 
+static int sqa_check_device(pc_ctx *c);
+
 int pc_synchronize(pc_ctx *c) {
   if (!c) return fail(PC_EINVAL, "ctx is NULL");
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  return PC_OK;
+  return sqa_check_device(c);
 }
 
 int pc_device_sm_count(pc_ctx *c, int *sms) {
@@ -234,7 +236,7 @@ int pc_sqa_get_table(pc_ctx *c, int sweep, uint32_t *out, int32_t *jq) {
 }
 
 static int sqa_enqueue(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev,
-                       int8_t *spins_dev) {
+                       int8_t *spins_dev, int first_chunk = 0, uint64_t wait_ns = 10000000000ull) {
   const SqaState &q = c->sqa;
   SqaArgs a;
   a.Lx = q.lat.L[0];
@@ -254,7 +256,45 @@ static int sqa_enqueue(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t 
   a.E = E_dev;
   a.best = best_dev;
   a.spins = spins_dev;
+  a.state = nullptr;
+  a.done = a.queue = a.err = nullptr;
+  a.R = R;
+  a.K = a.S;
+  a.n_items = R;
+  a.first_item = 0;
+  a.wait_ns = wait_ns;
+  if (a.S > 0) {
+    // persistent time-sliced schedule: about 32 (run, chunk) items per SM
+    SqaState &q = c->sqa;
+    int nch = (32 * c->sms + R - 1) / R;
+    if (nch > a.S) nch = a.S;
+    if (nch < 1) nch = 1;
+    a.K = (a.S + nch - 1) / nch;
+    nch = (a.S + a.K - 1) / a.K;
+    a.n_items = R * nch;
+    a.first_item = first_chunk * R;
+    const size_t words = (size_t)R * 2 * a.NB * a.N;
+    int rc;
+    if (q.d_state.n < words && (rc = q.d_state.alloc(words))) return rc;
+    if (q.d_sync.n < (size_t)R + 2 && (rc = q.d_sync.alloc((size_t)R + 2))) return rc;
+    PC_CUDA_TRY(cudaMemsetAsync(q.d_sync.p, 0, ((size_t)R + 2) * sizeof(int), c->stream));
+    a.state = q.d_state.p;
+    a.done = q.d_sync.p;
+    a.queue = q.d_sync.p + R;
+    a.err = q.d_sync.p + R + 1;
+    q.last_err = a.err;
+  }
   return sqa_launch(a, R, c->stream);
+}
+
+// Reads the device-side error flag of the last persistent anneal (after a
+// stream synchronisation).
+static int sqa_check_device(pc_ctx *c) {
+  if (!c->sqa.last_err) return PC_OK;
+  int e = 0;
+  PC_CUDA_TRY(cudaMemcpy(&e, c->sqa.last_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) return fail(PC_EDEVICE, "anneal: a wait for the previous chunk of a run timed out");
+  return PC_OK;
 }
 
 int pc_sqa_run_dev(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev) {
@@ -285,8 +325,24 @@ int pc_sqa_run(pc_ctx *c, int R, uint32_t run0, int64_t *E_out, int8_t *spins_ou
     PC_CUDA_TRY(cudaMemcpyAsync(spins_out, q.d_spins.p, nE * (size_t)q.lat.N, cudaMemcpyDeviceToHost,
                                 c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if ((rc = sqa_check_device(c))) return rc;
   if (E_out)
     for (size_t i = 0; i < nE; ++i) E_out[i] = hE[i];
+  return PC_OK;
+}
+
+int pc_sqa_selftest_wait(pc_ctx *c, int *status) {
+  if (!c || !c->sqa.ready || !status) return fail(PC_ESTATE, "pc_sqa_setup first");
+  if (c->sqa.S < 2) return fail(PC_EINVAL, "the self-test needs a schedule of at least 2 sweeps");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  const int R = 2;
+  SqaState &q = c->sqa;
+  int rc;
+  if (q.d_E.n < (size_t)R * q.P && (rc = q.d_E.alloc((size_t)R * q.P))) return rc;
+  // queue starts at chunk 1: no chunk 0 ever completes, so every wait runs out
+  if ((rc = sqa_enqueue(c, R, 0, q.d_E.p, nullptr, nullptr, 1, 50000000ull))) return rc;
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  *status = sqa_check_device(c);
   return PC_OK;
 }
 

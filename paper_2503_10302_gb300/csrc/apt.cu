@@ -123,7 +123,7 @@ struct Shared {
   int64_t *m64;      // best E, best sweep, hit sweep, target
   int32_t *m32;      // best buffer, flag, icm counters x3, any-swap flag
   uint8_t *jn;       // [2][H]
-  uint32_t *V;       // ICM cluster nibbles [G/2][2][H]
+  uint32_t *V;       // ICM cluster bits [2][H], then overlap bits [2][H]
   uint32_t *ikx;     // [64] per pair: Philox word 0, then k
   int32_t *ibit;     // [64] per pair: replica choice bit
   int32_t *inm;      // [64] per pair: mismatch count
@@ -325,19 +325,34 @@ __device__ __forceinline__ void block_scan16(const Shared &sh, const uint32_t (&
   __syncthreads();
 }
 
+// Nibble mask (bit 4i) <-> byte (bit i) of eight pairs.
+__device__ __forceinline__ uint32_t nib_to_byte(uint32_t z) {
+  uint32_t t = z & 0x11111111u;
+  t = (t | (t >> 3)) & 0x03030303u;
+  t = (t | (t >> 6)) & 0x000F000Fu;
+  return (t | (t >> 12)) & 0xFFu;
+}
+__device__ __forceinline__ uint32_t byte_to_nib(uint32_t b) {
+  uint32_t t = (b | (b << 12)) & 0x000F000Fu;
+  t = (t | (t << 6)) & 0x03030303u;
+  return (t | (t << 3)) & 0x11111111u;
+}
+
 // ICMop of Algorithm S2 for every temperature at once.  Pair r = 8h + i is
 // nibble i of groups h (label 0) and h + Gh (label 1), so the overlap of
-// eight pairs is X = S[h] ^ S[h + Gh].  The seed of pair r is the k-th site
-// (canonical order c*H + j) with X set, k = floor(x0 n_minus / 2^32); its
-// cluster is grown by an in-place flood fill V <- V | (X & OR_nbr V),
-// alternating colours, until no pair's cluster changes.  Clusters larger
-// than N/2 flip one whole replica (x1 bit 0: label 0 or 1), smaller ones
-// flip in both replicas; then all energies are recomputed.
+// eight pairs is one XOR; compressed, X[site] has bit r set where the two
+// replicas of temperature r disagree.  The seed of pair r is the k-th site
+// (canonical order c*H + j) with bit r set, k = floor(x0 n_minus / 2^32);
+// its cluster grows by an in-place flood fill V <- V | (X & OR_nbr V),
+// alternating colours, until no cluster changes.  Clusters larger than N/2
+// flip one whole replica (x1 bit 0: label 0 or 1), smaller ones flip in both
+// replicas; then all energies are recomputed.
 __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32_t t) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int N = k.geo.N, H = k.geo.H, Gh = k.Gc >> 1;
   const uint32_t *S = sh.S;
-  uint32_t *V = sh.V;
+  uint32_t *V = sh.V;          // [2][H] cluster bits (bit r: pair r)
+  uint32_t *X = sh.V + N;      // [2][H] overlap bits
   if (tid < 8 * Gh) {
     const int r = tid;
     if (r < k.T) {
@@ -345,24 +360,26 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
       sh.ikx[r] = x.x;
       sh.ibit[r] = (int)(x.y & 1u);
     }
-    sh.isz[r] = 0;
   }
   if (tid < 24) sh.imask[tid] = 0;
-  // (A) mismatch counts over this thread's contiguous canonical range
+  // (A) overlaps and mismatch counts over this thread's canonical range
   const int cr = (N + nt - 1) / nt, k0 = min(N, tid * cr), k1 = min(N, k0 + cr);
   uint32_t cnt[16], ex[16], tot[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) cnt[q] = 0;
   for (int kk = k0; kk < k1; ++kk) {
     const int c = kk >= H ? 1 : 0, j = kk - c * H;
+    uint32_t xb = 0;
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       if (h >= Gh) break;
       const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
-      V[(2 * h + c) * H + j] = 0u;
+      xb |= nib_to_byte(x) << (8 * h);
 #pragma unroll
       for (int m = 0; m < 4; ++m) cnt[4 * h + m] += (x >> (4 * m)) & 0x000F000Fu;
     }
+    X[kk] = xb;
+    V[kk] = 0u;
   }
   block_scan16(sh, cnt, ex, tot);
   // lane (h, m) low 16 bits: pair 8h + m; high 16 bits: pair 8h + m + 4
@@ -376,18 +393,15 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // seeds: the thread whose range holds the k-th mismatch of a pair plants it
   for (int r = 0; r < k.T; ++r) {
     const int h = r >> 3, i = r & 7, q = 4 * h + (i & 3), sh16 = (i >> 2) * 16;
-    const int nm = sh.inm[r];
-    if (nm == 0) continue;
+    if (sh.inm[r] == 0) continue;
     const int kth = (int)sh.ikx[r];
     const int lo = (int)((ex[q] >> sh16) & 0xFFFFu), n = (int)((cnt[q] >> sh16) & 0xFFFFu);
     if (kth < lo || kth >= lo + n) continue;
     int rem = kth - lo;
     for (int kk = k0; kk < k1; ++kk) {
-      const int c = kk >= H ? 1 : 0, j = kk - c * H;
-      const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
-      if ((x >> (4 * i)) & 1u) {
+      if ((X[kk] >> r) & 1u) {
         if (rem == 0) {
-          V[(2 * h + c) * H + j] |= 1u << (4 * i);
+          V[kk] |= 1u << r;
           break;
         }
         --rem;
@@ -399,26 +413,18 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   for (int it = 0; it < N; ++it) {
     int changed = 0;
     for (int c = 0; c < 2; ++c) {
+      const uint32_t *Vo = V + (1 - c) * H;
       for (int j = tid; j < H; j += nt) {
+        const uint32_t x = X[c * H + j];
+        const uint32_t v = V[c * H + j];
+        if (!(x & ~v)) continue;          // nothing left to add here
         int n[6];
-        bool nb_ready = false;
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          if (h >= Gh) break;
-          const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
-          if (!x) continue;
-          if (!nb_ready) {
-            neighbours(k.geo, c, j, n);
-            nb_ready = true;
-          }
-          const uint32_t *Vo = V + (2 * h + (1 - c)) * H;
-          const uint32_t o = Vo[n[0]] | Vo[n[1]] | Vo[n[2]] | Vo[n[3]] | Vo[n[4]] | Vo[n[5]];
-          const uint32_t v = V[(2 * h + c) * H + j];
-          const uint32_t nv = v | (x & o);
-          if (nv != v) {
-            V[(2 * h + c) * H + j] = nv;
-            changed = 1;
-          }
+        neighbours(k.geo, c, j, n);
+        const uint32_t o = Vo[n[0]] | Vo[n[1]] | Vo[n[2]] | Vo[n[3]] | Vo[n[4]] | Vo[n[5]];
+        const uint32_t nv = v | (x & o);
+        if (nv != v) {
+          V[c * H + j] = nv;
+          changed = 1;
         }
       }
       __syncthreads();
@@ -429,13 +435,13 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
 #pragma unroll
   for (int q = 0; q < 16; ++q) cnt[q] = 0;
   for (int kk = k0; kk < k1; ++kk) {
-    const int c = kk >= H ? 1 : 0, j = kk - c * H;
+    const uint32_t v = V[kk];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       if (h >= Gh) break;
-      const uint32_t v = V[(2 * h + c) * H + j];
+      const uint32_t z = byte_to_nib((v >> (8 * h)) & 0xFFu);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) cnt[4 * h + m] += (v >> (4 * m)) & 0x000F000Fu;
+      for (int m = 0; m < 4; ++m) cnt[4 * h + m] += (z >> (4 * m)) & 0x000F000Fu;
     }
   }
   block_scan16(sh, cnt, ex, tot);
@@ -458,10 +464,11 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // (E) flips
   for (int kk = tid; kk < N; kk += nt) {
     const int c = kk >= H ? 1 : 0, j = kk - c * H;
+    const uint32_t v = V[kk];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       if (h >= Gh) break;
-      const uint32_t vv = V[(2 * h + c) * H + j] & sh.imask[h];
+      const uint32_t vv = byte_to_nib((v >> (8 * h)) & 0xFFu) & sh.imask[h];
       sh.S[(2 * h + c) * H + j] ^= vv | sh.imask[8 + h];
       sh.S[(2 * (h + Gh) + c) * H + j] ^= vv | sh.imask[16 + h];
     }
@@ -593,7 +600,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.imask = cur;                                 cur += 24;
   sh.swm = cur;                                   cur += 16;
   sh.scan = cur;                                  cur += 16 * (nwarps + 1);
-  sh.V = cur;                                     cur += icm ? (size_t)(k.Gc / 2) * N : 0;
+  sh.V = cur;                                     cur += icm ? (size_t)2 * N : 0;   // V and X
   sh.jn = reinterpret_cast<uint8_t *>(cur);
 
   // load state
@@ -745,7 +752,7 @@ size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n
   size_t words = (size_t)Gc * N + 16 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
   words += 4 * 64 + 24 + 16 + 16 * ((size_t)nwarps + 1);
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
-  if (mode == APT_MODE_APT && icm) words += (size_t)(Gc / 2) * N;
+  if (mode == APT_MODE_APT && icm) words += (size_t)2 * N;
   return words * 4 + (size_t)N + 16;
 }
 

@@ -80,12 +80,18 @@ struct SqaState {
   PinnedBuf<uint8_t> stage;       // pinned staging of jneg + tables
   DevBuf<int32_t> d_E;            // per-call output scratch of pc_sqa_run
   DevBuf<int8_t> d_spins;
+  DevBuf<uint32_t> d_state;       // run states between chunks of the persistent schedule
+  DevBuf<int> d_sync;             // [R] chunks done, queue counter, error flag
+  int *last_err = nullptr;        // error flag of the last persistent anneal
   void release() {
     ready = false;
     d_jneg.reset();
     d_table.reset();
     d_E.reset();
     d_spins.reset();
+    d_state.reset();
+    d_sync.reset();
+    last_err = nullptr;
   }
 };
 

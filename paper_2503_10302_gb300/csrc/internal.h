@@ -42,6 +42,12 @@ struct SqaArgs {
   int32_t *E;              // [R][P]
   int32_t *best;           // [R][2] (nullable)
   int8_t *spins;           // [R][P][N] (nullable)
+  // persistent time-sliced schedule (state == nullptr: one CTA per run)
+  uint32_t *state;         // [R][2][NB][N] run states between chunks
+  int *done, *queue, *err; // [R] chunks done per run; work counter; error flag
+  int R, K, n_items;       // runs, sweeps per chunk, R * chunks
+  int first_item;          // first queue item (0; the wait self-test skips chunk 0)
+  uint64_t wait_ns;        // limit of one wait for a previous chunk
 };
 size_t sqa_smem_bytes(int N, int P);
 int sqa_launch(const SqaArgs &a, int R, cudaStream_t st);

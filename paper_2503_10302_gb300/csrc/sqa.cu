@@ -20,6 +20,19 @@
 #include "device.cuh"
 #include "internal.h"
 
+// Build-time tuning knobs of the anneal kernel (defaults are the tuned
+// values): keep one site's constants in registers across sweeps, unroll the
+// loop over slice blocks, CTAs per SM the register budget is sized for.
+#ifndef PC_SQA_HOIST
+#define PC_SQA_HOIST 1
+#endif
+#ifndef PC_SQA_UNROLL
+#define PC_SQA_UNROLL 1
+#endif
+#ifndef PC_SQA_MINB
+#define PC_SQA_MINB 1
+#endif
+
 namespace {
 using namespace pcdev;
 
@@ -147,7 +160,11 @@ __device__ __forceinline__ void update_site(const pc::SqaArgs &a, const uint32_t
   const int N = a.N;
   const int e = c ^ k.q;   // slice parity of this word's nibbles
   const uint32_t c2 = (uint32_t)c << 16;
+#if PC_SQA_UNROLL
+#pragma unroll
+#else
 #pragma unroll 1
+#endif
   for (int b = 0; b < NB; ++b) {
     const int bp = (b + 1 == NB) ? 0 : b + 1, bm = (b == 0) ? NB - 1 : b - 1;
     const uint32_t Ob = Wo[b * N + s];
@@ -173,41 +190,57 @@ __device__ __forceinline__ void update_site(const pc::SqaArgs &a, const uint32_t
   }
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait until *flag >= want (acquire); false after limit_ns.
+__device__ __forceinline__ bool wait_at_least(const int *flag, int want, uint64_t limit_ns) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+    if (v >= want) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+    __nanosleep(256);
+  }
+}
+
+// Anneal of sweeps [s0, s1) of one run.  s0 == 0 draws the random initial
+// state, otherwise the state comes from the run's slot in global memory;
+// s1 == S computes the final slice energies, otherwise the state goes back.
 template <int NB>
-__global__ void __launch_bounds__(512, 2) sqa_kernel(const pc::SqaArgs a) {
-  extern __shared__ __align__(16) uint32_t smem[];
+__device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, int32_t *Eacc,
+                                            const uint8_t *jn, const SiteK &kh, bool hoist,
+                                            int run, int s0, int s1) {
   const int N = a.N, P = a.P;
-  uint32_t *W = smem;                                       // [2][NB][N]
-  int32_t *Eacc = reinterpret_cast<int32_t *>(W + 2 * NB * N);   // [P]
-  uint8_t *jn = reinterpret_cast<uint8_t *>(Eacc + P);      // [N]
-  const int run = blockIdx.x;
   const uint32_t ent = a.run0 + (uint32_t)run;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const uint32_t k0 = a.k0, k1 = a.k1;
-
-  for (int i = tid; i < N; i += nt) jn[i] = a.jneg[i];
-  // Algorithm S1: all spins of all slices start random (+1 iff half < 2^15)
-  for (int idx = tid; idx < 2 * NB * N; idx += nt) {
-    const int s = idx % N, cb = idx / N, b = cb % NB, c = cb / NB;
-    const uint4 x = philox((uint32_t)s, 0u, ((uint32_t)c << 16) | (uint32_t)b,
-                           (ent << 8) | TAG_SQA_INIT, k0, k1);
-    uint32_t w = 0;
+  uint32_t *gstate = a.state ? a.state + (size_t)run * 2 * NB * N : nullptr;
+  if (s0 == 0) {
+    // Algorithm S1: all spins of all slices start random (+1 iff half < 2^15)
+    for (int idx = tid; idx < 2 * NB * N; idx += nt) {
+      const int s = idx % N, cb = idx / N, b = cb % NB, c = cb / NB;
+      const uint4 x = philox((uint32_t)s, 0u, ((uint32_t)c << 16) | (uint32_t)b,
+                             (ent << 8) | TAG_SQA_INIT, a.k0, a.k1);
+      uint32_t w = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) w |= (half_lo(x, i) < 0x8000u) ? (1u << (4 * i)) : 0u;
-    W[idx] = w;
+      for (int i = 0; i < 8; ++i) w |= (half_lo(x, i) < 0x8000u) ? (1u << (4 * i)) : 0u;
+      W[idx] = w;
+    }
+  } else {
+    for (int idx = tid; idx < 2 * NB * N; idx += nt) W[idx] = __ldcg(gstate + idx);
   }
   if (tid < 32) {
-    const uint32_t t = tid < 24 ? a.table[tid] : 0u;
-    s_Tf[0][tid] = t;
-    s_Th[0][tid] = t & 0xFFFF0000u;
+    const uint32_t t = (tid < 24 && s0 < a.S) ? a.table[(size_t)s0 * 24 + tid] : 0u;
+    s_Tf[s0 & 1][tid] = t;
+    s_Th[s0 & 1][tid] = t & 0xFFFF0000u;
   }
   __syncthreads();
-  // one site per thread (N <= blockDim): its constants stay in registers
-  const bool hoist = N <= nt;
-  SiteK kh;
-  if (hoist && tid < N) kh = site_consts(a, tid, jn);
 
-  for (int sw = 0; sw < a.S; ++sw) {
+  for (int sw = s0; sw < s1; ++sw) {
     // the transverse coupling of this sweep lives in its threshold table;
     // prefetch the next sweep's table into the other buffer
     if (tid < 32 && sw + 1 < a.S) {
@@ -232,6 +265,10 @@ __global__ void __launch_bounds__(512, 2) sqa_kernel(const pc::SqaArgs a) {
     }
   }
 
+  if (s1 < a.S) {
+    for (int idx = tid; idx < 2 * NB * N; idx += nt) __stcg(gstate + idx, W[idx]);
+    return;
+  }
   // Algorithm S1: classical energy of every slice (full J, no J_perp).  Each
   // bond has one endpoint with 3D parity 1, so E_k = 3N - 2 sum_{q(s)=1} sat.
   for (int k = tid; k < P; k += nt) Eacc[k] = 0;
@@ -282,6 +319,52 @@ __global__ void __launch_bounds__(512, 2) sqa_kernel(const pc::SqaArgs a) {
       }
     }
   }
+  __syncthreads();
+}
+
+// PERSIST = false: one CTA per run, the whole schedule.  PERSIST = true: a
+// persistent grid pulls (chunk, run) items in chunk-major order from a
+// queue; chunk k of a run waits (bounded) until chunk k-1 of that run has
+// stored its state.  Time-slicing the runs keeps every SM busy when the
+// number of runs is not a multiple of the number of SMs.
+template <int NB, bool PERSIST>
+__global__ void __launch_bounds__(512, PC_SQA_MINB) sqa_kernel(const pc::SqaArgs a) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ int s_item;
+  const int N = a.N, P = a.P;
+  uint32_t *W = smem;                                       // [2][NB][N]
+  int32_t *Eacc = reinterpret_cast<int32_t *>(W + 2 * NB * N);   // [P]
+  uint8_t *jn = reinterpret_cast<uint8_t *>(Eacc + P);      // [N]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < N; i += nt) jn[i] = a.jneg[i];
+  __syncthreads();
+  // one site per thread (N <= blockDim): its constants stay in registers
+  const bool hoist = PC_SQA_HOIST && N <= nt;
+  SiteK kh;
+  if (hoist && tid < N) kh = site_consts(a, tid, jn);
+  if (!PERSIST) {
+    anneal_span<NB>(a, W, Eacc, jn, kh, hoist, blockIdx.x, 0, a.S);
+    return;
+  }
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(a.queue, 1) + a.first_item;
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= a.n_items) break;
+    const int chunk = item / a.R, run = item - chunk * a.R;
+    const int s0 = chunk * a.K, s1 = min(a.S, s0 + a.K);
+    if (chunk > 0) {
+      if (tid == 0 && !wait_at_least(a.done + run, chunk, a.wait_ns)) atomicExch(a.err, 1);
+      __syncthreads();
+    }
+    anneal_span<NB>(a, W, Eacc, jn, kh, hoist, run, s0, s1);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.done + run), "r"(chunk + 1) : "memory");
+    }
+  }
 }
 
 __global__ void philox_kernel(const uint32_t *ctr, uint32_t *out, int64_t n, uint32_t k0,
@@ -298,11 +381,24 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t *out, int64_t n, uin
 template <int NB>
 int launch_nb(const pc::SqaArgs &a, int R, cudaStream_t st) {
   const size_t smem = pc::sqa_smem_bytes(a.N, a.P);
-  PC_CUDA_TRY(cudaFuncSetAttribute(sqa_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
   int tpb = ((a.N + 31) / 32) * 32;
   if (tpb > 512) tpb = 512;
-  sqa_kernel<NB><<<R, tpb, smem, st>>>(a);
+  if (!a.state) {
+    PC_CUDA_TRY(cudaFuncSetAttribute(sqa_kernel<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    sqa_kernel<NB, false><<<R, tpb, smem, st>>>(a);
+  } else {
+    PC_CUDA_TRY(cudaFuncSetAttribute(sqa_kernel<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    PC_CUDA_TRY(cudaGetDevice(&dev));
+    PC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sqa_kernel<NB, true>, tpb, smem));
+    if (per_sm < 1) per_sm = 1;
+    int grid = sms * per_sm;
+    if (grid > a.n_items) grid = a.n_items;
+    sqa_kernel<NB, true><<<grid, tpb, smem, st>>>(a);
+  }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
@@ -461,5 +557,12 @@ extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, co
   a.E = E_dev;
   a.best = best_dev;
   a.spins = nullptr;
+  a.state = nullptr;   // one CTA per run: no state scratch
+  a.done = a.queue = a.err = nullptr;
+  a.R = R;
+  a.K = n_sweeps;
+  a.n_items = R;
+  a.first_item = 0;
+  a.wait_ns = 0;
   return sqa_launch(a, R, st);
 }

@@ -55,6 +55,7 @@ SIGNATURES = {
     "pc_sqa_get_table": (c_int, [c_vp, c_int, c_u32p, ctypes.POINTER(ctypes.c_int32)]),
     "pc_sqa_run": (c_int, [c_vp, c_int, c_u32, c_i64p, c_i8p]),
     "pc_sqa_run_dev": (c_int, [c_vp, c_int, c_u32, c_vp, c_vp]),
+    "pc_sqa_selftest_wait": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "pc_sqa_anneal": (c_int, [c_vp, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p, c_int, c_u32, c_i64p]),
     "pc_sqa_anneal_noalloc": (c_int, [c_int, c_vp, c_u64, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p,
                                       c_int, c_u32, c_vp, c_vp]),
@@ -198,6 +199,12 @@ def pc_sqa_run(ctx, R: int, run0: int, P: int, N: int, want_spins: bool = False)
 
 def pc_sqa_run_dev(ctx, R: int, run0: int, E_dev_ptr: int, best_dev_ptr: int = 0) -> None:
     _call("pc_sqa_run_dev", ctx, R, c_u32(run0), c_vp(E_dev_ptr), c_vp(best_dev_ptr or None))
+
+
+def pc_sqa_selftest_wait(ctx) -> int:
+    st = c_int()
+    _call("pc_sqa_selftest_wait", ctx, ctypes.byref(st))
+    return st.value
 
 
 def pc_sqa_anneal(ctx, dims, J, P: int, T: float, gamma, R: int, run0: int = 0) -> np.ndarray:

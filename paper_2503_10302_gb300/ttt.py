@@ -248,16 +248,21 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("what", choices=["throughput", "c3", "c5", "all"])
     ap.add_argument("--sweeps", type=int, default=200)
+    ap.add_argument("--batch", choices=["apt_plain_L4", "apt_icm_64xL12", "apt_icm_mixed256"])
+    ap.add_argument("--icm", type=int, choices=[0, 1])
     ap.add_argument("--n-train", type=int, default=20000)
     ap.add_argument("--n-eval", type=int, default=128)
     ap.add_argument("--epochs", type=int, default=60)
     args = ap.parse_args()
     out = {}
     if args.what in ("throughput", "all"):
-        for name, batch in (("apt_plain_L4", W.apt_single(L=4)),
-                            ("apt_icm_64xL12", W.apt_uniform_batch(64, 12, 32)),
-                            ("apt_icm_mixed256", W.apt_mixed_batch())):
-            for icm in (True, False):
+        batches = {"apt_plain_L4": lambda: W.apt_single(L=4),
+                   "apt_icm_64xL12": lambda: W.apt_uniform_batch(64, 12, 32),
+                   "apt_icm_mixed256": lambda: W.apt_mixed_batch()}
+        names = [args.batch] if args.batch else list(batches)
+        for name in names:
+            batch = batches[name]()
+            for icm in ((True, False) if args.icm is None else (bool(args.icm),)):
                 out[f"{name}_icm{int(icm)}"] = apt_throughput(batch, args.sweeps, icm)
     if args.what in ("c3", "all"):
         out["c3"] = c3_time_to_target()

@@ -100,3 +100,19 @@ def test_sqa_full_size_sampled_runs(pc, orc):
     for r in picks:
         E_ref = orc.sqa_anneal(wl.dims, wl.J, wl.P, wl.T, wl.gamma, 1, run0=r, seed=0)
         assert np.array_equal(E[r], E_ref[0]), r
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(pc, orc):
+    """Every wait for a previous chunk runs out (nothing sets its flag); the
+    kernel returns, the host reports PC_EDEVICE, and the next anneal on the
+    same context is still bit-exact."""
+    dims, P = (4, 4, 4), 16
+    J = W.ea_couplings(dims, 2, 0)
+    gamma = W.linear_gamma_schedule(20)
+    ctx = pc.Context(0, 5)
+    pc.pc_sqa_setup(ctx.h, dims, J, P, 0.05, gamma)
+    assert pc.pc_sqa_selftest_wait(ctx.h) == pc.PC_EDEVICE
+    pc.pc_sqa_setup(ctx.h, dims, J, P, 0.05, gamma)
+    E = pc.pc_sqa_run(ctx.h, 3, 0, P, 64)
+    assert np.array_equal(E, orc.sqa_anneal(dims, J, P, 0.05, gamma, 3, seed=5))
+    ctx.close()
