@@ -96,6 +96,23 @@ int pc_apt_load(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
  * neighbour swaps of that attempt's parity.  Resumable: state, counters and
  * statistics carry over between calls.  Enqueued on the context stream. */
 int pc_apt_run(pc_ctx *ctx, int64_t n_swaps, int sweeps_per_swap, int icm);
+/* Autotuner of the fused kernel's launch shape: times trial_swaps attempts
+ * (with or without ICM) for 256, 384 and 512 threads per CTA on a scratch
+ * copy of the loaded batch (the loaded chains do not move), keeps the
+ * fastest for later pc_apt_run calls and returns it in *tpb.  The threads'
+ * split over sites and replica groups follows from the shape.  Results do
+ * not depend on the shape: randomness is keyed by slot and site. */
+int pc_apt_autotune(pc_ctx *ctx, int trial_swaps, int icm, int *tpb);
+/* Set the threads per CTA directly (multiple of 64 in [64, 512]). */
+int pc_apt_set_block_threads(pc_ctx *ctx, int tpb);
+/* Checkpoint / resume: pc_apt_save writes the batch's dynamic state
+ * (replica spins, energies, best energies and states, hit sweeps, targets,
+ * statistics, counters) to a file; pc_apt_restore reads it back into a
+ * context on which the same batch (shapes, ladders' sizes, entry ids, seed)
+ * was loaded.  Counter-based randomness makes the resumed chains identical
+ * to uninterrupted ones. */
+int pc_apt_save(pc_ctx *ctx, const char *path);
+int pc_apt_restore(pc_ctx *ctx, const char *path);
 /* Sweeps and swap attempts done since pc_apt_load. */
 int pc_apt_progress(pc_ctx *ctx, int64_t *sweeps, int64_t *swaps);
 /* Target energy for time-to-target: the first sweep count at which the

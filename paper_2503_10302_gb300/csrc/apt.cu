@@ -27,6 +27,25 @@
 #include "device.cuh"
 #include "internal.h"
 
+// Optional per-phase cycle counters of CTA 0 (build with -DPC_APT_PROFILE=1;
+// read with pc_apt_profile_read).  Off by default.
+#ifndef PC_APT_PROFILE
+#define PC_APT_PROFILE 0
+#endif
+#if PC_APT_PROFILE
+__device__ unsigned long long g_apt_prof[16];
+#define PROF_MARK(slot, t0)                                                     \
+  do {                                                                          \
+    if (blockIdx.x == 0 && threadIdx.x == 0) {                                  \
+      const long long t1_ = clock64();                                          \
+      atomicAdd(&g_apt_prof[slot], (unsigned long long)(t1_ - (t0)));           \
+      (t0) = t1_;                                                               \
+    }                                                                           \
+  } while (0)
+#else
+#define PROF_MARK(slot, t0) do { } while (0)
+#endif
+
 namespace {
 using namespace pcdev;
 using pc::AptArgs;
@@ -348,6 +367,7 @@ __device__ __forceinline__ uint32_t byte_to_nib(uint32_t b) {
 // flip one whole replica (x1 bit 0: label 0 or 1), smaller ones flip in both
 // replicas; then all energies are recomputed.
 __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32_t t) {
+  long long pt = clock64();
   const int tid = threadIdx.x, nt = blockDim.x;
   const int N = k.geo.N, H = k.geo.H, Gh = k.Gc >> 1;
   const uint32_t *S = sh.S;
@@ -382,6 +402,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     V[kk] = 0u;
   }
   block_scan16(sh, cnt, ex, tot);
+  PROF_MARK(4, pt);
   // lane (h, m) low 16 bits: pair 8h + m; high 16 bits: pair 8h + m + 4
   if (tid < 8 * Gh) {
     const int r = tid, h = r >> 3, i = r & 7, q = 4 * h + (i & 3);
@@ -409,11 +430,16 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     }
   }
   __syncthreads();
-  // (B) flood fill, alternating colours in place
+  PROF_MARK(5, pt);
+  // (B) flood fill.  The cluster is the least fixed point of the monotone
+  // update V <- V | (X & OR_nbr V); each site word has one writer (its
+  // thread), so a pass relaxes both colours without a barrier (a stale
+  // neighbour read only delays growth) and a pass with no change anywhere,
+  // started after a barrier, proves the fixed point.
   for (int it = 0; it < N; ++it) {
     int changed = 0;
     for (int c = 0; c < 2; ++c) {
-      const uint32_t *Vo = V + (1 - c) * H;
+      volatile const uint32_t *Vo = V + (1 - c) * H;
       for (int j = tid; j < H; j += nt) {
         const uint32_t x = X[c * H + j];
         const uint32_t v = V[c * H + j];
@@ -427,10 +453,10 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
           changed = 1;
         }
       }
-      __syncthreads();
     }
     if (!__syncthreads_or(changed)) break;
   }
+  PROF_MARK(6, pt);
   // (C) cluster sizes
 #pragma unroll
   for (int q = 0; q < 16; ++q) cnt[q] = 0;
@@ -461,6 +487,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     }
   }
   __syncthreads();
+  PROF_MARK(7, pt);
   // (E) flips
   for (int kk = tid; kk < N; kk += nt) {
     const int c = kk >= H ? 1 : 0, j = kk - c * H;
@@ -474,11 +501,13 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     }
   }
   __syncthreads();
+  PROF_MARK(8, pt);
   // (F) energies after the moves
   colour_phase<false, true>(a, k, sh, 1, 0u);
   __syncthreads();
   finish_energies(k, sh);
   __syncthreads();
+  PROF_MARK(9, pt);
 }
 
 // Replica exchange of attempt t (Sec. "Comparison with Adaptive Parallel
@@ -645,16 +674,19 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     finish_energies(k, sh);
     __syncthreads();
   } else {
+    long long pt = clock64();
     for (int it = 0; it < a.n_iter; ++it) {
       const uint32_t t = (uint32_t)(t0 + it);
       for (int qq = 0; qq < a.spp; ++qq) {
         const uint32_t s = (uint32_t)(s0 + (int64_t)it * a.spp + qq);
         colour_phase<true, false>(a, k, sh, 0, s);
         __syncthreads();
+        PROF_MARK(0, pt);
         colour_phase<true, true>(a, k, sh, 1, s);
         __syncthreads();
         finish_energies(k, sh);
         __syncthreads();
+        PROF_MARK(1, pt);
         if (a.mode == pc::APT_MODE_LADDER) {
           if ((int64_t)it * a.spp + qq >= a.window_from)
             for (int b = threadIdx.x; b < k.Bc; b += blockDim.x) {
@@ -676,12 +708,16 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
       if (a.mode != pc::APT_MODE_APT) continue;
       const int64_t sweeps = s0 + (int64_t)(it + 1) * a.spp;
       best_update(a, k, sh, p, sweeps);
+      PROF_MARK(2, pt);
       if (icm) {
         icm_all(a, k, sh, t);
+        pt = clock64();
         best_update(a, k, sh, p, sweeps);
+        PROF_MARK(10, pt);
       }
       swap_step(a, k, sh, p, t);
       __syncthreads();
+      PROF_MARK(3, pt);
     }
   }
 
@@ -772,6 +808,17 @@ int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t s
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
+
+#if PC_APT_PROFILE
+extern "C" int pc_apt_profile_read(unsigned long long *out, int reset) {
+  PC_CUDA_TRY(cudaMemcpyFromSymbol(out, g_apt_prof, sizeof(unsigned long long) * 16));
+  if (reset) {
+    unsigned long long z[16] = {0};
+    PC_CUDA_TRY(cudaMemcpyToSymbol(g_apt_prof, z, sizeof(z)));
+  }
+  return PC_OK;
+}
+#endif
 
 int apt_advance_launch(int64_t *ctr, int64_t sweeps, int64_t swaps, cudaStream_t st) {
   apt_advance_kernel<<<1, 1, 0, st>>>(ctr, sweeps, swaps);

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -19,7 +20,7 @@ namespace pc {
 
 namespace {
 
-constexpr int kTpb = 512;        // threads per CTA of the sweep kernel
+constexpr int kTpbDefault = 512; // threads per CTA of the sweep kernel (autotunable)
 constexpr int kMaxGcCta = 8;     // groups (64 buffers) per CTA
 constexpr int kChunkAttempts = 128;
 
@@ -37,17 +38,21 @@ struct Batch {
   DevBuf<int8_t> d_bestspins;
   DevBuf<int> d_cta;             // [4][n_cta]: prob, g0, gc, nch
   int n_cta = 0;
+  int tpb = kTpbDefault;
   size_t smem = 0;
   std::vector<uint32_t> h_pbit, h_swaptab, h_swapidx;
 };
 
-int choose_nch(int H, int Gc) {
+// Split of a CTA's threads into nch chunks of tpb/nch threads, each chunk
+// sweeping ceil(Gc/nch) groups of every site: the choice that minimises the
+// longest thread's work (site rounds x groups).
+int choose_nch(int H, int Gc, int tpb) {
   int best = 1, best_cost = INT_MAX;
   for (int nch = 1; nch <= 8; nch *= 2) {
-    if (kTpb % (32 * nch)) continue;
+    if (tpb % (32 * nch)) continue;
     const int gc = (Gc + nch - 1) / nch;
     if (gc > 4) continue;
-    const int tpc = kTpb / nch;
+    const int tpc = tpb / nch;
     const int cost = ((H + tpc - 1) / tpc) * gc;
     if (cost < best_cost) {
       best_cost = cost;
@@ -258,8 +263,8 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
       cp.push_back(i);
       cg0.push_back(g0);
       cgc.push_back(gc);
-      cnch.push_back(choose_nch(P.N / 2, gc));
-      smem = std::max(smem, apt_smem_bytes(P.N, gc, kTpb / 32, mode, icm, P.T, n_bins));
+      cnch.push_back(choose_nch(P.N / 2, gc, bt.tpb));
+      smem = std::max(smem, apt_smem_bytes(P.N, gc, bt.tpb / 32, mode, icm, P.T, n_bins));
     }
   }
   bt.n_cta = (int)cp.size();
@@ -297,6 +302,8 @@ int max_words(const Batch &bt) {
 struct AptImpl {
   Batch bt;
   int A = 0;
+  std::vector<ProbSpec> specs;        // the loaded problems (J copied below)
+  std::vector<std::vector<int8_t>> Jcopy;
   bool icm_ok = false;
   // CUDA graph of one chunk of kChunkAttempts swap attempts
   cudaGraphExec_t exec = nullptr;
@@ -318,6 +325,82 @@ void pc_apt_release_impl(pc_ctx *c) {
   delete apt_impl(c);
   c->apt_impl = nullptr;
 }
+
+// ------------------------------------------------------------ checkpoints
+namespace {
+
+constexpr uint64_t kCkptMagic = 0x31544B43504D4350ull;   // "PCMPCKT1"
+
+template <typename T>
+int dev_io(FILE *f, DevBuf<T> &b, bool save) {
+  std::vector<T> h(b.n);
+  if (save) {
+    PC_CUDA_TRY(cudaMemcpy(h.data(), b.p, b.n * sizeof(T), cudaMemcpyDeviceToHost));
+    if (fwrite(h.data(), sizeof(T), b.n, f) != b.n) return fail(PC_EINVAL, "checkpoint write failed");
+  } else {
+    if (fread(h.data(), sizeof(T), b.n, f) != b.n) return fail(PC_EINVAL, "checkpoint is truncated");
+    PC_CUDA_TRY(cudaMemcpy(b.p, h.data(), b.n * sizeof(T), cudaMemcpyHostToDevice));
+  }
+  return PC_OK;
+}
+
+// Identity of the loaded batch: problem shapes, ladders' sizes, entry ids
+// and the seed; a checkpoint restores only into an identical batch.
+std::vector<uint64_t> batch_identity(pc_ctx *c, const Batch &bt) {
+  std::vector<uint64_t> id = {c->seed, (uint64_t)bt.prob.size()};
+  for (const AptProbDev &P : bt.prob) {
+    id.push_back(((uint64_t)P.Lx << 40) | ((uint64_t)P.Ly << 20) | (uint64_t)P.Lz);
+    id.push_back(((uint64_t)P.T << 32) | ((uint64_t)P.A << 16) | (uint64_t)P.B);
+    id.push_back(P.ent);
+  }
+  return id;
+}
+
+int ckpt_io(pc_ctx *c, const char *path, bool save) {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  if (!path) return fail(PC_EINVAL, "path is NULL");
+  Batch &bt = apt_impl(c)->bt;
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  FILE *f = fopen(path, save ? "wb" : "rb");
+  if (!f) return fail(PC_EINVAL, std::string("cannot open checkpoint ") + path);
+  std::vector<uint64_t> id = batch_identity(c, bt);
+  int rc = PC_OK;
+  uint64_t hdr[3] = {kCkptMagic, (uint64_t)id.size(), 0};
+  if (save) {
+    hdr[2] = 0;
+    int64_t ctrs[2] = {c->apt.sweeps, c->apt.swaps};
+    if (fwrite(hdr, 8, 3, f) != 3 || fwrite(id.data(), 8, id.size(), f) != id.size() ||
+        fwrite(ctrs, 8, 2, f) != 2)
+      rc = fail(PC_EINVAL, "checkpoint write failed");
+  } else {
+    uint64_t h[3];
+    std::vector<uint64_t> fid(id.size());
+    int64_t ctrs[2];
+    if (fread(h, 8, 3, f) != 3 || h[0] != kCkptMagic || h[1] != id.size() ||
+        fread(fid.data(), 8, fid.size(), f) != fid.size() || fid != id || fread(ctrs, 8, 2, f) != 2)
+      rc = fail(PC_EINVAL, "checkpoint does not match the loaded batch");
+    else {
+      c->apt.sweeps = ctrs[0];
+      c->apt.swaps = ctrs[1];
+    }
+  }
+  if (!rc) rc = dev_io(f, bt.d_spins, save);
+  if (!rc) rc = dev_io(f, bt.d_E, save);
+  if (!rc) rc = dev_io(f, bt.d_temp, save);
+  if (!rc) rc = dev_io(f, bt.d_bestE, save);
+  if (!rc) rc = dev_io(f, bt.d_bestsweep, save);
+  if (!rc) rc = dev_io(f, bt.d_hit, save);
+  if (!rc) rc = dev_io(f, bt.d_target, save);
+  if (!rc) rc = dev_io(f, bt.d_bestbuf, save);
+  if (!rc) rc = dev_io(f, bt.d_bestspins, save);
+  if (!rc) rc = dev_io(f, bt.d_stats, save);
+  if (!rc) rc = dev_io(f, bt.d_ctr, save);
+  fclose(f);
+  return rc;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -360,6 +443,12 @@ int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, con
   c->apt_impl = im;
   c->apt.ready = false;
   im->A = n_labels;
+  im->Jcopy.resize(specs.size());
+  for (size_t i = 0; i < specs.size(); ++i) {
+    im->Jcopy[i].assign(specs[i].J, specs[i].J + 3 * (size_t)specs[i].lat.N);
+    specs[i].J = im->Jcopy[i].data();
+  }
+  im->specs = specs;
   int rc = build_batch(c, im->bt, specs, 0);
   if (rc) return rc;
   if ((rc = schedule(c, im->bt, {}, APT_MODE_APT, n_labels == 2, 0))) return rc;
@@ -367,7 +456,7 @@ int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, con
   a.tag_init = 1;   // TAG_APT_INIT
   if ((rc = apt_init_launch(a, n_inst, max_words(im->bt), c->stream))) return rc;
   a.mode = APT_MODE_ENERGY;
-  if ((rc = apt_launch(a, im->bt.n_cta, kTpb, im->bt.smem, c->stream))) return rc;
+  if ((rc = apt_launch(a, im->bt.n_cta, im->bt.tpb, im->bt.smem, c->stream))) return rc;
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->apt.ready = true;
   c->apt.n = n_inst;
@@ -385,7 +474,7 @@ static int apt_enqueue(pc_ctx *c, AptImpl *im, int n_iter, int spp, int icm) {
   a.icm = icm;
   a.tag_main = 2;    // TAG_APT_SWEEP
   a.tag_ref = 3;     // TAG_APT_REFINE
-  int rc = apt_launch(a, im->bt.n_cta, kTpb, im->bt.smem, c->stream);
+  int rc = apt_launch(a, im->bt.n_cta, im->bt.tpb, im->bt.smem, c->stream);
   if (rc) return rc;
   return apt_advance_launch(im->bt.d_ctr.p, (int64_t)n_iter * spp, n_iter, c->stream);
 }
@@ -441,6 +530,85 @@ int pc_apt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
   return PC_OK;
 }
 
+int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  if (trial_swaps < 1) return fail(PC_EINVAL, "trial_swaps must be >= 1");
+  AptImpl *im = apt_impl(c);
+  if (icm && im->A != 2) return fail(PC_EINVAL, "ICM needs two labels per temperature");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  const int cands[3] = {256, 384, 512};
+  int best = im->bt.tpb;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  PC_CUDA_TRY(cudaEventCreate(&e0));
+  PC_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = PC_OK;
+  for (int tpb : cands) {
+    // a scratch copy of the batch: the loaded chains are not advanced
+    Batch tmp;
+    tmp.tpb = tpb;
+    if ((rc = build_batch(c, tmp, im->specs, 0))) break;
+    if ((rc = schedule(c, tmp, {}, APT_MODE_APT, im->A == 2, 0))) {
+      rc = PC_OK;   // does not fit with this shape: skip it
+      continue;
+    }
+    AptArgs a = base_args(c, tmp);
+    a.tag_init = 1;
+    if ((rc = apt_init_launch(a, (int)im->specs.size(), max_words(tmp), c->stream))) break;
+    a.mode = APT_MODE_APT;
+    a.n_iter = trial_swaps;
+    a.spp = 1;
+    a.icm = icm ? 1 : 0;
+    a.tag_main = 2;
+    a.tag_ref = 3;
+    if ((rc = apt_launch(a, tmp.n_cta, tpb, tmp.smem, c->stream))) break;   // warm-up
+    PC_CUDA_TRY(cudaEventRecord(e0, c->stream));
+    if ((rc = apt_launch(a, tmp.n_cta, tpb, tmp.smem, c->stream))) break;
+    PC_CUDA_TRY(cudaEventRecord(e1, c->stream));
+    PC_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = tpb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (best != im->bt.tpb) {
+    im->bt.tpb = best;
+    if ((rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A == 2, 0))) return rc;
+    if (im->exec) cudaGraphExecDestroy(im->exec);
+    if (im->graph) cudaGraphDestroy(im->graph);
+    im->exec = nullptr;
+    im->graph = nullptr;
+  }
+  if (tpb_out) *tpb_out = best;
+  return PC_OK;
+}
+
+int pc_apt_set_block_threads(pc_ctx *c, int tpb) {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  if (tpb < 64 || tpb > 512 || tpb % 64) return fail(PC_EINVAL, "tpb must be a multiple of 64 in [64, 512]");
+  AptImpl *im = apt_impl(c);
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int old = im->bt.tpb;
+  im->bt.tpb = tpb;
+  int rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A == 2, 0);
+  if (rc) {
+    im->bt.tpb = old;
+    schedule(c, im->bt, {}, APT_MODE_APT, im->A == 2, 0);
+    return rc;
+  }
+  if (im->exec) cudaGraphExecDestroy(im->exec);
+  if (im->graph) cudaGraphDestroy(im->graph);
+  im->exec = nullptr;
+  im->graph = nullptr;
+  return PC_OK;
+}
+
 int pc_apt_progress(pc_ctx *c, int64_t *sweeps, int64_t *swaps) {
   if (!c || !c->apt.ready) return fail(PC_ESTATE, "pc_apt_load first");
   if (sweeps) *sweeps = c->apt.sweeps;
@@ -453,6 +621,9 @@ static int check_inst(pc_ctx *c, int inst) {
   if (inst < 0 || inst >= c->apt.n) return fail(PC_EINVAL, "instance index out of range");
   return PC_OK;
 }
+
+int pc_apt_save(pc_ctx *c, const char *path) { return ckpt_io(c, path, true); }
+int pc_apt_restore(pc_ctx *c, const char *path) { return ckpt_io(c, path, false); }
 
 int pc_apt_set_target(pc_ctx *c, int inst, int64_t e_target) {
   int rc = check_inst(c, inst);
@@ -627,7 +798,7 @@ int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t 
     a.window_from = sweeps - tail;
     a.tag_main = 7;   // TAG_LAD_SWEEP
     a.tag_ref = 8;    // TAG_LAD_REFINE
-    if ((rc = apt_launch(a, bt.n_cta, kTpb, bt.smem, c->stream))) return rc;
+    if ((rc = apt_launch(a, bt.n_cta, bt.tpb, bt.smem, c->stream))) return rc;
     s1.resize(bt.d_sum1.n);
     s2.resize(bt.d_sum2.n);
     PC_CUDA_TRY(cudaMemcpyAsync(s1.data(), bt.d_sum1.p, s1.size() * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -728,7 +899,7 @@ int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, u
   a.n_bins = n_bins;
   a.tag_main = 10;   // TAG_PIL_SWEEP
   a.tag_ref = 11;    // TAG_PIL_REFINE
-  if ((rc = apt_launch(a, bt.n_cta, kTpb, bt.smem, c->stream))) return rc;
+  if ((rc = apt_launch(a, bt.n_cta, bt.tpb, bt.smem, c->stream))) return rc;
   PC_CUDA_TRY(cudaMemcpyAsync(counts, bt.d_hist.p, (size_t)n_inst * n_beta * n_bins * 8,
                               cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));

@@ -6,7 +6,8 @@
 // 3D site s of parity q the slices of colour c are k = 2m + (c ^ q).  Eight
 // consecutive m of one (colour, site) share a 32-bit word, one spin per
 // nibble (bit 0 = spin +1), block b = m >> 3.  Shared memory holds
-// W[c][b][s] for the whole run (N * P / 2 bytes).  With this packing
+// W[c][s][b] for the whole run (N * P / 2 bytes; the NB words of a site are
+// contiguous, so they move as one vector access).  With this packing
 //  - the six spatial neighbours of a word are the words of the other colour
 //    at the neighbouring sites with the SAME block: nibble-aligned, and the
 //    coupling J (common to all slices) is one mask per direction;
@@ -81,7 +82,7 @@ __device__ __forceinline__ void spatial_counts(const pc::SqaArgs &a, const uint3
     const int n = neighbour(a, t, d);
     const uint32_t m = nib_mask((t.jb >> d) & 1u);
 #pragma unroll
-    for (int b = 0; b < NB; ++b) C[b] += Wo[b * a.N + n] ^ m;
+    for (int b = 0; b < NB; ++b) C[b] += Wo[(size_t)n * NB + b] ^ m;
   }
 }
 
@@ -152,42 +153,78 @@ __device__ __noinline__ uint32_t settle_ties(uint32_t w, uint4 x, uint4 y, uint3
   return w;
 }
 
+// NB consecutive words as one vector access (NB = 1, 2, 4, 8; else scalar).
+template <int NB>
+__device__ __forceinline__ void load_words(const uint32_t *p, uint32_t (&v)[NB]) {
+  if constexpr (NB % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < NB; q += 4) {
+      const uint4 t = *reinterpret_cast<const uint4 *>(p + q);
+      v[q] = t.x; v[q + 1] = t.y; v[q + 2] = t.z; v[q + 3] = t.w;
+    }
+  } else if constexpr (NB % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < NB; q += 2) {
+      const uint2 t = *reinterpret_cast<const uint2 *>(p + q);
+      v[q] = t.x; v[q + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) v[q] = p[q];
+  }
+}
+template <int NB>
+__device__ __forceinline__ void store_words(uint32_t *p, const uint32_t (&v)[NB]) {
+  if constexpr (NB % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < NB; q += 4)
+      *reinterpret_cast<uint4 *>(p + q) = make_uint4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+  } else if constexpr (NB % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < NB; q += 2) *reinterpret_cast<uint2 *>(p + q) = make_uint2(v[q], v[q + 1]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) p[q] = v[q];
+  }
+}
+
 // All NB words of one (site, colour) in one sweep.
 template <int NB>
 __device__ __forceinline__ void update_site(const pc::SqaArgs &a, const uint32_t *Wo, uint32_t *Wc,
                                             int s, const SiteK &k, int c, uint32_t sw,
                                             uint32_t boff, uint32_t ent) {
-  const int N = a.N;
   const int e = c ^ k.q;   // slice parity of this word's nibbles
   const uint32_t c2 = (uint32_t)c << 16;
-#if PC_SQA_UNROLL
+  uint32_t O[NB], C[NB], w[NB];
+  load_words<NB>(Wo + (size_t)s * NB, O);
 #pragma unroll
-#else
-#pragma unroll 1
-#endif
+  for (int b = 0; b < NB; ++b) C[b] = k.K;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    uint32_t Nw[NB];
+    load_words<NB>(Wo + (size_t)k.nb[d] * NB, Nw);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) C[b] += (uint32_t)k.eps[d] * Nw[b];
+  }
+#pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int bp = (b + 1 == NB) ? 0 : b + 1, bm = (b == 0) ? NB - 1 : b - 1;
-    const uint32_t Ob = Wo[b * N + s];
-    const uint32_t On = Wo[(e ? bp : bm) * N + s];
-    uint32_t C = k.K;
-#pragma unroll
-    for (int d = 0; d < 6; ++d) C += (uint32_t)k.eps[d] * Wo[b * N + k.nb[d]];
     // time neighbours k-1, k+1: the other colour's word and that word
     // shifted by one nibble (funnel shift through the adjacent block)
-    const uint32_t lo = e ? Ob : On;
-    const uint32_t hi = e ? On : Ob;
-    const uint32_t M = Ob + __funnelshift_r(lo, hi, e ? 4u : 28u);
-    const uint32_t Dlo = ((C & 0x0F0F0F0Fu) << 2) + ((M & 0x0F0F0F0Fu) << 5) + boff;
-    const uint32_t Dhi = (((C >> 4) & 0x0F0F0F0Fu) << 2) + (((M >> 4) & 0x0F0F0F0Fu) << 5) + boff;
+    const uint32_t lo = e ? O[b] : O[bm];
+    const uint32_t hi = e ? O[bp] : O[b];
+    const uint32_t M = O[b] + __funnelshift_r(lo, hi, e ? 4u : 28u);
+    const uint32_t Dlo = ((C[b] & 0x0F0F0F0Fu) << 2) + ((M & 0x0F0F0F0Fu) << 5) + boff;
+    const uint32_t Dhi = (((C[b] >> 4) & 0x0F0F0F0Fu) << 2) + (((M >> 4) & 0x0F0F0F0Fu) << 5) + boff;
     const uint4 x = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_SWEEP, a.k0, a.k1);
     bool tie = false;
-    uint32_t w = decide_word(x, Dlo, Dhi, tie);
+    w[b] = decide_word(x, Dlo, Dhi, tie);
     if (tie) {
       const uint4 y = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_REFINE, a.k0, a.k1);
-      w = settle_ties(w, x, y, Dlo, Dhi);
+      w[b] = settle_ties(w[b], x, y, Dlo, Dhi);
     }
-    Wc[b * N + s] = w;
   }
+  store_words<NB>(Wc + (size_t)s * NB, w);
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -222,7 +259,7 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
   if (s0 == 0) {
     // Algorithm S1: all spins of all slices start random (+1 iff half < 2^15)
     for (int idx = tid; idx < 2 * NB * N; idx += nt) {
-      const int s = idx % N, cb = idx / N, b = cb % NB, c = cb / NB;
+      const int b = idx % NB, cs = idx / NB, s = cs % N, c = cs / N;   // W[c][s][b]
       const uint4 x = philox((uint32_t)s, 0u, ((uint32_t)c << 16) | (uint32_t)b,
                              (ent << 8) | TAG_SQA_INIT, a.k0, a.k1);
       uint32_t w = 0;
@@ -283,7 +320,7 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
       uint32_t C[NB];
       spatial_counts<NB>(a, Wo, t, C);
       for (int b = 0; b < NB; ++b) {
-        const uint32_t w = Wc[b * N + s];
+        const uint32_t w = Wc[(size_t)s * NB + b];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int ci = (C[b] >> (4 * i)) & 0xF;
@@ -308,7 +345,7 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
   }
   if (a.spins) {
     for (int idx = tid; idx < 2 * NB * N; idx += nt) {
-      const int s = idx % N, cb = idx / N, b = cb % NB, c = cb / NB;
+      const int b = idx % NB, cs = idx / NB, s = cs % N, c = cs / N;   // W[c][s][b]
       const int r = (int)fdiv((uint32_t)s, a.mLx), x = s - r * a.Lx;
       const int z = (int)fdiv((uint32_t)r, a.mLy), y = r - z * a.Ly;
       const int e = c ^ ((x + y + z) & 1);

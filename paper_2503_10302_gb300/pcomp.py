@@ -43,6 +43,10 @@ SIGNATURES = {
     "pc_jperp_q": (ctypes.c_int32, [c_dbl, c_int, c_dbl]),
     "pc_apt_load": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_i32p, c_f64p, c_int, c_u32]),
     "pc_apt_run": (c_int, [c_vp, c_i64, c_int, c_int]),
+    "pc_apt_autotune": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_int)]),
+    "pc_apt_set_block_threads": (c_int, [c_vp, c_int]),
+    "pc_apt_save": (c_int, [c_vp, ctypes.c_char_p]),
+    "pc_apt_restore": (c_int, [c_vp, ctypes.c_char_p]),
     "pc_apt_progress": (c_int, [c_vp, c_i64p, c_i64p]),
     "pc_apt_set_target": (c_int, [c_vp, c_int, c_i64]),
     "pc_apt_get_state": (c_int, [c_vp, c_int, c_i8p, c_i64p, c_i32p]),
@@ -241,6 +245,24 @@ def pc_apt_load(ctx, dims, J_list, betas_list, n_labels: int = 2, entry0: int = 
 
 def pc_apt_run(ctx, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True) -> None:
     _call("pc_apt_run", ctx, c_i64(n_swaps), sweeps_per_swap, int(bool(icm)))
+
+
+def pc_apt_autotune(ctx, trial_swaps: int = 16, icm: bool = True) -> int:
+    t = c_int()
+    _call("pc_apt_autotune", ctx, trial_swaps, int(bool(icm)), ctypes.byref(t))
+    return t.value
+
+
+def pc_apt_set_block_threads(ctx, tpb: int) -> None:
+    _call("pc_apt_set_block_threads", ctx, tpb)
+
+
+def pc_apt_save(ctx, path: str) -> None:
+    _call("pc_apt_save", ctx, os.fsencode(path))
+
+
+def pc_apt_restore(ctx, path: str) -> None:
+    _call("pc_apt_restore", ctx, os.fsencode(path))
 
 
 def pc_apt_progress(ctx):

@@ -144,6 +144,63 @@ def c3_time_to_target(n_inst=64, L=12, rho=1e-3, best_runs=10, best_sweeps=10000
             "e_best_per_spin_mean": float((e_best / N).mean())}
 
 
+def c2_residual_vs_R(L=8, P=64, R=256, T=0.05, sweeps=10000, best_runs=10, best_sweeps=100000,
+                     Rs=(1, 4, 16, 64, 256)) -> Dict:
+    """DT-SQA on one L = 8 instance: residual energy of the best slice of a
+    run, and of the best of R independent runs as R grows.  E_best: best of
+    APT+ICM runs on the same instance.  The Gaussian extreme-value median of
+    the best of R (Eq. EVTmedianFinal) is reported beside the measurement."""
+    from scipy.special import erfcinv
+    wl = W.sqa_workload(L, P, R, T, sweeps)
+    N = L ** 3
+    ctx = pcomp.Context(0, 31)
+    timer = DeviceTimer(ctx)
+    pcomp.pc_sqa_setup(ctx.h, wl.dims, wl.J, P, T, wl.gamma)
+    import torch
+    E_dev = torch.empty((R, P), dtype=torch.int32, device="cuda")
+    dt = timer.time(lambda: pcomp.pc_sqa_run_dev(ctx.h, R, 0, E_dev.data_ptr()))
+    E = E_dev.cpu().numpy().astype(np.int64)
+    ctx.close()
+    ladder, _ = adaptive_ladders(np.array([[L] * 3], np.int32), [wl.J])
+    batch = W.AptBatch(np.array([[L] * 3], np.int32), [wl.J], [pcomp.pc_resample_ladder(ladder[0], 32)], 2)
+    e_best = int(best_energies(batch, best_runs, best_sweeps)[0])
+    run_best = E.min(axis=1)
+    e_best = min(e_best, int(run_best.min()))
+    rho_run = (run_best - e_best) / N
+    mu, sd = float(rho_run.mean()), float(rho_run.std(ddof=1))
+    out = {"L": L, "P": P, "R": R, "T": T, "sweeps": sweeps, "anneal_seconds": dt,
+           "flips_per_ns": N * P * R * sweeps / dt / 1e9, "e_best": e_best,
+           "rho_single_run": {"mean": mu, "std": sd}, "best_of_R": {}}
+    for r in Rs:
+        g = rho_run[: (R // r) * r].reshape(-1, r).min(axis=1)
+        pred = mu + np.sqrt(2.0) * sd * float(erfcinv(2.0 ** ((r - 1) / r)))
+        out["best_of_R"][str(r)] = {"groups": int(g.size), "mean": float(g.mean()),
+                                    "median": float(np.median(g)), "evt_median_gaussian": pred,
+                                    "hit_fraction_rho_le_1e-3": float((g <= 1e-3).mean())}
+    return out
+
+
+def c4_mixed_time_to_target(rho=1e-3, best_runs=10, best_sweeps=20000, max_sweeps=100000) -> Dict:
+    """256 mixed-size instances (L in {6..16}, 24-32 geometric temperatures
+    x 2): flips/ns of the fused kernel and per-instance time to rho_E."""
+    batch = W.apt_mixed_batch()
+    tp = apt_throughput(batch, 300, True)
+    e_best = best_energies(batch, best_runs, best_sweeps)
+    Ns = np.array([int(np.prod(d)) for d in batch.dims])
+    targets = np.floor(e_best + rho * Ns).astype(np.int64)
+    hit, t_sweep, total = run_to_target(batch, targets, max_sweeps)
+    ok = hit >= 0
+    per_L = {}
+    for Lv in sorted(set(int(d[0]) for d in batch.dims)):
+        sel = np.array([int(d[0]) == Lv for d in batch.dims])
+        h = hit[sel & ok]
+        per_L[str(Lv)] = {"instances": int(sel.sum()), "hit_fraction": float((hit[sel] >= 0).mean()),
+                          "median_hit_sweep": float(np.median(h)) if h.size else None,
+                          "median_time_s": float(np.median(h) * t_sweep) if h.size else None}
+    return {"flips_per_ns_icm": tp["flips_per_ns"], "apt_seconds_per_sweep": t_sweep,
+            "hit_fraction": float(ok.mean()), "per_L": per_L}
+
+
 def training_set(n: int, sizes=(6, 8, 10, 12, 14, 16), seed: int = W.SEED_TRAIN, ladder_kw=None,
                  chunk: int = 4096):
     """n generated instances (even L drawn from `sizes`), their adaptive
@@ -191,8 +248,9 @@ def train(X: np.ndarray, Y: np.ndarray, epochs: int = 60, batch: int = 256, lr: 
         perm = torch.from_numpy(rng.permutation(n)).cuda()
         Xp, Yp = Xd[perm].contiguous(), Yd[perm].contiguous()
         torch.cuda.synchronize()
+        lr_ep = lr * (0.1 ** (ep / max(1, epochs - 1)))     # decays tenfold over training
         for b0 in range(0, n - batch + 1, batch):
-            m.train_step_dev(batch, Xp[b0:].data_ptr(), Yp[b0:].data_ptr(), lr, loss.data_ptr())
+            m.train_step_dev(batch, Xp[b0:].data_ptr(), Yp[b0:].data_ptr(), lr_ep, loss.data_ptr())
         torch.cuda.synchronize()
         hist.append(float(loss.item()))
     t_train = time.perf_counter() - t0
@@ -221,13 +279,17 @@ def c5_learned_vs_adaptive(n_train=20000, n_eval=128, L=16, rho=1e-3, best_runs=
     # per-L mean training ladder (no instance information) for context
     mean_lad = Y[Ls == L].mean(axis=0).astype(np.float64) if (Ls == L).any() else Y.mean(axis=0)
     betas_m = [mean_lad + 1e-9 * np.arange(32) for _ in range(n_eval)]
+    Ya = np.stack(betas_a)
+    ladder_rmse = {"learned": float(np.sqrt(((np.stack(betas_l) - Ya) ** 2).mean())),
+                   "mean_ladder": float(np.sqrt(((mean_lad[None, :] - Ya) ** 2).mean()))}
     ref = W.AptBatch(dims, J, betas_a, 2)
     e_best = best_energies(ref, best_runs, best_sweeps)
     targets = np.floor(e_best + rho * N).astype(np.int64)
     out = {"n_train": n_train, "n_eval": n_eval, "L": L, "rho_target": rho,
            "train_ladder_seconds": t_lad_train, "train_feature_seconds": t_feat_train,
            "train_seconds": t_train, "train_loss_first_last": [hist[0], hist[-1]],
-           "ladder_settings": ladder_kw, "mean_ladder_len_L16": float(lens[Ls == L].mean()) if (Ls == L).any() else None}
+           "ladder_settings": ladder_kw, "mean_ladder_len_L16": float(lens[Ls == L].mean()) if (Ls == L).any() else None,
+           "ladder_rmse_vs_adaptive": ladder_rmse}
     for name, betas, t_pre in (("adaptive", betas_a, t_adapt), ("learned", betas_l, t_learn),
                                ("mean_ladder", betas_m, 0.0)):
         hit, t_sweep, total = run_to_target(W.AptBatch(dims, J, betas, 2), targets, max_sweeps)
@@ -246,13 +308,16 @@ def c5_learned_vs_adaptive(n_train=20000, n_eval=128, L=16, rho=1e-3, best_runs=
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("what", choices=["throughput", "c3", "c5", "all"])
+    ap.add_argument("what", choices=["throughput", "c2", "c3", "c4", "c5", "all"])
     ap.add_argument("--sweeps", type=int, default=200)
     ap.add_argument("--batch", choices=["apt_plain_L4", "apt_icm_64xL12", "apt_icm_mixed256"])
     ap.add_argument("--icm", type=int, choices=[0, 1])
     ap.add_argument("--n-train", type=int, default=20000)
     ap.add_argument("--n-eval", type=int, default=128)
     ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--best-runs", type=int, default=10)
+    ap.add_argument("--best-sweeps", type=int, default=20000)
+    ap.add_argument("--max-sweeps", type=int, default=100000)
     args = ap.parse_args()
     out = {}
     if args.what in ("throughput", "all"):
@@ -264,10 +329,16 @@ def main():
             batch = batches[name]()
             for icm in ((True, False) if args.icm is None else (bool(args.icm),)):
                 out[f"{name}_icm{int(icm)}"] = apt_throughput(batch, args.sweeps, icm)
+    if args.what in ("c2", "all"):
+        out["c2"] = c2_residual_vs_R()
     if args.what in ("c3", "all"):
         out["c3"] = c3_time_to_target()
+    if args.what in ("c4", "all"):
+        out["c4"] = c4_mixed_time_to_target()
     if args.what in ("c5", "all"):
-        out["c5"] = c5_learned_vs_adaptive(n_train=args.n_train, n_eval=args.n_eval, epochs=args.epochs)
+        out["c5"] = c5_learned_vs_adaptive(n_train=args.n_train, n_eval=args.n_eval, epochs=args.epochs,
+                                           best_runs=args.best_runs, best_sweeps=args.best_sweeps,
+                                           max_sweeps=args.max_sweeps)
     print(json.dumps(out, indent=1))
 
 

@@ -181,6 +181,57 @@ def test_c4_mixed_batch_sampled(pc, orc):
     ctx.close()
 
 
+def test_launch_shape_does_not_change_results(pc, orc):
+    """256, 384 and 512 threads per CTA (and the autotuner's choice) give
+    bit-identical chains."""
+    b = W.apt_uniform_batch(3, 8, 20)
+    states = []
+    for tpb in (256, 384, 512, None):
+        ctx = pc.Context(0, 13)
+        pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
+        if tpb is None:
+            assert pc.pc_apt_autotune(ctx.h, 8, True) in (256, 384, 512)
+        else:
+            pc.pc_apt_set_block_threads(ctx.h, tpb)
+        pc.pc_apt_run(ctx.h, 40, 1, True)
+        states.append([pc.pc_apt_get_state(ctx.h, i, 512, 40) for i in range(3)])
+        ctx.close()
+    for other in states[1:]:
+        for x, y in zip(states[0], other):
+            for u, v in zip(x, y):
+                assert np.array_equal(u, v)
+
+
+def test_checkpoint_resume_bit_exact(pc, tmp_path):
+    """200 attempts == 90, save, restore into a fresh context, 110 more."""
+    b = W.apt_uniform_batch(2, 6, 12)
+    c1 = pc.Context(0, 8)
+    pc.pc_apt_load(c1.h, b.dims, b.J, b.betas, 2, 0)
+    pc.pc_apt_run(c1.h, 200, 1, True)
+    c2 = pc.Context(0, 8)
+    pc.pc_apt_load(c2.h, b.dims, b.J, b.betas, 2, 0)
+    pc.pc_apt_run(c2.h, 90, 1, True)
+    path = str(tmp_path / "apt.ckpt")
+    pc.pc_apt_save(c2.h, path)
+    c2.close()
+    c3 = pc.Context(0, 8)
+    pc.pc_apt_load(c3.h, b.dims, b.J, b.betas, 2, 0)
+    pc.pc_apt_restore(c3.h, path)
+    pc.pc_apt_run(c3.h, 110, 1, True)
+    assert pc.pc_apt_progress(c3.h) == pc.pc_apt_progress(c1.h)
+    for i in range(2):
+        for u, v in zip(pc.pc_apt_get_state(c1.h, i, 216, 24), pc.pc_apt_get_state(c3.h, i, 216, 24)):
+            assert np.array_equal(u, v)
+        assert pc.pc_apt_get_best(c1.h, i, 216)["E"] == pc.pc_apt_get_best(c3.h, i, 216)["E"]
+        for u, v in zip(pc.pc_apt_get_stats(c1.h, i, 12, 2), pc.pc_apt_get_stats(c3.h, i, 12, 2)):
+            assert np.array_equal(u, v)
+    c4 = pc.Context(0, 9)    # another seed: refused
+    pc.pc_apt_load(c4.h, b.dims, b.J, b.betas, 2, 0)
+    with pytest.raises(pc.PcompError):
+        pc.pc_apt_restore(c4.h, path)
+    c1.close(); c3.close(); c4.close()
+
+
 def test_apt_rejects_bad_input(pc):
     ctx = pc.Context(0, 0)
     J = [W.ea_couplings((4, 4, 4), 1, 0)]
