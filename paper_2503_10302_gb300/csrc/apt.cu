@@ -55,7 +55,7 @@ constexpr int MAXGC = 4;   // groups handled per thread per site
 
 struct Geo {
   int Lx, Ly, Lz, N, H, hx;
-  uint32_t mhx, mLy;
+  uint32_t mhx, mLy, mLy2;
 };
 
 // Neighbours (other colour, colour-local index) of site (c, j), in the
@@ -94,11 +94,6 @@ __device__ __forceinline__ int lin_of(const Geo &g, int c, int j) {
   return 2 * jx + ((y + z + c) & 1) + g.Lx * row;
 }
 
-__device__ __forceinline__ int warp_sum(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-  return v;
-}
 
 // Threshold of nibble i for packed count C (thr points at the group's 64
 // entries: 8 buffers x 8 counts).
@@ -142,14 +137,13 @@ struct Shared {
   int64_t *m64;      // best E, best sweep, hit sweep, target
   int32_t *m32;      // best buffer, flag, icm counters x3, any-swap flag
   uint8_t *jn;       // [2][H]
-  uint32_t *V;       // ICM cluster bits [2][H], then overlap bits [2][H]
+  uint32_t *V;       // ICM cluster bits [2][H], overlap bits [2][H], transposed overlaps [N/32][32]
   uint32_t *ikx;     // [64] per pair: Philox word 0, then k
   int32_t *ibit;     // [64] per pair: replica choice bit
   int32_t *inm;      // [64] per pair: mismatch count
   int32_t *isz;      // [64] per pair: cluster size
   uint32_t *imask;   // [3][8] per half-group: cluster-flip, whole-flip label 0, label 1
   uint32_t *swm;     // [8] per group: in-group swap nibble mask; [8] cross-group flags
-  uint32_t *scan;    // [nwarps + 1][16] block-scan scratch
 };
 
 struct Cta {
@@ -302,46 +296,19 @@ __device__ void best_update(const AptArgs &a, const Cta &k, const Shared &sh, in
   __syncthreads();
 }
 
-// Block-wide exclusive scan of 16 words of two 16-bit lanes each (lane
-// totals < 2^16).  Returns the exclusive prefix in ex[] and the block total
-// in tot[] (valid in every thread).
-__device__ __forceinline__ void block_scan16(const Shared &sh, const uint32_t (&v)[16],
-                                             uint32_t (&ex)[16], uint32_t (&tot)[16]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  uint32_t inc[16];
+// 32 x 32 bit-matrix transpose across a warp: lane l holds row l on entry
+// (bit c = element (l, c)) and column l on exit (bit r = element (r, l)).
+// Five butterfly stages exchange the off-diagonal blocks of size 16..1.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    uint32_t x = v[q];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    inc[q] = x;
-    if (lane == 31) sh.scan[16 * warp + q] = x;
+  for (int j = 16; j >= 1; j >>= 1) {
+    const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                                                     : j == 2 ? 0x33333333u : 0x55555555u;
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
   }
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      uint32_t x = lane < nwarps ? sh.scan[16 * lane + q] : 0u;
-      uint32_t y = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t z = __shfl_up_sync(0xFFFFFFFFu, y, o);
-        if (lane >= o) y += z;
-      }
-      if (lane < nwarps) sh.scan[16 * lane + q] = y - x;   // exclusive warp offsets
-      if (lane == 31) sh.scan[16 * nwarps + q] = y;        // block total
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    ex[q] = sh.scan[16 * warp + q] + inc[q] - v[q];
-    tot[q] = sh.scan[16 * nwarps + q];
-  }
-  __syncthreads();
+  return x;
 }
 
 // Nibble mask (bit 4i) <-> byte (bit i) of eight pairs.
@@ -382,99 +349,217 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     }
   }
   if (tid < 24) sh.imask[tid] = 0;
-  // (A) overlaps and mismatch counts over this thread's canonical range
-  const int cr = (N + nt - 1) / nt, k0 = min(N, tid * cr), k1 = min(N, k0 + cr);
-  uint32_t cnt[16], ex[16], tot[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) cnt[q] = 0;
-  for (int kk = k0; kk < k1; ++kk) {
-    const int c = kk >= H ? 1 : 0, j = kk - c * H;
-    uint32_t xb = 0;
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      if (h >= Gh) break;
-      const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
-      xb |= nib_to_byte(x) << (8 * h);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) cnt[4 * h + m] += (x >> (4 * m)) & 0x000F000Fu;
-    }
-    X[kk] = xb;
-    V[kk] = 0u;
-  }
-  block_scan16(sh, cnt, ex, tot);
-  PROF_MARK(4, pt);
-  // lane (h, m) low 16 bits: pair 8h + m; high 16 bits: pair 8h + m + 4
-  if (tid < 8 * Gh) {
-    const int r = tid, h = r >> 3, i = r & 7, q = 4 * h + (i & 3);
-    const int nm = (int)((tot[q] >> ((i >> 2) * 16)) & 0xFFFFu);
-    sh.inm[r] = nm;
-    if (r < k.T) sh.ikx[r] = (uint32_t)(((uint64_t)sh.ikx[r] * (uint64_t)nm) >> 32);
+  if (tid < 64) {
+    sh.isz[tid] = 0;
+    sh.inm[tid] = 0;
   }
   __syncthreads();
-  // seeds: the thread whose range holds the k-th mismatch of a pair plants it
-  for (int r = 0; r < k.T; ++r) {
-    const int h = r >> 3, i = r & 7, q = 4 * h + (i & 3), sh16 = (i >> 2) * 16;
-    if (sh.inm[r] == 0) continue;
-    const int kth = (int)sh.ikx[r];
-    const int lo = (int)((ex[q] >> sh16) & 0xFFFFu), n = (int)((cnt[q] >> sh16) & 0xFFFFu);
-    if (kth < lo || kth >= lo + n) continue;
-    int rem = kth - lo;
-    for (int kk = k0; kk < k1; ++kk) {
-      if ((X[kk] >> r) & 1u) {
-        if (rem == 0) {
-          V[kk] |= 1u << r;
-          break;
-        }
-        --rem;
+  // (A) overlaps.  Warp w takes chunks of 32 sites in canonical order; the
+  // transpose of the chunk's X words gives lane r the chunk's mismatch
+  // bitmask of pair r, kept in Xt[chunk][r].
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5, nchunk = (N + 31) >> 5;
+  uint32_t *Xt = sh.V + 2 * N;   // [nchunk][32]
+  uint32_t nmis = 0;             // lane r: mismatches of pair r in this warp's chunks
+  for (int ch = warp; ch < nchunk; ch += nw) {
+    const int kk = ch * 32 + lane;
+    uint32_t xb = 0;
+    if (kk < N) {
+      const int c = kk >= H ? 1 : 0, j = kk - c * H;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        if (h >= Gh) break;
+        const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
+        xb |= nib_to_byte(x) << (8 * h);
       }
+      X[kk] = xb;
+      V[kk] = 0u;
+    }
+    const uint32_t col = warp_transpose32(xb);
+    Xt[ch * 32 + lane] = col;
+    nmis += __popc(col);
+  }
+  if (lane < k.T && nmis) atomicAdd(&sh.inm[lane], (int)nmis);
+  __syncthreads();
+  PROF_MARK(4, pt);
+  // seeds: warp w finds the k-th mismatch of pairs w, w + nw, ...: chunk
+  // counts by popcount, a warp scan over chunks, then the set bit inside
+  // the chunk
+  for (int r = warp; r < k.T; r += nw) {
+    const int nm = sh.inm[r];
+    if (nm == 0) continue;
+    const int kth = (int)(((uint64_t)sh.ikx[r] * (uint64_t)nm) >> 32);
+    int base = 0;
+    for (int ch0 = 0; ch0 < nchunk; ch0 += 32) {
+      const int ch = ch0 + lane;
+      uint32_t w = ch < nchunk ? Xt[ch * 32 + r] : 0u;
+      const int cn = __popc(w);
+      int inc = cn;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      const int ex = base + inc - cn;
+      const bool hit = kth >= ex && kth < ex + cn;
+      if (hit) {
+        // position of set bit number q (from 0) of w: binary search on
+        // popcounts of the low half of the remaining window
+        int q = kth - ex, pos = 0;
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1) {
+          const int cl = __popc(w & ((1u << h) - 1u));
+          if (q >= cl) {
+            q -= cl;
+            w >>= h;
+            pos += h;
+          }
+        }
+        atomicOr(&V[ch * 32 + pos], 1u << r);
+      }
+      if (__any_sync(0xFFFFFFFFu, hit)) break;
+      base += __shfl_sync(0xFFFFFFFFu, inc, 31);
     }
   }
   __syncthreads();
   PROF_MARK(5, pt);
   // (B) flood fill.  The cluster is the least fixed point of the monotone
-  // update V <- V | (X & OR_nbr V); each site word has one writer (its
-  // thread), so a pass relaxes both colours without a barrier (a stale
-  // neighbour read only delays growth) and a pass with no change anywhere,
-  // started after a barrier, proves the fixed point.
-  for (int it = 0; it < N; ++it) {
-    int changed = 0;
-    for (int c = 0; c < 2; ++c) {
-      volatile const uint32_t *Vo = V + (1 - c) * H;
-      for (int j = tid; j < H; j += nt) {
-        const uint32_t x = X[c * H + j];
-        const uint32_t v = V[c * H + j];
-        if (!(x & ~v)) continue;          // nothing left to add here
-        int n[6];
-        neighbours(k.geo, c, j, n);
-        const uint32_t o = Vo[n[0]] | Vo[n[1]] | Vo[n[2]] | Vo[n[3]] | Vo[n[4]] | Vo[n[5]];
-        const uint32_t nv = v | (x & o);
-        if (nv != v) {
-          V[c * H + j] = nv;
-          changed = 1;
+  // update V <- V | (X & OR_nbr V).  A thread owns 2x2x2 blocks of sites
+  // (bx, by, bz): per pass it reads the 24 outside neighbours of a block and
+  // closes the block internally (the cube has diameter 3), so a pass moves
+  // a cluster front by up to three sites.  Each site word has one writer,
+  // so passes run without inner barriers (a stale neighbour read only delays
+  // growth) and a pass with no change anywhere, started after a barrier,
+  // proves the fixed point.
+  {
+    const Geo &g = k.geo;
+    const int hx = g.hx, hy = g.Ly >> 1, nblk = N >> 3;
+    volatile const uint32_t *Vv = V;
+    // block geometry: site i = dx + 2 dy + 4 dz of block (bx, by, bz) has
+    // colour (dx+dy+dz)&1 and index bx + hx (y0 + dy + Ly (z0 + dz)) inside
+    // its colour; an outside neighbour is the opposite corner's word of the
+    // adjacent block, i.e. a site of this block shifted by one block step
+    struct Blk {
+      int kk[8];
+      uint32_t dx2, dy2, dz2;   // (minus, plus) block steps as two int16 each
+    };
+    auto make_blk = [&](int blk) {
+      Blk B;
+      const int rest = (int)fdiv((uint32_t)blk, g.mhx);           // blk / hx
+      const int bx = blk - rest * hx;
+      const int bz = (int)fdiv((uint32_t)rest, g.mLy2);           // rest / (Ly/2)
+      const int by = rest - bz * hy;
+      const int y0 = 2 * by, z0 = 2 * bz;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int dx = i & 1, dy = (i >> 1) & 1, dz = i >> 2;
+        B.kk[i] = ((dx + dy + dz) & 1) * H + bx + hx * (y0 + dy + g.Ly * (z0 + dz));
+      }
+      const int LyHx = g.Ly * hx;
+      auto pack = [](int m, int p) { return ((uint32_t)m & 0xFFFFu) | ((uint32_t)p << 16); };
+      B.dx2 = pack(bx == 0 ? hx - 1 : -1, bx + 1 == hx ? 1 - hx : 1);
+      B.dy2 = pack(hx * (y0 == 0 ? g.Ly - 2 : -2), hx * (y0 + 2 == g.Ly ? 2 - g.Ly : 2));
+      B.dz2 = pack(LyHx * (z0 == 0 ? g.Lz - 2 : -2), LyHx * (z0 + 2 == g.Lz ? 2 - g.Lz : 2));
+      return B;
+    };
+    // one relaxation of a block: outside neighbours, then the internal
+    // closure (three rounds reach across the cube); writes changed words
+    auto relax = [&](const Blk &B, const uint32_t (&x)[8], uint32_t (&v)[8]) {
+      uint32_t nv[8];
+      const int dxm = (int16_t)(B.dx2 & 0xFFFFu), dxp = (int16_t)(B.dx2 >> 16);
+      const int dym = (int16_t)(B.dy2 & 0xFFFFu), dyp = (int16_t)(B.dy2 >> 16);
+      const int dzm = (int16_t)(B.dz2 & 0xFFFFu), dzp = (int16_t)(B.dz2 >> 16);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int dx = i & 1, dy = (i >> 1) & 1, dz = i >> 2;
+        const uint32_t ox = Vv[B.kk[i ^ 1] + (dx ? dxp : dxm)];
+        const uint32_t oy = Vv[B.kk[i ^ 2] + (dy ? dyp : dym)];
+        const uint32_t oz = Vv[B.kk[i ^ 4] + (dz ? dzp : dzm)];
+        nv[i] = v[i] | (x[i] & (ox | oy | oz));
+      }
+#pragma unroll
+      for (int round = 0; round < 3; ++round) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) nv[i] |= x[i] & (nv[i ^ 1] | nv[i ^ 2] | nv[i ^ 4]);
+      }
+      int ch = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (nv[i] != v[i]) {
+          V[B.kk[i]] = nv[i];
+          v[i] = nv[i];
+          ch = 1;
         }
       }
+      return ch;
+    };
+    if (nblk <= nt) {
+      // one block per thread: its geometry and cluster words stay in
+      // registers across passes (the thread is their only writer)
+      Blk B;
+      uint32_t v[8];
+      bool open = false;
+      if (tid < nblk) {
+        B = make_blk(tid);
+        uint32_t o = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          v[i] = V[B.kk[i]];
+          o |= X[B.kk[i]] & ~v[i];
+        }
+        open = o != 0;
+      }
+      for (int it = 0; it < N; ++it) {
+        int changed = 0;
+        if (open) {
+          uint32_t x[8], o = 0;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) x[i] = X[B.kk[i]];
+          changed = relax(B, x, v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) o |= x[i] & ~v[i];
+          open = o != 0;
+        }
+        if (!__syncthreads_or(changed)) {
+#if PC_APT_PROFILE
+          if (blockIdx.x == 0 && tid == 0) atomicAdd(&g_apt_prof[11], (unsigned long long)(it + 1));
+#endif
+          break;
+        }
+      }
+    } else {
+      for (int it = 0; it < N; ++it) {
+        int changed = 0;
+        for (int blk = tid; blk < nblk; blk += nt) {
+          const Blk B = make_blk(blk);
+          uint32_t x[8], v[8];
+          uint32_t open = 0;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            x[i] = X[B.kk[i]];
+            v[i] = Vv[B.kk[i]];
+            open |= x[i] & ~v[i];
+          }
+          if (open) changed |= relax(B, x, v);
+        }
+        if (!__syncthreads_or(changed)) break;
+      }
     }
-    if (!__syncthreads_or(changed)) break;
   }
   PROF_MARK(6, pt);
-  // (C) cluster sizes
-#pragma unroll
-  for (int q = 0; q < 16; ++q) cnt[q] = 0;
-  for (int kk = k0; kk < k1; ++kk) {
-    const uint32_t v = V[kk];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      if (h >= Gh) break;
-      const uint32_t z = byte_to_nib((v >> (8 * h)) & 0xFFu);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) cnt[4 * h + m] += (z >> (4 * m)) & 0x000F000Fu;
+  // (C) cluster sizes: per chunk, lane r counts pair r's cluster sites
+  {
+    uint32_t sz = 0;
+    for (int ch = warp; ch < nchunk; ch += nw) {
+      const int kk = ch * 32 + lane;
+      sz += __popc(warp_transpose32(kk < N ? V[kk] : 0u));
     }
+    if (lane < k.T && sz) atomicAdd(&sh.isz[lane], (int)sz);
   }
-  block_scan16(sh, cnt, ex, tot);
+  __syncthreads();
   // (D) decisions
   if (tid < k.T) {
-    const int r = tid, h = r >> 3, i = r & 7, q = 4 * h + (i & 3);
-    const int size = (int)((tot[q] >> ((i >> 2) * 16)) & 0xFFFFu);
+    const int r = tid, h = r >> 3, i = r & 7;
+    const int size = sh.isz[r];
     const uint32_t bit = 1u << (4 * i);
     if (sh.inm[r] == 0) {
       atomicAdd(&sh.m32[2], 1);
@@ -554,19 +639,29 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
   __syncthreads();
   if (!sh.m32[5]) return;
   const int H = k.geo.H, G = k.Gc;
+  // groups touched by this attempt's swaps, and the groups g whose nibble 7
+  // pairs with nibble 0 of g + 1
+  uint32_t touch = 0, cross = 0;
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    if (g < G && sh.swm[g]) touch |= 1u << g;
+    if (g + 1 < G && sh.swm[8 + g]) cross |= 1u << g;
+  }
+  touch |= cross | (cross << 1);
   for (int kk = threadIdx.x; kk < 2 * H; kk += blockDim.x) {
     uint32_t *col = sh.S + kk;   // word (g, c, j) at col[g * 2H]
-    for (int g = 0; g < G; ++g) {
-      const uint32_t m = sh.swm[g];
-      if (m) {
-        uint32_t w = col[(size_t)g * 2 * H];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      if (((touch >> g) & 1u) && sh.swm[g]) {
+        const uint32_t w = col[(size_t)g * 2 * H], m = sh.swm[g];
         const uint32_t d = (w ^ (w >> 4)) & m;
         col[(size_t)g * 2 * H] = w ^ (d | (d << 4));
       }
     }
-    for (int g = 0; g + 1 < G; ++g) {
-      if (sh.swm[8 + g]) {
-        uint32_t w0 = col[(size_t)g * 2 * H], w1 = col[(size_t)(g + 1) * 2 * H];
+#pragma unroll
+    for (int g = 0; g < 7; ++g) {
+      if ((cross >> g) & 1u) {
+        const uint32_t w0 = col[(size_t)g * 2 * H], w1 = col[(size_t)(g + 1) * 2 * H];
         const uint32_t d = ((w0 >> 28) ^ w1) & 1u;
         col[(size_t)g * 2 * H] = w0 ^ (d << 28);
         col[(size_t)(g + 1) * 2 * H] = w1 ^ d;
@@ -589,6 +684,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.geo.hx = P.Lx >> 1;
   k.geo.mhx = P.mhx;
   k.geo.mLy = P.mLy;
+  k.geo.mLy2 = P.mLy2;
   k.T = P.T;
   k.Tp = P.Tp;
   k.A = P.A;
@@ -601,7 +697,6 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.tpc = blockDim.x / k.nch;
   k.gc = (k.Gc + k.nch - 1) / k.nch;
   const int N = P.N, G8 = 8 * k.Gc;
-  const int nwarps = blockDim.x >> 5;
   const int64_t s0 = a.ctr[0], t0 = a.ctr[1];
   const bool icm = a.mode == pc::APT_MODE_APT && a.icm;
   // carve shared memory
@@ -628,8 +723,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.isz = reinterpret_cast<int32_t *>(cur);      cur += 64;
   sh.imask = cur;                                 cur += 24;
   sh.swm = cur;                                   cur += 16;
-  sh.scan = cur;                                  cur += 16 * (nwarps + 1);
-  sh.V = cur;                                     cur += icm ? (size_t)2 * N : 0;   // V and X
+  sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 : 0;   // V, X, Xt
   sh.jn = reinterpret_cast<uint8_t *>(cur);
 
   // load state
@@ -721,6 +815,8 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     }
   }
 
+  // every thread's last histogram / sum update lands before the write-back
+  __syncthreads();
   // store state
   uint32_t *gSo = a.spins + P.spin_off + (size_t)k.g0 * N;
   for (int i = threadIdx.x; i < k.Gc * N; i += blockDim.x) gSo[i] = sh.S[i];
@@ -786,9 +882,9 @@ namespace pc {
 size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins) {
   const size_t G8 = 8 * (size_t)Gc;
   size_t words = (size_t)Gc * N + 16 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
-  words += 4 * 64 + 24 + 16 + 16 * ((size_t)nwarps + 1);
+  words += 4 * 64 + 24 + 16;
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
-  if (mode == APT_MODE_APT && icm) words += (size_t)2 * N;
+  if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31;   // V, X and the transposed X
   return words * 4 + (size_t)N + 16;
 }
 

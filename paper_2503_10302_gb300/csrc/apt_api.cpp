@@ -122,6 +122,7 @@ int build_batch(pc_ctx *c, Batch &bt, const std::vector<ProbSpec> &specs, int n_
     P.N = s.lat.N;
     P.mhx = recip32((uint32_t)(P.Lx / 2));
     P.mLy = recip32((uint32_t)P.Ly);
+    P.mLy2 = recip32((uint32_t)(P.Ly / 2));
     P.T = s.T;
     P.Tp = s.Tp;
     P.A = s.A;

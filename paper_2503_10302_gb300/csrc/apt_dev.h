@@ -13,6 +13,7 @@ enum : int { APT_MODE_APT = 0, APT_MODE_LADDER = 1, APT_MODE_PILOT = 2, APT_MODE
 struct AptProbDev {
   int Lx, Ly, Lz, N;
   uint32_t mhx, mLy;      // ceil(2^32 / (Lx/2)), ceil(2^32 / Ly)
+  uint32_t mLy2;          // ceil(2^32 / (Ly/2))
   int T, Tp, A, B;        // temperatures, padded temperatures 8*ceil(T/8), labels,
                           // buffers (APT: A * Tp; ladder / pilot: chains)
   uint32_t ent;           // Philox entry id

@@ -116,6 +116,26 @@ def test_mixed_shapes_batch(pc, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("tpb", [64, 512])
+def test_elongated_and_thin_lattices_with_icm(pc, orc, tpb):
+    """Long axes (Lx = 32), axes of length 2 (double bonds) and, at 64
+    threads, several 2x2x2 fill blocks and chunks per thread."""
+    shapes = [(32, 4, 4), (2, 2, 2), (8, 2, 4), (4, 16, 2), (16, 16, 16)]
+    temps = [8, 4, 7, 12, 16]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 8, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, 2)
+    ctx = pc.Context(0, 23)
+    pc.pc_apt_load(ctx.h, dims, J, betas, 2, 40)
+    pc.pc_apt_set_block_threads(ctx.h, tpb)
+    apt = orc.Apt(dims, J, betas, 2, seed=23, entry0=40)
+    pc.pc_apt_run(ctx.h, 25, 1, True)
+    apt.run(25, threads=8)
+    _compare(pc, apt, ctx, b, [(i, i) for i in range(len(shapes))])
+    ctx.close()
+
+
 def test_resume_and_chunking(pc, orc):
     """140 attempts in one call (graph replay + remainder) == 60 + 80."""
     b = W.apt_single(L=6, n_temps=10)
