@@ -160,13 +160,15 @@ struct Cta {
 // colour-1 endpoint, so the colour-1 pass gives E = 3N - 2 * satisfied).
 template <bool UPDATE, bool ENERGY>
 __device__ __forceinline__ void colour_phase(const AptArgs &a, const Cta &k, const Shared &sh,
-                                             int c, uint32_t sweep) {
+                                             int c, uint32_t sweep, int gtot) {
   const int tid = threadIdx.x;
   const int q = tid / k.tpc, lt = tid - q * k.tpc;
   const int H = k.geo.H;
-  const int gbeg = q * k.gc;
-  int gcnt = k.Gc - gbeg;
-  if (gcnt > k.gc) gcnt = k.gc;
+  // groups [0, gtot) over the nch thread chunks
+  const int gper = gtot == k.Gc ? k.gc : (gtot + k.nch - 1) / k.nch;
+  const int gbeg = q * gper;
+  int gcnt = gtot - gbeg;
+  if (gcnt > gper) gcnt = gper;
   uint32_t acc[MAXGC][4];
 #pragma unroll
   for (int u = 0; u < MAXGC; ++u)
@@ -587,12 +589,54 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   }
   __syncthreads();
   PROF_MARK(8, pt);
-  // (F) energies after the moves
-  colour_phase<false, true>(a, k, sh, 1, 0u);
+  // (F) energies after the moves.  A Houdayer move keeps E_a + E_b of its
+  // pair (the cluster's outside neighbours agree in both replicas; a whole
+  // replica flip changes no energy at h = 0), so only label 0 is recounted
+  // and label 1 follows as E_b' = E_a + E_b - E_a'.
+  colour_phase<false, true>(a, k, sh, 1, 0u, Gh);
   __syncthreads();
-  finish_energies(k, sh);
+  for (int b = tid; b < 8 * Gh; b += nt) {
+    const int e0 = 3 * N - 2 * sh.Eacc[b];
+    sh.E[b + 8 * Gh] += sh.E[b] - e0;
+    sh.E[b] = e0;
+    sh.Eacc[b] = 0;
+  }
   __syncthreads();
   PROF_MARK(9, pt);
+}
+
+// Applies the swap masks of the last attempt (sh.swm) to the words
+// [kb, ke) of every group plane ([0, H): colour 0, [H, 2H): colour 1).
+__device__ void swap_words(const Cta &k, const Shared &sh, int kb, int ke) {
+  const int H = k.geo.H, G = k.Gc;
+  // groups touched by the swaps, and the groups g whose nibble 7 pairs with
+  // nibble 0 of g + 1
+  uint32_t touch = 0, cross = 0;
+#pragma unroll
+  for (int g = 0; g < 8; ++g) {
+    if (g < G && sh.swm[g]) touch |= 1u << g;
+    if (g + 1 < G && sh.swm[8 + g]) cross |= 1u << g;
+  }
+  for (int kk = kb + threadIdx.x; kk < ke; kk += blockDim.x) {
+    uint32_t *col = sh.S + kk;   // word (g, c, j) at col[g * 2H]
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      if ((touch >> g) & 1u) {
+        const uint32_t w = col[(size_t)g * 2 * H], m = sh.swm[g];
+        const uint32_t d = (w ^ (w >> 4)) & m;
+        col[(size_t)g * 2 * H] = w ^ (d | (d << 4));
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < 7; ++g) {
+      if ((cross >> g) & 1u) {
+        const uint32_t w0 = col[(size_t)g * 2 * H], w1 = col[(size_t)(g + 1) * 2 * H];
+        const uint32_t d = ((w0 >> 28) ^ w1) & 1u;
+        col[(size_t)g * 2 * H] = w0 ^ (d << 28);
+        col[(size_t)(g + 1) * 2 * H] = w1 ^ d;
+      }
+    }
+  }
 }
 
 // Replica exchange of attempt t (Sec. "Comparison with Adaptive Parallel
@@ -638,36 +682,10 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
   }
   __syncthreads();
   if (!sh.m32[5]) return;
-  const int H = k.geo.H, G = k.Gc;
-  // groups touched by this attempt's swaps, and the groups g whose nibble 7
-  // pairs with nibble 0 of g + 1
-  uint32_t touch = 0, cross = 0;
-#pragma unroll
-  for (int g = 0; g < 8; ++g) {
-    if (g < G && sh.swm[g]) touch |= 1u << g;
-    if (g + 1 < G && sh.swm[8 + g]) cross |= 1u << g;
-  }
-  touch |= cross | (cross << 1);
-  for (int kk = threadIdx.x; kk < 2 * H; kk += blockDim.x) {
-    uint32_t *col = sh.S + kk;   // word (g, c, j) at col[g * 2H]
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      if (((touch >> g) & 1u) && sh.swm[g]) {
-        const uint32_t w = col[(size_t)g * 2 * H], m = sh.swm[g];
-        const uint32_t d = (w ^ (w >> 4)) & m;
-        col[(size_t)g * 2 * H] = w ^ (d | (d << 4));
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < 7; ++g) {
-      if ((cross >> g) & 1u) {
-        const uint32_t w0 = col[(size_t)g * 2 * H], w1 = col[(size_t)(g + 1) * 2 * H];
-        const uint32_t d = ((w0 >> 28) ^ w1) & 1u;
-        col[(size_t)g * 2 * H] = w0 ^ (d << 28);
-        col[(size_t)(g + 1) * 2 * H] = w1 ^ d;
-      }
-    }
-  }
+  // colour 0 is rewritten by the next sweep without being read (a Gibbs
+  // update depends on the neighbours only), so only colour 1 moves now; the
+  // kernel applies the last attempt's swaps to colour 0 before it stores
+  swap_words(k, sh, k.geo.H, 2 * k.geo.H);
 }
 
 __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
@@ -759,11 +777,12 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     sh.m32[0] = a.best_buf[p];
     sh.m32[1] = 0;
     sh.m32[2] = sh.m32[3] = sh.m32[4] = 0;
+    sh.m32[5] = 0;
   }
   __syncthreads();
 
   if (a.mode == pc::APT_MODE_ENERGY) {
-    colour_phase<false, true>(a, k, sh, 1, 0u);
+    colour_phase<false, true>(a, k, sh, 1, 0u, k.Gc);
     __syncthreads();
     finish_energies(k, sh);
     __syncthreads();
@@ -773,10 +792,10 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
       const uint32_t t = (uint32_t)(t0 + it);
       for (int qq = 0; qq < a.spp; ++qq) {
         const uint32_t s = (uint32_t)(s0 + (int64_t)it * a.spp + qq);
-        colour_phase<true, false>(a, k, sh, 0, s);
+        colour_phase<true, false>(a, k, sh, 0, s, k.Gc);
         __syncthreads();
         PROF_MARK(0, pt);
-        colour_phase<true, true>(a, k, sh, 1, s);
+        colour_phase<true, true>(a, k, sh, 1, s, k.Gc);
         __syncthreads();
         finish_energies(k, sh);
         __syncthreads();
@@ -815,8 +834,13 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     }
   }
 
-  // every thread's last histogram / sum update lands before the write-back
+  // every thread's last histogram / sum update lands before the write-back,
+  // and colour 0 takes the last attempt's swaps
   __syncthreads();
+  if (a.mode == pc::APT_MODE_APT && a.n_iter > 0 && sh.m32[5]) {
+    swap_words(k, sh, 0, k.geo.H);
+    __syncthreads();
+  }
   // store state
   uint32_t *gSo = a.spins + P.spin_off + (size_t)k.g0 * N;
   for (int i = threadIdx.x; i < k.Gc * N; i += blockDim.x) gSo[i] = sh.S[i];

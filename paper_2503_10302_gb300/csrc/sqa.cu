@@ -33,6 +33,9 @@
 #ifndef PC_SQA_MINB
 #define PC_SQA_MINB 1
 #endif
+#ifndef PC_SQA_TPB
+#define PC_SQA_TPB 512
+#endif
 
 namespace {
 using namespace pcdev;
@@ -250,7 +253,7 @@ __device__ __forceinline__ bool wait_at_least(const int *flag, int want, uint64_
 // s1 == S computes the final slice energies, otherwise the state goes back.
 template <int NB>
 __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, int32_t *Eacc,
-                                            const uint8_t *jn, const SiteK &kh, bool hoist,
+                                            const uint8_t *jn, const SiteK (&kh)[2], bool hoist,
                                             int run, int s0, int s1) {
   const int N = a.N, P = a.P;
   const uint32_t ent = a.run0 + (uint32_t)run;
@@ -291,7 +294,8 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
       const uint32_t *Wo = W + (1 - c) * NB * N;
       uint32_t *Wc = W + c * NB * N;
       if (hoist) {
-        if (tid < N) update_site<NB>(a, Wo, Wc, tid, kh, c, (uint32_t)sw, boff, ent);
+        if (tid < N) update_site<NB>(a, Wo, Wc, tid, kh[0], c, (uint32_t)sw, boff, ent);
+        if (tid + nt < N) update_site<NB>(a, Wo, Wc, tid + nt, kh[1], c, (uint32_t)sw, boff, ent);
       } else {
         for (int s = tid; s < N; s += nt) {
           const SiteK k = site_consts(a, s, jn);
@@ -365,7 +369,7 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
 // stored its state.  Time-slicing the runs keeps every SM busy when the
 // number of runs is not a multiple of the number of SMs.
 template <int NB, bool PERSIST>
-__global__ void __launch_bounds__(512, PC_SQA_MINB) sqa_kernel(const pc::SqaArgs a) {
+__global__ void __launch_bounds__(PC_SQA_TPB, PC_SQA_MINB) sqa_kernel(const pc::SqaArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ int s_item;
   const int N = a.N, P = a.P;
@@ -376,9 +380,12 @@ __global__ void __launch_bounds__(512, PC_SQA_MINB) sqa_kernel(const pc::SqaArgs
   for (int i = tid; i < N; i += nt) jn[i] = a.jneg[i];
   __syncthreads();
   // one site per thread (N <= blockDim): its constants stay in registers
-  const bool hoist = PC_SQA_HOIST && N <= nt;
-  SiteK kh;
-  if (hoist && tid < N) kh = site_consts(a, tid, jn);
+  // up to two sites per thread (N <= 2 blockDim): their constants stay in
+  // registers
+  const bool hoist = PC_SQA_HOIST && N <= 2 * nt;
+  SiteK kh[2];
+  if (hoist && tid < N) kh[0] = site_consts(a, tid, jn);
+  if (hoist && tid + nt < N) kh[1] = site_consts(a, tid + nt, jn);
   if (!PERSIST) {
     anneal_span<NB>(a, W, Eacc, jn, kh, hoist, blockIdx.x, 0, a.S);
     return;
@@ -419,7 +426,7 @@ template <int NB>
 int launch_nb(const pc::SqaArgs &a, int R, cudaStream_t st) {
   const size_t smem = pc::sqa_smem_bytes(a.N, a.P);
   int tpb = ((a.N + 31) / 32) * 32;
-  if (tpb > 512) tpb = 512;
+  if (tpb > PC_SQA_TPB) tpb = PC_SQA_TPB;
   if (!a.state) {
     PC_CUDA_TRY(cudaFuncSetAttribute(sqa_kernel<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
