@@ -10,7 +10,8 @@ energies: 512 * 64 * 256 * 10^4 = 8.39e10 attempted spin updates.
 value      device time of the anneal kernel (inputs resident on the GPU)
 e2e        the one-call C-ABI path from host data to host energies
            (pc_sqa_anneal: tables, uploads, anneal, download)
-roofline   integer-issue bound of the anneal kernel
+roofline   integer-issue bound of the anneal kernel (14 algorithmic int ops per
+           update against SMs x 128 lanes x clock)
 cpu_baseline  the CPU oracle on this host's cores, on a bounded sample
 
 `--impl reference` times the CPU oracle (the only reference this paper has)
@@ -36,9 +37,27 @@ sys.path.insert(0, ROOT)
 METRIC = "spin flips/ns on 1 GB300; time to target ρ_E, learned-ladder vs plain APT"
 UNIT = "flips/ns"
 L, P, R, T, SWEEPS = 8, 64, 256, 0.05, 10000
-# algorithmic 32-bit integer operations per spin update ("roofline")
+# algorithmic 32-bit integer operations per spin update: 1/8 of a
+# Philox4x32-10 call (5), the packed field of 8 spins (2), the per-spin table
+# index, load, compare, tie check and set (6.5), the store (0.5)
 ALG_OPS_PER_FLIP = 14.0
+# DRAM bytes (read + write) of one full-size anneal launch, from an ncu
+# capture (profiles/sqa_kernel_L8_P64_R256.md), valid while the kernel
+# sources hash to TRAFFIC_SRC_SHA256; otherwise the bench reports null.
+TRAFFIC_BYTES = 1727232          # mean of 3 timed launches: 1.33, 1.66, 2.19 MB
+TRAFFIC_SRC_SHA256 = "4f1dd8f4eb41b717499833d32e80133264701ab7a0610dab00329242148a4289"
+TRAFFIC_SOURCES = ("paper_2503_10302_gb300/csrc/sqa.cu", "paper_2503_10302_gb300/csrc/device.cuh",
+                   "paper_2503_10302_gb300/csrc/internal.h")
 WORKLOAD = f"DT-SQA 3D +-J L={L} periodic, P={P} slices, R={R} runs, T={T}, Gamma 3.0->1e-3 over {SWEEPS} sweeps"
+
+
+def kernel_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -130,6 +149,28 @@ def cpu_oracle_sample(target_s: float = 12.0):
     desc = (f"{runs} runs x first {sweeps} of {SWEEPS} sweeps of the same anneal "
             f"({flips:.3g} spin updates), OpenMP over runs")
     return flips / (dt * 1e9), cores, desc
+
+
+def cpu_oracle_apt_sample(target_s: float = 6.0):
+    """The CPU oracle on APT + ICM over the 64 x L = 12 batch (32 temperatures
+    x 2 labels, geometric ladder): attempts of one sweep + ICM + swaps, all
+    host cores (OpenMP over instances).  Returns (flips/ns, description);
+    flips count sweep updates, as the GPU's APT throughput does."""
+    import oracle
+    from paper_2503_10302_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    b = W.apt_uniform_batch(64, 12, 32)
+    apt = oracle.Apt(b.dims, b.J, b.betas, 2, seed=1)
+    t0 = time.perf_counter()
+    apt.run(2, 1, True, cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(max(2, min(1000, 2 * target_s / dt)))
+    t0 = time.perf_counter()
+    apt.run(n, 1, True, cores)
+    dt = time.perf_counter() - t0
+    flips = b.spins_per_sweep() * n
+    return flips / (dt * 1e9), (f"APT+ICM 64 x L=12, 32 T x 2 labels: {n} attempts "
+                                f"({flips:.3g} sweep updates), OpenMP over instances")
 
 
 def run_reference(args, rank, world):
@@ -262,7 +303,8 @@ def main() -> int:
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "pc_sqa_anneal (host J, schedule -> host energies)"},
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
-                     "frac": achieved_tops / peak_tops, "traffic": None,
+                     "frac": achieved_tops / peak_tops,
+                     "traffic": TRAFFIC_BYTES if kernel_sources_sha256() == TRAFFIC_SRC_SHA256 else None,
                      "kernel": "sqa_kernel",
                      "peak_note": f"{sms} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (issue bound)",
                      "ops_per_flip": ALG_OPS_PER_FLIP},
@@ -272,6 +314,8 @@ def main() -> int:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc = cpu_oracle_sample()
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        va, desca = cpu_oracle_apt_sample()
+        line["cpu_baseline"]["apt_icm_64xL12"] = {"value": va, "unit": UNIT, "cores": cores, "sample": desca}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

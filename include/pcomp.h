@@ -82,8 +82,8 @@ int32_t pc_jperp_q(double gamma, int P, double T);
  * ---------------------------------------------------------------------- */
 /* Load a batch of n_inst problems: dims [n][3], J concatenated [sum N][3],
  * n_temps [n], betas concatenated (strictly increasing per problem),
- * n_labels in {1, 2} replicas per temperature (ICM needs 2), and
- * 8 * ceil(n_temps / 8) * n_labels <= 64.  Problem i uses entry id entry0 + i in its
+ * n_labels in {1, 2, 4} replicas per temperature (ICM needs 2 or 4; the
+ * paper uses 4), and 8 * ceil(n_temps / 8) * n_labels <= 64.  Problem i uses entry id entry0 + i in its
  * Philox counters.  Builds the p-bit and swap tables, draws the random
  * initial state (Algorithm S2 "Initialize all replicas to random states")
  * and resets counters, best energies and statistics.  Replaces any batch
@@ -92,7 +92,9 @@ int pc_apt_load(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
                 const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0);
 /* n_swaps swap attempts; each = sweeps_per_swap checkerboard sweeps of all
  * replicas, replica energies, best-energy update, (icm != 0) one ICMop per
- * temperature on its two labels and a second best update, then the
+ * pair of labels of every temperature (two labels: the pair (0, 1); four:
+ * two pairs of a random perfect matching, Algorithm S2 "randomly partition
+ * ICM replicas into pairs") and a second best update, then the
  * neighbour swaps of that attempt's parity.  Resumable: state, counters and
  * statistics carry over between calls.  Enqueued on the context stream. */
 int pc_apt_run(pc_ctx *ctx, int64_t n_swaps, int sweeps_per_swap, int icm);
@@ -159,6 +161,13 @@ int pc_sqa_run(pc_ctx *ctx, int R, uint32_t run0, int64_t *E_out, int8_t *spins_
 /* Device-buffer variant: E_dev [R][P] int32 and best_dev [R][2] int32
  * (minimum slice energy, its slice index; lowest index on ties). */
 int pc_sqa_run_dev(pc_ctx *ctx, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev);
+/* As pc_sqa_run_dev, plus the replica-direction correlation of each run's
+ * final state (Supplementary Fig. S17, C_r = (1/N) sum_i s_{i,0} s_{i,r}):
+ * corr_dev [R][P] int32 (device, caller-owned) receives N * C_r, i.e.
+ * sum over sites of s(site, slice 0) * s(site, slice r), r = 0..P-1 (r = 0
+ * gives N).  PC_EINVAL if corr_dev is NULL with R > 0. */
+int pc_sqa_run_corr_dev(pc_ctx *ctx, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev,
+                        int32_t *corr_dev);
 /* Self-test of the bounded waits of the time-sliced anneal schedule: runs
  * two runs from their second chunk, so that no wait for a previous chunk
  * can succeed; every wait gives up after 50 ms.  *status receives the

@@ -72,6 +72,8 @@ def lib():
         L.or_apt_sweeps.restype = ctypes.c_int64
         L.or_icm_apply.argtypes = [i32p, u8p, i8p, i8p, u64, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint32, ctypes.c_uint32, i64p]
+        L.or_icm_pairing.argtypes = [u64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+                                     i32p]
         L.or_adaptive_ladder.argtypes = [i32p, u8p, i8p, i8p, ctypes.c_uint32, u64, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_int, f64p, f64p, P(ctypes.c_int)]
@@ -220,6 +222,14 @@ def icm_apply(dims, sa, sb, seed=0, entry=0, r=0, t=0, p=0, periodic=None):
                                    ctypes.c_uint32(entry), ctypes.c_uint32(r), ctypes.c_uint32(t),
                                    ctypes.c_uint32(p), _ptr(size, ctypes.c_int64)), "icm_apply")
     return br, int(size[0]), a, b
+
+
+def icm_pairing(seed, entry, r, t, n_labels=4):
+    """Matching index and label pairs of the ICM at temperature r, attempt t."""
+    q = np.zeros(4, np.int32)
+    m = _check(lib().or_icm_pairing(ctypes.c_uint64(seed), ctypes.c_uint32(entry), ctypes.c_uint32(r),
+                                    ctypes.c_uint32(t), n_labels, _ptr(q, ctypes.c_int32)), "icm_pairing")
+    return m, [int(v) for v in q[: (4 if n_labels == 4 else 2)]]
 
 
 def adaptive_ladder(dims, J, entry=0, seed=0, beta0=0.5, alpha=1.25, n_chains=100, sweeps=10000,

@@ -122,7 +122,7 @@ int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *
                   const int8_t *J, const int8_t *h, const int32_t *n_temps,
                   const double *betas, int n_labels, uint64_t seed, uint32_t entry0) {
   *out = NULL;
-  if (n_inst < 1 || n_labels < 1 || n_labels > 2) return -1;
+  if (n_inst < 1 || !(n_labels == 1 || n_labels == 2 || n_labels == 4)) return -1;
   or_apt *a = (or_apt *)calloc(1, sizeof(or_apt));
   if (!a) return -2;
   a->n = n_inst;
@@ -282,6 +282,33 @@ int or_icm_apply(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, i
   return br;
 }
 
+/* Random partition of the ICM labels of temperature r into pairs at attempt
+ * t (Algorithm S2 "Randomly partition ICM replicas into pairs"; Methods: two
+ * randomly chosen pairs per temperature with 4 labels).  Two labels form
+ * the one pair (0, 1).  Four labels have three perfect matchings,
+ * m = floor(3 x2 / 2^32) with x = the Philox block of pair 0's ICM draw:
+ * m = 0: (0,1)(2,3); m = 1: (0,2)(1,3); m = 2: (0,3)(1,2). */
+static int icm_matching(uint64_t seed, uint32_t ent, uint32_t r, uint32_t t, int A, int pairs[4]) {
+  static const int M[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
+  int m = 0;
+  if (A == 4) {
+    uint32_t ctr[4] = {r, t, 0u, (ent << 8) | OR_TAG_ICM}, x[4];
+    or_philox(ctr, seed, x);
+    m = (int)(((uint64_t)x[2] * 3u) >> 32);
+  }
+  for (int q = 0; q < 4; ++q) pairs[q] = M[m][q];
+  return m;
+}
+
+int or_icm_pairing(uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, int n_labels,
+                   int32_t *pairs) {
+  if (!pairs || !(n_labels == 2 || n_labels == 4)) return -1;
+  int q[4];
+  int m = icm_matching(seed, entry, r, t, n_labels, q);
+  for (int i = 0; i < (n_labels == 4 ? 4 : 2); ++i) pairs[i] = q[i];
+  return m;
+}
+
 /* Replica exchange at attempt t (0-based): even t pairs (0,1),(2,3),...
  * (the paper's odd-numbered attempt), odd t pairs (1,2),(3,4),...; within
  * each pair every label decides on its own with
@@ -314,7 +341,7 @@ static void swap_step(apt_entry *e, uint64_t seed, uint32_t t) {
 int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int threads) {
   if (!a || n_swaps < 0 || sweeps_per_swap < 1) return -1;
   for (int i = 0; i < a->n; ++i) {
-    if (icm && a->e[i].A != 2) return -1;
+    if (icm && a->e[i].A != 2 && a->e[i].A != 4) return -1;
     if (icm && a->e[i].h) return -1; /* whole-replica flip needs h = 0 */
   }
   int64_t s0 = a->sweeps_done, t0 = a->swaps_done;
@@ -334,8 +361,12 @@ int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int thr
         e->E[b] = or_energy_lat(&e->L, e->J, e->h, e->spin + (size_t)b * e->L.N);
       best_update(e, s);
       if (icm) {
-        for (int r = 0; r < e->T; ++r)
-          icm_op(e, a->seed, 2 * r, 2 * r + 1, (uint32_t)r, t, 0u);
+        for (int r = 0; r < e->T; ++r) {
+          int q[4];
+          icm_matching(a->seed, e->ent, (uint32_t)r, t, e->A, q);
+          for (int p = 0; p < e->A / 2; ++p)
+            icm_op(e, a->seed, r * e->A + q[2 * p], r * e->A + q[2 * p + 1], (uint32_t)r, t, (uint32_t)p);
+        }
         best_update(e, s);
       }
       swap_step(e, a->seed, t);

@@ -84,6 +84,11 @@ int64_t or_apt_sweeps(const or_apt *a);
 /* One ICMop on two configurations (ctr = (r, t, p, (entry<<8)|TAG_ICM));
    returns 0 no overlap mismatch, 1 cluster flipped in both, 2 one whole
    replica flipped; *cluster_size = size of the grown cluster. */
+/* Pairs of ICM labels at temperature r, attempt t (Algorithm S2 "Randomly
+ * partition ICM replicas into pairs"): pairs[0..1], pairs[2..3] (4 labels)
+ * or pairs[0..1] = (0, 1) (2 labels).  Returns the matching index 0..2. */
+int or_icm_pairing(uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, int n_labels,
+                   int32_t *pairs);
 int or_icm_apply(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb,
                  uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p,
                  int64_t *cluster_size);

@@ -236,7 +236,8 @@ int pc_sqa_get_table(pc_ctx *c, int sweep, uint32_t *out, int32_t *jq) {
 }
 
 static int sqa_enqueue(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev,
-                       int8_t *spins_dev, int first_chunk = 0, uint64_t wait_ns = 10000000000ull) {
+                       int8_t *spins_dev, int first_chunk = 0, uint64_t wait_ns = 10000000000ull,
+                       int32_t *corr_dev = nullptr) {
   const SqaState &q = c->sqa;
   SqaArgs a;
   a.Lx = q.lat.L[0];
@@ -256,6 +257,7 @@ static int sqa_enqueue(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t 
   a.E = E_dev;
   a.best = best_dev;
   a.spins = spins_dev;
+  a.corr = corr_dev;
   a.state = nullptr;
   a.done = a.queue = a.err = nullptr;
   a.R = R;
@@ -304,6 +306,16 @@ int pc_sqa_run_dev(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *bes
   if (R == 0) return PC_OK;
   PC_CUDA_TRY(cudaSetDevice(c->device));
   return sqa_enqueue(c, R, run0, E_dev, best_dev, nullptr);
+}
+
+int pc_sqa_run_corr_dev(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev,
+                        int32_t *corr_dev) {
+  if (!c || !c->sqa.ready) return fail(PC_ESTATE, "pc_sqa_setup first");
+  if (R < 0 || (R > 0 && (!E_dev || !corr_dev))) return fail(PC_EINVAL, "bad arguments");
+  if ((uint64_t)run0 + (uint64_t)R > (1ull << 24)) return fail(PC_EINVAL, "run ids must be < 2^24");
+  if (R == 0) return PC_OK;
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  return sqa_enqueue(c, R, run0, E_dev, best_dev, nullptr, 0, 10000000000ull, corr_dev);
 }
 
 int pc_sqa_run(pc_ctx *c, int R, uint32_t run0, int64_t *E_out, int8_t *spins_out) {

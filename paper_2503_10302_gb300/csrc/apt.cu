@@ -143,7 +143,8 @@ struct Shared {
   int32_t *inm;      // [64] per pair: mismatch count
   int32_t *isz;      // [64] per pair: cluster size
   uint32_t *imask;   // [3][8] per half-group: cluster-flip, whole-flip label 0, label 1
-  uint32_t *swm;     // [8] per group: in-group swap nibble mask; [8] cross-group flags
+  uint32_t *swm;     // [8] per group: in-group swap nibble mask; [8] cross-group flags;
+                     // [6] ICM matching nibble masks (4 labels)
 };
 
 struct Cta {
@@ -326,34 +327,55 @@ __device__ __forceinline__ uint32_t byte_to_nib(uint32_t b) {
   return (t | (t << 3)) & 0x11111111u;
 }
 
-// ICMop of Algorithm S2 for every temperature at once.  Pair r = 8h + i is
-// nibble i of groups h (label 0) and h + Gh (label 1), so the overlap of
-// eight pairs is one XOR; compressed, X[site] has bit r set where the two
-// replicas of temperature r disagree.  The seed of pair r is the k-th site
-// (canonical order c*H + j) with bit r set, k = floor(x0 n_minus / 2^32);
-// its cluster grows by an in-place flood fill V <- V | (X & OR_nbr V),
-// alternating colours, until no cluster changes.  Clusters larger than N/2
-// flip one whole replica (x1 bit 0: label 0 or 1), smaller ones flip in both
-// replicas; then all energies are recomputed.
+// ICMop of Algorithm S2 for every temperature at once.  With A labels per
+// temperature (2 or 4) the labels of temperature r = 8h + i sit in nibble i
+// of groups l*Gl + h, and pair p of the temperature's random matching owns
+// bit 8 (h A/2 + p) + i of the per-site overlap word X, so the overlaps of
+// eight pairs come from one XOR (two labels) or three masked XORs (four).
+// The seed of a pair is the k-th site (canonical order c*H + j) with its
+// bit set, k = floor(x0 n_minus / 2^32); its cluster grows by a flood fill
+// V <- V | (X & OR_nbr V) until no cluster changes.  Clusters larger than
+// N/2 flip one whole replica (x1 bit 0: the pair's first or second label),
+// smaller ones flip in both replicas; then the energies are updated.
 __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32_t t) {
   long long pt = clock64();
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int N = k.geo.N, H = k.geo.H, Gh = k.Gc >> 1;
+  const int N = k.geo.N, H = k.geo.H;
+  // A labels per temperature form A/2 pairs; label l's groups are
+  // l*Gl .. l*Gl + Gl - 1.  Pair p of temperature r = 8h + i owns bit
+  // 8 (h P + p) + i of the per-site overlap / cluster words.
+  const int A = k.A, P = A >> 1, Gl = k.Gc / A, nbits = 8 * Gl * P;
   const uint32_t *S = sh.S;
-  uint32_t *V = sh.V;          // [2][H] cluster bits (bit r: pair r)
+  uint32_t *V = sh.V;          // [2][H] cluster bits (one bit per pair)
   uint32_t *X = sh.V + N;      // [2][H] overlap bits
-  if (tid < 8 * Gh) {
-    const int r = tid;
+  int *match = sh.ibit + 32;   // [32] matching of the labels of each temperature
+  if (tid < nbits) {
+    const int pb = tid, beta = pb >> 3, h = beta / P, p = beta - h * P, r = 8 * h + (pb & 7);
     if (r < k.T) {
-      const uint4 x = philox((uint32_t)r, t, 0u, (k.ent << 8) | TAG_ICM, a.k0, a.k1);
-      sh.ikx[r] = x.x;
-      sh.ibit[r] = (int)(x.y & 1u);
+      const uint4 x = philox((uint32_t)r, t, (uint32_t)p, (k.ent << 8) | TAG_ICM, a.k0, a.k1);
+      sh.ikx[pb] = x.x;
+      sh.ibit[pb] = (int)(x.y & 1u);
+      // Algorithm S2 "randomly partition ICM replicas into pairs": with four
+      // labels, one of the three perfect matchings, floor(3 x2 / 2^32) of
+      // pair 0's draw; two labels always pair (0, 1)
+      if (p == 0) match[r] = A == 4 ? (int)(((uint64_t)x.z * 3u) >> 32) : 0;
     }
   }
   if (tid < 24) sh.imask[tid] = 0;
   if (tid < 64) {
     sh.isz[tid] = 0;
     sh.inm[tid] = 0;
+  }
+  __syncthreads();
+  if (A == 4 && tid < 3 * Gl) {
+    // nibble masks of the temperatures of group h that use matching m
+    const int h = tid / 3, m = tid - 3 * h;
+    uint32_t mk = 0;
+    for (int i = 0; i < 8; ++i) {
+      const int r = 8 * h + i;
+      if (r < k.T && match[r] == m) mk |= 0xFu << (4 * i);
+    }
+    sh.swm[16 + tid] = mk;
   }
   __syncthreads();
   // (A) overlaps.  Warp w takes chunks of 32 sites in canonical order; the
@@ -367,11 +389,27 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     uint32_t xb = 0;
     if (kk < N) {
       const int c = kk >= H ? 1 : 0, j = kk - c * H;
+      if (A == 2) {
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        if (h >= Gh) break;
-        const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gh) + c) * H + j];
-        xb |= nib_to_byte(x) << (8 * h);
+        for (int h = 0; h < 4; ++h) {
+          if (h >= Gl) break;
+          const uint32_t x = S[(2 * h + c) * H + j] ^ S[(2 * (h + Gl) + c) * H + j];
+          xb |= nib_to_byte(x) << (8 * h);
+        }
+      } else {
+        // the two labels of pair p depend on each temperature's matching:
+        // select nibbles by the matching masks
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h >= Gl) break;
+          uint32_t w[4];
+#pragma unroll
+          for (int l = 0; l < 4; ++l) w[l] = S[(2 * (l * Gl + h) + c) * H + j];
+          const uint32_t m0 = sh.swm[16 + 3 * h], m1 = sh.swm[17 + 3 * h], m2 = sh.swm[18 + 3 * h];
+          const uint32_t x0 = ((w[0] ^ w[1]) & m0) | ((w[0] ^ w[2]) & m1) | ((w[0] ^ w[3]) & m2);
+          const uint32_t x1 = ((w[2] ^ w[3]) & m0) | ((w[1] ^ w[3]) & m1) | ((w[1] ^ w[2]) & m2);
+          xb |= (nib_to_byte(x0) << (16 * h)) | (nib_to_byte(x1) << (16 * h + 8));
+        }
       }
       X[kk] = xb;
       V[kk] = 0u;
@@ -380,13 +418,14 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     Xt[ch * 32 + lane] = col;
     nmis += __popc(col);
   }
-  if (lane < k.T && nmis) atomicAdd(&sh.inm[lane], (int)nmis);
+  if (lane < nbits && nmis) atomicAdd(&sh.inm[lane], (int)nmis);
   __syncthreads();
   PROF_MARK(4, pt);
   // seeds: warp w finds the k-th mismatch of pairs w, w + nw, ...: chunk
   // counts by popcount, a warp scan over chunks, then the set bit inside
   // the chunk
-  for (int r = warp; r < k.T; r += nw) {
+  for (int r = warp; r < nbits; r += nw) {   // r: pair bit
+    if (8 * ((r >> 3) / P) + (r & 7) >= k.T) continue;
     const int nm = sh.inm[r];
     if (nm == 0) continue;
     const int kth = (int)(((uint64_t)sh.ikx[r] * (uint64_t)nm) >> 32);
@@ -555,22 +594,29 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
       const int kk = ch * 32 + lane;
       sz += __popc(warp_transpose32(kk < N ? V[kk] : 0u));
     }
-    if (lane < k.T && sz) atomicAdd(&sh.isz[lane], (int)sz);
+    if (lane < nbits && sz) atomicAdd(&sh.isz[lane], (int)sz);
   }
   __syncthreads();
-  // (D) decisions
-  if (tid < k.T) {
-    const int r = tid, h = r >> 3, i = r & 7;
-    const int size = sh.isz[r];
-    const uint32_t bit = 1u << (4 * i);
-    if (sh.inm[r] == 0) {
-      atomicAdd(&sh.m32[2], 1);
-    } else if (2 * size > N) {
-      atomicOr(&sh.imask[8 + 8 * sh.ibit[r] + h], bit);   // whole replica of label ibit
-      atomicAdd(&sh.m32[4], 1);
-    } else {
-      atomicOr(&sh.imask[h], bit);                          // cluster, both replicas
-      atomicAdd(&sh.m32[3], 1);
+  // (D) decisions.  imask[(g P + p)] (g = l Gl + h): nibbles of label l's
+  // group h flipped by pair p's cluster; imask[16 + g]: whole-replica flips.
+  if (tid < nbits) {
+    const int pb = tid, beta = pb >> 3, h = beta / P, p = beta - h * P, i = pb & 7, r = 8 * h + i;
+    if (r < k.T) {
+      const int m = match[r];
+      const int la = p == 0 ? 0 : (m == 0 ? 2 : 1);
+      const int lb = p == 0 ? m + 1 : (m == 2 ? 2 : 3);
+      const int size = sh.isz[pb];
+      const uint32_t bit = 1u << (4 * i);
+      if (sh.inm[pb] == 0) {
+        atomicAdd(&sh.m32[2], 1);
+      } else if (2 * size > N) {
+        atomicOr(&sh.imask[16 + (sh.ibit[pb] ? lb : la) * Gl + h], bit);   // one whole replica
+        atomicAdd(&sh.m32[4], 1);
+      } else {
+        atomicOr(&sh.imask[(la * Gl + h) * P + p], bit);                  // cluster, both replicas
+        atomicOr(&sh.imask[(lb * Gl + h) * P + p], bit);
+        atomicAdd(&sh.m32[3], 1);
+      }
     }
   }
   __syncthreads();
@@ -580,11 +626,13 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     const int c = kk >= H ? 1 : 0, j = kk - c * H;
     const uint32_t v = V[kk];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      if (h >= Gh) break;
-      const uint32_t vv = byte_to_nib((v >> (8 * h)) & 0xFFu) & sh.imask[h];
-      sh.S[(2 * h + c) * H + j] ^= vv | sh.imask[8 + h];
-      sh.S[(2 * (h + Gh) + c) * H + j] ^= vv | sh.imask[16 + h];
+    for (int g = 0; g < 8; ++g) {
+      if (g >= k.Gc) break;
+      const int h = g % Gl;
+      uint32_t f = sh.imask[16 + g];
+      for (int p = 0; p < P; ++p)
+        f |= byte_to_nib((v >> (8 * (h * P + p))) & 0xFFu) & sh.imask[g * P + p];
+      if (f) sh.S[(2 * g + c) * H + j] ^= f;
     }
   }
   __syncthreads();
@@ -593,13 +641,20 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // pair (the cluster's outside neighbours agree in both replicas; a whole
   // replica flip changes no energy at h = 0), so only label 0 is recounted
   // and label 1 follows as E_b' = E_a + E_b - E_a'.
-  colour_phase<false, true>(a, k, sh, 1, 0u, Gh);
-  __syncthreads();
-  for (int b = tid; b < 8 * Gh; b += nt) {
-    const int e0 = 3 * N - 2 * sh.Eacc[b];
-    sh.E[b + 8 * Gh] += sh.E[b] - e0;
-    sh.E[b] = e0;
-    sh.Eacc[b] = 0;
+  if (A == 2) {
+    colour_phase<false, true>(a, k, sh, 1, 0u, Gl);
+    __syncthreads();
+    for (int b = tid; b < 8 * Gl; b += nt) {
+      const int e0 = 3 * N - 2 * sh.Eacc[b];
+      sh.E[b + 8 * Gl] += sh.E[b] - e0;
+      sh.E[b] = e0;
+      sh.Eacc[b] = 0;
+    }
+  } else {
+    // the pairs change with the temperature: recount every label
+    colour_phase<false, true>(a, k, sh, 1, 0u, k.Gc);
+    __syncthreads();
+    finish_energies(k, sh);
   }
   __syncthreads();
   PROF_MARK(9, pt);
@@ -740,7 +795,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.inm = reinterpret_cast<int32_t *>(cur);      cur += 64;
   sh.isz = reinterpret_cast<int32_t *>(cur);      cur += 64;
   sh.imask = cur;                                 cur += 24;
-  sh.swm = cur;                                   cur += 16;
+  sh.swm = cur;                                   cur += 24;
   sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 : 0;   // V, X, Xt
   sh.jn = reinterpret_cast<uint8_t *>(cur);
 
@@ -906,7 +961,7 @@ namespace pc {
 size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins) {
   const size_t G8 = 8 * (size_t)Gc;
   size_t words = (size_t)Gc * N + 16 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
-  words += 4 * 64 + 24 + 16;
+  words += 4 * 64 + 24 + 24;
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
   if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31;   // V, X and the transposed X
   return words * 4 + (size_t)N + 16;

@@ -254,13 +254,25 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return (int64_t)bt.prob[(size_t)x].N * bt.prob[(size_t)x].B > (int64_t)bt.prob[(size_t)y].N * bt.prob[(size_t)y].B;
   });
+  // APT keeps a problem in one CTA (swaps and ICM couple all its groups).
+  // Ladder and pilot chains are independent, so their groups spread over
+  // about one CTA per SM when the batch is small.
+  int gmax = kMaxGcCta;
+  if (mode == APT_MODE_LADDER || mode == APT_MODE_PILOT) {
+    int64_t total = 0;
+    for (int i : order) total += bt.G[(size_t)i];
+    const int sms = c->sms > 0 ? c->sms : 1;
+    gmax = (int)std::min<int64_t>(kMaxGcCta, std::max<int64_t>(1, (total + sms - 1) / sms));
+  }
   std::vector<int> cp, cg0, cgc, cnch;
   size_t smem = 0;
   for (int i : order) {
     const AptProbDev &P = bt.prob[(size_t)i];
     const int G = bt.G[(size_t)i];
-    for (int g0 = 0; g0 < G; g0 += kMaxGcCta) {
-      const int gc = std::min(kMaxGcCta, G - g0);
+    // equal chunks of at most gmax groups
+    const int nchunk = (G + gmax - 1) / gmax, per = (G + nchunk - 1) / nchunk;
+    for (int g0 = 0; g0 < G; g0 += per) {
+      const int gc = std::min(per, G - g0);
       cp.push_back(i);
       cg0.push_back(g0);
       cgc.push_back(gc);
@@ -409,7 +421,8 @@ int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, con
                 const double *betas, int n_labels, uint32_t entry0) {
   if (!c || !dims || !J || !n_temps || !betas) return fail(PC_EINVAL, "NULL argument");
   if (n_inst < 1) return fail(PC_EINVAL, "n_inst must be >= 1");
-  if (n_labels < 1 || n_labels > 2) return fail(PC_EINVAL, "n_labels must be 1 or 2");
+  if (!(n_labels == 1 || n_labels == 2 || n_labels == 4))
+    return fail(PC_EINVAL, "n_labels must be 1, 2 or 4");
   if ((uint64_t)entry0 + (uint64_t)n_inst > (1ull << 24)) return fail(PC_EINVAL, "entry ids must be < 2^24");
   PC_CUDA_TRY(cudaSetDevice(c->device));
   std::vector<ProbSpec> specs((size_t)n_inst);
@@ -452,7 +465,7 @@ int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, con
   im->specs = specs;
   int rc = build_batch(c, im->bt, specs, 0);
   if (rc) return rc;
-  if ((rc = schedule(c, im->bt, {}, APT_MODE_APT, n_labels == 2, 0))) return rc;
+  if ((rc = schedule(c, im->bt, {}, APT_MODE_APT, n_labels >= 2, 0))) return rc;
   AptArgs a = base_args(c, im->bt);
   a.tag_init = 1;   // TAG_APT_INIT
   if ((rc = apt_init_launch(a, n_inst, max_words(im->bt), c->stream))) return rc;
@@ -484,7 +497,7 @@ int pc_apt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (n_swaps < 0 || sweeps_per_swap < 1) return fail(PC_EINVAL, "n_swaps >= 0, sweeps_per_swap >= 1");
   AptImpl *im = apt_impl(c);
-  if (icm && im->A != 2) return fail(PC_EINVAL, "ICM needs two labels per temperature");
+  if (icm && im->A < 2) return fail(PC_EINVAL, "ICM needs two or four labels per temperature");
   if (c->apt.sweeps + n_swaps * sweeps_per_swap > 0xFFFFFFFFll || c->apt.swaps + n_swaps > 0xFFFFFFFFll)
     return fail(PC_EINVAL, "sweep counter would exceed 2^32");
   PC_CUDA_TRY(cudaSetDevice(c->device));
@@ -535,7 +548,7 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (trial_swaps < 1) return fail(PC_EINVAL, "trial_swaps must be >= 1");
   AptImpl *im = apt_impl(c);
-  if (icm && im->A != 2) return fail(PC_EINVAL, "ICM needs two labels per temperature");
+  if (icm && im->A < 2) return fail(PC_EINVAL, "ICM needs two or four labels per temperature");
   PC_CUDA_TRY(cudaSetDevice(c->device));
   const int cands[3] = {256, 384, 512};
   int best = im->bt.tpb;
@@ -549,7 +562,7 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) {
     Batch tmp;
     tmp.tpb = tpb;
     if ((rc = build_batch(c, tmp, im->specs, 0))) break;
-    if ((rc = schedule(c, tmp, {}, APT_MODE_APT, im->A == 2, 0))) {
+    if ((rc = schedule(c, tmp, {}, APT_MODE_APT, im->A >= 2, 0))) {
       rc = PC_OK;   // does not fit with this shape: skip it
       continue;
     }
@@ -579,7 +592,7 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) {
   if (rc) return rc;
   if (best != im->bt.tpb) {
     im->bt.tpb = best;
-    if ((rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A == 2, 0))) return rc;
+    if ((rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0))) return rc;
     if (im->exec) cudaGraphExecDestroy(im->exec);
     if (im->graph) cudaGraphDestroy(im->graph);
     im->exec = nullptr;
@@ -597,10 +610,10 @@ int pc_apt_set_block_threads(pc_ctx *c, int tpb) {
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   const int old = im->bt.tpb;
   im->bt.tpb = tpb;
-  int rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A == 2, 0);
+  int rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0);
   if (rc) {
     im->bt.tpb = old;
-    schedule(c, im->bt, {}, APT_MODE_APT, im->A == 2, 0);
+    schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0);
     return rc;
   }
   if (im->exec) cudaGraphExecDestroy(im->exec);

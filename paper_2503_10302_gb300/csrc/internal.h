@@ -42,6 +42,7 @@ struct SqaArgs {
   int32_t *E;              // [R][P]
   int32_t *best;           // [R][2] (nullable)
   int8_t *spins;           // [R][P][N] (nullable)
+  int32_t *corr;           // [R][P] sum_s s(s,0) s(s,k) (nullable)
   // persistent time-sliced schedule (state == nullptr: one CTA per run)
   uint32_t *state;         // [R][2][NB][N] run states between chunks
   int *done, *queue, *err; // [R] chunks done per run; work counter; error flag

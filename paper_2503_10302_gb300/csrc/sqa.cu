@@ -253,7 +253,7 @@ __device__ __forceinline__ bool wait_at_least(const int *flag, int want, uint64_
 // s1 == S computes the final slice energies, otherwise the state goes back.
 template <int NB>
 __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, int32_t *Eacc,
-                                            const uint8_t *jn, const SiteK (&kh)[2], bool hoist,
+                                            const uint8_t *jn, const SiteK &kh, bool hoist,
                                             int run, int s0, int s1) {
   const int N = a.N, P = a.P;
   const uint32_t ent = a.run0 + (uint32_t)run;
@@ -294,8 +294,7 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
       const uint32_t *Wo = W + (1 - c) * NB * N;
       uint32_t *Wc = W + c * NB * N;
       if (hoist) {
-        if (tid < N) update_site<NB>(a, Wo, Wc, tid, kh[0], c, (uint32_t)sw, boff, ent);
-        if (tid + nt < N) update_site<NB>(a, Wo, Wc, tid + nt, kh[1], c, (uint32_t)sw, boff, ent);
+        if (tid < N) update_site<NB>(a, Wo, Wc, tid, kh, c, (uint32_t)sw, boff, ent);
       } else {
         for (int s = tid; s < N; s += nt) {
           const SiteK k = site_consts(a, s, jn);
@@ -347,6 +346,32 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
     a.best[2 * run] = Eacc[kb];
     a.best[2 * run + 1] = kb;
   }
+  if (a.corr) {
+    // replica-direction correlation (Fig. S17): sum over sites of
+    // s(s,0) s(s,k) = 2 #agree - N.  Slice k of site s is nibble (k>>1)&7 of
+    // word W[(k&1) ^ q(s)][s][k>>4].  Eacc is reused once the best slice
+    // has been read from it.
+    __syncthreads();
+    for (int k = tid; k < P; k += nt) Eacc[k] = 0;
+    __syncthreads();
+    for (int s = tid; s < N; s += nt) {
+      const int r = (int)fdiv((uint32_t)s, a.mLx), x = s - r * a.Lx;
+      const int z = (int)fdiv((uint32_t)r, a.mLy), y = r - z * a.Ly;
+      const int q = (x + y + z) & 1;
+      const uint32_t s0 = W[(size_t)q * NB * N + (size_t)s * NB] & 1u;   // slice 0
+      const uint32_t flip = s0 ? 0u : 0x11111111u;
+      for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < NB; ++b) {
+          const uint32_t agree = (W[(size_t)c * NB * N + (size_t)s * NB + b] ^ flip) & 0x11111111u;
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if ((agree >> (4 * i)) & 1u) atomicAdd(&Eacc[2 * (8 * b + i) + (c ^ q)], 1);
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < P; k += nt) a.corr[(size_t)run * P + k] = 2 * Eacc[k] - N;
+    __syncthreads();
+  }
   if (a.spins) {
     for (int idx = tid; idx < 2 * NB * N; idx += nt) {
       const int b = idx % NB, cs = idx / NB, s = cs % N, c = cs / N;   // W[c][s][b]
@@ -380,12 +405,10 @@ __global__ void __launch_bounds__(PC_SQA_TPB, PC_SQA_MINB) sqa_kernel(const pc::
   for (int i = tid; i < N; i += nt) jn[i] = a.jneg[i];
   __syncthreads();
   // one site per thread (N <= blockDim): its constants stay in registers
-  // up to two sites per thread (N <= 2 blockDim): their constants stay in
-  // registers
-  const bool hoist = PC_SQA_HOIST && N <= 2 * nt;
-  SiteK kh[2];
-  if (hoist && tid < N) kh[0] = site_consts(a, tid, jn);
-  if (hoist && tid + nt < N) kh[1] = site_consts(a, tid + nt, jn);
+  // one site per thread (N <= blockDim): its constants stay in registers
+  const bool hoist = PC_SQA_HOIST && N <= nt;
+  SiteK kh;
+  if (hoist && tid < N) kh = site_consts(a, tid, jn);
   if (!PERSIST) {
     anneal_span<NB>(a, W, Eacc, jn, kh, hoist, blockIdx.x, 0, a.S);
     return;
@@ -601,6 +624,7 @@ extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, co
   a.E = E_dev;
   a.best = best_dev;
   a.spins = nullptr;
+  a.corr = nullptr;
   a.state = nullptr;   // one CTA per run: no state scratch
   a.done = a.queue = a.err = nullptr;
   a.R = R;

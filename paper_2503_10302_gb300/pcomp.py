@@ -59,6 +59,7 @@ SIGNATURES = {
     "pc_sqa_get_table": (c_int, [c_vp, c_int, c_u32p, ctypes.POINTER(ctypes.c_int32)]),
     "pc_sqa_run": (c_int, [c_vp, c_int, c_u32, c_i64p, c_i8p]),
     "pc_sqa_run_dev": (c_int, [c_vp, c_int, c_u32, c_vp, c_vp]),
+    "pc_sqa_run_corr_dev": (c_int, [c_vp, c_int, c_u32, c_vp, c_vp, c_vp]),
     "pc_sqa_selftest_wait": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "pc_sqa_anneal": (c_int, [c_vp, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p, c_int, c_u32, c_i64p]),
     "pc_sqa_anneal_noalloc": (c_int, [c_int, c_vp, c_u64, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p,
@@ -203,6 +204,13 @@ def pc_sqa_run(ctx, R: int, run0: int, P: int, N: int, want_spins: bool = False)
 
 def pc_sqa_run_dev(ctx, R: int, run0: int, E_dev_ptr: int, best_dev_ptr: int = 0) -> None:
     _call("pc_sqa_run_dev", ctx, R, c_u32(run0), c_vp(E_dev_ptr), c_vp(best_dev_ptr or None))
+
+
+def pc_sqa_run_corr_dev(ctx, R: int, run0: int, E_dev_ptr: int, corr_dev_ptr: int,
+                        best_dev_ptr: int = 0) -> None:
+    """pc_sqa_run_dev plus corr [R][P] int32 = sum_s s(s,0) s(s,k) (Fig. S17's N C_k)."""
+    _call("pc_sqa_run_corr_dev", ctx, R, c_u32(run0), c_vp(E_dev_ptr), c_vp(best_dev_ptr or None),
+          c_vp(corr_dev_ptr))
 
 
 def pc_sqa_selftest_wait(ctx) -> int:

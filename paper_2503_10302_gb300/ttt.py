@@ -158,8 +158,23 @@ def c2_residual_vs_R(L=8, P=64, R=256, T=0.05, sweeps=10000, best_runs=10, best_
     pcomp.pc_sqa_setup(ctx.h, wl.dims, wl.J, P, T, wl.gamma)
     import torch
     E_dev = torch.empty((R, P), dtype=torch.int32, device="cuda")
+    C_dev = torch.empty((R, P), dtype=torch.int32, device="cuda")
     dt = timer.time(lambda: pcomp.pc_sqa_run_dev(ctx.h, R, 0, E_dev.data_ptr()))
     E = E_dev.cpu().numpy().astype(np.int64)
+    # replica-direction correlation of the final states (Fig. S17), same runs
+    pcomp.pc_sqa_run_corr_dev(ctx.h, R, 0, E_dev.data_ptr(), C_dev.data_ptr())
+    pcomp.pc_synchronize(ctx.h)
+    C_r = C_dev.cpu().numpy().astype(np.float64).mean(axis=0) / N
+    # C_r at the end of shorter anneals (the same schedule compressed to t_a
+    # sweeps), as in Fig. S17's dependence on the annealing time
+    C_ta = {}
+    for ta in (10, 100, 1000):
+        g = W.linear_gamma_schedule(ta)
+        pcomp.pc_sqa_setup(ctx.h, wl.dims, wl.J, P, T, g)
+        pcomp.pc_sqa_run_corr_dev(ctx.h, R, 0, E_dev.data_ptr(), C_dev.data_ptr())
+        pcomp.pc_synchronize(ctx.h)
+        c = C_dev.cpu().numpy().astype(np.float64).mean(axis=0) / N
+        C_ta[str(ta)] = [float(x) for x in c[: P // 2 + 1]]
     ctx.close()
     ladder, _ = adaptive_ladders(np.array([[L] * 3], np.int32), [wl.J])
     batch = W.AptBatch(np.array([[L] * 3], np.int32), [wl.J], [pcomp.pc_resample_ladder(ladder[0], 32)], 2)
@@ -170,7 +185,10 @@ def c2_residual_vs_R(L=8, P=64, R=256, T=0.05, sweeps=10000, best_runs=10, best_
     mu, sd = float(rho_run.mean()), float(rho_run.std(ddof=1))
     out = {"L": L, "P": P, "R": R, "T": T, "sweeps": sweeps, "anneal_seconds": dt,
            "flips_per_ns": N * P * R * sweeps / dt / 1e9, "e_best": e_best,
-           "rho_single_run": {"mean": mu, "std": sd}, "best_of_R": {}}
+           "rho_single_run": {"mean": mu, "std": sd}, "best_of_R": {},
+           "C_r_mean_over_runs": [float(x) for x in C_r[: P // 2 + 1]],
+           "C_r_by_anneal_sweeps": C_ta,
+           "C_r_length_1_over_e": int(np.argmax(C_r[: P // 2 + 1] < np.exp(-1.0))) or None}
     for r in Rs:
         g = rho_run[: (R // r) * r].reshape(-1, r).min(axis=1)
         pred = mu + np.sqrt(2.0) * sd * float(erfcinv(2.0 ** ((r - 1) / r)))

@@ -86,7 +86,8 @@ def test_c1_full_run_bit_exact(pc, orc):
     ctx.close()
 
 
-@pytest.mark.parametrize("spp,icm,labels", [(1, False, 2), (3, True, 2), (2, False, 1)])
+@pytest.mark.parametrize("spp,icm,labels", [(1, False, 2), (3, True, 2), (2, False, 1), (1, True, 4),
+                                            (2, False, 4)])
 def test_apt_variants(pc, orc, spp, icm, labels):
     b = W.apt_uniform_batch(2, 6, 7, n_labels=labels)
     ctx = pc.Context(0, 3)
@@ -132,6 +133,25 @@ def test_elongated_and_thin_lattices_with_icm(pc, orc, tpb):
     apt = orc.Apt(dims, J, betas, 2, seed=23, entry0=40)
     pc.pc_apt_run(ctx.h, 25, 1, True)
     apt.run(25, threads=8)
+    _compare(pc, apt, ctx, b, [(i, i) for i in range(len(shapes))])
+    ctx.close()
+
+
+def test_four_labels_sixteen_temperatures_with_icm(pc, orc):
+    """The paper's four ICM labels (two random pairs per temperature) at the
+    largest ladder one CTA holds (16 x 4 = 64 replicas), incl. a ragged
+    ladder (11 temperatures)."""
+    shapes = [(8, 8, 8), (6, 6, 6), (4, 4, 8)]
+    temps = [16, 11, 9]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 9, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, 4)
+    ctx = pc.Context(0, 29)
+    pc.pc_apt_load(ctx.h, dims, J, betas, 4, 7)
+    apt = orc.Apt(dims, J, betas, 4, seed=29, entry0=7)
+    pc.pc_apt_run(ctx.h, 60, 1, True)
+    apt.run(60, threads=8)
     _compare(pc, apt, ctx, b, [(i, i) for i in range(len(shapes))])
     ctx.close()
 

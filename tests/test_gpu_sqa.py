@@ -64,6 +64,29 @@ def test_sqa_bit_exact(pc, orc, dims, P, R, S, seed):
     assert np.array_equal(E, E_ref)
 
 
+@pytest.mark.parametrize("dims,P,R,S,seed", [CASES[0], CASES[2], CASES[5]])
+def test_replica_correlation_matches_oracle_spins(pc, orc, dims, P, R, S, seed):
+    """Fig. S17's C_r from the device reduction equals N^-1 sum_i s_i0 s_ir
+    computed from the oracle's final spins."""
+    import torch
+    J = W.ea_couplings(dims, W.SEED_INSTANCES, seed)
+    gamma = W.linear_gamma_schedule(S)
+    N = int(np.prod(dims))
+    E_ref, s_ref = orc.sqa_anneal(dims, J, P, 0.05, gamma, R, run0=3, seed=seed, want_spins=True)
+    want = np.einsum("rn,rkn->rk", s_ref[:, 0, :].astype(np.int64), s_ref.astype(np.int64))
+    ctx = pc.Context(0, seed)
+    pc.pc_sqa_setup(ctx.h, dims, J, P, 0.05, gamma)
+    E = torch.zeros((R, P), dtype=torch.int32, device="cuda")
+    C = torch.zeros((R, P), dtype=torch.int32, device="cuda")
+    pc.pc_sqa_run_corr_dev(ctx.h, R, 3, E.data_ptr(), C.data_ptr())
+    torch.cuda.synchronize()
+    ctx.close()
+    assert np.array_equal(E.cpu().numpy(), E_ref)
+    got = C.cpu().numpy()
+    assert np.array_equal(got, want)
+    assert (got[:, 0] == N).all()
+
+
 def test_sqa_zero_sweeps_is_random_init(pc, orc):
     dims, P = (4, 4, 4), 16
     J = W.ea_couplings(dims, 1, 0)

@@ -438,6 +438,55 @@ def test_icm_keeps_product_boltzmann(orc):
     assert abs(cov) < 0.1 * var
 
 
+def test_icm_pairing_is_a_uniform_random_partition(orc):
+    """Four labels: every draw is one of the three perfect matchings of
+    {0,1,2,3}, each with probability 1/3 (chi-square, 2 d.o.f.); two labels
+    always pair (0, 1)."""
+    counts = np.zeros(3)
+    allowed = {(0, 1, 2, 3): 0, (0, 2, 1, 3): 1, (0, 3, 1, 2): 2}
+    for r in range(40):
+        for t in range(300):
+            m, q = orc.icm_pairing(13, 5, r, t, 4)
+            assert allowed[tuple(q)] == m
+            counts[m] += 1
+            assert orc.icm_pairing(13, 5, r, t, 2) == (0, [0, 1])
+    exp = counts.sum() / 3
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 13.8      # p = 0.001 for 2 degrees of freedom
+
+
+def test_icm_four_labels_keep_product_boltzmann(orc):
+    """Four labels at one temperature with sweeps + two random-pair ICMs per
+    attempt: every label's marginal stays exp(-beta E), and labels stay
+    uncorrelated."""
+    dims = (2, 2, 2)
+    J = W.ea_couplings(dims, 73, 0)
+    beta = 0.8
+    E = X.energies(X.lattice_edges(dims), J, None, X.all_states(8))
+    p = X.boltzmann(E, beta)
+    n_ch, n_sw = 24, 1200
+    apt = orc.Apt(np.tile([2, 2, 2], (n_ch, 1)), [J] * n_ch, [np.array([beta])] * n_ch, n_labels=4, seed=6)
+    apt.run(10, icm=True)
+    Es = [[] for _ in range(4)]
+    for _ in range(n_sw):
+        apt.run(1, icm=True)
+        for i in range(n_ch):
+            s, e, _ = apt.state(i)
+            for a in range(4):
+                assert e[a] == orc.energy(dims, J, s[a])
+                Es[a].append(e[a])
+    _, _, icm = apt.stats(0)
+    assert icm[1] + icm[2] > 0 and icm.sum() == 2 * (n_sw + 10)
+    mean = (p * E).sum()
+    var = (p * E ** 2).sum() - mean ** 2
+    for arr in Es:
+        m, se = X.batch_mean_stderr(np.array(arr).reshape(n_sw, n_ch).T.ravel())
+        assert abs(m - mean) < 5 * se
+    for a in range(4):
+        for b in range(a + 1, 4):
+            assert abs(np.cov(np.array(Es[a], float), np.array(Es[b], float))[0, 1]) < 0.1 * var
+
+
 # ---------------------------------------------------------------- APT run
 def test_apt_energies_and_best_consistent(orc):
     b = W.apt_single(L=4)
