@@ -90,6 +90,16 @@ int32_t pc_jperp_q(double gamma, int P, double T);
  * loaded before. */
 int pc_apt_load(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
                 const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0);
+/* As pc_apt_load with boundary conditions per axis: periodic [n][3] (host,
+ * nonzero = periodic, NULL = all periodic).  An open axis has no bonds
+ * across its ends (the paper's instances are open in x and y, Methods); its
+ * forward couplings J[3 s + axis] at the far end are ignored.  Lengths stay
+ * even on every axis (checkerboard layout).  Sites on an open face see a
+ * local field I = sum of their present bonds, odd I included; energies sum
+ * the present bonds only. */
+int pc_apt_load_bc(pc_ctx *ctx, int n_inst, const int32_t *dims, const uint8_t *periodic,
+                   const int8_t *J, const int32_t *n_temps, const double *betas, int n_labels,
+                   uint32_t entry0);
 /* n_swaps swap attempts; each = sweeps_per_swap checkerboard sweeps of all
  * replicas, replica energies, best-energy update, (icm != 0) one ICMop per
  * pair of labels of every temperature (two labels: the pair (0, 1); four:
@@ -98,6 +108,13 @@ int pc_apt_load(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
  * neighbour swaps of that attempt's parity.  Resumable: state, counters and
  * statistics carry over between calls.  Enqueued on the context stream. */
 int pc_apt_run(pc_ctx *ctx, int64_t n_swaps, int sweeps_per_swap, int icm);
+/* Swap rule of later pc_apt_run calls.  joint = 0 (default, Methods: swaps
+ * only between equal labels): every label of a temperature pair decides on
+ * its own.  joint = 1 (Algorithm S2 read literally, "swap the p-bit states
+ * of all corresponding iso-temperature replicas"): one decision per pair
+ * moves all labels, accepted with min(1, exp(dbeta sum_a dE_a)) from word 0
+ * of the label-0 swap draw. */
+int pc_apt_set_joint_swap(pc_ctx *ctx, int joint);
 /* Autotuner of the fused kernel's launch shape: times trial_swaps attempts
  * (with or without ICM) for 256, 384 and 512 threads per CTA on a scratch
  * copy of the loaded batch (the loaded chains do not move), keeps the

@@ -65,6 +65,7 @@ def lib():
         L.or_apt_destroy.argtypes = [ctypes.c_void_p]
         L.or_apt_run.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_apt_set_target.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]
+        L.or_apt_set_joint_swap.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_apt_state.argtypes = [ctypes.c_void_p, ctypes.c_int, i8p, i64p, i32p]
         L.or_apt_best.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p, i32p, i64p, i8p]
         L.or_apt_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p, i64p]
@@ -177,6 +178,9 @@ class Apt:
 
     def run(self, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True, threads: int = 0):
         _check(lib().or_apt_run(self.h, n_swaps, sweeps_per_swap, int(icm), threads), "apt_run")
+
+    def set_joint_swap(self, joint: bool):
+        _check(lib().or_apt_set_joint_swap(self.h, int(bool(joint))), "set_joint_swap")
 
     def set_target(self, inst: int, e_target: int):
         _check(lib().or_apt_set_target(self.h, inst, e_target), "set_target")

@@ -98,6 +98,7 @@ struct or_apt {
   int n;
   apt_entry *e;
   uint64_t seed;
+  int joint;   /* 1: one swap decision per temperature pair for all labels */
   int64_t sweeps_done, swaps_done;
 };
 
@@ -313,9 +314,37 @@ int or_icm_pairing(uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, int n_
  * (the paper's odd-numbered attempt), odd t pairs (1,2),(3,4),...; within
  * each pair every label decides on its own with
  * p_swap = min(1, exp(dbeta dE)), dE = E_{r+1} - E_r, dbeta = b_{r+1}-b_r. */
-static void swap_step(apt_entry *e, uint64_t seed, uint32_t t) {
+static void swap_states(apt_entry *e, int sA, int sB) {
   const int N = e->L.N;
+  int8_t *pA = e->spin + (size_t)sA * N, *pB = e->spin + (size_t)sB * N;
+  memcpy(e->tmp, pA, (size_t)N);
+  memcpy(pA, pB, (size_t)N);
+  memcpy(pB, e->tmp, (size_t)N);
+  int64_t te = e->E[sA];
+  e->E[sA] = e->E[sB];
+  e->E[sB] = te;
+}
+
+static void swap_step(apt_entry *e, uint64_t seed, uint32_t t, int joint) {
   for (int r = (int)(t & 1u); r + 1 < e->T; r += 2) {
+    if (joint) {
+      /* Algorithm S2 read literally: one decision swaps all iso-temperature
+       * replicas of the pair; the move exchanges A states at once, so its
+       * Metropolis ratio is the product exp(dbeta sum_a dE_a) */
+      int64_t dE = 0;
+      for (int a = 0; a < e->A; ++a) dE += e->E[(r + 1) * e->A + a] - e->E[r * e->A + a];
+      uint32_t ctr[4] = {(uint32_t)r, t, 0u, (e->ent << 8) | OR_TAG_SWAP}, x[4];
+      or_philox(ctr, seed, x);
+      int accept = (dE >= 0) || (x[0] < or_swap_threshold(e->beta[r + 1] - e->beta[r], dE));
+      for (int a = 0; a < e->A; ++a) {
+        e->att[r * e->A + a]++;
+        if (accept) {
+          swap_states(e, r * e->A + a, (r + 1) * e->A + a);
+          e->acc[r * e->A + a]++;
+        }
+      }
+      continue;
+    }
     for (int a = 0; a < e->A; ++a) {
       const int sA = r * e->A + a, sB = (r + 1) * e->A + a;
       int64_t dE = e->E[sB] - e->E[sA];
@@ -325,13 +354,7 @@ static void swap_step(apt_entry *e, uint64_t seed, uint32_t t) {
       e->att[r * e->A + a]++;
       if (accept) {
         /* swap the p-bit states (and energies) of the two replicas */
-        int8_t *pA = e->spin + (size_t)sA * N, *pB = e->spin + (size_t)sB * N;
-        memcpy(e->tmp, pA, (size_t)N);
-        memcpy(pA, pB, (size_t)N);
-        memcpy(pB, e->tmp, (size_t)N);
-        int64_t te = e->E[sA];
-        e->E[sA] = e->E[sB];
-        e->E[sB] = te;
+        swap_states(e, sA, sB);
         e->acc[r * e->A + a]++;
       }
     }
@@ -369,12 +392,18 @@ int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int thr
         }
         best_update(e, s);
       }
-      swap_step(e, a->seed, t);
+      swap_step(e, a->seed, t, a->joint);
     }
   }
   (void)threads;
   a->sweeps_done += n_swaps * sweeps_per_swap;
   a->swaps_done += n_swaps;
+  return 0;
+}
+
+int or_apt_set_joint_swap(or_apt *a, int joint) {
+  if (!a) return -1;
+  a->joint = joint != 0;
   return 0;
 }
 

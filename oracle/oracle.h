@@ -70,6 +70,10 @@ void or_apt_destroy(or_apt *a);
 /* n_swaps swap attempts, each preceded by sweeps_per_swap sweeps.
    icm: 0 off, 1 on.  threads: OpenMP threads over problems (<=0: default). */
 int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int threads);
+/* Swap rule: 0 (default) = each label decides on its own (Methods); 1 = one
+ * decision per temperature pair swaps all labels, accepted with
+ * min(1, exp(dbeta sum_a dE_a)) (Algorithm S2 read literally). */
+int or_apt_set_joint_swap(or_apt *a, int joint);
 int or_apt_set_target(or_apt *a, int inst, int64_t e_target);
 /* spins [B][N] in slot order (slot r*A + a: temperature r, label a);
    energies [B]; temperature index of each slot [B] (= slot / A). */

@@ -95,25 +95,29 @@ __device__ __forceinline__ int lin_of(const Geo &g, int c, int j) {
 }
 
 
-// Threshold of nibble i for packed count C (thr points at the group's 64
-// entries: 8 buffers x 8 counts).
+// Threshold of nibble i (thr points at the group's 128 entries: 8 buffers x
+// 16, entry I + 6 for I = -6..6).  SCALE 1: C holds I + 6 per nibble;
+// SCALE 2: C holds the satisfied count of a site with all six bonds, whose
+// entry is 2C.
+template <int SCALE>
 __device__ __forceinline__ uint32_t decide8_grp(const uint4 &x, uint32_t C, const uint32_t *thrh,
                                                 bool &tie) {
   uint32_t w = 0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const uint32_t v = half_hi(x, i), th = thrh[8 * i + ((C >> (4 * i)) & 0xFu)];
+    const uint32_t v = half_hi(x, i), th = thrh[16 * i + SCALE * ((C >> (4 * i)) & 0xFu)];
     w |= (v < th) ? (1u << (4 * i)) : 0u;
     tie |= (v == th);
   }
   return w;
 }
 
+template <int SCALE>
 __device__ __noinline__ uint32_t refine8_grp(uint32_t w, uint4 x, uint4 y, uint32_t C,
                                              const uint32_t *thr) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const uint32_t t = thr[8 * i + ((C >> (4 * i)) & 0xFu)];
+    const uint32_t t = thr[16 * i + SCALE * ((C >> (4 * i)) & 0xFu)];
     const uint32_t v = half_hi(x, i);
     if (v == (t & 0xFFFF0000u)) {
       const uint32_t u = v | half_lo(y, i);
@@ -125,8 +129,8 @@ __device__ __noinline__ uint32_t refine8_grp(uint32_t w, uint4 x, uint4 y, uint3
 
 struct Shared {
   uint32_t *S;       // [Gc][2][H]
-  uint32_t *thr;     // [Gc*8][8]
-  uint32_t *thrh;    // [Gc*8][8] high halves
+  uint32_t *thr;     // [Gc*8][16] p-bit thresholds, entry I + 6
+  uint32_t *thrh;    // [Gc*8][16] their high halves
   int32_t *temp_of;  // [Gc*8]
   int32_t *buf_of;   // [Gc*8] (unused by the fixed-slot APT mode)
   int32_t *E;        // [Gc*8]
@@ -136,7 +140,7 @@ struct Shared {
   int64_t *sum1, *sum2;   // ladder sums [Gc*8]
   int64_t *m64;      // best E, best sweep, hit sweep, target
   int32_t *m32;      // best buffer, flag, icm counters x3, any-swap flag
-  uint8_t *jn;       // [2][H]
+  uint16_t *jn;      // [2][H] coupling signs (bits 0-5) and missing bonds (8-13)
   uint32_t *V;       // ICM cluster bits [2][H], overlap bits [2][H], transposed overlaps [N/32][32]
   uint32_t *ikx;     // [64] per pair: Philox word 0, then k
   int32_t *ibit;     // [64] per pair: replica choice bit
@@ -150,6 +154,8 @@ struct Shared {
 struct Cta {
   Geo geo;
   int T, Tp, A, B, Bc, Gc, g0;
+  int nbonds;        // bonds present (3N with periodic axes)
+  uint32_t open;     // bit a: axis a open
   uint32_t ent;
   // thread chunking of the site loop: nch chunks of tpc threads, gc groups each
   int nch, tpc, gc;
@@ -158,10 +164,13 @@ struct Cta {
 // One colour phase of a sweep over the CTA's groups.  UPDATE: Eq. synapse +
 // Eq. neuron for every site of colour c.  ENERGY: accumulate, per buffer,
 // the satisfied bonds of the colour-c sites (every bond has exactly one
-// colour-1 endpoint, so the colour-1 pass gives E = 3N - 2 * satisfied).
-template <bool UPDATE, bool ENERGY>
-__device__ __forceinline__ void colour_phase(const AptArgs &a, const Cta &k, const Shared &sh,
-                                             int c, uint32_t sweep, int gtot) {
+// colour-1 endpoint, so the colour-1 pass gives E = nbonds - 2 * satisfied).
+// A site missing k of its six bonds (open boundaries) counts its satisfied
+// present bonds C, so I = 2C - (6 - k); the threshold row is indexed by
+// I + 6 = 2C + k, formed for eight spins at once as 2C + k * 0x11111111.
+template <bool UPDATE, bool ENERGY, bool OPEN>
+__device__ __forceinline__ void colour_phase_t(const AptArgs &a, const Cta &k, const Shared &sh,
+                                               int c, uint32_t sweep, int gtot) {
   const int tid = threadIdx.x;
   const int q = tid / k.tpc, lt = tid - q * k.tpc;
   const int H = k.geo.H;
@@ -181,6 +190,8 @@ __device__ __forceinline__ void colour_phase(const AptArgs &a, const Cta &k, con
       int n[6];
       neighbours(k.geo, c, j, n);
       const uint32_t jb = sh.jn[c * H + j];
+      const uint32_t miss = OPEN ? (jb >> 8) & 0x3Fu : 0u;
+      const uint32_t K = OPEN ? (uint32_t)__popc(miss) * 0x11111111u : 0u;
       uint32_t jm[6];
 #pragma unroll
       for (int d = 0; d < 6; ++d) jm[d] = nib_mask((jb >> d) & 1u);
@@ -192,16 +203,23 @@ __device__ __forceinline__ void colour_phase(const AptArgs &a, const Cta &k, con
         uint32_t C = 0;
 #pragma unroll
         for (int d = 0; d < 6; ++d) C += Wo[n[d]] ^ jm[d];
+        if (OPEN && miss) {   // boundary site of an open axis: drop the absent bonds
+#pragma unroll
+          for (int d = 0; d < 6; ++d)
+            if ((miss >> d) & 1u) C -= Wo[n[d]] ^ jm[d];
+        }
         uint32_t w;
         uint32_t *dst = sh.S + (size_t)(2 * gl + c) * H + j;
         if (UPDATE) {
           const uint32_t g = (uint32_t)(k.g0 + gl);
           const uint4 x = philox((uint32_t)j, sweep, c2 | g, (k.ent << 8) | a.tag_main, a.k0, a.k1);
           bool tie = false;
-          w = decide8_grp(x, C, sh.thrh + 64 * gl, tie);
+          // threshold index I + 6 = 2C + k per nibble (2C with every bond)
+          const uint32_t D = OPEN ? 2u * C + K : C;
+          w = decide8_grp<OPEN ? 1 : 2>(x, D, sh.thrh + 128 * gl, tie);
           if (tie) {
             const uint4 y = philox((uint32_t)j, sweep, c2 | g, (k.ent << 8) | a.tag_ref, a.k0, a.k1);
-            w = refine8_grp(w, x, y, C, sh.thr + 64 * gl);
+            w = refine8_grp<OPEN ? 1 : 2>(w, x, y, D, sh.thr + 128 * gl);
           }
           *dst = w;
         } else {
@@ -209,7 +227,7 @@ __device__ __forceinline__ void colour_phase(const AptArgs &a, const Cta &k, con
         }
         if (ENERGY) {
           const uint32_t full = w * 0xFu;    // nibble of all ones where the spin is +1
-          const uint32_t sat = (C & full) | ((0x66666666u - C) & ~full);
+          const uint32_t sat = (C & full) | ((0x66666666u - K - C) & ~full);
 #pragma unroll
           for (int m = 0; m < 4; ++m) acc[u][m] += (sat >> (4 * m)) & 0x000F000Fu;
         }
@@ -237,10 +255,20 @@ __device__ __forceinline__ void colour_phase(const AptArgs &a, const Cta &k, con
   }
 }
 
-// E_b = 3N - 2 * (satisfied bonds); resets the accumulators.
+// Periodic problems take the path without absent-bond handling.
+template <bool UPDATE, bool ENERGY>
+__device__ __forceinline__ void colour_phase(const AptArgs &a, const Cta &k, const Shared &sh, int c,
+                                             uint32_t sweep, int gtot) {
+  if (k.open)
+    colour_phase_t<UPDATE, ENERGY, true>(a, k, sh, c, sweep, gtot);
+  else
+    colour_phase_t<UPDATE, ENERGY, false>(a, k, sh, c, sweep, gtot);
+}
+
+// E_b = nbonds - 2 * (satisfied bonds); resets the accumulators.
 __device__ __forceinline__ void finish_energies(const Cta &k, const Shared &sh) {
   for (int b = threadIdx.x; b < 8 * k.Gc; b += blockDim.x) {
-    sh.E[b] = 3 * k.geo.N - 2 * sh.Eacc[b];
+    sh.E[b] = k.nbonds - 2 * sh.Eacc[b];
     sh.Eacc[b] = 0;
   }
 }
@@ -344,13 +372,13 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // A labels per temperature form A/2 pairs; label l's groups are
   // l*Gl .. l*Gl + Gl - 1.  Pair p of temperature r = 8h + i owns bit
   // 8 (h P + p) + i of the per-site overlap / cluster words.
-  const int A = k.A, P = A >> 1, Gl = k.Gc / A, nbits = 8 * Gl * P;
+  const int A = k.A, P = A >> 1, Gl = k.Gc >> P, nbits = 8 * Gl * P;   // A is 2 or 4
   const uint32_t *S = sh.S;
   uint32_t *V = sh.V;          // [2][H] cluster bits (one bit per pair)
   uint32_t *X = sh.V + N;      // [2][H] overlap bits
   int *match = sh.ibit + 32;   // [32] matching of the labels of each temperature
   if (tid < nbits) {
-    const int pb = tid, beta = pb >> 3, h = beta / P, p = beta - h * P, r = 8 * h + (pb & 7);
+    const int pb = tid, beta = pb >> 3, h = beta >> (P - 1), p = beta - h * P, r = 8 * h + (pb & 7);
     if (r < k.T) {
       const uint4 x = philox((uint32_t)r, t, (uint32_t)p, (k.ent << 8) | TAG_ICM, a.k0, a.k1);
       sh.ikx[pb] = x.x;
@@ -425,7 +453,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // counts by popcount, a warp scan over chunks, then the set bit inside
   // the chunk
   for (int r = warp; r < nbits; r += nw) {   // r: pair bit
-    if (8 * ((r >> 3) / P) + (r & 7) >= k.T) continue;
+    if (8 * ((r >> 3) >> (P - 1)) + (r & 7) >= k.T) continue;
     const int nm = sh.inm[r];
     if (nm == 0) continue;
     const int kth = (int)(((uint64_t)sh.ikx[r] * (uint64_t)nm) >> 32);
@@ -482,6 +510,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     struct Blk {
       int kk[8];
       uint32_t dx2, dy2, dz2;   // (minus, plus) block steps as two int16 each
+      uint32_t ok;              // bits -x,+x,-y,+y,-z,+z: outside neighbour present
     };
     auto make_blk = [&](int blk) {
       Blk B;
@@ -500,6 +529,11 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
       B.dx2 = pack(bx == 0 ? hx - 1 : -1, bx + 1 == hx ? 1 - hx : 1);
       B.dy2 = pack(hx * (y0 == 0 ? g.Ly - 2 : -2), hx * (y0 + 2 == g.Ly ? 2 - g.Ly : 2));
       B.dz2 = pack(LyHx * (z0 == 0 ? g.Lz - 2 : -2), LyHx * (z0 + 2 == g.Lz ? 2 - g.Lz : 2));
+      // an open axis has no bond across its ends
+      B.ok = 0x3Fu;
+      if (k.open & 1u) B.ok &= ~((bx == 0 ? 1u : 0u) | (bx + 1 == hx ? 2u : 0u));
+      if (k.open & 2u) B.ok &= ~((y0 == 0 ? 4u : 0u) | (y0 + 2 == g.Ly ? 8u : 0u));
+      if (k.open & 4u) B.ok &= ~((z0 == 0 ? 16u : 0u) | (z0 + 2 == g.Lz ? 32u : 0u));
       return B;
     };
     // one relaxation of a block: outside neighbours, then the internal
@@ -512,9 +546,12 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int dx = i & 1, dy = (i >> 1) & 1, dz = i >> 2;
-        const uint32_t ox = Vv[B.kk[i ^ 1] + (dx ? dxp : dxm)];
-        const uint32_t oy = Vv[B.kk[i ^ 2] + (dy ? dyp : dym)];
-        const uint32_t oz = Vv[B.kk[i ^ 4] + (dz ? dzp : dzm)];
+        const uint32_t mx = ((B.ok >> dx) & 1u) ? ~0u : 0u;
+        const uint32_t my = ((B.ok >> (2 + dy)) & 1u) ? ~0u : 0u;
+        const uint32_t mz = ((B.ok >> (4 + dz)) & 1u) ? ~0u : 0u;
+        const uint32_t ox = Vv[B.kk[i ^ 1] + (dx ? dxp : dxm)] & mx;
+        const uint32_t oy = Vv[B.kk[i ^ 2] + (dy ? dyp : dym)] & my;
+        const uint32_t oz = Vv[B.kk[i ^ 4] + (dz ? dzp : dzm)] & mz;
         nv[i] = v[i] | (x[i] & (ox | oy | oz));
       }
 #pragma unroll
@@ -600,7 +637,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // (D) decisions.  imask[(g P + p)] (g = l Gl + h): nibbles of label l's
   // group h flipped by pair p's cluster; imask[16 + g]: whole-replica flips.
   if (tid < nbits) {
-    const int pb = tid, beta = pb >> 3, h = beta / P, p = beta - h * P, i = pb & 7, r = 8 * h + i;
+    const int pb = tid, beta = pb >> 3, h = beta >> (P - 1), p = beta - h * P, i = pb & 7, r = 8 * h + i;
     if (r < k.T) {
       const int m = match[r];
       const int la = p == 0 ? 0 : (m == 0 ? 2 : 1);
@@ -625,14 +662,26 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   for (int kk = tid; kk < N; kk += nt) {
     const int c = kk >= H ? 1 : 0, j = kk - c * H;
     const uint32_t v = V[kk];
+    if (A == 2) {
 #pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      if (g >= k.Gc) break;
-      const int h = g % Gl;
-      uint32_t f = sh.imask[16 + g];
-      for (int p = 0; p < P; ++p)
-        f |= byte_to_nib((v >> (8 * (h * P + p))) & 0xFFu) & sh.imask[g * P + p];
-      if (f) sh.S[(2 * g + c) * H + j] ^= f;
+      for (int h = 0; h < 4; ++h) {
+        if (h >= Gl) break;
+        const uint32_t vv = byte_to_nib((v >> (8 * h)) & 0xFFu);
+        sh.S[(2 * h + c) * H + j] ^= (vv & sh.imask[h]) | sh.imask[16 + h];
+        sh.S[(2 * (Gl + h) + c) * H + j] ^= (vv & sh.imask[Gl + h]) | sh.imask[16 + Gl + h];
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h >= Gl) break;
+        const uint32_t n0 = byte_to_nib((v >> (16 * h)) & 0xFFu);
+        const uint32_t n1 = byte_to_nib((v >> (16 * h + 8)) & 0xFFu);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const int g = l * Gl + h;
+          sh.S[(2 * g + c) * H + j] ^= sh.imask[16 + g] | (n0 & sh.imask[2 * g]) | (n1 & sh.imask[2 * g + 1]);
+        }
+      }
     }
   }
   __syncthreads();
@@ -645,7 +694,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     colour_phase<false, true>(a, k, sh, 1, 0u, Gl);
     __syncthreads();
     for (int b = tid; b < 8 * Gl; b += nt) {
-      const int e0 = 3 * N - 2 * sh.Eacc[b];
+      const int e0 = k.nbonds - 2 * sh.Eacc[b];
       sh.E[b + 8 * Gl] += sh.E[b] - e0;
       sh.E[b] = e0;
       sh.Eacc[b] = 0;
@@ -709,10 +758,15 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
     const int np = (k.T - q) / 2;
     const int A = k.A;
     int any = 0;
-    for (int idx = lane; idx < np * A; idx += 32) {
-      const int r = q + 2 * (idx / A), al = idx % A;
+    // joint mode (Algorithm S2 read literally): lane idx decides pair idx
+    // for all labels at once, with the summed energy difference
+    const int nd = a.joint_swap ? np : np * A;
+    for (int idx = lane; idx < nd; idx += 32) {
+      const int r = q + 2 * (a.joint_swap ? idx : idx / A), al = a.joint_swap ? 0 : idx % A;
       const int bA = al * k.Tp + r, bB = bA + 1;
-      const int dE = sh.E[bB] - sh.E[bA];
+      int dE = sh.E[bB] - sh.E[bA];
+      if (a.joint_swap)
+        for (int l = 1; l < A; ++l) dE += sh.E[l * k.Tp + r + 1] - sh.E[l * k.Tp + r];
       bool acc = dE >= 0;
       if (!acc) {
         const uint4 x = philox((uint32_t)r, t, (uint32_t)al, (k.ent << 8) | TAG_SWAP, a.k0, a.k1);
@@ -721,15 +775,18 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
         const uint32_t th = ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
         acc = x.x < th;
       }
-      sh.satt[r * A + al] += 1;
-      if (acc) {
-        sh.sacc[r * A + al] += 1;
-        const int eA = sh.E[bA];
-        sh.E[bA] = sh.E[bB];
-        sh.E[bB] = eA;
-        if ((bA & 7) != 7) atomicOr(&sh.swm[bA >> 3], 1u << (4 * (bA & 7)));
-        else sh.swm[8 + (bA >> 3)] = 1u;
-        any = 1;
+      for (int l = al; l < (a.joint_swap ? A : al + 1); ++l) {
+        const int lA = l * k.Tp + r, lB = lA + 1;
+        sh.satt[r * A + l] += 1;
+        if (acc) {
+          sh.sacc[r * A + l] += 1;
+          const int eA = sh.E[lA];
+          sh.E[lA] = sh.E[lB];
+          sh.E[lB] = eA;
+          if ((lA & 7) != 7) atomicOr(&sh.swm[lA >> 3], 1u << (4 * (lA & 7)));
+          else sh.swm[8 + (lA >> 3)] = 1u;
+          any = 1;
+        }
       }
     }
     any = __any_sync(0xFFFFFFFFu, any);
@@ -758,6 +815,8 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.geo.mhx = P.mhx;
   k.geo.mLy = P.mLy;
   k.geo.mLy2 = P.mLy2;
+  k.nbonds = P.nbonds;
+  k.open = P.open;
   k.T = P.T;
   k.Tp = P.Tp;
   k.A = P.A;
@@ -776,8 +835,8 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   Shared sh;
   uint32_t *cur = smem;
   sh.S = cur;            cur += (size_t)k.Gc * N;
-  sh.thr = cur;          cur += 8 * G8;
-  sh.thrh = cur;         cur += 8 * G8;
+  sh.thr = cur;          cur += 16 * G8;
+  sh.thrh = cur;         cur += 16 * G8;
   sh.temp_of = reinterpret_cast<int32_t *>(cur);  cur += G8;
   sh.buf_of = reinterpret_cast<int32_t *>(cur);   cur += G8;
   sh.E = reinterpret_cast<int32_t *>(cur);        cur += G8;
@@ -797,7 +856,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.imask = cur;                                 cur += 24;
   sh.swm = cur;                                   cur += 24;
   sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 : 0;   // V, X, Xt
-  sh.jn = reinterpret_cast<uint8_t *>(cur);
+  sh.jn = reinterpret_cast<uint16_t *>(cur);
 
   // load state
   const uint32_t *gS = a.spins + P.spin_off + (size_t)k.g0 * N;
@@ -812,10 +871,10 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     sh.Eacc[b] = 0;
     sh.sum1[b] = 0;
     sh.sum2[b] = 0;
-    for (int e = 0; e < 8; ++e) {
-      const uint32_t th = a.pbit[P.pbit_off + 8 * tb + e];
-      sh.thr[8 * b + e] = th;
-      sh.thrh[8 * b + e] = th & 0xFFFF0000u;
+    for (int e = 0; e < 16; ++e) {
+      const uint32_t th = a.pbit[P.pbit_off + 16 * tb + e];
+      sh.thr[16 * b + e] = th;
+      sh.thrh[16 * b + e] = th & 0xFFFF0000u;
     }
   }
   for (int i = threadIdx.x; i < 64; i += blockDim.x) {
@@ -960,11 +1019,11 @@ namespace pc {
 
 size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins) {
   const size_t G8 = 8 * (size_t)Gc;
-  size_t words = (size_t)Gc * N + 16 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
+  size_t words = (size_t)Gc * N + 32 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
   words += 4 * 64 + 24 + 24;
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
   if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31;   // V, X and the transposed X
-  return words * 4 + (size_t)N + 16;
+  return words * 4 + (size_t)N * 2 + 16;
 }
 
 int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st) {

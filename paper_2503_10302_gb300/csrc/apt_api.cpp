@@ -32,7 +32,7 @@ struct Batch {
   // device arrays
   DevBuf<AptProbDev> d_prob;
   DevBuf<uint32_t> d_spins, d_pbit, d_swaptab, d_swapidx;
-  DevBuf<uint8_t> d_jneg;
+  DevBuf<uint16_t> d_jneg;
   DevBuf<int32_t> d_temp, d_buf, d_E, d_bestbuf;
   DevBuf<int64_t> d_bestE, d_bestsweep, d_hit, d_target, d_stats, d_sum1, d_sum2, d_hist, d_ctr;
   DevBuf<int8_t> d_bestspins;
@@ -62,17 +62,25 @@ int choose_nch(int H, int Gc, int tpb) {
   return best;
 }
 
-// Per (colour, j) coupling signs: bit d set iff J along direction d
-// (+x, -x, +y, -y, +z, -z) is -1.
-std::vector<uint8_t> pack_jneg_cj(const Lattice &lat, const int8_t *J) {
+// Per (colour, j): bit d set iff J along direction d (+x, -x, +y, -y, +z,
+// -z) is -1, bit 8 + d set iff that bond is absent (an open axis has no bond
+// across its ends).  *nbonds receives the number of bonds present.
+std::vector<uint16_t> pack_jn_cj(const Lattice &lat, const uint8_t per[3], const int8_t *J, int *nbonds) {
   std::vector<uint8_t> bylin = pack_jneg(lat, J);
-  const int Lx = lat.L[0], Ly = lat.L[1], H = lat.N / 2;
-  std::vector<uint8_t> out((size_t)lat.N);
+  const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2], H = lat.N / 2;
+  std::vector<uint16_t> out((size_t)lat.N);
+  int nb = 0;
   for (int s = 0; s < lat.N; ++s) {
     const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
     const int c = (x + y + z) & 1;
-    out[(size_t)c * H + (s >> 1)] = bylin[(size_t)s];
+    uint16_t miss = 0;
+    if (!per[0]) miss |= (uint16_t)((x == 0 ? 2 : 0) | (x == Lx - 1 ? 1 : 0));
+    if (!per[1]) miss |= (uint16_t)((y == 0 ? 8 : 0) | (y == Ly - 1 ? 4 : 0));
+    if (!per[2]) miss |= (uint16_t)((z == 0 ? 32 : 0) | (z == Lz - 1 ? 16 : 0));
+    for (int d = 0; d < 6; d += 2) nb += ((miss >> d) & 1) ? 0 : 1;   // forward bonds
+    out[(size_t)c * H + (s >> 1)] = (uint16_t)(((uint16_t)bylin[(size_t)s] & ~miss & 0x3F) | (miss << 8));
   }
+  *nbonds = nb;
   return out;
 }
 
@@ -91,6 +99,7 @@ void unpack_spins(const AptProbDev &P, const uint32_t *words, int B, int8_t *out
 
 struct ProbSpec {
   Lattice lat;
+  uint8_t per[3] = {1, 1, 1};     // periodic axes
   const int8_t *J;
   int T, Tp, A, B;
   uint32_t ent;
@@ -106,7 +115,7 @@ int build_batch(pc_ctx *c, Batch &bt, const std::vector<ProbSpec> &specs, int n_
   bt.G.assign((size_t)n, 0);
   size_t spin_w = 0, jneg_b = 0, pbit_w = 0, swapidx_w = 0, buf_n = 0, best_b = 0, stat_n = 0,
          hist_n = 0;
-  std::vector<uint8_t> h_jneg;
+  std::vector<uint16_t> h_jneg;
   bt.h_pbit.clear();
   bt.h_swaptab.clear();
   bt.h_swapidx.clear();
@@ -131,22 +140,25 @@ int build_batch(pc_ctx *c, Batch &bt, const std::vector<ProbSpec> &specs, int n_
     P.spin_off = (uint32_t)spin_w;
     spin_w += (size_t)G * P.N;
     P.jneg_off = (uint32_t)jneg_b;
-    std::vector<uint8_t> jn = pack_jneg_cj(s.lat, s.J);
+    std::vector<uint16_t> jn = pack_jn_cj(s.lat, s.per, s.J, &P.nbonds);
+    P.open = (s.per[0] ? 0u : 1u) | (s.per[1] ? 0u : 2u) | (s.per[2] ? 0u : 4u);
     h_jneg.insert(h_jneg.end(), jn.begin(), jn.end());
     jneg_b += (size_t)P.N;
     P.pbit_off = (uint32_t)pbit_w;
     for (int t = 0; t < s.T; ++t) {
-      for (int cc = 0; cc < 7; ++cc) bt.h_pbit.push_back(pc_pbit_threshold(s.beta[(size_t)t], 2 * cc - 6));
-      bt.h_pbit.push_back(0u);
+      // entry I + 6 for every local field I = -6..6 (odd I at open boundaries)
+      for (int e = 0; e < 13; ++e) bt.h_pbit.push_back(pc_pbit_threshold(s.beta[(size_t)t], e - 6));
+      for (int e = 13; e < 16; ++e) bt.h_pbit.push_back(0u);
     }
-    pbit_w += (size_t)8 * s.T;
+    pbit_w += (size_t)16 * s.T;
     P.swapidx_off = (uint32_t)swapidx_w;
     for (int r = 0; r + 1 < s.T; ++r) {
       const uint32_t off = (uint32_t)bt.h_swaptab.size();
       const double db = s.beta[(size_t)r + 1] - s.beta[(size_t)r];
       bt.h_swaptab.push_back(0xFFFFFFFFu);   // dE = 0: always accepted
       if (s.swaps) {
-        for (int64_t k = 1; k <= 3 * (int64_t)P.N; ++k) {
+        // |dE| <= 6N per label; the joint rule sums the A labels
+        for (int64_t k = 1; k <= 3 * (int64_t)P.N * s.A; ++k) {
           const uint32_t th = pc_swap_threshold(db, -2 * k);
           if (th == 0u) break;
           bt.h_swaptab.push_back(th);
@@ -186,7 +198,7 @@ int build_batch(pc_ctx *c, Batch &bt, const std::vector<ProbSpec> &specs, int n_
     return rc;
   cudaStream_t st = c->stream;
   PC_CUDA_TRY(cudaMemcpyAsync(bt.d_prob.p, bt.prob.data(), sizeof(AptProbDev) * n, cudaMemcpyHostToDevice, st));
-  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_jneg.p, h_jneg.data(), h_jneg.size(), cudaMemcpyHostToDevice, st));
+  PC_CUDA_TRY(cudaMemcpyAsync(bt.d_jneg.p, h_jneg.data(), h_jneg.size() * 2, cudaMemcpyHostToDevice, st));
   PC_CUDA_TRY(cudaMemcpyAsync(bt.d_pbit.p, bt.h_pbit.data(), bt.h_pbit.size() * 4, cudaMemcpyHostToDevice, st));
   PC_CUDA_TRY(cudaMemcpyAsync(bt.d_swaptab.p, bt.h_swaptab.data(), bt.h_swaptab.size() * 4,
                               cudaMemcpyHostToDevice, st));
@@ -322,6 +334,7 @@ struct AptImpl {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   int g_spp = -1, g_icm = -1;
+  int joint = 0;                      // joint-label swap rule
   ~AptImpl() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -364,7 +377,7 @@ std::vector<uint64_t> batch_identity(pc_ctx *c, const Batch &bt) {
   for (const AptProbDev &P : bt.prob) {
     id.push_back(((uint64_t)P.Lx << 40) | ((uint64_t)P.Ly << 20) | (uint64_t)P.Lz);
     id.push_back(((uint64_t)P.T << 32) | ((uint64_t)P.A << 16) | (uint64_t)P.B);
-    id.push_back(P.ent);
+    id.push_back(((uint64_t)P.open << 32) | P.ent);
   }
   return id;
 }
@@ -419,6 +432,11 @@ extern "C" {
 
 int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, const int32_t *n_temps,
                 const double *betas, int n_labels, uint32_t entry0) {
+  return pc_apt_load_bc(c, n_inst, dims, nullptr, J, n_temps, betas, n_labels, entry0);
+}
+
+int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *periodic, const int8_t *J,
+                   const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0) {
   if (!c || !dims || !J || !n_temps || !betas) return fail(PC_EINVAL, "NULL argument");
   if (n_inst < 1) return fail(PC_EINVAL, "n_inst must be >= 1");
   if (!(n_labels == 1 || n_labels == 2 || n_labels == 4))
@@ -431,6 +449,7 @@ int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, con
     ProbSpec &s = specs[(size_t)i];
     int rc = check_lattice(dims + 3 * i, J + 3 * joff, &s.lat);
     if (rc) return rc;
+    for (int ax = 0; ax < 3; ++ax) s.per[ax] = periodic ? (periodic[3 * i + ax] != 0) : 1;
     s.J = J + 3 * joff;
     s.T = n_temps[i];
     s.A = n_labels;
@@ -486,11 +505,20 @@ static int apt_enqueue(pc_ctx *c, AptImpl *im, int n_iter, int spp, int icm) {
   a.n_iter = n_iter;
   a.spp = spp;
   a.icm = icm;
+  a.joint_swap = im->joint;
   a.tag_main = 2;    // TAG_APT_SWEEP
   a.tag_ref = 3;     // TAG_APT_REFINE
   int rc = apt_launch(a, im->bt.n_cta, im->bt.tpb, im->bt.smem, c->stream);
   if (rc) return rc;
   return apt_advance_launch(im->bt.d_ctr.p, (int64_t)n_iter * spp, n_iter, c->stream);
+}
+
+int pc_apt_set_joint_swap(pc_ctx *c, int joint) {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  AptImpl *im = apt_impl(c);
+  im->joint = joint ? 1 : 0;
+  im->g_spp = -1;   // the captured chunk bakes the rule in: capture again
+  return PC_OK;
 }
 
 int pc_apt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
@@ -738,7 +766,7 @@ int pc_apt_get_pbit_table(pc_ctx *c, int inst, uint32_t *out) {
   Batch &bt = apt_impl(c)->bt;
   const AptProbDev &P = bt.prob[(size_t)inst];
   for (int t = 0; t < P.T; ++t)
-    for (int cc = 0; cc < 7; ++cc) out[7 * t + cc] = bt.h_pbit[P.pbit_off + 8 * t + cc];
+    for (int cc = 0; cc < 7; ++cc) out[7 * t + cc] = bt.h_pbit[P.pbit_off + 16 * t + 2 * cc];
   return PC_OK;
 }
 
@@ -799,9 +827,9 @@ int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t 
   std::vector<int64_t> s1, s2;
   for (int step = 0; step < max_len; ++step) {
     // thresholds of each active instance's current beta
-    std::vector<uint32_t> pb((size_t)8 * n_inst, 0u);
+    std::vector<uint32_t> pb((size_t)16 * n_inst, 0u);
     for (int i = 0; i < n_inst; ++i)
-      for (int cc = 0; cc < 7; ++cc) pb[(size_t)8 * i + cc] = pc_pbit_threshold(beta[(size_t)i], 2 * cc - 6);
+      for (int e = 0; e < 13; ++e) pb[(size_t)16 * i + e] = pc_pbit_threshold(beta[(size_t)i], e - 6);
     PC_CUDA_TRY(cudaMemcpyAsync(bt.d_pbit.p, pb.data(), pb.size() * 4, cudaMemcpyHostToDevice, c->stream));
     if ((rc = schedule(c, bt, active, APT_MODE_LADDER, 0, 0))) return rc;
     if ((rc = set_counters(c, bt, (int64_t)step * sweeps, 0))) return rc;

@@ -14,12 +14,14 @@ struct AptProbDev {
   int Lx, Ly, Lz, N;
   uint32_t mhx, mLy;      // ceil(2^32 / (Lx/2)), ceil(2^32 / Ly)
   uint32_t mLy2;          // ceil(2^32 / (Ly/2))
+  uint32_t open;          // bit a: axis a has open boundaries (no wrap-around bonds)
+  int nbonds;             // bonds present (3N when every axis is periodic)
   int T, Tp, A, B;        // temperatures, padded temperatures 8*ceil(T/8), labels,
                           // buffers (APT: A * Tp; ladder / pilot: chains)
   uint32_t ent;           // Philox entry id
   uint32_t spin_off;      // words: [G][2][N/2]
-  uint32_t jneg_off;      // bytes: [2][N/2] coupling signs per (colour, j)
-  uint32_t pbit_off;      // words: [T][8] p-bit thresholds, count c = 0..6
+  uint32_t jneg_off;      // [2][N/2] per (colour, j): bits 0-5 coupling signs, 8-13 missing bonds
+  uint32_t pbit_off;      // words: [T][16] p-bit thresholds, index I + 6 for I = -6..6
   uint32_t swapidx_off;   // words: [T-1][2] (offset, length) of each pair's swap table
   uint32_t buf_off;       // per-buffer arrays (temp_of, buf_of, E, sums)
   uint32_t best_off;      // bytes: best state [N] in lin order
@@ -31,7 +33,7 @@ struct AptArgs {
   const AptProbDev *prob;
   const int *cta_prob, *cta_g0, *cta_gc, *cta_nch;
   uint32_t *spins;
-  const uint8_t *jneg;
+  const uint16_t *jneg;
   const uint32_t *pbit, *swaptab, *swapidx;
   int32_t *temp_of, *buf_of, *E;
   int64_t *best_E, *best_sweep, *hit_sweep;
@@ -43,6 +45,7 @@ struct AptArgs {
   int64_t *hist;          // pilot histograms
   int n_bins;
   int mode, n_iter, spp, icm;
+  int joint_swap;         // 1: one swap decision per temperature pair for all labels
   int64_t *ctr;           // [2]: sweeps and swap attempts done before this launch
   int64_t window_from;
   uint32_t tag_init, tag_main, tag_ref;

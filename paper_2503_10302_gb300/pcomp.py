@@ -42,7 +42,9 @@ SIGNATURES = {
     "pc_swap_threshold": (c_u32, [c_dbl, c_i64]),
     "pc_jperp_q": (ctypes.c_int32, [c_dbl, c_int, c_dbl]),
     "pc_apt_load": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_i32p, c_f64p, c_int, c_u32]),
+    "pc_apt_load_bc": (c_int, [c_vp, c_int, c_i32p, c_vp, c_i8p, c_i32p, c_f64p, c_int, c_u32]),
     "pc_apt_run": (c_int, [c_vp, c_i64, c_int, c_int]),
+    "pc_apt_set_joint_swap": (c_int, [c_vp, c_int]),
     "pc_apt_autotune": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_int)]),
     "pc_apt_set_block_threads": (c_int, [c_vp, c_int]),
     "pc_apt_save": (c_int, [c_vp, ctypes.c_char_p]),
@@ -249,6 +251,21 @@ def pc_apt_load(ctx, dims, J_list, betas_list, n_labels: int = 2, entry0: int = 
     be = np.ascontiguousarray(np.concatenate([np.asarray(b, np.float64) for b in betas_list]))
     _call("pc_apt_load", ctx, len(J_list), ptr(d, ctypes.c_int32), ptr(J, ctypes.c_int8),
           ptr(nt, ctypes.c_int32), ptr(be, ctypes.c_double), n_labels, c_u32(entry0))
+
+
+def pc_apt_load_bc(ctx, dims, periodic, J_list, betas_list, n_labels: int = 2, entry0: int = 0) -> None:
+    """pc_apt_load with per-axis boundary conditions (periodic [n][3], nonzero = periodic)."""
+    d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(-1, 3))
+    per = np.ascontiguousarray(np.asarray(periodic, np.uint8).reshape(-1, 3))
+    J = _concat_J(J_list)
+    nt = np.ascontiguousarray([len(b) for b in betas_list], dtype=np.int32)
+    be = np.ascontiguousarray(np.concatenate([np.asarray(b, np.float64) for b in betas_list]))
+    _call("pc_apt_load_bc", ctx, len(J_list), ptr(d, ctypes.c_int32), per.ctypes.data, ptr(J, ctypes.c_int8),
+          ptr(nt, ctypes.c_int32), ptr(be, ctypes.c_double), n_labels, c_u32(entry0))
+
+
+def pc_apt_set_joint_swap(ctx, joint: bool) -> None:
+    _call("pc_apt_set_joint_swap", ctx, int(bool(joint)))
 
 
 def pc_apt_run(ctx, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True) -> None:

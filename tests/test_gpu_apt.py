@@ -156,6 +156,46 @@ def test_four_labels_sixteen_temperatures_with_icm(pc, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("labels", [2, 4])
+def test_open_boundaries_with_icm(pc, orc, labels):
+    """Open axes (the paper's instances are open in x and y): absent bonds,
+    odd local fields at the faces, energies over the present bonds, and ICM
+    clusters that do not wrap."""
+    shapes = [(8, 8, 8), (6, 4, 8), (4, 4, 4), (2, 4, 6), (12, 12, 4)]
+    per = [(0, 0, 1), (0, 1, 1), (0, 0, 0), (1, 1, 0), (0, 0, 1)]
+    temps = [8, 12, 5, 7, 16]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 10, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, labels)
+    ctx = pc.Context(0, 31)
+    pc.pc_apt_load_bc(ctx.h, dims, per, J, betas, labels, 3)
+    apt = orc.Apt(dims, J, betas, labels, seed=31, entry0=3, periodic=np.array(per, np.uint8))
+    pc.pc_apt_run(ctx.h, 40, 1, True)
+    apt.run(40, threads=8)
+    _compare(pc, apt, ctx, b, [(i, i) for i in range(len(shapes))])
+    for i, s in enumerate(shapes):   # energies really are open-lattice energies
+        st, E, _ = pc.pc_apt_get_state(ctx.h, i, int(np.prod(s)), temps[i] * labels)
+        assert E[0] == orc.energy(s, J[i], st[0], periodic=per[i])
+    ctx.close()
+
+
+@pytest.mark.parametrize("labels,icm", [(2, True), (4, True), (1, False)])
+def test_joint_label_swaps(pc, orc, labels, icm):
+    """The joint swap rule (one decision per temperature pair for all labels)
+    against the oracle, across a graph-replayed chunk (140 attempts)."""
+    b = W.apt_uniform_batch(3, 4, 8 if labels == 4 else 13, n_labels=labels)
+    ctx = pc.Context(0, 17)
+    pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, labels, 0)
+    pc.pc_apt_set_joint_swap(ctx.h, True)
+    apt = orc.Apt(b.dims, b.J, b.betas, labels, seed=17)
+    apt.set_joint_swap(True)
+    pc.pc_apt_run(ctx.h, 140, 1, icm)
+    apt.run(140, 1, icm, threads=8)
+    _compare(pc, apt, ctx, b)
+    ctx.close()
+
+
 def test_resume_and_chunking(pc, orc):
     """140 attempts in one call (graph replay + remainder) == 60 + 80."""
     b = W.apt_single(L=6, n_temps=10)

@@ -410,6 +410,49 @@ def test_icm_seed_is_uniform_over_mismatch_sites(orc):
     assert stats.chisquare(obs, exp).pvalue > 1e-6
 
 
+def test_joint_label_swaps_keep_product_boltzmann(orc):
+    """Joint swaps (one decision moves both labels of a temperature pair):
+    each temperature's marginal stays exp(-beta_r E), and the acceptance
+    equals E[min(1, exp(dbeta (dE_1 + dE_2)))] under the product measure,
+    computed exactly from the convolution of the two labels' dE laws."""
+    dims = (2, 2, 2)
+    J = W.ea_couplings(dims, 53, 0)
+    betas = np.array([0.3, 0.8, 1.4])
+    E = X.energies(X.lattice_edges(dims), J, None, X.all_states(8))
+    n_ch, n_sw = 32, 1500
+    apt = orc.Apt(np.tile([2, 2, 2], (n_ch, 1)), [J] * n_ch, [betas] * n_ch, n_labels=2, seed=12)
+    apt.set_joint_swap(True)
+    apt.run(20, icm=False)
+    per_t = [[] for _ in betas]
+    for _ in range(n_sw):
+        apt.run(1, icm=False)
+        for i in range(n_ch):
+            s, e, temp = apt.state(i)
+            for b in range(6):
+                per_t[temp[b]].append(e[b])
+    for r, beta in enumerate(betas):
+        p = X.boltzmann(E, beta)
+        m, se = X.batch_mean_stderr(np.array(per_t[r], float).reshape(n_sw, n_ch * 2).T.ravel())
+        assert abs(m - (p * E).sum()) < 5 * se, r
+    att = np.zeros((2, 2)); acc = np.zeros((2, 2))
+    for i in range(n_ch):
+        a, c, _ = apt.stats(i)
+        att += a; acc += c
+        assert np.array_equal(a[:, 0], a[:, 1]) and np.array_equal(c[:, 0], c[:, 1])
+    for r in range(2):
+        p0, p1 = X.boltzmann(E, betas[r]), X.boltzmann(E, betas[r + 1])
+        # law of dE = E_{r+1} - E_r for one label
+        law = {}
+        for ea, pa in zip(E, p0):
+            for eb, pb in zip(E, p1):
+                law[eb - ea] = law.get(eb - ea, 0.0) + pa * pb
+        db = betas[r + 1] - betas[r]
+        acc_exact = sum(q1 * q2 * min(1.0, math.exp(db * (d1 + d2)))
+                        for d1, q1 in law.items() for d2, q2 in law.items())
+        rate = acc[r, 0] / att[r, 0]
+        assert abs(rate - acc_exact) < 10 * math.sqrt(acc_exact * (1 - acc_exact) / att[r, 0])
+
+
 def test_icm_keeps_product_boltzmann(orc):
     """Two labels at one temperature with sweeps + ICM: each replica's
     marginal stays exp(-beta E) and the pair is independent."""
