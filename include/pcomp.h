@@ -83,7 +83,8 @@ int32_t pc_jperp_q(double gamma, int P, double T);
 /* Load a batch of n_inst problems: dims [n][3], J concatenated [sum N][3],
  * n_temps [n], betas concatenated (strictly increasing per problem),
  * n_labels in {1, 2, 4} replicas per temperature (ICM needs 2 or 4; the
- * paper uses 4), and 8 * ceil(n_temps / 8) * n_labels <= 64.  Problem i uses entry id entry0 + i in its
+ * paper uses 4), n_temps <= 32 and 8 * ceil(n_temps / 8) * n_labels <= 128
+ * (above 64 the problem runs as two CTAs, see pc_apt_set_split).  Problem i uses entry id entry0 + i in its
  * Philox counters.  Builds the p-bit and swap tables, draws the random
  * initial state (Algorithm S2 "Initialize all replicas to random states")
  * and resets counters, best energies and statistics.  Replaces any batch
@@ -115,6 +116,17 @@ int pc_apt_run(pc_ctx *ctx, int64_t n_swaps, int sweeps_per_swap, int icm);
  * moves all labels, accepted with min(1, exp(dbeta sum_a dE_a)) from word 0
  * of the label-0 swap draw. */
 int pc_apt_set_joint_swap(pc_ctx *ctx, int joint);
+/* Placement of each problem: one CTA, or a cluster of two CTAs that split
+ * its temperatures (rank 0 the colder half).  The two CTAs exchange the
+ * boundary swap and the best-energy candidates through distributed shared
+ * memory; results are identical either way.  A problem with more than 64
+ * replicas (e.g. 32 temperatures x 4 labels) always splits and needs at
+ * least 9 temperatures in every problem of the batch.  pref: 0 (default)
+ * also splits when the batch fills at most half the SMs; 1 splits only when
+ * needed; 2 splits whenever every problem has at least 9 temperatures.
+ * pc_apt_is_split reports the current placement. */
+int pc_apt_set_split(pc_ctx *ctx, int pref);
+int pc_apt_is_split(pc_ctx *ctx, int *split);
 /* Autotuner of the fused kernel's launch shape: times trial_swaps attempts
  * (with or without ICM) for 256, 384 and 512 threads per CTA on a scratch
  * copy of the loaded batch (the loaded chains do not move), keeps the

@@ -21,6 +21,7 @@
 // replicas' states (Algorithm S2) with SWAR nibble swaps, and the overlap of
 // eight ICM pairs is one XOR of two words, which makes the cluster growth a
 // nibble-parallel flood fill over all pairs at once.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "apt_dev.h"
@@ -149,11 +150,19 @@ struct Shared {
   uint32_t *imask;   // [3][8] per half-group: cluster-flip, whole-flip label 0, label 1
   uint32_t *swm;     // [8] per group: in-group swap nibble mask; [8] cross-group flags;
                      // [6] ICM matching nibble masks (4 labels)
+  int32_t *gmap;     // [8] global group of each local group
+  int32_t *xch;      // split problems: [2][4] boundary energies by attempt parity;
+                     // [8] accepted boundary labels; [12..17] the peer's best at launch end
+  uint32_t *stage;   // [2][4][64] peer boundary spins by attempt parity, one bit per site
 };
 
 struct Cta {
   Geo geo;
   int T, Tp, A, B, Bc, Gc, g0;
+  // this CTA holds, for every label, the temperature groups [g0, g0 + Gu) of
+  // the Glp groups per label (APT; ladder / pilot: A = 1, groups g0 ..);
+  // split problems run as a cluster of two CTAs, rank 0 holding the colder half
+  int Gu, Glp, split, rank;
   int nbonds;        // bonds present (3N with periodic axes)
   uint32_t open;     // bit a: axis a open
   uint32_t ent;
@@ -211,7 +220,7 @@ __device__ __forceinline__ void colour_phase_t(const AptArgs &a, const Cta &k, c
         uint32_t w;
         uint32_t *dst = sh.S + (size_t)(2 * gl + c) * H + j;
         if (UPDATE) {
-          const uint32_t g = (uint32_t)(k.g0 + gl);
+          const uint32_t g = (uint32_t)sh.gmap[gl];
           const uint4 x = philox((uint32_t)j, sweep, c2 | g, (k.ent << 8) | a.tag_main, a.k0, a.k1);
           bool tie = false;
           // threshold index I + 6 = 2C + k per nibble (2C with every bond)
@@ -275,13 +284,18 @@ __device__ __forceinline__ void finish_energies(const Cta &k, const Shared &sh) 
 
 // Minimum-energy selection (Algorithm S2 output): strict improvement, lowest
 // slot index (r * A + a) on ties; copies the state of the new best replica.
+// The two CTAs of a split problem track their own candidates (rank 1 into a
+// scratch state) and combine them at the end of the launch: the global best
+// is the lower energy, found at the earlier sweep, rank 0 (the lower slots)
+// on ties, and the target is first hit at the earlier of the two hits.
 __device__ void best_update(const AptArgs &a, const Cta &k, const Shared &sh, int p,
                             int64_t sweeps) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     int bestE = 0x7FFFFFFF, bests = 0x7FFFFFFF, bestb = 0;
     for (int b = lane; b < 8 * k.Gc; b += 32) {
-      const int r = b % k.Tp, lab = b / k.Tp;
+      const int gb = 8 * sh.gmap[b >> 3] + (b & 7);
+      const int r = gb % k.Tp, lab = gb / k.Tp;
       if (r >= k.T) continue;
       const int e = sh.E[b], slot = r * k.A + lab;
       if (e < bestE || (e == bestE && slot < bests)) {
@@ -306,7 +320,8 @@ __device__ void best_update(const AptArgs &a, const Cta &k, const Shared &sh, in
       if ((int64_t)bestE < sh.m64[0]) {
         sh.m64[0] = bestE;
         sh.m64[1] = sweeps;
-        sh.m32[0] = bestb;
+        sh.m32[0] = 8 * sh.gmap[bestb >> 3] + (bestb & 7);
+        sh.m32[7] = bestb;
         flag = 1;
       }
       if (sh.m64[2] < 0 && sh.m64[0] <= sh.m64[3]) sh.m64[2] = sweeps;
@@ -315,13 +330,14 @@ __device__ void best_update(const AptArgs &a, const Cta &k, const Shared &sh, in
   }
   __syncthreads();
   if (sh.m32[1]) {
-    const int b = sh.m32[0];
+    const int b = sh.m32[7];
     const int g = b >> 3, i = b & 7;
     const AptProbDev &P = a.prob[p];
+    int8_t *dst = (k.rank ? a.best_spins2 : a.best_spins) + P.best_off;
     for (int kk = threadIdx.x; kk < k.geo.N; kk += blockDim.x) {
       const int c = kk >= k.geo.H ? 1 : 0, j = kk - c * k.geo.H;
       const uint32_t w = sh.S[(size_t)(2 * g + c) * k.geo.H + j];
-      a.best_spins[P.best_off + lin_of(k.geo, c, j)] = ((w >> (4 * i)) & 1u) ? 1 : -1;
+      dst[lin_of(k.geo, c, j)] = ((w >> (4 * i)) & 1u) ? 1 : -1;
     }
   }
   __syncthreads();
@@ -372,13 +388,14 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // A labels per temperature form A/2 pairs; label l's groups are
   // l*Gl .. l*Gl + Gl - 1.  Pair p of temperature r = 8h + i owns bit
   // 8 (h P + p) + i of the per-site overlap / cluster words.
-  const int A = k.A, P = A >> 1, Gl = k.Gc >> P, nbits = 8 * Gl * P;   // A is 2 or 4
+  const int A = k.A, P = A >> 1, Gl = k.Gu, nbits = 8 * Gl * P;   // A is 2 or 4
+  const int r0 = 8 * k.g0;   // first temperature held here
   const uint32_t *S = sh.S;
   uint32_t *V = sh.V;          // [2][H] cluster bits (one bit per pair)
   uint32_t *X = sh.V + N;      // [2][H] overlap bits
   int *match = sh.ibit + 32;   // [32] matching of the labels of each temperature
   if (tid < nbits) {
-    const int pb = tid, beta = pb >> 3, h = beta >> (P - 1), p = beta - h * P, r = 8 * h + (pb & 7);
+    const int pb = tid, beta = pb >> 3, h = beta >> (P - 1), p = beta - h * P, r = r0 + 8 * h + (pb & 7);
     if (r < k.T) {
       const uint4 x = philox((uint32_t)r, t, (uint32_t)p, (k.ent << 8) | TAG_ICM, a.k0, a.k1);
       sh.ikx[pb] = x.x;
@@ -400,7 +417,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
     const int h = tid / 3, m = tid - 3 * h;
     uint32_t mk = 0;
     for (int i = 0; i < 8; ++i) {
-      const int r = 8 * h + i;
+      const int r = r0 + 8 * h + i;
       if (r < k.T && match[r] == m) mk |= 0xFu << (4 * i);
     }
     sh.swm[16 + tid] = mk;
@@ -453,7 +470,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // counts by popcount, a warp scan over chunks, then the set bit inside
   // the chunk
   for (int r = warp; r < nbits; r += nw) {   // r: pair bit
-    if (8 * ((r >> 3) >> (P - 1)) + (r & 7) >= k.T) continue;
+    if (r0 + 8 * ((r >> 3) >> (P - 1)) + (r & 7) >= k.T) continue;
     const int nm = sh.inm[r];
     if (nm == 0) continue;
     const int kth = (int)(((uint64_t)sh.ikx[r] * (uint64_t)nm) >> 32);
@@ -637,7 +654,8 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   // (D) decisions.  imask[(g P + p)] (g = l Gl + h): nibbles of label l's
   // group h flipped by pair p's cluster; imask[16 + g]: whole-replica flips.
   if (tid < nbits) {
-    const int pb = tid, beta = pb >> 3, h = beta >> (P - 1), p = beta - h * P, i = pb & 7, r = 8 * h + i;
+    const int pb = tid, beta = pb >> 3, h = beta >> (P - 1), p = beta - h * P, i = pb & 7,
+              r = r0 + 8 * h + i;
     if (r < k.T) {
       const int m = match[r];
       const int la = p == 0 ? 0 : (m == 0 ? 2 : 1);
@@ -710,8 +728,11 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
 }
 
 // Applies the swap masks of the last attempt (sh.swm) to the words
-// [kb, ke) of every group plane ([0, H): colour 0, [H, 2H): colour 1).
-__device__ void swap_words(const Cta &k, const Shared &sh, int kb, int ke) {
+// [kb, ke) of every group plane ([0, H): colour 0, [H, 2H): colour 1).  A
+// split problem's boundary swap (bmask: accepted labels) also writes the
+// peer CTA's spins, pushed into `stage`, into this CTA's boundary nibble.
+__device__ void swap_words(const Cta &k, const Shared &sh, int kb, int ke, uint32_t bmask,
+                           const uint32_t *stage) {
   const int H = k.geo.H, G = k.Gc;
   // groups touched by the swaps, and the groups g whose nibble 7 pairs with
   // nibble 0 of g + 1
@@ -721,6 +742,9 @@ __device__ void swap_words(const Cta &k, const Shared &sh, int kb, int ke) {
     if (g < G && sh.swm[g]) touch |= 1u << g;
     if (g + 1 < G && sh.swm[8 + g]) cross |= 1u << g;
   }
+  // rank 0 receives into nibble 7 of each label's last group, rank 1 into
+  // nibble 0 of each label's first group
+  const int bsh = k.rank == 0 ? 28 : 0, bgoff = k.rank == 0 ? k.Gu - 1 : 0;
   for (int kk = kb + threadIdx.x; kk < ke; kk += blockDim.x) {
     uint32_t *col = sh.S + kk;   // word (g, c, j) at col[g * 2H]
 #pragma unroll
@@ -740,6 +764,37 @@ __device__ void swap_words(const Cta &k, const Shared &sh, int kb, int ke) {
         col[(size_t)(g + 1) * 2 * H] = w1 ^ d;
       }
     }
+    if (bmask) {
+      const int e = kk - kb;
+      for (int l = 0; l < k.A; ++l) {
+        if (!((bmask >> l) & 1u)) continue;
+        const uint32_t bit = (stage[64 * l + (e >> 5)] >> (e & 31)) & 1u;
+        uint32_t *wp = col + (size_t)(l * k.Gu + bgoff) * 2 * H;
+        *wp = (*wp & ~(1u << bsh)) | (bit << bsh);
+      }
+    }
+  }
+}
+
+// Split problems: writes this CTA's boundary spins of the words
+// [kb, kb + H) (one colour), every label, one bit per site, into the peer
+// CTA's stage[par] (distributed shared memory).  Rank 0 sends its hottest
+// temperature (nibble 7 of each label's last group), rank 1 its coldest
+// (nibble 0 of each label's first group).
+__device__ void push_boundary(const Cta &k, const Shared &sh, int kb, int par) {
+  namespace cg = cooperative_groups;
+  const int H = k.geo.H;
+  uint32_t *pstage = cg::this_cluster().map_shared_rank(sh.stage, k.rank ^ 1) + 256 * par;
+  const int sh_own = k.rank == 0 ? 28 : 0, goff = k.rank == 0 ? k.Gu - 1 : 0;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int base = (threadIdx.x >> 5) * 32; base < H; base += nw * 32) {
+    const int e = base + lane;
+    for (int l = 0; l < k.A; ++l) {
+      uint32_t bit = 0;
+      if (e < H) bit = (sh.S[(size_t)(l * k.Gu + goff) * 2 * H + kb + e] >> sh_own) & 1u;
+      const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
+      if (lane == 0) pstage[64 * l + (base >> 5)] = word;
+    }
   }
 }
 
@@ -747,36 +802,53 @@ __device__ void swap_words(const Cta &k, const Shared &sh, int kb, int ke) {
 // Tempering"; Methods): even t pairs (0,1),(2,3)..., odd t (1,2),(3,4)...;
 // each label decides on its own; p_swap = min(1, exp(dbeta dE)).  Accepted
 // pairs exchange their p-bit states (SWAR nibble swaps over all sites) and
-// energies.
+// energies.  A split problem pushes its boundary spins and energies to the
+// peer CTA before one cluster barrier; both CTAs then decide the boundary
+// pair from the same energies and random word, and take the peer's spins
+// for the accepted labels.  Buffers alternate with the attempt's parity, so
+// one barrier per attempt orders every exchange.
 __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int p, uint32_t t) {
   const AptProbDev &P = a.prob[p];
+  const int A = k.A, q = (int)(t & 1u);
+  const int r0 = 8 * k.g0, r1 = min(8 * (k.g0 + k.Gu), k.T);   // temperatures held here
+  // local buffer of (label l, temperature r): l * 8 Gu + r - r0
+  const int lb = 8 * k.Gu;
+  auto swap_table = [&](int r, int dE) {
+    const int kk = (-dE) >> 1;
+    const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
+    return ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
+  };
+  const int par = (int)(t & 1u);
+  if (k.split) {
+    // energies of this side of the boundary pair, and its colour-1 spins
+    const int rb_own = k.rank == 0 ? r1 - 1 : r0;
+    int *pe = cooperative_groups::this_cluster().map_shared_rank(sh.xch, k.rank ^ 1) + 4 * par;
+    if (threadIdx.x < A) pe[threadIdx.x] = sh.E[threadIdx.x * lb + rb_own - r0];
+    push_boundary(k, sh, k.geo.H, par);
+  }
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     if (lane < 16) sh.swm[lane] = 0;
     __syncwarp();
-    const int q = (int)(t & 1u);
-    const int np = (k.T - q) / 2;
-    const int A = k.A;
+    const int first = r0 + q;                          // r0 is even
+    const int np = r1 - 1 > first ? (r1 - first) / 2 : 0;   // pairs (r, r + 1), r + 1 < r1
     int any = 0;
     // joint mode (Algorithm S2 read literally): lane idx decides pair idx
     // for all labels at once, with the summed energy difference
     const int nd = a.joint_swap ? np : np * A;
     for (int idx = lane; idx < nd; idx += 32) {
-      const int r = q + 2 * (a.joint_swap ? idx : idx / A), al = a.joint_swap ? 0 : idx % A;
-      const int bA = al * k.Tp + r, bB = bA + 1;
+      const int r = first + 2 * (a.joint_swap ? idx : idx / A), al = a.joint_swap ? 0 : idx % A;
+      const int bA = al * lb + r - r0, bB = bA + 1;
       int dE = sh.E[bB] - sh.E[bA];
       if (a.joint_swap)
-        for (int l = 1; l < A; ++l) dE += sh.E[l * k.Tp + r + 1] - sh.E[l * k.Tp + r];
+        for (int l = 1; l < A; ++l) dE += sh.E[l * lb + r - r0 + 1] - sh.E[l * lb + r - r0];
       bool acc = dE >= 0;
       if (!acc) {
         const uint4 x = philox((uint32_t)r, t, (uint32_t)al, (k.ent << 8) | TAG_SWAP, a.k0, a.k1);
-        const int kk = (-dE) >> 1;
-        const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
-        const uint32_t th = ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
-        acc = x.x < th;
+        acc = x.x < swap_table(r, dE);
       }
       for (int l = al; l < (a.joint_swap ? A : al + 1); ++l) {
-        const int lA = l * k.Tp + r, lB = lA + 1;
+        const int lA = l * lb + r - r0, lB = lA + 1;
         sh.satt[r * A + l] += 1;
         if (acc) {
           sh.sacc[r * A + l] += 1;
@@ -792,12 +864,53 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
     any = __any_sync(0xFFFFFFFFu, any);
     if (lane == 0) sh.m32[5] = any;
   }
-  __syncthreads();
-  if (!sh.m32[5]) return;
+  uint32_t bmask = 0;
+  if (k.split) {
+    cooperative_groups::this_cluster().sync();   // the peer's energies and spins have landed
+    // the pair (rb - 1, rb) across the two CTAs, if this attempt's parity
+    const int rb = k.rank == 0 ? r1 : r0;
+    if (threadIdx.x == 0) {
+      uint32_t accm = 0;
+      if (rb < k.T && ((rb - 1) & 1) == q) {
+        const int rb_own = k.rank == 0 ? r1 - 1 : r0;
+        const int *pe = sh.xch + 4 * par;   // the peer's energies
+        int e_lo[4], e_hi[4];               // energies at rb - 1 (rank 0's) and rb (rank 1's)
+        for (int l = 0; l < A; ++l) {
+          const int own = sh.E[l * lb + rb_own - r0];
+          e_lo[l] = k.rank == 0 ? own : pe[l];
+          e_hi[l] = k.rank == 0 ? pe[l] : own;
+        }
+        for (int l = 0; l < (a.joint_swap ? 1 : A); ++l) {
+          int dE = e_hi[l] - e_lo[l];
+          if (a.joint_swap)
+            for (int m = 1; m < A; ++m) dE += e_hi[m] - e_lo[m];
+          bool acc = dE >= 0;
+          if (!acc) {
+            const uint4 x = philox((uint32_t)(rb - 1), t, (uint32_t)l, (k.ent << 8) | TAG_SWAP, a.k0, a.k1);
+            acc = x.x < swap_table(rb - 1, dE);
+          }
+          if (acc) accm |= a.joint_swap ? (1u << A) - 1u : 1u << l;
+        }
+        for (int l = 0; l < A; ++l) {
+          if (k.rank == 0) sh.satt[(rb - 1) * A + l] += 1;   // counted once, by rank 0
+          if ((accm >> l) & 1u) {
+            if (k.rank == 0) sh.sacc[(rb - 1) * A + l] += 1;
+            sh.E[l * lb + rb_own - r0] = k.rank == 0 ? e_hi[l] : e_lo[l];
+          }
+        }
+      }
+      sh.xch[8] = (int)accm;
+    }
+    __syncthreads();
+    bmask = (uint32_t)sh.xch[8];
+  } else {
+    __syncthreads();
+  }
+  if (!sh.m32[5] && !bmask) return;
   // colour 0 is rewritten by the next sweep without being read (a Gibbs
   // update depends on the neighbours only), so only colour 1 moves now; the
   // kernel applies the last attempt's swaps to colour 0 before it stores
-  swap_words(k, sh, k.geo.H, 2 * k.geo.H);
+  swap_words(k, sh, k.geo.H, 2 * k.geo.H, bmask, sh.stage + 256 * par);
 }
 
 __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
@@ -824,25 +937,37 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.g0 = a.cta_g0[cta];
   k.Gc = a.cta_gc[cta];
   k.Bc = min(8 * k.Gc, P.B - 8 * k.g0);
+  k.split = a.split;
+  k.rank = a.split ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+  if (a.mode == pc::APT_MODE_APT || a.mode == pc::APT_MODE_ENERGY) {
+    k.Gu = k.Gc / k.A;   // A is 1, 2 or 4
+    k.Glp = k.Tp >> 3;
+  } else {
+    k.Gu = k.Gc;
+    k.Glp = (k.B + 7) >> 3;
+  }
   k.ent = P.ent;
   k.nch = a.cta_nch[cta];
   k.tpc = blockDim.x / k.nch;
   k.gc = (k.Gc + k.nch - 1) / k.nch;
-  const int N = P.N, G8 = 8 * k.Gc;
+  const int N = P.N;
+  // both CTAs of a split problem carve shared memory alike (rank 0 holds the
+  // larger half), so that distributed-shared-memory addresses correspond
+  const int Gcarve = a.split ? k.A * ((k.Glp + 1) >> 1) : k.Gc, G8 = 8 * Gcarve;
   const int64_t s0 = a.ctr[0], t0 = a.ctr[1];
   const bool icm = a.mode == pc::APT_MODE_APT && a.icm;
   // carve shared memory
   Shared sh;
   uint32_t *cur = smem;
-  sh.S = cur;            cur += (size_t)k.Gc * N;
+  sh.S = cur;            cur += (size_t)Gcarve * N;
   sh.thr = cur;          cur += 16 * G8;
   sh.thrh = cur;         cur += 16 * G8;
   sh.temp_of = reinterpret_cast<int32_t *>(cur);  cur += G8;
   sh.buf_of = reinterpret_cast<int32_t *>(cur);   cur += G8;
   sh.E = reinterpret_cast<int32_t *>(cur);        cur += G8;
   sh.Eacc = reinterpret_cast<int32_t *>(cur);     cur += G8;
-  sh.satt = reinterpret_cast<int32_t *>(cur);     cur += 64;
-  sh.sacc = reinterpret_cast<int32_t *>(cur);     cur += 64;
+  sh.satt = reinterpret_cast<int32_t *>(cur);     cur += 128;
+  sh.sacc = reinterpret_cast<int32_t *>(cur);     cur += 128;
   sh.m32 = reinterpret_cast<int32_t *>(cur);      cur += 8;
   cur += ((uintptr_t)cur & 4) ? 1 : 0;            // 8-byte align
   sh.m64 = reinterpret_cast<int64_t *>(cur);      cur += 8;
@@ -855,15 +980,21 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.isz = reinterpret_cast<int32_t *>(cur);      cur += 64;
   sh.imask = cur;                                 cur += 24;
   sh.swm = cur;                                   cur += 24;
+  sh.gmap = reinterpret_cast<int32_t *>(cur);     cur += 8;
+  sh.xch = reinterpret_cast<int32_t *>(cur);      cur += 24;
+  sh.stage = cur;                                 cur += a.split ? 512 : 0;
   sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 : 0;   // V, X, Xt
   sh.jn = reinterpret_cast<uint16_t *>(cur);
 
-  // load state
-  const uint32_t *gS = a.spins + P.spin_off + (size_t)k.g0 * N;
-  for (int i = threadIdx.x; i < k.Gc * N; i += blockDim.x) sh.S[i] = gS[i];
+  // load state: local group u is global group gmap[u]
+  if (threadIdx.x < 8)
+    sh.gmap[threadIdx.x] = (threadIdx.x / max(k.Gu, 1)) * k.Glp + k.g0 + threadIdx.x % max(k.Gu, 1);
+  __syncthreads();
+  for (int i = threadIdx.x; i < k.Gc * N; i += blockDim.x)
+    sh.S[i] = a.spins[P.spin_off + (size_t)sh.gmap[i / N] * N + i % N];
   for (int i = threadIdx.x; i < N; i += blockDim.x) sh.jn[i] = a.jneg[P.jneg_off + i];
-  for (int b = threadIdx.x; b < G8; b += blockDim.x) {
-    const int gb = 8 * k.g0 + b;
+  for (int b = threadIdx.x; b < 8 * k.Gc; b += blockDim.x) {
+    const int gb = 8 * sh.gmap[b >> 3] + (b & 7);
     const int tb = (b < k.Bc) ? a.temp_of[P.buf_off + gb] : 0;
     sh.temp_of[b] = tb;
     sh.buf_of[b] = (b < k.Bc) ? a.buf_of[P.buf_off + gb] : 0;
@@ -877,10 +1008,11 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
       sh.thrh[16 * b + e] = th & 0xFFFF0000u;
     }
   }
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) {
     sh.satt[i] = 0;
     sh.sacc[i] = 0;
   }
+  if (threadIdx.x < 24) sh.xch[threadIdx.x] = 0;
   if (a.mode == pc::APT_MODE_PILOT)
     for (int i = threadIdx.x; i < k.T * a.n_bins; i += blockDim.x) sh.hist[i] = 0;
   if (threadIdx.x == 0) {
@@ -891,7 +1023,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     sh.m32[0] = a.best_buf[p];
     sh.m32[1] = 0;
     sh.m32[2] = sh.m32[3] = sh.m32[4] = 0;
-    sh.m32[5] = 0;
+    sh.m32[5] = sh.m32[6] = sh.m32[7] = 0;
   }
   __syncthreads();
 
@@ -951,15 +1083,61 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   // every thread's last histogram / sum update lands before the write-back,
   // and colour 0 takes the last attempt's swaps
   __syncthreads();
-  if (a.mode == pc::APT_MODE_APT && a.n_iter > 0 && sh.m32[5]) {
-    swap_words(k, sh, 0, k.geo.H);
-    __syncthreads();
+  if (a.mode == pc::APT_MODE_APT && a.n_iter > 0) {
+    const int lpar = (int)((t0 + a.n_iter - 1) & 1);   // parity of the last attempt
+    uint32_t bmask = 0;
+    if (k.split) {
+      // colour-0 spins of the last boundary swap, and this rank's best
+      // candidate, to the peer (the other parity's buffers are free)
+      push_boundary(k, sh, 0, lpar ^ 1);
+      if (threadIdx.x == 0) {
+        int *px = cooperative_groups::this_cluster().map_shared_rank(sh.xch, k.rank ^ 1);
+        px[12] = (int)sh.m64[0];
+        px[13] = sh.m32[0];
+        px[14] = (int)(uint32_t)((uint64_t)sh.m64[1] & 0xFFFFFFFFu);
+        px[15] = (int)(uint32_t)((uint64_t)sh.m64[1] >> 32);
+        px[16] = (int)(uint32_t)((uint64_t)sh.m64[2] & 0xFFFFFFFFu);
+        px[17] = (int)(uint32_t)((uint64_t)sh.m64[2] >> 32);
+      }
+      cooperative_groups::this_cluster().sync();   // last access to the peer's memory
+      if (threadIdx.x == 0) {
+        const int64_t pE = sh.xch[12];
+        const int64_t psw = (int64_t)(((uint64_t)(uint32_t)sh.xch[15] << 32) | (uint32_t)sh.xch[14]);
+        const int64_t phit = (int64_t)(((uint64_t)(uint32_t)sh.xch[17] << 32) | (uint32_t)sh.xch[16]);
+        // rank 0's candidate against rank 1's: lower energy, earlier sweep,
+        // then rank 0 (its slots are the lower ones)
+        const int64_t E0 = k.rank == 0 ? sh.m64[0] : pE, E1 = k.rank == 0 ? pE : sh.m64[0];
+        const int64_t S0 = k.rank == 0 ? sh.m64[1] : psw, S1 = k.rank == 0 ? psw : sh.m64[1];
+        const bool win1 = E1 < E0 || (E1 == E0 && S1 < S0);
+        int copy = 0;
+        if (k.rank == 0 && win1) {
+          sh.m64[0] = pE;
+          sh.m64[1] = psw;
+          sh.m32[0] = sh.xch[13];
+        }
+        if (k.rank == 1) copy = win1 && sh.m64[0] == E1 && sh.m64[1] == S1 && sh.m64[1] >= s0;
+        const int64_t h = sh.m64[2];
+        sh.m64[2] = h < 0 ? phit : (phit < 0 ? h : min(h, phit));
+        sh.m32[1] = copy;
+      }
+      __syncthreads();
+      bmask = (uint32_t)sh.xch[8];
+      if (sh.m32[1]) {   // rank 1 found the problem's best: it moves its state
+        const AptProbDev &Pb = a.prob[p];
+        for (int i = threadIdx.x; i < N; i += blockDim.x)
+          a.best_spins[Pb.best_off + i] = a.best_spins2[Pb.best_off + i];
+      }
+    }
+    if (sh.m32[5] || bmask) {
+      swap_words(k, sh, 0, k.geo.H, bmask, sh.stage + 256 * (lpar ^ 1));
+      __syncthreads();
+    }
   }
   // store state
-  uint32_t *gSo = a.spins + P.spin_off + (size_t)k.g0 * N;
-  for (int i = threadIdx.x; i < k.Gc * N; i += blockDim.x) gSo[i] = sh.S[i];
+  for (int i = threadIdx.x; i < k.Gc * N; i += blockDim.x)
+    a.spins[P.spin_off + (size_t)sh.gmap[i / N] * N + i % N] = sh.S[i];
   for (int b = threadIdx.x; b < k.Bc; b += blockDim.x) {
-    const int gb = 8 * k.g0 + b;
+    const int gb = 8 * sh.gmap[b >> 3] + (b & 7);
     a.temp_of[P.buf_off + gb] = sh.temp_of[b];
     a.buf_of[P.buf_off + gb] = sh.buf_of[b];
     a.E[P.buf_off + gb] = sh.E[b];
@@ -973,15 +1151,16 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
       atomicAdd(reinterpret_cast<unsigned long long *>(&a.hist[P.hist_off + i]),
                 (unsigned long long)sh.hist[i]);
   if (a.mode == pc::APT_MODE_APT) {
+    // statistics: both CTAs of a split problem add theirs
+    unsigned long long *st = reinterpret_cast<unsigned long long *>(a.stats + P.stat_off);
     const int npair = (k.T - 1) * k.A;
     for (int i = threadIdx.x; i < npair; i += blockDim.x) {
-      a.stats[P.stat_off + i] += sh.satt[i];
-      a.stats[P.stat_off + npair + i] += sh.sacc[i];
+      if (sh.satt[i]) atomicAdd(st + i, (unsigned long long)sh.satt[i]);
+      if (sh.sacc[i]) atomicAdd(st + npair + i, (unsigned long long)sh.sacc[i]);
     }
-    if (threadIdx.x == 0) {
-      a.stats[P.stat_off + 2 * npair + 0] += sh.m32[2];
-      a.stats[P.stat_off + 2 * npair + 1] += sh.m32[3];
-      a.stats[P.stat_off + 2 * npair + 2] += sh.m32[4];
+    if (threadIdx.x < 3 && sh.m32[2 + threadIdx.x])
+      atomicAdd(st + 2 * npair + threadIdx.x, (unsigned long long)sh.m32[2 + threadIdx.x]);
+    if (threadIdx.x == 0 && k.rank == 0) {
       a.best_E[p] = sh.m64[0];
       a.best_sweep[p] = sh.m64[1];
       a.hit_sweep[p] = sh.m64[2];
@@ -1020,7 +1199,7 @@ namespace pc {
 size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins) {
   const size_t G8 = 8 * (size_t)Gc;
   size_t words = (size_t)Gc * N + 32 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
-  words += 4 * 64 + 24 + 24;
+  words += 4 * 64 + 24 + 24 + 128 + 8 + 24 + 512;   // + larger swap stats, group map, exchange, stage
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
   if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31;   // V, X and the transposed X
   return words * 4 + (size_t)N * 2 + 16;
@@ -1038,7 +1217,24 @@ int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t s
     PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     set_for[dev] = smem;
   }
-  apt_kernel<<<n_cta, tpb, smem, st>>>(a);
+  if (!a.split) {
+    apt_kernel<<<n_cta, tpb, smem, st>>>(a);
+  } else {
+    // split problems: consecutive CTA pairs form one cluster
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)n_cta);
+    cfg.blockDim = dim3((unsigned)tpb);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, apt_kernel, a));
+  }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }

@@ -35,10 +35,12 @@ struct Batch {
   DevBuf<uint16_t> d_jneg;
   DevBuf<int32_t> d_temp, d_buf, d_E, d_bestbuf;
   DevBuf<int64_t> d_bestE, d_bestsweep, d_hit, d_target, d_stats, d_sum1, d_sum2, d_hist, d_ctr;
-  DevBuf<int8_t> d_bestspins;
+  DevBuf<int8_t> d_bestspins, d_bestspins2;   // best states; rank-1 candidates of split problems
   DevBuf<int> d_cta;             // [4][n_cta]: prob, g0, gc, nch
   int n_cta = 0;
   int tpb = kTpbDefault;
+  int split = 0;         // APT problems run as clusters of two CTAs (by temperature)
+  int split_pref = 0;    // 0: when needed or when the batch fills at most half the SMs; 1: only when needed; 2: whenever possible
   size_t smem = 0;
   std::vector<uint32_t> h_pbit, h_swaptab, h_swapidx;
 };
@@ -194,6 +196,7 @@ int build_batch(pc_ctx *c, Batch &bt, const std::vector<ProbSpec> &specs, int n_
       (rc = bt.d_bestE.alloc((size_t)n)) || (rc = bt.d_bestsweep.alloc((size_t)n)) ||
       (rc = bt.d_hit.alloc((size_t)n)) || (rc = bt.d_target.alloc((size_t)n)) ||
       (rc = bt.d_bestbuf.alloc((size_t)n)) || (rc = bt.d_bestspins.alloc(best_b)) ||
+      (rc = bt.d_bestspins2.alloc(best_b)) ||
       (rc = bt.d_stats.alloc(stat_n)) || (rc = bt.d_hist.alloc(hist_n)) || (rc = bt.d_ctr.alloc(2)))
     return rc;
   cudaStream_t st = c->stream;
@@ -235,6 +238,7 @@ AptArgs base_args(pc_ctx *c, Batch &bt) {
   a.pbit = bt.d_pbit.p;
   a.swaptab = bt.d_swaptab.p;
   a.swapidx = bt.d_swapidx.p;
+  a.split = bt.split;
   a.temp_of = bt.d_temp.p;
   a.buf_of = bt.d_buf.p;
   a.E = bt.d_E.p;
@@ -244,6 +248,7 @@ AptArgs base_args(pc_ctx *c, Batch &bt) {
   a.target = bt.d_target.p;
   a.best_buf = bt.d_bestbuf.p;
   a.best_spins = bt.d_bestspins.p;
+  a.best_spins2 = bt.d_bestspins2.p;
   a.stats = bt.d_stats.p;
   a.sum1 = bt.d_sum1.p;
   a.sum2 = bt.d_sum2.p;
@@ -266,9 +271,23 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return (int64_t)bt.prob[(size_t)x].N * bt.prob[(size_t)x].B > (int64_t)bt.prob[(size_t)y].N * bt.prob[(size_t)y].B;
   });
-  // APT keeps a problem in one CTA (swaps and ICM couple all its groups).
+  // APT keeps a problem in one CTA (swaps and ICM couple all its groups), or
+  // in a cluster of two CTAs that split its temperatures: needed above 64
+  // replicas, and chosen for speed when the batch fills at most half the SMs.
   // Ladder and pilot chains are independent, so their groups spread over
   // about one CTA per SM when the batch is small.
+  bt.split = 0;
+  if (mode == APT_MODE_APT && !order.empty()) {
+    bool need = false, can = true;
+    for (int i : order) {
+      need = need || bt.prob[(size_t)i].B > 64;
+      can = can && (bt.prob[(size_t)i].Tp >> 3) >= 2;
+    }
+    if (need && !can)
+      return fail(PC_EINVAL, "a batch with more than 64 replicas in a problem needs >= 9 temperatures everywhere");
+    const bool small = 2 * (int64_t)order.size() <= c->sms;
+    bt.split = need || (can && (bt.split_pref == 2 || (bt.split_pref == 0 && small)));
+  }
   int gmax = kMaxGcCta;
   if (mode == APT_MODE_LADDER || mode == APT_MODE_PILOT) {
     int64_t total = 0;
@@ -281,6 +300,19 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
   for (int i : order) {
     const AptProbDev &P = bt.prob[(size_t)i];
     const int G = bt.G[(size_t)i];
+    if (bt.split) {
+      // rank 0: temperature groups [0, h1) of every label, rank 1: [h1, Glp)
+      const int Glp = P.Tp >> 3, h1 = (Glp + 1) / 2;
+      for (int rank = 0; rank < 2; ++rank) {
+        const int g0 = rank ? h1 : 0, gu = rank ? Glp - h1 : h1;
+        cp.push_back(i);
+        cg0.push_back(g0);
+        cgc.push_back(P.A * gu);
+        cnch.push_back(choose_nch(P.N / 2, P.A * gu, bt.tpb));
+      }
+      smem = std::max(smem, apt_smem_bytes(P.N, P.A * h1, bt.tpb / 32, mode, icm, P.T, n_bins));
+      continue;
+    }
     // equal chunks of at most gmax groups
     const int nchunk = (G + gmax - 1) / gmax, per = (G + nchunk - 1) / nchunk;
     for (int g0 = 0; g0 < G; g0 += per) {
@@ -455,8 +487,10 @@ int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *pe
     s.A = n_labels;
     s.Tp = 8 * ((s.T + 7) / 8);
     s.B = s.Tp * n_labels;     // replica of (r, a) in buffer a * Tp + r
-    if (s.T < 1 || s.B > 64)
-      return fail(PC_EINVAL, "need 1 <= n_temps and 8*ceil(n_temps/8) * n_labels <= 64");
+    // up to 64 replicas in one CTA; up to 128 (e.g. 32 temperatures x 4
+    // labels) in a cluster of two CTAs that split the temperatures
+    if (s.T < 1 || s.T > 32 || s.B > 128)
+      return fail(PC_EINVAL, "need 1 <= n_temps <= 32 and 8*ceil(n_temps/8) * n_labels <= 128");
     s.ent = entry0 + (uint32_t)i;
     s.beta.assign(betas + boff, betas + boff + s.T);
     for (int t = 0; t < s.T; ++t) {
@@ -589,6 +623,7 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) {
     // a scratch copy of the batch: the loaded chains are not advanced
     Batch tmp;
     tmp.tpb = tpb;
+    tmp.split_pref = im->bt.split_pref;
     if ((rc = build_batch(c, tmp, im->specs, 0))) break;
     if ((rc = schedule(c, tmp, {}, APT_MODE_APT, im->A >= 2, 0))) {
       rc = PC_OK;   // does not fit with this shape: skip it
@@ -627,6 +662,33 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) {
     im->graph = nullptr;
   }
   if (tpb_out) *tpb_out = best;
+  return PC_OK;
+}
+
+int pc_apt_set_split(pc_ctx *c, int pref) {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  if (pref < 0 || pref > 2) return fail(PC_EINVAL, "pref must be 0, 1 or 2");
+  AptImpl *im = apt_impl(c);
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int old = im->bt.split_pref;
+  im->bt.split_pref = pref;
+  int rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0);
+  if (rc) {
+    im->bt.split_pref = old;
+    schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0);
+    return rc;
+  }
+  if (im->exec) cudaGraphExecDestroy(im->exec);
+  if (im->graph) cudaGraphDestroy(im->graph);
+  im->exec = nullptr;
+  im->graph = nullptr;
+  return PC_OK;
+}
+
+int pc_apt_is_split(pc_ctx *c, int *split) {
+  if (!c || !c->apt.ready || !apt_impl(c) || !split) return fail(PC_ESTATE, "pc_apt_load first");
+  *split = apt_impl(c)->bt.split;
   return PC_OK;
 }
 

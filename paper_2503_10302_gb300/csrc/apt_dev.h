@@ -40,12 +40,14 @@ struct AptArgs {
   const int64_t *target;
   int32_t *best_buf;
   int8_t *best_spins;
+  int8_t *best_spins2;    // best-state candidates of rank 1 (split problems), same layout
   int64_t *stats;
   int64_t *sum1, *sum2;   // ladder: per-buffer sums of E and E^2
   int64_t *hist;          // pilot histograms
   int n_bins;
   int mode, n_iter, spp, icm;
   int joint_swap;         // 1: one swap decision per temperature pair for all labels
+  int split;              // 1: every problem runs as a cluster of two CTAs (by temperature)
   int64_t *ctr;           // [2]: sweeps and swap attempts done before this launch
   int64_t window_from;
   uint32_t tag_init, tag_main, tag_ref;

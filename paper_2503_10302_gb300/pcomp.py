@@ -45,6 +45,8 @@ SIGNATURES = {
     "pc_apt_load_bc": (c_int, [c_vp, c_int, c_i32p, c_vp, c_i8p, c_i32p, c_f64p, c_int, c_u32]),
     "pc_apt_run": (c_int, [c_vp, c_i64, c_int, c_int]),
     "pc_apt_set_joint_swap": (c_int, [c_vp, c_int]),
+    "pc_apt_set_split": (c_int, [c_vp, c_int]),
+    "pc_apt_is_split": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "pc_apt_autotune": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_int)]),
     "pc_apt_set_block_threads": (c_int, [c_vp, c_int]),
     "pc_apt_save": (c_int, [c_vp, ctypes.c_char_p]),
@@ -266,6 +268,17 @@ def pc_apt_load_bc(ctx, dims, periodic, J_list, betas_list, n_labels: int = 2, e
 
 def pc_apt_set_joint_swap(ctx, joint: bool) -> None:
     _call("pc_apt_set_joint_swap", ctx, int(bool(joint)))
+
+
+def pc_apt_set_split(ctx, pref: int) -> None:
+    """0: split when needed or when the batch is small; 1: only when needed; 2: whenever possible."""
+    _call("pc_apt_set_split", ctx, int(pref))
+
+
+def pc_apt_is_split(ctx) -> bool:
+    v = c_int()
+    _call("pc_apt_is_split", ctx, ctypes.byref(v))
+    return bool(v.value)
 
 
 def pc_apt_run(ctx, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True) -> None:

@@ -18,7 +18,7 @@ def pc():
 
 def _compare(pc, orc_apt, ctx, batch, insts=None, entry0=0):
     """GPU problem i vs oracle problem i - entry0 offset mapping."""
-    insts = range(batch.n) if insts is None else insts
+    insts = [(i, i) for i in range(batch.n)] if insts is None else insts
     for gi, oi in insts:
         N = int(np.prod(batch.dims[gi]))
         T = len(batch.betas[gi])
@@ -196,6 +196,60 @@ def test_joint_label_swaps(pc, orc, labels, icm):
     ctx.close()
 
 
+@pytest.mark.parametrize("labels,joint", [(2, False), (4, False), (2, True), (1, False)])
+def test_split_placement_is_bit_identical_and_matches_oracle(pc, orc, labels, joint):
+    """The same batch as one CTA per problem and as two-CTA clusters that
+    split the temperatures (even and uneven halves: 13, 24 and 32
+    temperatures), across a graph-replayed chunk, against the oracle."""
+    temps = [13, 24, 32] if labels < 4 else [13, 16, 12]
+    shapes = [(6, 6, 6), (8, 8, 8), (4, 6, 8)]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 11, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, labels)
+    res = []
+    for pref in (1, 2):
+        ctx = pc.Context(0, 37)
+        pc.pc_apt_load(ctx.h, dims, J, betas, labels, 2)
+        pc.pc_apt_set_split(ctx.h, pref)
+        assert pc.pc_apt_is_split(ctx.h) == (pref == 2)
+        pc.pc_apt_set_joint_swap(ctx.h, joint)
+        pc.pc_apt_run(ctx.h, 150, 1, labels > 1)
+        res.append([pc.pc_apt_get_state(ctx.h, i, int(np.prod(s)), temps[i] * labels) for i, s in enumerate(shapes)]
+                   + [pc.pc_apt_get_best(ctx.h, i, int(np.prod(s)))["E"] for i, s in enumerate(shapes)])
+        if pref == 2:
+            apt = orc.Apt(dims, J, betas, labels, seed=37, entry0=2)
+            apt.set_joint_swap(joint)
+            apt.run(150, 1, labels > 1, threads=8)
+            _compare(pc, apt, ctx, b)
+        ctx.close()
+    for x, y in zip(*res):
+        if isinstance(x, tuple):
+            for u, v in zip(x, y):
+                assert np.array_equal(u, v)
+        else:
+            assert x == y
+
+
+def test_four_labels_thirty_two_temperatures(pc, orc):
+    """The paper's APT shape: 32 temperatures x 4 ICM labels = 128 replicas
+    per problem (two CTAs per problem), with open x, y boundaries."""
+    shapes = [(8, 8, 8), (6, 6, 4)]
+    per = [(0, 0, 1), (1, 1, 1)]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 12, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(32), W.geometric_ladder(27)]
+    b = W.AptBatch(dims, J, betas, 4)
+    ctx = pc.Context(0, 41)
+    pc.pc_apt_load_bc(ctx.h, dims, per, J, betas, 4, 0)
+    assert pc.pc_apt_is_split(ctx.h)
+    apt = orc.Apt(dims, J, betas, 4, seed=41, periodic=np.array(per, np.uint8))
+    pc.pc_apt_run(ctx.h, 60, 1, True)
+    apt.run(60, threads=8)
+    _compare(pc, apt, ctx, b)
+    ctx.close()
+
+
 def test_resume_and_chunking(pc, orc):
     """140 attempts in one call (graph replay + remainder) == 60 + 80."""
     b = W.apt_single(L=6, n_temps=10)
@@ -318,7 +372,9 @@ def test_apt_rejects_bad_input(pc):
     with pytest.raises(pc.PcompError):
         pc.pc_apt_run(ctx.h, 10, 1, True)                          # before load
     with pytest.raises(pc.PcompError):
-        pc.pc_apt_load(ctx.h, [(4, 4, 4)], J, [W.geometric_ladder(33)], 2, 0)   # > 64 replicas
+        pc.pc_apt_load(ctx.h, [(4, 4, 4)], J, [W.geometric_ladder(33)], 2, 0)   # > 32 temperatures
+    with pytest.raises(pc.PcompError):   # 128 replicas need two CTAs; 5 temperatures cannot split
+        pc.pc_apt_load(ctx.h, [(4, 4, 4)] * 2, J * 2, [W.geometric_ladder(32), W.geometric_ladder(5)], 4, 0)
     with pytest.raises(pc.PcompError):
         pc.pc_apt_load(ctx.h, [(4, 4, 4)], J, [np.array([1.0, 0.5])], 2, 0)     # not increasing
     with pytest.raises(pc.PcompError):
