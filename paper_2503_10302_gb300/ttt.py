@@ -183,9 +183,14 @@ def c2_residual_vs_R(L=8, P=64, R=256, T=0.05, sweeps=10000, best_runs=10, best_
     e_best = min(e_best, int(run_best.min()))
     rho_run = (run_best - e_best) / N
     mu, sd = float(rho_run.mean()), float(rho_run.std(ddof=1))
+    # the Gaussian-fit check behind the EVT median: shape of the per-run
+    # residual-energy distribution (Sec. S2: it skews left at long anneals)
+    from scipy import stats as sst
+    gauss = {"skewness": float(sst.skew(rho_run)), "excess_kurtosis": float(sst.kurtosis(rho_run)),
+             "shapiro_p": float(sst.shapiro(rho_run).pvalue) if rho_run.size >= 3 else None}
     out = {"L": L, "P": P, "R": R, "T": T, "sweeps": sweeps, "anneal_seconds": dt,
            "flips_per_ns": N * P * R * sweeps / dt / 1e9, "e_best": e_best,
-           "rho_single_run": {"mean": mu, "std": sd}, "best_of_R": {},
+           "rho_single_run": {"mean": mu, "std": sd, "gaussian_check": gauss}, "best_of_R": {},
            "C_r_mean_over_runs": [float(x) for x in C_r[: P // 2 + 1]],
            "C_r_by_anneal_sweeps": C_ta,
            "C_r_length_1_over_e": int(np.argmax(C_r[: P // 2 + 1] < np.exp(-1.0))) or None}
