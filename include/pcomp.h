@@ -179,6 +179,12 @@ int pc_apt_get_swap_table(pc_ctx *ctx, int inst, int pair, uint32_t *out, int ma
  * threshold tables and uploads everything. */
 int pc_sqa_setup(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, double T,
                  int n_sweeps, const double *gamma);
+/* As pc_sqa_setup with per-axis boundary conditions: periodic [3] (host,
+ * nonzero = periodic, NULL = all periodic).  An open axis has no bonds
+ * across its ends (the paper's instances are open in x and y); lengths stay
+ * even; slice energies sum the present bonds. */
+int pc_sqa_setup_bc(pc_ctx *ctx, const int32_t *dims, const uint8_t *periodic, const int8_t *J,
+                    int P, double T, int n_sweeps, const double *gamma);
 /* Threshold table of sweep s: out[3][7] for n = s_{k-1} + s_{k+1} in
  * {-2, 0, 2} and intra-slice field I = 2c - 6; *jq = J_perp in Q16.16. */
 int pc_sqa_get_table(pc_ctx *ctx, int sweep, uint32_t *out, int32_t *jq);
@@ -214,7 +220,7 @@ int pc_sqa_anneal(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, doub
  * caching allocator or a fixed arena) or code that must not allocate on a
  * latency-critical path.  It runs the same kernel as pc_sqa_run_dev with the
  * same results, but keeps its scratch (packed couplings and per-sweep
- * threshold tables) in a static device array of about 0.94 MiB that every
+ * threshold tables) in a static device array of about 1.57 MiB that every
  * GPU loading this library holds until the process exits.
  *   device, stream   CUDA device and stream (NULL: legacy default stream).
  *   seed             Philox key.

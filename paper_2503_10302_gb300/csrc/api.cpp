@@ -63,6 +63,24 @@ std::vector<uint8_t> pack_jneg(const Lattice &lat, const int8_t *J) {
   return out;
 }
 
+std::vector<uint16_t> pack_jn16(const Lattice &lat, const uint8_t per[3], const int8_t *J, int *nbonds) {
+  std::vector<uint8_t> signs = pack_jneg(lat, J);
+  const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2];
+  std::vector<uint16_t> out((size_t)lat.N);
+  int nb = 0;
+  for (int s = 0; s < lat.N; ++s) {
+    const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
+    uint16_t miss = 0;   // bit d: direction d (+x, -x, +y, -y, +z, -z) absent
+    if (!per[0]) miss |= (uint16_t)((x == 0 ? 2 : 0) | (x == Lx - 1 ? 1 : 0));
+    if (!per[1]) miss |= (uint16_t)((y == 0 ? 8 : 0) | (y == Ly - 1 ? 4 : 0));
+    if (!per[2]) miss |= (uint16_t)((z == 0 ? 32 : 0) | (z == Lz - 1 ? 16 : 0));
+    for (int d = 0; d < 6; d += 2) nb += ((miss >> d) & 1) ? 0 : 1;   // forward bonds
+    out[(size_t)s] = (uint16_t)(((uint16_t)signs[(size_t)s] & ~miss & 0x3F) | (miss << 8));
+  }
+  *nbonds = nb;
+  return out;
+}
+
 // floor(2^32 p) clamped to [0, 2^32 - 1].
 static uint32_t threshold_of(double p) {
   const double t = std::floor(std::ldexp(p, 32));
@@ -183,10 +201,17 @@ int pc_philox(pc_ctx *c, int64_t n, const uint32_t *ctr, uint32_t *out) {
 // ------------------------------------------------------------------ DT-SQA
 int pc_sqa_setup(pc_ctx *c, const int32_t *dims, const int8_t *J, int P, double T, int n_sweeps,
                  const double *gamma) {
+  return pc_sqa_setup_bc(c, dims, nullptr, J, P, T, n_sweeps, gamma);
+}
+
+int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, const int8_t *J, int P,
+                    double T, int n_sweeps, const double *gamma) {
   if (!c || !J || (n_sweeps > 0 && !gamma)) return fail(PC_EINVAL, "NULL argument");
   Lattice lat;
   int rc = check_lattice(dims, J, &lat);
   if (rc) return rc;
+  uint8_t per[3];
+  for (int ax = 0; ax < 3; ++ax) per[ax] = periodic ? (periodic[ax] != 0) : 1;
   if (P < 16 || P % 16 || P > 128) return fail(PC_EINVAL, "P must be a multiple of 16 in [16, 128]");
   if ((int64_t)lat.N * P > 262144) return fail(PC_EINVAL, "N * P must be <= 262144");
   if (!(T > 0.0) || n_sweeps < 0) return fail(PC_EINVAL, "T must be > 0 and n_sweeps >= 0");
@@ -202,24 +227,25 @@ int pc_sqa_setup(pc_ctx *c, const int32_t *dims, const int8_t *J, int P, double 
   q.T = T;
   q.S = n_sweeps;
   q.jq.resize((size_t)n_sweeps);
-  q.table.assign((size_t)(n_sweeps > 0 ? n_sweeps : 1) * 24, 0u);
+  q.table.assign((size_t)(n_sweeps > 0 ? n_sweeps : 1) * kSqaTab, 0u);
   const double beta_eff = 1.0 / ((double)P * T);
   for (int s = 0; s < n_sweeps; ++s) {
     const int32_t jq = pc_jperp_q(gamma[s], P, T);
     q.jq[(size_t)s] = jq;
+    // every in-slice field I = -6..6 (odd at open faces) and time count m
     for (int m = 0; m < 3; ++m)
-      for (int cc = 0; cc < 7; ++cc)
-        q.table[(size_t)s * 24 + cc + 8 * m] = sqa_threshold(beta_eff, 2 * cc - 6, jq, 2 * m - 2);
+      for (int e = 0; e < 13; ++e)
+        q.table[(size_t)s * kSqaTab + e + 13 * m] = sqa_threshold(beta_eff, e - 6, jq, 2 * m - 2);
   }
-  std::vector<uint8_t> jn = pack_jneg(lat, J);
+  std::vector<uint16_t> jn = pack_jn16(lat, per, J, &q.nbonds);
   if ((rc = q.d_jneg.alloc(jn.size()))) return rc;
   if ((rc = q.d_table.alloc(q.table.size()))) return rc;
   // stage through pinned memory: one copy of each array
-  const size_t tb = q.table.size() * 4, jb = (jn.size() + 15) / 16 * 16;
+  const size_t tb = q.table.size() * 4, jb = (jn.size() * 2 + 15) / 16 * 16;
   if ((rc = q.stage.reserve(jb + tb))) return rc;
-  std::memcpy(q.stage.p, jn.data(), jn.size());
+  std::memcpy(q.stage.p, jn.data(), jn.size() * 2);
   std::memcpy(q.stage.p + jb, q.table.data(), tb);
-  PC_CUDA_TRY(cudaMemcpyAsync(q.d_jneg.p, q.stage.p, jn.size(), cudaMemcpyHostToDevice, c->stream));
+  PC_CUDA_TRY(cudaMemcpyAsync(q.d_jneg.p, q.stage.p, jn.size() * 2, cudaMemcpyHostToDevice, c->stream));
   PC_CUDA_TRY(cudaMemcpyAsync(q.d_table.p, q.stage.p + jb, tb, cudaMemcpyHostToDevice, c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   q.ready = true;
@@ -230,7 +256,7 @@ int pc_sqa_get_table(pc_ctx *c, int sweep, uint32_t *out, int32_t *jq) {
   if (!c || !c->sqa.ready) return fail(PC_ESTATE, "pc_sqa_setup first");
   if (sweep < 0 || sweep >= c->sqa.S) return fail(PC_EINVAL, "sweep out of range");
   for (int m = 0; m < 3; ++m)
-    for (int cc = 0; cc < 7; ++cc) out[7 * m + cc] = c->sqa.table[(size_t)sweep * 24 + cc + 8 * m];
+    for (int cc = 0; cc < 7; ++cc) out[7 * m + cc] = c->sqa.table[(size_t)sweep * kSqaTab + 2 * cc + 13 * m];
   if (jq) *jq = c->sqa.jq[(size_t)sweep];
   return PC_OK;
 }
@@ -253,6 +279,7 @@ static int sqa_enqueue(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t 
   a.k0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
   a.k1 = (uint32_t)(c->seed >> 32);
   a.jneg = q.d_jneg.p;
+  a.nbonds = q.nbonds;
   a.table = q.d_table.p;
   a.E = E_dev;
   a.best = best_dev;

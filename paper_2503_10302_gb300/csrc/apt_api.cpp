@@ -64,25 +64,16 @@ int choose_nch(int H, int Gc, int tpb) {
   return best;
 }
 
-// Per (colour, j): bit d set iff J along direction d (+x, -x, +y, -y, +z,
-// -z) is -1, bit 8 + d set iff that bond is absent (an open axis has no bond
-// across its ends).  *nbonds receives the number of bonds present.
+// pack_jn16's words in (colour, j) order: coupling signs (bits 0-5) and
+// absent bonds (bits 8-13) of site (c, j).  *nbonds receives the bonds present.
 std::vector<uint16_t> pack_jn_cj(const Lattice &lat, const uint8_t per[3], const int8_t *J, int *nbonds) {
-  std::vector<uint8_t> bylin = pack_jneg(lat, J);
-  const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2], H = lat.N / 2;
+  std::vector<uint16_t> bylin = pack_jn16(lat, per, J, nbonds);
+  const int Lx = lat.L[0], Ly = lat.L[1], H = lat.N / 2;
   std::vector<uint16_t> out((size_t)lat.N);
-  int nb = 0;
   for (int s = 0; s < lat.N; ++s) {
     const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
-    const int c = (x + y + z) & 1;
-    uint16_t miss = 0;
-    if (!per[0]) miss |= (uint16_t)((x == 0 ? 2 : 0) | (x == Lx - 1 ? 1 : 0));
-    if (!per[1]) miss |= (uint16_t)((y == 0 ? 8 : 0) | (y == Ly - 1 ? 4 : 0));
-    if (!per[2]) miss |= (uint16_t)((z == 0 ? 32 : 0) | (z == Lz - 1 ? 16 : 0));
-    for (int d = 0; d < 6; d += 2) nb += ((miss >> d) & 1) ? 0 : 1;   // forward bonds
-    out[(size_t)c * H + (s >> 1)] = (uint16_t)(((uint16_t)bylin[(size_t)s] & ~miss & 0x3F) | (miss << 8));
+    out[(size_t)((x + y + z) & 1) * H + (s >> 1)] = bylin[(size_t)s];
   }
-  *nbonds = nb;
   return out;
 }
 

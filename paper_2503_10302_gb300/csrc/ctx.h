@@ -75,7 +75,8 @@ struct SqaState {
   double T = 0;
   std::vector<uint32_t> table;   // [S][24]
   std::vector<int32_t> jq;       // [S]
-  DevBuf<uint8_t> d_jneg;
+  DevBuf<uint16_t> d_jneg;
+  int nbonds = 0;
   DevBuf<uint32_t> d_table;
   PinnedBuf<uint8_t> stage;       // pinned staging of jneg + tables
   DevBuf<int32_t> d_E;            // per-call output scratch of pc_sqa_run

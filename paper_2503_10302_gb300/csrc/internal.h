@@ -28,17 +28,23 @@ struct Lattice {
 // jneg byte of every site: bit d set iff the coupling on direction d
 // (0:+x 1:-x 2:+y 3:-y 4:+z 5:-z) is -1.
 std::vector<uint8_t> pack_jneg(const Lattice &lat, const int8_t *J);
+// Per site (lin order): bits 0-5 coupling signs as pack_jneg for the bonds
+// present, bits 8-13 the absent bonds (an open axis has no bond across its
+// ends; per[a] = 0 marks axis a open).  *nbonds receives the bonds present.
+std::vector<uint16_t> pack_jn16(const Lattice &lat, const uint8_t per[3], const int8_t *J, int *nbonds);
 int check_lattice(const int32_t *dims, const int8_t *J, Lattice *out);
 uint32_t recip32(uint32_t d);   // ceil(2^32 / d)
 uint32_t sqa_threshold(double beta_eff, int I, int32_t jq, int n);
 
 // ---------------------------------------------------------------- DT-SQA
+constexpr int kSqaTab = 40;   // threshold words per sweep: [3 m][13 I] (+1 pad)
 struct SqaArgs {
   int Lx, Ly, Lz, N, P, NB, S;
   uint32_t mLx, mLy;       // reciprocals of Lx and Ly
   uint32_t run0, k0, k1;
-  const uint8_t *jneg;     // [N]
-  const uint32_t *table;   // [S][24]: index c + 8 m
+  const uint16_t *jneg;    // [N] pack_jn16 words
+  int nbonds;              // bonds present (3N with periodic axes)
+  const uint32_t *table;   // [S][40]: index I + 6 + 13 m (I = -6..6, m = 0..2)
   int32_t *E;              // [R][P]
   int32_t *best;           // [R][2] (nullable)
   int8_t *spins;           // [R][P][N] (nullable)

@@ -46,7 +46,7 @@ struct Site {
   uint32_t jb;
 };
 
-__device__ __forceinline__ Site site_of(const pc::SqaArgs &a, int s, const uint8_t *jn) {
+__device__ __forceinline__ Site site_of(const pc::SqaArgs &a, int s, const uint16_t *jn) {
   Site t;
   t.s = s;
   const int r = (int)fdiv((uint32_t)s, a.mLx);   // s / Lx
@@ -73,7 +73,7 @@ __device__ __forceinline__ int neighbour(const pc::SqaArgs &a, const Site &t, in
 }
 
 // Nibble-packed counts, per block, of satisfied terms J_d s_nbr = +1 over
-// the six spatial directions (Eq. synapse with I = 2C - 6).  XOR with the
+// the spatial bonds present (Eq. synapse with I = 2C - deg).  XOR with the
 // all-nibbles mask turns a neighbour spin into J_d s_nbr for J_d = -1.
 template <int NB>
 __device__ __forceinline__ void spatial_counts(const pc::SqaArgs &a, const uint32_t *Wo,
@@ -82,6 +82,7 @@ __device__ __forceinline__ void spatial_counts(const pc::SqaArgs &a, const uint3
   for (int b = 0; b < NB; ++b) C[b] = 0;
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
+    if ((t.jb >> (8 + d)) & 1u) continue;   // absent bond (open axis)
     const int n = neighbour(a, t, d);
     const uint32_t m = nib_mask((t.jb >> d) & 1u);
 #pragma unroll
@@ -96,45 +97,50 @@ __device__ __forceinline__ void spatial_counts(const pc::SqaArgs &a, const uint3
 // six multiply-adds per word.
 struct SiteK {
   int nb[6];
-  int eps[6];
+  int eps[6];        // +-1, 0 for an absent bond
   uint32_t K;
+  uint32_t kb;       // absent bonds k: 2k in every byte (threshold index I + 6 = 2C + k)
   int q;
 };
 
-__device__ __forceinline__ SiteK site_consts(const pc::SqaArgs &a, int s, const uint8_t *jn) {
+__device__ __forceinline__ SiteK site_consts(const pc::SqaArgs &a, int s, const uint16_t *jn) {
   const Site t = site_of(a, s, jn);
   SiteK k;
   k.q = t.q;
-  int nneg = 0;
+  int nneg = 0, nmiss = 0;
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     k.nb[d] = neighbour(a, t, d);
-    const int neg = (t.jb >> d) & 1;
-    k.eps[d] = 1 - 2 * neg;
-    nneg += neg;
+    const int neg = (t.jb >> d) & 1, miss = (t.jb >> (8 + d)) & 1;
+    k.eps[d] = miss ? 0 : 1 - 2 * neg;
+    nneg += miss ? 0 : neg;
+    nmiss += miss;
   }
   k.K = 0x11111111u * (uint32_t)nneg;
+  k.kb = 0x01010101u * (uint32_t)(2 * nmiss);
   return k;
 }
 
 // Threshold tables in static shared memory, so that a byte of a packed
-// index word is directly an address offset: [2 sweeps][32 entries],
-// entry c + 8 m, high halves (Th) and full values (Tf).
-__shared__ __align__(16) uint32_t s_Th[2][32];
-__shared__ __align__(16) uint32_t s_Tf[2][32];
+// index word is directly an address offset: [2 sweeps][40 entries], entry
+// I + 6 + 13 m for in-slice field I = -6..6 and time count m = 0..2; top
+// halves (Th, 16-bit, 2-byte steps) and full values (Tf).
+__shared__ __align__(16) uint16_t s_Th[2][pc::kSqaTab];
+__shared__ __align__(16) uint32_t s_Tf[2][pc::kSqaTab];
 
 // Eq. neuron for the 8 nibbles of one word.  Byte k of Dlo / Dhi is the
-// byte offset of the threshold of nibble 2k / 2k+1 in s_Th (index * 4 plus
-// 128 for the odd sweep's buffer).
+// byte offset of the threshold of nibble 2k / 2k+1 in s_Th (index * 2 plus
+// 80 for the odd sweep's buffer).  The main half decides against the top
+// half of the threshold; equality is a tie.
 __device__ __forceinline__ uint32_t decide_word(const uint4 &x, uint32_t Dlo, uint32_t Dhi, bool &tie) {
   uint32_t w = 0;
   const char *base = reinterpret_cast<const char *>(&s_Th[0][0]);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const uint32_t off = __byte_perm((i & 1) ? Dhi : Dlo, 0u, 0x4440u + (uint32_t)(i >> 1));
-    const uint32_t th = *reinterpret_cast<const uint32_t *>(base + off);
+    const uint32_t th = *reinterpret_cast<const uint16_t *>(base + off);
     const uint32_t xw = word_of(x, i >> 1);
-    const uint32_t v = (i & 1) ? (xw & 0xFFFF0000u) : (xw << 16);
+    const uint32_t v = (i & 1) ? (xw >> 16) : (xw & 0xFFFFu);
     w |= (v < th) ? (1u << (4 * i)) : 0u;
     tie |= (v == th);
   }
@@ -146,7 +152,7 @@ __device__ __noinline__ uint32_t settle_ties(uint32_t w, uint4 x, uint4 y, uint3
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const uint32_t off = __byte_perm((i & 1) ? Dhi : Dlo, 0u, 0x4440u + (uint32_t)(i >> 1));
-    const uint32_t t = *reinterpret_cast<const uint32_t *>(base + off);
+    const uint32_t t = *reinterpret_cast<const uint32_t *>(base + 2 * off);
     const uint32_t v = half_hi(x, i);
     if (v == (t & 0xFFFF0000u)) {
       const uint32_t u = v | half_lo(y, i);
@@ -217,8 +223,10 @@ __device__ __forceinline__ void update_site(const pc::SqaArgs &a, const uint32_t
     const uint32_t lo = e ? O[b] : O[bm];
     const uint32_t hi = e ? O[bp] : O[b];
     const uint32_t M = O[b] + __funnelshift_r(lo, hi, e ? 4u : 28u);
-    const uint32_t Dlo = ((C[b] & 0x0F0F0F0Fu) << 2) + ((M & 0x0F0F0F0Fu) << 5) + boff;
-    const uint32_t Dhi = (((C[b] >> 4) & 0x0F0F0F0Fu) << 2) + (((M >> 4) & 0x0F0F0F0Fu) << 5) + boff;
+    // byte offsets 2 (2C + k + 13 m) + 80 (odd sweep): at most 156
+    const uint32_t kb = k.kb + boff;
+    const uint32_t Dlo = ((C[b] & 0x0F0F0F0Fu) << 2) + (M & 0x0F0F0F0Fu) * 26u + kb;
+    const uint32_t Dhi = (((C[b] >> 4) & 0x0F0F0F0Fu) << 2) + ((M >> 4) & 0x0F0F0F0Fu) * 26u + kb;
     const uint4 x = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_SWEEP, a.k0, a.k1);
     bool tie = false;
     w[b] = decide_word(x, Dlo, Dhi, tie);
@@ -253,7 +261,7 @@ __device__ __forceinline__ bool wait_at_least(const int *flag, int want, uint64_
 // s1 == S computes the final slice energies, otherwise the state goes back.
 template <int NB>
 __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, int32_t *Eacc,
-                                            const uint8_t *jn, const SiteK &kh, bool hoist,
+                                            const uint16_t *jn, const SiteK &kh, bool hoist,
                                             int run, int s0, int s1) {
   const int N = a.N, P = a.P;
   const uint32_t ent = a.run0 + (uint32_t)run;
@@ -273,22 +281,22 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
   } else {
     for (int idx = tid; idx < 2 * NB * N; idx += nt) W[idx] = __ldcg(gstate + idx);
   }
-  if (tid < 32) {
-    const uint32_t t = (tid < 24 && s0 < a.S) ? a.table[(size_t)s0 * 24 + tid] : 0u;
+  if (tid < pc::kSqaTab) {
+    const uint32_t t = s0 < a.S ? a.table[(size_t)s0 * pc::kSqaTab + tid] : 0u;
     s_Tf[s0 & 1][tid] = t;
-    s_Th[s0 & 1][tid] = t & 0xFFFF0000u;
+    s_Th[s0 & 1][tid] = (uint16_t)(t >> 16);
   }
   __syncthreads();
 
   for (int sw = s0; sw < s1; ++sw) {
     // the transverse coupling of this sweep lives in its threshold table;
     // prefetch the next sweep's table into the other buffer
-    if (tid < 32 && sw + 1 < a.S) {
-      const uint32_t t = tid < 24 ? a.table[(size_t)(sw + 1) * 24 + tid] : 0u;
+    if (tid < pc::kSqaTab && sw + 1 < a.S) {
+      const uint32_t t = a.table[(size_t)(sw + 1) * pc::kSqaTab + tid];
       s_Tf[(sw + 1) & 1][tid] = t;
-      s_Th[(sw + 1) & 1][tid] = t & 0xFFFF0000u;
+      s_Th[(sw + 1) & 1][tid] = (uint16_t)(t >> 16);
     }
-    const uint32_t boff = (sw & 1) ? 0x80808080u : 0u;
+    const uint32_t boff = (sw & 1) ? 0x50505050u : 0u;   // 80 bytes: the odd sweep's table
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
       const uint32_t *Wo = W + (1 - c) * NB * N;
@@ -310,7 +318,7 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
     return;
   }
   // Algorithm S1: classical energy of every slice (full J, no J_perp).  Each
-  // bond has one endpoint with 3D parity 1, so E_k = 3N - 2 sum_{q(s)=1} sat.
+  // bond has one endpoint with 3D parity 1, so E_k = nbonds - 2 sum_{q(s)=1} sat.
   for (int k = tid; k < P; k += nt) Eacc[k] = 0;
   __syncthreads();
   for (int c = 0; c < 2; ++c) {
@@ -322,12 +330,13 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
       const int e = c ^ 1;
       uint32_t C[NB];
       spatial_counts<NB>(a, Wo, t, C);
+      const int deg = 6 - __popc((t.jb >> 8) & 0x3Fu);
       for (int b = 0; b < NB; ++b) {
         const uint32_t w = Wc[(size_t)s * NB + b];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int ci = (C[b] >> (4 * i)) & 0xF;
-          const int sat = ((w >> (4 * i)) & 1u) ? ci : 6 - ci;
+          const int sat = ((w >> (4 * i)) & 1u) ? ci : deg - ci;
           atomicAdd(&Eacc[2 * (8 * b + i) + e], sat);
         }
       }
@@ -335,7 +344,7 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
   }
   __syncthreads();
   for (int k = tid; k < P; k += nt) {
-    Eacc[k] = 3 * N - 2 * Eacc[k];
+    Eacc[k] = a.nbonds - 2 * Eacc[k];
     a.E[(size_t)run * P + k] = Eacc[k];
   }
   __syncthreads();
@@ -400,7 +409,7 @@ __global__ void __launch_bounds__(PC_SQA_TPB, PC_SQA_MINB) sqa_kernel(const pc::
   const int N = a.N, P = a.P;
   uint32_t *W = smem;                                       // [2][NB][N]
   int32_t *Eacc = reinterpret_cast<int32_t *>(W + 2 * NB * N);   // [P]
-  uint8_t *jn = reinterpret_cast<uint8_t *>(Eacc + P);      // [N]
+  uint16_t *jn = reinterpret_cast<uint16_t *>(Eacc + P);    // [N]
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < N; i += nt) jn[i] = a.jneg[i];
   __syncthreads();
@@ -409,27 +418,27 @@ __global__ void __launch_bounds__(PC_SQA_TPB, PC_SQA_MINB) sqa_kernel(const pc::
   const bool hoist = PC_SQA_HOIST && N <= nt;
   SiteK kh;
   if (hoist && tid < N) kh = site_consts(a, tid, jn);
-  if (!PERSIST) {
+  if constexpr (!PERSIST) {
     anneal_span<NB>(a, W, Eacc, jn, kh, hoist, blockIdx.x, 0, a.S);
-    return;
-  }
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(a.queue, 1) + a.first_item;
-    __syncthreads();
-    const int item = s_item;
-    __syncthreads();
-    if (item >= a.n_items) break;
-    const int chunk = item / a.R, run = item - chunk * a.R;
-    const int s0 = chunk * a.K, s1 = min(a.S, s0 + a.K);
-    if (chunk > 0) {
-      if (tid == 0 && !wait_at_least(a.done + run, chunk, a.wait_ns)) atomicExch(a.err, 1);
+  } else {
+    for (;;) {
+      if (tid == 0) s_item = atomicAdd(a.queue, 1) + a.first_item;
       __syncthreads();
-    }
-    anneal_span<NB>(a, W, Eacc, jn, kh, hoist, run, s0, s1);
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.done + run), "r"(chunk + 1) : "memory");
+      const int item = s_item;
+      __syncthreads();
+      if (item >= a.n_items) break;
+      const int chunk = item / a.R, run = item - chunk * a.R;
+      const int s0 = chunk * a.K, s1 = min(a.S, s0 + a.K);
+      if (chunk > 0) {
+        if (tid == 0 && !wait_at_least(a.done + run, chunk, a.wait_ns)) atomicExch(a.err, 1);
+        __syncthreads();
+      }
+      anneal_span<NB>(a, W, Eacc, jn, kh, hoist, run, s0, s1);
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.done + run), "r"(chunk + 1) : "memory");
+      }
     }
   }
 }
@@ -476,7 +485,7 @@ namespace pc {
 
 size_t sqa_smem_bytes(int N, int P) {
   const int NB = P / 16;
-  return (size_t)2 * NB * N * 4 + (size_t)P * 4 + (size_t)N;
+  return (size_t)2 * NB * N * 4 + (size_t)P * 4 + (size_t)N * 2;
 }
 
 int sqa_launch(const SqaArgs &a, int R, cudaStream_t st) {
@@ -514,12 +523,12 @@ int philox_launch(const uint32_t *ctr, uint32_t *out, int64_t n, uint32_t k0, ui
 // keeps its scratch (the packed couplings and the per-sweep threshold
 // tables) in the file-scope device array below instead of in
 // library-allocated buffers.  Every GPU that loads this library keeps this
-// array (about 0.94 MiB) until the process exits.
+// array (about 1.57 MiB) until the process exits.
 namespace {
 
 constexpr int kNoallocMaxSweeps = 10240;
-constexpr int kNoallocJnegBytes = 4096;   // N <= 4096 sites
-constexpr size_t kNoallocTableBytes = (size_t)kNoallocMaxSweeps * 24 * 4;
+constexpr int kNoallocJnegBytes = 8192;   // N <= 4096 sites, 16-bit coupling words
+constexpr size_t kNoallocTableBytes = (size_t)kNoallocMaxSweeps * pc::kSqaTab * 4;
 constexpr size_t kNoallocBytes = kNoallocJnegBytes + kNoallocTableBytes;
 
 static __device__ __align__(256) unsigned char g_sqa_noalloc_scratch[kNoallocBytes];
@@ -570,9 +579,10 @@ extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, co
   if (R == 0) return PC_OK;
   cudaStream_t st = (cudaStream_t)stream;
 
-  // couplings: one byte per site, staged through a stack buffer
+  // couplings: one 16-bit word per site (periodic: no absent bonds), staged
+  // through a stack buffer
   {
-    uint8_t jn[kNoallocJnegBytes];
+    uint16_t jn[kNoallocJnegBytes / 2];
     const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2];
     for (int s = 0; s < lat.N; ++s) {
       const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
@@ -581,29 +591,29 @@ extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, co
       const int zm = x + Lx * (y + Ly * ((z + Lz - 1) % Lz));
       const int8_t j6[6] = {J[3 * s], J[3 * xm], J[3 * s + 1], J[3 * ym + 1], J[3 * s + 2],
                             J[3 * zm + 2]};
-      uint8_t m = 0;
+      uint16_t m = 0;
       for (int d = 0; d < 6; ++d)
-        if (j6[d] < 0) m |= (uint8_t)(1u << d);
+        if (j6[d] < 0) m |= (uint16_t)(1u << d);
       jn[s] = m;
     }
-    PC_CUDA_TRY(cudaMemcpyAsync(scratch, jn, (size_t)lat.N, cudaMemcpyHostToDevice, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(scratch, jn, (size_t)lat.N * 2, cudaMemcpyHostToDevice, st));
   }
   // per-sweep threshold tables, 64 sweeps per staged copy
   {
     constexpr int kChunk = 64;
-    uint32_t tab[kChunk * 24];
+    constexpr int W = pc::kSqaTab;
+    uint32_t tab[kChunk * W];
     const double beta_eff = 1.0 / ((double)P * T);
     for (int s0 = 0; s0 < n_sweeps; s0 += kChunk) {
       const int ns = (n_sweeps - s0 < kChunk) ? n_sweeps - s0 : kChunk;
       for (int k = 0; k < ns; ++k) {
         const int32_t jq = pc_jperp_q(gamma[s0 + k], P, T);
-        for (int e = 0; e < 24; ++e) tab[24 * k + e] = 0u;
+        for (int e = 0; e < W; ++e) tab[W * k + e] = 0u;
         for (int m = 0; m < 3; ++m)
-          for (int cc = 0; cc < 7; ++cc)
-            tab[24 * k + cc + 8 * m] = sqa_threshold(beta_eff, 2 * cc - 6, jq, 2 * m - 2);
+          for (int e = 0; e < 13; ++e) tab[W * k + e + 13 * m] = sqa_threshold(beta_eff, e - 6, jq, 2 * m - 2);
       }
-      PC_CUDA_TRY(cudaMemcpyAsync(scratch + kNoallocJnegBytes + (size_t)s0 * 96, tab,
-                                  (size_t)ns * 96, cudaMemcpyHostToDevice, st));
+      PC_CUDA_TRY(cudaMemcpyAsync(scratch + kNoallocJnegBytes + (size_t)s0 * W * 4, tab,
+                                  (size_t)ns * W * 4, cudaMemcpyHostToDevice, st));
     }
   }
   SqaArgs a;
@@ -619,7 +629,8 @@ extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, co
   a.run0 = run0;
   a.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
   a.k1 = (uint32_t)(seed >> 32);
-  a.jneg = scratch;
+  a.jneg = reinterpret_cast<const uint16_t *>(scratch);
+  a.nbonds = 3 * lat.N;
   a.table = reinterpret_cast<const uint32_t *>(scratch + kNoallocJnegBytes);
   a.E = E_dev;
   a.best = best_dev;

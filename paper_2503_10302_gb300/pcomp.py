@@ -60,6 +60,7 @@ SIGNATURES = {
     "pc_apt_get_pbit_table": (c_int, [c_vp, c_int, c_u32p]),
     "pc_apt_get_swap_table": (c_int, [c_vp, c_int, c_int, c_u32p, c_int, ctypes.POINTER(c_int)]),
     "pc_sqa_setup": (c_int, [c_vp, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p]),
+    "pc_sqa_setup_bc": (c_int, [c_vp, c_i32p, c_vp, c_i8p, c_int, c_dbl, c_int, c_f64p]),
     "pc_sqa_get_table": (c_int, [c_vp, c_int, c_u32p, ctypes.POINTER(ctypes.c_int32)]),
     "pc_sqa_run": (c_int, [c_vp, c_int, c_u32, c_i64p, c_i8p]),
     "pc_sqa_run_dev": (c_int, [c_vp, c_int, c_u32, c_vp, c_vp]),
@@ -189,6 +190,15 @@ def pc_sqa_setup(ctx, dims, J, P: int, T: float, gamma) -> None:
     d, j = _dims(dims), _J(J)
     g = np.ascontiguousarray(np.asarray(gamma, np.float64))
     _call("pc_sqa_setup", ctx, ptr(d, ctypes.c_int32), ptr(j, ctypes.c_int8), P, T, len(g),
+          ptr(g, ctypes.c_double))
+
+
+def pc_sqa_setup_bc(ctx, dims, periodic, J, P: int, T: float, gamma) -> None:
+    """pc_sqa_setup with per-axis boundary conditions (periodic [3], nonzero = periodic)."""
+    d, j = _dims(dims), _J(J)
+    per = np.ascontiguousarray(np.asarray(periodic, np.uint8).reshape(3))
+    g = np.ascontiguousarray(np.asarray(gamma, np.float64))
+    _call("pc_sqa_setup_bc", ctx, ptr(d, ctypes.c_int32), per.ctypes.data, ptr(j, ctypes.c_int8), P, T, len(g),
           ptr(g, ctypes.c_double))
 
 

@@ -87,6 +87,26 @@ def test_replica_correlation_matches_oracle_spins(pc, orc, dims, P, R, S, seed):
     assert (got[:, 0] == N).all()
 
 
+@pytest.mark.parametrize("dims,per,P,R,S", [((8, 8, 4), (0, 0, 1), 32, 4, 20),
+                                              ((4, 6, 8), (0, 1, 0), 16, 3, 30),
+                                              ((6, 6, 6), (0, 0, 0), 64, 2, 12)])
+def test_sqa_open_boundaries_bit_exact(pc, orc, dims, per, P, R, S):
+    """Open axes (the paper's instances are open in x and y): absent bonds,
+    odd in-slice fields at the faces, slice energies over the present bonds."""
+    J = W.ea_couplings(dims, W.SEED_INSTANCES, 77)
+    gamma = W.linear_gamma_schedule(S)
+    N = int(np.prod(dims))
+    E_ref, s_ref = orc.sqa_anneal(dims, J, P, 0.05, gamma, R, run0=5, seed=3, want_spins=True,
+                                  periodic=np.array(per, np.uint8))
+    ctx = pc.Context(0, 3)
+    pc.pc_sqa_setup_bc(ctx.h, dims, per, J, P, 0.05, gamma)
+    E, s = pc.pc_sqa_run(ctx.h, R, 5, P, N, want_spins=True)
+    ctx.close()
+    assert np.array_equal(s, s_ref)
+    assert np.array_equal(E, E_ref)
+    assert E[0, 0] == orc.energy(dims, J, s_ref[0, 0], periodic=per)
+
+
 def test_sqa_zero_sweeps_is_random_init(pc, orc):
     dims, P = (4, 4, 4), 16
     J = W.ea_couplings(dims, 1, 0)
