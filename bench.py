@@ -44,8 +44,8 @@ ALG_OPS_PER_FLIP = 14.0
 # DRAM bytes (read + write) of one full-size anneal launch, from an ncu
 # capture (profiles/sqa_kernel_L8_P64_R256.md), valid while the kernel
 # sources hash to TRAFFIC_SRC_SHA256; otherwise the bench reports null.
-TRAFFIC_BYTES = 1727232          # mean of 3 timed launches: 1.33, 1.66, 2.19 MB
-TRAFFIC_SRC_SHA256 = "4f1dd8f4eb41b717499833d32e80133264701ab7a0610dab00329242148a4289"
+TRAFFIC_BYTES = 2282752          # mean of 3 timed launches: 1.75, 2.44, 2.66 MB
+TRAFFIC_SRC_SHA256 = "c40b8108e9f86da26b7a1d47dad004d35658fbfccd261d14aa271528710655e3"
 TRAFFIC_SOURCES = ("paper_2503_10302_gb300/csrc/sqa.cu", "paper_2503_10302_gb300/csrc/device.cuh",
                    "paper_2503_10302_gb300/csrc/internal.h")
 WORKLOAD = f"DT-SQA 3D +-J L={L} periodic, P={P} slices, R={R} runs, T={T}, Gamma 3.0->1e-3 over {SWEEPS} sweeps"

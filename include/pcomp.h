@@ -91,16 +91,23 @@ int32_t pc_jperp_q(double gamma, int P, double T);
  * loaded before. */
 int pc_apt_load(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
                 const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0);
-/* As pc_apt_load with boundary conditions per axis: periodic [n][3] (host,
- * nonzero = periodic, NULL = all periodic).  An open axis has no bonds
- * across its ends (the paper's instances are open in x and y, Methods); its
- * forward couplings J[3 s + axis] at the far end are ignored.  Lengths stay
- * even on every axis (checkerboard layout).  Sites on an open face see a
- * local field I = sum of their present bonds, odd I included; energies sum
- * the present bonds only. */
+/* As pc_apt_load with boundary conditions per axis and vacancies:
+ * periodic [n][3] (host, nonzero = periodic, NULL = all periodic) and
+ * present [sum N] (host, 0 = vacancy / missing spin, NULL = none).
+ *   - An open axis has no bonds across its ends (the paper's instances are
+ *     open in x and y, Methods); its forward couplings J[3 s + axis] at the
+ *     far end are ignored.
+ *   - A vacancy has no bonds; it takes no part in ICM (never mismatched),
+ *     its spin in the returned states is meaningless, and the ICM
+ *     big-cluster rule compares with half of the spins present.  An odd
+ *     length on an open axis is a lattice padded to even length with a
+ *     vacant end layer.
+ *   - Lengths stay even on every axis (checkerboard layout).
+ *   - Sites on an open face or next to a vacancy see a local field over
+ *     their present bonds, odd I included; energies sum the present bonds. */
 int pc_apt_load_bc(pc_ctx *ctx, int n_inst, const int32_t *dims, const uint8_t *periodic,
-                   const int8_t *J, const int32_t *n_temps, const double *betas, int n_labels,
-                   uint32_t entry0);
+                   const uint8_t *present, const int8_t *J, const int32_t *n_temps,
+                   const double *betas, int n_labels, uint32_t entry0);
 /* n_swaps swap attempts; each = sweeps_per_swap checkerboard sweeps of all
  * replicas, replica energies, best-energy update, (icm != 0) one ICMop per
  * pair of labels of every temperature (two labels: the pair (0, 1); four:
@@ -179,12 +186,12 @@ int pc_apt_get_swap_table(pc_ctx *ctx, int inst, int pair, uint32_t *out, int ma
  * threshold tables and uploads everything. */
 int pc_sqa_setup(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, double T,
                  int n_sweeps, const double *gamma);
-/* As pc_sqa_setup with per-axis boundary conditions: periodic [3] (host,
- * nonzero = periodic, NULL = all periodic).  An open axis has no bonds
- * across its ends (the paper's instances are open in x and y); lengths stay
- * even; slice energies sum the present bonds. */
-int pc_sqa_setup_bc(pc_ctx *ctx, const int32_t *dims, const uint8_t *periodic, const int8_t *J,
-                    int P, double T, int n_sweeps, const double *gamma);
+/* As pc_sqa_setup with per-axis boundary conditions and vacancies:
+ * periodic [3] (host, nonzero = periodic, NULL = all periodic), present [N]
+ * (host, 0 = vacancy, NULL = none), as for pc_apt_load_bc.  Slice energies
+ * sum the present bonds. */
+int pc_sqa_setup_bc(pc_ctx *ctx, const int32_t *dims, const uint8_t *periodic, const uint8_t *present,
+                    const int8_t *J, int P, double T, int n_sweeps, const double *gamma);
 /* Threshold table of sweep s: out[3][7] for n = s_{k-1} + s_{k+1} in
  * {-2, 0, 2} and intra-slice field I = 2c - 6; *jq = J_perp in Q16.16. */
 int pc_sqa_get_table(pc_ctx *ctx, int sweep, uint32_t *out, int32_t *jq);

@@ -59,8 +59,8 @@ def lib():
         L.or_jperp_q.restype = ctypes.c_int32
         L.or_sqa_threshold.argtypes = [ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_int]
         L.or_sqa_threshold.restype = ctypes.c_uint32
-        L.or_energy.argtypes = [i32p, u8p, i8p, i8p, i8p, i64p]
-        L.or_apt_create.argtypes = [P(ctypes.c_void_p), ctypes.c_int, i32p, u8p, i8p, i8p, i32p,
+        L.or_energy.argtypes = [i32p, u8p, u8p, i8p, i8p, i8p, i64p]
+        L.or_apt_create.argtypes = [P(ctypes.c_void_p), ctypes.c_int, i32p, u8p, u8p, i8p, i8p, i32p,
                                     f64p, ctypes.c_int, u64, ctypes.c_uint32]
         L.or_apt_destroy.argtypes = [ctypes.c_void_p]
         L.or_apt_run.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -80,7 +80,7 @@ def lib():
                                          ctypes.c_double, ctypes.c_int, f64p, f64p, P(ctypes.c_int)]
         L.or_pilot_hist.argtypes = [i32p, u8p, i8p, i8p, ctypes.c_uint32, u64, ctypes.c_int, f64p,
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p]
-        L.or_sqa_anneal.argtypes = [i32p, u8p, i8p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+        L.or_sqa_anneal.argtypes = [i32p, u8p, u8p, i8p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                     f64p, ctypes.c_int, ctypes.c_uint32, u64, i64p, i8p, ctypes.c_int]
         _lib = L
     return _lib
@@ -133,13 +133,19 @@ def sqa_threshold(beta_eff: float, I: int, jq: int, n: int) -> int:
     return int(lib().or_sqa_threshold(beta_eff, I, jq, n))
 
 
-def energy(dims, J, spins, h=None, periodic=None) -> int:
+def _present(present) -> Optional[np.ndarray]:
+    return None if present is None else np.ascontiguousarray(np.asarray(present, dtype=np.uint8).ravel())
+
+
+def energy(dims, J, spins, h=None, periodic=None, present=None) -> int:
     d, p = _dims(dims), _per(periodic)
+    pr = _present(present)
     J = np.ascontiguousarray(J, dtype=np.int8)
     s = np.ascontiguousarray(spins, dtype=np.int8)
     hh = None if h is None else np.ascontiguousarray(h, dtype=np.int8)
     out = np.zeros(1, dtype=np.int64)
-    _check(lib().or_energy(_ptr(d, ctypes.c_int32), _ptr(p, ctypes.c_uint8), _ptr(J, ctypes.c_int8),
+    _check(lib().or_energy(_ptr(d, ctypes.c_int32), _ptr(p, ctypes.c_uint8), _ptr(pr, ctypes.c_uint8),
+                           _ptr(J, ctypes.c_int8),
                            _ptr(hh, ctypes.c_int8), _ptr(s, ctypes.c_int8), _ptr(out, ctypes.c_int64)),
            "energy")
     return int(out[0])
@@ -149,7 +155,7 @@ class Apt:
     """Batch of APT problems advanced in lockstep (Algorithm S2)."""
 
     def __init__(self, dims, J_list, betas_list, n_labels=2, seed=0, entry0=0,
-                 h_list=None, periodic=None):
+                 h_list=None, periodic=None, present_list=None):
         n = len(J_list)
         self.dims = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(n, 3))
         self.N = [int(np.prod(d)) for d in self.dims]
@@ -161,10 +167,12 @@ class Apt:
             np.asarray(periodic, dtype=np.uint8).reshape(n, 3))
         h = None if h_list is None else np.ascontiguousarray(
             np.concatenate([np.asarray(x, np.int8) for x in h_list]))
-        self._keep = (J, betas, per, h)
+        pres = None if present_list is None else np.ascontiguousarray(
+            np.concatenate([np.asarray(x, np.uint8).ravel() for x in present_list]))
+        self._keep = (J, betas, per, h, pres)
         handle = ctypes.c_void_p()
         _check(lib().or_apt_create(ctypes.byref(handle), n, _ptr(self.dims, ctypes.c_int32),
-                                   _ptr(per, ctypes.c_uint8), _ptr(J, ctypes.c_int8),
+                                   _ptr(per, ctypes.c_uint8), _ptr(pres, ctypes.c_uint8), _ptr(J, ctypes.c_int8),
                                    _ptr(h, ctypes.c_int8), _ptr(self.n_temps, ctypes.c_int32),
                                    _ptr(betas, ctypes.c_double), n_labels, ctypes.c_uint64(seed),
                                    ctypes.c_uint32(entry0)), "apt_create")
@@ -266,14 +274,17 @@ def pilot_hist(dims, J, betas, entry=0, seed=0, chains_per_beta=8, sweeps=256, b
     return counts
 
 
-def sqa_anneal(dims, J, P, T, gamma, R, run0=0, seed=0, want_spins=False, threads=0, periodic=None):
+def sqa_anneal(dims, J, P, T, gamma, R, run0=0, seed=0, want_spins=False, threads=0, periodic=None,
+               present=None):
     d, p = _dims(dims), _per(periodic)
+    pr = _present(present)
     J = np.ascontiguousarray(J, dtype=np.int8)
     gamma = np.ascontiguousarray(gamma, dtype=np.float64)
     N = int(np.prod(d))
     E = np.zeros((R, P), np.int64)
     s = np.zeros((R, P, N), np.int8) if want_spins else None
-    _check(lib().or_sqa_anneal(_ptr(d, ctypes.c_int32), _ptr(p, ctypes.c_uint8), _ptr(J, ctypes.c_int8),
+    _check(lib().or_sqa_anneal(_ptr(d, ctypes.c_int32), _ptr(p, ctypes.c_uint8), _ptr(pr, ctypes.c_uint8),
+                               _ptr(J, ctypes.c_int8),
                                P, T, len(gamma), _ptr(gamma, ctypes.c_double), R, ctypes.c_uint32(run0),
                                ctypes.c_uint64(seed), _ptr(E, ctypes.c_int64), _ptr(s, ctypes.c_int8),
                                threads), "sqa_anneal")

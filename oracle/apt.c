@@ -120,7 +120,7 @@ void or_apt_destroy(or_apt *a) {
 }
 
 int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *periodic,
-                  const int8_t *J, const int8_t *h, const int32_t *n_temps,
+                  const uint8_t *present, const int8_t *J, const int8_t *h, const int32_t *n_temps,
                   const double *betas, int n_labels, uint64_t seed, uint32_t entry0) {
   *out = NULL;
   if (n_inst < 1 || !(n_labels == 1 || n_labels == 2 || n_labels == 4)) return -1;
@@ -134,6 +134,7 @@ int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *
   for (int i = 0; i < n_inst; ++i) {
     apt_entry *e = &a->e[i];
     int rc = or_lat_init(&e->L, dims + 3 * i, periodic ? periodic + 3 * i : NULL);
+    if (!rc) rc = or_lat_set_present(&e->L, present ? present + joff : NULL);
     if (rc) { or_apt_destroy(a); return rc; }
     int N = e->L.N;
     e->T = n_temps[i];
@@ -206,8 +207,9 @@ static void best_update(apt_entry *e, int64_t sweeps) {
 static int icm_core(const or_lat *L, int8_t *sa, int8_t *sb, const uint32_t x[4],
                     int32_t *queue, uint8_t *inC, int64_t *size_out) {
   int N = L->N;
+  const uint8_t *vac = L->vac;
   int64_t nminus = 0;
-  for (int lin = 0; lin < N; ++lin) nminus += (sa[lin] != sb[lin]);
+  for (int lin = 0; lin < N; ++lin) nminus += (sa[lin] != sb[lin]) && !(vac && vac[lin]);
   *size_out = 0;
   if (nminus == 0) return 0;
   int64_t k = (int64_t)(((uint64_t)x[0] * (uint64_t)nminus) >> 32);
@@ -215,7 +217,7 @@ static int icm_core(const or_lat *L, int8_t *sa, int8_t *sb, const uint32_t x[4]
   int64_t cnt = 0;
   for (int c = 0; c < 2 && seed_site < 0; ++c)
     for (int lin = 0; lin < N; ++lin) {
-      if (or_colour(L, lin) != c || sa[lin] == sb[lin]) continue;
+      if (or_colour(L, lin) != c || sa[lin] == sb[lin] || (vac && vac[lin])) continue;
       if (cnt == k) { seed_site = lin; break; }
       ++cnt;
     }
@@ -233,7 +235,7 @@ static int icm_core(const or_lat *L, int8_t *sa, int8_t *sb, const uint32_t x[4]
     }
   }
   *size_out = tail;
-  if (2 * (int64_t)tail > (int64_t)N) {
+  if (2 * (int64_t)tail > (int64_t)L->nreal) {   /* more than half of the spins present */
     int8_t *sf = (x[1] & 1u) ? sb : sa;
     for (int lin = 0; lin < N; ++lin) sf[lin] = (int8_t)-sf[lin];
     return 2;

@@ -91,6 +91,7 @@ uint32_t or_sqa_threshold(double beta_eff, int64_t I, int32_t jq, int n) {
 /* ------------------------------------------------------------------------ */
 int or_lat_init(or_lat *L, const int32_t dims[3], const uint8_t periodic[3]) {
   memset(L, 0, sizeof(*L));
+  L->vac = NULL;
   for (int a = 0; a < 3; ++a) {
     if (dims[a] < 1 || dims[a] > 4096) return -1;
     L->L[a] = dims[a];
@@ -101,6 +102,7 @@ int or_lat_init(or_lat *L, const int32_t dims[3], const uint8_t periodic[3]) {
   }
   L->N = dims[0] * dims[1] * dims[2];
   if (L->N > (1 << 24)) return -1;
+  L->nreal = L->N;
   L->nb = (int32_t *)malloc(sizeof(int32_t) * 6 * (size_t)L->N);
   if (!L->nb) return -2;
   for (int lin = 0; lin < L->N; ++lin) {
@@ -122,9 +124,29 @@ int or_lat_init(or_lat *L, const int32_t dims[3], const uint8_t periodic[3]) {
   return 0;
 }
 
+int or_lat_set_present(or_lat *L, const uint8_t *present) {
+  if (!present) return 0;
+  L->vac = (uint8_t *)calloc((size_t)L->N, 1);
+  if (!L->vac) return -2;
+  L->nreal = 0;
+  for (int lin = 0; lin < L->N; ++lin) {
+    L->vac[lin] = present[lin] ? 0 : 1;
+    L->nreal += present[lin] ? 1 : 0;
+  }
+  /* a bond exists only between two present sites */
+  for (int lin = 0; lin < L->N; ++lin)
+    for (int d = 0; d < 6; ++d) {
+      int n = L->nb[6 * lin + d];
+      if (n >= 0 && (L->vac[lin] || L->vac[n])) L->nb[6 * lin + d] = -1;
+    }
+  return 0;
+}
+
 void or_lat_free(or_lat *L) {
   free(L->nb);
   L->nb = NULL;
+  free(L->vac);
+  L->vac = NULL;
 }
 
 int or_colour(const or_lat *L, int lin) {
@@ -144,7 +166,7 @@ int or_coupling(const or_lat *L, const int8_t *J, int lin, int dir) {
 
 /* Eq. synapse: I_i = sum_j J_ij s_j + h_i. */
 int64_t or_field(const or_lat *L, const int8_t *J, const int8_t *h, const int8_t *s, int lin) {
-  int64_t I = h ? h[lin] : 0;
+  int64_t I = (h && !(L->vac && L->vac[lin])) ? h[lin] : 0;
   for (int dir = 0; dir < 6; ++dir) {
     int n = L->nb[6 * lin + dir];
     if (n >= 0) I += (int64_t)or_coupling(L, J, lin, dir) * s[n];
@@ -161,16 +183,17 @@ int64_t or_energy_lat(const or_lat *L, const int8_t *J, const int8_t *h, const i
       int n = L->nb[6 * lin + 2 * a];
       if (n >= 0) E -= (int64_t)J[3 * lin + a] * s[lin] * s[n];
     }
-    if (h) E -= (int64_t)h[lin] * s[lin];
+    if (h && !(L->vac && L->vac[lin])) E -= (int64_t)h[lin] * s[lin];
   }
   return E;
 }
 
-int or_energy(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+int or_energy(const int32_t dims[3], const uint8_t periodic[3], const uint8_t *present, const int8_t *J,
               const int8_t *h, const int8_t *spin, int64_t *E_out) {
   or_lat L;
   int rc = or_lat_init(&L, dims, periodic);
   if (rc) return rc;
+  if ((rc = or_lat_set_present(&L, present))) { or_lat_free(&L); return rc; }
   *E_out = or_energy_lat(&L, J, h, spin);
   or_lat_free(&L);
   return 0;

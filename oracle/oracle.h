@@ -56,7 +56,9 @@ int32_t  or_jperp_q(double gamma, int P, double T);   /* round(2^16 J_perp) */
 uint32_t or_sqa_threshold(double beta_eff, int64_t I, int32_t jq, int n);
 
 /* Energy E = -sum_bonds J s s - sum h s of one configuration (int64). */
-int or_energy(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+/* present [N] (nullable): 0 marks a vacancy (missing spin) with no bonds;
+ * the same convention holds for or_apt_create and or_sqa_anneal. */
+int or_energy(const int32_t dims[3], const uint8_t periodic[3], const uint8_t *present, const int8_t *J,
               const int8_t *h, const int8_t *spin, int64_t *E_out);
 
 /* ---------------- adaptive parallel tempering (Algorithm S2) ---------------- */
@@ -64,6 +66,7 @@ typedef struct or_apt or_apt;
 /* n_inst problems; dims/periodic [n][3]; J concatenated [sum N][3];
    h concatenated [sum N] or NULL; n_temps[n]; betas concatenated. */
 int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *periodic,
+                  const uint8_t *present,
                   const int8_t *J, const int8_t *h, const int32_t *n_temps,
                   const double *betas, int n_labels, uint64_t seed, uint32_t entry0);
 void or_apt_destroy(or_apt *a);
@@ -117,7 +120,7 @@ int or_pilot_hist(const int32_t dims[3], const uint8_t periodic[3], const int8_t
 /* ---------------- DT-SQA (Eq. S.3, Algorithm S1) ---------------- */
 /* R runs (global ids run0..run0+R-1) of P slices; E_out [R][P] final classical
    slice energies; spins_out [R][P][N] or NULL. */
-int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const uint8_t *present, const int8_t *J,
                   int P, double T, int n_sweeps, const double *gamma, int R,
                   uint32_t run0, uint64_t seed, int64_t *E_out, int8_t *spins_out,
                   int threads);

@@ -7,10 +7,15 @@ typedef struct {
   int L[3];
   int per[3];
   int N;
-  int32_t *nb; /* [N][6] neighbour index along +x,-x,+y,-y,+z,-z; -1 if absent */
+  int32_t *nb;  /* [N][6] neighbour index along +x,-x,+y,-y,+z,-z; -1 if absent */
+  uint8_t *vac; /* [N] 1 at a vacancy (missing spin), or NULL */
+  int nreal;    /* spins present */
 } or_lat;
 
 int or_lat_init(or_lat *L, const int32_t dims[3], const uint8_t periodic[3]);
+/* Marks the sites with present[lin] == 0 as vacancies: they lose every bond
+ * (their own and their neighbours' towards them).  NULL leaves all present. */
+int or_lat_set_present(or_lat *L, const uint8_t *present);
 void or_lat_free(or_lat *L);
 int or_colour(const or_lat *L, int lin);
 int or_coupling(const or_lat *L, const int8_t *J, int lin, int dir);

@@ -75,7 +75,7 @@ static void sqa_run(const or_lat *L, const int8_t *J, int P, double T, int n_swe
   free(tab);
 }
 
-int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const int8_t *J,
+int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const uint8_t *present, const int8_t *J,
                   int P, double T, int n_sweeps, const double *gamma, int R,
                   uint32_t run0, uint64_t seed, int64_t *E_out, int8_t *spins_out,
                   int threads) {
@@ -84,7 +84,8 @@ int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const int8_t
     if (!(gamma[i] > 0)) return -1;
   or_lat L;
   int rc = or_lat_init(&L, dims, periodic);
-  if (rc) return rc;
+  if (!rc) rc = or_lat_set_present(&L, present);
+  if (rc) { or_lat_free(&L); return rc; }
   int64_t Imax = or_field_bound(&L, J, NULL);
   int N = L.N;
 #ifdef _OPENMP

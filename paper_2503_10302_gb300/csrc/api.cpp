@@ -63,21 +63,35 @@ std::vector<uint8_t> pack_jneg(const Lattice &lat, const int8_t *J) {
   return out;
 }
 
-std::vector<uint16_t> pack_jn16(const Lattice &lat, const uint8_t per[3], const int8_t *J, int *nbonds) {
+std::vector<uint16_t> pack_jn16(const Lattice &lat, const uint8_t per[3], const uint8_t *present,
+                                const int8_t *J, int *nbonds, int *nreal) {
   std::vector<uint8_t> signs = pack_jneg(lat, J);
   const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2];
   std::vector<uint16_t> out((size_t)lat.N);
-  int nb = 0;
+  int nb = 0, nr = 0;
   for (int s = 0; s < lat.N; ++s) {
     const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
     uint16_t miss = 0;   // bit d: direction d (+x, -x, +y, -y, +z, -z) absent
     if (!per[0]) miss |= (uint16_t)((x == 0 ? 2 : 0) | (x == Lx - 1 ? 1 : 0));
     if (!per[1]) miss |= (uint16_t)((y == 0 ? 8 : 0) | (y == Ly - 1 ? 4 : 0));
     if (!per[2]) miss |= (uint16_t)((z == 0 ? 32 : 0) | (z == Lz - 1 ? 16 : 0));
+    const bool vac = present && !present[s];
+    if (vac) {
+      miss = 0x3F;
+    } else if (present) {
+      const int xp = (x + 1) % Lx + Lx * (y + Ly * z), xm = (x + Lx - 1) % Lx + Lx * (y + Ly * z);
+      const int yp = x + Lx * ((y + 1) % Ly + Ly * z), ym = x + Lx * ((y + Ly - 1) % Ly + Ly * z);
+      const int zp = x + Lx * (y + Ly * ((z + 1) % Lz)), zm = x + Lx * (y + Ly * ((z + Lz - 1) % Lz));
+      const int nbr[6] = {xp, xm, yp, ym, zp, zm};
+      for (int d = 0; d < 6; ++d)
+        if (!present[nbr[d]]) miss |= (uint16_t)(1u << d);
+    }
     for (int d = 0; d < 6; d += 2) nb += ((miss >> d) & 1) ? 0 : 1;   // forward bonds
-    out[(size_t)s] = (uint16_t)(((uint16_t)signs[(size_t)s] & ~miss & 0x3F) | (miss << 8));
+    nr += vac ? 0 : 1;
+    out[(size_t)s] = (uint16_t)(((uint16_t)signs[(size_t)s] & ~miss & 0x3F) | (miss << 8) | (vac ? 0x8000 : 0));
   }
   *nbonds = nb;
+  *nreal = nr;
   return out;
 }
 
@@ -201,11 +215,11 @@ int pc_philox(pc_ctx *c, int64_t n, const uint32_t *ctr, uint32_t *out) {
 // ------------------------------------------------------------------ DT-SQA
 int pc_sqa_setup(pc_ctx *c, const int32_t *dims, const int8_t *J, int P, double T, int n_sweeps,
                  const double *gamma) {
-  return pc_sqa_setup_bc(c, dims, nullptr, J, P, T, n_sweeps, gamma);
+  return pc_sqa_setup_bc(c, dims, nullptr, nullptr, J, P, T, n_sweeps, gamma);
 }
 
-int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, const int8_t *J, int P,
-                    double T, int n_sweeps, const double *gamma) {
+int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, const uint8_t *present,
+                    const int8_t *J, int P, double T, int n_sweeps, const double *gamma) {
   if (!c || !J || (n_sweeps > 0 && !gamma)) return fail(PC_EINVAL, "NULL argument");
   Lattice lat;
   int rc = check_lattice(dims, J, &lat);
@@ -237,7 +251,8 @@ int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, con
       for (int e = 0; e < 13; ++e)
         q.table[(size_t)s * kSqaTab + e + 13 * m] = sqa_threshold(beta_eff, e - 6, jq, 2 * m - 2);
   }
-  std::vector<uint16_t> jn = pack_jn16(lat, per, J, &q.nbonds);
+  int nreal = 0;
+  std::vector<uint16_t> jn = pack_jn16(lat, per, present, J, &q.nbonds, &nreal);
   if ((rc = q.d_jneg.alloc(jn.size()))) return rc;
   if ((rc = q.d_table.alloc(q.table.size()))) return rc;
   // stage through pinned memory: one copy of each array

@@ -164,6 +164,7 @@ struct Cta {
   // split problems run as a cluster of two CTAs, rank 0 holding the colder half
   int Gu, Glp, split, rank;
   int nbonds;        // bonds present (3N with periodic axes)
+  int nreal;         // spins present (N without vacancies)
   uint32_t open;     // bit a: axis a open
   uint32_t ent;
   // thread chunking of the site loop: nch chunks of tpc threads, gc groups each
@@ -456,6 +457,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
           xb |= (nib_to_byte(x0) << (16 * h)) | (nib_to_byte(x1) << (16 * h + 8));
         }
       }
+      if (sh.jn[kk] & 0x8000u) xb = 0;   // a vacancy has no overlap: never a seed or member
       X[kk] = xb;
       V[kk] = 0u;
     }
@@ -664,7 +666,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
       const uint32_t bit = 1u << (4 * i);
       if (sh.inm[pb] == 0) {
         atomicAdd(&sh.m32[2], 1);
-      } else if (2 * size > N) {
+      } else if (2 * size > k.nreal) {   // more than half of the spins present
         atomicOr(&sh.imask[16 + (sh.ibit[pb] ? lb : la) * Gl + h], bit);   // one whole replica
         atomicAdd(&sh.m32[4], 1);
       } else {
@@ -929,6 +931,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.geo.mLy = P.mLy;
   k.geo.mLy2 = P.mLy2;
   k.nbonds = P.nbonds;
+  k.nreal = P.nreal;
   k.open = P.open;
   k.T = P.T;
   k.Tp = P.Tp;

@@ -64,10 +64,11 @@ int choose_nch(int H, int Gc, int tpb) {
   return best;
 }
 
-// pack_jn16's words in (colour, j) order: coupling signs (bits 0-5) and
-// absent bonds (bits 8-13) of site (c, j).  *nbonds receives the bonds present.
-std::vector<uint16_t> pack_jn_cj(const Lattice &lat, const uint8_t per[3], const int8_t *J, int *nbonds) {
-  std::vector<uint16_t> bylin = pack_jn16(lat, per, J, nbonds);
+// pack_jn16's words in (colour, j) order: coupling signs (bits 0-5), absent
+// bonds (bits 8-13) and the vacancy flag (bit 15) of site (c, j).
+std::vector<uint16_t> pack_jn_cj(const Lattice &lat, const uint8_t per[3], const uint8_t *present,
+                                 const int8_t *J, int *nbonds, int *nreal) {
+  std::vector<uint16_t> bylin = pack_jn16(lat, per, present, J, nbonds, nreal);
   const int Lx = lat.L[0], Ly = lat.L[1], H = lat.N / 2;
   std::vector<uint16_t> out((size_t)lat.N);
   for (int s = 0; s < lat.N; ++s) {
@@ -93,6 +94,7 @@ void unpack_spins(const AptProbDev &P, const uint32_t *words, int B, int8_t *out
 struct ProbSpec {
   Lattice lat;
   uint8_t per[3] = {1, 1, 1};     // periodic axes
+  const uint8_t *present = nullptr;   // [N] 0 = vacancy, or none
   const int8_t *J;
   int T, Tp, A, B;
   uint32_t ent;
@@ -133,8 +135,11 @@ int build_batch(pc_ctx *c, Batch &bt, const std::vector<ProbSpec> &specs, int n_
     P.spin_off = (uint32_t)spin_w;
     spin_w += (size_t)G * P.N;
     P.jneg_off = (uint32_t)jneg_b;
-    std::vector<uint16_t> jn = pack_jn_cj(s.lat, s.per, s.J, &P.nbonds);
-    P.open = (s.per[0] ? 0u : 1u) | (s.per[1] ? 0u : 2u) | (s.per[2] ? 0u : 4u);
+    std::vector<uint16_t> jn = pack_jn_cj(s.lat, s.per, s.present, s.J, &P.nbonds, &P.nreal);
+    // bits 0-2: open axes; bit 3: some other absent bond (a vacancy).  Any
+    // bit selects the sweep path that handles absent bonds.
+    P.open = (s.per[0] ? 0u : 1u) | (s.per[1] ? 0u : 2u) | (s.per[2] ? 0u : 4u) |
+             (P.nreal < P.N ? 8u : 0u);
     h_jneg.insert(h_jneg.end(), jn.begin(), jn.end());
     jneg_b += (size_t)P.N;
     P.pbit_off = (uint32_t)pbit_w;
@@ -352,6 +357,7 @@ struct AptImpl {
   int A = 0;
   std::vector<ProbSpec> specs;        // the loaded problems (J copied below)
   std::vector<std::vector<int8_t>> Jcopy;
+  std::vector<std::vector<uint8_t>> Pcopy;   // vacancy masks of the loaded problems
   bool icm_ok = false;
   // CUDA graph of one chunk of kChunkAttempts swap attempts
   cudaGraphExec_t exec = nullptr;
@@ -455,11 +461,12 @@ extern "C" {
 
 int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, const int32_t *n_temps,
                 const double *betas, int n_labels, uint32_t entry0) {
-  return pc_apt_load_bc(c, n_inst, dims, nullptr, J, n_temps, betas, n_labels, entry0);
+  return pc_apt_load_bc(c, n_inst, dims, nullptr, nullptr, J, n_temps, betas, n_labels, entry0);
 }
 
-int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *periodic, const int8_t *J,
-                   const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0) {
+int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *periodic,
+                   const uint8_t *present, const int8_t *J, const int32_t *n_temps, const double *betas,
+                   int n_labels, uint32_t entry0) {
   if (!c || !dims || !J || !n_temps || !betas) return fail(PC_EINVAL, "NULL argument");
   if (n_inst < 1) return fail(PC_EINVAL, "n_inst must be >= 1");
   if (!(n_labels == 1 || n_labels == 2 || n_labels == 4))
@@ -473,6 +480,7 @@ int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *pe
     int rc = check_lattice(dims + 3 * i, J + 3 * joff, &s.lat);
     if (rc) return rc;
     for (int ax = 0; ax < 3; ++ax) s.per[ax] = periodic ? (periodic[3 * i + ax] != 0) : 1;
+    s.present = present ? present + joff : nullptr;
     s.J = J + 3 * joff;
     s.T = n_temps[i];
     s.A = n_labels;
@@ -502,9 +510,14 @@ int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *pe
   c->apt.ready = false;
   im->A = n_labels;
   im->Jcopy.resize(specs.size());
+  im->Pcopy.resize(specs.size());
   for (size_t i = 0; i < specs.size(); ++i) {
     im->Jcopy[i].assign(specs[i].J, specs[i].J + 3 * (size_t)specs[i].lat.N);
     specs[i].J = im->Jcopy[i].data();
+    if (specs[i].present) {
+      im->Pcopy[i].assign(specs[i].present, specs[i].present + (size_t)specs[i].lat.N);
+      specs[i].present = im->Pcopy[i].data();
+    }
   }
   im->specs = specs;
   int rc = build_batch(c, im->bt, specs, 0);

@@ -14,8 +14,9 @@ struct AptProbDev {
   int Lx, Ly, Lz, N;
   uint32_t mhx, mLy;      // ceil(2^32 / (Lx/2)), ceil(2^32 / Ly)
   uint32_t mLy2;          // ceil(2^32 / (Ly/2))
-  uint32_t open;          // bit a: axis a has open boundaries (no wrap-around bonds)
+  uint32_t open;          // bit a < 3: axis a open (no wrap-around bonds); bit 3: vacancies
   int nbonds;             // bonds present (3N when every axis is periodic)
+  int nreal;              // spins present (N without vacancies)
   int T, Tp, A, B;        // temperatures, padded temperatures 8*ceil(T/8), labels,
                           // buffers (APT: A * Tp; ladder / pilot: chains)
   uint32_t ent;           // Philox entry id

@@ -29,9 +29,12 @@ struct Lattice {
 // (0:+x 1:-x 2:+y 3:-y 4:+z 5:-z) is -1.
 std::vector<uint8_t> pack_jneg(const Lattice &lat, const int8_t *J);
 // Per site (lin order): bits 0-5 coupling signs as pack_jneg for the bonds
-// present, bits 8-13 the absent bonds (an open axis has no bond across its
-// ends; per[a] = 0 marks axis a open).  *nbonds receives the bonds present.
-std::vector<uint16_t> pack_jn16(const Lattice &lat, const uint8_t per[3], const int8_t *J, int *nbonds);
+// present, bits 8-13 the absent bonds, bit 15 a vacancy.  A bond is absent
+// across the ends of an open axis (per[a] = 0) and next to a vacancy
+// (present[s] = 0, a missing spin; present may be NULL).  *nbonds and
+// *nreal receive the bonds and spins present.
+std::vector<uint16_t> pack_jn16(const Lattice &lat, const uint8_t per[3], const uint8_t *present,
+                                const int8_t *J, int *nbonds, int *nreal);
 int check_lattice(const int32_t *dims, const int8_t *J, Lattice *out);
 uint32_t recip32(uint32_t d);   // ceil(2^32 / d)
 uint32_t sqa_threshold(double beta_eff, int I, int32_t jq, int n);

@@ -281,21 +281,22 @@ __device__ __forceinline__ void anneal_span(const pc::SqaArgs &a, uint32_t *W, i
   } else {
     for (int idx = tid; idx < 2 * NB * N; idx += nt) W[idx] = __ldcg(gstate + idx);
   }
-  if (tid < pc::kSqaTab) {
-    const uint32_t t = s0 < a.S ? a.table[(size_t)s0 * pc::kSqaTab + tid] : 0u;
-    s_Tf[s0 & 1][tid] = t;
-    s_Th[s0 & 1][tid] = (uint16_t)(t >> 16);
+  for (int e = tid; e < pc::kSqaTab; e += nt) {   // small runs have fewer threads than entries
+    const uint32_t t = s0 < a.S ? a.table[(size_t)s0 * pc::kSqaTab + e] : 0u;
+    s_Tf[s0 & 1][e] = t;
+    s_Th[s0 & 1][e] = (uint16_t)(t >> 16);
   }
   __syncthreads();
 
   for (int sw = s0; sw < s1; ++sw) {
     // the transverse coupling of this sweep lives in its threshold table;
     // prefetch the next sweep's table into the other buffer
-    if (tid < pc::kSqaTab && sw + 1 < a.S) {
-      const uint32_t t = a.table[(size_t)(sw + 1) * pc::kSqaTab + tid];
-      s_Tf[(sw + 1) & 1][tid] = t;
-      s_Th[(sw + 1) & 1][tid] = (uint16_t)(t >> 16);
-    }
+    if (sw + 1 < a.S)
+      for (int e = tid; e < pc::kSqaTab; e += nt) {
+        const uint32_t t = a.table[(size_t)(sw + 1) * pc::kSqaTab + e];
+        s_Tf[(sw + 1) & 1][e] = t;
+        s_Th[(sw + 1) & 1][e] = (uint16_t)(t >> 16);
+      }
     const uint32_t boff = (sw & 1) ? 0x50505050u : 0u;   // 80 bytes: the odd sweep's table
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {

@@ -42,7 +42,7 @@ SIGNATURES = {
     "pc_swap_threshold": (c_u32, [c_dbl, c_i64]),
     "pc_jperp_q": (ctypes.c_int32, [c_dbl, c_int, c_dbl]),
     "pc_apt_load": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_i32p, c_f64p, c_int, c_u32]),
-    "pc_apt_load_bc": (c_int, [c_vp, c_int, c_i32p, c_vp, c_i8p, c_i32p, c_f64p, c_int, c_u32]),
+    "pc_apt_load_bc": (c_int, [c_vp, c_int, c_i32p, c_vp, c_vp, c_i8p, c_i32p, c_f64p, c_int, c_u32]),
     "pc_apt_run": (c_int, [c_vp, c_i64, c_int, c_int]),
     "pc_apt_set_joint_swap": (c_int, [c_vp, c_int]),
     "pc_apt_set_split": (c_int, [c_vp, c_int]),
@@ -60,7 +60,7 @@ SIGNATURES = {
     "pc_apt_get_pbit_table": (c_int, [c_vp, c_int, c_u32p]),
     "pc_apt_get_swap_table": (c_int, [c_vp, c_int, c_int, c_u32p, c_int, ctypes.POINTER(c_int)]),
     "pc_sqa_setup": (c_int, [c_vp, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p]),
-    "pc_sqa_setup_bc": (c_int, [c_vp, c_i32p, c_vp, c_i8p, c_int, c_dbl, c_int, c_f64p]),
+    "pc_sqa_setup_bc": (c_int, [c_vp, c_i32p, c_vp, c_vp, c_i8p, c_int, c_dbl, c_int, c_f64p]),
     "pc_sqa_get_table": (c_int, [c_vp, c_int, c_u32p, ctypes.POINTER(ctypes.c_int32)]),
     "pc_sqa_run": (c_int, [c_vp, c_int, c_u32, c_i64p, c_i8p]),
     "pc_sqa_run_dev": (c_int, [c_vp, c_int, c_u32, c_vp, c_vp]),
@@ -193,12 +193,15 @@ def pc_sqa_setup(ctx, dims, J, P: int, T: float, gamma) -> None:
           ptr(g, ctypes.c_double))
 
 
-def pc_sqa_setup_bc(ctx, dims, periodic, J, P: int, T: float, gamma) -> None:
-    """pc_sqa_setup with per-axis boundary conditions (periodic [3], nonzero = periodic)."""
+def pc_sqa_setup_bc(ctx, dims, periodic, J, P: int, T: float, gamma, present=None) -> None:
+    """pc_sqa_setup with per-axis boundary conditions (periodic [3], nonzero = periodic)
+    and an optional vacancy mask (present [N], 0 = vacancy)."""
     d, j = _dims(dims), _J(J)
-    per = np.ascontiguousarray(np.asarray(periodic, np.uint8).reshape(3))
+    per = None if periodic is None else np.ascontiguousarray(np.asarray(periodic, np.uint8).reshape(3))
+    pres = None if present is None else np.ascontiguousarray(np.asarray(present, np.uint8).ravel())
     g = np.ascontiguousarray(np.asarray(gamma, np.float64))
-    _call("pc_sqa_setup_bc", ctx, ptr(d, ctypes.c_int32), per.ctypes.data, ptr(j, ctypes.c_int8), P, T, len(g),
+    _call("pc_sqa_setup_bc", ctx, ptr(d, ctypes.c_int32), None if per is None else per.ctypes.data,
+          None if pres is None else pres.ctypes.data, ptr(j, ctypes.c_int8), P, T, len(g),
           ptr(g, ctypes.c_double))
 
 
@@ -265,15 +268,20 @@ def pc_apt_load(ctx, dims, J_list, betas_list, n_labels: int = 2, entry0: int = 
           ptr(nt, ctypes.c_int32), ptr(be, ctypes.c_double), n_labels, c_u32(entry0))
 
 
-def pc_apt_load_bc(ctx, dims, periodic, J_list, betas_list, n_labels: int = 2, entry0: int = 0) -> None:
-    """pc_apt_load with per-axis boundary conditions (periodic [n][3], nonzero = periodic)."""
+def pc_apt_load_bc(ctx, dims, periodic, J_list, betas_list, n_labels: int = 2, entry0: int = 0,
+                   present_list=None) -> None:
+    """pc_apt_load with per-axis boundary conditions (periodic [n][3], nonzero =
+    periodic) and optional vacancy masks (present_list: per instance [N], 0 = vacancy)."""
     d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(-1, 3))
-    per = np.ascontiguousarray(np.asarray(periodic, np.uint8).reshape(-1, 3))
+    per = None if periodic is None else np.ascontiguousarray(np.asarray(periodic, np.uint8).reshape(-1, 3))
+    pres = None if present_list is None else np.ascontiguousarray(
+        np.concatenate([np.asarray(p, np.uint8).ravel() for p in present_list]))
     J = _concat_J(J_list)
     nt = np.ascontiguousarray([len(b) for b in betas_list], dtype=np.int32)
     be = np.ascontiguousarray(np.concatenate([np.asarray(b, np.float64) for b in betas_list]))
-    _call("pc_apt_load_bc", ctx, len(J_list), ptr(d, ctypes.c_int32), per.ctypes.data, ptr(J, ctypes.c_int8),
-          ptr(nt, ctypes.c_int32), ptr(be, ctypes.c_double), n_labels, c_u32(entry0))
+    _call("pc_apt_load_bc", ctx, len(J_list), ptr(d, ctypes.c_int32), None if per is None else per.ctypes.data,
+          None if pres is None else pres.ctypes.data, ptr(J, ctypes.c_int8), ptr(nt, ctypes.c_int32),
+          ptr(be, ctypes.c_double), n_labels, c_u32(entry0))
 
 
 def pc_apt_set_joint_swap(ctx, joint: bool) -> None:

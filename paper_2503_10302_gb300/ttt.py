@@ -124,19 +124,20 @@ def features(dims, J_list, seed=13, entry0=0, chains_per_beta=8, sweeps=256, bur
 
 
 def c3_time_to_target(n_inst=64, L=12, rho=1e-3, best_runs=10, best_sweeps=100000,
-                      max_sweeps=100000) -> Dict:
-    """64 instances of L = 12, adaptive ladder resampled to 32 x 2 labels."""
+                      max_sweeps=100000, labels=2) -> Dict:
+    """64 instances of L = 12, adaptive ladder resampled to 32 temperatures x
+    `labels` ICM labels (4: the paper's setting, 128 replicas per problem)."""
     dims = np.tile(np.array([L, L, L], np.int32), (n_inst, 1))
     J = [W.ea_couplings((L, L, L), W.SEED_INSTANCES, i) for i in range(n_inst)]
     ladders, t_lad = adaptive_ladders(dims, J)
     betas = [pcomp.pc_resample_ladder(b, 32) for b in ladders]
-    batch = W.AptBatch(dims, J, betas, 2)
-    e_best = best_energies(batch, best_runs, best_sweeps)
+    batch = W.AptBatch(dims, J, betas, labels)
+    e_best = best_energies(W.AptBatch(dims, J, betas, 2), best_runs, best_sweeps)
     N = L ** 3
     targets = np.floor(e_best + rho * N).astype(np.int64)
     hit, t_sweep, total = run_to_target(batch, targets, max_sweeps)
     ok = hit >= 0
-    return {"instances": n_inst, "L": L, "rho_target": rho, "ladder_seconds": t_lad,
+    return {"instances": n_inst, "L": L, "labels": labels, "rho_target": rho, "ladder_seconds": t_lad,
             "ladder_lengths": [len(b) for b in ladders], "apt_seconds_per_sweep": t_sweep,
             "hit_fraction": float(ok.mean()),
             "median_hit_sweep": float(np.median(hit[ok])) if ok.any() else None,
@@ -341,6 +342,7 @@ def main():
     ap.add_argument("--best-runs", type=int, default=10)
     ap.add_argument("--best-sweeps", type=int, default=20000)
     ap.add_argument("--max-sweeps", type=int, default=100000)
+    ap.add_argument("--labels", type=int, default=2, choices=[2, 4], help="ICM labels (c3)")
     args = ap.parse_args()
     out = {}
     if args.what in ("throughput", "all"):
@@ -355,7 +357,7 @@ def main():
     if args.what in ("c2", "all"):
         out["c2"] = c2_residual_vs_R()
     if args.what in ("c3", "all"):
-        out["c3"] = c3_time_to_target()
+        out["c3"] = c3_time_to_target(labels=args.labels)
     if args.what in ("c4", "all"):
         out["c4"] = c4_mixed_time_to_target()
     if args.what in ("c5", "all"):

@@ -129,3 +129,29 @@ def mlp_init(sizes: Sequence[int], seed: int) -> List[Tuple[np.ndarray, np.ndarr
         W = rng.uniform(-bound, bound, size=(fan_out, fan_in)).astype(np.float32)
         params.append((W, np.zeros(fan_out, dtype=np.float32)))
     return params
+
+
+def pad_odd_open(dims, periodic, J) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """An instance with odd lengths on open axes (e.g. the paper's 15 x 15 x 12,
+    open in x and y) as an even-length lattice whose extra end layers are
+    vacancies.  Returns (padded dims, present [N_pad], J [N_pad][3]); the
+    original site (x, y, z) keeps its coordinates.  Odd periodic lengths are
+    not bipartite and are refused."""
+    dims = [int(v) for v in dims]
+    per = [int(bool(v)) for v in periodic]
+    for a in range(3):
+        if dims[a] % 2 and per[a]:
+            raise ValueError("odd length on a periodic axis: the lattice is not bipartite")
+    pd = [v + (v % 2) for v in dims]
+    J = np.asarray(J, np.int8).reshape(dims[2], dims[1], dims[0], 3)
+    Jp = np.ones((pd[2], pd[1], pd[0], 3), np.int8)
+    Jp[: dims[2], : dims[1], : dims[0]] = J
+    present = np.zeros((pd[2], pd[1], pd[0]), np.uint8)
+    present[: dims[2], : dims[1], : dims[0]] = 1
+    return np.array(pd, np.int32), present.ravel(), Jp.reshape(-1, 3)
+
+
+def random_vacancies(dims, fraction: float, seed: int) -> np.ndarray:
+    """present [N] with about `fraction` of the sites missing (seeded)."""
+    rng = np.random.Generator(np.random.Philox(key=[seed, 0xEEEE]))
+    return (rng.random(int(np.prod(dims))) >= fraction).astype(np.uint8)

@@ -250,6 +250,35 @@ def test_four_labels_thirty_two_temperatures(pc, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("labels,pref", [(2, 1), (2, 2), (4, 2)])
+def test_vacancies_and_odd_open_lattices(pc, orc, labels, pref):
+    """Missing spins (random vacancies) and odd open lengths padded with a
+    vacant layer (5 x 7 x 4, and the paper's 15 x 15 x 12 shape), with ICM,
+    one-CTA and two-CTA placements."""
+    cases = [((8, 8, 8), (1, 1, 1), None), ((5, 7, 4), (0, 0, 1), "odd"), ((6, 6, 6), (0, 1, 1), None),
+             ((15, 15, 12), (0, 0, 1), "odd")]
+    dims, per, J, present, temps = [], [], [], [], []
+    for i, (d, p_, kind) in enumerate(cases):
+        Ji = W.ea_couplings(d, 13, i)
+        if kind == "odd":
+            pd, pres, Jp = W.pad_odd_open(d, p_, Ji)
+        else:
+            pd, pres, Jp = np.array(d, np.int32), W.random_vacancies(d, 0.08, i), Ji
+        dims.append(pd); per.append(p_); J.append(Jp); present.append(pres)
+        temps.append(16 if labels == 4 else 12 + 4 * i)
+    dims = np.array(dims, np.int32)
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, labels)
+    ctx = pc.Context(0, 43)
+    pc.pc_apt_load_bc(ctx.h, dims, per, J, betas, labels, 0, present_list=present)
+    pc.pc_apt_set_split(ctx.h, pref)
+    apt = orc.Apt(dims, J, betas, labels, seed=43, periodic=np.array(per, np.uint8), present_list=present)
+    pc.pc_apt_run(ctx.h, 30, 1, True)
+    apt.run(30, threads=8)
+    _compare(pc, apt, ctx, b)
+    ctx.close()
+
+
 def test_resume_and_chunking(pc, orc):
     """140 attempts in one call (graph replay + remainder) == 60 + 80."""
     b = W.apt_single(L=6, n_temps=10)

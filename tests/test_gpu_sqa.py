@@ -107,6 +107,26 @@ def test_sqa_open_boundaries_bit_exact(pc, orc, dims, per, P, R, S):
     assert E[0, 0] == orc.energy(dims, J, s_ref[0, 0], periodic=per)
 
 
+@pytest.mark.parametrize("dims,per,kind", [((8, 8, 8), (1, 1, 1), "vac"), ((7, 5, 4), (0, 0, 1), "odd")])
+def test_sqa_vacancies_and_odd_open_lattice(pc, orc, dims, per, kind):
+    """Missing spins and an odd open lattice padded with a vacant layer."""
+    J = W.ea_couplings(dims, W.SEED_INSTANCES, 78)
+    if kind == "odd":
+        dims, present, J = W.pad_odd_open(dims, per, J)
+    else:
+        present = W.random_vacancies(dims, 0.1, 5)
+    gamma = W.linear_gamma_schedule(15)
+    N = int(np.prod(dims))
+    E_ref, s_ref = orc.sqa_anneal(dims, J, 32, 0.05, gamma, 3, run0=2, seed=4, want_spins=True,
+                                  periodic=np.array(per, np.uint8), present=present)
+    ctx = pc.Context(0, 4)
+    pc.pc_sqa_setup_bc(ctx.h, dims, per, J, 32, 0.05, gamma, present=present)
+    E, s = pc.pc_sqa_run(ctx.h, 3, 2, 32, N, want_spins=True)
+    ctx.close()
+    assert np.array_equal(s, s_ref)
+    assert np.array_equal(E, E_ref)
+
+
 def test_sqa_zero_sweeps_is_random_init(pc, orc):
     dims, P = (4, 4, 4), 16
     J = W.ea_couplings(dims, 1, 0)

@@ -243,6 +243,87 @@ def test_gibbs_sampler_matches_enumeration_periodic(orc, beta):
     assert abs(m - (p * E).sum()) < 5 * se + 1e-9
 
 
+def test_vacancies_remove_their_bonds(orc):
+    """A vacancy (missing spin) has no bonds: the lattice energy equals the
+    explicit graph energy over the bonds between present sites, whatever
+    the vacancy spins are."""
+    rng = np.random.default_rng(3)
+    for dims, per in (((4, 4, 4), (1, 1, 1)), ((4, 2, 6), (0, 1, 0)), ((6, 4, 2), (0, 0, 1))):
+        J = W.ea_couplings(dims, 61, 0)
+        N = int(np.prod(dims))
+        present = (rng.random(N) > 0.2).astype(np.uint8)
+        edges = [e for e in X.lattice_edges(dims, per) if present[e[0]] and present[e[1]]]
+        for _ in range(5):
+            s = rng.choice(np.array([-1, 1], np.int8), size=N)
+            want = int(X.energies(edges, J, None, s[None, :])[0])
+            assert orc.energy(dims, J, s, periodic=per, present=present) == want
+            s2 = s.copy()
+            s2[present == 0] *= -1          # vacancy spins do not count
+            assert orc.energy(dims, J, s2, periodic=per, present=present) == want
+
+
+def test_gibbs_sampler_with_vacancies_matches_enumeration(orc):
+    """The present spins of a lattice with vacancies sample exp(-beta E) of
+    the graph without them (12 present spins of a 2x2x4 lattice)."""
+    dims, per = (2, 2, 4), (0, 0, 1)
+    J = W.ea_couplings(dims, 62, 0)
+    present = np.ones(16, np.uint8)
+    present[[3, 9, 14, 6]] = 0
+    keep = np.flatnonzero(present)
+    beta = 0.7
+    edges = [e for e in X.lattice_edges(dims, per) if present[e[0]] and present[e[1]]]
+    n = 32
+    apt = orc.Apt(np.tile(dims, (n, 1)), [J] * n, [np.array([beta])] * n, n_labels=1, seed=8,
+                  periodic=np.tile(per, (n, 1)), present_list=[present] * n)
+    apt.run(20, icm=False)
+    Es = []
+    for _ in range(1500):
+        apt.run(1, icm=False)
+        for i in range(0, n, 2):
+            s, e, _ = apt.state(i)
+            Es.append(e[0])
+    # exact mean energy over the 2^12 states of the present spins
+    sub = X.all_states(len(keep))
+    states = np.ones((sub.shape[0], 16), np.int8)
+    states[:, keep] = sub
+    E = X.energies(edges, J, None, states)
+    p = X.boltzmann(E, beta)
+    m, se = X.batch_mean_stderr(np.array(Es, float).reshape(1500, n // 2).T.ravel())
+    assert abs(m - (p * E).sum()) < 5 * se
+
+
+def test_icm_with_vacancies_keeps_product_boltzmann(orc):
+    """Two labels with ICM on a lattice with vacancies: each replica keeps
+    exp(-beta E) of the graph without the missing spins."""
+    dims, per = (2, 2, 4), (1, 1, 1)
+    J = W.ea_couplings(dims, 63, 0)
+    present = np.ones(16, np.uint8)
+    present[[2, 13]] = 0
+    keep = np.flatnonzero(present)
+    beta = 0.9
+    edges = [e for e in X.lattice_edges(dims, per) if present[e[0]] and present[e[1]]]
+    sub = X.all_states(len(keep))
+    states = np.ones((sub.shape[0], 16), np.int8)
+    states[:, keep] = sub
+    E = X.energies(edges, J, None, states)
+    p = X.boltzmann(E, beta)
+    n = 24
+    apt = orc.Apt(np.tile(dims, (n, 1)), [J] * n, [np.array([beta])] * n, n_labels=2, seed=5,
+                  present_list=[present] * n)
+    apt.run(10, icm=True)
+    Ea = []
+    for _ in range(1200):
+        apt.run(1, icm=True)
+        for i in range(n):
+            s, e, _ = apt.state(i)
+            assert e[0] == orc.energy(dims, J, s[0], present=present)
+            Ea.append(e[0])
+    _, _, icm = apt.stats(0)
+    assert icm[1] + icm[2] > 0
+    m, se = X.batch_mean_stderr(np.array(Ea, float).reshape(1200, n).T.ravel())
+    assert abs(m - (p * E).sum()) < 5 * se
+
+
 def test_gibbs_sampler_open_lattice_with_field(orc):
     """Open x, y / periodic z with integer fields: 16 spins, exact by enumeration."""
     dims, per = (2, 2, 4), (0, 0, 1)
@@ -682,3 +763,20 @@ def test_pilot_histogram_totals_and_limits(orc):
     zero = np.zeros((64, 3), np.int8)
     c = orc.pilot_hist(dims, zero, np.array([1.0]), chains_per_beta=2, sweeps=5, burn=0)
     assert c[0, 63] == 10             # E = 0 -> last bin
+
+
+def test_odd_open_lattice_equals_padded_lattice_with_vacancies(orc):
+    """An odd open length (the paper's 15 x 15 x 12 is open in x, y) padded
+    with a vacant end layer has the same energy function as the odd
+    lattice itself."""
+    rng = np.random.default_rng(9)
+    for dims, per in (((5, 7, 4), (0, 0, 1)), ((3, 3, 3), (0, 0, 0)), ((15, 15, 12), (0, 0, 1))):
+        J = W.ea_couplings(dims, 64, 0)
+        pd, present, Jp = W.pad_odd_open(dims, per, J)
+        for _ in range(3):
+            s = rng.choice(np.array([-1, 1], np.int8), size=int(np.prod(dims)))
+            sp = rng.choice(np.array([-1, 1], np.int8), size=int(np.prod(pd)))
+            sp.reshape(pd[2], pd[1], pd[0])[: dims[2], : dims[1], : dims[0]] = s.reshape(dims[2], dims[1], dims[0])
+            assert orc.energy(dims, J, s, periodic=per) == orc.energy(pd, Jp, sp, periodic=per, present=present)
+    with pytest.raises(ValueError):
+        W.pad_odd_open((5, 4, 4), (1, 1, 1), W.ea_couplings((5, 4, 4), 1, 0))
