@@ -16,7 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
-_SRCS = ["core.c", "apt.c", "sqa.c"]
+_SRCS = ["core.c", "apt.c", "sqa.c", "graph.c"]
 
 TAG_APT_INIT, TAG_APT_SWEEP, TAG_APT_REFINE, TAG_SWAP, TAG_ICM = 1, 2, 3, 4, 5
 TAG_LAD_INIT, TAG_LAD_SWEEP, TAG_LAD_REFINE = 6, 7, 8
@@ -82,6 +82,24 @@ def lib():
                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64p]
         L.or_sqa_anneal.argtypes = [i32p, u8p, u8p, i8p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                     f64p, ctypes.c_int, ctypes.c_uint32, u64, i64p, i8p, ctypes.c_int]
+        L.or_graph_check.argtypes = [ctypes.c_int, i32p, i32p, i8p]
+        L.or_dsatur.argtypes = [ctypes.c_int, i32p, i32p, i32p, P(ctypes.c_int)]
+        L.or_graph_sqa_colouring.argtypes = [ctypes.c_int, i32p, ctypes.c_int, i32p, P(ctypes.c_int)]
+        L.or_graph_energy.argtypes = [ctypes.c_int, i32p, i32p, i8p, i8p, i8p, i64p]
+        L.or_gapt_create.argtypes = [P(ctypes.c_void_p), ctypes.c_int, i32p, i32p, i32p, i8p, i8p, i32p,
+                                     i32p, f64p, ctypes.c_int, u64, ctypes.c_uint32]
+        L.or_gapt_destroy.argtypes = [ctypes.c_void_p]
+        L.or_gapt_run.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.or_gapt_set_joint_swap.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_gapt_set_target.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]
+        L.or_gapt_state.argtypes = [ctypes.c_void_p, ctypes.c_int, i8p, i64p, i32p]
+        L.or_gapt_best.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p, i32p, i64p, i8p]
+        L.or_gapt_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p, i64p]
+        L.or_gicm_apply.argtypes = [ctypes.c_int, i32p, i32p, i32p, i8p, i8p, u64, ctypes.c_uint32,
+                                    ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, i64p]
+        L.or_gsqa_anneal.argtypes = [ctypes.c_int, i32p, i32p, i8p, i8p, i32p, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, f64p, ctypes.c_int, ctypes.c_uint32, u64, i64p, i8p,
+                                     ctypes.c_int]
         _lib = L
     return _lib
 
@@ -288,4 +306,154 @@ def sqa_anneal(dims, J, P, T, gamma, R, run0=0, seed=0, want_spins=False, thread
                                P, T, len(gamma), _ptr(gamma, ctypes.c_double), R, ctypes.c_uint32(run0),
                                ctypes.c_uint64(seed), _ptr(E, ctypes.c_int64), _ptr(s, ctypes.c_int8),
                                threads), "sqa_anneal")
+    return (E, s) if want_spins else E
+
+
+# ---------------------------------------------------------------- general graphs
+TAG_G_INIT, TAG_G_SWEEP, TAG_G_REFINE, TAG_G_SWAP, TAG_G_ICM = 15, 16, 17, 18, 19
+TAG_GS_INIT, TAG_GS_SWEEP, TAG_GS_REFINE = 20, 21, 22
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).ravel())
+
+
+def _i8(a) -> Optional[np.ndarray]:
+    return None if a is None else np.ascontiguousarray(np.asarray(a, dtype=np.int8).ravel())
+
+
+def graph_check(rp, col, w=None) -> bool:
+    rp, col, w = _i32(rp), _i32(col), _i8(w)
+    return lib().or_graph_check(len(rp) - 1, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                _ptr(w, ctypes.c_int8)) == 0
+
+
+def dsatur(rp, col) -> Tuple[np.ndarray, int]:
+    """DSATUR colouring of a CSR graph: (colour [n], number of colours)."""
+    rp, col = _i32(rp), _i32(col)
+    n = len(rp) - 1
+    out = np.zeros(n, np.int32)
+    C = ctypes.c_int(0)
+    _check(lib().or_dsatur(n, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                           _ptr(out, ctypes.c_int32), ctypes.byref(C)), "dsatur")
+    return out, C.value
+
+
+def graph_sqa_colouring(colour, P: int) -> Tuple[np.ndarray, int]:
+    """Colours [P][n] of the replicated DT-SQA network and their count."""
+    colour = _i32(colour)
+    n = len(colour)
+    out = np.zeros((P, n), np.int32)
+    C = ctypes.c_int(0)
+    _check(lib().or_graph_sqa_colouring(n, _ptr(colour, ctypes.c_int32), P, _ptr(out, ctypes.c_int32),
+                                        ctypes.byref(C)), "graph_sqa_colouring")
+    return out, C.value
+
+
+def graph_energy(rp, col, w, spins, h=None) -> int:
+    rp, col, w, hh = _i32(rp), _i32(col), _i8(w), _i8(h)
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    out = np.zeros(1, np.int64)
+    _check(lib().or_graph_energy(len(rp) - 1, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                 _ptr(w, ctypes.c_int8), _ptr(hh, ctypes.c_int8), _ptr(s, ctypes.c_int8),
+                                 _ptr(out, ctypes.c_int64)), "graph_energy")
+    return int(out[0])
+
+
+class GApt:
+    """Batch of APT problems on general graphs (Algorithm S2 with a colormap).
+
+    graphs: list of (rp, col, w) CSR triples; colours: list of colour arrays or
+    None (DSATUR); slot order r * A + a as in :class:`Apt`.
+    """
+
+    def __init__(self, graphs, betas_list, n_labels=2, seed=0, entry0=0, h_list=None, colours=None):
+        n = len(graphs)
+        self.nv = [len(g[0]) - 1 for g in graphs]
+        nv = np.ascontiguousarray(self.nv, dtype=np.int32)
+        rp = np.ascontiguousarray(np.concatenate([_i32(g[0]) for g in graphs]))
+        col = np.ascontiguousarray(np.concatenate([_i32(g[1]) for g in graphs]))
+        w = np.ascontiguousarray(np.concatenate([_i8(g[2]) for g in graphs]))
+        h = None if h_list is None else np.ascontiguousarray(np.concatenate([_i8(x) for x in h_list]))
+        cl = None if colours is None else np.ascontiguousarray(np.concatenate([_i32(c) for c in colours]))
+        self.n_temps = np.ascontiguousarray([len(b) for b in betas_list], dtype=np.int32)
+        betas = np.ascontiguousarray(np.concatenate([np.asarray(b, np.float64) for b in betas_list]))
+        self.n_labels = n_labels
+        self._keep = (nv, rp, col, w, h, cl, betas)
+        handle = ctypes.c_void_p()
+        _check(lib().or_gapt_create(ctypes.byref(handle), n, _ptr(nv, ctypes.c_int32), _ptr(rp, ctypes.c_int32),
+                                    _ptr(col, ctypes.c_int32), _ptr(w, ctypes.c_int8), _ptr(h, ctypes.c_int8),
+                                    _ptr(cl, ctypes.c_int32), _ptr(self.n_temps, ctypes.c_int32),
+                                    _ptr(betas, ctypes.c_double), n_labels, ctypes.c_uint64(seed),
+                                    ctypes.c_uint32(entry0)), "gapt_create")
+        self.h = handle
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.or_gapt_destroy(self.h)
+            self.h = None
+
+    def run(self, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True, threads: int = 0):
+        _check(lib().or_gapt_run(self.h, n_swaps, sweeps_per_swap, int(icm), threads), "gapt_run")
+
+    def set_joint_swap(self, joint: bool):
+        _check(lib().or_gapt_set_joint_swap(self.h, int(bool(joint))), "gapt_set_joint_swap")
+
+    def set_target(self, prob: int, e_target: int):
+        _check(lib().or_gapt_set_target(self.h, prob, e_target), "gapt_set_target")
+
+    def state(self, prob: int):
+        B = int(self.n_temps[prob]) * self.n_labels
+        s = np.zeros((B, self.nv[prob]), np.int8)
+        E = np.zeros(B, np.int64)
+        c = np.zeros(self.nv[prob], np.int32)
+        _check(lib().or_gapt_state(self.h, prob, _ptr(s, ctypes.c_int8), _ptr(E, ctypes.c_int64),
+                                   _ptr(c, ctypes.c_int32)), "gapt_state")
+        return s, E, c
+
+    def best(self, prob: int):
+        E = np.zeros(1, np.int64); sw = np.zeros(1, np.int64); hit = np.zeros(1, np.int64)
+        b = np.zeros(1, np.int32); s = np.zeros(self.nv[prob], np.int8)
+        _check(lib().or_gapt_best(self.h, prob, _ptr(E, ctypes.c_int64), _ptr(sw, ctypes.c_int64),
+                                  _ptr(b, ctypes.c_int32), _ptr(hit, ctypes.c_int64),
+                                  _ptr(s, ctypes.c_int8)), "gapt_best")
+        return dict(E=int(E[0]), sweep=int(sw[0]), buf=int(b[0]), hit_sweep=int(hit[0]), spins=s)
+
+    def stats(self, prob: int):
+        T, A = int(self.n_temps[prob]), self.n_labels
+        att = np.zeros((max(T - 1, 0), A), np.int64); acc = np.zeros_like(att)
+        icm = np.zeros(3, np.int64)
+        _check(lib().or_gapt_stats(self.h, prob, _ptr(att, ctypes.c_int64), _ptr(acc, ctypes.c_int64),
+                                   _ptr(icm, ctypes.c_int64)), "gapt_stats")
+        return att, acc, icm
+
+
+def gicm_apply(rp, col, colour, sa, sb, seed=0, entry=0, r=0, t=0, p=0):
+    """One ICMop on copies of (sa, sb) on a graph; returns (branch, size, sa', sb')."""
+    rp, col, colour = _i32(rp), _i32(col), _i32(colour)
+    a = np.ascontiguousarray(sa, dtype=np.int8).copy()
+    b = np.ascontiguousarray(sb, dtype=np.int8).copy()
+    size = np.zeros(1, np.int64)
+    br = _check(lib().or_gicm_apply(len(rp) - 1, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                    _ptr(colour, ctypes.c_int32), _ptr(a, ctypes.c_int8), _ptr(b, ctypes.c_int8),
+                                    ctypes.c_uint64(seed), ctypes.c_uint32(entry), ctypes.c_uint32(r),
+                                    ctypes.c_uint32(t), ctypes.c_uint32(p), _ptr(size, ctypes.c_int64)),
+                "gicm_apply")
+    return br, int(size[0]), a, b
+
+
+def gsqa_anneal(rp, col, w, P, T, gamma, R, run0=0, seed=0, h=None, colour=None, want_spins=False,
+                threads=0):
+    """DT-SQA on a graph: final slice energies [R][P] (and spins [R][P][n])."""
+    rp, col, w, hh = _i32(rp), _i32(col), _i8(w), _i8(h)
+    cl = None if colour is None else _i32(colour)
+    gamma = np.ascontiguousarray(gamma, dtype=np.float64)
+    n = len(rp) - 1
+    E = np.zeros((R, P), np.int64)
+    s = np.zeros((R, P, n), np.int8) if want_spins else None
+    _check(lib().or_gsqa_anneal(n, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32), _ptr(w, ctypes.c_int8),
+                                _ptr(hh, ctypes.c_int8), _ptr(cl, ctypes.c_int32), P, T, len(gamma),
+                                _ptr(gamma, ctypes.c_double), R, ctypes.c_uint32(run0), ctypes.c_uint64(seed),
+                                _ptr(E, ctypes.c_int64), _ptr(s, ctypes.c_int8), threads), "gsqa_anneal")
     return (E, s) if want_spins else E

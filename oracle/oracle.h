@@ -41,7 +41,10 @@ enum {
   OR_TAG_SWAP = 4, OR_TAG_ICM = 5,
   OR_TAG_LAD_INIT = 6, OR_TAG_LAD_SWEEP = 7, OR_TAG_LAD_REFINE = 8,
   OR_TAG_PIL_INIT = 9, OR_TAG_PIL_SWEEP = 10, OR_TAG_PIL_REFINE = 11,
-  OR_TAG_SQA_INIT = 12, OR_TAG_SQA_SWEEP = 13, OR_TAG_SQA_REFINE = 14
+  OR_TAG_SQA_INIT = 12, OR_TAG_SQA_SWEEP = 13, OR_TAG_SQA_REFINE = 14,
+  /* general sparse graphs (graph.c) */
+  OR_TAG_G_INIT = 15, OR_TAG_G_SWEEP = 16, OR_TAG_G_REFINE = 17, OR_TAG_G_SWAP = 18,
+  OR_TAG_G_ICM = 19, OR_TAG_GS_INIT = 20, OR_TAG_GS_SWEEP = 21, OR_TAG_GS_REFINE = 22
 };
 
 /* Philox4x32-10 on one counter. */
@@ -124,6 +127,77 @@ int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const uint8_
                   int P, double T, int n_sweeps, const double *gamma, int R,
                   uint32_t run0, uint64_t seed, int64_t *E_out, int8_t *spins_out,
                   int threads);
+
+/* ---------------- general sparse graphs (graph.c) ---------------- */
+/* A graph of n p-bits is given in CSR form: the neighbours of v are
+ * col[rp[v] .. rp[v+1]-1] with integer weights w (J_vu, nonzero), listed in
+ * both directions with equal weights, no self-loops, no repeats; biases h
+ * [n] or NULL.  Couplings are integers: fixed-point weights with f
+ * fractional bits are passed as integers with beta scaled by 2^-f.
+ *
+ * Colour classes: a proper colouring colour[v] in [0, C) (C <= 32); the
+ * colour-local index of v is j(v) = #{u < v : colour[u] = colour[v]}; the
+ * canonical vertex order is colour 0 by increasing v, then colour 1, ...
+ *
+ * Randomness (APT on graphs): replica in slot (temperature r, label a) has
+ * id b = 32 a + r (T <= 32); vertex v of colour c at sweep s uses
+ *   hi = v_{j&7}(Philox((j >> 3, s, (c << 16) | b, (e << 8) | TAG_G_SWEEP)))
+ *   lo = the same half of the TAG_G_REFINE block;  +1 iff (hi<<16|lo) < T.
+ * Initial spin: +1 iff v_{j&7}(Philox((j>>3, 0, (c<<16)|b, (e<<8)|TAG_G_INIT))) < 2^15.
+ * Swap of pair (r, r+1), label a, attempt t: word 0 of P(r, t, a, (e<<8)|TAG_G_SWAP).
+ * ICM of pair p at temperature r, attempt t: P(r, t, p, (e<<8)|TAG_G_ICM),
+ * words as in the lattice path (seed k, whole-replica bit, 4-label matching).
+ *
+ * DT-SQA on graphs: slice k of vertex v has colour (colour[v] + f(k)) mod C'
+ * with f(k) = k & 1, except f(P-1) = 2 when P is odd; C' = max(C, 2) for
+ * even P and max(C, 3) for odd P.  A class is ordered by k, then v; (v, k)
+ * of class c with class-local index j in run q uses
+ *   v_{j&7}(Philox((j >> 3, s, c, (q << 8) | TAG_GS_SWEEP / TAG_GS_REFINE))). */
+
+/* 0 if (rp, col, w) is a valid symmetric graph as above; -1 otherwise. */
+int or_graph_check(int n, const int32_t *rp, const int32_t *col, const int8_t *w);
+/* DSATUR (Brelaz 1979): repeatedly colour the uncoloured vertex of largest
+ * saturation (distinct colours among its coloured neighbours), ties by the
+ * largest degree in the uncoloured subgraph, then the smallest index, with
+ * the smallest colour absent from its neighbours.  *n_colours = C. */
+int or_dsatur(int n, const int32_t *rp, const int32_t *col, int32_t *colour, int *n_colours);
+/* Colours [P][n] of the replicated DT-SQA network (rule above); *n_colours = C'. */
+int or_graph_sqa_colouring(int n, const int32_t *colour, int P, int32_t *out, int *n_colours);
+/* E = -sum_{u<v} w_uv s_u s_v - sum_v h_v s_v. */
+int or_graph_energy(int n, const int32_t *rp, const int32_t *col, const int8_t *w,
+                    const int8_t *h, const int8_t *spin, int64_t *E_out);
+
+typedef struct or_gapt or_gapt;
+/* n_prob graphs; n_vert[i]; rp concatenated ([n_i + 1] each, local
+ * offsets), col/w concatenated (local vertex ids), h concatenated or NULL,
+ * colour concatenated or NULL (DSATUR); n_temps[i] <= 32; betas
+ * concatenated; n_labels in {1, 2, 4}. */
+int or_gapt_create(or_gapt **out, int n_prob, const int32_t *n_vert, const int32_t *rp,
+                   const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
+                   const int32_t *n_temps, const double *betas, int n_labels, uint64_t seed,
+                   uint32_t entry0);
+void or_gapt_destroy(or_gapt *g);
+int or_gapt_run(or_gapt *g, int64_t n_swaps, int sweeps_per_swap, int icm, int threads);
+int or_gapt_set_joint_swap(or_gapt *g, int joint);
+int or_gapt_set_target(or_gapt *g, int prob, int64_t e_target);
+/* spins [B][n] and energies [B] in slot order r*A + a; colours [n] used. */
+int or_gapt_state(const or_gapt *g, int prob, int8_t *spins, int64_t *energies, int32_t *colour);
+int or_gapt_best(const or_gapt *g, int prob, int64_t *E, int64_t *sweep, int32_t *buf,
+                 int64_t *hit_sweep, int8_t *spins);
+int or_gapt_stats(const or_gapt *g, int prob, int64_t *att, int64_t *acc, int64_t *icm);
+
+/* One ICMop on two configurations of a coloured graph (ctr = (r, t, p,
+ * (entry<<8)|TAG_G_ICM)); returns 0 / 1 / 2 as or_icm_apply. */
+int or_gicm_apply(int n, const int32_t *rp, const int32_t *col, const int32_t *colour, int8_t *sa,
+                  int8_t *sb, uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p,
+                  int64_t *cluster_size);
+
+/* R runs of P slices on a graph; colour NULL -> DSATUR; E_out [R][P]
+ * classical slice energies (with h); spins_out [R][P][n] or NULL. */
+int or_gsqa_anneal(int n, const int32_t *rp, const int32_t *col, const int8_t *w,
+                   const int8_t *h, const int32_t *colour, int P, double T, int n_sweeps,
+                   const double *gamma, int R, uint32_t run0, uint64_t seed, int64_t *E_out,
+                   int8_t *spins_out, int threads);
 
 #ifdef __cplusplus
 }

@@ -155,3 +155,137 @@ def random_vacancies(dims, fraction: float, seed: int) -> np.ndarray:
     """present [N] with about `fraction` of the sites missing (seeded)."""
     rng = np.random.Generator(np.random.Philox(key=[seed, 0xEEEE]))
     return (rng.random(int(np.prod(dims))) >= fraction).astype(np.uint8)
+
+
+# ---------------------------------------------------------------- general sparse graphs
+SEED_GRAPHS = 5000
+
+
+@dataclasses.dataclass
+class Graph:
+    """A symmetric sparse graph in CSR form: the neighbours of v are
+    ``col[rp[v]:rp[v+1]]`` (ascending) with integer weights ``w`` (nonzero,
+    equal in both directions)."""
+    rp: np.ndarray    # [n + 1] int32
+    col: np.ndarray   # [m] int32
+    w: np.ndarray     # [m] int8
+
+    @property
+    def n(self) -> int:
+        return len(self.rp) - 1
+
+    def edges(self) -> List[Tuple[int, int, int]]:
+        """(u, v, w) with u < v, each edge once."""
+        out = []
+        for v in range(self.n):
+            for q in range(self.rp[v], self.rp[v + 1]):
+                if self.col[q] > v:
+                    out.append((v, int(self.col[q]), int(self.w[q])))
+        return out
+
+
+def csr_from_edges(n: int, edges, weights=None) -> Graph:
+    """Symmetric CSR from an undirected edge list; repeated pairs are merged by
+    adding their weights and zero-weight pairs are dropped."""
+    acc = {}
+    edges = list(edges)
+    weights = [1] * len(edges) if weights is None else list(weights)
+    for (u, v), wt in zip(edges, weights):
+        u, v = int(u), int(v)
+        if u == v:
+            raise ValueError("self-loop")
+        key = (min(u, v), max(u, v))
+        acc[key] = acc.get(key, 0) + int(wt)
+    adj = [[] for _ in range(n)]
+    for (u, v), wt in acc.items():
+        if wt == 0:
+            continue
+        if not -127 <= wt <= 127:
+            raise ValueError("weight out of int8 range")
+        adj[u].append((v, wt))
+        adj[v].append((u, wt))
+    rp = np.zeros(n + 1, np.int32)
+    col, w = [], []
+    for v in range(n):
+        for u, wt in sorted(adj[v]):
+            col.append(u)
+            w.append(wt)
+        rp[v + 1] = len(col)
+    return Graph(rp, np.asarray(col, np.int32), np.asarray(w, np.int8))
+
+
+def lattice_graph(dims, periodic, J, present=None) -> Tuple[Graph, np.ndarray]:
+    """The bond graph of a 3D lattice with couplings J [N][3] (forward bonds
+    +x, +y, +z) and optional vacancies; any lengths, odd periodic ones
+    included.  Vertices are the present sites in lin order; returns the graph
+    and the lin of every vertex."""
+    lx, ly, lz = (int(v) for v in dims)
+    per = [1, 1, 1] if periodic is None else [int(bool(v)) for v in periodic]
+    N = lx * ly * lz
+    pres = np.ones(N, bool) if present is None else np.asarray(present).ravel().astype(bool)
+    sites = np.flatnonzero(pres).astype(np.int32)
+    vid = -np.ones(N, np.int64)
+    vid[sites] = np.arange(len(sites))
+    J = np.asarray(J, np.int8).reshape(N, 3)
+    L = (lx, ly, lz)
+    edges, ws = [], []
+    for lin in sites:
+        c = [lin % lx, (lin // lx) % ly, lin // (lx * ly)]
+        for a in range(3):
+            cc = list(c)
+            cc[a] += 1
+            if cc[a] == L[a]:
+                if not per[a]:
+                    continue
+                cc[a] = 0
+            nb = cc[0] + lx * (cc[1] + ly * cc[2])
+            if nb == lin or not pres[nb]:
+                continue
+            edges.append((vid[lin], vid[nb]))
+            ws.append(int(J[lin, a]))
+    return csr_from_edges(len(sites), edges, ws), sites
+
+
+def random_graph(n: int, mean_degree: float, seed: int, wmax: int = 1, index: int = 0) -> Graph:
+    """Erdos-Renyi graph G(n, p = mean_degree / (n - 1)) with weights drawn
+    uniformly from {-wmax..wmax} without 0."""
+    rng = np.random.Generator(np.random.Philox(key=[SEED_GRAPHS + seed, index]))
+    p = min(1.0, mean_degree / max(n - 1, 1))
+    iu, ju = np.triu_indices(n, 1)
+    keep = rng.random(len(iu)) < p
+    mags = rng.integers(1, wmax + 1, size=int(keep.sum()))
+    signs = 2 * rng.integers(0, 2, size=int(keep.sum())) - 1
+    return csr_from_edges(n, zip(iu[keep], ju[keep]), mags * signs)
+
+
+def random_biases(n: int, hmax: int, seed: int) -> np.ndarray:
+    """Biases h [n] drawn uniformly from {-hmax..hmax}."""
+    rng = np.random.Generator(np.random.Philox(key=[SEED_GRAPHS + seed, 0xB1A5]))
+    return rng.integers(-hmax, hmax + 1, size=n).astype(np.int8)
+
+
+def dimer_embedding(dims, J, ferro: int = 2) -> Graph:
+    """A logical periodic +-J lattice embedded with dimers, in the manner of
+    annealer embeddings: logical spin i becomes physical spins 2i and 2i+1
+    joined by a ferromagnetic coupling of strength `ferro`.  The logical bond
+    along +x joins the first halves and along +y the second halves, each with
+    J; the bond along +z is split over two couplers, from both halves of i to
+    the second half of its neighbour, each with J.  The split couplers close
+    triangles with the chains, so the graph is not bipartite."""
+    lx, ly, lz = (int(v) for v in dims)
+    N = lx * ly * lz
+    J = np.asarray(J, np.int8).reshape(N, 3)
+    edges, ws = [], []
+    for lin in range(N):
+        edges.append((2 * lin, 2 * lin + 1))
+        ws.append(ferro)
+        c = [lin % lx, (lin // lx) % ly, lin // (lx * ly)]
+        for a in range(3):
+            cc = list(c)
+            cc[a] = (cc[a] + 1) % (lx, ly, lz)[a]
+            nb = cc[0] + lx * (cc[1] + ly * cc[2])
+            pairs = ((0, 0),) if a == 0 else (((1, 1),) if a == 1 else ((0, 1), (1, 1)))
+            for hi, hj in pairs:
+                edges.append((2 * lin + hi, 2 * nb + hj))
+                ws.append(int(J[lin, a]))
+    return csr_from_edges(2 * N, edges, ws)
