@@ -275,6 +275,76 @@ int pc_pilot_hist(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J,
 /* [cbrt(N)/16, fraction of J > 0, fraction of frustrated plaquettes]. */
 int pc_instance_features(const int32_t *dims, const int8_t *J, double *out3);
 
+/* ------------------------------------------------------------------------
+ * General sparse graphs.  Algorithms S1 and S2 take weights, biases and a
+ * colormap; the Methods ("Graph Coloring of 3D Cubic Spin Glass Instances")
+ * colour the p-bits with DSATUR, need 2 to 4 colours when spins are missing
+ * or instances are embedded, and one more colour for the replicated DT-SQA
+ * network when the number of replicas is odd.
+ *
+ * A graph of n p-bits is CSR on the host: the neighbours of v are
+ * col[row_ptr[v] .. row_ptr[v+1]-1] (0-based, row_ptr[0] = 0) with int8
+ * weights w (J_vu, nonzero, equal in both directions, each pair listed once
+ * per direction, no self-loops); biases h [n] int8 or NULL.  Weights are
+ * integers: fixed-point weights with f fractional bits are passed as
+ * integers with beta scaled by 2^-f.  Limits: degree <= 1023, |h_v| +
+ * sum_u |w_vu| <= 127, at most 32 colours.  A colormap colour [n] (values
+ * 0..C-1, proper) may be given; NULL colours the graph with DSATUR.
+ * Energies are E = -sum_{u<v} w_uv s_u s_v - sum_v h_v s_v (Eq. ising_energy).
+ * ---------------------------------------------------------------------- */
+/* DSATUR (Brelaz 1979): repeatedly colour the uncoloured vertex of largest
+ * saturation (distinct colours among its coloured neighbours), ties by the
+ * largest degree among uncoloured neighbours, then the smallest index, with
+ * the smallest colour free at its neighbours.  colour [n] host output,
+ * *n_colours = C.  PC_EINVAL for a malformed graph or more than 32 colours. */
+int pc_graph_dsatur(int n, const int32_t *row_ptr, const int32_t *col, int32_t *colour,
+                    int *n_colours);
+/* Load n_prob APT problems on graphs (Algorithm S2): n_vert [n_prob];
+ * row_ptr concatenated ([n_i + 1] each, local offsets), col and w
+ * concatenated (local vertex ids), h concatenated or NULL, colour
+ * concatenated or NULL (DSATUR per problem); n_temps [n_prob] <= 32, betas
+ * concatenated (strictly increasing), n_labels in {1, 2, 4}.  Slot (r, a)
+ * = temperature r, label a; replica id 32 a + r in the counters of problem
+ * entry entry0 + i.  Shared memory holds a problem: 4 ((2 Imax + 1) 32 +
+ * n (A + 2)) bytes must fit the device's per-block limit.  Draws the random
+ * initial states and computes their energies; replaces any graph batch
+ * loaded before (the lattice APT batch is separate). */
+int pc_gapt_load(pc_ctx *ctx, int n_prob, const int32_t *n_vert, const int32_t *row_ptr,
+                 const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
+                 const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0);
+/* n_swaps attempts, each: sweeps_per_swap sweeps (colour class by colour
+ * class), energies, best tracking, ICM on every temperature when icm != 0
+ * (n_labels 2 or 4, all h = 0) followed by best tracking, and the replica
+ * exchange of pairs (r, r+1), r = t mod 2, t mod 2 + 2, ...  Resumable. */
+int pc_gapt_run(pc_ctx *ctx, int64_t n_swaps, int sweeps_per_swap, int icm);
+/* 0 (default): each label decides its swap; 1: one decision per pair with
+ * the labels' summed dE (as pc_apt_set_joint_swap). */
+int pc_gapt_set_joint_swap(pc_ctx *ctx, int joint);
+/* Best-energy target of problem `prob` (time to target). */
+int pc_gapt_set_target(pc_ctx *ctx, int prob, int64_t e_target);
+/* Energies [n_temps * n_labels] in slot order r * n_labels + a. */
+int pc_gapt_get_energies(pc_ctx *ctx, int prob, int64_t *E);
+/* Spins [n_temps * n_labels][n] (+-1) in slot order, original vertex order. */
+int pc_gapt_get_spins(pc_ctx *ctx, int prob, int8_t *spins);
+/* The colormap in use [n] (given or DSATUR). */
+int pc_gapt_get_colours(pc_ctx *ctx, int prob, int32_t *colour);
+/* Best energy so far, sweep count when found, slot, target hit sweep (-1:
+ * not yet), best state [n] (nullable; zeros before the first run). */
+int pc_gapt_get_best(pc_ctx *ctx, int prob, int64_t *E, int64_t *sweep, int32_t *slot,
+                     int64_t *hit_sweep, int8_t *spins);
+/* Swap attempts / accepts [n_temps-1][n_labels]; icm [3] as pc_apt_get_stats. */
+int pc_gapt_get_stats(pc_ctx *ctx, int prob, int64_t *att, int64_t *acc, int64_t *icm);
+/* DT-SQA on a graph (Eq. S.3, Algorithm S1): R runs (ids run0 ..) of P >= 2
+ * slices at temperature T under gamma[n_sweeps] (all > 0).  The replicated
+ * network takes colour (colour[v] + f(k)) mod C' for slice k, f(k) = k & 1
+ * except f(P-1) = 2 for odd P, C' = max(C, 2) (even P) or max(C, 3) (odd P).
+ * E_out [R][P] classical slice energies (biases included); spins_out
+ * [R][P][n] or NULL.  P n 4 bytes of state must fit in shared memory. */
+int pc_gsqa_anneal(pc_ctx *ctx, int n, const int32_t *row_ptr, const int32_t *col,
+                   const int8_t *w, const int8_t *h, const int32_t *colour, int P, double T,
+                   int n_sweeps, const double *gamma, int R, uint32_t run0, int64_t *E_out,
+                   int8_t *spins_out);
+
 /* MLP 259 -> 256 -> 256 -> 256 -> 32 (ReLU hidden), head
  * beta_k = beta_min + sum_{m<=k} softplus(o_m), loss = mean (beta - y)^2,
  * fp32 on the GPU, Adam.  W[l] is [out][in] row-major, b[l] is [out]. */

@@ -166,6 +166,7 @@ void pc_destroy(pc_ctx *c) {
   cudaStreamSynchronize(c->stream);
   c->sqa.release();
   pc_apt_release_impl(c);
+  pc_graph_release_impl(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }

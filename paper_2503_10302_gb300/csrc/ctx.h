@@ -116,6 +116,8 @@ struct pc_ctx {
   pc::SqaState sqa;
   pc::AptState apt;
   void *apt_impl = nullptr;
+  void *graph_impl = nullptr;   // APT batch on general graphs (graph_api.cpp)
 };
 
 void pc_apt_release_impl(pc_ctx *c);
+void pc_graph_release_impl(pc_ctx *c);

@@ -1,0 +1,622 @@
+// p-computer kernels on general sparse graphs: APT with replica exchange,
+// ICM and minimum-energy tracking (Algorithm S2) and DT-SQA on the
+// replicated network (Eq. S.3, Algorithm S1), both swept colour class by
+// colour class as the colormap of the paper's graph-coloured architecture
+// prescribes (Methods, "Graph Coloring of 3D Cubic Spin Glass Instances").
+//
+// Layout: one 32-bit word per (vertex, label) holds 32 replicas, one per
+// lane.  In APT the lanes are the temperatures of one label; in DT-SQA they
+// are 32 independent runs.  A warp updates one vertex for all 32 replicas at
+// once: its neighbours' words are warp-uniform shared-memory broadcasts,
+// each lane extracts its own bit, accumulates Eq. synapse, looks up Eq.
+// neuron's threshold in a [field][lane] table (bank = lane, conflict free)
+// and the 32 decisions are packed back with one ballot.  One Philox call of
+// a lane serves 8 consecutive vertices of its colour class (16-bit halves;
+// the refine block settles ties exactly, as in the lattice kernels).
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "device.cuh"
+#include "graph_dev.h"
+#include "internal.h"
+
+namespace pc {
+namespace {
+
+using pcdev::half_hi;
+using pcdev::half_lo;
+using pcdev::philox;
+
+struct GShared {
+  int off[kGMaxColours + 1];
+  int32_t E[4][32];              // energy of label a, temperature r
+  uint32_t wcnt[kGWarps][32];    // per-warp bit counts (ICM)
+  uint32_t x0[2][32], x1[2][32]; // ICM draws per pair set and temperature
+  uint32_t mcode[32];            // 4-label matching per temperature
+  uint32_t nm[32];               // mismatch counts
+  uint32_t sel[2][4];            // bit r: label k is the first / second of the pair
+  uint32_t whole[4];             // bit r: label k flips entirely
+  uint32_t small;                // bit r: the cluster flips in both replicas
+  uint32_t swmask[4];            // accepted swaps per label (bit r: pair r, r+1)
+  uint32_t att[128], acc[128];   // swap counters [r * A + a]
+  unsigned long long icm[3];
+  long long bestE, bestSweep, bestSlot, hit, target;
+  int copy_slot;
+};
+
+struct GCta {
+  int n, C, T, Imax, tid, lane, warp;
+  uint32_t ent, k0, k1;
+  const int2 *vinfo;
+  const uint32_t *adj;
+  uint32_t *S;                   // [n][A]
+  uint32_t *X;                   // [n] overlap mismatch (ICM)
+  volatile uint32_t *Cl;         // [n] cluster bits (ICM)
+  const uint32_t *Th;            // [2 Imax + 1][32]
+  uint32_t *best_bits;
+};
+
+__device__ __forceinline__ int vi_deg(int2 v) { return v.y & 1023; }
+__device__ __forceinline__ int vi_kl(int2 v) { return (v.y >> 10) & 1023; }
+__device__ __forceinline__ int vi_h(int2 v) { return (int)(int8_t)(uint8_t)((uint32_t)v.y >> 20); }
+__device__ __forceinline__ int ent_w(uint32_t e) { return (int)(int8_t)(uint8_t)(e & 0xFFu); }
+
+// Eq. synapse over neighbours [e0, e1) of lane's replica in label word a.
+template <int A>
+__device__ __forceinline__ int field_part(const GCta &k, const uint32_t *ad, int e0, int e1, int a,
+                                          int I) {
+  for (int e = e0; e < e1; ++e) {
+    const uint32_t en = __ldg(ad + e);
+    const int w = ent_w(en);
+    const uint32_t sw = k.S[(en >> 8) * A + a];
+    I += ((sw >> k.lane) & 1u) ? w : -w;
+  }
+  return I;
+}
+
+// Random initial states (Algorithm S2): +1 iff the init half is below 2^15.
+template <int A>
+__device__ void g_init(const GCta &k, GShared &sh) {
+  const int a = k.warp % A;
+  for (int c = 0; c < k.C; ++c) {
+    const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
+    const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(32 * a + k.lane);
+    const uint32_t c3 = (k.ent << 8) | pcdev::TAG_G_INIT;
+    for (int q = k.warp / A; 8 * q < nc; q += kGWarps / A) {
+      const uint4 x = philox((uint32_t)q, 0u, c2, c3, k.k0, k.k1);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (8 * q + i >= nc) break;
+        const bool up = k.lane < k.T && half_lo(x, i) < 0x8000u;
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
+        if (k.lane == 0) k.S[(o0 + 8 * q + i) * A + a] = word;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// One sweep, colour class by colour class (Algorithm S2's p-computer loop).
+// With wantE the energy of every replica (Eq. ising_energy) is gathered on
+// the way: each bond is counted at its endpoint of higher colour, whose
+// lower-colour neighbours already hold this sweep's values.
+template <int A>
+__device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s, bool wantE) {
+  if (wantE && k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
+  const int a = k.warp % A;
+  const uint32_t c3m = (k.ent << 8) | pcdev::TAG_G_SWEEP;
+  const uint32_t c3r = (k.ent << 8) | pcdev::TAG_G_REFINE;
+  int eacc = 0;
+  for (int c = 0; c < k.C; ++c) {
+    const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
+    const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(32 * a + k.lane);
+    for (int q = k.warp / A; 8 * q < nc; q += kGWarps / A) {
+      const uint4 x = philox((uint32_t)q, s, c2, c3m, k.k0, k.k1);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (8 * q + i >= nc) break;
+        const int p = o0 + 8 * q + i;
+        const int2 vi = __ldg(k.vinfo + p);
+        const uint32_t *ad = k.adj + vi.x;
+        const int kl = vi_kl(vi);
+        const int Ilow = field_part<A>(k, ad, 0, kl, a, vi_h(vi));
+        const int I = field_part<A>(k, ad, kl, vi_deg(vi), a, Ilow);
+        const uint32_t th = k.Th[(I + k.Imax) * 32 + k.lane];
+        const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
+        bool up = v < thi;
+        if (v == thi) {   // probability 2^-16: settle with the refine half
+          const uint4 y = philox((uint32_t)q, s, c2, c3r, k.k0, k.k1);
+          up = (v | half_lo(y, i)) < th;
+        }
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
+        if (k.lane == 0) k.S[p * A + a] = word;
+        eacc += up ? -Ilow : Ilow;
+      }
+    }
+    __syncthreads();
+  }
+  if (wantE) {
+    atomicAdd(&sh.E[a][k.lane], eacc);
+    __syncthreads();
+  }
+}
+
+// Energies of all replicas from the current state (after ICM, at load).
+template <int A>
+__device__ void g_energy(const GCta &k, GShared &sh) {
+  if (k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
+  __syncthreads();
+  const int a = k.warp % A;
+  int eacc = 0;
+  for (int p = k.warp / A; p < k.n; p += kGWarps / A) {
+    const int2 vi = __ldg(k.vinfo + p);
+    const int Ilow = field_part<A>(k, k.adj + vi.x, 0, vi_kl(vi), a, vi_h(vi));
+    eacc += ((k.S[p * A + a] >> k.lane) & 1u) ? -Ilow : Ilow;
+  }
+  atomicAdd(&sh.E[a][k.lane], eacc);
+  __syncthreads();
+}
+
+// Minimum-energy tracking: lowest slot r*A + a on ties, strict improvement;
+// an improvement copies that replica's state into the best-state bits.
+template <int A>
+__device__ void g_best(const GCta &k, GShared &sh, long long sweeps) {
+  if (k.warp == 0) {
+    int bE = INT_MAX, bB = INT_MAX;
+    if (k.lane < k.T)
+      for (int aa = 0; aa < A; ++aa) {
+        const int e = sh.E[aa][k.lane];
+        if (e < bE) { bE = e; bB = k.lane * A + aa; }
+      }
+    for (int o = 16; o; o >>= 1) {
+      const int oE = __shfl_xor_sync(0xFFFFFFFFu, bE, o), oB = __shfl_xor_sync(0xFFFFFFFFu, bB, o);
+      if (oE < bE || (oE == bE && oB < bB)) { bE = oE; bB = oB; }
+    }
+    if (k.lane == 0) {
+      sh.copy_slot = -1;
+      if ((long long)bE < sh.bestE) {
+        sh.bestE = bE;
+        sh.bestSweep = sweeps;
+        sh.bestSlot = bB;
+        sh.copy_slot = bB;
+      }
+      if (sh.hit < 0 && sh.bestE <= sh.target) sh.hit = sweeps;
+    }
+  }
+  __syncthreads();
+  const int cs = sh.copy_slot;
+  if (cs >= 0) {
+    const int r = cs / A, aa = cs % A;
+    for (int w = k.warp; 32 * w < k.n; w += kGWarps) {
+      const int p = 32 * w + k.lane;
+      const bool bit = p < k.n && ((k.S[p * A + aa] >> r) & 1u);
+      const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
+      if (k.lane == 0) k.best_bits[w] = word;
+    }
+  }
+  __syncthreads();
+}
+
+// Replica exchange at attempt t: pairs (r, r+1) with r = t mod 2, t mod 2 + 2,
+// ...; per label (or jointly over labels) accept with min(1, exp(dbeta dE))
+// through the pair's table by |dE|.  Accepted pairs exchange their states
+// (bit r and r+1 of every word of the label) and energies.
+template <int A>
+__device__ void g_swap(const GCta &k, GShared &sh, uint32_t t, int joint, const uint32_t *swaptab,
+                       const uint32_t *swapidx) {
+  if (k.tid < 4) sh.swmask[k.tid] = 0u;
+  __syncthreads();
+  const int r0 = (int)(t & 1u), npairs = (k.T - r0) / 2;
+  const uint32_t c3 = (k.ent << 8) | pcdev::TAG_G_SWAP;
+  if (joint) {
+    if (k.tid < npairs) {
+      const int r = r0 + 2 * k.tid;
+      long long dE = 0;
+      for (int aa = 0; aa < A; ++aa) dE += (long long)sh.E[aa][r + 1] - sh.E[aa][r];
+      const uint32_t x = philox((uint32_t)r, t, 0u, c3, k.k0, k.k1).x;
+      bool acc = dE >= 0;
+      if (!acc) {
+        const long long d = -dE;
+        acc = d < (long long)swapidx[2 * r + 1] && x < swaptab[swapidx[2 * r] + d];
+      }
+      for (int aa = 0; aa < A; ++aa) {
+        sh.att[r * A + aa]++;
+        if (acc) {
+          sh.acc[r * A + aa]++;
+          atomicOr(&sh.swmask[aa], 1u << r);
+        }
+      }
+    }
+  } else if (k.tid < npairs * A) {
+    const int r = r0 + 2 * (k.tid / A), aa = k.tid % A;
+    const long long dE = (long long)sh.E[aa][r + 1] - sh.E[aa][r];
+    const uint32_t x = philox((uint32_t)r, t, (uint32_t)aa, c3, k.k0, k.k1).x;
+    bool acc = dE >= 0;
+    if (!acc) {
+      const long long d = -dE;
+      acc = d < (long long)swapidx[2 * r + 1] && x < swaptab[swapidx[2 * r] + d];
+    }
+    sh.att[r * A + aa]++;
+    if (acc) {
+      sh.acc[r * A + aa]++;
+      atomicOr(&sh.swmask[aa], 1u << r);
+    }
+  }
+  __syncthreads();
+  for (int i = k.tid; i < k.n * A; i += kGThreads) {
+    const uint32_t M = sh.swmask[i % A];
+    if (M) {
+      const uint32_t w = k.S[i], d = (w ^ (w >> 1)) & M;
+      k.S[i] = w ^ d ^ (d << 1);
+    }
+  }
+  if (k.warp < A) {
+    const uint32_t M = sh.swmask[k.warp];
+    const int e = sh.E[k.warp][k.lane];
+    int src = k.lane;
+    if ((M >> k.lane) & 1u) src = k.lane + 1;
+    else if (k.lane > 0 && ((M >> (k.lane - 1)) & 1u)) src = k.lane - 1;
+    const int o = __shfl_sync(0xFFFFFFFFu, e, src);
+    sh.E[k.warp][k.lane] = o;
+  }
+  __syncthreads();
+}
+
+// ICMop of Algorithm S2 for every temperature at once (bit r of the words =
+// temperature r).  Per pair set: the overlap mismatch X, its count per
+// temperature, the seed = the k-th mismatch vertex in canonical order
+// (k = floor(x0 n_minus / 2^32)), the seed's connected component in X by a
+// bit-parallel flood fill over the graph, then either the cluster flips in
+// both replicas or, when it holds more than half of the n spins, one whole
+// replica (x1 bit 0) flips.
+template <int A>
+__device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
+  const uint32_t c3 = (k.ent << 8) | pcdev::TAG_G_ICM;
+  if (k.tid < 32 * (A / 2)) {
+    const int pp = k.tid >> 5, r = k.tid & 31;
+    if (r < k.T) {
+      const uint4 x = philox((uint32_t)r, t, (uint32_t)pp, c3, k.k0, k.k1);
+      sh.x0[pp][r] = x.x;
+      sh.x1[pp][r] = x.y;
+      if (pp == 0) sh.mcode[r] = (uint32_t)(((unsigned long long)x.z * 3ull) >> 32);
+    }
+  }
+  __syncthreads();
+  const int per = (k.n + kGWarps - 1) / kGWarps;
+  const int lo = min(k.n, k.warp * per), hi = min(k.n, lo + per);
+  for (int pp = 0; pp < A / 2; ++pp) {
+    if (k.warp == 0) {
+      // the 4-label matchings (0,1)(2,3), (0,2)(1,3), (0,3)(1,2)
+      const bool valid = k.lane < k.T;
+      int la = 0, lb = 1;
+      if (A == 4) {
+        const int m = valid ? (int)sh.mcode[k.lane] : 0;
+        const int M[3][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}};
+        la = M[m][2 * pp];
+        lb = M[m][2 * pp + 1];
+      }
+      for (int kk = 0; kk < A; ++kk) {
+        const uint32_t sa = __ballot_sync(0xFFFFFFFFu, valid && la == kk);
+        const uint32_t sb = __ballot_sync(0xFFFFFFFFu, valid && lb == kk);
+        if (k.lane == 0) {
+          sh.sel[0][kk] = sa;
+          sh.sel[1][kk] = sb;
+        }
+      }
+    }
+    __syncthreads();
+    uint32_t selA[A], selB[A];
+#pragma unroll
+    for (int kk = 0; kk < A; ++kk) {
+      selA[kk] = sh.sel[0][kk];
+      selB[kk] = sh.sel[1][kk];
+    }
+    for (int p = k.tid; p < k.n; p += kGThreads) {
+      uint32_t xa = 0, xb = 0;
+#pragma unroll
+      for (int kk = 0; kk < A; ++kk) {
+        const uint32_t w = k.S[p * A + kk];
+        xa |= w & selA[kk];
+        xb |= w & selB[kk];
+      }
+      k.X[p] = xa ^ xb;
+      k.Cl[p] = 0u;
+    }
+    __syncthreads();
+    uint32_t cnt = 0;
+    for (int p = lo; p < hi; ++p) cnt += (k.X[p] >> k.lane) & 1u;
+    sh.wcnt[k.warp][k.lane] = cnt;
+    __syncthreads();
+    {
+      uint32_t pre = 0, tot = 0;
+      for (int w = 0; w < kGWarps; ++w) {
+        const uint32_t c = sh.wcnt[w][k.lane];
+        pre += w < k.warp ? c : 0u;
+        tot += c;
+      }
+      if (k.warp == 0) sh.nm[k.lane] = tot;
+      if (k.lane < k.T && tot > 0) {
+        const uint32_t kk = (uint32_t)(((unsigned long long)sh.x0[pp][k.lane] * tot) >> 32);
+        if (kk >= pre && kk < pre + cnt) {
+          uint32_t seen = pre;
+          for (int p = lo; p < hi; ++p)
+            if ((k.X[p] >> k.lane) & 1u) {
+              if (seen == kk) {
+                atomicOr((uint32_t *)&k.Cl[p], 1u << k.lane);
+                break;
+              }
+              ++seen;
+            }
+        }
+      }
+    }
+    __syncthreads();
+    // flood fill: grow every seed inside X until nothing changes; each
+    // change adds a bit, so at most 32 n passes
+    for (;;) {
+      int changed = 0;
+      for (int p = k.tid; p < k.n; p += kGThreads) {
+        const uint32_t cl = k.Cl[p], cand = k.X[p] & ~cl;
+        if (cand) {
+          const int2 vi = __ldg(k.vinfo + p);
+          const uint32_t *ad = k.adj + vi.x;
+          uint32_t nb = 0;
+          for (int e = 0, d = vi_deg(vi); e < d; ++e) nb |= k.Cl[__ldg(ad + e) >> 8];
+          const uint32_t nw = cl | (cand & nb);
+          if (nw != cl) {
+            k.Cl[p] = nw;
+            changed = 1;
+          }
+        }
+      }
+      if (!__syncthreads_or(changed)) break;
+    }
+    cnt = 0;
+    for (int p = lo; p < hi; ++p) cnt += (k.Cl[p] >> k.lane) & 1u;
+    sh.wcnt[k.warp][k.lane] = cnt;
+    __syncthreads();
+    if (k.warp == 0) {
+      uint32_t size = 0;
+      for (int w = 0; w < kGWarps; ++w) size += sh.wcnt[w][k.lane];
+      const bool valid = k.lane < k.T, has = valid && sh.nm[k.lane] > 0;
+      const bool big = has && 2ull * size > (unsigned long long)k.n;
+      const bool second = (sh.x1[pp][k.lane] & 1u) != 0u;
+      const uint32_t smallM = __ballot_sync(0xFFFFFFFFu, has && !big);
+      const uint32_t wA = __ballot_sync(0xFFFFFFFFu, big && !second);
+      const uint32_t wB = __ballot_sync(0xFFFFFFFFu, big && second);
+      const uint32_t none = __ballot_sync(0xFFFFFFFFu, valid && !has);
+      if (k.lane == 0) {
+        sh.small = smallM;
+        for (int kk = 0; kk < A; ++kk) sh.whole[kk] = (wA & sh.sel[0][kk]) | (wB & sh.sel[1][kk]);
+        sh.icm[0] += __popc(none);
+        sh.icm[1] += __popc(smallM);
+        sh.icm[2] += __popc(wA | wB);
+      }
+    }
+    __syncthreads();
+    const uint32_t smallM = sh.small;
+    for (int i = k.tid; i < k.n * A; i += kGThreads) {
+      const int p = i / A, kk = i % A;
+      k.S[i] ^= (k.Cl[p] & smallM & (selA[kk] | selB[kk])) | sh.whole[kk];
+    }
+    __syncthreads();
+  }
+}
+
+template <int A>
+__global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init) {
+  extern __shared__ __align__(16) uint32_t dyn[];
+  __shared__ GShared sh;
+  const GProbDev &P = a.prob[blockIdx.x];
+  GCta k;
+  k.n = P.n;
+  k.C = P.C;
+  k.T = P.T;
+  k.Imax = P.Imax;
+  k.tid = threadIdx.x;
+  k.lane = threadIdx.x & 31;
+  k.warp = threadIdx.x >> 5;
+  k.ent = P.ent;
+  k.k0 = a.k0;
+  k.k1 = a.k1;
+  k.vinfo = a.vinfo + P.vbase;
+  k.adj = a.adj + P.abase;
+  uint32_t *Th = dyn;
+  const int nth = (2 * P.Imax + 1) * 32;
+  k.Th = Th;
+  k.S = Th + nth;
+  k.X = k.S + (size_t)P.n * A;
+  k.Cl = k.X + P.n;
+  k.best_bits = a.best_bits + P.bestbase;
+  uint32_t *gS = a.spins + (size_t)P.vbase * A;
+  if (k.tid <= k.C) sh.off[k.tid] = P.off[k.tid];
+  for (int i = k.tid; i < nth; i += kGThreads) Th[i] = a.pbit[P.thbase + i];
+  const long long *gb = a.best + 4 * (size_t)blockIdx.x;
+  if (init) {
+    __syncthreads();
+    g_init<A>(k, sh);
+    g_energy<A>(k, sh);
+  } else {
+    for (int i = k.tid; i < P.n * A; i += kGThreads) k.S[i] = gS[i];
+    if (k.tid < 128) {
+      sh.E[k.tid >> 5][k.tid & 31] = a.E[128 * (size_t)blockIdx.x + k.tid];
+      sh.att[k.tid] = 0u;
+      sh.acc[k.tid] = 0u;
+    }
+    if (k.tid == 0) {
+      sh.bestE = gb[0];
+      sh.bestSweep = gb[1];
+      sh.bestSlot = gb[2];
+      sh.hit = gb[3];
+      sh.target = a.target[blockIdx.x];
+      sh.icm[0] = sh.icm[1] = sh.icm[2] = 0ull;
+    }
+    __syncthreads();
+    const uint32_t *swidx = a.swapidx + P.swbase;
+    for (int t = 0; t < a.n_swaps; ++t) {
+      const uint32_t tt = a.swap0 + (uint32_t)t;
+      for (int q = 0; q < a.spp; ++q)
+        g_sweep<A>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q), q == a.spp - 1);
+      const long long done = (long long)a.sweep0 + (long long)(t + 1) * a.spp;
+      g_best<A>(k, sh, done);
+      if (A >= 2 && a.icm) {
+        g_icm<A>(k, sh, tt);
+        g_energy<A>(k, sh);
+        g_best<A>(k, sh, done);
+      }
+      g_swap<A>(k, sh, tt, a.joint, a.swaptab, swidx);
+    }
+    unsigned long long *st = a.stats + P.statbase;
+    const int np = (P.T > 1 ? P.T - 1 : 0) * A;
+    for (int i = k.tid; i < np; i += kGThreads) {
+      st[i] += sh.att[i];
+      st[np + i] += sh.acc[i];
+    }
+    if (k.tid == 0) {
+      st[2 * np] += sh.icm[0];
+      st[2 * np + 1] += sh.icm[1];
+      st[2 * np + 2] += sh.icm[2];
+      long long *b = a.best + 4 * (size_t)blockIdx.x;
+      b[0] = sh.bestE;
+      b[1] = sh.bestSweep;
+      b[2] = sh.bestSlot;
+      b[3] = sh.hit;
+    }
+  }
+  for (int i = k.tid; i < P.n * A; i += kGThreads) gS[i] = k.S[i];
+  if (k.tid < 128) a.E[128 * (size_t)blockIdx.x + k.tid] = sh.E[k.tid >> 5][k.tid & 31];
+}
+
+template <int A>
+int gapt_launch_t(const GAptArgs &a, int n_prob, size_t smem, bool init, cudaStream_t st) {
+  PC_CUDA_TRY(cudaFuncSetAttribute(gapt_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  gapt_kernel<A><<<n_prob, kGThreads, smem, st>>>(a, init ? 1 : 0);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+// DT-SQA on the replicated network of a graph (Eq. S.3, Algorithm S1).  A
+// CTA anneals 32 runs (one per lane); the P x n words of its runs stay in
+// shared memory for the whole anneal.  Per sweep the [3][2 Imax + 1]
+// threshold table of that sweep's transverse coupling is staged in shared
+// memory; per colour class of the replicated network, warps take chunks of 8
+// class entries (slice k, vertex p).  The field is Eq. synapse in slice k plus
+// the two neighbouring slices' spins of the same vertex.
+__global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
+  extern __shared__ __align__(16) uint32_t dyn[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nt = 2 * a.Imax + 1, ntab = 3 * nt;
+  uint32_t *tab = dyn;                       // [2][3][2 Imax + 1]
+  uint32_t *W = dyn + 2 * ntab;              // [P][n]
+  const int n = a.n, P = a.P;
+  const uint32_t run = a.run0 + 32u * blockIdx.x + (uint32_t)lane;
+  const uint32_t c3i = (run << 8) | pcdev::TAG_GS_INIT;
+  const uint32_t c3m = (run << 8) | pcdev::TAG_GS_SWEEP;
+  const uint32_t c3r = (run << 8) | pcdev::TAG_GS_REFINE;
+  // Algorithm S1: random initial states of all slices
+  for (int c = 0; c < a.Cp; ++c) {
+    const int o0 = a.cls_off[c], nc = a.cls_off[c + 1] - o0;
+    for (int q = warp; 8 * q < nc; q += kGWarps) {
+      const uint4 x = philox((uint32_t)q, 0u, (uint32_t)c, c3i, a.k0, a.k1);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (8 * q + i >= nc) break;
+        const uint32_t e = __ldg(a.cls + o0 + 8 * q + i);
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, half_lo(x, i) < 0x8000u);
+        if (lane == 0) W[(e >> 20) * n + (e & 0xFFFFFu)] = word;
+      }
+    }
+  }
+  for (int s = 0; s < a.S; ++s) {
+    uint32_t *T = tab + (s & 1) * ntab;
+    for (int i = tid; i < ntab; i += kGThreads) T[i] = __ldg(a.table + (size_t)s * ntab + i);
+    __syncthreads();
+    for (int c = 0; c < a.Cp; ++c) {
+      const int o0 = a.cls_off[c], nc = a.cls_off[c + 1] - o0;
+      for (int q = warp; 8 * q < nc; q += kGWarps) {
+        const uint4 x = philox((uint32_t)q, (uint32_t)s, (uint32_t)c, c3m, a.k0, a.k1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (8 * q + i >= nc) break;
+          const uint32_t e = __ldg(a.cls + o0 + 8 * q + i);
+          const int k = (int)(e >> 20), p = (int)(e & 0xFFFFFu);
+          const uint32_t *Wk = W + (size_t)k * n;
+          const int2 vi = __ldg(a.vinfo + p);
+          const uint32_t *ad = a.adj + vi.x;
+          int I = vi_h(vi);
+          for (int q2 = 0, d = vi_deg(vi); q2 < d; ++q2) {
+            const uint32_t en = __ldg(ad + q2);
+            const int w = ent_w(en);
+            I += ((Wk[en >> 8] >> lane) & 1u) ? w : -w;
+          }
+          const int kd = k == 0 ? P - 1 : k - 1, ku = k == P - 1 ? 0 : k + 1;
+          const uint32_t nup = ((W[(size_t)kd * n + p] >> lane) & 1u) + ((W[(size_t)ku * n + p] >> lane) & 1u);
+          const uint32_t th = T[nup * nt + (I + a.Imax)];
+          const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
+          bool up = v < thi;
+          if (v == thi) {
+            const uint4 y = philox((uint32_t)q, (uint32_t)s, (uint32_t)c, c3r, a.k0, a.k1);
+            up = (v | half_lo(y, i)) < th;
+          }
+          const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
+          if (lane == 0) W[(size_t)k * n + p] = word;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // Algorithm S1: classical energy of every slice (bonds at their endpoint
+  // of higher colour, biases included)
+  const int runs_here = min(32, a.R - 32 * (int)blockIdx.x);
+  for (int k = 0; k < P; ++k) {
+    const uint32_t *Wk = W + (size_t)k * n;
+    long long eacc = 0;
+    for (int p = warp; p < n; p += kGWarps) {
+      const int2 vi = __ldg(a.vinfo + p);
+      const uint32_t *ad = a.adj + vi.x;
+      int Ilow = vi_h(vi);
+      for (int q2 = 0, kl = vi_kl(vi); q2 < kl; ++q2) {
+        const uint32_t en = __ldg(ad + q2);
+        const int w = ent_w(en);
+        Ilow += ((Wk[en >> 8] >> lane) & 1u) ? w : -w;
+      }
+      eacc += ((Wk[p] >> lane) & 1u) ? -Ilow : Ilow;
+    }
+    if (lane < runs_here)
+      atomicAdd((unsigned long long *)&a.E[(size_t)(32 * blockIdx.x + lane) * P + k],
+                (unsigned long long)eacc);
+  }
+  if (a.spins)
+    for (int i = tid; i < P * n; i += kGThreads) a.spins[(size_t)blockIdx.x * P * n + i] = W[i];
+}
+
+}  // namespace
+
+size_t gsqa_smem_bytes(int n, int P, int Imax) {
+  return sizeof(uint32_t) * ((size_t)6 * (2 * Imax + 1) + (size_t)P * n);
+}
+
+int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st) {
+  PC_CUDA_TRY(cudaFuncSetAttribute(gsqa_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  gsqa_kernel<<<(a.R + 31) / 32, kGThreads, smem, st>>>(a);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
+size_t gapt_smem_bytes(int n, int A, int Imax) {
+  return sizeof(uint32_t) * ((size_t)(2 * Imax + 1) * 32 + (size_t)n * A + (size_t)2 * n);
+}
+
+int gapt_launch(const GAptArgs &a, int n_prob, int A, size_t smem, bool init, cudaStream_t st) {
+  switch (A) {
+    case 1: return gapt_launch_t<1>(a, n_prob, smem, init, st);
+    case 2: return gapt_launch_t<2>(a, n_prob, smem, init, st);
+    case 4: return gapt_launch_t<4>(a, n_prob, smem, init, st);
+    default: return fail(PC_EINVAL, "n_labels must be 1, 2 or 4");
+  }
+}
+
+}  // namespace pc

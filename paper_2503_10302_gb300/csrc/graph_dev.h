@@ -1,0 +1,77 @@
+// Device-side description of p-computer problems on general sparse graphs
+// (Algorithms S1 and S2 with weights, biases and a colormap), shared by the
+// host layer (graph_api.cpp) and the kernels (graph.cu).
+//
+// Vertices are renumbered colour-major: class c holds the vertices of colour
+// c in increasing original index, at new indices off[c] .. off[c+1]-1, so the
+// colour-local index of new vertex p is p - off[c] and the canonical ICM
+// order is increasing p.
+//
+//   vinfo[p] = {start, deg | kl << 10 | (h & 0xFF) << 20}
+//     start: first adjacency entry; deg: neighbours; kl: neighbours of a
+//     lower colour (they come first: adjacency is sorted by new index);
+//     h: the bias, int8.
+//   adj[e]   = (u << 8) | (w & 0xFF): neighbour u (new index), weight int8.
+//   spins    : word [p][a] holds label a's bit for 32 temperatures (lane r =
+//     temperature r, bit set = spin +1); unused temperatures stay 0.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pc {
+
+constexpr int kGMaxColours = 32;
+constexpr int kGMaxDeg = 1023;
+constexpr int kGMaxImax = 127;
+constexpr int kGThreads = 512;
+constexpr int kGWarps = kGThreads / 32;
+
+struct GProbDev {
+  int n, C, T, A, Imax, m;
+  uint32_t ent;                 // problem entry of the counters
+  uint32_t vbase;               // first vertex in vinfo / spins ([n][A] words from vbase * A)
+  uint32_t abase;               // first adjacency entry
+  uint32_t thbase;              // first word of the [2 Imax + 1][32] p-bit table
+  uint32_t swbase;              // first (offset, length) pair in swapidx
+  uint32_t bestbase;            // first word of the best-state bits
+  uint32_t statbase;            // first counter: att[T-1][A], acc[T-1][A], icm[3]
+  int off[kGMaxColours + 1];
+};
+
+struct GAptArgs {
+  const GProbDev *prob;
+  const int2 *vinfo;
+  const uint32_t *adj;
+  const uint32_t *pbit;         // [2 Imax + 1][32] per problem (zero columns for r >= T)
+  const uint32_t *swaptab;      // thresholds by |dE| (entry 0: always accepted)
+  const uint32_t *swapidx;      // per pair: offset, length
+  uint32_t *spins;              // [n][A] words per problem
+  int32_t *E;                   // [n_prob][4][32]
+  uint32_t *best_bits;          // [ceil(n/32)] words per problem
+  long long *best;              // [n_prob][4]: E, sweep, slot, hit sweep
+  const long long *target;      // [n_prob]
+  unsigned long long *stats;    // counters per problem
+  uint32_t k0, k1;
+  uint32_t sweep0, swap0;       // counters of the first sweep / attempt of this launch
+  int n_swaps, spp, icm, joint;
+};
+
+struct GSqaArgs {
+  int n, P, Cp, S, Imax, R;     // vertices, slices, colours, sweeps, field bound, runs
+  uint32_t run0, k0, k1;
+  const int2 *vinfo;            // as above
+  const uint32_t *adj;
+  const uint32_t *cls;          // [P n]: class-major list of k * n + p
+  const int *cls_off;           // [Cp + 1]
+  const uint32_t *table;        // [S][3][2 Imax + 1]
+  long long *E;                 // [R][P]
+  uint32_t *spins;              // [ceil(R/32)][P][n] words (nullable)
+};
+
+size_t gapt_smem_bytes(int n, int A, int Imax);
+int gapt_launch(const GAptArgs &a, int n_prob, int A, size_t smem, bool init, cudaStream_t st);
+size_t gsqa_smem_bytes(int n, int P, int Imax);
+int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st);
+
+}  // namespace pc

@@ -75,6 +75,19 @@ SIGNATURES = {
     "pc_pilot_hist": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_u32, c_int, c_f64p, c_int, c_int, c_int,
                               c_int, c_i64p]),
     "pc_instance_features": (c_int, [c_i32p, c_i8p, c_f64p]),
+    "pc_graph_dsatur": (c_int, [c_int, c_i32p, c_i32p, c_i32p, ctypes.POINTER(c_int)]),
+    "pc_gapt_load": (c_int, [c_vp, c_int, c_i32p, c_i32p, c_i32p, c_i8p, c_vp, c_vp, c_i32p, c_f64p,
+                             c_int, c_u32]),
+    "pc_gapt_run": (c_int, [c_vp, c_i64, c_int, c_int]),
+    "pc_gapt_set_joint_swap": (c_int, [c_vp, c_int]),
+    "pc_gapt_set_target": (c_int, [c_vp, c_int, c_i64]),
+    "pc_gapt_get_energies": (c_int, [c_vp, c_int, c_i64p]),
+    "pc_gapt_get_spins": (c_int, [c_vp, c_int, c_i8p]),
+    "pc_gapt_get_colours": (c_int, [c_vp, c_int, c_i32p]),
+    "pc_gapt_get_best": (c_int, [c_vp, c_int, c_i64p, c_i64p, c_i32p, c_i64p, c_i8p]),
+    "pc_gapt_get_stats": (c_int, [c_vp, c_int, c_i64p, c_i64p, c_i64p]),
+    "pc_gsqa_anneal": (c_int, [c_vp, c_int, c_i32p, c_i32p, c_i8p, c_vp, c_vp, c_int, c_dbl, c_int, c_f64p,
+                               c_int, c_u32, c_i64p, c_vp]),
     "pc_mlp_create": (c_int, [c_vp, ctypes.POINTER(c_vp), c_f32pp, c_f32pp, c_flt]),
     "pc_mlp_destroy": (None, [c_vp]),
     "pc_mlp_forward": (c_int, [c_vp, c_int, c_f32p, c_f32p]),
@@ -511,3 +524,106 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ---------------------------------------------------------------- general graphs
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).ravel())
+
+
+def _i8(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int8).ravel())
+
+
+def pc_graph_dsatur(row_ptr, col):
+    """DSATUR colouring of a CSR graph: (colour [n], number of colours)."""
+    rp, cl = _i32(row_ptr), _i32(col)
+    n = len(rp) - 1
+    out = np.zeros(n, np.int32)
+    C = c_int(0)
+    _call("pc_graph_dsatur", n, ptr(rp, ctypes.c_int32), ptr(cl, ctypes.c_int32), ptr(out, ctypes.c_int32),
+          ctypes.byref(C))
+    return out, C.value
+
+
+def pc_gapt_load(ctx, graphs, betas_list, n_labels: int = 2, entry0: int = 0, h_list=None,
+                 colours=None) -> None:
+    """graphs: list of (row_ptr, col, w) CSR triples; h_list / colours: per
+    problem arrays or None (no biases / DSATUR colouring)."""
+    nv = np.ascontiguousarray([len(g[0]) - 1 for g in graphs], dtype=np.int32)
+    rp = np.ascontiguousarray(np.concatenate([_i32(g[0]) for g in graphs]))
+    cl = np.ascontiguousarray(np.concatenate([_i32(g[1]) for g in graphs]))
+    w = np.ascontiguousarray(np.concatenate([_i8(g[2]) for g in graphs]))
+    h = None if h_list is None else np.ascontiguousarray(np.concatenate([_i8(x) for x in h_list]))
+    co = None if colours is None else np.ascontiguousarray(np.concatenate([_i32(x) for x in colours]))
+    nt = np.ascontiguousarray([len(b) for b in betas_list], dtype=np.int32)
+    be = np.ascontiguousarray(np.concatenate([np.asarray(b, np.float64) for b in betas_list]))
+    _call("pc_gapt_load", ctx, len(graphs), ptr(nv, ctypes.c_int32), ptr(rp, ctypes.c_int32),
+          ptr(cl, ctypes.c_int32), ptr(w, ctypes.c_int8), None if h is None else h.ctypes.data,
+          None if co is None else co.ctypes.data, ptr(nt, ctypes.c_int32), ptr(be, ctypes.c_double),
+          n_labels, c_u32(entry0))
+
+
+def pc_gapt_run(ctx, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True) -> None:
+    _call("pc_gapt_run", ctx, c_i64(n_swaps), sweeps_per_swap, int(bool(icm)))
+
+
+def pc_gapt_set_joint_swap(ctx, joint: bool) -> None:
+    _call("pc_gapt_set_joint_swap", ctx, int(bool(joint)))
+
+
+def pc_gapt_set_target(ctx, prob: int, e_target: int) -> None:
+    _call("pc_gapt_set_target", ctx, prob, c_i64(e_target))
+
+
+def pc_gapt_get_energies(ctx, prob: int, T: int, A: int) -> np.ndarray:
+    E = np.zeros(T * A, np.int64)
+    _call("pc_gapt_get_energies", ctx, prob, ptr(E, ctypes.c_int64))
+    return E
+
+
+def pc_gapt_get_spins(ctx, prob: int, T: int, A: int, n: int) -> np.ndarray:
+    s = np.zeros((T * A, n), np.int8)
+    _call("pc_gapt_get_spins", ctx, prob, ptr(s, ctypes.c_int8))
+    return s
+
+
+def pc_gapt_get_colours(ctx, prob: int, n: int) -> np.ndarray:
+    c = np.zeros(n, np.int32)
+    _call("pc_gapt_get_colours", ctx, prob, ptr(c, ctypes.c_int32))
+    return c
+
+
+def pc_gapt_get_best(ctx, prob: int, n: int):
+    E, sw, hit = c_i64(), c_i64(), c_i64()
+    b = ctypes.c_int32()
+    s = np.zeros(n, np.int8)
+    _call("pc_gapt_get_best", ctx, prob, ctypes.byref(E), ctypes.byref(sw), ctypes.byref(b),
+          ctypes.byref(hit), ptr(s, ctypes.c_int8))
+    return dict(E=E.value, sweep=sw.value, buf=b.value, hit_sweep=hit.value, spins=s)
+
+
+def pc_gapt_get_stats(ctx, prob: int, T: int, A: int):
+    att = np.zeros((max(T - 1, 0), A), np.int64)
+    acc = np.zeros_like(att)
+    icm = np.zeros(3, np.int64)
+    _call("pc_gapt_get_stats", ctx, prob, ptr(att, ctypes.c_int64), ptr(acc, ctypes.c_int64),
+          ptr(icm, ctypes.c_int64))
+    return att, acc, icm
+
+
+def pc_gsqa_anneal(ctx, row_ptr, col, w, P: int, T: float, gamma, R: int, run0: int = 0, h=None,
+                   colour=None, want_spins: bool = False):
+    """DT-SQA on a graph: slice energies [R][P] (and spins [R][P][n])."""
+    rp, cl, ww = _i32(row_ptr), _i32(col), _i8(w)
+    hh = None if h is None else _i8(h)
+    co = None if colour is None else _i32(colour)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    n = len(rp) - 1
+    E = np.zeros((R, P), np.int64)
+    s = np.zeros((R, P, n), np.int8) if want_spins else None
+    _call("pc_gsqa_anneal", ctx, n, ptr(rp, ctypes.c_int32), ptr(cl, ctypes.c_int32), ptr(ww, ctypes.c_int8),
+          None if hh is None else hh.ctypes.data, None if co is None else co.ctypes.data, P, T, len(g),
+          ptr(g, ctypes.c_double), R, c_u32(run0), ptr(E, ctypes.c_int64),
+          None if s is None else s.ctypes.data)
+    return (E, s) if want_spins else E

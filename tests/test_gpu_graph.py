@@ -1,0 +1,156 @@
+"""APT + ICM and DT-SQA on general sparse graphs, GPU against the CPU oracle:
+bit-exact spins, energies, best energies and states, hit sweeps, swap and
+ICM statistics, for DSATUR-coloured graphs with 1 to 4 colours (odd periodic
+lattices, dimer embeddings with couplings of strength 2, random weighted
+graphs with biases) and odd and even numbers of Trotter slices."""
+import numpy as np
+import pytest
+
+from paper_2503_10302_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    from paper_2503_10302_gb300 import build, pcomp
+    build.build()
+    return pcomp
+
+
+def _trip(g):
+    return (g.rp, g.col, g.w)
+
+
+def _compare(pc, ctx, o, graphs, betas, A):
+    for i, g in enumerate(graphs):
+        T = len(betas[i])
+        E1 = pc.pc_gapt_get_energies(ctx.h, i, T, A)
+        s1 = pc.pc_gapt_get_spins(ctx.h, i, T, A, g.n)
+        s2, E2, c2 = o.state(i)
+        assert np.array_equal(pc.pc_gapt_get_colours(ctx.h, i, g.n), c2), ("colours", i)
+        assert np.array_equal(E1, E2), ("energies", i, E1, E2)
+        assert np.array_equal(s1, s2), ("spins", i)
+        b1, b2 = pc.pc_gapt_get_best(ctx.h, i, g.n), o.best(i)
+        for key in ("E", "sweep", "buf", "hit_sweep"):
+            assert b1[key] == b2[key], (key, i, b1[key], b2[key])
+        if b2["sweep"] >= 0:
+            assert np.array_equal(b1["spins"], b2["spins"]), ("best spins", i)
+        att, acc, icm = pc.pc_gapt_get_stats(ctx.h, i, T, A)
+        att2, acc2, icm2 = o.stats(i)
+        assert np.array_equal(att, att2) and np.array_equal(acc, acc2), ("swap stats", i)
+        assert np.array_equal(icm, icm2), ("icm stats", i, icm, icm2)
+
+
+def _mixed_graphs():
+    """Several tiles of work per colour and ragged tails: graphs whose colour
+    classes are not multiples of 8 vertices."""
+    return [W.lattice_graph((5, 5, 4), (1, 1, 1), W.ea_couplings((5, 5, 4), 1000, 0))[0],
+            W.dimer_embedding((4, 4, 4), W.ea_couplings((4, 4, 4), 1000, 1)),
+            W.random_graph(333, 4.0, 7, wmax=3),
+            W.lattice_graph((6, 6, 6), (0, 1, 1), W.ea_couplings((6, 6, 6), 1000, 2),
+                            W.random_vacancies((6, 6, 6), 0.15, 5))[0]]
+
+
+@pytest.mark.parametrize("A,icm,spp", [(2, True, 1), (4, True, 1), (1, False, 1), (2, False, 3),
+                                       (2, True, 2)])
+def test_gapt_matches_oracle(pc, orc, A, icm, spp):
+    graphs = _mixed_graphs()
+    betas = [W.geometric_ladder(T, 0.2, 3.0) for T in (32, 17, 24, 9)]
+    seed = 1234 + A
+    ctx = pc.Context(0, seed)
+    pc.pc_gapt_load(ctx.h, [_trip(g) for g in graphs], betas, A, 5)
+    o = orc.GApt([_trip(g) for g in graphs], betas, n_labels=A, seed=seed, entry0=5)
+    _compare(pc, ctx, o, graphs, betas, A)          # initial states and energies
+    for i, g in enumerate(graphs):
+        o.set_target(i, -int(1.2 * g.n))
+        pc.pc_gapt_set_target(ctx.h, i, -int(1.2 * g.n))
+    for n_sw in (1, 7, 40):
+        pc.pc_gapt_run(ctx.h, n_sw, spp, icm)
+        o.run(n_sw, spp, icm)
+        _compare(pc, ctx, o, graphs, betas, A)
+    ctx.close()
+
+
+def test_gapt_with_biases_and_joint_swaps(pc, orc):
+    graphs = [W.random_graph(200, 5.0, 11, wmax=4), W.random_graph(77, 2.0, 12, wmax=2)]
+    hs = [W.random_biases(g.n, 3, 20 + i) for i, g in enumerate(graphs)]
+    betas = [W.geometric_ladder(20, 0.1, 2.0), W.geometric_ladder(31, 0.3, 4.0)]
+    ctx = pc.Context(0, 99)
+    pc.pc_gapt_load(ctx.h, [_trip(g) for g in graphs], betas, 2, 0, h_list=hs)
+    o = orc.GApt([_trip(g) for g in graphs], betas, n_labels=2, seed=99, h_list=hs)
+    pc.pc_gapt_set_joint_swap(ctx.h, True)
+    o.set_joint_swap(True)
+    pc.pc_gapt_run(ctx.h, 30, 1, False)
+    o.run(30, 1, False)
+    _compare(pc, ctx, o, graphs, betas, 2)
+    pc.pc_gapt_set_joint_swap(ctx.h, False)
+    o.set_joint_swap(False)
+    pc.pc_gapt_run(ctx.h, 20, 2, False)
+    o.run(20, 2, False)
+    _compare(pc, ctx, o, graphs, betas, 2)
+    with pytest.raises(RuntimeError):
+        pc.pc_gapt_run(ctx.h, 1, 1, True)           # ICM refuses biases
+    ctx.close()
+
+
+def test_gapt_given_colormap_and_edge_cases(pc, orc):
+    """A caller's colormap (here 4 colours on a bipartite graph), a graph
+    without edges (1 colour) and one temperature."""
+    g1 = W.lattice_graph((4, 4, 4), (1, 1, 1), W.ea_couplings((4, 4, 4), 1000, 3))[0]
+    lin = np.arange(64)
+    col1 = (((lin % 4) + (lin // 4) % 4 + lin // 16) % 2 + 2 * (lin % 3 == 0)).astype(np.int32)
+    g2 = W.csr_from_edges(13, [])
+    graphs, colours = [g1, g2], [col1, None]
+    betas = [W.geometric_ladder(8, 0.2, 3.0), np.array([0.7])]
+    ctx = pc.Context(0, 3)
+    cl = [col1, orc.dsatur(g2.rp, g2.col)[0]]
+    pc.pc_gapt_load(ctx.h, [_trip(g) for g in graphs], betas, 2, 0, colours=cl)
+    o = orc.GApt([_trip(g) for g in graphs], betas, n_labels=2, seed=3, colours=cl)
+    for _ in range(3):
+        pc.pc_gapt_run(ctx.h, 9, 1, True)
+        o.run(9, 1, True)
+        _compare(pc, ctx, o, graphs, betas, 2)
+    ctx.close()
+
+
+def test_gapt_refuses_bad_input(pc):
+    ctx = pc.Context(0, 0)
+    g = W.csr_from_edges(4, [(0, 1), (1, 2), (2, 3), (3, 0)])
+    bad_colour = [np.zeros(4, np.int32)]
+    with pytest.raises(RuntimeError):
+        pc.pc_gapt_load(ctx.h, [_trip(g)], [np.array([0.5, 1.0])], 2, 0, colours=bad_colour)
+    with pytest.raises(RuntimeError):
+        pc.pc_gapt_load(ctx.h, [_trip(g)], [np.array([1.0, 0.5])], 2)    # not increasing
+    with pytest.raises(RuntimeError):
+        pc.pc_gapt_load(ctx.h, [_trip(g)], [np.linspace(0.1, 1, 33)], 2)  # 33 temperatures
+    heavy = W.csr_from_edges(3, [(0, 1), (1, 2)], [100, 100])
+    with pytest.raises(RuntimeError):
+        pc.pc_gapt_load(ctx.h, [_trip(heavy)], [np.array([0.5])], 1)    # |field| > 127
+    ctx.close()
+
+
+@pytest.mark.parametrize("P", [2, 3, 4, 5, 8])
+def test_gsqa_matches_oracle(pc, orc, P):
+    cases = [(W.dimer_embedding((2, 2, 2), W.ea_couplings((2, 2, 2), 1000, 4)), None),
+             (W.random_graph(70, 3.0, 8, wmax=3), W.random_biases(70, 2, 8)),
+             (W.lattice_graph((3, 3, 4), (1, 1, 1), W.ea_couplings((3, 3, 4), 1000, 5))[0], None)]
+    gamma = W.linear_gamma_schedule(37, 3.0, 0.05)
+    for gi, (g, h) in enumerate(cases):
+        R = 45
+        ctx = pc.Context(0, 17 + gi)
+        E1, s1 = pc.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, P, 0.3, gamma, R, run0=11, h=h, want_spins=True)
+        E2, s2 = orc.gsqa_anneal(g.rp, g.col, g.w, P, 0.3, gamma, R, run0=11, seed=17 + gi, h=h,
+                                 want_spins=True)
+        assert np.array_equal(s1, s2), (P, gi)
+        assert np.array_equal(E1, E2), (P, gi)
+        ctx.close()
+
+
+def test_gsqa_zero_sweeps_is_the_initial_state(pc, orc):
+    g = W.random_graph(40, 2.0, 3)
+    ctx = pc.Context(0, 5)
+    E1, s1 = pc.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, 3, 0.5, np.zeros(0), 33, want_spins=True)
+    E2, s2 = orc.gsqa_anneal(g.rp, g.col, g.w, 3, 0.5, np.zeros(0), 33, seed=5, want_spins=True)
+    assert np.array_equal(s1, s2) and np.array_equal(E1, E2)
+    ctx.close()
