@@ -530,6 +530,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
       }
     }
   }
+  __syncthreads();
   for (int s = 0; s < a.S; ++s) {
     uint32_t *T = tab + (s & 1) * ntab;
     for (int i = tid; i < ntab; i += kGThreads) T[i] = __ldg(a.table + (size_t)s * ntab + i);

@@ -330,9 +330,56 @@ def c5_learned_vs_adaptive(n_train=20000, n_eval=128, L=16, rho=1e-3, best_runs=
     return out
 
 
+def graph_apt_throughput(graphs: Sequence[W.Graph], n_temps: int = 32, labels: int = 2, sweeps: int = 200,
+                         icm: bool = True, seed: int = 1) -> Dict:
+    """APT (+ICM) on general graphs: sweep updates per ns, end to end."""
+    ctx = pcomp.Context(0, seed)
+    timer = DeviceTimer(ctx)
+    betas = [W.geometric_ladder(n_temps, 0.2, 3.0)] * len(graphs)
+    pcomp.pc_gapt_load(ctx.h, [(g.rp, g.col, g.w) for g in graphs], betas, labels, 0)
+    pcomp.pc_gapt_run(ctx.h, 10, 1, icm)
+    dt = timer.time(lambda: pcomp.pc_gapt_run(ctx.h, sweeps, 1, icm))
+    colours = max(int(pcomp.pc_gapt_get_colours(ctx.h, i, g.n).max()) + 1 for i, g in enumerate(graphs))
+    ctx.close()
+    per_sweep = sum(g.n for g in graphs) * n_temps * labels
+    return {"flips_per_ns": per_sweep * sweeps / dt / 1e9, "seconds": dt, "sweeps": sweeps, "icm": icm,
+            "spins_per_sweep": per_sweep, "colours": colours, "problems": len(graphs)}
+
+
+def graph_sqa_throughput(g: W.Graph, P: int = 64, R: int = 4864, sweeps: int = 1000, T: float = 0.05,
+                         seed: int = 1) -> Dict:
+    """DT-SQA on a graph: spin updates per ns of one anneal (launch, tables
+    and the copies of its inputs and outputs included)."""
+    ctx = pcomp.Context(0, seed)
+    gamma = W.linear_gamma_schedule(sweeps)
+    pcomp.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, P, T, gamma[:10], R)
+    t0 = time.perf_counter()
+    E = pcomp.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, P, T, gamma, R)
+    dt = time.perf_counter() - t0
+    ctx.close()
+    flips = g.n * P * R * sweeps
+    return {"flips_per_ns": flips / dt / 1e9, "seconds": dt, "sweeps": sweeps, "P": P, "R": R, "n": g.n,
+            "min_energy": int(E.min())}
+
+
+def graph_workloads(name: str) -> List[W.Graph]:
+    if name == "dimer_64xL8":
+        return [W.dimer_embedding((8, 8, 8), W.ea_couplings((8, 8, 8), W.SEED_INSTANCES, i)) for i in range(64)]
+    if name == "lattice15x15x12_64":
+        d = (15, 15, 12)
+        return [W.lattice_graph(d, (1, 1, 1), W.ea_couplings(d, W.SEED_INSTANCES, i))[0] for i in range(64)]
+    if name == "lattice12_64":
+        d = (12, 12, 12)
+        return [W.lattice_graph(d, (1, 1, 1), W.ea_couplings(d, W.SEED_INSTANCES, i))[0] for i in range(64)]
+    if name == "random4096_152":
+        return [W.sparse_random_graph(4096, 6.0, i, wmax=3) for i in range(152)]
+    raise ValueError(name)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("what", choices=["throughput", "c2", "c3", "c4", "c5", "all"])
+    ap.add_argument("what", choices=["throughput", "graph", "c2", "c3", "c4", "c5", "all"])
+    ap.add_argument("--graph", choices=["dimer_64xL8", "lattice15x15x12_64", "lattice12_64", "random4096_152"])
     ap.add_argument("--sweeps", type=int, default=200)
     ap.add_argument("--batch", choices=["apt_plain_L4", "apt_icm_64xL12", "apt_icm_mixed256"])
     ap.add_argument("--icm", type=int, choices=[0, 1])
@@ -354,6 +401,20 @@ def main():
             batch = batches[name]()
             for icm in ((True, False) if args.icm is None else (bool(args.icm),)):
                 out[f"{name}_icm{int(icm)}"] = apt_throughput(batch, args.sweeps, icm)
+    if args.what in ("graph", "all"):
+        names = [args.graph] if args.graph else ["dimer_64xL8", "lattice15x15x12_64", "lattice12_64",
+                                                 "random4096_152"]
+        for name in names:
+            graphs = graph_workloads(name)
+            for labels in (2, 4):
+                for icm in ((True, False) if args.icm is None else (bool(args.icm),)):
+                    out[f"graph_{name}_A{labels}_icm{int(icm)}"] = graph_apt_throughput(
+                        graphs, 32, labels, args.sweeps, icm)
+        out["graph_sqa_dimerL4_P64"] = graph_sqa_throughput(
+            W.dimer_embedding((4, 4, 4), W.ea_couplings((4, 4, 4), W.SEED_INSTANCES, 0)), 64, 4864, 1000)
+        out["graph_sqa_lattice5x5x4_P65"] = graph_sqa_throughput(
+            W.lattice_graph((5, 5, 4), (1, 1, 1), W.ea_couplings((5, 5, 4), W.SEED_INSTANCES, 0))[0], 65, 4864,
+            1000)
     if args.what in ("c2", "all"):
         out["c2"] = c2_residual_vs_R()
     if args.what in ("c3", "all"):

@@ -258,6 +258,21 @@ def random_graph(n: int, mean_degree: float, seed: int, wmax: int = 1, index: in
     return csr_from_edges(n, zip(iu[keep], ju[keep]), mags * signs)
 
 
+def sparse_random_graph(n: int, mean_degree: float, seed: int, wmax: int = 1, index: int = 0) -> Graph:
+    """A large sparse random graph: n * mean_degree / 2 vertex pairs drawn
+    uniformly (self-pairs dropped, repeated pairs merged), weights drawn
+    uniformly from {-wmax..wmax} without 0 (the sum of a repeated pair's
+    weights, zero sums dropped)."""
+    rng = np.random.Generator(np.random.Philox(key=[SEED_GRAPHS + seed, 0x5A00 + index]))
+    m = int(round(n * mean_degree / 2))
+    u = rng.integers(0, n, size=m)
+    v = rng.integers(0, n, size=m)
+    keep = u != v
+    mags = rng.integers(1, wmax + 1, size=m)
+    signs = 2 * rng.integers(0, 2, size=m) - 1
+    return csr_from_edges(n, zip(u[keep], v[keep]), (mags * signs)[keep])
+
+
 def random_biases(n: int, hmax: int, seed: int) -> np.ndarray:
     """Biases h [n] drawn uniformly from {-hmax..hmax}."""
     rng = np.random.Generator(np.random.Philox(key=[SEED_GRAPHS + seed, 0xB1A5]))
