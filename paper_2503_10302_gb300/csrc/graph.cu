@@ -63,17 +63,43 @@ __device__ __forceinline__ int vi_kl(int2 v) { return (v.y >> 10) & 1023; }
 __device__ __forceinline__ int vi_h(int2 v) { return (int)(int8_t)(uint8_t)((uint32_t)v.y >> 20); }
 __device__ __forceinline__ int ent_w(uint32_t e) { return (int)(int8_t)(uint8_t)(e & 0xFFu); }
 
-// Eq. synapse over neighbours [e0, e1) of lane's replica in label word a.
-template <int A>
-__device__ __forceinline__ int field_part(const GCta &k, const uint32_t *ad, int e0, int e1, int a,
-                                          int I) {
-  for (int e = e0; e < e1; ++e) {
-    const uint32_t en = __ldg(ad + e);
-    const int w = ent_w(en);
-    const uint32_t sw = k.S[(en >> 8) * A + a];
-    I += ((sw >> k.lane) & 1u) ? w : -w;
+// Eq. synapse of the lane's replica in label word a over the deg
+// neighbours at ad: .x = h + sum_u w_vu s_u, .y = the same over the first kl
+// (lower-colour) neighbours.  Groups of 4 and 2 neighbours issue their
+// loads together, so the adjacency -> spin-word -> add chains overlap.
+template <int A, bool LOW>
+__device__ __forceinline__ int2 field(const uint32_t *S, int lane, const uint32_t *ad, int deg, int kl, int a,
+                                      int h) {
+  int I = h, Il = h, e = 0;
+  for (; e + 4 <= deg; e += 4) {
+    uint32_t en[4], sw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) en[j] = __ldg(ad + e + j);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sw[j] = S[(en[j] >> 8) * A + a];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int w = ent_w(en[j]), c = ((sw[j] >> lane) & 1u) ? w : -w;
+      I += c;
+      if (LOW) Il += (e + j < kl) ? c : 0;
+    }
   }
-  return I;
+  if (e + 2 <= deg) {
+    const uint32_t e0 = __ldg(ad + e), e1 = __ldg(ad + e + 1);
+    const uint32_t s0 = S[(e0 >> 8) * A + a], s1 = S[(e1 >> 8) * A + a];
+    const int w0 = ent_w(e0), w1 = ent_w(e1);
+    const int c0 = ((s0 >> lane) & 1u) ? w0 : -w0, c1 = ((s1 >> lane) & 1u) ? w1 : -w1;
+    I += c0 + c1;
+    if (LOW) Il += (e < kl ? c0 : 0) + (e + 1 < kl ? c1 : 0);
+    e += 2;
+  }
+  if (e < deg) {
+    const uint32_t e0 = __ldg(ad + e);
+    const int w0 = ent_w(e0), c0 = ((S[(e0 >> 8) * A + a] >> lane) & 1u) ? w0 : -w0;
+    I += c0;
+    if (LOW) Il += e < kl ? c0 : 0;
+  }
+  return make_int2(I, Il);
 }
 
 // Random initial states (Algorithm S2): +1 iff the init half is below 2^15.
@@ -102,9 +128,9 @@ __device__ void g_init(const GCta &k, GShared &sh) {
 // With wantE the energy of every replica (Eq. ising_energy) is gathered on
 // the way: each bond is counted at its endpoint of higher colour, whose
 // lower-colour neighbours already hold this sweep's values.
-template <int A>
-__device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s, bool wantE) {
-  if (wantE && k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
+template <int A, bool WANT_E>
+__device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
+  if (WANT_E && k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
   const int a = k.warp % A;
   const uint32_t c3m = (k.ent << 8) | pcdev::TAG_G_SWEEP;
   const uint32_t c3r = (k.ent << 8) | pcdev::TAG_G_REFINE;
@@ -119,10 +145,8 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s, bool wantE) {
         if (8 * q + i >= nc) break;
         const int p = o0 + 8 * q + i;
         const int2 vi = __ldg(k.vinfo + p);
-        const uint32_t *ad = k.adj + vi.x;
-        const int kl = vi_kl(vi);
-        const int Ilow = field_part<A>(k, ad, 0, kl, a, vi_h(vi));
-        const int I = field_part<A>(k, ad, kl, vi_deg(vi), a, Ilow);
+        const int2 f = field<A, WANT_E>(k.S, k.lane, k.adj + vi.x, vi_deg(vi), vi_kl(vi), a, vi_h(vi));
+        const int I = f.x, Ilow = f.y;
         const uint32_t th = k.Th[(I + k.Imax) * 32 + k.lane];
         const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
         bool up = v < thi;
@@ -132,12 +156,12 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s, bool wantE) {
         }
         const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
         if (k.lane == 0) k.S[p * A + a] = word;
-        eacc += up ? -Ilow : Ilow;
+        if (WANT_E) eacc += up ? -Ilow : Ilow;
       }
     }
     __syncthreads();
   }
-  if (wantE) {
+  if (WANT_E) {
     atomicAdd(&sh.E[a][k.lane], eacc);
     __syncthreads();
   }
@@ -152,7 +176,7 @@ __device__ void g_energy(const GCta &k, GShared &sh) {
   int eacc = 0;
   for (int p = k.warp / A; p < k.n; p += kGWarps / A) {
     const int2 vi = __ldg(k.vinfo + p);
-    const int Ilow = field_part<A>(k, k.adj + vi.x, 0, vi_kl(vi), a, vi_h(vi));
+    const int Ilow = field<A, false>(k.S, k.lane, k.adj + vi.x, vi_kl(vi), 0, a, vi_h(vi)).x;
     eacc += ((k.S[p * A + a] >> k.lane) & 1u) ? -Ilow : Ilow;
   }
   atomicAdd(&sh.E[a][k.lane], eacc);
@@ -457,8 +481,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
     const uint32_t *swidx = a.swapidx + P.swbase;
     for (int t = 0; t < a.n_swaps; ++t) {
       const uint32_t tt = a.swap0 + (uint32_t)t;
-      for (int q = 0; q < a.spp; ++q)
-        g_sweep<A>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q), q == a.spp - 1);
+      for (int q = 0; q + 1 < a.spp; ++q) g_sweep<A, false>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q));
+      g_sweep<A, true>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + a.spp - 1));
       const long long done = (long long)a.sweep0 + (long long)(t + 1) * a.spp;
       g_best<A>(k, sh, done);
       if (A >= 2 && a.icm) {
@@ -547,12 +571,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
           const uint32_t *Wk = W + (size_t)k * n;
           const int2 vi = __ldg(a.vinfo + p);
           const uint32_t *ad = a.adj + vi.x;
-          int I = vi_h(vi);
-          for (int q2 = 0, d = vi_deg(vi); q2 < d; ++q2) {
-            const uint32_t en = __ldg(ad + q2);
-            const int w = ent_w(en);
-            I += ((Wk[en >> 8] >> lane) & 1u) ? w : -w;
-          }
+          const int I = field<1, false>(Wk, lane, ad, vi_deg(vi), 0, 0, vi_h(vi)).x;
           const int kd = k == 0 ? P - 1 : k - 1, ku = k == P - 1 ? 0 : k + 1;
           const uint32_t nup = ((W[(size_t)kd * n + p] >> lane) & 1u) + ((W[(size_t)ku * n + p] >> lane) & 1u);
           const uint32_t th = T[nup * nt + (I + a.Imax)];
@@ -578,12 +597,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
     for (int p = warp; p < n; p += kGWarps) {
       const int2 vi = __ldg(a.vinfo + p);
       const uint32_t *ad = a.adj + vi.x;
-      int Ilow = vi_h(vi);
-      for (int q2 = 0, kl = vi_kl(vi); q2 < kl; ++q2) {
-        const uint32_t en = __ldg(ad + q2);
-        const int w = ent_w(en);
-        Ilow += ((Wk[en >> 8] >> lane) & 1u) ? w : -w;
-      }
+      const int Ilow = field<1, false>(Wk, lane, ad, vi_kl(vi), 0, 0, vi_h(vi)).x;
       eacc += ((Wk[p] >> lane) & 1u) ? -Ilow : Ilow;
     }
     if (lane < runs_here)

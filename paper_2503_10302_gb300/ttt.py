@@ -380,6 +380,8 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("what", choices=["throughput", "graph", "c2", "c3", "c4", "c5", "all"])
     ap.add_argument("--graph", choices=["dimer_64xL8", "lattice15x15x12_64", "lattice12_64", "random4096_152"])
+    ap.add_argument("--graph-labels", type=int, choices=[2, 4], help="graph: one label count only")
+    ap.add_argument("--no-sqa", action="store_true", help="graph: skip the DT-SQA lines")
     ap.add_argument("--sweeps", type=int, default=200)
     ap.add_argument("--batch", choices=["apt_plain_L4", "apt_icm_64xL12", "apt_icm_mixed256"])
     ap.add_argument("--icm", type=int, choices=[0, 1])
@@ -406,10 +408,11 @@ def main():
                                                  "random4096_152"]
         for name in names:
             graphs = graph_workloads(name)
-            for labels in (2, 4):
+            for labels in ((2, 4) if args.graph_labels is None else (args.graph_labels,)):
                 for icm in ((True, False) if args.icm is None else (bool(args.icm),)):
                     out[f"graph_{name}_A{labels}_icm{int(icm)}"] = graph_apt_throughput(
                         graphs, 32, labels, args.sweeps, icm)
+    if args.what in ("graph", "all") and not args.no_sqa:
         out["graph_sqa_dimerL4_P64"] = graph_sqa_throughput(
             W.dimer_embedding((4, 4, 4), W.ea_couplings((4, 4, 4), W.SEED_INSTANCES, 0)), 64, 4864, 1000)
         out["graph_sqa_lattice5x5x4_P65"] = graph_sqa_throughput(
