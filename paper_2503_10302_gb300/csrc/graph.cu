@@ -48,6 +48,8 @@ struct GShared {
 
 struct GCta {
   int n, C, T, Imax, tid, lane, warp;
+  uint32_t sh;                   // 31 - lane
+  int ushift;                    // adjacency byte offset >> ushift = neighbour index
   uint32_t ent, k0, k1;
   const int2 *vinfo;
   const uint32_t *adj;
@@ -63,43 +65,60 @@ __device__ __forceinline__ int vi_kl(int2 v) { return (v.y >> 10) & 1023; }
 __device__ __forceinline__ int vi_h(int2 v) { return (int)(int8_t)(uint8_t)((uint32_t)v.y >> 20); }
 __device__ __forceinline__ int ent_w(uint32_t e) { return (int)(int8_t)(uint8_t)(e & 0xFFu); }
 
-// Eq. synapse of the lane's replica in label word a over the deg
-// neighbours at ad: .x = h + sum_u w_vu s_u, .y = the same over the first kl
-// (lower-colour) neighbours.  Groups of 4 and 2 neighbours issue their
-// loads together, so the adjacency -> spin-word -> add chains overlap.
-template <int A, bool LOW>
-__device__ __forceinline__ int2 field(const uint32_t *S, int lane, const uint32_t *ad, int deg, int kl, int a,
+template <bool SM>
+__device__ __forceinline__ uint32_t ld_adj(const uint32_t *ad, int e) {
+  if (SM) return ad[e];
+  return __ldg(ad + e);
+}
+template <bool SM>
+__device__ __forceinline__ int2 ld_vi(const int2 *vi, int p) {
+  if (SM) return vi[p];
+  return __ldg(vi + p);
+}
+
+// Eq. synapse of the lane's replica over the deg neighbours at ad; Sa is the
+// label's first spin word and an entry's top 24 bits are the byte offset of
+// the neighbour's word from it.  With m = -1 (spin +1) or 0 (spin -1) taken
+// by shifting the lane's bit into the sign, the neighbour adds
+// (w ^ ~m) + m + 1 = +-w; the +1s are added once at the end.  .x = h +
+// sum_u w_vu s_u, .y = the same over the first kl (lower-colour)
+// neighbours.  Groups of 4 and 2 neighbours issue their loads together.
+template <bool LOW, bool SM>
+__device__ __forceinline__ int2 field(const uint32_t *Sa, uint32_t sh, const uint32_t *ad, int deg, int kl,
                                       int h) {
-  int I = h, Il = h, e = 0;
+  const char *Sb = reinterpret_cast<const char *>(Sa);
+  int acc = 0, accl = 0, e = 0;
   for (; e + 4 <= deg; e += 4) {
     uint32_t en[4], sw[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) en[j] = __ldg(ad + e + j);
+    for (int j = 0; j < 4; ++j) en[j] = ld_adj<SM>(ad, e + j);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) sw[j] = S[(en[j] >> 8) * A + a];
+    for (int j = 0; j < 4; ++j) sw[j] = *reinterpret_cast<const uint32_t *>(Sb + (en[j] >> 8));
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int w = ent_w(en[j]), c = ((sw[j] >> lane) & 1u) ? w : -w;
-      I += c;
-      if (LOW) Il += (e + j < kl) ? c : 0;
+      const int m = (int)(sw[j] << sh) >> 31, c = (ent_w(en[j]) ^ ~m) + m;
+      acc += c;
+      if (LOW) accl += (e + j < kl) ? c : 0;
     }
   }
   if (e + 2 <= deg) {
-    const uint32_t e0 = __ldg(ad + e), e1 = __ldg(ad + e + 1);
-    const uint32_t s0 = S[(e0 >> 8) * A + a], s1 = S[(e1 >> 8) * A + a];
-    const int w0 = ent_w(e0), w1 = ent_w(e1);
-    const int c0 = ((s0 >> lane) & 1u) ? w0 : -w0, c1 = ((s1 >> lane) & 1u) ? w1 : -w1;
-    I += c0 + c1;
-    if (LOW) Il += (e < kl ? c0 : 0) + (e + 1 < kl ? c1 : 0);
+    const uint32_t e0 = ld_adj<SM>(ad, e), e1 = ld_adj<SM>(ad, e + 1);
+    const uint32_t s0 = *reinterpret_cast<const uint32_t *>(Sb + (e0 >> 8));
+    const uint32_t s1 = *reinterpret_cast<const uint32_t *>(Sb + (e1 >> 8));
+    const int m0 = (int)(s0 << sh) >> 31, m1 = (int)(s1 << sh) >> 31;
+    const int c0 = (ent_w(e0) ^ ~m0) + m0, c1 = (ent_w(e1) ^ ~m1) + m1;
+    acc += c0 + c1;
+    if (LOW) accl += (e < kl ? c0 : 0) + (e + 1 < kl ? c1 : 0);
     e += 2;
   }
   if (e < deg) {
-    const uint32_t e0 = __ldg(ad + e);
-    const int w0 = ent_w(e0), c0 = ((S[(e0 >> 8) * A + a] >> lane) & 1u) ? w0 : -w0;
-    I += c0;
-    if (LOW) Il += e < kl ? c0 : 0;
+    const uint32_t e0 = ld_adj<SM>(ad, e);
+    const int m0 = (int)(*reinterpret_cast<const uint32_t *>(Sb + (e0 >> 8)) << sh) >> 31;
+    const int c0 = (ent_w(e0) ^ ~m0) + m0;
+    acc += c0;
+    if (LOW) accl += e < kl ? c0 : 0;
   }
-  return make_int2(I, Il);
+  return make_int2(h + acc + deg, h + accl + kl);
 }
 
 // Random initial states (Algorithm S2): +1 iff the init half is below 2^15.
@@ -128,7 +147,7 @@ __device__ void g_init(const GCta &k, GShared &sh) {
 // With wantE the energy of every replica (Eq. ising_energy) is gathered on
 // the way: each bond is counted at its endpoint of higher colour, whose
 // lower-colour neighbours already hold this sweep's values.
-template <int A, bool WANT_E>
+template <int A, bool WANT_E, bool SM>
 __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
   if (WANT_E && k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
   const int a = k.warp % A;
@@ -144,8 +163,8 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
       for (int i = 0; i < 8; ++i) {
         if (8 * q + i >= nc) break;
         const int p = o0 + 8 * q + i;
-        const int2 vi = __ldg(k.vinfo + p);
-        const int2 f = field<A, WANT_E>(k.S, k.lane, k.adj + vi.x, vi_deg(vi), vi_kl(vi), a, vi_h(vi));
+        const int2 vi = ld_vi<SM>(k.vinfo, p);
+        const int2 f = field<WANT_E, SM>(k.S + a, k.sh, k.adj + vi.x, vi_deg(vi), vi_kl(vi), vi_h(vi));
         const int I = f.x, Ilow = f.y;
         const uint32_t th = k.Th[(I + k.Imax) * 32 + k.lane];
         const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
@@ -168,15 +187,15 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
 }
 
 // Energies of all replicas from the current state (after ICM, at load).
-template <int A>
+template <int A, bool SM>
 __device__ void g_energy(const GCta &k, GShared &sh) {
   if (k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
   __syncthreads();
   const int a = k.warp % A;
   int eacc = 0;
   for (int p = k.warp / A; p < k.n; p += kGWarps / A) {
-    const int2 vi = __ldg(k.vinfo + p);
-    const int Ilow = field<A, false>(k.S, k.lane, k.adj + vi.x, vi_kl(vi), 0, a, vi_h(vi)).x;
+    const int2 vi = ld_vi<SM>(k.vinfo, p);
+    const int Ilow = field<false, SM>(k.S + a, k.sh, k.adj + vi.x, vi_kl(vi), 0, vi_h(vi)).x;
     eacc += ((k.S[p * A + a] >> k.lane) & 1u) ? -Ilow : Ilow;
   }
   atomicAdd(&sh.E[a][k.lane], eacc);
@@ -295,7 +314,7 @@ __device__ void g_swap(const GCta &k, GShared &sh, uint32_t t, int joint, const 
 // bit-parallel flood fill over the graph, then either the cluster flips in
 // both replicas or, when it holds more than half of the n spins, one whole
 // replica (x1 bit 0) flips.
-template <int A>
+template <int A, bool SM>
 __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
   const uint32_t c3 = (k.ent << 8) | pcdev::TAG_G_ICM;
   if (k.tid < 32 * (A / 2)) {
@@ -384,10 +403,10 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
       for (int p = k.tid; p < k.n; p += kGThreads) {
         const uint32_t cl = k.Cl[p], cand = k.X[p] & ~cl;
         if (cand) {
-          const int2 vi = __ldg(k.vinfo + p);
+          const int2 vi = ld_vi<SM>(k.vinfo, p);
           const uint32_t *ad = k.adj + vi.x;
           uint32_t nb = 0;
-          for (int e = 0, d = vi_deg(vi); e < d; ++e) nb |= k.Cl[__ldg(ad + e) >> 8];
+          for (int e = 0, d = vi_deg(vi); e < d; ++e) nb |= k.Cl[ld_adj<SM>(ad, e) >> k.ushift];
           const uint32_t nw = cl | (cand & nb);
           if (nw != cl) {
             k.Cl[p] = nw;
@@ -429,7 +448,9 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
   }
 }
 
-template <int A>
+// SM: the problem's vertex table and adjacency are staged in shared memory
+// (when they fit) instead of being read through the L1 cache.
+template <int A, bool SM>
 __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init) {
   extern __shared__ __align__(16) uint32_t dyn[];
   __shared__ GShared sh;
@@ -445,14 +466,27 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   k.ent = P.ent;
   k.k0 = a.k0;
   k.k1 = a.k1;
-  k.vinfo = a.vinfo + P.vbase;
-  k.adj = a.adj + P.abase;
+  k.sh = 31u - (uint32_t)k.lane;
+  k.ushift = A == 1 ? 2 : (A == 2 ? 3 : 4);
   uint32_t *Th = dyn;
   const int nth = (2 * P.Imax + 1) * 32;
   k.Th = Th;
   k.S = Th + nth;
   k.X = k.S + (size_t)P.n * A;
   k.Cl = k.X + P.n;
+  if (SM) {
+    // vertex table at an 8-byte boundary after the cluster words, then the adjacency
+    const size_t vo = ((size_t)(nth + P.n * (A + 2)) + 1) & ~(size_t)1;
+    int2 *vs = reinterpret_cast<int2 *>(dyn + vo);
+    uint32_t *as = dyn + vo + 2 * (size_t)P.n;
+    for (int i = k.tid; i < P.n; i += kGThreads) vs[i] = a.vinfo[P.vbase + i];
+    for (int i = k.tid; i < P.m; i += kGThreads) as[i] = a.adj[P.abase + i];
+    k.vinfo = vs;
+    k.adj = as;
+  } else {
+    k.vinfo = a.vinfo + P.vbase;
+    k.adj = a.adj + P.abase;
+  }
   k.best_bits = a.best_bits + P.bestbase;
   uint32_t *gS = a.spins + (size_t)P.vbase * A;
   if (k.tid <= k.C) sh.off[k.tid] = P.off[k.tid];
@@ -461,7 +495,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   if (init) {
     __syncthreads();
     g_init<A>(k, sh);
-    g_energy<A>(k, sh);
+    g_energy<A, SM>(k, sh);
   } else {
     for (int i = k.tid; i < P.n * A; i += kGThreads) k.S[i] = gS[i];
     if (k.tid < 128) {
@@ -481,13 +515,13 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
     const uint32_t *swidx = a.swapidx + P.swbase;
     for (int t = 0; t < a.n_swaps; ++t) {
       const uint32_t tt = a.swap0 + (uint32_t)t;
-      for (int q = 0; q + 1 < a.spp; ++q) g_sweep<A, false>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q));
-      g_sweep<A, true>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + a.spp - 1));
+      for (int q = 0; q + 1 < a.spp; ++q) g_sweep<A, false, SM>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q));
+      g_sweep<A, true, SM>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + a.spp - 1));
       const long long done = (long long)a.sweep0 + (long long)(t + 1) * a.spp;
       g_best<A>(k, sh, done);
       if (A >= 2 && a.icm) {
-        g_icm<A>(k, sh, tt);
-        g_energy<A>(k, sh);
+        g_icm<A, SM>(k, sh, tt);
+        g_energy<A, SM>(k, sh);
         g_best<A>(k, sh, done);
       }
       g_swap<A>(k, sh, tt, a.joint, a.swaptab, swidx);
@@ -513,11 +547,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   if (k.tid < 128) a.E[128 * (size_t)blockIdx.x + k.tid] = sh.E[k.tid >> 5][k.tid & 31];
 }
 
-template <int A>
+template <int A, bool SM>
 int gapt_launch_t(const GAptArgs &a, int n_prob, size_t smem, bool init, cudaStream_t st) {
-  PC_CUDA_TRY(cudaFuncSetAttribute(gapt_kernel<A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PC_CUDA_TRY(cudaFuncSetAttribute(gapt_kernel<A, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
-  gapt_kernel<A><<<n_prob, kGThreads, smem, st>>>(a, init ? 1 : 0);
+  gapt_kernel<A, SM><<<n_prob, kGThreads, smem, st>>>(a, init ? 1 : 0);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
@@ -536,6 +570,12 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
   uint32_t *tab = dyn;                       // [2][3][2 Imax + 1]
   uint32_t *W = dyn + 2 * ntab;              // [P][n]
   const int n = a.n, P = a.P;
+  const size_t vo = (2 * (size_t)ntab + (size_t)P * n + 1) & ~(size_t)1;
+  int2 *vinfo = reinterpret_cast<int2 *>(dyn + vo);   // staged vertex table and adjacency
+  uint32_t *adj = dyn + vo + 2 * (size_t)n;
+  for (int i = tid; i < n; i += kGThreads) vinfo[i] = a.vinfo[i];
+  for (int i = tid; i < a.m; i += kGThreads) adj[i] = a.adj[i];
+  const uint32_t sh = 31u - (uint32_t)lane;
   const uint32_t run = a.run0 + 32u * blockIdx.x + (uint32_t)lane;
   const uint32_t c3i = (run << 8) | pcdev::TAG_GS_INIT;
   const uint32_t c3m = (run << 8) | pcdev::TAG_GS_SWEEP;
@@ -569,9 +609,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
           const uint32_t e = __ldg(a.cls + o0 + 8 * q + i);
           const int k = (int)(e >> 20), p = (int)(e & 0xFFFFFu);
           const uint32_t *Wk = W + (size_t)k * n;
-          const int2 vi = __ldg(a.vinfo + p);
-          const uint32_t *ad = a.adj + vi.x;
-          const int I = field<1, false>(Wk, lane, ad, vi_deg(vi), 0, 0, vi_h(vi)).x;
+          const int2 vi = vinfo[p];
+          const int I = field<false, true>(Wk, sh, adj + vi.x, vi_deg(vi), 0, vi_h(vi)).x;
           const int kd = k == 0 ? P - 1 : k - 1, ku = k == P - 1 ? 0 : k + 1;
           const uint32_t nup = ((W[(size_t)kd * n + p] >> lane) & 1u) + ((W[(size_t)ku * n + p] >> lane) & 1u);
           const uint32_t th = T[nup * nt + (I + a.Imax)];
@@ -595,9 +634,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
     const uint32_t *Wk = W + (size_t)k * n;
     long long eacc = 0;
     for (int p = warp; p < n; p += kGWarps) {
-      const int2 vi = __ldg(a.vinfo + p);
-      const uint32_t *ad = a.adj + vi.x;
-      const int Ilow = field<1, false>(Wk, lane, ad, vi_kl(vi), 0, 0, vi_h(vi)).x;
+      const int2 vi = vinfo[p];
+      const int Ilow = field<false, true>(Wk, sh, adj + vi.x, vi_kl(vi), 0, vi_h(vi)).x;
       eacc += ((Wk[p] >> lane) & 1u) ? -Ilow : Ilow;
     }
     if (lane < runs_here)
@@ -610,8 +648,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
 
 }  // namespace
 
-size_t gsqa_smem_bytes(int n, int P, int Imax) {
-  return sizeof(uint32_t) * ((size_t)6 * (2 * Imax + 1) + (size_t)P * n);
+size_t gsqa_smem_bytes(int n, int P, int Imax, int m) {
+  const size_t base = (size_t)6 * (2 * Imax + 1) + (size_t)P * n;
+  return sizeof(uint32_t) * (((base + 1) & ~(size_t)1) + 2 * (size_t)n + (size_t)m);
 }
 
 int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st) {
@@ -621,15 +660,21 @@ int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st) {
   return PC_OK;
 }
 
-size_t gapt_smem_bytes(int n, int A, int Imax) {
-  return sizeof(uint32_t) * ((size_t)(2 * Imax + 1) * 32 + (size_t)n * A + (size_t)2 * n);
+size_t gapt_smem_bytes(int n, int A, int Imax, int m) {
+  const size_t base = (size_t)(2 * Imax + 1) * 32 + (size_t)n * (A + 2);
+  if (m < 0) return sizeof(uint32_t) * base;
+  return sizeof(uint32_t) * (((base + 1) & ~(size_t)1) + 2 * (size_t)n + (size_t)m);
 }
 
-int gapt_launch(const GAptArgs &a, int n_prob, int A, size_t smem, bool init, cudaStream_t st) {
-  switch (A) {
-    case 1: return gapt_launch_t<1>(a, n_prob, smem, init, st);
-    case 2: return gapt_launch_t<2>(a, n_prob, smem, init, st);
-    case 4: return gapt_launch_t<4>(a, n_prob, smem, init, st);
+int gapt_launch(const GAptArgs &a, int n_prob, int A, bool staged, size_t smem, bool init,
+                cudaStream_t st) {
+  switch (A * 2 + (staged ? 1 : 0)) {
+    case 2: return gapt_launch_t<1, false>(a, n_prob, smem, init, st);
+    case 3: return gapt_launch_t<1, true>(a, n_prob, smem, init, st);
+    case 4: return gapt_launch_t<2, false>(a, n_prob, smem, init, st);
+    case 5: return gapt_launch_t<2, true>(a, n_prob, smem, init, st);
+    case 8: return gapt_launch_t<4, false>(a, n_prob, smem, init, st);
+    case 9: return gapt_launch_t<4, true>(a, n_prob, smem, init, st);
     default: return fail(PC_EINVAL, "n_labels must be 1, 2 or 4");
   }
 }

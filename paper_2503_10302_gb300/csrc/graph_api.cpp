@@ -93,9 +93,10 @@ int dsatur(int n, const int32_t *rp, const int32_t *col, std::vector<int32_t> &c
   return PC_OK;
 }
 
-// Checks, colours (given or DSATUR) and renumbers one graph.
+// Checks, colours (given or DSATUR) and renumbers one graph; adjacency
+// entries carry the byte offset word_bytes * u of neighbour u's spin words.
 int build_graph(int n, const int32_t *rp, const int32_t *col, const int8_t *w, const int8_t *h,
-                const int32_t *colour, HGraph &g) {
+                const int32_t *colour, int word_bytes, HGraph &g) {
   int rc = check_graph(n, rp, col, w);
   if (rc) return rc;
   if (!w) return fail(PC_EINVAL, "graph: weights are NULL");
@@ -154,7 +155,8 @@ int build_graph(int n, const int32_t *rp, const int32_t *col, const int8_t *w, c
     const int hv = h ? (int)h[v] : 0;
     g.vinfo[p] = make_int2((int)g.adj.size(),
                            (int)((uint32_t)row.size() | ((uint32_t)kl << 10) | (((uint32_t)hv & 0xFFu) << 20)));
-    for (const auto &e : row) g.adj.push_back(((uint32_t)e.first << 8) | ((uint32_t)e.second & 0xFFu));
+    for (const auto &e : row)
+      g.adj.push_back(((uint32_t)(word_bytes * e.first) << 8) | ((uint32_t)e.second & 0xFFu));
   }
   return PC_OK;
 }
@@ -179,7 +181,8 @@ struct GImpl {
   DevBuf<int32_t> d_E;
   DevBuf<long long> d_best, d_target;
   DevBuf<unsigned long long> d_stats;
-  size_t smem = 0;
+  size_t smem = 0, smem_staged = 0;
+  bool staged = false;
   int64_t sweeps = 0, swaps = 0;
   int joint = 0;
   bool ready = false;
@@ -275,7 +278,7 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
     if (n < 1) return fail(PC_EINVAL, "n_vert must be >= 1");
     const int32_t *rpi = row_ptr + roff;
     if ((rc = build_graph(n, rpi, col + eoff, w + eoff, h ? h + voff : nullptr,
-                          colour ? colour + voff : nullptr, g)))
+                          colour ? colour + voff : nullptr, 4 * n_labels, g)))
       return rc;
     const int T = n_temps[i];
     if (T < 1 || T > 32) return fail(PC_EINVAL, "n_temps must lie in 1..32");
@@ -320,7 +323,8 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
     if (T == 1) swapidx.push_back(0u), swapidx.push_back(0u);
     stats.resize(stats.size() + 2 * (size_t)(T > 1 ? T - 1 : 0) * n_labels + 3, 0ull);
     bestw += (size_t)(n + 31) / 32;
-    im->smem = std::max(im->smem, gapt_smem_bytes(n, n_labels, g.Imax));
+    im->smem = std::max(im->smem, gapt_smem_bytes(n, n_labels, g.Imax, -1));
+    im->smem_staged = std::max(im->smem_staged, gapt_smem_bytes(n, n_labels, g.Imax, (int)g.adj.size()));
     im->hp.push_back(P);
     voff += (size_t)n;
     eoff += (size_t)rpi[n];
@@ -328,6 +332,9 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
     boff += (size_t)T;
   }
   if ((rc = static_smem_guard(c, im->smem))) return rc;
+  // stage vertex tables and adjacency in shared memory when the largest problem allows
+  im->staged = im->smem_staged + 8192 <= (size_t)c->smem_optin;
+  if (im->staged) im->smem = im->smem_staged;
   if (swaptab.empty()) swaptab.push_back(0u);
   if (adj.empty()) adj.push_back(0u);
   cudaStream_t st = c->stream;
@@ -347,7 +354,7 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
       (rc = im->d_E.alloc(128 * (size_t)n_prob)) || (rc = im->d_best_bits.zero(st)))
     return rc;
   GAptArgs a = make_args(c, im);
-  if ((rc = gapt_launch(a, n_prob, n_labels, im->smem, true, st))) return rc;
+  if ((rc = gapt_launch(a, n_prob, n_labels, im->staged, im->smem, true, st))) return rc;
   PC_CUDA_TRY(cudaStreamSynchronize(st));
   im->ready = true;
   return PC_OK;
@@ -372,7 +379,7 @@ int pc_gapt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
     a.n_swaps = chunk;
     a.sweep0 = (uint32_t)im->sweeps;
     a.swap0 = (uint32_t)im->swaps;
-    if ((rc = gapt_launch(a, im->n_prob, im->A, im->smem, false, c->stream))) return rc;
+    if ((rc = gapt_launch(a, im->n_prob, im->A, im->staged, im->smem, false, c->stream))) return rc;
     im->sweeps += (int64_t)chunk * sweeps_per_swap;
     im->swaps += chunk;
     left -= chunk;
@@ -500,9 +507,9 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
   for (int s = 0; s < n_sweeps; ++s)
     if (!(gamma[s] > 0)) return fail(PC_EINVAL, "gamma must be > 0");
   HGraph g;
-  int rc = build_graph(n, row_ptr, col, w, h, colour, g);
+  int rc = build_graph(n, row_ptr, col, w, h, colour, 4, g);
   if (rc) return rc;
-  const size_t smem = gsqa_smem_bytes(n, P, g.Imax);
+  const size_t smem = gsqa_smem_bytes(n, P, g.Imax, (int)g.adj.size());
   if ((rc = static_smem_guard(c, smem))) return rc;
   // colour classes of the replicated network, each ordered by slice, then vertex
   const int Cp = std::max(g.C, (P & 1) ? 3 : 2);
@@ -548,6 +555,7 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
   a.S = n_sweeps;
   a.Imax = g.Imax;
   a.R = R;
+  a.m = (int)g.adj.size();
   a.run0 = run0;
   a.k0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
   a.k1 = (uint32_t)(c->seed >> 32);

@@ -11,7 +11,9 @@
 //     start: first adjacency entry; deg: neighbours; kl: neighbours of a
 //     lower colour (they come first: adjacency is sorted by new index);
 //     h: the bias, int8.
-//   adj[e]   = (u << 8) | (w & 0xFF): neighbour u (new index), weight int8.
+//   adj[e]   = (o << 8) | (w & 0xFF): weight int8 and o = the byte offset of
+//     neighbour u's first spin word (4 A u in APT with A labels, 4 u in
+//     DT-SQA).
 //   spins    : word [p][a] holds label a's bit for 32 temperatures (lane r =
 //     temperature r, bit set = spin +1); unused temperatures stay 0.
 #pragma once
@@ -58,7 +60,7 @@ struct GAptArgs {
 };
 
 struct GSqaArgs {
-  int n, P, Cp, S, Imax, R;     // vertices, slices, colours, sweeps, field bound, runs
+  int n, P, Cp, S, Imax, R, m;  // vertices, slices, colours, sweeps, field bound, runs, adjacency entries
   uint32_t run0, k0, k1;
   const int2 *vinfo;            // as above
   const uint32_t *adj;
@@ -69,9 +71,12 @@ struct GSqaArgs {
   uint32_t *spins;              // [ceil(R/32)][P][n] words (nullable)
 };
 
-size_t gapt_smem_bytes(int n, int A, int Imax);
-int gapt_launch(const GAptArgs &a, int n_prob, int A, size_t smem, bool init, cudaStream_t st);
-size_t gsqa_smem_bytes(int n, int P, int Imax);
+// m < 0: vertex table and adjacency read from global memory; m >= 0: staged
+// in shared memory as well (m adjacency entries).
+size_t gapt_smem_bytes(int n, int A, int Imax, int m);
+int gapt_launch(const GAptArgs &a, int n_prob, int A, bool staged, size_t smem, bool init,
+                cudaStream_t st);
+size_t gsqa_smem_bytes(int n, int P, int Imax, int m);
 int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st);
 
 }  // namespace pc

@@ -154,3 +154,19 @@ def test_gsqa_zero_sweeps_is_the_initial_state(pc, orc):
     E2, s2 = orc.gsqa_anneal(g.rp, g.col, g.w, 3, 0.5, np.zeros(0), 33, seed=5, want_spins=True)
     assert np.array_equal(s1, s2) and np.array_equal(E1, E2)
     ctx.close()
+
+
+def test_gapt_large_graph_reads_adjacency_from_global_memory(pc, orc):
+    """A graph whose vertex table and adjacency do not fit in shared memory
+    next to its 4 labels of spin words: the kernel reads them through the L1
+    cache instead (the same results)."""
+    g = W.sparse_random_graph(7000, 6.0, 2, wmax=2)
+    betas = [W.geometric_ladder(32, 0.2, 3.0)]
+    ctx = pc.Context(0, 41)
+    pc.pc_gapt_load(ctx.h, [_trip(g)], betas, 4, 0)
+    o = orc.GApt([_trip(g)], betas, n_labels=4, seed=41)
+    for n_sw in (2, 6):
+        pc.pc_gapt_run(ctx.h, n_sw, 1, True)
+        o.run(n_sw, 1, True)
+        _compare(pc, ctx, o, [g], betas, 4)
+    ctx.close()
