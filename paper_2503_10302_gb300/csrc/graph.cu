@@ -49,7 +49,7 @@ struct GShared {
 struct GCta {
   int n, C, T, Imax, tid, lane, warp;
   uint32_t sh;                   // 31 - lane
-  int ushift;                    // adjacency byte offset >> ushift = neighbour index
+  int ushift;                    // adjacency entry >> ushift = neighbour index (8 + log2(4 A))
   uint32_t ent, k0, k1;
   const int2 *vinfo;
   const uint32_t *adj;
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   k.k0 = a.k0;
   k.k1 = a.k1;
   k.sh = 31u - (uint32_t)k.lane;
-  k.ushift = A == 1 ? 2 : (A == 2 ? 3 : 4);
+  k.ushift = 8 + (A == 1 ? 2 : (A == 2 ? 3 : 4));
   uint32_t *Th = dyn;
   const int nth = (2 * P.Imax + 1) * 32;
   k.Th = Th;
