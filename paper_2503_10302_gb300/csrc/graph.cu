@@ -49,7 +49,9 @@ struct GShared {
 struct GCta {
   int n, C, T, Imax, tid, lane, warp;
   uint32_t sh;                   // 31 - lane
-  int ushift;                    // adjacency entry >> ushift = neighbour index (8 + log2(4 A))
+  int ushift;                    // (entry >> 8) - ubase >> ushift = neighbour index
+  uint32_t ubase;                // byte offset of the spin words from the dynamic base
+  const char *dynb;              // dynamic shared-memory base
   uint32_t ent, k0, k1;
   const int2 *vinfo;
   const uint32_t *adj;
@@ -76,49 +78,40 @@ __device__ __forceinline__ int2 ld_vi(const int2 *vi, int p) {
   return __ldg(vi + p);
 }
 
-// Eq. synapse of the lane's replica over the deg neighbours at ad; Sa is the
-// label's first spin word and an entry's top 24 bits are the byte offset of
-// the neighbour's word from it.  With m = -1 (spin +1) or 0 (spin -1) taken
-// by shifting the lane's bit into the sign, the neighbour adds
-// (w ^ ~m) + m + 1 = +-w; the +1s are added once at the end.  .x = h +
-// sum_u w_vu s_u, .y = the same over the first kl (lower-colour)
-// neighbours.  Groups of 4 and 2 neighbours issue their loads together.
-template <bool LOW, bool SM>
-__device__ __forceinline__ int2 field(const uint32_t *Sa, uint32_t sh, const uint32_t *ad, int deg, int kl,
-                                      int h) {
-  const char *Sb = reinterpret_cast<const char *>(Sa);
-  int acc = 0, accl = 0, e = 0;
-  for (; e + 4 <= deg; e += 4) {
-    uint32_t en[4], sw[4];
+// Eq. synapse over neighbours [e0, e1) for the lane's replica in each of the
+// A labels.  An adjacency entry's top 24 bits are the byte offset, from the
+// dynamic shared-memory base `dynb`, of the neighbour's word of label 0 (its
+// label-a word follows at +4a).  With m = -1 (spin +1) or 0 (spin -1) taken
+// by shifting the lane's bit into the sign, a neighbour adds
+// (w ^ ~m) + m + 1 = +-w; the caller adds the +1s (the neighbour count).
+// The entry is decoded once for all labels; pairs of neighbours issue their
+// loads together.
+template <int A, bool SM>
+__device__ __forceinline__ void field_acc(const char *dynb, uint32_t sh, const uint32_t *ad, int e0,
+                                          int e1, int (&acc)[A]) {
+  int e = e0;
+  for (; e + 2 <= e1; e += 2) {
+    const uint32_t n0 = ld_adj<SM>(ad, e), n1 = ld_adj<SM>(ad, e + 1);
+    const char *p0 = dynb + (n0 >> 8), *p1 = dynb + (n1 >> 8);
+    const int w0 = ent_w(n0), w1 = ent_w(n1);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) en[j] = ld_adj<SM>(ad, e + j);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) sw[j] = *reinterpret_cast<const uint32_t *>(Sb + (en[j] >> 8));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int m = (int)(sw[j] << sh) >> 31, c = (ent_w(en[j]) ^ ~m) + m;
-      acc += c;
-      if (LOW) accl += (e + j < kl) ? c : 0;
+    for (int a = 0; a < A; ++a) {
+      const uint32_t s0 = *reinterpret_cast<const uint32_t *>(p0 + 4 * a);
+      const uint32_t s1 = *reinterpret_cast<const uint32_t *>(p1 + 4 * a);
+      const int m0 = (int)(s0 << sh) >> 31, m1 = (int)(s1 << sh) >> 31;
+      acc[a] += ((w0 ^ ~m0) + m0) + ((w1 ^ ~m1) + m1);
     }
   }
-  if (e + 2 <= deg) {
-    const uint32_t e0 = ld_adj<SM>(ad, e), e1 = ld_adj<SM>(ad, e + 1);
-    const uint32_t s0 = *reinterpret_cast<const uint32_t *>(Sb + (e0 >> 8));
-    const uint32_t s1 = *reinterpret_cast<const uint32_t *>(Sb + (e1 >> 8));
-    const int m0 = (int)(s0 << sh) >> 31, m1 = (int)(s1 << sh) >> 31;
-    const int c0 = (ent_w(e0) ^ ~m0) + m0, c1 = (ent_w(e1) ^ ~m1) + m1;
-    acc += c0 + c1;
-    if (LOW) accl += (e < kl ? c0 : 0) + (e + 1 < kl ? c1 : 0);
-    e += 2;
+  if (e < e1) {
+    const uint32_t n0 = ld_adj<SM>(ad, e);
+    const char *p0 = dynb + (n0 >> 8);
+    const int w0 = ent_w(n0);
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int m0 = (int)(*reinterpret_cast<const uint32_t *>(p0 + 4 * a) << sh) >> 31;
+      acc[a] += (w0 ^ ~m0) + m0;
+    }
   }
-  if (e < deg) {
-    const uint32_t e0 = ld_adj<SM>(ad, e);
-    const int m0 = (int)(*reinterpret_cast<const uint32_t *>(Sb + (e0 >> 8)) << sh) >> 31;
-    const int c0 = (ent_w(e0) ^ ~m0) + m0;
-    acc += c0;
-    if (LOW) accl += e < kl ? c0 : 0;
-  }
-  return make_int2(h + acc + deg, h + accl + kl);
 }
 
 // Random initial states (Algorithm S2): +1 iff the init half is below 2^15.
@@ -144,44 +137,61 @@ __device__ void g_init(const GCta &k, GShared &sh) {
 }
 
 // One sweep, colour class by colour class (Algorithm S2's p-computer loop).
-// With wantE the energy of every replica (Eq. ising_energy) is gathered on
-// the way: each bond is counted at its endpoint of higher colour, whose
-// lower-colour neighbours already hold this sweep's values.
+// A warp takes chunks of 8 vertices of the class and updates every label's
+// replicas of each vertex.  With WANT_E the energy of every replica (Eq.
+// ising_energy) is gathered on the way: each bond is counted at its endpoint
+// of higher colour, whose lower-colour neighbours (the first kl) already
+// hold this sweep's values.
 template <int A, bool WANT_E, bool SM>
 __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
   if (WANT_E && k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
-  const int a = k.warp % A;
   const uint32_t c3m = (k.ent << 8) | pcdev::TAG_G_SWEEP;
   const uint32_t c3r = (k.ent << 8) | pcdev::TAG_G_REFINE;
-  int eacc = 0;
+  int eacc[A];
+#pragma unroll
+  for (int a = 0; a < A; ++a) eacc[a] = 0;
   for (int c = 0; c < k.C; ++c) {
     const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
-    const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(32 * a + k.lane);
-    for (int q = k.warp / A; 8 * q < nc; q += kGWarps / A) {
-      const uint4 x = philox((uint32_t)q, s, c2, c3m, k.k0, k.k1);
+    const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)k.lane;
+    for (int q = k.warp; 8 * q < nc; q += kGWarps) {
+      uint4 x[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) x[a] = philox((uint32_t)q, s, c2 + 32u * a, c3m, k.k0, k.k1);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         if (8 * q + i >= nc) break;
         const int p = o0 + 8 * q + i;
         const int2 vi = ld_vi<SM>(k.vinfo, p);
-        const int2 f = field<WANT_E, SM>(k.S + a, k.sh, k.adj + vi.x, vi_deg(vi), vi_kl(vi), vi_h(vi));
-        const int I = f.x, Ilow = f.y;
-        const uint32_t th = k.Th[(I + k.Imax) * 32 + k.lane];
-        const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
-        bool up = v < thi;
-        if (v == thi) {   // probability 2^-16: settle with the refine half
-          const uint4 y = philox((uint32_t)q, s, c2, c3r, k.k0, k.k1);
-          up = (v | half_lo(y, i)) < th;
+        const uint32_t *ad = k.adj + vi.x;
+        const int deg = vi_deg(vi), kl = vi_kl(vi), h = vi_h(vi);
+        int acc[A], Il[A];
+#pragma unroll
+        for (int a = 0; a < A; ++a) acc[a] = 0;
+        field_acc<A, SM>(k.dynb, k.sh, ad, 0, kl, acc);
+#pragma unroll
+        for (int a = 0; a < A; ++a) Il[a] = h + acc[a] + kl;
+        field_acc<A, SM>(k.dynb, k.sh, ad, kl, deg, acc);
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          const int I = h + acc[a] + deg;
+          const uint32_t th = k.Th[(I + k.Imax) * 32 + k.lane];
+          const uint32_t v = half_hi(x[a], i), thi = th & 0xFFFF0000u;
+          bool up = v < thi;
+          if (v == thi) {   // probability 2^-16: settle with the refine half
+            const uint4 y = philox((uint32_t)q, s, c2 + 32u * a, c3r, k.k0, k.k1);
+            up = (v | half_lo(y, i)) < th;
+          }
+          const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
+          if (k.lane == 0) k.S[p * A + a] = word;
+          if (WANT_E) eacc[a] += up ? -Il[a] : Il[a];
         }
-        const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
-        if (k.lane == 0) k.S[p * A + a] = word;
-        if (WANT_E) eacc += up ? -Ilow : Ilow;
       }
     }
     __syncthreads();
   }
   if (WANT_E) {
-    atomicAdd(&sh.E[a][k.lane], eacc);
+#pragma unroll
+    for (int a = 0; a < A; ++a) atomicAdd(&sh.E[a][k.lane], eacc[a]);
     __syncthreads();
   }
 }
@@ -191,14 +201,23 @@ template <int A, bool SM>
 __device__ void g_energy(const GCta &k, GShared &sh) {
   if (k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
   __syncthreads();
-  const int a = k.warp % A;
-  int eacc = 0;
-  for (int p = k.warp / A; p < k.n; p += kGWarps / A) {
+  int eacc[A];
+#pragma unroll
+  for (int a = 0; a < A; ++a) eacc[a] = 0;
+  for (int p = k.warp; p < k.n; p += kGWarps) {
     const int2 vi = ld_vi<SM>(k.vinfo, p);
-    const int Ilow = field<false, SM>(k.S + a, k.sh, k.adj + vi.x, vi_kl(vi), 0, vi_h(vi)).x;
-    eacc += ((k.S[p * A + a] >> k.lane) & 1u) ? -Ilow : Ilow;
+    int acc[A];
+#pragma unroll
+    for (int a = 0; a < A; ++a) acc[a] = 0;
+    field_acc<A, SM>(k.dynb, k.sh, k.adj + vi.x, 0, vi_kl(vi), acc);
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+      const int Il = vi_h(vi) + acc[a] + vi_kl(vi);
+      eacc[a] += ((k.S[p * A + a] >> k.lane) & 1u) ? -Il : Il;
+    }
   }
-  atomicAdd(&sh.E[a][k.lane], eacc);
+#pragma unroll
+  for (int a = 0; a < A; ++a) atomicAdd(&sh.E[a][k.lane], eacc[a]);
   __syncthreads();
 }
 
@@ -406,7 +425,8 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
           const int2 vi = ld_vi<SM>(k.vinfo, p);
           const uint32_t *ad = k.adj + vi.x;
           uint32_t nb = 0;
-          for (int e = 0, d = vi_deg(vi); e < d; ++e) nb |= k.Cl[ld_adj<SM>(ad, e) >> k.ushift];
+          for (int e = 0, d = vi_deg(vi); e < d; ++e)
+            nb |= k.Cl[((ld_adj<SM>(ad, e) >> 8) - k.ubase) >> k.ushift];
           const uint32_t nw = cl | (cand & nb);
           if (nw != cl) {
             k.Cl[p] = nw;
@@ -467,11 +487,13 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   k.k0 = a.k0;
   k.k1 = a.k1;
   k.sh = 31u - (uint32_t)k.lane;
-  k.ushift = 8 + (A == 1 ? 2 : (A == 2 ? 3 : 4));
+  k.ushift = A == 1 ? 2 : (A == 2 ? 3 : 4);
+  k.dynb = reinterpret_cast<const char *>(dyn);
   uint32_t *Th = dyn;
   const int nth = (2 * P.Imax + 1) * 32;
   k.Th = Th;
   k.S = Th + nth;
+  k.ubase = 4u * (uint32_t)nth;
   k.X = k.S + (size_t)P.n * A;
   k.Cl = k.X + P.n;
   if (SM) {
@@ -610,7 +632,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
           const int k = (int)(e >> 20), p = (int)(e & 0xFFFFFu);
           const uint32_t *Wk = W + (size_t)k * n;
           const int2 vi = vinfo[p];
-          const int I = field<false, true>(Wk, sh, adj + vi.x, vi_deg(vi), 0, vi_h(vi)).x;
+          int acc[1] = {0};
+          field_acc<1, true>(reinterpret_cast<const char *>(Wk), sh, adj + vi.x, 0, vi_deg(vi), acc);
+          const int I = vi_h(vi) + acc[0] + vi_deg(vi);
           const int kd = k == 0 ? P - 1 : k - 1, ku = k == P - 1 ? 0 : k + 1;
           const uint32_t nup = ((W[(size_t)kd * n + p] >> lane) & 1u) + ((W[(size_t)ku * n + p] >> lane) & 1u);
           const uint32_t th = T[nup * nt + (I + a.Imax)];
@@ -635,7 +659,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
     long long eacc = 0;
     for (int p = warp; p < n; p += kGWarps) {
       const int2 vi = vinfo[p];
-      const int Ilow = field<false, true>(Wk, sh, adj + vi.x, vi_kl(vi), 0, vi_h(vi)).x;
+      int acc[1] = {0};
+      field_acc<1, true>(reinterpret_cast<const char *>(Wk), sh, adj + vi.x, 0, vi_kl(vi), acc);
+      const int Ilow = vi_h(vi) + acc[0] + vi_kl(vi);
       eacc += ((Wk[p] >> lane) & 1u) ? -Ilow : Ilow;
     }
     if (lane < runs_here)

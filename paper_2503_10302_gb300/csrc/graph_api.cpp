@@ -280,6 +280,9 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
     if ((rc = build_graph(n, rpi, col + eoff, w + eoff, h ? h + voff : nullptr,
                           colour ? colour + voff : nullptr, 4 * n_labels, g)))
       return rc;
+    // the kernel addresses spin words by their byte offset from the dynamic
+    // shared-memory base, where they follow the [2 Imax + 1][32] p-bit table
+    for (auto &e : g.adj) e += (uint32_t)(4 * (2 * g.Imax + 1) * 32) << 8;
     const int T = n_temps[i];
     if (T < 1 || T > 32) return fail(PC_EINVAL, "n_temps must lie in 1..32");
     const double *beta = betas + boff;
