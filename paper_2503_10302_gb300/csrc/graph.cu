@@ -67,6 +67,10 @@ __device__ __forceinline__ int vi_kl(int2 v) { return (v.y >> 10) & 1023; }
 __device__ __forceinline__ int vi_h(int2 v) { return (int)(int8_t)(uint8_t)((uint32_t)v.y >> 20); }
 __device__ __forceinline__ int ent_w(uint32_t e) { return (int)(int8_t)(uint8_t)(e & 0xFFu); }
 
+__device__ __forceinline__ uint32_t word_sel(const uint4 &x, int w) {
+  return w == 0 ? x.x : (w == 1 ? x.y : (w == 2 ? x.z : x.w));
+}
+
 template <bool SM>
 __device__ __forceinline__ uint32_t ld_adj(const uint32_t *ad, int e) {
   if (SM) return ad[e];
@@ -157,33 +161,42 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
       uint4 x[A];
 #pragma unroll
       for (int a = 0; a < A; ++a) x[a] = philox((uint32_t)q, s, c2 + 32u * a, c3m, k.k0, k.k1);
+      // Philox word wd serves vertices 2 wd and 2 wd + 1 of the chunk (low,
+      // high half); the loop over words stays rolled to keep the code small
+#pragma unroll 1
+      for (int wd = 0; wd < 4 && 8 * q + 2 * wd < nc; ++wd) {
+        uint32_t xw[A];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (8 * q + i >= nc) break;
-        const int p = o0 + 8 * q + i;
-        const int2 vi = ld_vi<SM>(k.vinfo, p);
-        const uint32_t *ad = k.adj + vi.x;
-        const int deg = vi_deg(vi), kl = vi_kl(vi), h = vi_h(vi);
-        int acc[A], Il[A];
+        for (int a = 0; a < A; ++a) xw[a] = word_sel(x[a], wd);
 #pragma unroll
-        for (int a = 0; a < A; ++a) acc[a] = 0;
-        field_acc<A, SM>(k.dynb, k.sh, ad, 0, kl, acc);
+        for (int hh = 0; hh < 2; ++hh) {
+          const int i = 2 * wd + hh;
+          if (8 * q + i >= nc) break;
+          const int p = o0 + 8 * q + i;
+          const int2 vi = ld_vi<SM>(k.vinfo, p);
+          const uint32_t *ad = k.adj + vi.x;
+          const int deg = vi_deg(vi), kl = vi_kl(vi), h = vi_h(vi);
+          int acc[A], Il[A];
 #pragma unroll
-        for (int a = 0; a < A; ++a) Il[a] = h + acc[a] + kl;
-        field_acc<A, SM>(k.dynb, k.sh, ad, kl, deg, acc);
+          for (int a = 0; a < A; ++a) acc[a] = 0;
+          field_acc<A, SM>(k.dynb, k.sh, ad, 0, kl, acc);
 #pragma unroll
-        for (int a = 0; a < A; ++a) {
-          const int I = h + acc[a] + deg;
-          const uint32_t th = k.Th[(I + k.Imax) * 32 + k.lane];
-          const uint32_t v = half_hi(x[a], i), thi = th & 0xFFFF0000u;
-          bool up = v < thi;
-          if (v == thi) {   // probability 2^-16: settle with the refine half
-            const uint4 y = philox((uint32_t)q, s, c2 + 32u * a, c3r, k.k0, k.k1);
-            up = (v | half_lo(y, i)) < th;
+          for (int a = 0; a < A; ++a) Il[a] = h + acc[a] + kl;
+          field_acc<A, SM>(k.dynb, k.sh, ad, kl, deg, acc);
+#pragma unroll
+          for (int a = 0; a < A; ++a) {
+            const int I = h + acc[a] + deg;
+            const uint32_t th = k.Th[(I + k.Imax) * 32 + k.lane];
+            const uint32_t v = hh ? (xw[a] & 0xFFFF0000u) : (xw[a] << 16), thi = th & 0xFFFF0000u;
+            bool up = v < thi;
+            if (v == thi) {   // probability 2^-16: settle with the refine half
+              const uint32_t yw = word_sel(philox((uint32_t)q, s, c2 + 32u * a, c3r, k.k0, k.k1), wd);
+              up = (v | (hh ? (yw >> 16) : (yw & 0xFFFFu))) < th;
+            }
+            const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
+            if (k.lane == 0) k.S[p * A + a] = word;
+            if (WANT_E) eacc[a] += up ? -Il[a] : Il[a];
           }
-          const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
-          if (k.lane == 0) k.S[p * A + a] = word;
-          if (WANT_E) eacc[a] += up ? -Il[a] : Il[a];
         }
       }
     }
