@@ -10,10 +10,7 @@ enum : uint32_t {
   TAG_APT_INIT = 1, TAG_APT_SWEEP = 2, TAG_APT_REFINE = 3, TAG_SWAP = 4, TAG_ICM = 5,
   TAG_LAD_INIT = 6, TAG_LAD_SWEEP = 7, TAG_LAD_REFINE = 8,
   TAG_PIL_INIT = 9, TAG_PIL_SWEEP = 10, TAG_PIL_REFINE = 11,
-  TAG_SQA_INIT = 12, TAG_SQA_SWEEP = 13, TAG_SQA_REFINE = 14,
-  // general sparse graphs
-  TAG_G_INIT = 15, TAG_G_SWEEP = 16, TAG_G_REFINE = 17, TAG_G_SWAP = 18, TAG_G_ICM = 19,
-  TAG_GS_INIT = 20, TAG_GS_SWEEP = 21, TAG_GS_REFINE = 22
+  TAG_SQA_INIT = 12, TAG_SQA_SWEEP = 13, TAG_SQA_REFINE = 14
 };
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Per round the two

@@ -29,6 +29,12 @@ using pcdev::half_hi;
 using pcdev::half_lo;
 using pcdev::philox;
 
+// Counter tags of the general-graph draws (the lattice kernels use 1..14).
+enum : uint32_t {
+  TAG_G_INIT = 15, TAG_G_SWEEP = 16, TAG_G_REFINE = 17, TAG_G_SWAP = 18, TAG_G_ICM = 19,
+  TAG_GS_INIT = 20, TAG_GS_SWEEP = 21, TAG_GS_REFINE = 22
+};
+
 struct GShared {
   int off[kGMaxColours + 1];
   int32_t E[4][32];              // energy of label a, temperature r
@@ -125,7 +131,7 @@ __device__ void g_init(const GCta &k, GShared &sh) {
   for (int c = 0; c < k.C; ++c) {
     const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
     const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(32 * a + k.lane);
-    const uint32_t c3 = (k.ent << 8) | pcdev::TAG_G_INIT;
+    const uint32_t c3 = (k.ent << 8) | TAG_G_INIT;
     for (int q = k.warp / A; 8 * q < nc; q += kGWarps / A) {
       const uint4 x = philox((uint32_t)q, 0u, c2, c3, k.k0, k.k1);
 #pragma unroll
@@ -149,8 +155,8 @@ __device__ void g_init(const GCta &k, GShared &sh) {
 template <int A, bool WANT_E, bool SM>
 __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
   if (WANT_E && k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
-  const uint32_t c3m = (k.ent << 8) | pcdev::TAG_G_SWEEP;
-  const uint32_t c3r = (k.ent << 8) | pcdev::TAG_G_REFINE;
+  const uint32_t c3m = (k.ent << 8) | TAG_G_SWEEP;
+  const uint32_t c3r = (k.ent << 8) | TAG_G_REFINE;
   int eacc[A];
 #pragma unroll
   for (int a = 0; a < A; ++a) eacc[a] = 0;
@@ -284,7 +290,7 @@ __device__ void g_swap(const GCta &k, GShared &sh, uint32_t t, int joint, const 
   if (k.tid < 4) sh.swmask[k.tid] = 0u;
   __syncthreads();
   const int r0 = (int)(t & 1u), npairs = (k.T - r0) / 2;
-  const uint32_t c3 = (k.ent << 8) | pcdev::TAG_G_SWAP;
+  const uint32_t c3 = (k.ent << 8) | TAG_G_SWAP;
   if (joint) {
     if (k.tid < npairs) {
       const int r = r0 + 2 * k.tid;
@@ -348,7 +354,7 @@ __device__ void g_swap(const GCta &k, GShared &sh, uint32_t t, int joint, const 
 // replica (x1 bit 0) flips.
 template <int A, bool SM>
 __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
-  const uint32_t c3 = (k.ent << 8) | pcdev::TAG_G_ICM;
+  const uint32_t c3 = (k.ent << 8) | TAG_G_ICM;
   if (k.tid < 32 * (A / 2)) {
     const int pp = k.tid >> 5, r = k.tid & 31;
     if (r < k.T) {
@@ -612,9 +618,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
   for (int i = tid; i < a.m; i += kGThreads) adj[i] = a.adj[i];
   const uint32_t sh = 31u - (uint32_t)lane;
   const uint32_t run = a.run0 + 32u * blockIdx.x + (uint32_t)lane;
-  const uint32_t c3i = (run << 8) | pcdev::TAG_GS_INIT;
-  const uint32_t c3m = (run << 8) | pcdev::TAG_GS_SWEEP;
-  const uint32_t c3r = (run << 8) | pcdev::TAG_GS_REFINE;
+  const uint32_t c3i = (run << 8) | TAG_GS_INIT;
+  const uint32_t c3m = (run << 8) | TAG_GS_SWEEP;
+  const uint32_t c3r = (run << 8) | TAG_GS_REFINE;
   // Algorithm S1: random initial states of all slices
   for (int c = 0; c < a.Cp; ++c) {
     const int o0 = a.cls_off[c], nc = a.cls_off[c + 1] - o0;
