@@ -224,12 +224,12 @@ void or_gapt_destroy(or_gapt *g) {
 static void g_init_slot(const g_entry *e, int b, uint64_t seed) {
   for (int v = 0; v < e->n; ++v) {
     const int j = e->cidx[v];
-    uint32_t ctr[4] = {(uint32_t)(j >> 3), 0u,
-                       ((uint32_t)e->colour[v] << 16) | (uint32_t)e->rid[b],
+    uint32_t ctr[4] = {(uint32_t)j, 0u,
+                       ((uint32_t)e->colour[v] << 16) | (uint32_t)(e->rid[b] >> 3),
                        (e->ent << 8) | OR_TAG_G_INIT};
     uint32_t x[4];
     or_philox(ctr, seed, x);
-    e->spin[(size_t)b * e->n + v] = (or_half(x, j & 7) < 0x8000u) ? 1 : -1;
+    e->spin[(size_t)b * e->n + v] = (or_half(x, e->rid[b] & 7) < 0x8000u) ? 1 : -1;
   }
 }
 
@@ -245,9 +245,9 @@ static void g_sweep(g_entry *e, uint64_t seed, uint32_t s) {
         if (e->colour[v] != c) continue;
         int64_t I = g_field(e->rp, e->col, e->w, e->h, sb, v);
         const int j = e->cidx[v];
-        uint32_t u = or_uniform32(seed, (uint32_t)(j >> 3), s,
-                                  ((uint32_t)c << 16) | (uint32_t)e->rid[b], e->ent,
-                                  OR_TAG_G_SWEEP, OR_TAG_G_REFINE, j & 7);
+        uint32_t u = or_uniform32(seed, (uint32_t)j, s,
+                                  ((uint32_t)c << 16) | (uint32_t)(e->rid[b] >> 3), e->ent,
+                                  OR_TAG_G_SWEEP, OR_TAG_G_REFINE, e->rid[b] & 7);
         sb[v] = (u < T[I + e->Imax]) ? 1 : -1;
       }
     }

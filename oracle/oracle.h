@@ -140,10 +140,12 @@ int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const uint8_
  * canonical vertex order is colour 0 by increasing v, then colour 1, ...
  *
  * Randomness (APT on graphs): replica in slot (temperature r, label a) has
- * id b = 32 a + r (T <= 32); vertex v of colour c at sweep s uses
- *   hi = v_{j&7}(Philox((j >> 3, s, (c << 16) | b, (e << 8) | TAG_G_SWEEP)))
+ * id b = 32 a + r (T <= 32), group g = b >> 3 and half i = b & 7, as the
+ * lattice path's replica groups; vertex v of colour c (colour-local index j)
+ * at sweep s uses
+ *   hi = v_i(Philox((j, s, (c << 16) | g, (e << 8) | TAG_G_SWEEP)))
  *   lo = the same half of the TAG_G_REFINE block;  +1 iff (hi<<16|lo) < T.
- * Initial spin: +1 iff v_{j&7}(Philox((j>>3, 0, (c<<16)|b, (e<<8)|TAG_G_INIT))) < 2^15.
+ * Initial spin: +1 iff v_i(Philox((j, 0, (c<<16)|g, (e<<8)|TAG_G_INIT))) < 2^15.
  * Swap of pair (r, r+1), label a, attempt t: word 0 of P(r, t, a, (e<<8)|TAG_G_SWAP).
  * ICM of pair p at temperature r, attempt t: P(r, t, p, (e<<8)|TAG_G_ICM),
  * words as in the lattice path (seed k, whole-replica bit, 4-label matching).

@@ -4,15 +4,14 @@
 // colour class as the colormap of the paper's graph-coloured architecture
 // prescribes (Methods, "Graph Coloring of 3D Cubic Spin Glass Instances").
 //
-// Layout: one 32-bit word per (vertex, label) holds 32 replicas, one per
-// lane.  In APT the lanes are the temperatures of one label; in DT-SQA they
-// are 32 independent runs.  A warp updates one vertex for all 32 replicas at
-// once: its neighbours' words are warp-uniform shared-memory broadcasts,
-// each lane extracts its own bit, accumulates Eq. synapse, looks up Eq.
-// neuron's threshold in a [field][lane] table (bank = lane, conflict free)
-// and the 32 decisions are packed back with one ballot.  One Philox call of
-// a lane serves 8 consecutive vertices of its colour class (16-bit halves;
-// the refine block settles ties exactly, as in the lattice kernels).
+// Layout: one 32-bit word per (vertex, label) holds 32 replicas.  In APT
+// they are the 32 temperatures of one label and a thread owns a (vertex,
+// label) pair: the field of all 32 replicas is summed bit-sliced over the
+// neighbour words, then each replica looks up Eq. neuron's threshold and
+// compares it with its half of a Philox block that serves 8 replicas (16-bit
+// halves; the refine block settles ties exactly, as in the lattice kernels).
+// In DT-SQA the 32 bits are independent runs and a warp updates one vertex,
+// one run per lane.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -54,6 +53,7 @@ struct GShared {
 
 struct GCta {
   int n, C, T, Imax, tid, lane, warp;
+  int ths;                       // row length of the [temperature][field] table
   uint32_t sh;                   // 31 - lane
   int ushift;                    // (entry >> 8) - ubase >> ushift = neighbour index
   uint32_t ubase;                // byte offset of the spin words from the dynamic base
@@ -72,10 +72,6 @@ __device__ __forceinline__ int vi_deg(int2 v) { return v.y & 1023; }
 __device__ __forceinline__ int vi_kl(int2 v) { return (v.y >> 10) & 1023; }
 __device__ __forceinline__ int vi_h(int2 v) { return (int)(int8_t)(uint8_t)((uint32_t)v.y >> 20); }
 __device__ __forceinline__ int ent_w(uint32_t e) { return (int)(int8_t)(uint8_t)(e & 0xFFu); }
-
-__device__ __forceinline__ uint32_t word_sel(const uint4 &x, int w) {
-  return w == 0 ? x.x : (w == 1 ? x.y : (w == 2 ? x.z : x.w));
-}
 
 template <bool SM>
 __device__ __forceinline__ uint32_t ld_adj(const uint32_t *ad, int e) {
@@ -124,119 +120,220 @@ __device__ __forceinline__ void field_acc(const char *dynb, uint32_t sh, const u
   }
 }
 
-// Random initial states (Algorithm S2): +1 iff the init half is below 2^15.
+// ---------------------------------------------------------------- bit-sliced sweeps
+// A thread owns one (vertex, label) pair: its 32-bit spin word holds the
+// label's 32 temperatures.  The field of all 32 replicas is summed
+// bit-sliced: with t = the neighbour's word, inverted when w < 0 (bit set:
+// w s_u = +|w|), C = sum_u |w_vu| t_u is kept as NP bit planes, and
+// I = 2 C - W + h with W = sum_u |w_vu|.  Each replica then reads its count,
+// looks up Eq. neuron's threshold in a [temperature][field] table (rows of
+// odd length 2 Imax + 1, so lanes with different fields hit different
+// banks) and compares it with its half of the group's Philox block.
+
+// Adds wabs * t (wabs in 1..127) to the bit-sliced counter P (ripple carry).
+template <int NP>
+__device__ __forceinline__ void vadd(uint32_t (&P)[NP], uint32_t t, uint32_t wabs) {
+  if (wabs == 1u) {
+    uint32_t c = t;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const uint32_t n = P[q] & c;
+      P[q] ^= c;
+      c = n;
+    }
+    return;
+  }
+#pragma unroll
+  for (int b = 0; b < 7; ++b) {
+    if (!((wabs >> b) & 1u)) continue;
+    uint32_t c = t;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      if (q < b) continue;
+      const uint32_t n = P[q] & c;
+      P[q] ^= c;
+      c = n;
+    }
+  }
+}
+
+// Count of replica r held in the planes (r a compile-time constant after unrolling).
+template <int NP>
+__device__ __forceinline__ int vget(const uint32_t (&P)[NP], int r) {
+  int C = 0;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) C |= (int)((P[q] >> r) & 1u) << q;
+  return C;
+}
+
+// Adds the neighbours [e0, e1) of one vertex, label a, into the planes;
+// returns their sum of |w|.
+template <int A, int NP, bool SM>
+__device__ __forceinline__ int vfield(const char *dynb, const uint32_t *ad, int e0, int e1, int a,
+                                      uint32_t (&P)[NP]) {
+  int W = 0;
+  for (int e = e0; e < e1; ++e) {
+    const uint32_t en = ld_adj<SM>(ad, e);
+    const int w = ent_w(en);
+    uint32_t t = *reinterpret_cast<const uint32_t *>(dynb + (en >> 8) + 4 * a);
+    if (w < 0) t = ~t;
+    const uint32_t wabs = (uint32_t)(w < 0 ? -w : w);
+    vadd<NP>(P, t, wabs);
+    W += (int)wabs;
+  }
+  return W;
+}
+
+// Item i of a phase -> (vertex offset, label): the 32 threads of a warp share
+// a label and take 32 consecutive vertices.
+template <int A>
+__device__ __forceinline__ void item_of(int i, int &v, int &a) {
+  const int wi = i >> 5;
+  a = wi % A;
+  v = 32 * (wi / A) + (i & 31);
+}
+
+// Random initial states (Algorithm S2): replica b = 32 a + r takes half
+// b & 7 of P(j, 0, (c << 16) | (b >> 3), (e << 8) | TAG_G_INIT); +1 iff it is
+// below 2^15.
 template <int A>
 __device__ void g_init(const GCta &k, GShared &sh) {
-  const int a = k.warp % A;
+  const uint32_t c3 = (k.ent << 8) | TAG_G_INIT;
   for (int c = 0; c < k.C; ++c) {
     const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
-    const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(32 * a + k.lane);
-    const uint32_t c3 = (k.ent << 8) | TAG_G_INIT;
-    for (int q = k.warp / A; 8 * q < nc; q += kGWarps / A) {
-      const uint4 x = philox((uint32_t)q, 0u, c2, c3, k.k0, k.k1);
+    const int nitems = 32 * A * ((nc + 31) / 32);
+    for (int it = k.tid; it < nitems; it += kGThreads) {
+      int j, a;
+      item_of<A>(it, j, a);
+      if (j >= nc) continue;
+      uint32_t word = 0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (8 * q + i >= nc) break;
-        const bool up = k.lane < k.T && half_lo(x, i) < 0x8000u;
-        const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
-        if (k.lane == 0) k.S[(o0 + 8 * q + i) * A + a] = word;
+      for (int g = 0; g < 4; ++g) {
+        const uint4 x = philox((uint32_t)j, 0u, ((uint32_t)c << 16) | (uint32_t)(4 * a + g), c3, k.k0, k.k1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (8 * g + i < k.T && half_lo(x, i) < 0x8000u) word |= 1u << (8 * g + i);
       }
+      k.S[(o0 + j) * A + a] = word;
     }
   }
   __syncthreads();
 }
 
-// One sweep, colour class by colour class (Algorithm S2's p-computer loop).
-// A warp takes chunks of 8 vertices of the class and updates every label's
-// replicas of each vertex.  With WANT_E the energy of every replica (Eq.
-// ising_energy) is gathered on the way: each bond is counted at its endpoint
-// of higher colour, whose lower-colour neighbours (the first kl) already
-// hold this sweep's values.
-template <int A, bool WANT_E, bool SM>
+// One sweep, colour class by colour class (Algorithm S2's p-computer loop):
+// every (vertex, label) of the class in parallel.  Replica b = 32 a + r
+// takes half b & 7 of P(j, s, (c << 16) | (b >> 3), (e << 8) | TAG), so one
+// Philox call serves 8 replicas of the vertex.
+template <int A, int NP, bool SM>
 __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
-  if (WANT_E && k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
   const uint32_t c3m = (k.ent << 8) | TAG_G_SWEEP;
   const uint32_t c3r = (k.ent << 8) | TAG_G_REFINE;
-  int eacc[A];
-#pragma unroll
-  for (int a = 0; a < A; ++a) eacc[a] = 0;
   for (int c = 0; c < k.C; ++c) {
     const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
-    const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)k.lane;
-    for (int q = k.warp; 8 * q < nc; q += kGWarps) {
-      uint4 x[A];
+    const int nitems = 32 * A * ((nc + 31) / 32);
+    for (int it = k.tid; it < nitems; it += kGThreads) {
+      int j, a;
+      item_of<A>(it, j, a);
+      if (j >= nc) continue;
+      const int p = o0 + j;
+      const int2 vi = ld_vi<SM>(k.vinfo, p);
+      uint32_t P[NP];
 #pragma unroll
-      for (int a = 0; a < A; ++a) x[a] = philox((uint32_t)q, s, c2 + 32u * a, c3m, k.k0, k.k1);
-      // Philox word wd serves vertices 2 wd and 2 wd + 1 of the chunk (low,
-      // high half); the loop over words stays rolled to keep the code small
-#pragma unroll 1
-      for (int wd = 0; wd < 4 && 8 * q + 2 * wd < nc; ++wd) {
-        uint32_t xw[A];
+      for (int q = 0; q < NP; ++q) P[q] = 0u;
+      const int W = vfield<A, NP, SM>(k.dynb, k.adj + vi.x, 0, vi_deg(vi), a, P);
+      const int base = vi_h(vi) - W + k.Imax;   // I + Imax = 2 C + base
+      const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(4 * a);
+      uint32_t word = 0u, tie = 0u;
 #pragma unroll
-        for (int a = 0; a < A; ++a) xw[a] = word_sel(x[a], wd);
+      for (int g = 0; g < 4; ++g) {
+        const uint4 x = philox((uint32_t)j, s, c2 + (uint32_t)g, c3m, k.k0, k.k1);
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          const int i = 2 * wd + hh;
-          if (8 * q + i >= nc) break;
-          const int p = o0 + 8 * q + i;
-          const int2 vi = ld_vi<SM>(k.vinfo, p);
-          const uint32_t *ad = k.adj + vi.x;
-          const int deg = vi_deg(vi), kl = vi_kl(vi), h = vi_h(vi);
-          int acc[A], Il[A];
-#pragma unroll
-          for (int a = 0; a < A; ++a) acc[a] = 0;
-          field_acc<A, SM>(k.dynb, k.sh, ad, 0, kl, acc);
-#pragma unroll
-          for (int a = 0; a < A; ++a) Il[a] = h + acc[a] + kl;
-          field_acc<A, SM>(k.dynb, k.sh, ad, kl, deg, acc);
-#pragma unroll
-          for (int a = 0; a < A; ++a) {
-            const int I = h + acc[a] + deg;
-            const uint32_t th = k.Th[(I + k.Imax) * 32 + k.lane];
-            const uint32_t v = hh ? (xw[a] & 0xFFFF0000u) : (xw[a] << 16), thi = th & 0xFFFF0000u;
-            bool up = v < thi;
-            if (v == thi) {   // probability 2^-16: settle with the refine half
-              const uint32_t yw = word_sel(philox((uint32_t)q, s, c2 + 32u * a, c3r, k.k0, k.k1), wd);
-              up = (v | (hh ? (yw >> 16) : (yw & 0xFFFFu))) < th;
-            }
-            const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
-            if (k.lane == 0) k.S[p * A + a] = word;
-            if (WANT_E) eacc[a] += up ? -Il[a] : Il[a];
-          }
+        for (int i = 0; i < 8; ++i) {
+          const int r = 8 * g + i;
+          const uint32_t th = k.Th[r * k.ths + 2 * vget<NP>(P, r) + base];
+          const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
+          word |= (v < thi ? 1u : 0u) << r;
+          tie |= (v == thi ? 1u : 0u) << r;
         }
       }
-    }
-    __syncthreads();
-  }
-  if (WANT_E) {
+      while (tie) {   // probability 2^-16 per replica: settle with the refine half
+        const int r = __ffs((int)tie) - 1;
+        tie &= tie - 1u;
+        const uint32_t cg = c2 + (uint32_t)(r >> 3);
+        const uint4 x = philox((uint32_t)j, s, cg, c3m, k.k0, k.k1);
+        const uint4 y = philox((uint32_t)j, s, cg, c3r, k.k0, k.k1);
+        int C = 0;
 #pragma unroll
-    for (int a = 0; a < A; ++a) atomicAdd(&sh.E[a][k.lane], eacc[a]);
+        for (int q = 0; q < NP; ++q) C |= (int)((P[q] >> r) & 1u) << q;
+        const uint32_t th = k.Th[r * k.ths + 2 * C + base];
+        const uint32_t u = (half_lo(x, r & 7) << 16) | half_lo(y, r & 7);
+        word = (u < th) ? (word | (1u << r)) : (word & ~(1u << r));
+      }
+      k.S[p * A + a] = word;
+    }
     __syncthreads();
   }
 }
 
-// Energies of all replicas from the current state (after ICM, at load).
-template <int A, bool SM>
+// Warp transpose of a 32 x 32 bit matrix: lane r returns the word whose bit
+// l is bit r of lane l's x (block-recursive swap of off-diagonal blocks).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int d = 16 >> st;
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, d);
+    x = (lane & d) ? ((x & ~M[st]) | ((y >> d) & M[st])) : ((x & M[st]) | ((y << d) & ~M[st]));
+  }
+  return x;
+}
+
+// Energies of all replicas from the current state (Eq. ising_energy), each
+// bond counted at its endpoint of higher colour.  For vertex v with
+// lower-colour count Cl (weights |w|), their sum of |w| W_l, and y = its spin
+// word (inverted when h < 0):
+//   e_v = W_l + |h| - 2 U,   U = (s_v = +1 ? Cl : W_l - Cl) + |h| y.
+// U is formed bit-sliced (U <= Imax < 2^NP); each warp (one label, 32
+// vertices) transposes the planes and counts bits per replica.
+template <int A, int NP, bool SM>
 __device__ void g_energy(const GCta &k, GShared &sh) {
   if (k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
   __syncthreads();
-  int eacc[A];
+  int eacc = 0, a_w = 0;
+  const int nitems = 32 * A * ((k.n + 31) / 32);
+  for (int it0 = 32 * k.warp; it0 < nitems; it0 += kGThreads) {
+    int v, a;
+    item_of<A>(it0 + k.lane, v, a);
+    a_w = a;
+    uint32_t U[NP];
 #pragma unroll
-  for (int a = 0; a < A; ++a) eacc[a] = 0;
-  for (int p = k.warp; p < k.n; p += kGWarps) {
-    const int2 vi = ld_vi<SM>(k.vinfo, p);
-    int acc[A];
+    for (int q = 0; q < NP; ++q) U[q] = 0u;
+    int K = 0;
+    if (v < k.n) {
+      const int2 vi = ld_vi<SM>(k.vinfo, v);
+      uint32_t Pl[NP];
 #pragma unroll
-    for (int a = 0; a < A; ++a) acc[a] = 0;
-    field_acc<A, SM>(k.dynb, k.sh, k.adj + vi.x, 0, vi_kl(vi), acc);
+      for (int q = 0; q < NP; ++q) Pl[q] = 0u;
+      const int Wl = vfield<A, NP, SM>(k.dynb, k.adj + vi.x, 0, vi_kl(vi), a, Pl);
+      const uint32_t x = k.S[v * A + a];
+      uint32_t cy = 0xFFFFFFFFu;   // Wl - Cl = Wl + ~Cl + 1
 #pragma unroll
-    for (int a = 0; a < A; ++a) {
-      const int Il = vi_h(vi) + acc[a] + vi_kl(vi);
-      eacc[a] += ((k.S[p * A + a] >> k.lane) & 1u) ? -Il : Il;
+      for (int q = 0; q < NP; ++q) {
+        const uint32_t wb = ((Wl >> q) & 1) ? 0xFFFFFFFFu : 0u, nb = ~Pl[q];
+        const uint32_t d = wb ^ nb ^ cy;
+        cy = (wb & nb) | (wb & cy) | (nb & cy);
+        U[q] = (x & Pl[q]) | (~x & d);
+      }
+      const int h = vi_h(vi), ha = h < 0 ? -h : h;
+      if (ha) vadd<NP>(U, h < 0 ? ~x : x, (uint32_t)ha);
+      K = Wl + ha;
     }
-  }
+    int cnt = 0;
 #pragma unroll
-  for (int a = 0; a < A; ++a) atomicAdd(&sh.E[a][k.lane], eacc[a]);
+    for (int q = 0; q < NP; ++q) cnt += __popc(transpose32(U[q], k.lane)) << q;
+    eacc += (int)__reduce_add_sync(0xFFFFFFFFu, (unsigned)K) - 2 * cnt;
+  }
+  atomicAdd(&sh.E[a_w][k.lane], eacc);
   __syncthreads();
 }
 
@@ -487,9 +584,10 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
   }
 }
 
-// SM: the problem's vertex table and adjacency are staged in shared memory
-// (when they fit) instead of being read through the L1 cache.
-template <int A, bool SM>
+// NP: bit planes of the field counts (2^NP > Imax).  SM: the problem's
+// vertex table and adjacency are staged in shared memory (when they fit)
+// instead of being read through the L1 cache.
+template <int A, int NP, bool SM>
 __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init) {
   extern __shared__ __align__(16) uint32_t dyn[];
   __shared__ GShared sh;
@@ -512,6 +610,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   const int nth = (2 * P.Imax + 1) * 32;
   k.Th = Th;
   k.S = Th + nth;
+  k.ths = 2 * P.Imax + 1;
   k.ubase = 4u * (uint32_t)nth;
   k.X = k.S + (size_t)P.n * A;
   k.Cl = k.X + P.n;
@@ -536,7 +635,7 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   if (init) {
     __syncthreads();
     g_init<A>(k, sh);
-    g_energy<A, SM>(k, sh);
+    g_energy<A, NP, SM>(k, sh);
   } else {
     for (int i = k.tid; i < P.n * A; i += kGThreads) k.S[i] = gS[i];
     if (k.tid < 128) {
@@ -556,13 +655,13 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
     const uint32_t *swidx = a.swapidx + P.swbase;
     for (int t = 0; t < a.n_swaps; ++t) {
       const uint32_t tt = a.swap0 + (uint32_t)t;
-      for (int q = 0; q + 1 < a.spp; ++q) g_sweep<A, false, SM>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q));
-      g_sweep<A, true, SM>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + a.spp - 1));
+      for (int q = 0; q < a.spp; ++q) g_sweep<A, NP, SM>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q));
+      g_energy<A, NP, SM>(k, sh);
       const long long done = (long long)a.sweep0 + (long long)(t + 1) * a.spp;
       g_best<A>(k, sh, done);
       if (A >= 2 && a.icm) {
         g_icm<A, SM>(k, sh, tt);
-        g_energy<A, SM>(k, sh);
+        g_energy<A, NP, SM>(k, sh);
         g_best<A>(k, sh, done);
       }
       g_swap<A>(k, sh, tt, a.joint, a.swaptab, swidx);
@@ -588,11 +687,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   if (k.tid < 128) a.E[128 * (size_t)blockIdx.x + k.tid] = sh.E[k.tid >> 5][k.tid & 31];
 }
 
-template <int A, bool SM>
+template <int A, int NP, bool SM>
 int gapt_launch_t(const GAptArgs &a, int n_prob, size_t smem, bool init, cudaStream_t st) {
-  PC_CUDA_TRY(cudaFuncSetAttribute(gapt_kernel<A, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PC_CUDA_TRY(cudaFuncSetAttribute(gapt_kernel<A, NP, SM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
-  gapt_kernel<A, SM><<<n_prob, kGThreads, smem, st>>>(a, init ? 1 : 0);
+  gapt_kernel<A, NP, SM><<<n_prob, kGThreads, smem, st>>>(a, init ? 1 : 0);
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
@@ -711,15 +810,22 @@ size_t gapt_smem_bytes(int n, int A, int Imax, int m) {
   return sizeof(uint32_t) * (((base + 1) & ~(size_t)1) + 2 * (size_t)n + (size_t)m);
 }
 
-int gapt_launch(const GAptArgs &a, int n_prob, int A, bool staged, size_t smem, bool init,
+int gapt_launch(const GAptArgs &a, int n_prob, int A, int Imax, bool staged, size_t smem, bool init,
                 cudaStream_t st) {
-  switch (A * 2 + (staged ? 1 : 0)) {
-    case 2: return gapt_launch_t<1, false>(a, n_prob, smem, init, st);
-    case 3: return gapt_launch_t<1, true>(a, n_prob, smem, init, st);
-    case 4: return gapt_launch_t<2, false>(a, n_prob, smem, init, st);
-    case 5: return gapt_launch_t<2, true>(a, n_prob, smem, init, st);
-    case 8: return gapt_launch_t<4, false>(a, n_prob, smem, init, st);
-    case 9: return gapt_launch_t<4, true>(a, n_prob, smem, init, st);
+  const bool small = Imax <= 7;   // 3 planes hold every field count
+  switch (A * 4 + (small ? 0 : 2) + (staged ? 1 : 0)) {
+    case 4: return gapt_launch_t<1, 3, false>(a, n_prob, smem, init, st);
+    case 5: return gapt_launch_t<1, 3, true>(a, n_prob, smem, init, st);
+    case 6: return gapt_launch_t<1, 7, false>(a, n_prob, smem, init, st);
+    case 7: return gapt_launch_t<1, 7, true>(a, n_prob, smem, init, st);
+    case 8: return gapt_launch_t<2, 3, false>(a, n_prob, smem, init, st);
+    case 9: return gapt_launch_t<2, 3, true>(a, n_prob, smem, init, st);
+    case 10: return gapt_launch_t<2, 7, false>(a, n_prob, smem, init, st);
+    case 11: return gapt_launch_t<2, 7, true>(a, n_prob, smem, init, st);
+    case 16: return gapt_launch_t<4, 3, false>(a, n_prob, smem, init, st);
+    case 17: return gapt_launch_t<4, 3, true>(a, n_prob, smem, init, st);
+    case 18: return gapt_launch_t<4, 7, false>(a, n_prob, smem, init, st);
+    case 19: return gapt_launch_t<4, 7, true>(a, n_prob, smem, init, st);
     default: return fail(PC_EINVAL, "n_labels must be 1, 2 or 4");
   }
 }

@@ -170,7 +170,7 @@ int upload(DevBuf<T> &d, const std::vector<T> &h, cudaStream_t st) {
 }
 
 struct GImpl {
-  int n_prob = 0, A = 0;
+  int n_prob = 0, A = 0, Imax = 0;   // Imax: largest field bound of the batch
   bool any_h = false;
   std::vector<HGraph> g;
   std::vector<int> T;
@@ -290,6 +290,7 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
       if (!(beta[t] > beta[t - 1])) return fail(PC_EINVAL, "betas must increase strictly");
     im->T[i] = T;
     im->any_h |= g.any_h;
+    im->Imax = std::max(im->Imax, g.Imax);
     GProbDev P{};
     P.n = n;
     P.C = g.C;
@@ -307,8 +308,8 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
     for (int cc = 0; cc <= kGMaxColours; ++cc) P.off[cc] = g.off[cc];
     vinfo.insert(vinfo.end(), g.vinfo.begin(), g.vinfo.end());
     adj.insert(adj.end(), g.adj.begin(), g.adj.end());
-    for (int I = -g.Imax; I <= g.Imax; ++I)
-      for (int r = 0; r < 32; ++r) pbit.push_back(r < T ? pc_pbit_threshold(beta[r], I) : 0u);
+    for (int r = 0; r < 32; ++r)
+      for (int I = -g.Imax; I <= g.Imax; ++I) pbit.push_back(r < T ? pc_pbit_threshold(beta[r], I) : 0u);
     for (int r = 0; r + 1 < T; ++r) {
       const uint32_t o = (uint32_t)swaptab.size();
       const double db = beta[r + 1] - beta[r];
@@ -357,7 +358,7 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
       (rc = im->d_E.alloc(128 * (size_t)n_prob)) || (rc = im->d_best_bits.zero(st)))
     return rc;
   GAptArgs a = make_args(c, im);
-  if ((rc = gapt_launch(a, n_prob, n_labels, im->staged, im->smem, true, st))) return rc;
+  if ((rc = gapt_launch(a, n_prob, n_labels, im->Imax, im->staged, im->smem, true, st))) return rc;
   PC_CUDA_TRY(cudaStreamSynchronize(st));
   im->ready = true;
   return PC_OK;
@@ -382,7 +383,7 @@ int pc_gapt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
     a.n_swaps = chunk;
     a.sweep0 = (uint32_t)im->sweeps;
     a.swap0 = (uint32_t)im->swaps;
-    if ((rc = gapt_launch(a, im->n_prob, im->A, im->staged, im->smem, false, c->stream))) return rc;
+    if ((rc = gapt_launch(a, im->n_prob, im->A, im->Imax, im->staged, im->smem, false, c->stream))) return rc;
     im->sweeps += (int64_t)chunk * sweeps_per_swap;
     im->swaps += chunk;
     left -= chunk;

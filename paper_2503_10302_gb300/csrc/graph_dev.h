@@ -34,7 +34,7 @@ struct GProbDev {
   uint32_t ent;                 // problem entry of the counters
   uint32_t vbase;               // first vertex in vinfo / spins ([n][A] words from vbase * A)
   uint32_t abase;               // first adjacency entry
-  uint32_t thbase;              // first word of the [2 Imax + 1][32] p-bit table
+  uint32_t thbase;              // first word of the [32][2 Imax + 1] p-bit table
   uint32_t swbase;              // first (offset, length) pair in swapidx
   uint32_t bestbase;            // first word of the best-state bits
   uint32_t statbase;            // first counter: att[T-1][A], acc[T-1][A], icm[3]
@@ -45,7 +45,7 @@ struct GAptArgs {
   const GProbDev *prob;
   const int2 *vinfo;
   const uint32_t *adj;
-  const uint32_t *pbit;         // [2 Imax + 1][32] per problem (zero columns for r >= T)
+  const uint32_t *pbit;         // [32][2 Imax + 1] per problem (zero rows for r >= T)
   const uint32_t *swaptab;      // thresholds by |dE| (entry 0: always accepted)
   const uint32_t *swapidx;      // per pair: offset, length
   uint32_t *spins;              // [n][A] words per problem
@@ -74,7 +74,8 @@ struct GSqaArgs {
 // m < 0: vertex table and adjacency read from global memory; m >= 0: staged
 // in shared memory as well (m adjacency entries).
 size_t gapt_smem_bytes(int n, int A, int Imax, int m);
-int gapt_launch(const GAptArgs &a, int n_prob, int A, bool staged, size_t smem, bool init,
+// Imax: the batch's largest field bound (selects the bit-plane count).
+int gapt_launch(const GAptArgs &a, int n_prob, int A, int Imax, bool staged, size_t smem, bool init,
                 cudaStream_t st);
 size_t gsqa_smem_bytes(int n, int P, int Imax, int m);
 int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st);
