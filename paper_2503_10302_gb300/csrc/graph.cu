@@ -531,32 +531,24 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
       }
     }
     __syncthreads();
-    // flood fill: grow every seed inside X until nothing changes.  Between
-    // barriers a thread rescans its vertices up to 3 times while they change
-    // (reading the other threads' words as they are written), so a pass
-    // spans several hops.  Each pass with a change adds a bit: at most 32 n
-    // passes.
+    // flood fill: grow every seed inside X until nothing changes; each
+    // change adds a bit, so at most 32 n passes
     for (;;) {
       int changed = 0;
-      for (int rep = 0; rep < 3; ++rep) {
-        int local = 0;
-        for (int p = k.tid; p < k.n; p += kGThreads) {
-          const uint32_t cl = k.Cl[p], cand = k.X[p] & ~cl;
-          if (cand) {
-            const int2 vi = ld_vi<SM>(k.vinfo, p);
-            const uint32_t *ad = k.adj + vi.x;
-            uint32_t nb = 0;
-            for (int e = 0, d = vi_deg(vi); e < d; ++e)
-              nb |= k.Cl[((ld_adj<SM>(ad, e) >> 8) - k.ubase) >> k.ushift];
-            const uint32_t nw = cl | (cand & nb);
-            if (nw != cl) {
-              k.Cl[p] = nw;
-              local = 1;
-            }
+      for (int p = k.tid; p < k.n; p += kGThreads) {
+        const uint32_t cl = k.Cl[p], cand = k.X[p] & ~cl;
+        if (cand) {
+          const int2 vi = ld_vi<SM>(k.vinfo, p);
+          const uint32_t *ad = k.adj + vi.x;
+          uint32_t nb = 0;
+          for (int e = 0, d = vi_deg(vi); e < d; ++e)
+            nb |= k.Cl[((ld_adj<SM>(ad, e) >> 8) - k.ubase) >> k.ushift];
+          const uint32_t nw = cl | (cand & nb);
+          if (nw != cl) {
+            k.Cl[p] = nw;
+            changed = 1;
           }
         }
-        changed |= local;
-        if (!local) break;
       }
       if (!__syncthreads_or(changed)) break;
     }
