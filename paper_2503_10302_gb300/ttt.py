@@ -376,9 +376,53 @@ def graph_workloads(name: str) -> List[W.Graph]:
     raise ValueError(name)
 
 
+def graph_time_to_target(name: str = "dimer_64xL8", labels: int = 2, rho: float = 1e-3, best_runs: int = 10,
+                         best_sweeps: int = 20000, max_sweeps: int = 100000, chunk: int = 256) -> Dict:
+    """Time to rho_E <= rho on a graph workload with APT+ICM on the general-
+    graph kernels (32 geometric temperatures 0.2-3.0; E_best = the minimum
+    over best_runs runs with sweep-to-swap ratio 10)."""
+    graphs = graph_workloads(name)
+    trip = [(g.rp, g.col, g.w) for g in graphs]
+    betas = [W.geometric_ladder(32, 0.2, 3.0)] * len(graphs)
+    n_prob = len(graphs)
+    best = np.full(n_prob, np.iinfo(np.int64).max, np.int64)
+    for r in range(best_runs):
+        ctx = pcomp.Context(0, 100 + r)
+        pcomp.pc_gapt_load(ctx.h, trip, betas, 2, 0)
+        pcomp.pc_gapt_run(ctx.h, max(1, best_sweeps // 10), 10, True)
+        for i, g in enumerate(graphs):
+            best[i] = min(best[i], pcomp.pc_gapt_get_best(ctx.h, i, g.n)["E"])
+        ctx.close()
+    n = np.array([g.n for g in graphs])
+    targets = np.floor(best + rho * n).astype(np.int64)
+    ctx = pcomp.Context(0, 7)
+    pcomp.pc_gapt_load(ctx.h, trip, betas, labels, 0)
+    for i, t in enumerate(targets):
+        pcomp.pc_gapt_set_target(ctx.h, i, int(t))
+    pcomp.pc_synchronize(ctx.h)
+    t0 = time.perf_counter()
+    done = 0
+    hit = np.full(n_prob, -1, np.int64)
+    while done < max_sweeps:
+        pcomp.pc_gapt_run(ctx.h, chunk, 1, True)
+        done += chunk
+        hit = np.array([pcomp.pc_gapt_get_best(ctx.h, i, g.n)["hit_sweep"] for i, g in enumerate(graphs)])
+        if (hit >= 0).all():
+            break
+    total = time.perf_counter() - t0
+    ctx.close()
+    ok = hit >= 0
+    t_sweep = total / done
+    return {"workload": name, "problems": n_prob, "labels": labels, "rho_target": rho,
+            "apt_seconds_per_sweep": t_sweep, "hit_fraction": float(ok.mean()),
+            "median_hit_sweep": float(np.median(hit[ok])) if ok.any() else None,
+            "median_time_to_target_s": float(np.median(hit[ok]) * t_sweep) if ok.any() else None,
+            "e_best_per_spin_mean": float((best / n).mean())}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("what", choices=["throughput", "graph", "c2", "c3", "c4", "c5", "all"])
+    ap.add_argument("what", choices=["throughput", "graph", "graph-ttt", "c2", "c3", "c4", "c5", "all"])
     ap.add_argument("--graph", choices=["dimer_64xL8", "lattice15x15x12_64", "lattice12_64", "random4096_152"])
     ap.add_argument("--graph-labels", type=int, choices=[2, 4], help="graph: one label count only")
     ap.add_argument("--no-sqa", action="store_true", help="graph: skip the DT-SQA lines")
@@ -418,6 +462,12 @@ def main():
         out["graph_sqa_lattice5x5x4_P65"] = graph_sqa_throughput(
             W.lattice_graph((5, 5, 4), (1, 1, 1), W.ea_couplings((5, 5, 4), W.SEED_INSTANCES, 0))[0], 65, 4864,
             1000)
+    if args.what == "graph-ttt":
+        for name in ([args.graph] if args.graph else ["dimer_64xL8", "lattice15x15x12_64"]):
+            for labels in ((2, 4) if args.graph_labels is None else (args.graph_labels,)):
+                out[f"gttt_{name}_A{labels}"] = graph_time_to_target(
+                    name, labels, best_runs=args.best_runs, best_sweeps=args.best_sweeps,
+                    max_sweeps=args.max_sweeps)
     if args.what in ("c2", "all"):
         out["c2"] = c2_residual_vs_R()
     if args.what in ("c3", "all"):
