@@ -95,6 +95,10 @@ def lib():
         L.or_gapt_state.argtypes = [ctypes.c_void_p, ctypes.c_int, i8p, i64p, i32p]
         L.or_gapt_best.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p, i32p, i64p, i8p]
         L.or_gapt_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p, i64p]
+        L.or_graph_adaptive_ladder.argtypes = [ctypes.c_int, i32p, i32p, i8p, i8p, i32p, ctypes.c_uint32, u64,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_double, ctypes.c_int, f64p, f64p,
+                                               P(ctypes.c_int)]
         L.or_gicm_apply.argtypes = [ctypes.c_int, i32p, i32p, i32p, i8p, i8p, u64, ctypes.c_uint32,
                                     ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, i64p]
         L.or_gsqa_anneal.argtypes = [ctypes.c_int, i32p, i32p, i8p, i8p, i32p, ctypes.c_int, ctypes.c_double,
@@ -312,6 +316,7 @@ def sqa_anneal(dims, J, P, T, gamma, R, run0=0, seed=0, want_spins=False, thread
 # ---------------------------------------------------------------- general graphs
 TAG_G_INIT, TAG_G_SWEEP, TAG_G_REFINE, TAG_G_SWAP, TAG_G_ICM = 15, 16, 17, 18, 19
 TAG_GS_INIT, TAG_GS_SWEEP, TAG_GS_REFINE = 20, 21, 22
+TAG_GL_INIT, TAG_GL_SWEEP, TAG_GL_REFINE = 23, 24, 25
 
 
 def _i32(a) -> np.ndarray:
@@ -457,3 +462,19 @@ def gsqa_anneal(rp, col, w, P, T, gamma, R, run0=0, seed=0, h=None, colour=None,
                                 _ptr(gamma, ctypes.c_double), R, ctypes.c_uint32(run0), ctypes.c_uint64(seed),
                                 _ptr(E, ctypes.c_int64), _ptr(s, ctypes.c_int8), threads), "gsqa_anneal")
     return (E, s) if want_spins else E
+
+
+def graph_adaptive_ladder(rp, col, w, h=None, colour=None, entry=0, seed=0, beta0=0.5, alpha=1.25,
+                          n_chains=100, sweeps=10000, tail=1000, tol=1.0, max_len=64):
+    """Adaptive beta ladder on a graph: (betas, sigmas, converged)."""
+    rp, col, w, hh = _i32(rp), _i32(col), _i8(w), _i8(h)
+    cl = None if colour is None else _i32(colour)
+    beta = np.zeros(max_len, np.float64); sig = np.zeros(max_len, np.float64)
+    n = ctypes.c_int(0)
+    rc = _check(lib().or_graph_adaptive_ladder(len(rp) - 1, _ptr(rp, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                               _ptr(w, ctypes.c_int8), _ptr(hh, ctypes.c_int8),
+                                               _ptr(cl, ctypes.c_int32), ctypes.c_uint32(entry),
+                                               ctypes.c_uint64(seed), beta0, alpha, n_chains, sweeps, tail, tol,
+                                               max_len, _ptr(beta, ctypes.c_double), _ptr(sig, ctypes.c_double),
+                                               ctypes.byref(n)), "graph_adaptive_ladder")
+    return beta[: n.value].copy(), sig[: n.value].copy(), rc == 0

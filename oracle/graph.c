@@ -674,3 +674,85 @@ int or_gsqa_anneal(int n, const int32_t *rp, const int32_t *col, const int8_t *w
   free(base); free(rcol); free(ridx);
   return 0;
 }
+
+/* ---------------- adaptive ladder on graphs ---------------- */
+/* Algorithm S2's preprocessing (Methods, "APT details") on a graph: n_chains
+ * chains sweep `sweeps` times at beta_t, warm-started from the previous
+ * step; sigma_E is the square root of the chains' mean unbiased variance of
+ * their last `tail` post-sweep energies; beta_{t+1} = beta_t + alpha /
+ * sigma_E; stop at the first beta with sigma_E < tol. */
+int or_graph_adaptive_ladder(int n, const int32_t *rp, const int32_t *col, const int8_t *w,
+                             const int8_t *h, const int32_t *colour, uint32_t entry, uint64_t seed,
+                             double beta0, double alpha, int n_chains, int sweeps, int tail,
+                             double tol, int max_len, double *beta_out, double *sigma_out,
+                             int *len_out) {
+  if (n_chains < 1 || n_chains > 128 || sweeps < 1 || tail < 2 || tail > sweeps || max_len < 1 ||
+      !(beta0 > 0))
+    return -1;
+  double b1 = 1.0;
+  or_gapt *g = NULL;
+  int32_t nv = n, T = 1;
+  /* one problem with one "temperature" per chain is built through the APT
+     set-up only for its graph checks, colouring and colour-local indices */
+  int rc = or_gapt_create(&g, 1, &nv, rp, col, w, h, colour, &T, &b1, 1, seed, entry);
+  if (rc) return rc;
+  g_entry *e = &g->e[0];
+  const int64_t Imax = e->Imax;
+  int8_t *spin = (int8_t *)malloc((size_t)n_chains * n);
+  int64_t *sE = (int64_t *)malloc(sizeof(int64_t) * n_chains);
+  int64_t *sE2 = (int64_t *)malloc(sizeof(int64_t) * n_chains);
+  uint32_t *tab = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(2 * Imax + 1));
+  for (int b = 0; b < n_chains; ++b)
+    for (int v = 0; v < n; ++v) {
+      const int j = e->cidx[v];
+      uint32_t ctr[4] = {(uint32_t)j, 0u, ((uint32_t)e->colour[v] << 16) | (uint32_t)(b >> 3),
+                         (entry << 8) | OR_TAG_GL_INIT};
+      uint32_t x[4];
+      or_philox(ctr, seed, x);
+      spin[(size_t)b * n + v] = (or_half(x, b & 7) < 0x8000u) ? 1 : -1;
+    }
+  double beta = beta0;
+  int len = 0, status = 1;
+  uint32_t s = 0;
+  while (len < max_len) {
+    for (int64_t I = -Imax; I <= Imax; ++I) tab[I + Imax] = or_pbit_threshold(beta, I);
+    memset(sE, 0, sizeof(int64_t) * n_chains);
+    memset(sE2, 0, sizeof(int64_t) * n_chains);
+    for (int k = 0; k < sweeps; ++k, ++s) {
+      for (int c = 0; c < e->C; ++c)
+        for (int b = 0; b < n_chains; ++b) {
+          int8_t *sb = spin + (size_t)b * n;
+          for (int v = 0; v < n; ++v) {
+            if (e->colour[v] != c) continue;
+            int64_t I = g_field(e->rp, e->col, e->w, e->h, sb, v);
+            uint32_t u = or_uniform32(seed, (uint32_t)e->cidx[v], s,
+                                      ((uint32_t)c << 16) | (uint32_t)(b >> 3), entry,
+                                      OR_TAG_GL_SWEEP, OR_TAG_GL_REFINE, b & 7);
+            sb[v] = (u < tab[I + Imax]) ? 1 : -1;
+          }
+        }
+      if (k >= sweeps - tail)
+        for (int b = 0; b < n_chains; ++b) {
+          int64_t E = g_energy(n, e->rp, e->col, e->w, e->h, spin + (size_t)b * n);
+          sE[b] += E;
+          sE2[b] += E * E;
+        }
+    }
+    double mean_var = 0.0;
+    for (int b = 0; b < n_chains; ++b) {
+      int64_t num = (int64_t)tail * sE2[b] - sE[b] * sE[b];
+      mean_var += (double)num / ((double)tail * (double)(tail - 1));
+    }
+    mean_var /= (double)n_chains;
+    double sigma = sqrt(mean_var);
+    beta_out[len] = beta;
+    if (sigma_out) sigma_out[len] = sigma;
+    ++len;
+    if (sigma < tol) { status = 0; break; }
+    beta = beta + alpha / sigma;
+  }
+  *len_out = len;
+  free(spin); free(sE); free(sE2); free(tab);
+  or_gapt_destroy(g);
+  return status;
+}

@@ -44,7 +44,8 @@ enum {
   OR_TAG_SQA_INIT = 12, OR_TAG_SQA_SWEEP = 13, OR_TAG_SQA_REFINE = 14,
   /* general sparse graphs (graph.c) */
   OR_TAG_G_INIT = 15, OR_TAG_G_SWEEP = 16, OR_TAG_G_REFINE = 17, OR_TAG_G_SWAP = 18,
-  OR_TAG_G_ICM = 19, OR_TAG_GS_INIT = 20, OR_TAG_GS_SWEEP = 21, OR_TAG_GS_REFINE = 22
+  OR_TAG_G_ICM = 19, OR_TAG_GS_INIT = 20, OR_TAG_GS_SWEEP = 21, OR_TAG_GS_REFINE = 22,
+  OR_TAG_GL_INIT = 23, OR_TAG_GL_SWEEP = 24, OR_TAG_GL_REFINE = 25
 };
 
 /* Philox4x32-10 on one counter. */
@@ -193,6 +194,16 @@ int or_gapt_stats(const or_gapt *g, int prob, int64_t *att, int64_t *acc, int64_
 int or_gicm_apply(int n, const int32_t *rp, const int32_t *col, const int32_t *colour, int8_t *sa,
                   int8_t *sb, uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p,
                   int64_t *cluster_size);
+
+/* Adaptive beta ladder on a graph (Algorithm S2 preprocessing, as
+ * or_adaptive_ladder): chain b (< 128) draws like APT replica id b with the
+ * TAG_GL_* tags, the sweep counter running on across beta steps.  colour
+ * NULL -> DSATUR.  Returns 1 if max_len was reached before sigma_E < tol. */
+int or_graph_adaptive_ladder(int n, const int32_t *rp, const int32_t *col, const int8_t *w,
+                             const int8_t *h, const int32_t *colour, uint32_t entry, uint64_t seed,
+                             double beta0, double alpha, int n_chains, int sweeps, int tail,
+                             double tol, int max_len, double *beta_out, double *sigma_out,
+                             int *len_out);
 
 /* R runs of P slices on a graph; colour NULL -> DSATUR; E_out [R][P]
  * classical slice energies (with h); spins_out [R][P][n] or NULL. */

@@ -448,3 +448,31 @@ def test_graph_sqa_energies_are_slice_energies(orc):
     for r in range(3):
         for k in range(5):
             assert E[r, k] == orc.graph_energy(g.rp, g.col, g.w, s[r, k], h)
+
+
+# ---------------------------------------------------------------- adaptive ladder on graphs
+def test_graph_adaptive_ladder_first_step_matches_enumeration(orc):
+    """sigma_E at beta_0 equals the standard deviation of E under the exact
+    Boltzmann law of a 7-vertex frustrated graph with weights and biases, and
+    beta_1 = beta_0 + alpha / sigma_E (Algorithm S2 preprocessing)."""
+    g = _frustrated_graph(23)
+    h = np.array([1, 0, -1, 0, 2, 0, -1], np.int8)
+    E = _exact_graph_energies(g, h).astype(np.float64)
+    b0 = 0.4
+    p = X.boltzmann(E.astype(np.int64), b0)
+    sd = math.sqrt((p * E ** 2).sum() - (p * E).sum() ** 2)
+    beta, sig, ok = orc.graph_adaptive_ladder(g.rp, g.col, g.w, h=h, beta0=b0, alpha=1.25, n_chains=128,
+                                              sweeps=700, tail=600, tol=0.1, max_len=2)
+    assert abs(sig[0] - sd) < 0.04 * sd, (sig[0], sd)
+    assert beta[1] == pytest.approx(b0 + 1.25 / sig[0], rel=1e-12)
+
+
+def test_graph_adaptive_ladder_stop_rules(orc):
+    g0 = _graph(9, [])
+    beta, sig, ok = orc.graph_adaptive_ladder(g0.rp, g0.col, g0.w, n_chains=8, sweeps=20, tail=10)
+    assert ok and len(beta) == 1 and sig[0] == 0.0
+    g = W.dimer_embedding((4, 4, 4), W.ea_couplings((4, 4, 4), 1000, 6))
+    beta, sig, ok = orc.graph_adaptive_ladder(g.rp, g.col, g.w, n_chains=8, sweeps=40, tail=20, max_len=3)
+    assert not ok and len(beta) == 3
+    beta, sig, ok = orc.graph_adaptive_ladder(g.rp, g.col, g.w, n_chains=32, sweeps=300, tail=200, max_len=64)
+    assert ok and np.all(np.diff(beta) > 0) and sig[-1] < 1.0 <= sig[-2]
