@@ -334,6 +334,20 @@ int pc_gapt_get_best(pc_ctx *ctx, int prob, int64_t *E, int64_t *sweep, int32_t 
                      int64_t *hit_sweep, int8_t *spins);
 /* Swap attempts / accepts [n_temps-1][n_labels]; icm [3] as pc_apt_get_stats. */
 int pc_gapt_get_stats(pc_ctx *ctx, int prob, int64_t *att, int64_t *acc, int64_t *icm);
+/* Adaptive beta ladder on graphs (Algorithm S2 preprocessing, as
+ * pc_adaptive_ladder): for each of n_prob graphs (arrays as pc_gapt_load,
+ * Philox entry entry0 + i) n_chains <= 128 chains sweep `sweeps` times at
+ * beta_t (warm start), sigma_E = sqrt(mean over chains of the unbiased
+ * variance of the last `tail` post-sweep energies), beta_{t+1} = beta_t +
+ * alpha / sigma_E, until sigma_E < tol.  Chain b draws as APT replica id b
+ * with the ladder's own counter tags.  Outputs [n_prob][max_len] betas and
+ * sigmas (sigma_out nullable), len [n_prob], converged [n_prob] (nullable;
+ * 0 if max_len was reached first).  Leaves any loaded graph batch alone. */
+int pc_graph_adaptive_ladder(pc_ctx *ctx, int n_prob, const int32_t *n_vert, const int32_t *row_ptr,
+                             const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
+                             uint32_t entry0, double beta0, double alpha, int n_chains, int sweeps,
+                             int tail, double tol, int max_len, double *beta_out, double *sigma_out,
+                             int32_t *len_out, int32_t *converged_out);
 /* DT-SQA on a graph (Eq. S.3, Algorithm S1): R runs (ids run0 ..) of P >= 2
  * slices at temperature T under gamma[n_sweeps] (all > 0).  The replicated
  * network takes colour (colour[v] + f(k)) mod C' for slice k, f(k) = k & 1

@@ -59,6 +59,7 @@ struct GCta {
   uint32_t ubase;                // byte offset of the spin words from the dynamic base
   const char *dynb;              // dynamic shared-memory base
   uint32_t ent, k0, k1;
+  uint32_t tag_init, tag_sweep, tag_refine;
   const int2 *vinfo;
   const uint32_t *adj;
   uint32_t *S;                   // [n][A]
@@ -198,7 +199,7 @@ __device__ __forceinline__ void item_of(int i, int &v, int &a) {
 // below 2^15.
 template <int A>
 __device__ void g_init(const GCta &k, GShared &sh) {
-  const uint32_t c3 = (k.ent << 8) | TAG_G_INIT;
+  const uint32_t c3 = (k.ent << 8) | k.tag_init;
   for (int c = 0; c < k.C; ++c) {
     const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
     const int nitems = 32 * A * ((nc + 31) / 32);
@@ -226,8 +227,8 @@ __device__ void g_init(const GCta &k, GShared &sh) {
 // Philox call serves 8 replicas of the vertex.
 template <int A, int NP, bool SM>
 __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
-  const uint32_t c3m = (k.ent << 8) | TAG_G_SWEEP;
-  const uint32_t c3r = (k.ent << 8) | TAG_G_REFINE;
+  const uint32_t c3m = (k.ent << 8) | k.tag_sweep;
+  const uint32_t c3r = (k.ent << 8) | k.tag_refine;
   for (int c = 0; c < k.C; ++c) {
     const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
     const int nitems = 32 * A * ((nc + 31) / 32);
@@ -591,6 +592,7 @@ template <int A, int NP, bool SM>
 __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init) {
   extern __shared__ __align__(16) uint32_t dyn[];
   __shared__ GShared sh;
+  if (a.active && !a.active[blockIdx.x]) return;   // converged ladder problem
   const GProbDev &P = a.prob[blockIdx.x];
   GCta k;
   k.n = P.n;
@@ -603,6 +605,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   k.ent = P.ent;
   k.k0 = a.k0;
   k.k1 = a.k1;
+  k.tag_init = a.tag_init;
+  k.tag_sweep = a.tag_sweep;
+  k.tag_refine = a.tag_refine;
   k.sh = 31u - (uint32_t)k.lane;
   k.ushift = A == 1 ? 2 : (A == 2 ? 3 : 4);
   k.dynb = reinterpret_cast<const char *>(dyn);
@@ -657,6 +662,15 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
       const uint32_t tt = a.swap0 + (uint32_t)t;
       for (int q = 0; q < a.spp; ++q) g_sweep<A, NP, SM>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q));
       g_energy<A, NP, SM>(k, sh);
+      if (a.ladder) {
+        // thread tid reads (and next zeroes) only its own slot's energy
+        if (t >= a.window_from && k.tid < 32 * A) {
+          const long long e = sh.E[k.tid >> 5][k.tid & 31];
+          a.sum1[128 * (size_t)blockIdx.x + k.tid] += e;
+          a.sum2[128 * (size_t)blockIdx.x + k.tid] += e * e;
+        }
+        continue;
+      }
       const long long done = (long long)a.sweep0 + (long long)(t + 1) * a.spp;
       g_best<A>(k, sh, done);
       if (A >= 2 && a.icm) {

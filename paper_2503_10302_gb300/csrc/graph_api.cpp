@@ -2,6 +2,7 @@
 // colouring, colour-major renumbering, threshold tables, and the APT batch
 // and DT-SQA launches (kernels in graph.cu).
 #include <algorithm>
+#include <cmath>
 #include <climits>
 #include <cstring>
 #include <set>
@@ -223,6 +224,9 @@ GAptArgs make_args(pc_ctx *c, GImpl *im) {
   a.k0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
   a.k1 = (uint32_t)(c->seed >> 32);
   a.joint = im->joint;
+  a.tag_init = kTagGInit;
+  a.tag_sweep = kTagGSweep;
+  a.tag_refine = kTagGRefine;
   return a;
 }
 
@@ -251,18 +255,16 @@ int pc_graph_dsatur(int n, const int32_t *row_ptr, const int32_t *col, int32_t *
   return PC_OK;
 }
 
-int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *row_ptr,
-                 const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
-                 const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0) {
-  if (!c) return fail(PC_EINVAL, "ctx is NULL");
-  if (n_prob < 1 || !n_vert || !row_ptr || !col || !w || !n_temps || !betas)
-    return fail(PC_EINVAL, "pc_gapt_load: n_prob >= 1 and non-NULL arrays required");
-  if (!(n_labels == 1 || n_labels == 2 || n_labels == 4))
-    return fail(PC_EINVAL, "n_labels must be 1, 2 or 4");
-  PC_CUDA_TRY(cudaSetDevice(c->device));
-  pc_graph_release_impl(c);
-  GImpl *im = new GImpl();
-  c->graph_impl = im;
+}  // extern "C"
+
+namespace pc {
+namespace {
+
+// Builds a graph batch into im and draws its initial states with tag_init.
+int gload(pc_ctx *c, GImpl *im, int n_prob, const int32_t *n_vert, const int32_t *row_ptr,
+          const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
+          const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0,
+          uint32_t tag_init) {
   im->n_prob = n_prob;
   im->A = n_labels;
   im->g.resize(n_prob);
@@ -358,11 +360,33 @@ int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *ro
       (rc = im->d_E.alloc(128 * (size_t)n_prob)) || (rc = im->d_best_bits.zero(st)))
     return rc;
   GAptArgs a = make_args(c, im);
+  a.tag_init = tag_init;
   if ((rc = gapt_launch(a, n_prob, n_labels, im->Imax, im->staged, im->smem, true, st))) return rc;
   PC_CUDA_TRY(cudaStreamSynchronize(st));
   im->ready = true;
   return PC_OK;
 }
+
+}  // namespace
+}  // namespace pc
+
+extern "C" int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *row_ptr,
+                            const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
+                            const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0) {
+  if (!c) return fail(PC_EINVAL, "ctx is NULL");
+  if (n_prob < 1 || !n_vert || !row_ptr || !col || !w || !n_temps || !betas)
+    return fail(PC_EINVAL, "pc_gapt_load: n_prob >= 1 and non-NULL arrays required");
+  if (!(n_labels == 1 || n_labels == 2 || n_labels == 4))
+    return fail(PC_EINVAL, "n_labels must be 1, 2 or 4");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  pc_graph_release_impl(c);
+  GImpl *im = new GImpl();
+  c->graph_impl = im;
+  return gload(c, im, n_prob, n_vert, row_ptr, col, w, h, colour, n_temps, betas, n_labels, entry0,
+               kTagGInit);
+}
+
+extern "C" {
 
 int pc_gapt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
   int rc = gimpl_ready(c, 0);
@@ -586,6 +610,100 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
         for (int v = 0; v < n; ++v)
           spins_out[((size_t)r * P + k) * n + v] =
               ((wd[((size_t)(r >> 5) * P + k) * n + g.newid[v]] >> (r & 31)) & 1u) ? 1 : -1;
+  return PC_OK;
+}
+
+int pc_graph_adaptive_ladder(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *row_ptr,
+                             const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
+                             uint32_t entry0, double beta0, double alpha, int n_chains, int sweeps,
+                             int tail, double tol, int max_len, double *beta_out, double *sigma_out,
+                             int32_t *len_out, int32_t *converged_out) {
+  if (!c || !beta_out || !len_out) return fail(PC_EINVAL, "NULL argument");
+  if (n_prob < 1 || n_chains < 1 || n_chains > 128 || sweeps < 1 || tail < 2 || tail > sweeps ||
+      max_len < 1 || !(beta0 > 0.0) || !(alpha > 0.0))
+    return fail(PC_EINVAL, "bad ladder parameters (1 <= n_chains <= 128, 2 <= tail <= sweeps)");
+  if ((int64_t)sweeps * max_len > 0xFFFFFFFFll) return fail(PC_EINVAL, "sweep counter would exceed 2^32");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  const int A = n_chains <= 32 ? 1 : (n_chains <= 64 ? 2 : 4);
+  // the batch is built as 32 "temperatures" per label; every row of the
+  // p-bit table is rewritten with the problem's current beta at each step
+  std::vector<int32_t> nt((size_t)n_prob, 32);
+  std::vector<double> dummy;
+  for (int i = 0; i < n_prob; ++i)
+    for (int r = 0; r < 32; ++r) dummy.push_back(1.0 + r);
+  GImpl im;
+  int rc = gload(c, &im, n_prob, n_vert, row_ptr, col, w, h, colour, nt.data(), dummy.data(), A, entry0,
+                 kTagGLInit);
+  if (rc) return rc;
+  for (int i = 0; i < n_prob; ++i) {
+    const long long eb = im.g[(size_t)i].Ebound;
+    if ((double)tail * (double)eb * (double)eb > 4.0e18) return fail(PC_EINVAL, "tail too long for exact int64 sums");
+  }
+  DevBuf<long long> d_s1, d_s2;
+  DevBuf<int> d_active;
+  if ((rc = d_s1.alloc(128 * (size_t)n_prob)) || (rc = d_s2.alloc(128 * (size_t)n_prob)) ||
+      (rc = d_active.alloc((size_t)n_prob)))
+    return rc;
+  cudaStream_t st = c->stream;
+  std::vector<double> beta((size_t)n_prob, beta0);
+  std::vector<int> active((size_t)n_prob, 1), len((size_t)n_prob, 0), conv((size_t)n_prob, 0);
+  std::vector<uint32_t> pbit(im.d_pbit.n, 0u);
+  std::vector<long long> s1(128 * (size_t)n_prob), s2(128 * (size_t)n_prob);
+  for (int step = 0; step < max_len; ++step) {
+    for (int i = 0; i < n_prob; ++i) {
+      const int Imax = im.g[(size_t)i].Imax, nt2 = 2 * Imax + 1;
+      uint32_t *row = pbit.data() + im.hp[(size_t)i].thbase;
+      for (int I = -Imax; I <= Imax; ++I) row[I + Imax] = pc_pbit_threshold(beta[(size_t)i], I);
+      for (int r = 1; r < 32; ++r) std::memcpy(row + (size_t)r * nt2, row, sizeof(uint32_t) * nt2);
+    }
+    PC_CUDA_TRY(cudaMemcpyAsync(im.d_pbit.p, pbit.data(), pbit.size() * 4, cudaMemcpyHostToDevice, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(d_active.p, active.data(), active.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if ((rc = d_s1.zero(st)) || (rc = d_s2.zero(st))) return rc;
+    GAptArgs a = make_args(c, &im);
+    a.tag_sweep = kTagGLSweep;
+    a.tag_refine = kTagGLRefine;
+    a.ladder = 1;
+    a.window_from = sweeps - tail;
+    a.sum1 = d_s1.p;
+    a.sum2 = d_s2.p;
+    a.active = d_active.p;
+    a.spp = 1;
+    a.n_swaps = sweeps;
+    a.sweep0 = (uint32_t)((int64_t)step * sweeps);
+    if ((rc = gapt_launch(a, n_prob, A, im.Imax, im.staged, im.smem, false, st))) return rc;
+    PC_CUDA_TRY(cudaMemcpyAsync(s1.data(), d_s1.p, s1.size() * 8, cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaMemcpyAsync(s2.data(), d_s2.p, s2.size() * 8, cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+    int left = 0;
+    for (int i = 0; i < n_prob; ++i) {
+      if (!active[(size_t)i]) continue;
+      // sigma_E: square root of the chains' mean unbiased variance (chain b = slot 32 a + r)
+      double mean_var = 0.0;
+      for (int b = 0; b < n_chains; ++b) {
+        const long long q1 = s1[128 * (size_t)i + b], q2 = s2[128 * (size_t)i + b];
+        const long long num = (long long)tail * q2 - q1 * q1;
+        mean_var += (double)num / ((double)tail * (double)(tail - 1));
+      }
+      mean_var /= (double)n_chains;
+      const double sigma = std::sqrt(mean_var);
+      beta_out[(size_t)i * max_len + len[(size_t)i]] = beta[(size_t)i];
+      if (sigma_out) sigma_out[(size_t)i * max_len + len[(size_t)i]] = sigma;
+      ++len[(size_t)i];
+      if (sigma < tol) {
+        conv[(size_t)i] = 1;
+        active[(size_t)i] = 0;
+      } else {
+        beta[(size_t)i] = beta[(size_t)i] + alpha / sigma;
+        left += len[(size_t)i] < max_len;
+        if (len[(size_t)i] >= max_len) active[(size_t)i] = 0;
+      }
+    }
+    if (!left) break;
+  }
+  for (int i = 0; i < n_prob; ++i) {
+    len_out[i] = len[(size_t)i];
+    if (converged_out) converged_out[i] = conv[(size_t)i];
+  }
   return PC_OK;
 }
 

@@ -27,6 +27,9 @@ constexpr int kGMaxColours = 32;
 constexpr int kGMaxDeg = 1023;
 constexpr int kGMaxImax = 127;
 constexpr int kGThreads = 512;
+// counter tags of the APT and adaptive-ladder draws on graphs
+constexpr uint32_t kTagGInit = 15, kTagGSweep = 16, kTagGRefine = 17;
+constexpr uint32_t kTagGLInit = 23, kTagGLSweep = 24, kTagGLRefine = 25;
 constexpr int kGWarps = kGThreads / 32;
 
 struct GProbDev {
@@ -57,6 +60,14 @@ struct GAptArgs {
   uint32_t k0, k1;
   uint32_t sweep0, swap0;       // counters of the first sweep / attempt of this launch
   int n_swaps, spp, icm, joint;
+  // counter tags of the initial-state and sweep draws
+  uint32_t tag_init, tag_sweep, tag_refine;
+  // adaptive-ladder mode (ladder != 0): no ICM, best tracking or swaps; the
+  // energies of attempts t >= window_from accumulate into sum1 / sum2
+  // ([n_prob][128], slot 32 a + r); problems with active[i] == 0 are skipped
+  int ladder, window_from;
+  long long *sum1, *sum2;
+  const int *active;
 };
 
 struct GSqaArgs {

@@ -86,6 +86,9 @@ SIGNATURES = {
     "pc_gapt_get_colours": (c_int, [c_vp, c_int, c_i32p]),
     "pc_gapt_get_best": (c_int, [c_vp, c_int, c_i64p, c_i64p, c_i32p, c_i64p, c_i8p]),
     "pc_gapt_get_stats": (c_int, [c_vp, c_int, c_i64p, c_i64p, c_i64p]),
+    "pc_graph_adaptive_ladder": (c_int, [c_vp, c_int, c_i32p, c_i32p, c_i32p, c_i8p, c_vp, c_vp, c_u32, c_dbl,
+                                         c_dbl, c_int, c_int, c_int, c_dbl, c_int, c_f64p, c_f64p, c_i32p,
+                                         c_i32p]),
     "pc_gsqa_anneal": (c_int, [c_vp, c_int, c_i32p, c_i32p, c_i8p, c_vp, c_vp, c_int, c_dbl, c_int, c_f64p,
                                c_int, c_u32, c_i64p, c_vp]),
     "pc_mlp_create": (c_int, [c_vp, ctypes.POINTER(c_vp), c_f32pp, c_f32pp, c_flt]),
@@ -627,3 +630,26 @@ def pc_gsqa_anneal(ctx, row_ptr, col, w, P: int, T: float, gamma, R: int, run0: 
           ptr(g, ctypes.c_double), R, c_u32(run0), ptr(E, ctypes.c_int64),
           None if s is None else s.ctypes.data)
     return (E, s) if want_spins else E
+
+
+def pc_graph_adaptive_ladder(ctx, graphs, entry0: int = 0, beta0: float = 0.5, alpha: float = 1.25,
+                             n_chains: int = 100, sweeps: int = 10000, tail: int = 1000, tol: float = 1.0,
+                             max_len: int = 64, h_list=None, colours=None):
+    """Adaptive ladders of graphs [(row_ptr, col, w)]: list of (betas, sigmas, converged)."""
+    nv = np.ascontiguousarray([len(g[0]) - 1 for g in graphs], dtype=np.int32)
+    rp = np.ascontiguousarray(np.concatenate([_i32(g[0]) for g in graphs]))
+    cl = np.ascontiguousarray(np.concatenate([_i32(g[1]) for g in graphs]))
+    w = np.ascontiguousarray(np.concatenate([_i8(g[2]) for g in graphs]))
+    h = None if h_list is None else np.ascontiguousarray(np.concatenate([_i8(x) for x in h_list]))
+    co = None if colours is None else np.ascontiguousarray(np.concatenate([_i32(x) for x in colours]))
+    n = len(graphs)
+    beta = np.zeros((n, max_len), np.float64)
+    sig = np.zeros((n, max_len), np.float64)
+    ln = np.zeros(n, np.int32)
+    conv = np.zeros(n, np.int32)
+    _call("pc_graph_adaptive_ladder", ctx, n, ptr(nv, ctypes.c_int32), ptr(rp, ctypes.c_int32),
+          ptr(cl, ctypes.c_int32), ptr(w, ctypes.c_int8), None if h is None else h.ctypes.data,
+          None if co is None else co.ctypes.data, c_u32(entry0), beta0, alpha, n_chains, sweeps, tail, tol,
+          max_len, ptr(beta, ctypes.c_double), ptr(sig, ctypes.c_double), ptr(ln, ctypes.c_int32),
+          ptr(conv, ctypes.c_int32))
+    return [(beta[i, :ln[i]].copy(), sig[i, :ln[i]].copy(), bool(conv[i])) for i in range(n)]

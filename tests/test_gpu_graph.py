@@ -170,3 +170,23 @@ def test_gapt_large_graph_reads_adjacency_from_global_memory(pc, orc):
         o.run(n_sw, 1, True)
         _compare(pc, ctx, o, [g], betas, 4)
     ctx.close()
+
+
+
+@pytest.mark.parametrize("n_chains", [24, 40, 100])
+def test_graph_adaptive_ladder_matches_oracle(pc, orc, n_chains):
+    """Identical betas and sigmas: the chains' post-sweep energy sums are
+    exact integers on both sides and sigma_E follows the same formula."""
+    graphs = [W.dimer_embedding((2, 2, 2), W.ea_couplings((2, 2, 2), 1000, 8)),
+              W.random_graph(90, 3.0, 9, wmax=2),
+              W.lattice_graph((3, 3, 4), (1, 1, 1), W.ea_couplings((3, 3, 4), 1000, 9))[0]]
+    hs = [np.zeros(graphs[0].n, np.int8), W.random_biases(graphs[1].n, 2, 9), np.zeros(graphs[2].n, np.int8)]
+    ctx = pc.Context(0, 77)
+    out = pc.pc_graph_adaptive_ladder(ctx.h, [_trip(g) for g in graphs], entry0=3, n_chains=n_chains,
+                                      sweeps=120, tail=60, max_len=6, h_list=hs)
+    for i, g in enumerate(graphs):
+        b2, s2, ok2 = orc.graph_adaptive_ladder(g.rp, g.col, g.w, h=hs[i], entry=3 + i, seed=77,
+                                                n_chains=n_chains, sweeps=120, tail=60, max_len=6)
+        b1, s1, ok1 = out[i]
+        assert ok1 == ok2 and np.array_equal(b1, b2) and np.array_equal(s1, s2), (i, b1, b2)
+    ctx.close()
