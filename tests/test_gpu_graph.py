@@ -190,3 +190,38 @@ def test_graph_adaptive_ladder_matches_oracle(pc, orc, n_chains):
         b1, s1, ok1 = out[i]
         assert ok1 == ok2 and np.array_equal(b1, b2) and np.array_equal(s1, s2), (i, b1, b2)
     ctx.close()
+
+
+def test_gapt_fuzz_shapes(pc, orc):
+    """Random shapes against the oracle: single vertices, stars with a hub of
+    degree 200, heavy weights (field bounds up to 127), biases, 1 to 32
+    temperatures and every label count."""
+    rng = np.random.default_rng(123)
+    for trial in range(12):
+        A = [1, 2, 4][trial % 3]
+        kind = trial % 4
+        if kind == 0:
+            g = W.csr_from_edges(1 + trial, [])
+        elif kind == 1:
+            leaves = 200
+            g = W.csr_from_edges(leaves + 1, [(0, i) for i in range(1, leaves + 1)])
+        elif kind == 2:
+            g = W.random_graph(int(rng.integers(20, 700)), float(rng.uniform(1, 8)), 300 + trial, wmax=2)
+        else:
+            g = W.random_graph(40, 3.0, 400 + trial, wmax=25)
+        deg = np.diff(g.rp)
+        bound = np.array([np.abs(g.w[g.rp[v]:g.rp[v + 1]]).sum() for v in range(g.n)])
+        hmax = int(max(0, min(5, 127 - bound.max())))
+        h = W.random_biases(g.n, hmax, trial) if (trial % 2 and hmax) else None
+        T = int(rng.integers(1, 33))
+        betas = [np.sort(rng.uniform(0.05, 2.5, T)) + np.arange(T) * 1e-3]
+        icm = A >= 2 and h is None
+        ctx = pc.Context(0, 500 + trial)
+        pc.pc_gapt_load(ctx.h, [_trip(g)], betas, A, trial, h_list=None if h is None else [h])
+        o = orc.GApt([_trip(g)], betas, n_labels=A, seed=500 + trial, entry0=trial,
+                     h_list=None if h is None else [h])
+        pc.pc_gapt_run(ctx.h, 5, 1 + trial % 2, icm)
+        o.run(5, 1 + trial % 2, icm)
+        _compare(pc, ctx, o, [g], betas, A)
+        ctx.close()
+        assert deg.max(initial=0) <= 200
