@@ -296,15 +296,16 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
 //   e_v = W_l + |h| - 2 U,   U = (s_v = +1 ? Cl : W_l - Cl) + |h| y.
 // U is formed bit-sliced (U <= Imax < 2^NP); each warp (one label, 32
 // vertices) transposes the planes and counts bits per replica.
-template <int A, int NP, bool SM>
+// AL: only the first AL labels are counted (their rows of E are rewritten).
+template <int A, int NP, bool SM, int AL = A>
 __device__ void g_energy(const GCta &k, GShared &sh) {
-  if (k.tid < 128) sh.E[k.tid >> 5][k.tid & 31] = 0;
+  if (k.tid < 32 * AL) sh.E[k.tid >> 5][k.tid & 31] = 0;
   __syncthreads();
   int eacc = 0, a_w = 0;
-  const int nitems = 32 * A * ((k.n + 31) / 32);
+  const int nitems = 32 * AL * ((k.n + 31) / 32);
   for (int it0 = 32 * k.warp; it0 < nitems; it0 += kGThreads) {
     int v, a;
-    item_of<A>(it0 + k.lane, v, a);
+    item_of<AL>(it0 + k.lane, v, a);
     a_w = a;
     uint32_t U[NP];
 #pragma unroll
@@ -463,7 +464,8 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
     }
   }
   __syncthreads();
-  const int per = (k.n + kGWarps - 1) / kGWarps;
+  // warp ranges of whole 32-vertex blocks (counts by transpose and popcount)
+  const int per = 32 * ((k.n + 32 * kGWarps - 1) / (32 * kGWarps));
   const int lo = min(k.n, k.warp * per), hi = min(k.n, lo + per);
   for (int pp = 0; pp < A / 2; ++pp) {
     if (k.warp == 0) {
@@ -505,7 +507,10 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
     }
     __syncthreads();
     uint32_t cnt = 0;
-    for (int p = lo; p < hi; ++p) cnt += (k.X[p] >> k.lane) & 1u;
+    for (int p0 = lo; p0 < hi; p0 += 32) {
+      const int p = p0 + k.lane;
+      cnt += __popc(transpose32(p < hi ? k.X[p] : 0u, k.lane));
+    }
     sh.wcnt[k.warp][k.lane] = cnt;
     __syncthreads();
     {
@@ -554,7 +559,10 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
       if (!__syncthreads_or(changed)) break;
     }
     cnt = 0;
-    for (int p = lo; p < hi; ++p) cnt += (k.Cl[p] >> k.lane) & 1u;
+    for (int p0 = lo; p0 < hi; p0 += 32) {
+      const int p = p0 + k.lane;
+      cnt += __popc(transpose32(p < hi ? k.Cl[p] : 0u, k.lane));
+    }
     sh.wcnt[k.warp][k.lane] = cnt;
     __syncthreads();
     if (k.warp == 0) {
@@ -675,7 +683,17 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
       g_best<A>(k, sh, done);
       if (A >= 2 && a.icm) {
         g_icm<A, SM>(k, sh, tt);
-        g_energy<A, NP, SM>(k, sh);
+        if (A == 2) {
+          // a cluster move keeps each pair's E_0 + E_1 and a whole-replica
+          // flip keeps both (h = 0): recount label 0, label 1 follows
+          int keep = 0;
+          if (k.tid < 32) keep = sh.E[0][k.tid] + sh.E[1][k.tid];
+          g_energy<A, NP, SM, 1>(k, sh);
+          if (k.tid < 32) sh.E[1][k.tid] = keep - sh.E[0][k.tid];
+          __syncthreads();
+        } else {
+          g_energy<A, NP, SM>(k, sh);
+        }
         g_best<A>(k, sh, done);
       }
       g_swap<A>(k, sh, tt, a.joint, a.swaptab, swidx);
