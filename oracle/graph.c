@@ -602,10 +602,10 @@ static void gsqa_run(int n, const int32_t *rp, const int32_t *col, const int8_t 
     for (int v = 0; v < n; ++v) {
       const size_t kv = (size_t)k * n + v;
       const int j = ridx[kv];
-      uint32_t ctr[4] = {(uint32_t)(j >> 3), 0u, (uint32_t)rcol[kv], (run << 8) | OR_TAG_GS_INIT};
+      uint32_t ctr[4] = {(uint32_t)j, 0u, (uint32_t)rcol[kv], ((run >> 3) << 8) | OR_TAG_GS_INIT};
       uint32_t x[4];
       or_philox(ctr, seed, x);
-      s[kv] = (or_half(x, j & 7) < 0x8000u) ? 1 : -1;
+      s[kv] = (or_half(x, (int)(run & 7u)) < 0x8000u) ? 1 : -1;
     }
   for (int sw = 0; sw < n_sweeps; ++sw) {
     int32_t jq = or_jperp_q(gamma[sw], P, T);
@@ -624,8 +624,8 @@ static void gsqa_run(int n, const int32_t *rp, const int32_t *col, const int8_t 
           int64_t I = g_field(rp, col, w, h, sk, v);
           int nb = sdn[v] + sup[v];
           const int j = ridx[kv];
-          uint32_t u = or_uniform32(seed, (uint32_t)(j >> 3), (uint32_t)sw, (uint32_t)c, run,
-                                    OR_TAG_GS_SWEEP, OR_TAG_GS_REFINE, j & 7);
+          uint32_t u = or_uniform32(seed, (uint32_t)j, (uint32_t)sw, (uint32_t)c, run >> 3,
+                                    OR_TAG_GS_SWEEP, OR_TAG_GS_REFINE, (int)(run & 7u));
           uint32_t thr = tab[(size_t)((nb + 2) / 2) * (2 * Imax + 1) + (I + Imax)];
           sk[v] = (u < thr) ? 1 : -1;
         }

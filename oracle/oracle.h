@@ -155,7 +155,8 @@ int or_sqa_anneal(const int32_t dims[3], const uint8_t periodic[3], const uint8_
  * with f(k) = k & 1, except f(P-1) = 2 when P is odd; C' = max(C, 2) for
  * even P and max(C, 3) for odd P.  A class is ordered by k, then v; (v, k)
  * of class c with class-local index j in run q uses
- *   v_{j&7}(Philox((j >> 3, s, c, (q << 8) | TAG_GS_SWEEP / TAG_GS_REFINE))). */
+ *   v_{q&7}(Philox((j, s, c, ((q >> 3) << 8) | TAG_GS_SWEEP / TAG_GS_REFINE))),
+ * so one call serves 8 consecutive runs. */
 
 /* 0 if (rp, col, w) is a valid symmetric graph as above; -1 otherwise. */
 int or_graph_check(int n, const int32_t *rp, const int32_t *col, const int8_t *w);

@@ -85,42 +85,6 @@ __device__ __forceinline__ int2 ld_vi(const int2 *vi, int p) {
   return __ldg(vi + p);
 }
 
-// Eq. synapse over neighbours [e0, e1) for the lane's replica in each of the
-// A labels.  An adjacency entry's top 24 bits are the byte offset, from the
-// dynamic shared-memory base `dynb`, of the neighbour's word of label 0 (its
-// label-a word follows at +4a).  With m = -1 (spin +1) or 0 (spin -1) taken
-// by shifting the lane's bit into the sign, a neighbour adds
-// (w ^ ~m) + m + 1 = +-w; the caller adds the +1s (the neighbour count).
-// The entry is decoded once for all labels; pairs of neighbours issue their
-// loads together.
-template <int A, bool SM>
-__device__ __forceinline__ void field_acc(const char *dynb, uint32_t sh, const uint32_t *ad, int e0,
-                                          int e1, int (&acc)[A]) {
-  int e = e0;
-  for (; e + 2 <= e1; e += 2) {
-    const uint32_t n0 = ld_adj<SM>(ad, e), n1 = ld_adj<SM>(ad, e + 1);
-    const char *p0 = dynb + (n0 >> 8), *p1 = dynb + (n1 >> 8);
-    const int w0 = ent_w(n0), w1 = ent_w(n1);
-#pragma unroll
-    for (int a = 0; a < A; ++a) {
-      const uint32_t s0 = *reinterpret_cast<const uint32_t *>(p0 + 4 * a);
-      const uint32_t s1 = *reinterpret_cast<const uint32_t *>(p1 + 4 * a);
-      const int m0 = (int)(s0 << sh) >> 31, m1 = (int)(s1 << sh) >> 31;
-      acc[a] += ((w0 ^ ~m0) + m0) + ((w1 ^ ~m1) + m1);
-    }
-  }
-  if (e < e1) {
-    const uint32_t n0 = ld_adj<SM>(ad, e);
-    const char *p0 = dynb + (n0 >> 8);
-    const int w0 = ent_w(n0);
-#pragma unroll
-    for (int a = 0; a < A; ++a) {
-      const int m0 = (int)(*reinterpret_cast<const uint32_t *>(p0 + 4 * a) << sh) >> 31;
-      acc[a] += (w0 ^ ~m0) + m0;
-    }
-  }
-}
-
 // ---------------------------------------------------------------- bit-sliced sweeps
 // A thread owns one (vertex, label) pair: its 32-bit spin word holds the
 // label's 32 temperatures.  The field of all 32 replicas is summed
@@ -728,95 +692,139 @@ int gapt_launch_t(const GAptArgs &a, int n_prob, size_t smem, bool init, cudaStr
   return PC_OK;
 }
 
-// DT-SQA on the replicated network of a graph (Eq. S.3, Algorithm S1).  A
-// CTA anneals 32 runs (one per lane); the P x n words of its runs stay in
-// shared memory for the whole anneal.  Per sweep the [3][2 Imax + 1]
-// threshold table of that sweep's transverse coupling is staged in shared
-// memory; per colour class of the replicated network, warps take chunks of 8
-// class entries (slice k, vertex p).  The field is Eq. synapse in slice k plus
-// the two neighbouring slices' spins of the same vertex.
+// DT-SQA on the replicated network of a graph (Eq. S.3, Algorithm S1),
+// multi-spin coded: a CTA anneals 32 runs, whose spins of one (slice,
+// vertex) share a word, and a thread owns one entry (slice k, vertex p) of
+// the colour class being swept.  The in-slice field is summed bit-sliced
+// over the neighbour words (NP planes); the two time neighbours' words give
+// each run's count of +1 neighbours in imaginary time.  Run q takes half
+// q & 7 of P(j, s, c, ((q >> 3) << 8) | TAG) (j: class-local index), so one
+// Philox call serves 8 runs.  The sweep's [3][2 Imax + 1] table is staged in
+// shared memory, one copy per lane when it is small (REP), so that threads
+// with different fields do not collide on a bank.  All P n words stay in
+// shared memory for the whole anneal.
+template <int NP, bool REP>
 __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
   extern __shared__ __align__(16) uint32_t dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nt = 2 * a.Imax + 1, ntab = 3 * nt;
-  uint32_t *tab = dyn;                       // [2][3][2 Imax + 1]
-  uint32_t *W = dyn + 2 * ntab;              // [P][n]
+  const int nt = 2 * a.Imax + 1, ntab = 3 * nt, TB = REP ? 32 * ntab : ntab;
+  uint32_t *tab = dyn;                       // [2][TB]
+  uint32_t *W = dyn + 2 * TB;                // [P][n]
   const int n = a.n, P = a.P;
-  const size_t vo = (2 * (size_t)ntab + (size_t)P * n + 1) & ~(size_t)1;
+  const size_t vo = (2 * (size_t)TB + (size_t)P * n + 1) & ~(size_t)1;
   int2 *vinfo = reinterpret_cast<int2 *>(dyn + vo);   // staged vertex table and adjacency
   uint32_t *adj = dyn + vo + 2 * (size_t)n;
   for (int i = tid; i < n; i += kGThreads) vinfo[i] = a.vinfo[i];
   for (int i = tid; i < a.m; i += kGThreads) adj[i] = a.adj[i];
-  const uint32_t sh = 31u - (uint32_t)lane;
-  const uint32_t run = a.run0 + 32u * blockIdx.x + (uint32_t)lane;
-  const uint32_t c3i = (run << 8) | TAG_GS_INIT;
-  const uint32_t c3m = (run << 8) | TAG_GS_SWEEP;
-  const uint32_t c3r = (run << 8) | TAG_GS_REFINE;
+  const uint32_t g0 = (a.run0 >> 3) + 4u * blockIdx.x;   // run group of bit 0 (run0 % 8 == 0)
   // Algorithm S1: random initial states of all slices
   for (int c = 0; c < a.Cp; ++c) {
     const int o0 = a.cls_off[c], nc = a.cls_off[c + 1] - o0;
-    for (int q = warp; 8 * q < nc; q += kGWarps) {
-      const uint4 x = philox((uint32_t)q, 0u, (uint32_t)c, c3i, a.k0, a.k1);
+    for (int j = tid; j < nc; j += kGThreads) {
+      const uint32_t e = __ldg(a.cls + o0 + j);
+      uint32_t word = 0u;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (8 * q + i >= nc) break;
-        const uint32_t e = __ldg(a.cls + o0 + 8 * q + i);
-        const uint32_t word = __ballot_sync(0xFFFFFFFFu, half_lo(x, i) < 0x8000u);
-        if (lane == 0) W[(e >> 20) * n + (e & 0xFFFFFu)] = word;
+      for (int g = 0; g < 4; ++g) {
+        const uint4 x = philox((uint32_t)j, 0u, (uint32_t)c, ((g0 + g) << 8) | TAG_GS_INIT, a.k0, a.k1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (half_lo(x, i) < 0x8000u) word |= 1u << (8 * g + i);
       }
+      W[(size_t)(e >> 20) * n + (e & 0xFFFFFu)] = word;
     }
   }
   __syncthreads();
   for (int s = 0; s < a.S; ++s) {
-    uint32_t *T = tab + (s & 1) * ntab;
-    for (int i = tid; i < ntab; i += kGThreads) T[i] = __ldg(a.table + (size_t)s * ntab + i);
+    uint32_t *T = tab + (s & 1) * TB;
+    const uint32_t *gt = a.table + (size_t)s * ntab;
+    for (int i = tid; i < TB; i += kGThreads) T[i] = __ldg(gt + (REP ? (i >> 5) : i));
     __syncthreads();
     for (int c = 0; c < a.Cp; ++c) {
       const int o0 = a.cls_off[c], nc = a.cls_off[c + 1] - o0;
-      for (int q = warp; 8 * q < nc; q += kGWarps) {
-        const uint4 x = philox((uint32_t)q, (uint32_t)s, (uint32_t)c, c3m, a.k0, a.k1);
+      for (int j = tid; j < nc; j += kGThreads) {
+        const uint32_t e = __ldg(a.cls + o0 + j);
+        const int k = (int)(e >> 20), p = (int)(e & 0xFFFFFu);
+        const uint32_t *Wk = W + (size_t)k * n;
+        const int2 vi = vinfo[p];
+        uint32_t Pl[NP];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if (8 * q + i >= nc) break;
-          const uint32_t e = __ldg(a.cls + o0 + 8 * q + i);
-          const int k = (int)(e >> 20), p = (int)(e & 0xFFFFFu);
-          const uint32_t *Wk = W + (size_t)k * n;
-          const int2 vi = vinfo[p];
-          int acc[1] = {0};
-          field_acc<1, true>(reinterpret_cast<const char *>(Wk), sh, adj + vi.x, 0, vi_deg(vi), acc);
-          const int I = vi_h(vi) + acc[0] + vi_deg(vi);
-          const int kd = k == 0 ? P - 1 : k - 1, ku = k == P - 1 ? 0 : k + 1;
-          const uint32_t nup = ((W[(size_t)kd * n + p] >> lane) & 1u) + ((W[(size_t)ku * n + p] >> lane) & 1u);
-          const uint32_t th = T[nup * nt + (I + a.Imax)];
-          const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
-          bool up = v < thi;
-          if (v == thi) {
-            const uint4 y = philox((uint32_t)q, (uint32_t)s, (uint32_t)c, c3r, a.k0, a.k1);
-            up = (v | half_lo(y, i)) < th;
+        for (int q = 0; q < NP; ++q) Pl[q] = 0u;
+        const int Ws = vfield<1, NP, true>(reinterpret_cast<const char *>(Wk), adj + vi.x, 0, vi_deg(vi), 0, Pl);
+        const int base = vi_h(vi) - Ws + a.Imax;   // in-slice I + Imax = 2 C + base
+        const int kd = k == 0 ? P - 1 : k - 1, ku = k == P - 1 ? 0 : k + 1;
+        const uint32_t wd = W[(size_t)kd * n + p], wu = W[(size_t)ku * n + p];
+        uint32_t word = 0u, tie = 0u;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, ((g0 + g) << 8) | TAG_GS_SWEEP, a.k0, a.k1);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = 8 * g + i;
+            const int idx = (int)(((wd >> r) & 1u) + ((wu >> r) & 1u)) * nt + 2 * vget<NP>(Pl, r) + base;
+            const uint32_t th = REP ? T[32 * idx + lane] : T[idx];
+            const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
+            word |= (v < thi ? 1u : 0u) << r;
+            tie |= (v == thi ? 1u : 0u) << r;
           }
-          const uint32_t word = __ballot_sync(0xFFFFFFFFu, up);
-          if (lane == 0) W[(size_t)k * n + p] = word;
         }
+        while (tie) {   // probability 2^-16 per run: settle with the refine half
+          const int r = __ffs((int)tie) - 1;
+          tie &= tie - 1u;
+          const uint32_t gq = (g0 + (uint32_t)(r >> 3)) << 8;
+          const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, gq | TAG_GS_SWEEP, a.k0, a.k1);
+          const uint4 y = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, gq | TAG_GS_REFINE, a.k0, a.k1);
+          int C = 0;
+#pragma unroll
+          for (int q = 0; q < NP; ++q) C |= (int)((Pl[q] >> r) & 1u) << q;
+          const int idx = (int)(((wd >> r) & 1u) + ((wu >> r) & 1u)) * nt + 2 * C + base;
+          const uint32_t th = REP ? T[32 * idx + lane] : T[idx];
+          const uint32_t u = (half_lo(x, r & 7) << 16) | half_lo(y, r & 7);
+          word = (u < th) ? (word | (1u << r)) : (word & ~(1u << r));
+        }
+        W[(size_t)k * n + p] = word;
       }
       __syncthreads();
     }
   }
   // Algorithm S1: classical energy of every slice (bonds at their endpoint
-  // of higher colour, biases included)
+  // of higher base colour, biases included), bit-sliced as in the APT
+  // energy pass: e_v = W_l + |h| - 2 U per run, U counted per run by warp
+  // transposes over blocks of 32 vertices
   const int runs_here = min(32, a.R - 32 * (int)blockIdx.x);
-  for (int k = 0; k < P; ++k) {
+  const int nb32 = (n + 31) / 32;
+  for (int it0 = 32 * warp; it0 < 32 * P * nb32; it0 += kGThreads) {
+    const int blk = it0 >> 5, k = blk / nb32, v = 32 * (blk % nb32) + lane;
     const uint32_t *Wk = W + (size_t)k * n;
-    long long eacc = 0;
-    for (int p = warp; p < n; p += kGWarps) {
-      const int2 vi = vinfo[p];
-      int acc[1] = {0};
-      field_acc<1, true>(reinterpret_cast<const char *>(Wk), sh, adj + vi.x, 0, vi_kl(vi), acc);
-      const int Ilow = vi_h(vi) + acc[0] + vi_kl(vi);
-      eacc += ((Wk[p] >> lane) & 1u) ? -Ilow : Ilow;
+    uint32_t U[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) U[q] = 0u;
+    int K = 0;
+    if (v < n) {
+      const int2 vi = vinfo[v];
+      uint32_t Pl[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) Pl[q] = 0u;
+      const int Wl = vfield<1, NP, true>(reinterpret_cast<const char *>(Wk), adj + vi.x, 0, vi_kl(vi), 0, Pl);
+      const uint32_t x = Wk[v];
+      uint32_t cy = 0xFFFFFFFFu;   // Wl - Cl = Wl + ~Cl + 1
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const uint32_t wb = ((Wl >> q) & 1) ? 0xFFFFFFFFu : 0u, nb = ~Pl[q];
+        const uint32_t d = wb ^ nb ^ cy;
+        cy = (wb & nb) | (wb & cy) | (nb & cy);
+        U[q] = (x & Pl[q]) | (~x & d);
+      }
+      const int h = vi_h(vi), ha = h < 0 ? -h : h;
+      if (ha) vadd<NP>(U, h < 0 ? ~x : x, (uint32_t)ha);
+      K = Wl + ha;
     }
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) cnt += __popc(transpose32(U[q], lane)) << q;
+    const long long ek = (long long)__reduce_add_sync(0xFFFFFFFFu, (unsigned)K) - 2LL * cnt;
     if (lane < runs_here)
-      atomicAdd((unsigned long long *)&a.E[(size_t)(32 * blockIdx.x + lane) * P + k],
-                (unsigned long long)eacc);
+      atomicAdd(reinterpret_cast<unsigned long long *>(&a.E[(size_t)(32 * blockIdx.x + lane) * P + k]),
+                (unsigned long long)ek);
   }
   if (a.spins)
     for (int i = tid; i < P * n; i += kGThreads) a.spins[(size_t)blockIdx.x * P * n + i] = W[i];
@@ -825,13 +833,20 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
 }  // namespace
 
 size_t gsqa_smem_bytes(int n, int P, int Imax, int m) {
-  const size_t base = (size_t)6 * (2 * Imax + 1) + (size_t)P * n;
+  const size_t ntab = (size_t)3 * (2 * Imax + 1), TB = Imax <= 7 ? 32 * ntab : ntab;
+  const size_t base = 2 * TB + (size_t)P * n;
   return sizeof(uint32_t) * (((base + 1) & ~(size_t)1) + 2 * (size_t)n + (size_t)m);
 }
 
 int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st) {
-  PC_CUDA_TRY(cudaFuncSetAttribute(gsqa_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  gsqa_kernel<<<(a.R + 31) / 32, kGThreads, smem, st>>>(a);
+  const int grid = (a.R + 31) / 32;
+  if (a.Imax <= 7) {
+    PC_CUDA_TRY(cudaFuncSetAttribute(gsqa_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    gsqa_kernel<3, true><<<grid, kGThreads, smem, st>>>(a);
+  } else {
+    PC_CUDA_TRY(cudaFuncSetAttribute(gsqa_kernel<7, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    gsqa_kernel<7, false><<<grid, kGThreads, smem, st>>>(a);
+  }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }

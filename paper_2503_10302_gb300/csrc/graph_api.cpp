@@ -534,6 +534,9 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
     return fail(PC_EINVAL, "pc_gsqa_anneal: P in 2..2047, T > 0, R >= 1, gamma and E_out required");
   for (int s = 0; s < n_sweeps; ++s)
     if (!(gamma[s] > 0)) return fail(PC_EINVAL, "gamma must be > 0");
+  // a word holds 32 runs and one Philox call serves 8 of them
+  if (run0 % 8 != 0) return fail(PC_EINVAL, "run0 must be a multiple of 8");
+  if ((uint64_t)run0 + (uint64_t)R + 32 > (1ull << 27)) return fail(PC_EINVAL, "run ids must stay below 2^27");
   HGraph g;
   int rc = build_graph(n, row_ptr, col, w, h, colour, 4, g);
   if (rc) return rc;

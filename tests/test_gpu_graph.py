@@ -139,12 +139,31 @@ def test_gsqa_matches_oracle(pc, orc, P):
     for gi, (g, h) in enumerate(cases):
         R = 45
         ctx = pc.Context(0, 17 + gi)
-        E1, s1 = pc.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, P, 0.3, gamma, R, run0=11, h=h, want_spins=True)
-        E2, s2 = orc.gsqa_anneal(g.rp, g.col, g.w, P, 0.3, gamma, R, run0=11, seed=17 + gi, h=h,
+        E1, s1 = pc.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, P, 0.3, gamma, R, run0=16, h=h, want_spins=True)
+        E2, s2 = orc.gsqa_anneal(g.rp, g.col, g.w, P, 0.3, gamma, R, run0=16, seed=17 + gi, h=h,
                                  want_spins=True)
         assert np.array_equal(s1, s2), (P, gi)
         assert np.array_equal(E1, E2), (P, gi)
         ctx.close()
+
+
+def test_gsqa_refuses_unaligned_run_ids(pc):
+    g = W.random_graph(20, 2.0, 1)
+    ctx = pc.Context(0, 1)
+    with pytest.raises(RuntimeError):
+        pc.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, 4, 0.5, np.full(3, 1.0), 8, run0=3)
+    ctx.close()
+
+
+def test_gsqa_heavy_weights_take_the_wide_planes(pc, orc):
+    """Field bounds above 7 take 7 bit planes and an unreplicated table."""
+    g = W.random_graph(50, 3.0, 21, wmax=9)
+    gamma = W.linear_gamma_schedule(25, 3.0, 0.1)
+    ctx = pc.Context(0, 9)
+    E1, s1 = pc.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, 6, 0.4, gamma, 40, run0=8, want_spins=True)
+    E2, s2 = orc.gsqa_anneal(g.rp, g.col, g.w, 6, 0.4, gamma, 40, run0=8, seed=9, want_spins=True)
+    assert np.array_equal(s1, s2) and np.array_equal(E1, E2)
+    ctx.close()
 
 
 def test_gsqa_zero_sweeps_is_the_initial_state(pc, orc):
