@@ -440,6 +440,7 @@ def main():
     ap.add_argument("--graph", choices=["dimer_64xL8", "lattice15x15x12_64", "lattice12_64", "random4096_152"])
     ap.add_argument("--graph-labels", type=int, choices=[2, 4], help="graph: one label count only")
     ap.add_argument("--no-sqa", action="store_true", help="graph: skip the DT-SQA lines")
+    ap.add_argument("--sqa-only", action="store_true", help="graph: only the DT-SQA lines")
     ap.add_argument("--adaptive", action="store_true", help="graph-ttt: adaptive ladders instead of geometric")
     ap.add_argument("--sweeps", type=int, default=200)
     ap.add_argument("--batch", choices=["apt_plain_L4", "apt_icm_64xL12", "apt_icm_mixed256"])
@@ -462,7 +463,7 @@ def main():
             batch = batches[name]()
             for icm in ((True, False) if args.icm is None else (bool(args.icm),)):
                 out[f"{name}_icm{int(icm)}"] = apt_throughput(batch, args.sweeps, icm)
-    if args.what in ("graph", "all"):
+    if args.what in ("graph", "all") and not args.sqa_only:
         names = [args.graph] if args.graph else ["dimer_64xL8", "lattice15x15x12_64", "lattice12_64",
                                                  "random4096_152"]
         for name in names:
