@@ -353,8 +353,10 @@ int pc_graph_adaptive_ladder(pc_ctx *ctx, int n_prob, const int32_t *n_vert, con
  * network takes colour (colour[v] + f(k)) mod C' for slice k, f(k) = k & 1
  * except f(P-1) = 2 for odd P, C' = max(C, 2) (even P) or max(C, 3) (odd P).
  * E_out [R][P] classical slice energies (biases included); spins_out
- * [R][P][n] or NULL.  P n 4 bytes of state must fit in shared memory.
- * run0 is a multiple of 8 (one Philox call serves runs 8g .. 8g+7). */
+ * [R][P][n] or NULL.  A run group's P n words of state live in shared
+ * memory: in one CTA when they fit, else split by slices over a cluster of
+ * 2, 4 or 8 CTAs (P n 4 bytes / 8 must fit one CTA).  run0 is a multiple of
+ * 8 (one Philox call serves runs 8g .. 8g+7). */
 int pc_gsqa_anneal(pc_ctx *ctx, int n, const int32_t *row_ptr, const int32_t *col,
                    const int8_t *w, const int8_t *h, const int32_t *colour, int P, double T,
                    int n_sweeps, const double *gamma, int R, uint32_t run0, int64_t *E_out,

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cooperative_groups.h>
 #include <cstdint>
 
 #include "device.cuh"
@@ -703,24 +704,51 @@ int gapt_launch_t(const GAptArgs &a, int n_prob, size_t smem, bool init, cudaStr
 // shared memory, one copy per lane when it is small (REP), so that threads
 // with different fields do not collide on a bank.  All P n words stay in
 // shared memory for the whole anneal.
-template <int NP, bool REP>
+//
+// CL: the slices of a run group are split over a thread-block cluster of
+// a.CS CTAs (rank r holds slices [r P / CS, (r+1) P / CS)), for anneals whose
+// P n words do not fit one CTA.  Only the time neighbours of a range's end
+// slices live in a neighbouring CTA; they are read through distributed
+// shared memory, and every colour phase ends with a cluster barrier.
+template <int NP, bool REP, bool CL>
 __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
+  namespace cg = cooperative_groups;
   extern __shared__ __align__(16) uint32_t dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nt = 2 * a.Imax + 1, ntab = 3 * nt, TB = REP ? 32 * ntab : ntab;
-  uint32_t *tab = dyn;                       // [2][TB]
-  uint32_t *W = dyn + 2 * TB;                // [P][n]
   const int n = a.n, P = a.P;
-  const size_t vo = (2 * (size_t)TB + (size_t)P * n + 1) & ~(size_t)1;
+  const int CS = CL ? a.CS : 1, rank = CL ? (int)cg::this_cluster().block_rank() : 0;
+  const int grp = (int)blockIdx.x / CS;                       // run group (32 runs)
+  const int kb = rank * P / CS, ke = (rank + 1) * P / CS;     // own slices [kb, ke)
+  const int nkmax = (P + CS - 1) / CS;                        // equal carve in every CTA
+  uint32_t *tab = dyn;                       // [2][TB]
+  uint32_t *W = dyn + 2 * TB;                // [nkmax][n]: slice k at (k - kb) n
+  const size_t vo = (2 * (size_t)TB + (size_t)nkmax * n + 1) & ~(size_t)1;
   int2 *vinfo = reinterpret_cast<int2 *>(dyn + vo);   // staged vertex table and adjacency
   uint32_t *adj = dyn + vo + 2 * (size_t)n;
   for (int i = tid; i < n; i += kGThreads) vinfo[i] = a.vinfo[i];
   for (int i = tid; i < a.m; i += kGThreads) adj[i] = a.adj[i];
-  const uint32_t g0 = (a.run0 >> 3) + 4u * blockIdx.x;   // run group of bit 0 (run0 % 8 == 0)
+  // the end slices' outer time neighbours: the last slice of rank - 1 and
+  // the first slice of rank + 1 (this CTA itself without a cluster)
+  const int rl = (rank + CS - 1) % CS, rr = (rank + 1) % CS;
+  const uint32_t *Wl = W + (size_t)((rl + 1) * P / CS - rl * P / CS - 1) * n;
+  const uint32_t *Wr = W;
+  if (CL) {
+    Wl = cg::this_cluster().map_shared_rank(W, rl) + (size_t)((rl + 1) * P / CS - rl * P / CS - 1) * n;
+    Wr = cg::this_cluster().map_shared_rank(W, rr);
+  }
+  const uint32_t g0 = (a.run0 >> 3) + 4u * (uint32_t)grp;   // run group of bit 0 (run0 % 8 == 0)
+  // this CTA's part of colour class c: entries [o0 + lo, o0 + hi) of the class list
+  auto part = [&](int c, int &o0, int &lo, int &hi) {
+    o0 = a.cls_off[c];
+    lo = CL ? a.cls_rank[c * (CS + 1) + rank] : 0;
+    hi = CL ? a.cls_rank[c * (CS + 1) + rank + 1] : a.cls_off[c + 1] - o0;
+  };
   // Algorithm S1: random initial states of all slices
   for (int c = 0; c < a.Cp; ++c) {
-    const int o0 = a.cls_off[c], nc = a.cls_off[c + 1] - o0;
-    for (int j = tid; j < nc; j += kGThreads) {
+    int o0, lo, hi;
+    part(c, o0, lo, hi);
+    for (int j = lo + tid; j < hi; j += kGThreads) {
       const uint32_t e = __ldg(a.cls + o0 + j);
       uint32_t word = 0u;
 #pragma unroll
@@ -730,29 +758,31 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
         for (int i = 0; i < 8; ++i)
           if (half_lo(x, i) < 0x8000u) word |= 1u << (8 * g + i);
       }
-      W[(size_t)(e >> 20) * n + (e & 0xFFFFFu)] = word;
+      W[(size_t)((int)(e >> 20) - kb) * n + (e & 0xFFFFFu)] = word;
     }
   }
-  __syncthreads();
+  if (CL) cg::this_cluster().sync();
+  else __syncthreads();
   for (int s = 0; s < a.S; ++s) {
     uint32_t *T = tab + (s & 1) * TB;
     const uint32_t *gt = a.table + (size_t)s * ntab;
     for (int i = tid; i < TB; i += kGThreads) T[i] = __ldg(gt + (REP ? (i >> 5) : i));
     __syncthreads();
     for (int c = 0; c < a.Cp; ++c) {
-      const int o0 = a.cls_off[c], nc = a.cls_off[c + 1] - o0;
-      for (int j = tid; j < nc; j += kGThreads) {
+      int o0, lo, hi;
+      part(c, o0, lo, hi);
+      for (int j = lo + tid; j < hi; j += kGThreads) {
         const uint32_t e = __ldg(a.cls + o0 + j);
         const int k = (int)(e >> 20), p = (int)(e & 0xFFFFFu);
-        const uint32_t *Wk = W + (size_t)k * n;
+        const uint32_t *Wk = W + (size_t)(k - kb) * n;
         const int2 vi = vinfo[p];
         uint32_t Pl[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) Pl[q] = 0u;
         const int Ws = vfield<1, NP, true>(reinterpret_cast<const char *>(Wk), adj + vi.x, 0, vi_deg(vi), 0, Pl);
         const int base = vi_h(vi) - Ws + a.Imax;   // in-slice I + Imax = 2 C + base
-        const int kd = k == 0 ? P - 1 : k - 1, ku = k == P - 1 ? 0 : k + 1;
-        const uint32_t wd = W[(size_t)kd * n + p], wu = W[(size_t)ku * n + p];
+        const uint32_t wd = k > kb ? Wk[p - n] : Wl[p];
+        const uint32_t wu = k + 1 < ke ? Wk[p + n] : Wr[p];
         uint32_t word = 0u, tie = 0u;
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
@@ -781,20 +811,21 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
           const uint32_t u = (half_lo(x, r & 7) << 16) | half_lo(y, r & 7);
           word = (u < th) ? (word | (1u << r)) : (word & ~(1u << r));
         }
-        W[(size_t)k * n + p] = word;
+        W[(size_t)(k - kb) * n + p] = word;
       }
-      __syncthreads();
+      if (CL) cg::this_cluster().sync();
+      else __syncthreads();
     }
   }
   // Algorithm S1: classical energy of every slice (bonds at their endpoint
   // of higher base colour, biases included), bit-sliced as in the APT
   // energy pass: e_v = W_l + |h| - 2 U per run, U counted per run by warp
   // transposes over blocks of 32 vertices
-  const int runs_here = min(32, a.R - 32 * (int)blockIdx.x);
+  const int runs_here = min(32, a.R - 32 * grp);
   const int nb32 = (n + 31) / 32;
-  for (int it0 = 32 * warp; it0 < 32 * P * nb32; it0 += kGThreads) {
-    const int blk = it0 >> 5, k = blk / nb32, v = 32 * (blk % nb32) + lane;
-    const uint32_t *Wk = W + (size_t)k * n;
+  for (int it0 = 32 * warp; it0 < 32 * (ke - kb) * nb32; it0 += kGThreads) {
+    const int blk = it0 >> 5, k = kb + blk / nb32, v = 32 * (blk % nb32) + lane;
+    const uint32_t *Wk = W + (size_t)(k - kb) * n;
     uint32_t U[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) U[q] = 0u;
@@ -823,32 +854,51 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
     for (int q = 0; q < NP; ++q) cnt += __popc(transpose32(U[q], lane)) << q;
     const long long ek = (long long)__reduce_add_sync(0xFFFFFFFFu, (unsigned)K) - 2LL * cnt;
     if (lane < runs_here)
-      atomicAdd(reinterpret_cast<unsigned long long *>(&a.E[(size_t)(32 * blockIdx.x + lane) * P + k]),
+      atomicAdd(reinterpret_cast<unsigned long long *>(&a.E[(size_t)(32 * grp + lane) * P + k]),
                 (unsigned long long)ek);
   }
   if (a.spins)
-    for (int i = tid; i < P * n; i += kGThreads) a.spins[(size_t)blockIdx.x * P * n + i] = W[i];
+    for (int i = tid; i < (ke - kb) * n; i += kGThreads) a.spins[((size_t)grp * P + kb) * n + i] = W[i];
 }
 
 }  // namespace
 
-size_t gsqa_smem_bytes(int n, int P, int Imax, int m) {
+size_t gsqa_smem_bytes(int n, int P, int Imax, int m, int CS) {
   const size_t ntab = (size_t)3 * (2 * Imax + 1), TB = Imax <= 7 ? 32 * ntab : ntab;
-  const size_t base = 2 * TB + (size_t)P * n;
+  const size_t base = 2 * TB + (size_t)((P + CS - 1) / CS) * n;
   return sizeof(uint32_t) * (((base + 1) & ~(size_t)1) + 2 * (size_t)n + (size_t)m);
 }
 
-int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st) {
-  const int grid = (a.R + 31) / 32;
-  if (a.Imax <= 7) {
-    PC_CUDA_TRY(cudaFuncSetAttribute(gsqa_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    gsqa_kernel<3, true><<<grid, kGThreads, smem, st>>>(a);
+template <int NP, bool REP, bool CL>
+int gsqa_launch_t(const GSqaArgs &a, size_t smem, cudaStream_t st) {
+  PC_CUDA_TRY(cudaFuncSetAttribute(gsqa_kernel<NP, REP, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  const unsigned grid = (unsigned)(((a.R + 31) / 32) * (CL ? a.CS : 1));
+  if (!CL) {
+    gsqa_kernel<NP, REP, CL><<<grid, kGThreads, smem, st>>>(a);
   } else {
-    PC_CUDA_TRY(cudaFuncSetAttribute(gsqa_kernel<7, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    gsqa_kernel<7, false><<<grid, kGThreads, smem, st>>>(a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3((unsigned)kGThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, gsqa_kernel<NP, REP, CL>, a));
   }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
+}
+
+int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st) {
+  const bool small = a.Imax <= 7, cl = a.CS > 1;
+  if (small) return cl ? gsqa_launch_t<3, true, true>(a, smem, st) : gsqa_launch_t<3, true, false>(a, smem, st);
+  return cl ? gsqa_launch_t<7, false, true>(a, smem, st) : gsqa_launch_t<7, false, false>(a, smem, st);
 }
 
 size_t gapt_smem_bytes(int n, int A, int Imax, int m) {

@@ -540,7 +540,11 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
   HGraph g;
   int rc = build_graph(n, row_ptr, col, w, h, colour, 4, g);
   if (rc) return rc;
-  const size_t smem = gsqa_smem_bytes(n, P, g.Imax, (int)g.adj.size());
+  // the slices of a run group go to a cluster of CS CTAs when one CTA cannot hold them
+  int CS = 1;
+  while (CS < 8 && 2 * CS <= P && gsqa_smem_bytes(n, P, g.Imax, (int)g.adj.size(), CS) + 8192 > (size_t)c->smem_optin)
+    CS *= 2;
+  const size_t smem = gsqa_smem_bytes(n, P, g.Imax, (int)g.adj.size(), CS);
   if ((rc = static_smem_guard(c, smem))) return rc;
   // colour classes of the replicated network, each ordered by slice, then vertex
   const int Cp = std::max(g.C, (P & 1) ? 3 : 2);
@@ -556,6 +560,15 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
     }
   }
   cls_off[Cp] = (int)cls.size();
+  // per class, the list offsets where each cluster rank's slices begin
+  std::vector<int> cls_rank((size_t)Cp * (CS + 1), 0);
+  for (int cp = 0; cp < Cp; ++cp)
+    for (int r = 0; r <= CS; ++r) {
+      const int kfirst = r * P / CS;
+      int o = cls_off[cp];
+      while (o < cls_off[cp + 1] && (int)(cls[o] >> 20) < kfirst) ++o;
+      cls_rank[(size_t)cp * (CS + 1) + r] = o - cls_off[cp];
+    }
   const int nt = 2 * g.Imax + 1;
   std::vector<uint32_t> table((size_t)std::max(n_sweeps, 1) * 3 * nt);
   const double beta_eff = 1.0 / ((double)P * T);
@@ -569,13 +582,14 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
   cudaStream_t st = c->stream;
   DevBuf<int2> d_vinfo;
   DevBuf<uint32_t> d_adj, d_cls, d_table, d_spins;
-  DevBuf<int> d_off;
+  DevBuf<int> d_off, d_rank;
   DevBuf<long long> d_E;
   std::vector<uint32_t> adj = g.adj;
   if (adj.empty()) adj.push_back(0u);
   const int groups = (R + 31) / 32;
   if ((rc = upload(d_vinfo, g.vinfo, st)) || (rc = upload(d_adj, adj, st)) || (rc = upload(d_cls, cls, st)) ||
       (rc = upload(d_off, cls_off, st)) || (rc = upload(d_table, table, st)) ||
+      (rc = upload(d_rank, cls_rank, st)) ||
       (rc = d_E.alloc((size_t)R * P)) || (rc = d_E.zero(st)))
     return rc;
   if (spins_out && (rc = d_spins.alloc((size_t)groups * P * n))) return rc;
@@ -597,6 +611,8 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
   a.table = d_table.p;
   a.E = d_E.p;
   a.spins = spins_out ? d_spins.p : nullptr;
+  a.CS = CS;
+  a.cls_rank = d_rank.p;
   if ((rc = gsqa_launch(a, smem, st))) return rc;
   std::vector<long long> E((size_t)R * P);
   PC_CUDA_TRY(cudaMemcpyAsync(E.data(), d_E.p, E.size() * 8, cudaMemcpyDeviceToHost, st));

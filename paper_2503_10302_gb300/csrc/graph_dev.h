@@ -80,6 +80,8 @@ struct GSqaArgs {
   const uint32_t *table;        // [S][3][2 Imax + 1]
   long long *E;                 // [R][P]
   uint32_t *spins;              // [ceil(R/32)][P][n] words (nullable)
+  int CS;                       // CTAs per run group (cluster size; 1: one CTA holds all slices)
+  const int *cls_rank;          // [Cp][CS + 1]: class-list offsets of each CTA's slices (CS > 1)
 };
 
 // m < 0: vertex table and adjacency read from global memory; m >= 0: staged
@@ -88,7 +90,7 @@ size_t gapt_smem_bytes(int n, int A, int Imax, int m);
 // Imax: the batch's largest field bound (selects the bit-plane count).
 int gapt_launch(const GAptArgs &a, int n_prob, int A, int Imax, bool staged, size_t smem, bool init,
                 cudaStream_t st);
-size_t gsqa_smem_bytes(int n, int P, int Imax, int m);
+size_t gsqa_smem_bytes(int n, int P, int Imax, int m, int CS);
 int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st);
 
 }  // namespace pc

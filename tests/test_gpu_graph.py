@@ -166,6 +166,26 @@ def test_gsqa_heavy_weights_take_the_wide_planes(pc, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", ["dimer_P512", "random_odd_P203"])
+def test_gsqa_cluster_split_matches_oracle(pc, orc, case):
+    """Anneals too large for one CTA: the slices of a run group are split over
+    a cluster of 2 (dimer embedding, P = 512) or 8 CTAs (1000-vertex graph
+    with heavy weights, odd P = 203), boundary slices read through
+    distributed shared memory."""
+    if case == "dimer_P512":
+        g, P, sw, h = W.dimer_embedding((4, 4, 4), W.ea_couplings((4, 4, 4), 1000, 12)), 512, 12, None
+    else:
+        g, P, sw = W.sparse_random_graph(1000, 4.0, 5, wmax=6), 203, 8
+        h = W.random_biases(g.n, 2, 5)
+    gamma = W.linear_gamma_schedule(sw, 2.0, 0.2)
+    R = 40
+    ctx = pc.Context(0, 31)
+    E1, s1 = pc.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, P, 0.2, gamma, R, run0=24, h=h, want_spins=True)
+    E2, s2 = orc.gsqa_anneal(g.rp, g.col, g.w, P, 0.2, gamma, R, run0=24, seed=31, h=h, want_spins=True)
+    assert np.array_equal(s1, s2) and np.array_equal(E1, E2)
+    ctx.close()
+
+
 def test_gsqa_zero_sweeps_is_the_initial_state(pc, orc):
     g = W.random_graph(40, 2.0, 3)
     ctx = pc.Context(0, 5)
