@@ -710,7 +710,9 @@ int gapt_launch_t(const GAptArgs &a, int n_prob, size_t smem, bool init, cudaStr
 // P n words do not fit one CTA.  Only the time neighbours of a range's end
 // slices live in a neighbouring CTA; they are read through distributed
 // shared memory, and every colour phase ends with a cluster barrier.
-template <int NP, bool REP, bool CL>
+// SMG: the vertex table and adjacency are staged in shared memory (else
+// they are read through the L1 cache).
+template <int NP, bool REP, bool CL, bool SMG>
 __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
   namespace cg = cooperative_groups;
   extern __shared__ __align__(16) uint32_t dyn[];
@@ -724,10 +726,16 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
   uint32_t *tab = dyn;                       // [2][TB]
   uint32_t *W = dyn + 2 * TB;                // [nkmax][n]: slice k at (k - kb) n
   const size_t vo = (2 * (size_t)TB + (size_t)nkmax * n + 1) & ~(size_t)1;
-  int2 *vinfo = reinterpret_cast<int2 *>(dyn + vo);   // staged vertex table and adjacency
-  uint32_t *adj = dyn + vo + 2 * (size_t)n;
-  for (int i = tid; i < n; i += kGThreads) vinfo[i] = a.vinfo[i];
-  for (int i = tid; i < a.m; i += kGThreads) adj[i] = a.adj[i];
+  const int2 *vinfo = a.vinfo;
+  const uint32_t *adj = a.adj;
+  if (SMG) {   // staged vertex table and adjacency
+    int2 *vs = reinterpret_cast<int2 *>(dyn + vo);
+    uint32_t *as = dyn + vo + 2 * (size_t)n;
+    for (int i = tid; i < n; i += kGThreads) vs[i] = a.vinfo[i];
+    for (int i = tid; i < a.m; i += kGThreads) as[i] = a.adj[i];
+    vinfo = vs;
+    adj = as;
+  }
   // the end slices' outer time neighbours: the last slice of rank - 1 and
   // the first slice of rank + 1 (this CTA itself without a cluster)
   const int rl = (rank + CS - 1) % CS, rr = (rank + 1) % CS;
@@ -775,11 +783,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
         const uint32_t e = __ldg(a.cls + o0 + j);
         const int k = (int)(e >> 20), p = (int)(e & 0xFFFFFu);
         const uint32_t *Wk = W + (size_t)(k - kb) * n;
-        const int2 vi = vinfo[p];
+        const int2 vi = ld_vi<SMG>(vinfo, p);
         uint32_t Pl[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) Pl[q] = 0u;
-        const int Ws = vfield<1, NP, true>(reinterpret_cast<const char *>(Wk), adj + vi.x, 0, vi_deg(vi), 0, Pl);
+        const int Ws = vfield<1, NP, SMG>(reinterpret_cast<const char *>(Wk), adj + vi.x, 0, vi_deg(vi), 0, Pl);
         const int base = vi_h(vi) - Ws + a.Imax;   // in-slice I + Imax = 2 C + base
         const uint32_t wd = k > kb ? Wk[p - n] : Wl[p];
         const uint32_t wu = k + 1 < ke ? Wk[p + n] : Wr[p];
@@ -831,11 +839,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
     for (int q = 0; q < NP; ++q) U[q] = 0u;
     int K = 0;
     if (v < n) {
-      const int2 vi = vinfo[v];
+      const int2 vi = ld_vi<SMG>(vinfo, v);
       uint32_t Pl[NP];
 #pragma unroll
       for (int q = 0; q < NP; ++q) Pl[q] = 0u;
-      const int Wl = vfield<1, NP, true>(reinterpret_cast<const char *>(Wk), adj + vi.x, 0, vi_kl(vi), 0, Pl);
+      const int Wl = vfield<1, NP, SMG>(reinterpret_cast<const char *>(Wk), adj + vi.x, 0, vi_kl(vi), 0, Pl);
       const uint32_t x = Wk[v];
       uint32_t cy = 0xFFFFFFFFu;   // Wl - Cl = Wl + ~Cl + 1
 #pragma unroll
@@ -866,16 +874,17 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
 size_t gsqa_smem_bytes(int n, int P, int Imax, int m, int CS) {
   const size_t ntab = (size_t)3 * (2 * Imax + 1), TB = Imax <= 7 ? 32 * ntab : ntab;
   const size_t base = 2 * TB + (size_t)((P + CS - 1) / CS) * n;
+  if (m < 0) return sizeof(uint32_t) * base;
   return sizeof(uint32_t) * (((base + 1) & ~(size_t)1) + 2 * (size_t)n + (size_t)m);
 }
 
-template <int NP, bool REP, bool CL>
+template <int NP, bool REP, bool CL, bool SMG>
 int gsqa_launch_t(const GSqaArgs &a, size_t smem, cudaStream_t st) {
-  PC_CUDA_TRY(cudaFuncSetAttribute(gsqa_kernel<NP, REP, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+  auto kern = gsqa_kernel<NP, REP, CL, SMG>;
+  PC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const unsigned grid = (unsigned)(((a.R + 31) / 32) * (CL ? a.CS : 1));
   if (!CL) {
-    gsqa_kernel<NP, REP, CL><<<grid, kGThreads, smem, st>>>(a);
+    kern<<<grid, kGThreads, smem, st>>>(a);
   } else {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -889,16 +898,24 @@ int gsqa_launch_t(const GSqaArgs &a, size_t smem, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, gsqa_kernel<NP, REP, CL>, a));
+    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
   }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
 }
 
-int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st) {
-  const bool small = a.Imax <= 7, cl = a.CS > 1;
-  if (small) return cl ? gsqa_launch_t<3, true, true>(a, smem, st) : gsqa_launch_t<3, true, false>(a, smem, st);
-  return cl ? gsqa_launch_t<7, false, true>(a, smem, st) : gsqa_launch_t<7, false, false>(a, smem, st);
+int gsqa_launch(const GSqaArgs &a, bool staged, size_t smem, cudaStream_t st) {
+  const int sel = (a.Imax <= 7 ? 4 : 0) + (a.CS > 1 ? 2 : 0) + (staged ? 1 : 0);
+  switch (sel) {
+    case 0: return gsqa_launch_t<7, false, false, false>(a, smem, st);
+    case 1: return gsqa_launch_t<7, false, false, true>(a, smem, st);
+    case 2: return gsqa_launch_t<7, false, true, false>(a, smem, st);
+    case 3: return gsqa_launch_t<7, false, true, true>(a, smem, st);
+    case 4: return gsqa_launch_t<3, true, false, false>(a, smem, st);
+    case 5: return gsqa_launch_t<3, true, false, true>(a, smem, st);
+    case 6: return gsqa_launch_t<3, true, true, false>(a, smem, st);
+    default: return gsqa_launch_t<3, true, true, true>(a, smem, st);
+  }
 }
 
 size_t gapt_smem_bytes(int n, int A, int Imax, int m) {

@@ -540,11 +540,21 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
   HGraph g;
   int rc = build_graph(n, row_ptr, col, w, h, colour, 4, g);
   if (rc) return rc;
-  // the slices of a run group go to a cluster of CS CTAs when one CTA cannot hold them
+  // the slices of a run group go to a cluster of CS CTAs when one CTA cannot
+  // hold them; the graph itself is staged in shared memory when it still fits
+  const size_t budget = (size_t)c->smem_optin - 8192;
   int CS = 1;
-  while (CS < 8 && 2 * CS <= P && gsqa_smem_bytes(n, P, g.Imax, (int)g.adj.size(), CS) + 8192 > (size_t)c->smem_optin)
-    CS *= 2;
-  const size_t smem = gsqa_smem_bytes(n, P, g.Imax, (int)g.adj.size(), CS);
+  bool staged = true;
+  auto fits = [&](int cs, bool st_) {
+    return gsqa_smem_bytes(n, P, g.Imax, st_ ? (int)g.adj.size() : -1, cs) <= budget;
+  };
+  while (!fits(CS, true) && CS < 8 && 2 * CS <= P) CS *= 2;
+  if (!fits(CS, true)) {
+    staged = false;
+    CS = 1;
+    while (!fits(CS, false) && CS < 8 && 2 * CS <= P) CS *= 2;
+  }
+  const size_t smem = gsqa_smem_bytes(n, P, g.Imax, staged ? (int)g.adj.size() : -1, CS);
   if ((rc = static_smem_guard(c, smem))) return rc;
   // colour classes of the replicated network, each ordered by slice, then vertex
   const int Cp = std::max(g.C, (P & 1) ? 3 : 2);
@@ -613,7 +623,7 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
   a.spins = spins_out ? d_spins.p : nullptr;
   a.CS = CS;
   a.cls_rank = d_rank.p;
-  if ((rc = gsqa_launch(a, smem, st))) return rc;
+  if ((rc = gsqa_launch(a, staged, smem, st))) return rc;
   std::vector<long long> E((size_t)R * P);
   PC_CUDA_TRY(cudaMemcpyAsync(E.data(), d_E.p, E.size() * 8, cudaMemcpyDeviceToHost, st));
   std::vector<uint32_t> wd;

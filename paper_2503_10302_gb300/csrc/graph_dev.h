@@ -91,6 +91,7 @@ size_t gapt_smem_bytes(int n, int A, int Imax, int m);
 int gapt_launch(const GAptArgs &a, int n_prob, int A, int Imax, bool staged, size_t smem, bool init,
                 cudaStream_t st);
 size_t gsqa_smem_bytes(int n, int P, int Imax, int m, int CS);
-int gsqa_launch(const GSqaArgs &a, size_t smem, cudaStream_t st);
+// staged: vertex table and adjacency in shared memory (m >= 0 in gsqa_smem_bytes)
+int gsqa_launch(const GSqaArgs &a, bool staged, size_t smem, cudaStream_t st);
 
 }  // namespace pc

@@ -475,6 +475,11 @@ def main():
     if args.what in ("graph", "all") and not args.no_sqa:
         out["graph_sqa_dimerL4_P64"] = graph_sqa_throughput(
             W.dimer_embedding((4, 4, 4), W.ea_couplings((4, 4, 4), W.SEED_INSTANCES, 0)), 64, 4864, 1000)
+        # an embedding of the paper's 15 x 15 x 12 shape (5400 p-bits, 4 colours): a run
+        # group's slices are split over a CTA cluster
+        d = (15, 15, 12)
+        out["graph_sqa_dimer15x15x12_P64"] = graph_sqa_throughput(
+            W.dimer_embedding(d, W.ea_couplings(d, W.SEED_INSTANCES, 0)), 64, 4864, 1000)
         out["graph_sqa_lattice5x5x4_P65"] = graph_sqa_throughput(
             W.lattice_graph((5, 5, 4), (1, 1, 1), W.ea_couplings((5, 5, 4), W.SEED_INSTANCES, 0))[0], 65, 4864,
             1000)

@@ -166,14 +166,19 @@ def test_gsqa_heavy_weights_take_the_wide_planes(pc, orc):
     ctx.close()
 
 
-@pytest.mark.parametrize("case", ["dimer_P512", "random_odd_P203"])
+@pytest.mark.parametrize("case", ["dimer_P512", "random_odd_P203", "dimer_15x15x24_P16"])
 def test_gsqa_cluster_split_matches_oracle(pc, orc, case):
     """Anneals too large for one CTA: the slices of a run group are split over
-    a cluster of 2 (dimer embedding, P = 512) or 8 CTAs (1000-vertex graph
-    with heavy weights, odd P = 203), boundary slices read through
-    distributed shared memory."""
+    a cluster of 2 (dimer embedding, P = 512), 8 (1000-vertex graph with heavy
+    weights, odd P = 203) or 4 CTAs (10800-p-bit embedding whose graph is read
+    from global memory), boundary slices read through distributed shared
+    memory."""
     if case == "dimer_P512":
         g, P, sw, h = W.dimer_embedding((4, 4, 4), W.ea_couplings((4, 4, 4), 1000, 12)), 512, 12, None
+    elif case == "dimer_15x15x24_P16":
+        # 10800 p-bits: the graph itself stays in global memory (read through L1)
+        d = (15, 15, 24)
+        g, P, sw, h = W.dimer_embedding(d, W.ea_couplings(d, 1000, 13)), 16, 3, None
     else:
         g, P, sw = W.sparse_random_graph(1000, 4.0, 5, wmax=6), 203, 8
         h = W.random_biases(g.n, 2, 5)
