@@ -22,25 +22,6 @@
 #include "graph_dev.h"
 #include "internal.h"
 
-// Optional per-phase cycle counters of CTA 0 (build with -DPC_GRAPH_PROFILE=1;
-// read with pc_graph_profile_read).  Off by default.
-#ifndef PC_GRAPH_PROFILE
-#define PC_GRAPH_PROFILE 0
-#endif
-#if PC_GRAPH_PROFILE
-__device__ unsigned long long g_graph_prof[16];
-#define GPROF(slot, t0)                                                         \
-  do {                                                                          \
-    if (blockIdx.x == 0 && threadIdx.x == 0) {                                  \
-      const long long t1_ = clock64();                                          \
-      atomicAdd(&g_graph_prof[slot], (unsigned long long)(t1_ - (t0)));         \
-      (t0) = t1_;                                                               \
-    }                                                                           \
-  } while (0)
-#else
-#define GPROF(slot, t0) do { } while (0)
-#endif
-
 namespace pc {
 namespace {
 
@@ -436,7 +417,7 @@ __device__ void g_swap(const GCta &k, GShared &sh, uint32_t t, int joint, const 
 // both replicas or, when it holds more than half of the n spins, one whole
 // replica (x1 bit 0) flips.
 template <int A, bool SM>
-__device__ void g_icm(const GCta &k, GShared &sh, uint32_t t, long long &pt) {
+__device__ void g_icm(const GCta &k, GShared &sh, uint32_t t) {
   const uint32_t c3 = (k.ent << 8) | TAG_G_ICM;
   if (k.tid < 32 * (A / 2)) {
     const int pp = k.tid >> 5, r = k.tid & 31;
@@ -490,7 +471,6 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t, long long &pt) {
       k.Cl[p] = 0u;
     }
     __syncthreads();
-    GPROF(3, pt);
     uint32_t cnt = 0;
     for (int p0 = lo; p0 < hi; p0 += 32) {
       const int p = p0 + k.lane;
@@ -522,13 +502,9 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t, long long &pt) {
       }
     }
     __syncthreads();
-    GPROF(4, pt);
     // flood fill: grow every seed inside X until nothing changes; each
     // change adds a bit, so at most 32 n passes
     for (;;) {
-#if PC_GRAPH_PROFILE
-      if (blockIdx.x == 0 && k.tid == 0) atomicAdd(&g_graph_prof[6], 1ull);
-#endif
       int changed = 0;
       for (int p = k.tid; p < k.n; p += kGThreads) {
         const uint32_t cl = k.Cl[p], cand = k.X[p] & ~cl;
@@ -547,7 +523,6 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t, long long &pt) {
       }
       if (!__syncthreads_or(changed)) break;
     }
-    GPROF(5, pt);
     cnt = 0;
     for (int p0 = lo; p0 < hi; p0 += 32) {
       const int p = p0 + k.lane;
@@ -580,7 +555,6 @@ __device__ void g_icm(const GCta &k, GShared &sh, uint32_t t, long long &pt) {
       k.S[i] ^= (k.Cl[p] & smallM & (selA[kk] | selB[kk])) | sh.whole[kk];
     }
     __syncthreads();
-    GPROF(7, pt);
   }
 }
 
@@ -657,16 +631,10 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
     }
     __syncthreads();
     const uint32_t *swidx = a.swapidx + P.swbase;
-    long long pt = 0;
-#if PC_GRAPH_PROFILE
-    pt = clock64();
-#endif
     for (int t = 0; t < a.n_swaps; ++t) {
       const uint32_t tt = a.swap0 + (uint32_t)t;
       for (int q = 0; q < a.spp; ++q) g_sweep<A, NP, SM>(k, sh, a.sweep0 + (uint32_t)(t * a.spp + q));
-      GPROF(0, pt);
       g_energy<A, NP, SM>(k, sh);
-      GPROF(1, pt);
       if (a.ladder) {
         // thread tid reads (and next zeroes) only its own slot's energy
         if (t >= a.window_from && k.tid < 32 * A) {
@@ -678,9 +646,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
       }
       const long long done = (long long)a.sweep0 + (long long)(t + 1) * a.spp;
       g_best<A>(k, sh, done);
-      GPROF(2, pt);
       if (A >= 2 && a.icm) {
-        g_icm<A, SM>(k, sh, tt, pt);
+        g_icm<A, SM>(k, sh, tt);
         if (A == 2) {
           // a cluster move keeps each pair's E_0 + E_1 and a whole-replica
           // flip keeps both (h = 0): recount label 0, label 1 follows
@@ -692,12 +659,9 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
         } else {
           g_energy<A, NP, SM>(k, sh);
         }
-        GPROF(8, pt);
         g_best<A>(k, sh, done);
-        GPROF(2, pt);
       }
       g_swap<A>(k, sh, tt, a.joint, a.swaptab, swidx);
-      GPROF(9, pt);
     }
     unsigned long long *st = a.stats + P.statbase;
     const int np = (P.T > 1 ? P.T - 1 : 0) * A;
@@ -981,14 +945,3 @@ int gapt_launch(const GAptArgs &a, int n_prob, int A, int Imax, bool staged, siz
 }
 
 }  // namespace pc
-
-#if PC_GRAPH_PROFILE
-extern "C" int pc_graph_profile_read(unsigned long long *out, int reset) {
-  PC_CUDA_TRY(cudaMemcpyFromSymbol(out, g_graph_prof, sizeof(unsigned long long) * 16));
-  if (reset) {
-    unsigned long long z[16] = {0};
-    PC_CUDA_TRY(cudaMemcpyToSymbol(g_graph_prof, z, sizeof(z)));
-  }
-  return 0;
-}
-#endif
