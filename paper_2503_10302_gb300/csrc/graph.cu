@@ -10,8 +10,8 @@
 // neighbour words, then each replica looks up Eq. neuron's threshold and
 // compares it with its half of a Philox block that serves 8 replicas (16-bit
 // halves; the refine block settles ties exactly, as in the lattice kernels).
-// In DT-SQA the 32 bits are independent runs and a warp updates one vertex,
-// one run per lane.
+// In DT-SQA the 32 bits are 32 independent runs and a thread owns one
+// (slice, vertex) entry of the replicated network, in the same way.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -55,7 +55,6 @@ struct GShared {
 struct GCta {
   int n, C, T, Imax, tid, lane, warp;
   int ths;                       // row length of the [temperature][field] table
-  uint32_t sh;                   // 31 - lane
   int ushift;                    // (entry >> 8) - ubase >> ushift = neighbour index
   uint32_t ubase;                // byte offset of the spin words from the dynamic base
   const char *dynb;              // dynamic shared-memory base
@@ -581,7 +580,6 @@ __global__ void __launch_bounds__(kGThreads, 1) gapt_kernel(GAptArgs a, int init
   k.tag_init = a.tag_init;
   k.tag_sweep = a.tag_sweep;
   k.tag_refine = a.tag_refine;
-  k.sh = 31u - (uint32_t)k.lane;
   k.ushift = A == 1 ? 2 : (A == 2 ? 3 : 4);
   k.dynb = reinterpret_cast<const char *>(dyn);
   uint32_t *Th = dyn;

@@ -75,7 +75,7 @@ struct GSqaArgs {
   uint32_t run0, k0, k1;
   const int2 *vinfo;            // as above
   const uint32_t *adj;
-  const uint32_t *cls;          // [P n]: class-major list of k * n + p
+  const uint32_t *cls;          // [P n]: class-major list of (k << 20) | p
   const int *cls_off;           // [Cp + 1]
   const uint32_t *table;        // [S][3][2 Imax + 1]
   long long *E;                 // [R][P]
