@@ -185,23 +185,20 @@ __device__ void g_init(const GCta &k, GShared &sh) {
   __syncthreads();
 }
 
-// One sweep, colour class by colour class (Algorithm S2's p-computer loop).
-// A thread owns one half (16 temperatures) of a (vertex, label) word: the two
-// threads of a word sum the same field planes, and twice as many items even
-// out the work of uneven colour classes.  Replica b = 32 a + r takes half
-// b & 7 of P(j, s, (c << 16) | (b >> 3), (e << 8) | TAG), so one Philox call
-// serves 8 replicas of the vertex.
+// One sweep, colour class by colour class (Algorithm S2's p-computer loop):
+// every (vertex, label) of the class in parallel.  Replica b = 32 a + r
+// takes half b & 7 of P(j, s, (c << 16) | (b >> 3), (e << 8) | TAG), so one
+// Philox call serves 8 replicas of the vertex.
 template <int A, int NP, bool SM>
 __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
   const uint32_t c3m = (k.ent << 8) | k.tag_sweep;
   const uint32_t c3r = (k.ent << 8) | k.tag_refine;
   for (int c = 0; c < k.C; ++c) {
     const int o0 = sh.off[c], nc = sh.off[c + 1] - o0;
-    const int nitems = 64 * A * ((nc + 31) / 32);
+    const int nitems = 32 * A * ((nc + 31) / 32);
     for (int it = k.tid; it < nitems; it += kGThreads) {
-      const int hf = it & 1;   // replicas 16 hf .. 16 hf + 15
       int j, a;
-      item_of<A>(it >> 1, j, a);
+      item_of<A>(it, j, a);
       if (j >= nc) continue;
       const int p = o0 + j;
       const int2 vi = ld_vi<SM>(k.vinfo, p);
@@ -209,19 +206,16 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
 #pragma unroll
       for (int q = 0; q < NP; ++q) P[q] = 0u;
       const int W = vfield<A, NP, SM>(k.dynb, k.adj + vi.x, 0, vi_deg(vi), a, P);
-#pragma unroll
-      for (int q = 0; q < NP; ++q) P[q] >>= 16 * hf;
       const int base = vi_h(vi) - W + k.Imax;   // I + Imax = 2 C + base
-      const uint32_t *Th = k.Th + 16 * hf * k.ths;
-      const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(4 * a + 2 * hf);
+      const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(4 * a);
       uint32_t word = 0u, tie = 0u;
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
+      for (int g = 0; g < 4; ++g) {
         const uint4 x = philox((uint32_t)j, s, c2 + (uint32_t)g, c3m, k.k0, k.k1);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int r = 8 * g + i;   // temperature 16 hf + r
-          const uint32_t th = Th[r * k.ths + 2 * vget<NP>(P, r) + base];
+          const int r = 8 * g + i;
+          const uint32_t th = k.Th[r * k.ths + 2 * vget<NP>(P, r) + base];
           const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
           word |= (v < thi ? 1u : 0u) << r;
           tie |= (v == thi ? 1u : 0u) << r;
@@ -236,11 +230,11 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
         int C = 0;
 #pragma unroll
         for (int q = 0; q < NP; ++q) C |= (int)((P[q] >> r) & 1u) << q;
-        const uint32_t th = Th[r * k.ths + 2 * C + base];
+        const uint32_t th = k.Th[r * k.ths + 2 * C + base];
         const uint32_t u = (half_lo(x, r & 7) << 16) | half_lo(y, r & 7);
         word = (u < th) ? (word | (1u << r)) : (word & ~(1u << r));
       }
-      reinterpret_cast<uint16_t *>(k.S + p * A + a)[hf] = (uint16_t)word;
+      k.S[p * A + a] = word;
     }
     __syncthreads();
   }
