@@ -362,6 +362,54 @@ def graph_sqa_throughput(g: W.Graph, P: int = 64, R: int = 4864, sweeps: int = 1
             "min_energy": int(E.min())}
 
 
+def gsqa_embedded_scaling(dims=(15, 15, 12), n_inst: int = 4, Ps=(16, 64), tas=(100, 1000, 10000),
+                          runs: int = 256, T: float = 0.05, best_runs: int = 4,
+                          best_sweeps: int = 20000) -> Dict:
+    """DT-SQA on dimer embeddings of logical +-J lattices (4 colours,
+    couplings of strength 2), the embedded-instance setting of Fig. S15:
+    residual energy per p-bit of the best slice, rho = (E_min - E_best)/n,
+    against the annealing time t_a for P Trotter replicas, and the fitted
+    slope kappa_f of log rho against log t_a.  E_best: the best of APT+ICM
+    runs on the same graphs (sweep-to-swap ratio 10) and of every anneal."""
+    graphs = [W.dimer_embedding(dims, W.ea_couplings(dims, W.SEED_INSTANCES, i)) for i in range(n_inst)]
+    trip = [(g.rp, g.col, g.w) for g in graphs]
+    best = np.full(n_inst, np.iinfo(np.int64).max, np.int64)
+    t0 = time.perf_counter()
+    for r in range(best_runs):
+        ctx = pcomp.Context(0, 200 + r)
+        pcomp.pc_gapt_load(ctx.h, trip, [W.geometric_ladder(32, 0.2, 3.0)] * n_inst, 2, 0)
+        pcomp.pc_gapt_run(ctx.h, max(1, best_sweeps // 10), 10, True)
+        for i, g in enumerate(graphs):
+            best[i] = min(best[i], pcomp.pc_gapt_get_best(ctx.h, i, g.n)["E"])
+        ctx.close()
+    t_best = time.perf_counter() - t0
+    emin = {}
+    secs = {}
+    for P in Ps:
+        for ta in tas:
+            gamma = W.linear_gamma_schedule(ta)
+            ctx = pcomp.Context(0, 300 + P)
+            t0 = time.perf_counter()
+            emin[(P, ta)] = np.stack([pcomp.pc_gsqa_anneal(ctx.h, g.rp, g.col, g.w, P, T, gamma, runs).min(axis=1)
+                                      for g in graphs])   # [inst][run]
+            secs[(P, ta)] = time.perf_counter() - t0
+            ctx.close()
+            best = np.minimum(best, emin[(P, ta)].min(axis=1))
+    n = graphs[0].n
+    out = {"dims_logical": list(dims), "p_bits": n, "instances": n_inst, "runs": runs, "T": T,
+           "apt_best_seconds": t_best, "e_best_per_pbit": [float(b / n) for b in best], "by_P": {}}
+    for P in Ps:
+        rows = []
+        for ta in tas:
+            rho = (emin[(P, ta)] - best[:, None]) / n
+            rows.append({"t_a": ta, "rho_mean": float(rho.mean()), "rho_median": float(np.median(rho)),
+                         "hit_fraction_rho_0": float((rho == 0).mean()), "seconds": secs[(P, ta)]})
+        r = np.array([max(x["rho_mean"], 1e-12) for x in rows])
+        kappa = float(-np.polyfit(np.log(np.array(tas, float)), np.log(r), 1)[0])
+        out["by_P"][str(P)] = {"rows": rows, "kappa_f": kappa}
+    return out
+
+
 def graph_workloads(name: str) -> List[W.Graph]:
     if name == "dimer_64xL8":
         return [W.dimer_embedding((8, 8, 8), W.ea_couplings((8, 8, 8), W.SEED_INSTANCES, i)) for i in range(64)]
@@ -436,7 +484,8 @@ def graph_time_to_target(name: str = "dimer_64xL8", labels: int = 2, rho: float 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("what", choices=["throughput", "graph", "graph-ttt", "c2", "c3", "c4", "c5", "all"])
+    ap.add_argument("what", choices=["throughput", "graph", "graph-ttt", "gsqa-embedded", "c2", "c3", "c4", "c5",
+                                     "all"])
     ap.add_argument("--graph", choices=["dimer_64xL8", "lattice15x15x12_64", "lattice12_64", "random4096_152"])
     ap.add_argument("--graph-labels", type=int, choices=[2, 4], help="graph: one label count only")
     ap.add_argument("--no-sqa", action="store_true", help="graph: skip the DT-SQA lines")
@@ -489,6 +538,8 @@ def main():
                 out[f"gttt_{name}_A{labels}{'_adaptive' if args.adaptive else ''}"] = graph_time_to_target(
                     name, labels, best_runs=args.best_runs, best_sweeps=args.best_sweeps,
                     max_sweeps=args.max_sweeps, adaptive=args.adaptive)
+    if args.what == "gsqa-embedded":
+        out["gsqa_embedded"] = gsqa_embedded_scaling()
     if args.what in ("c2", "all"):
         out["c2"] = c2_residual_vs_R()
     if args.what in ("c3", "all"):
