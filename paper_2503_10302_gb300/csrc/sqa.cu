@@ -215,22 +215,43 @@ __device__ __forceinline__ void update_site(const pc::SqaArgs &a, const uint32_t
 #pragma unroll
     for (int b = 0; b < NB; ++b) C[b] += (uint32_t)k.eps[d] * Nw[b];
   }
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
+  // time neighbours k-1, k+1 of word b: the other colour's word and that
+  // word shifted by one nibble (funnel shift through the adjacent block);
+  // byte offsets 2 (2C + k + 13 m) + 80 (odd sweep): at most 156
+  const uint32_t kb = k.kb + boff;
+  auto offsets = [&](int b, uint32_t &Dlo, uint32_t &Dhi) {
     const int bp = (b + 1 == NB) ? 0 : b + 1, bm = (b == 0) ? NB - 1 : b - 1;
-    // time neighbours k-1, k+1: the other colour's word and that word
-    // shifted by one nibble (funnel shift through the adjacent block)
     const uint32_t lo = e ? O[b] : O[bm];
     const uint32_t hi = e ? O[bp] : O[b];
     const uint32_t M = O[b] + __funnelshift_r(lo, hi, e ? 4u : 28u);
-    // byte offsets 2 (2C + k + 13 m) + 80 (odd sweep): at most 156
-    const uint32_t kb = k.kb + boff;
-    const uint32_t Dlo = ((C[b] & 0x0F0F0F0Fu) << 2) + (M & 0x0F0F0F0Fu) * 26u + kb;
-    const uint32_t Dhi = (((C[b] >> 4) & 0x0F0F0F0Fu) << 2) + ((M >> 4) & 0x0F0F0F0Fu) * 26u + kb;
+    Dlo = ((C[b] & 0x0F0F0F0Fu) << 2) + (M & 0x0F0F0F0Fu) * 26u + kb;
+    Dhi = (((C[b] >> 4) & 0x0F0F0F0Fu) << 2) + ((M >> 4) & 0x0F0F0F0Fu) * 26u + kb;
+  };
+  // up to 4 words, the decisions form one branch-free block and ties
+  // (probability 2^-16 per spin) are settled after it; with more words the
+  // register budget settles each word's ties at once
+  uint32_t tmask = 0u;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    uint32_t Dlo, Dhi;
+    offsets(b, Dlo, Dhi);
     const uint4 x = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_SWEEP, a.k0, a.k1);
     bool tie = false;
     w[b] = decide_word(x, Dlo, Dhi, tie);
-    if (tie) {
+    if constexpr (NB <= 4) {
+      tmask |= tie ? (1u << b) : 0u;
+    } else if (tie) {
+      const uint4 y = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_REFINE, a.k0, a.k1);
+      w[b] = settle_ties(w[b], x, y, Dlo, Dhi);
+    }
+  }
+  if (NB <= 4 && tmask) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (!((tmask >> b) & 1u)) continue;
+      uint32_t Dlo, Dhi;
+      offsets(b, Dlo, Dhi);
+      const uint4 x = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_SWEEP, a.k0, a.k1);
       const uint4 y = philox((uint32_t)s, sw, c2 | (uint32_t)b, (ent << 8) | TAG_SQA_REFINE, a.k0, a.k1);
       w[b] = settle_ties(w[b], x, y, Dlo, Dhi);
     }
