@@ -134,7 +134,7 @@ __shared__ __align__(16) uint32_t s_Tf[2][pc::kSqaTab];
 // half of the threshold; equality is a tie.
 __device__ __forceinline__ uint32_t decide_word(const uint4 &x, uint32_t Dlo, uint32_t Dhi, bool &tie) {
   uint32_t w = 0;
-  int tp = 1;   // product of the differences: 0 when some half equals its threshold
+  uint32_t tp = 1u;   // product of the differences (mod 2^32): 0 when some half equals its threshold
   const char *base = reinterpret_cast<const char *>(&s_Th[0][0]);
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -144,7 +144,7 @@ __device__ __forceinline__ uint32_t decide_word(const uint4 &x, uint32_t Dlo, ui
     const uint32_t v = (i & 1) ? (xw >> 16) : (xw & 0xFFFFu);
     const int d = (int)v - (int)th;   // both below 2^16: negative iff v < th
     w |= ((uint32_t)d >> 31) << (4 * i);
-    tp *= d;
+    tp *= (uint32_t)d;
   }
   // a zero product flags a tie; a product that merely wraps to 0 only sends
   // the word through settle_ties, which rechecks every half exactly
