@@ -100,16 +100,22 @@ __device__ __forceinline__ int lin_of(const Geo &g, int c, int j) {
 // 16, entry I + 6 for I = -6..6).  SCALE 1: C holds I + 6 per nibble;
 // SCALE 2: C holds the satisfied count of a site with all six bonds, whose
 // entry is 2C.
+// thrh holds the thresholds' top halves shifted down (below 2^16), so the
+// sign of main half - threshold half is the decision; a zero product of the
+// differences (mod 2^32) flags a possible tie, which refine8_grp settles
+// exactly (a product that only wraps to 0 costs a needless refine).
 template <int SCALE>
 __device__ __forceinline__ uint32_t decide8_grp(const uint4 &x, uint32_t C, const uint32_t *thrh,
                                                 bool &tie) {
-  uint32_t w = 0;
+  uint32_t w = 0, tp = 1u;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const uint32_t v = half_hi(x, i), th = thrh[16 * i + SCALE * ((C >> (4 * i)) & 0xFu)];
-    w |= (v < th) ? (1u << (4 * i)) : 0u;
-    tie |= (v == th);
+    const uint32_t v = half_lo(x, i), th = thrh[16 * i + SCALE * ((C >> (4 * i)) & 0xFu)];
+    const int d = (int)v - (int)th;
+    w |= ((uint32_t)d >> 31) << (4 * i);
+    tp *= (uint32_t)d;
   }
+  tie |= (tp == 0u);
   return w;
 }
 
@@ -131,7 +137,7 @@ __device__ __noinline__ uint32_t refine8_grp(uint32_t w, uint4 x, uint4 y, uint3
 struct Shared {
   uint32_t *S;       // [Gc][2][H]
   uint32_t *thr;     // [Gc*8][16] p-bit thresholds, entry I + 6
-  uint32_t *thrh;    // [Gc*8][16] their high halves
+  uint32_t *thrh;    // [Gc*8][16] their high halves, shifted down
   int32_t *temp_of;  // [Gc*8]
   int32_t *buf_of;   // [Gc*8] (unused by the fixed-slot APT mode)
   int32_t *E;        // [Gc*8]
@@ -1008,7 +1014,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     for (int e = 0; e < 16; ++e) {
       const uint32_t th = a.pbit[P.pbit_off + 16 * tb + e];
       sh.thr[16 * b + e] = th;
-      sh.thrh[16 * b + e] = th & 0xFFFF0000u;
+      sh.thrh[16 * b + e] = th >> 16;
     }
   }
   for (int i = threadIdx.x; i < 128; i += blockDim.x) {
