@@ -208,7 +208,10 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
       const int W = vfield<A, NP, SM>(k.dynb, k.adj + vi.x, 0, vi_deg(vi), a, P);
       const int base = vi_h(vi) - W + k.Imax;   // I + Imax = 2 C + base
       const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(4 * a);
-      uint32_t word = 0u, tie = 0u;
+      // the sign of (main half - threshold top half) decides; a zero product
+      // of the differences (mod 2^32) flags a possible tie (probability about
+      // 32 x 2^-16 per word), settled exactly below
+      uint32_t word = 0u, tp = 1u;
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
         const uint4 x = philox((uint32_t)j, s, c2 + (uint32_t)g, c3m, k.k0, k.k1);
@@ -216,23 +219,33 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
         for (int i = 0; i < 8; ++i) {
           const int r = 8 * g + i;
           const uint32_t th = k.Th[r * k.ths + 2 * vget<NP>(P, r) + base];
-          const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
-          word |= (v < thi ? 1u : 0u) << r;
-          tie |= (v == thi ? 1u : 0u) << r;
+          const int d = (int)half_lo(x, i) - (int)(th >> 16);
+          word |= ((uint32_t)d >> 31) << r;
+          tp *= (uint32_t)d;
         }
       }
-      while (tie) {   // probability 2^-16 per replica: settle with the refine half
-        const int r = __ffs((int)tie) - 1;
-        tie &= tie - 1u;
-        const uint32_t cg = c2 + (uint32_t)(r >> 3);
-        const uint4 x = philox((uint32_t)j, s, cg, c3m, k.k0, k.k1);
-        const uint4 y = philox((uint32_t)j, s, cg, c3r, k.k0, k.k1);
-        int C = 0;
-#pragma unroll
-        for (int q = 0; q < NP; ++q) C |= (int)((P[q] >> r) & 1u) << q;
-        const uint32_t th = k.Th[r * k.ths + 2 * C + base];
-        const uint32_t u = (half_lo(x, r & 7) << 16) | half_lo(y, r & 7);
-        word = (u < th) ? (word | (1u << r)) : (word & ~(1u << r));
+      if (tp == 0u) {
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+          const uint4 x = philox((uint32_t)j, s, c2 + (uint32_t)g, c3m, k.k0, k.k1);
+          uint4 y = make_uint4(0u, 0u, 0u, 0u);
+          bool have_y = false;
+#pragma unroll 1
+          for (int i = 0; i < 8; ++i) {
+            const int r = 8 * g + i;
+            int C = 0;
+            for (int q = 0; q < NP; ++q) C |= (int)((P[q] >> r) & 1u) << q;
+            const uint32_t th = k.Th[r * k.ths + 2 * C + base];
+            const uint32_t v = half_lo(x, i);
+            if (v != (th >> 16)) continue;
+            if (!have_y) {
+              y = philox((uint32_t)j, s, c2 + (uint32_t)g, c3r, k.k0, k.k1);
+              have_y = true;
+            }
+            const uint32_t u = (v << 16) | half_lo(y, i);
+            word = (u < th) ? (word | (1u << r)) : (word & ~(1u << r));
+          }
+        }
       }
       k.S[p * A + a] = word;
     }
@@ -789,7 +802,8 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
         const int base = vi_h(vi) - Ws + a.Imax;   // in-slice I + Imax = 2 C + base
         const uint32_t wd = k > kb ? Wk[p - n] : Wl[p];
         const uint32_t wu = k + 1 < ke ? Wk[p + n] : Wr[p];
-        uint32_t word = 0u, tie = 0u;
+        // decisions and the exact settlement of possible ties as in g_sweep
+        uint32_t word = 0u, tp = 1u;
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, ((g0 + g) << 8) | TAG_GS_SWEEP, a.k0, a.k1);
@@ -798,24 +812,35 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
             const int r = 8 * g + i;
             const int idx = (int)(((wd >> r) & 1u) + ((wu >> r) & 1u)) * nt + 2 * vget<NP>(Pl, r) + base;
             const uint32_t th = REP ? T[32 * idx + lane] : T[idx];
-            const uint32_t v = half_hi(x, i), thi = th & 0xFFFF0000u;
-            word |= (v < thi ? 1u : 0u) << r;
-            tie |= (v == thi ? 1u : 0u) << r;
+            const int d = (int)half_lo(x, i) - (int)(th >> 16);
+            word |= ((uint32_t)d >> 31) << r;
+            tp *= (uint32_t)d;
           }
         }
-        while (tie) {   // probability 2^-16 per run: settle with the refine half
-          const int r = __ffs((int)tie) - 1;
-          tie &= tie - 1u;
-          const uint32_t gq = (g0 + (uint32_t)(r >> 3)) << 8;
-          const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, gq | TAG_GS_SWEEP, a.k0, a.k1);
-          const uint4 y = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, gq | TAG_GS_REFINE, a.k0, a.k1);
-          int C = 0;
-#pragma unroll
-          for (int q = 0; q < NP; ++q) C |= (int)((Pl[q] >> r) & 1u) << q;
-          const int idx = (int)(((wd >> r) & 1u) + ((wu >> r) & 1u)) * nt + 2 * C + base;
-          const uint32_t th = REP ? T[32 * idx + lane] : T[idx];
-          const uint32_t u = (half_lo(x, r & 7) << 16) | half_lo(y, r & 7);
-          word = (u < th) ? (word | (1u << r)) : (word & ~(1u << r));
+        if (tp == 0u) {
+#pragma unroll 1
+          for (int g = 0; g < 4; ++g) {
+            const uint32_t gq = (g0 + (uint32_t)g) << 8;
+            const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, gq | TAG_GS_SWEEP, a.k0, a.k1);
+            uint4 y = make_uint4(0u, 0u, 0u, 0u);
+            bool have_y = false;
+#pragma unroll 1
+            for (int i = 0; i < 8; ++i) {
+              const int r = 8 * g + i;
+              int C = 0;
+              for (int q = 0; q < NP; ++q) C |= (int)((Pl[q] >> r) & 1u) << q;
+              const int idx = (int)(((wd >> r) & 1u) + ((wu >> r) & 1u)) * nt + 2 * C + base;
+              const uint32_t th = REP ? T[32 * idx + lane] : T[idx];
+              const uint32_t v = half_lo(x, i);
+              if (v != (th >> 16)) continue;
+              if (!have_y) {
+                y = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, gq | TAG_GS_REFINE, a.k0, a.k1);
+                have_y = true;
+              }
+              const uint32_t u = (v << 16) | half_lo(y, i);
+              word = (u < th) ? (word | (1u << r)) : (word & ~(1u << r));
+            }
+          }
         }
         W[(size_t)(k - kb) * n + p] = word;
       }
