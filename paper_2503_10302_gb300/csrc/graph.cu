@@ -208,13 +208,15 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
       const int W = vfield<A, NP, SM>(k.dynb, k.adj + vi.x, 0, vi_deg(vi), a, P);
       const int base = vi_h(vi) - W + k.Imax;   // I + Imax = 2 C + base
       const uint32_t c2 = ((uint32_t)c << 16) | (uint32_t)(4 * a);
-      // the sign of (main half - threshold top half) decides; a zero product
-      // of the differences (mod 2^32) flags a possible tie (probability about
-      // 32 x 2^-16 per word), settled exactly below
-      uint32_t word = 0u, tp = 1u;
+      // the sign of (main half - threshold top half) decides; per group of 8
+      // replicas a zero product of the differences (mod 2^32) flags a
+      // possible tie, settled exactly below (8 differences rarely wrap the
+      // product to 0; a wrap only costs a needless check)
+      uint32_t word = 0u, gmask = 0u;
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
         const uint4 x = philox((uint32_t)j, s, c2 + (uint32_t)g, c3m, k.k0, k.k1);
+        uint32_t tp = 1u;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int r = 8 * g + i;
@@ -223,10 +225,12 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
           word |= ((uint32_t)d >> 31) << r;
           tp *= (uint32_t)d;
         }
+        gmask |= (tp == 0u ? 1u : 0u) << g;
       }
-      if (tp == 0u) {
+      if (gmask) {
 #pragma unroll 1
         for (int g = 0; g < 4; ++g) {
+          if (!((gmask >> g) & 1u)) continue;
           const uint4 x = philox((uint32_t)j, s, c2 + (uint32_t)g, c3m, k.k0, k.k1);
           uint4 y = make_uint4(0u, 0u, 0u, 0u);
           bool have_y = false;
@@ -803,10 +807,11 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
         const uint32_t wd = k > kb ? Wk[p - n] : Wl[p];
         const uint32_t wu = k + 1 < ke ? Wk[p + n] : Wr[p];
         // decisions and the exact settlement of possible ties as in g_sweep
-        uint32_t word = 0u, tp = 1u;
+        uint32_t word = 0u, gmask = 0u;
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
           const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, ((g0 + g) << 8) | TAG_GS_SWEEP, a.k0, a.k1);
+          uint32_t tp = 1u;
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int r = 8 * g + i;
@@ -816,10 +821,12 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
             word |= ((uint32_t)d >> 31) << r;
             tp *= (uint32_t)d;
           }
+          gmask |= (tp == 0u ? 1u : 0u) << g;
         }
-        if (tp == 0u) {
+        if (gmask) {
 #pragma unroll 1
           for (int g = 0; g < 4; ++g) {
+            if (!((gmask >> g) & 1u)) continue;
             const uint32_t gq = (g0 + (uint32_t)g) << 8;
             const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, gq | TAG_GS_SWEEP, a.k0, a.k1);
             uint4 y = make_uint4(0u, 0u, 0u, 0u);
