@@ -100,23 +100,24 @@ __device__ __forceinline__ int lin_of(const Geo &g, int c, int j) {
 // 16, entry I + 6 for I = -6..6).  SCALE 1: C holds I + 6 per nibble;
 // SCALE 2: C holds the satisfied count of a site with all six bonds, whose
 // entry is 2C.
-// thrh holds the thresholds' top halves shifted down (below 2^16), so the
-// sign of main half - threshold half is the decision; a zero product of the
-// differences (mod 2^32) flags a possible tie, which refine8_grp settles
-// exactly (a product that only wraps to 0 costs a needless refine).
+// thrh holds the thresholds' top halves t shifted down (below 2^16): the
+// sign of d = v - t for the main half v is the decision, and the top 4 bits
+// of each d are shifted into w so that bit 3 of nibble i carries half i's
+// sign.  A zero product of the differences (mod 2^32) flags a possible tie,
+// which refine8_grp settles exactly (a product that only wraps to 0 costs a
+// needless refine).
 template <int SCALE>
 __device__ __forceinline__ uint32_t decide8_grp(const uint4 &x, uint32_t C, const uint32_t *thrh,
                                                 bool &tie) {
   uint32_t w = 0, tp = 1u;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const uint32_t v = half_lo(x, i), th = thrh[16 * i + SCALE * ((C >> (4 * i)) & 0xFu)];
-    const int d = (int)v - (int)th;
-    w |= ((uint32_t)d >> 31) << (4 * i);
-    tp *= (uint32_t)d;
+  for (int i = 7; i >= 0; --i) {
+    const uint32_t d = half_lo(x, i) - thrh[16 * i + SCALE * ((C >> (4 * i)) & 0xFu)];
+    w = __funnelshift_l(d, w, 4);
+    tp *= d;
   }
   tie |= (tp == 0u);
-  return w;
+  return (w >> 3) & 0x11111111u;
 }
 
 template <int SCALE>

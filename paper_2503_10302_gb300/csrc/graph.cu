@@ -214,16 +214,16 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
       // product to 0; a wrap only costs a needless check)
       uint32_t word = 0u, gmask = 0u;
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 3; g >= 0; --g) {
         const uint4 x = philox((uint32_t)j, s, c2 + (uint32_t)g, c3m, k.k0, k.k1);
         uint32_t tp = 1u;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 7; i >= 0; --i) {
           const int r = 8 * g + i;
           const uint32_t th = k.Th[r * k.ths + 2 * vget<NP>(P, r) + base];
-          const int d = (int)half_lo(x, i) - (int)(th >> 16);
-          word |= ((uint32_t)d >> 31) << r;
-          tp *= (uint32_t)d;
+          const uint32_t d = half_lo(x, i) - (th >> 16);
+          word = __funnelshift_l(d, word, 1);   // shift in the sign of d as bit 0
+          tp *= d;
         }
         gmask |= (tp == 0u ? 1u : 0u) << g;
       }
@@ -809,17 +809,17 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
         // decisions and the exact settlement of possible ties as in g_sweep
         uint32_t word = 0u, gmask = 0u;
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
+        for (int g = 3; g >= 0; --g) {
           const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, ((g0 + g) << 8) | TAG_GS_SWEEP, a.k0, a.k1);
           uint32_t tp = 1u;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
+          for (int i = 7; i >= 0; --i) {
             const int r = 8 * g + i;
             const int idx = (int)(((wd >> r) & 1u) + ((wu >> r) & 1u)) * nt + 2 * vget<NP>(Pl, r) + base;
             const uint32_t th = REP ? T[32 * idx + lane] : T[idx];
-            const int d = (int)half_lo(x, i) - (int)(th >> 16);
-            word |= ((uint32_t)d >> 31) << r;
-            tp *= (uint32_t)d;
+            const uint32_t d = half_lo(x, i) - (th >> 16);
+            word = __funnelshift_l(d, word, 1);   // shift in the sign of d as bit 0
+            tp *= d;
           }
           gmask |= (tp == 0u ? 1u : 0u) << g;
         }

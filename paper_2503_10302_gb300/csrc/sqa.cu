@@ -123,33 +123,36 @@ __device__ __forceinline__ SiteK site_consts(const pc::SqaArgs &a, int s, const 
 
 // Threshold tables in static shared memory, so that a byte of a packed
 // index word is directly an address offset: [2 sweeps][40 entries], entry
-// I + 6 + 13 m for in-slice field I = -6..6 and time count m = 0..2; top
-// halves (Th, 16-bit, 2-byte steps) and full values (Tf).
+// I + 6 + 13 m for in-slice field I = -6..6 and time count m = 0..2;
+// top halves (Th, 16-bit, 2-byte steps) and full values (Tf).
 __shared__ __align__(16) uint16_t s_Th[2][pc::kSqaTab];
 __shared__ __align__(16) uint32_t s_Tf[2][pc::kSqaTab];
 
 // Eq. neuron for the 8 nibbles of one word.  Byte k of Dlo / Dhi is the
 // byte offset of the threshold of nibble 2k / 2k+1 in s_Th (index * 2 plus
-// 80 for the odd sweep's buffer).  The main half decides against the top
-// half of the threshold; equality is a tie.
+// 80 for the odd sweep's buffer).  The main half v decides against the top
+// half t of the threshold: d = v - t is negative iff v < t, and d = 0 is a
+// tie, which the main half cannot decide.
 __device__ __forceinline__ uint32_t decide_word(const uint4 &x, uint32_t Dlo, uint32_t Dhi, bool &tie) {
   uint32_t w = 0;
   uint32_t tp = 1u;   // product of the differences (mod 2^32): 0 when some half equals its threshold
   const char *base = reinterpret_cast<const char *>(&s_Th[0][0]);
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 7; i >= 0; --i) {
     const uint32_t off = __byte_perm((i & 1) ? Dhi : Dlo, 0u, 0x4440u + (uint32_t)(i >> 1));
     const uint32_t th = *reinterpret_cast<const uint16_t *>(base + off);
     const uint32_t xw = word_of(x, i >> 1);
     const uint32_t v = (i & 1) ? (xw >> 16) : (xw & 0xFFFFu);
-    const int d = (int)v - (int)th;   // both below 2^16: negative iff v < th
-    w |= ((uint32_t)d >> 31) << (4 * i);
-    tp *= (uint32_t)d;
+    const uint32_t d = v - th;   // both below 2^16: bit 31 set iff v < th
+    // the top 4 bits of d enter w as its new nibble 0, so after the loop
+    // bit 3 of nibble i is the sign of half i's difference
+    w = __funnelshift_l(d, w, 4);
+    tp *= d;
   }
   // a zero product flags a tie; a product that merely wraps to 0 only sends
   // the word through settle_ties, which rechecks every half exactly
   tie |= (tp == 0);
-  return w;
+  return (w >> 3) & 0x11111111u;
 }
 
 __device__ __noinline__ uint32_t settle_ties(uint32_t w, uint4 x, uint4 y, uint32_t Dlo, uint32_t Dhi) {
