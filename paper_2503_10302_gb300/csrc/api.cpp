@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ctx.h"
@@ -236,7 +237,11 @@ int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, con
     return fail(PC_EINVAL, "run does not fit in shared memory");
   PC_CUDA_TRY(cudaSetDevice(c->device));
   SqaState &q = c->sqa;
-  q.release();
+  // device buffers are kept from the previous setup when they are large
+  // enough; the copies below are ordered after any anneal still queued on
+  // the context's stream
+  q.ready = false;
+  q.last_err = nullptr;
   q.lat = lat;
   q.P = P;
   q.T = T;
@@ -244,18 +249,34 @@ int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, con
   q.jq.resize((size_t)n_sweeps);
   q.table.assign((size_t)(n_sweeps > 0 ? n_sweeps : 1) * kSqaTab, 0u);
   const double beta_eff = 1.0 / ((double)P * T);
-  for (int s = 0; s < n_sweeps; ++s) {
-    const int32_t jq = pc_jperp_q(gamma[s], P, T);
-    q.jq[(size_t)s] = jq;
-    // every in-slice field I = -6..6 (odd at open faces) and time count m
-    for (int m = 0; m < 3; ++m)
-      for (int e = 0; e < 13; ++e)
-        q.table[(size_t)s * kSqaTab + e + 13 * m] = sqa_threshold(beta_eff, e - 6, jq, 2 * m - 2);
+  // every sweep's row is independent: long schedules are built by several
+  // host threads (the rows do not depend on how they are split)
+  auto rows = [&](int s0, int s1) {
+    for (int s = s0; s < s1; ++s) {
+      const int32_t jq = pc_jperp_q(gamma[s], P, T);
+      q.jq[(size_t)s] = jq;
+      // every in-slice field I = -6..6 (odd at open faces) and time count m
+      for (int m = 0; m < 3; ++m)
+        for (int e = 0; e < 13; ++e)
+          q.table[(size_t)s * kSqaTab + e + 13 * m] = sqa_threshold(beta_eff, e - 6, jq, 2 * m - 2);
+    }
+  };
+  int nth = (int)std::thread::hardware_concurrency();
+  if (nth > 16) nth = 16;
+  if (nth > n_sweeps / 512) nth = n_sweeps / 512;
+  if (nth <= 1) {
+    rows(0, n_sweeps);
+  } else {
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nth; ++i)
+      pool.emplace_back(rows, (int)((int64_t)n_sweeps * i / nth), (int)((int64_t)n_sweeps * (i + 1) / nth));
+    rows(0, n_sweeps / nth);
+    for (auto &t : pool) t.join();
   }
   int nreal = 0;
   std::vector<uint16_t> jn = pack_jn16(lat, per, present, J, &q.nbonds, &nreal);
-  if ((rc = q.d_jneg.alloc(jn.size()))) return rc;
-  if ((rc = q.d_table.alloc(q.table.size()))) return rc;
+  if (q.d_jneg.n < jn.size() && (rc = q.d_jneg.alloc(jn.size()))) return rc;
+  if (q.d_table.n < q.table.size() && (rc = q.d_table.alloc(q.table.size()))) return rc;
   // stage through pinned memory: one copy of each array
   const size_t tb = q.table.size() * 4, jb = (jn.size() * 2 + 15) / 16 * 16;
   if ((rc = q.stage.reserve(jb + tb))) return rc;
