@@ -131,6 +131,31 @@ __device__ __forceinline__ int vget(const uint32_t (&P)[NP], int r) {
   return C;
 }
 
+// Bits 8g .. 8g+3 of w as the bytes of lo (bit 8g + i in byte i) and bits
+// 8g+4 .. 8g+7 as the bytes of hi: the four bits of a nibble times
+// 1 + 2^7 + 2^14 + 2^21 land, without carries, on bits 0, 8, 16 and 24.
+__device__ __forceinline__ void spread_byte(uint32_t w, int g, uint32_t &lo, uint32_t &hi) {
+  const uint32_t x = __byte_perm(w, 0u, 0x4440u + (uint32_t)g);
+  lo = ((x & 0xFu) * 0x00204081u) & 0x01010101u;
+  hi = ((x >> 4) * 0x00204081u) & 0x01010101u;
+}
+
+// Counts of replicas 8g .. 8g+7 from the NP planes, doubled, as bytes:
+// C2lo holds 2 C of replicas 8g .. 8g+3, C2hi of 8g+4 .. 8g+7 (2 C is at
+// most 2 (2^NP - 1) <= 254, so no byte carries into the next).
+template <int NP>
+__device__ __forceinline__ void counts2_bytes(const uint32_t (&P)[NP], int g, uint32_t &C2lo, uint32_t &C2hi) {
+  C2lo = 0u;
+  C2hi = 0u;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    uint32_t l, h;
+    spread_byte(P[q], g, l, h);
+    C2lo += l << (q + 1);
+    C2hi += h << (q + 1);
+  }
+}
+
 // Adds the neighbours [e0, e1) of one vertex, label a, into the planes;
 // returns their sum of |w|.
 template <int A, int NP, bool SM>
@@ -217,10 +242,17 @@ __device__ void g_sweep(const GCta &k, GShared &sh, uint32_t s) {
       for (int g = 3; g >= 0; --g) {
         const uint4 x = philox((uint32_t)j, s, c2 + (uint32_t)g, c3m, k.k0, k.k1);
         uint32_t tp = 1u;
+        // the group's table columns 2 C + base = I + Imax (at most
+        // 2 Imax <= 254) as bytes, 4 replicas per word
+        uint32_t Jlo, Jhi;
+        counts2_bytes<NP>(P, g, Jlo, Jhi);
+        Jlo += 0x01010101u * (uint32_t)base;
+        Jhi += 0x01010101u * (uint32_t)base;
 #pragma unroll
         for (int i = 7; i >= 0; --i) {
           const int r = 8 * g + i;
-          const uint32_t th = k.Th[r * k.ths + 2 * vget<NP>(P, r) + base];
+          const int col = (int)__byte_perm(i < 4 ? Jlo : Jhi, 0u, 0x4440u + (uint32_t)(i & 3));
+          const uint32_t th = k.Th[r * k.ths + col];
           const uint32_t d = half_lo(x, i) - (th >> 16);
           word = __funnelshift_l(d, word, 1);   // shift in the sign of d as bit 0
           tp *= d;
@@ -812,10 +844,24 @@ __global__ void __launch_bounds__(kGThreads, 1) gsqa_kernel(GSqaArgs a) {
         for (int g = 3; g >= 0; --g) {
           const uint4 x = philox((uint32_t)j, (uint32_t)s, (uint32_t)c, ((g0 + g) << 8) | TAG_GS_SWEEP, a.k0, a.k1);
           uint32_t tp = 1u;
+          // three planes (Imax <= 7): the group's table indices
+          // m nt + 2 C + base (below 2 nt + 2 Imax + 1 <= 59) as bytes,
+          // 4 runs per word, m the time-neighbour count
+          uint32_t Jlo = 0u, Jhi = 0u;
+          if constexpr (NP == 3) {
+            uint32_t dl, dh, ul, uh;
+            counts2_bytes<NP>(Pl, g, Jlo, Jhi);
+            spread_byte(wd, g, dl, dh);
+            spread_byte(wu, g, ul, uh);
+            Jlo += (dl + ul) * (uint32_t)nt + 0x01010101u * (uint32_t)base;
+            Jhi += (dh + uh) * (uint32_t)nt + 0x01010101u * (uint32_t)base;
+          }
 #pragma unroll
           for (int i = 7; i >= 0; --i) {
             const int r = 8 * g + i;
-            const int idx = (int)(((wd >> r) & 1u) + ((wu >> r) & 1u)) * nt + 2 * vget<NP>(Pl, r) + base;
+            int idx;
+            if constexpr (NP == 3) idx = (int)__byte_perm(i < 4 ? Jlo : Jhi, 0u, 0x4440u + (uint32_t)(i & 3));
+            else idx = (int)(((wd >> r) & 1u) + ((wu >> r) & 1u)) * nt + 2 * vget<NP>(Pl, r) + base;
             const uint32_t th = REP ? T[32 * idx + lane] : T[idx];
             const uint32_t d = half_lo(x, i) - (th >> 16);
             word = __funnelshift_l(d, word, 1);   // shift in the sign of d as bit 0

@@ -37,6 +37,36 @@ def test_sqa_tables_equal_oracle(pc, orc):
     ctx.close()
 
 
+def _check_all_rows(pc, orc, ctx, wl):
+    beta_eff = 1.0 / (wl.P * wl.T)
+    for s in range(len(wl.gamma)):
+        tab, jq = pc.pc_sqa_get_table(ctx.h, s)
+        assert jq == orc.jperp_q(wl.gamma[s], wl.P, wl.T), s
+        for m, n in enumerate((-2, 0, 2)):
+            for c in range(7):
+                assert tab[m, c] == orc.sqa_threshold(beta_eff, 2 * c - 6, jq, n), (s, m, c)
+
+
+def test_sqa_long_schedules_threaded_rows_and_reused_buffers(pc, orc):
+    """Long schedules build their table rows on several host threads, in
+    splits that do not divide the schedule evenly; later setups on the same
+    context reuse (or grow) the device buffers.  Every row equals the
+    oracle's, and an anneal after a shrinking setup stays bit-exact."""
+    ctx = pc.Context(0, 21)
+    for L, P, S in ((4, 64, 1531), (6, 32, 4099), (4, 16, 1031)):
+        wl = W.sqa_workload(L=L, P=P, R=1, n_sweeps=S, index=S)
+        pc.pc_sqa_setup(ctx.h, wl.dims, wl.J, wl.P, wl.T, wl.gamma)
+        _check_all_rows(pc, orc, ctx, wl)
+    dims, P, R, S, seed = (4, 4, 4), 16, 3, 20, 21
+    J = W.ea_couplings(dims, W.SEED_INSTANCES, seed)
+    gamma = W.linear_gamma_schedule(S)
+    E_ref = orc.sqa_anneal(dims, J, P, 0.05, gamma, R, run0=0, seed=seed)
+    pc.pc_sqa_setup(ctx.h, dims, J, P, 0.05, gamma)
+    E = pc.pc_sqa_run(ctx.h, R, 0, P, int(np.prod(dims)))
+    ctx.close()
+    assert np.array_equal(E, E_ref)
+
+
 CASES = [
     # dims, P, R, sweeps, seed
     ((4, 4, 4), 16, 6, 40, 0),
