@@ -100,19 +100,26 @@ __device__ __forceinline__ int lin_of(const Geo &g, int c, int j) {
 // 16, entry I + 6 for I = -6..6).  SCALE 1: C holds I + 6 per nibble;
 // SCALE 2: C holds the satisfied count of a site with all six bonds, whose
 // entry is 2C.
-// thrh holds the thresholds' top halves t shifted down (below 2^16): the
-// sign of d = v - t for the main half v is the decision, and the top 4 bits
-// of each d are shifted into w so that bit 3 of nibble i carries half i's
-// sign.  A zero product of the differences (mod 2^32) flags a possible tie,
-// which refine8_grp settles exactly (a product that only wraps to 0 costs a
-// needless refine).
+// thrh holds the thresholds' top halves t as 16-bit entries in the same
+// [buffer][16] order, so the entry of nibble i sits at byte offset
+// 32 i + 2 SCALE c_i <= 248: the offsets of 4 nibbles are formed in one word
+// and each is taken out with one byte extract.  The sign of d = v - t for
+// the main half v is the decision, and the top 4 bits of each d are shifted
+// into w so that bit 3 of nibble i carries half i's sign.  A zero product
+// of the differences (mod 2^32) flags a possible tie, which refine8_grp
+// settles exactly (a product that only wraps to 0 costs a needless refine).
 template <int SCALE>
-__device__ __forceinline__ uint32_t decide8_grp(const uint4 &x, uint32_t C, const uint32_t *thrh,
+__device__ __forceinline__ uint32_t decide8_grp(const uint4 &x, uint32_t C, const uint16_t *thrh,
                                                 bool &tie) {
+  const char *base = reinterpret_cast<const char *>(thrh);
+  // byte k of Dlo: offset of nibble 2k (64 k + 2 SCALE c); of Dhi: nibble 2k+1
+  const uint32_t Dlo = (C & 0x0F0F0F0Fu) * (2u * SCALE) + 0xC0804000u;
+  const uint32_t Dhi = ((C >> 4) & 0x0F0F0F0Fu) * (2u * SCALE) + 0xE0A06020u;
   uint32_t w = 0, tp = 1u;
 #pragma unroll
   for (int i = 7; i >= 0; --i) {
-    const uint32_t d = half_lo(x, i) - thrh[16 * i + SCALE * ((C >> (4 * i)) & 0xFu)];
+    const uint32_t off = __byte_perm((i & 1) ? Dhi : Dlo, 0u, 0x4440u + (uint32_t)(i >> 1));
+    const uint32_t d = half_lo(x, i) - *reinterpret_cast<const uint16_t *>(base + off);
     w = __funnelshift_l(d, w, 4);
     tp *= d;
   }
@@ -138,7 +145,7 @@ __device__ __noinline__ uint32_t refine8_grp(uint32_t w, uint4 x, uint4 y, uint3
 struct Shared {
   uint32_t *S;       // [Gc][2][H]
   uint32_t *thr;     // [Gc*8][16] p-bit thresholds, entry I + 6
-  uint32_t *thrh;    // [Gc*8][16] their high halves, shifted down
+  uint16_t *thrh;    // [Gc*8][16] their high halves (16-bit)
   int32_t *temp_of;  // [Gc*8]
   int32_t *buf_of;   // [Gc*8] (unused by the fixed-slot APT mode)
   int32_t *E;        // [Gc*8]
@@ -971,7 +978,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   uint32_t *cur = smem;
   sh.S = cur;            cur += (size_t)Gcarve * N;
   sh.thr = cur;          cur += 16 * G8;
-  sh.thrh = cur;         cur += 16 * G8;
+  sh.thrh = reinterpret_cast<uint16_t *>(cur);   cur += 16 * G8;   // uses half of its carve
   sh.temp_of = reinterpret_cast<int32_t *>(cur);  cur += G8;
   sh.buf_of = reinterpret_cast<int32_t *>(cur);   cur += G8;
   sh.E = reinterpret_cast<int32_t *>(cur);        cur += G8;
@@ -1015,7 +1022,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     for (int e = 0; e < 16; ++e) {
       const uint32_t th = a.pbit[P.pbit_off + 16 * tb + e];
       sh.thr[16 * b + e] = th;
-      sh.thrh[16 * b + e] = th >> 16;
+      sh.thrh[16 * b + e] = (uint16_t)(th >> 16);
     }
   }
   for (int i = threadIdx.x; i < 128; i += blockDim.x) {
