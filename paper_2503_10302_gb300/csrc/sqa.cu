@@ -444,7 +444,6 @@ __global__ void __launch_bounds__(PC_SQA_TPB, PC_SQA_MINB) sqa_kernel(const pc::
   for (int i = tid; i < N; i += nt) jn[i] = a.jneg[i];
   __syncthreads();
   // one site per thread (N <= blockDim): its constants stay in registers
-  // one site per thread (N <= blockDim): its constants stay in registers
   const bool hoist = PC_SQA_HOIST && N <= nt;
   SiteK kh;
   if (hoist && tid < N) kh = site_consts(a, tid, jn);
