@@ -267,10 +267,20 @@ int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, con
   if (nth <= 1) {
     rows(0, n_sweeps);
   } else {
+    auto lo = [&](int i) { return (int)((int64_t)n_sweeps * i / nth); };
     std::vector<std::thread> pool;
-    for (int i = 1; i < nth; ++i)
-      pool.emplace_back(rows, (int)((int64_t)n_sweeps * i / nth), (int)((int64_t)n_sweeps * (i + 1) / nth));
-    rows(0, n_sweeps / nth);
+    int made = 1;   // parts 1 .. made-1 run on their own threads
+    try {
+      for (int i = 1; i < nth; ++i) {
+        pool.emplace_back(rows, lo(i), lo(i + 1));
+        ++made;
+      }
+    } catch (...) {
+      // no thread could be started for part `made`: this thread builds it
+      // and the rest below
+    }
+    rows(0, lo(1));
+    for (int i = made; i < nth; ++i) rows(lo(i), lo(i + 1));
     for (auto &t : pool) t.join();
   }
   int nreal = 0;
