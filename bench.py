@@ -45,7 +45,7 @@ ALG_OPS_PER_FLIP = 14.0
 # capture (profiles/sqa_kernel_L8_P64_R256.md), valid while the kernel
 # sources hash to TRAFFIC_SRC_SHA256; otherwise the bench reports null.
 TRAFFIC_BYTES = 2359808          # mean of 3 timed launches: 2.34, 2.36, 2.38 MB
-TRAFFIC_SRC_SHA256 = "88c03be1829fe0c26b7b6776957080be53276221f6e69549c729dddcb149f002"
+TRAFFIC_SRC_SHA256 = "976abb0409016844245ab7e7ace6cc3f9b2f6339f07b5d5ec1382bde29689850"
 TRAFFIC_SOURCES = ("paper_2503_10302_gb300/csrc/sqa.cu", "paper_2503_10302_gb300/csrc/device.cuh",
                    "paper_2503_10302_gb300/csrc/internal.h")
 WORKLOAD = f"DT-SQA 3D +-J L={L} periodic, P={P} slices, R={R} runs, T={T}, Gamma 3.0->1e-3 over {SWEEPS} sweeps"

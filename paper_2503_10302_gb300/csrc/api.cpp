@@ -5,6 +5,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <thread>
 #include <vector>
@@ -21,6 +23,20 @@ void set_error(const std::string &msg) { g_error = msg; }
 int fail(int code, const std::string &msg) {
   g_error = msg;
   return code;
+}
+
+int fail_exception() {
+  try {
+    throw;
+  } catch (const std::bad_alloc &) {
+    return fail(PC_ENOMEM, "host allocation failed");
+  } catch (const std::length_error &) {
+    return fail(PC_ENOMEM, "host allocation too large");
+  } catch (const std::exception &e) {
+    return fail(PC_EINVAL, std::string("unexpected error: ") + e.what());
+  } catch (...) {
+    return fail(PC_EINVAL, "unexpected error");
+  }
 }
 
 uint32_t recip32(uint32_t d) {
@@ -135,7 +151,7 @@ int32_t pc_jperp_q(double gamma, int P, double T) {
   return (int32_t)std::llround(jp * 65536.0);
 }
 
-int pc_create(pc_ctx **out, int device, uint64_t seed) {
+int pc_create(pc_ctx **out, int device, uint64_t seed) try {
   if (!out) return fail(PC_EINVAL, "out is NULL");
   *out = nullptr;
   int n = 0;
@@ -159,9 +175,11 @@ int pc_create(pc_ctx **out, int device, uint64_t seed) {
   c->own_stream = true;
   *out = c;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-void pc_destroy(pc_ctx *c) {
+void pc_destroy(pc_ctx *c) try {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
@@ -170,9 +188,10 @@ void pc_destroy(pc_ctx *c) {
   pc_graph_release_impl(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
+} catch (...) {
 }
 
-int pc_set_stream(pc_ctx *c, void *stream) {
+int pc_set_stream(pc_ctx *c, void *stream) try {
   if (!c) return fail(PC_EINVAL, "ctx is NULL");
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -180,24 +199,30 @@ int pc_set_stream(pc_ctx *c, void *stream) {
   c->stream = (cudaStream_t)stream;
   c->own_stream = false;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 static int sqa_check_device(pc_ctx *c);
 
-int pc_synchronize(pc_ctx *c) {
+int pc_synchronize(pc_ctx *c) try {
   if (!c) return fail(PC_EINVAL, "ctx is NULL");
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return sqa_check_device(c);
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_device_sm_count(pc_ctx *c, int *sms) {
+int pc_device_sm_count(pc_ctx *c, int *sms) try {
   if (!c || !sms) return fail(PC_EINVAL, "NULL argument");
   *sms = c->sms;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_philox(pc_ctx *c, int64_t n, const uint32_t *ctr, uint32_t *out) {
+int pc_philox(pc_ctx *c, int64_t n, const uint32_t *ctr, uint32_t *out) try {
   if (!c || n < 0 || (n > 0 && (!ctr || !out))) return fail(PC_EINVAL, "bad arguments");
   if (n == 0) return PC_OK;
   PC_CUDA_TRY(cudaSetDevice(c->device));
@@ -212,16 +237,20 @@ int pc_philox(pc_ctx *c, int64_t n, const uint32_t *ctr, uint32_t *out) {
   PC_CUDA_TRY(cudaMemcpyAsync(out, dout.p, (size_t)n * 16, cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 // ------------------------------------------------------------------ DT-SQA
 int pc_sqa_setup(pc_ctx *c, const int32_t *dims, const int8_t *J, int P, double T, int n_sweeps,
-                 const double *gamma) {
+                 const double *gamma) try {
   return pc_sqa_setup_bc(c, dims, nullptr, nullptr, J, P, T, n_sweeps, gamma);
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, const uint8_t *present,
-                    const int8_t *J, int P, double T, int n_sweeps, const double *gamma) {
+                    const int8_t *J, int P, double T, int n_sweeps, const double *gamma) try {
   if (!c || !J || (n_sweeps > 0 && !gamma)) return fail(PC_EINVAL, "NULL argument");
   Lattice lat;
   int rc = check_lattice(dims, J, &lat);
@@ -297,15 +326,19 @@ int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, con
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   q.ready = true;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_sqa_get_table(pc_ctx *c, int sweep, uint32_t *out, int32_t *jq) {
+int pc_sqa_get_table(pc_ctx *c, int sweep, uint32_t *out, int32_t *jq) try {
   if (!c || !c->sqa.ready) return fail(PC_ESTATE, "pc_sqa_setup first");
   if (sweep < 0 || sweep >= c->sqa.S) return fail(PC_EINVAL, "sweep out of range");
   for (int m = 0; m < 3; ++m)
     for (int cc = 0; cc < 7; ++cc) out[7 * m + cc] = c->sqa.table[(size_t)sweep * kSqaTab + 2 * cc + 13 * m];
   if (jq) *jq = c->sqa.jq[(size_t)sweep];
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 static int sqa_enqueue(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev,
@@ -373,26 +406,30 @@ static int sqa_check_device(pc_ctx *c) {
   return PC_OK;
 }
 
-int pc_sqa_run_dev(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev) {
+int pc_sqa_run_dev(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev) try {
   if (!c || !c->sqa.ready) return fail(PC_ESTATE, "pc_sqa_setup first");
   if (R < 0 || (R > 0 && !E_dev)) return fail(PC_EINVAL, "bad arguments");
   if ((uint64_t)run0 + (uint64_t)R > (1ull << 24)) return fail(PC_EINVAL, "run ids must be < 2^24");
   if (R == 0) return PC_OK;
   PC_CUDA_TRY(cudaSetDevice(c->device));
   return sqa_enqueue(c, R, run0, E_dev, best_dev, nullptr);
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_sqa_run_corr_dev(pc_ctx *c, int R, uint32_t run0, int32_t *E_dev, int32_t *best_dev,
-                        int32_t *corr_dev) {
+                        int32_t *corr_dev) try {
   if (!c || !c->sqa.ready) return fail(PC_ESTATE, "pc_sqa_setup first");
   if (R < 0 || (R > 0 && (!E_dev || !corr_dev))) return fail(PC_EINVAL, "bad arguments");
   if ((uint64_t)run0 + (uint64_t)R > (1ull << 24)) return fail(PC_EINVAL, "run ids must be < 2^24");
   if (R == 0) return PC_OK;
   PC_CUDA_TRY(cudaSetDevice(c->device));
   return sqa_enqueue(c, R, run0, E_dev, best_dev, nullptr, 0, 10000000000ull, corr_dev);
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_sqa_run(pc_ctx *c, int R, uint32_t run0, int64_t *E_out, int8_t *spins_out) {
+int pc_sqa_run(pc_ctx *c, int R, uint32_t run0, int64_t *E_out, int8_t *spins_out) try {
   if (!c || !c->sqa.ready) return fail(PC_ESTATE, "pc_sqa_setup first");
   if (R < 0) return fail(PC_EINVAL, "R must be >= 0");
   if ((uint64_t)run0 + (uint64_t)R > (1ull << 24)) return fail(PC_EINVAL, "run ids must be < 2^24");
@@ -415,9 +452,11 @@ int pc_sqa_run(pc_ctx *c, int R, uint32_t run0, int64_t *E_out, int8_t *spins_ou
   if (E_out)
     for (size_t i = 0; i < nE; ++i) E_out[i] = hE[i];
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_sqa_selftest_wait(pc_ctx *c, int *status) {
+int pc_sqa_selftest_wait(pc_ctx *c, int *status) try {
   if (!c || !c->sqa.ready || !status) return fail(PC_ESTATE, "pc_sqa_setup first");
   if (c->sqa.S < 2) return fail(PC_EINVAL, "the self-test needs a schedule of at least 2 sweeps");
   PC_CUDA_TRY(cudaSetDevice(c->device));
@@ -430,13 +469,17 @@ int pc_sqa_selftest_wait(pc_ctx *c, int *status) {
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   *status = sqa_check_device(c);
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_sqa_anneal(pc_ctx *c, const int32_t *dims, const int8_t *J, int P, double T, int n_sweeps,
-                  const double *gamma, int R, uint32_t run0, int64_t *E_out) {
+                  const double *gamma, int R, uint32_t run0, int64_t *E_out) try {
   int rc = pc_sqa_setup(c, dims, J, P, T, n_sweeps, gamma);
   if (rc) return rc;
   return pc_sqa_run(c, R, run0, E_out, nullptr);
+} catch (...) {
+  return pc::fail_exception();
 }
 
 }  // extern "C"

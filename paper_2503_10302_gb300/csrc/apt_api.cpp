@@ -376,9 +376,10 @@ using namespace pc;
 
 static AptImpl *apt_impl(pc_ctx *c) { return static_cast<AptImpl *>(c->apt_impl); }
 
-void pc_apt_release_impl(pc_ctx *c) {
+void pc_apt_release_impl(pc_ctx *c) try {
   delete apt_impl(c);
   c->apt_impl = nullptr;
+} catch (...) {
 }
 
 // ------------------------------------------------------------ checkpoints
@@ -460,13 +461,15 @@ int ckpt_io(pc_ctx *c, const char *path, bool save) {
 extern "C" {
 
 int pc_apt_load(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, const int32_t *n_temps,
-                const double *betas, int n_labels, uint32_t entry0) {
+                const double *betas, int n_labels, uint32_t entry0) try {
   return pc_apt_load_bc(c, n_inst, dims, nullptr, nullptr, J, n_temps, betas, n_labels, entry0);
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *periodic,
                    const uint8_t *present, const int8_t *J, const int32_t *n_temps, const double *betas,
-                   int n_labels, uint32_t entry0) {
+                   int n_labels, uint32_t entry0) try {
   if (!c || !dims || !J || !n_temps || !betas) return fail(PC_EINVAL, "NULL argument");
   if (n_inst < 1) return fail(PC_EINVAL, "n_inst must be >= 1");
   if (!(n_labels == 1 || n_labels == 2 || n_labels == 4))
@@ -535,6 +538,8 @@ int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *pe
   c->apt.sweeps = 0;
   c->apt.swaps = 0;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 static int apt_enqueue(pc_ctx *c, AptImpl *im, int n_iter, int spp, int icm) {
@@ -551,15 +556,17 @@ static int apt_enqueue(pc_ctx *c, AptImpl *im, int n_iter, int spp, int icm) {
   return apt_advance_launch(im->bt.d_ctr.p, (int64_t)n_iter * spp, n_iter, c->stream);
 }
 
-int pc_apt_set_joint_swap(pc_ctx *c, int joint) {
+int pc_apt_set_joint_swap(pc_ctx *c, int joint) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   AptImpl *im = apt_impl(c);
   im->joint = joint ? 1 : 0;
   im->g_spp = -1;   // the captured chunk bakes the rule in: capture again
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
+int pc_apt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (n_swaps < 0 || sweeps_per_swap < 1) return fail(PC_EINVAL, "n_swaps >= 0, sweeps_per_swap >= 1");
   AptImpl *im = apt_impl(c);
@@ -608,9 +615,11 @@ int pc_apt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
   c->apt.sweeps += n_swaps * sweeps_per_swap;
   c->apt.swaps += n_swaps;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) {
+int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (trial_swaps < 1) return fail(PC_EINVAL, "trial_swaps must be >= 1");
   AptImpl *im = apt_impl(c);
@@ -667,9 +676,11 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) {
   }
   if (tpb_out) *tpb_out = best;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_set_split(pc_ctx *c, int pref) {
+int pc_apt_set_split(pc_ctx *c, int pref) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (pref < 0 || pref > 2) return fail(PC_EINVAL, "pref must be 0, 1 or 2");
   AptImpl *im = apt_impl(c);
@@ -688,15 +699,19 @@ int pc_apt_set_split(pc_ctx *c, int pref) {
   im->exec = nullptr;
   im->graph = nullptr;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_is_split(pc_ctx *c, int *split) {
+int pc_apt_is_split(pc_ctx *c, int *split) try {
   if (!c || !c->apt.ready || !apt_impl(c) || !split) return fail(PC_ESTATE, "pc_apt_load first");
   *split = apt_impl(c)->bt.split;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_set_block_threads(pc_ctx *c, int tpb) {
+int pc_apt_set_block_threads(pc_ctx *c, int tpb) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (tpb < 64 || tpb > 512 || tpb % 64) return fail(PC_EINVAL, "tpb must be a multiple of 64 in [64, 512]");
   AptImpl *im = apt_impl(c);
@@ -715,13 +730,17 @@ int pc_apt_set_block_threads(pc_ctx *c, int tpb) {
   im->exec = nullptr;
   im->graph = nullptr;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_progress(pc_ctx *c, int64_t *sweeps, int64_t *swaps) {
+int pc_apt_progress(pc_ctx *c, int64_t *sweeps, int64_t *swaps) try {
   if (!c || !c->apt.ready) return fail(PC_ESTATE, "pc_apt_load first");
   if (sweeps) *sweeps = c->apt.sweeps;
   if (swaps) *swaps = c->apt.swaps;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 static int check_inst(pc_ctx *c, int inst) {
@@ -730,10 +749,10 @@ static int check_inst(pc_ctx *c, int inst) {
   return PC_OK;
 }
 
-int pc_apt_save(pc_ctx *c, const char *path) { return ckpt_io(c, path, true); }
-int pc_apt_restore(pc_ctx *c, const char *path) { return ckpt_io(c, path, false); }
+int pc_apt_save(pc_ctx *c, const char *path) try { return ckpt_io(c, path, true); } catch (...) { return pc::fail_exception(); }
+int pc_apt_restore(pc_ctx *c, const char *path) try { return ckpt_io(c, path, false); } catch (...) { return pc::fail_exception(); }
 
-int pc_apt_set_target(pc_ctx *c, int inst, int64_t e_target) {
+int pc_apt_set_target(pc_ctx *c, int inst, int64_t e_target) try {
   int rc = check_inst(c, inst);
   if (rc) return rc;
   Batch &bt = apt_impl(c)->bt;
@@ -746,9 +765,11 @@ int pc_apt_set_target(pc_ctx *c, int inst, int64_t e_target) {
   PC_CUDA_TRY(cudaMemcpy(bt.d_target.p + inst, &e_target, 8, cudaMemcpyHostToDevice));
   PC_CUDA_TRY(cudaMemcpy(bt.d_hit.p + inst, &hit, 8, cudaMemcpyHostToDevice));
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_get_state(pc_ctx *c, int inst, int8_t *spins, int64_t *energies, int32_t *temp_of) {
+int pc_apt_get_state(pc_ctx *c, int inst, int8_t *spins, int64_t *energies, int32_t *temp_of) try {
   int rc = check_inst(c, inst);
   if (rc) return rc;
   Batch &bt = apt_impl(c)->bt;
@@ -775,10 +796,12 @@ int pc_apt_get_state(pc_ctx *c, int inst, int8_t *spins, int64_t *energies, int3
   if (temp_of)
     for (int sl = 0; sl < nslot; ++sl) temp_of[sl] = sl / P.A;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_apt_get_best(pc_ctx *c, int inst, int64_t *E, int64_t *sweep, int32_t *buf, int64_t *hit_sweep,
-                    int8_t *spins) {
+                    int8_t *spins) try {
   int rc = check_inst(c, inst);
   if (rc) return rc;
   Batch &bt = apt_impl(c)->bt;
@@ -797,9 +820,11 @@ int pc_apt_get_best(pc_ctx *c, int inst, int64_t *E, int64_t *sweep, int32_t *bu
     PC_CUDA_TRY(cudaMemcpy(spins, bt.d_bestspins.p + bt.prob[(size_t)inst].best_off,
                            (size_t)bt.prob[(size_t)inst].N, cudaMemcpyDeviceToHost));
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_get_best_all(pc_ctx *c, int64_t *E, int64_t *hit_sweep) {
+int pc_apt_get_best_all(pc_ctx *c, int64_t *E, int64_t *hit_sweep) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   Batch &bt = apt_impl(c)->bt;
   const size_t n = bt.prob.size();
@@ -808,9 +833,11 @@ int pc_apt_get_best_all(pc_ctx *c, int64_t *E, int64_t *hit_sweep) {
   if (hit_sweep) PC_CUDA_TRY(cudaMemcpyAsync(hit_sweep, bt.d_hit.p, 8 * n, cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_get_stats(pc_ctx *c, int inst, int64_t *att, int64_t *acc, int64_t *icm) {
+int pc_apt_get_stats(pc_ctx *c, int inst, int64_t *att, int64_t *acc, int64_t *icm) try {
   int rc = check_inst(c, inst);
   if (rc) return rc;
   Batch &bt = apt_impl(c)->bt;
@@ -824,9 +851,11 @@ int pc_apt_get_stats(pc_ctx *c, int inst, int64_t *att, int64_t *acc, int64_t *i
   if (acc) std::memcpy(acc, s.data() + np, 8 * (size_t)np);
   if (icm) std::memcpy(icm, s.data() + 2 * np, 24);
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_get_pbit_table(pc_ctx *c, int inst, uint32_t *out) {
+int pc_apt_get_pbit_table(pc_ctx *c, int inst, uint32_t *out) try {
   int rc = check_inst(c, inst);
   if (rc) return rc;
   Batch &bt = apt_impl(c)->bt;
@@ -834,9 +863,11 @@ int pc_apt_get_pbit_table(pc_ctx *c, int inst, uint32_t *out) {
   for (int t = 0; t < P.T; ++t)
     for (int cc = 0; cc < 7; ++cc) out[7 * t + cc] = bt.h_pbit[P.pbit_off + 16 * t + 2 * cc];
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_apt_get_swap_table(pc_ctx *c, int inst, int pair, uint32_t *out, int max_len, int *len) {
+int pc_apt_get_swap_table(pc_ctx *c, int inst, int pair, uint32_t *out, int max_len, int *len) try {
   int rc = check_inst(c, inst);
   if (rc) return rc;
   Batch &bt = apt_impl(c)->bt;
@@ -846,13 +877,15 @@ int pc_apt_get_swap_table(pc_ctx *c, int inst, int pair, uint32_t *out, int max_
   if (len) *len = (int)n;
   for (int k = 0; k < max_len && k < (int)n; ++k) out[k] = bt.h_swaptab[off + k];
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 // ------------------------------------------------------------------ ladder
 int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
                        double beta0, double alpha, int n_chains, int sweeps, int tail, double tol,
                        int max_len, double *beta_out, double *sigma_out, int32_t *len_out,
-                       int32_t *converged_out) {
+                       int32_t *converged_out) try {
   if (!c || !dims || !J || !beta_out || !len_out) return fail(PC_EINVAL, "NULL argument");
   if (n_inst < 1 || n_chains < 1 || n_chains > 4096 || sweeps < 1 || tail < 2 || tail > sweeps ||
       max_len < 1 || !(beta0 > 0.0) || !(alpha > 0.0))
@@ -944,9 +977,11 @@ int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t 
     if (converged_out) converged_out[i] = conv[(size_t)i];
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_resample_ladder(const double *beta, int len, int n, double *out) {
+int pc_resample_ladder(const double *beta, int len, int n, double *out) try {
   if (!beta || !out || len < 1 || n < 2) return fail(PC_EINVAL, "bad arguments");
   if (len == 1) {
     for (int k = 0; k < n; ++k) out[k] = beta[0];
@@ -960,12 +995,14 @@ int pc_resample_ladder(const double *beta, int len, int n, double *out) {
     out[k] = beta[lo] * (1.0 - w) + beta[lo + 1] * w;
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 // ------------------------------------------------------------------ pilot
 int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
                   int n_beta, const double *betas, int chains_per_beta, int sweeps, int burn, int n_bins,
-                  int64_t *counts) {
+                  int64_t *counts) try {
   if (!c || !dims || !J || !betas || !counts) return fail(PC_EINVAL, "NULL argument");
   if (n_inst < 1 || n_beta < 1 || chains_per_beta < 1 || n_beta * chains_per_beta > 64 || sweeps < 1 ||
       burn < 0 || burn >= sweeps || n_bins < 1 || n_bins > 256 || n_beta * n_bins > 2048)
@@ -1012,9 +1049,11 @@ int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, u
                               cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_instance_features(const int32_t *dims, const int8_t *J, double *out3) {
+int pc_instance_features(const int32_t *dims, const int8_t *J, double *out3) try {
   if (!dims || !J || !out3) return fail(PC_EINVAL, "NULL argument");
   Lattice lat;
   int rc = check_lattice(dims, J, &lat);
@@ -1039,6 +1078,8 @@ int pc_instance_features(const int32_t *dims, const int8_t *J, double *out3) {
   out3[1] = (double)pos / (3.0 * N);
   out3[2] = (double)frust / (3.0 * N);
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 }  // extern "C"

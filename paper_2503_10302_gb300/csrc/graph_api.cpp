@@ -235,15 +235,16 @@ GAptArgs make_args(pc_ctx *c, GImpl *im) {
 
 using namespace pc;
 
-void pc_graph_release_impl(pc_ctx *c) {
+void pc_graph_release_impl(pc_ctx *c) try {
   delete gimpl(c);
   c->graph_impl = nullptr;
+} catch (...) {
 }
 
 extern "C" {
 
 int pc_graph_dsatur(int n, const int32_t *row_ptr, const int32_t *col, int32_t *colour,
-                    int *n_colours) {
+                    int *n_colours) try {
   if (!colour) return fail(PC_EINVAL, "colour is NULL");
   int rc = check_graph(n, row_ptr, col, nullptr);
   if (rc) return rc;
@@ -253,6 +254,8 @@ int pc_graph_dsatur(int n, const int32_t *row_ptr, const int32_t *col, int32_t *
   std::memcpy(colour, cl.data(), sizeof(int32_t) * n);
   if (n_colours) *n_colours = C;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 }  // extern "C"
@@ -372,7 +375,7 @@ int gload(pc_ctx *c, GImpl *im, int n_prob, const int32_t *n_vert, const int32_t
 
 extern "C" int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *row_ptr,
                             const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
-                            const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0) {
+                            const int32_t *n_temps, const double *betas, int n_labels, uint32_t entry0) try {
   if (!c) return fail(PC_EINVAL, "ctx is NULL");
   if (n_prob < 1 || !n_vert || !row_ptr || !col || !w || !n_temps || !betas)
     return fail(PC_EINVAL, "pc_gapt_load: n_prob >= 1 and non-NULL arrays required");
@@ -384,11 +387,13 @@ extern "C" int pc_gapt_load(pc_ctx *c, int n_prob, const int32_t *n_vert, const 
   c->graph_impl = im;
   return gload(c, im, n_prob, n_vert, row_ptr, col, w, h, colour, n_temps, betas, n_labels, entry0,
                kTagGInit);
+} catch (...) {
+  return pc::fail_exception();
 }
 
 extern "C" {
 
-int pc_gapt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
+int pc_gapt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) try {
   int rc = gimpl_ready(c, 0);
   if (rc) return rc;
   GImpl *im = gimpl(c);
@@ -413,16 +418,20 @@ int pc_gapt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) {
     left -= chunk;
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_gapt_set_joint_swap(pc_ctx *c, int joint) {
+int pc_gapt_set_joint_swap(pc_ctx *c, int joint) try {
   int rc = gimpl_ready(c, 0);
   if (rc) return rc;
   gimpl(c)->joint = joint != 0;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_gapt_set_target(pc_ctx *c, int prob, int64_t e_target) {
+int pc_gapt_set_target(pc_ctx *c, int prob, int64_t e_target) try {
   int rc = gimpl_ready(c, prob);
   if (rc) return rc;
   GImpl *im = gimpl(c);
@@ -436,9 +445,11 @@ int pc_gapt_set_target(pc_ctx *c, int prob, int64_t e_target) {
   PC_CUDA_TRY(cudaMemcpyAsync(im->d_target.p + prob, &t, sizeof(t), cudaMemcpyHostToDevice, c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_gapt_get_energies(pc_ctx *c, int prob, int64_t *E) {
+int pc_gapt_get_energies(pc_ctx *c, int prob, int64_t *E) try {
   int rc = gimpl_ready(c, prob);
   if (rc) return rc;
   if (!E) return fail(PC_EINVAL, "E is NULL");
@@ -451,9 +462,11 @@ int pc_gapt_get_energies(pc_ctx *c, int prob, int64_t *E) {
   for (int r = 0; r < T; ++r)
     for (int a = 0; a < A; ++a) E[r * A + a] = e[32 * a + r];
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_gapt_get_spins(pc_ctx *c, int prob, int8_t *spins) {
+int pc_gapt_get_spins(pc_ctx *c, int prob, int8_t *spins) try {
   int rc = gimpl_ready(c, prob);
   if (rc) return rc;
   if (!spins) return fail(PC_EINVAL, "spins is NULL");
@@ -470,19 +483,23 @@ int pc_gapt_get_spins(pc_ctx *c, int prob, int8_t *spins) {
       for (int v = 0; v < n; ++v)
         spins[((size_t)r * A + a) * n + v] = ((wd[(size_t)g.newid[v] * A + a] >> r) & 1u) ? 1 : -1;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_gapt_get_colours(pc_ctx *c, int prob, int32_t *colour) {
+int pc_gapt_get_colours(pc_ctx *c, int prob, int32_t *colour) try {
   int rc = gimpl_ready(c, prob);
   if (rc) return rc;
   if (!colour) return fail(PC_EINVAL, "colour is NULL");
   const HGraph &g = gimpl(c)->g[prob];
   std::memcpy(colour, g.colour.data(), sizeof(int32_t) * g.n);
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_gapt_get_best(pc_ctx *c, int prob, int64_t *E, int64_t *sweep, int32_t *slot,
-                     int64_t *hit_sweep, int8_t *spins) {
+                     int64_t *hit_sweep, int8_t *spins) try {
   int rc = gimpl_ready(c, prob);
   if (rc) return rc;
   GImpl *im = gimpl(c);
@@ -505,9 +522,11 @@ int pc_gapt_get_best(pc_ctx *c, int prob, int64_t *E, int64_t *sweep, int32_t *s
     }
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_gapt_get_stats(pc_ctx *c, int prob, int64_t *att, int64_t *acc, int64_t *icm) {
+int pc_gapt_get_stats(pc_ctx *c, int prob, int64_t *att, int64_t *acc, int64_t *icm) try {
   int rc = gimpl_ready(c, prob);
   if (rc) return rc;
   GImpl *im = gimpl(c);
@@ -524,11 +543,13 @@ int pc_gapt_get_stats(pc_ctx *c, int prob, int64_t *att, int64_t *acc, int64_t *
   if (icm)
     for (int i = 0; i < 3; ++i) icm[i] = (int64_t)s[2 * np + i];
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col, const int8_t *w,
                    const int8_t *h, const int32_t *colour, int P, double T, int n_sweeps,
-                   const double *gamma, int R, uint32_t run0, int64_t *E_out, int8_t *spins_out) {
+                   const double *gamma, int R, uint32_t run0, int64_t *E_out, int8_t *spins_out) try {
   if (!c) return fail(PC_EINVAL, "ctx is NULL");
   if (P < 2 || P > 2047 || !(T > 0) || n_sweeps < 0 || R < 1 || !E_out || (n_sweeps > 0 && !gamma))
     return fail(PC_EINVAL, "pc_gsqa_anneal: P in 2..2047, T > 0, R >= 1, gamma and E_out required");
@@ -640,13 +661,15 @@ int pc_gsqa_anneal(pc_ctx *c, int n, const int32_t *row_ptr, const int32_t *col,
           spins_out[((size_t)r * P + k) * n + v] =
               ((wd[((size_t)(r >> 5) * P + k) * n + g.newid[v]] >> (r & 31)) & 1u) ? 1 : -1;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_graph_adaptive_ladder(pc_ctx *c, int n_prob, const int32_t *n_vert, const int32_t *row_ptr,
                              const int32_t *col, const int8_t *w, const int8_t *h, const int32_t *colour,
                              uint32_t entry0, double beta0, double alpha, int n_chains, int sweeps,
                              int tail, double tol, int max_len, double *beta_out, double *sigma_out,
-                             int32_t *len_out, int32_t *converged_out) {
+                             int32_t *len_out, int32_t *converged_out) try {
   if (!c || !beta_out || !len_out) return fail(PC_EINVAL, "NULL argument");
   if (n_prob < 1 || n_chains < 1 || n_chains > 128 || sweeps < 1 || tail < 2 || tail > sweeps ||
       max_len < 1 || !(beta0 > 0.0) || !(alpha > 0.0))
@@ -734,6 +757,8 @@ int pc_graph_adaptive_ladder(pc_ctx *c, int n_prob, const int32_t *n_vert, const
     if (converged_out) converged_out[i] = conv[(size_t)i];
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 }  // extern "C"

@@ -12,6 +12,11 @@ namespace pc {
 
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
+// Status of the exception being handled (call inside a catch block only):
+// PC_ENOMEM for failed host allocations, PC_EINVAL otherwise.  Every C-ABI
+// entry point ends in a handler that calls it, so no exception leaves the
+// library.
+int fail_exception();
 
 #define PC_CUDA_TRY(call)                                                          \
   do {                                                                             \

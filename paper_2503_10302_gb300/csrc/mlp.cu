@@ -278,7 +278,7 @@ int adam(pc_mlp *mm, float lr) {
 
 extern "C" {
 
-int pc_mlp_create(pc_ctx *c, pc_mlp **out, const float *const *W, const float *const *b, float beta_min) {
+int pc_mlp_create(pc_ctx *c, pc_mlp **out, const float *const *W, const float *const *b, float beta_min) try {
   if (!c || !out || !W || !b) return fail(PC_EINVAL, "NULL argument");
   *out = nullptr;
   PC_CUDA_TRY(cudaSetDevice(c->device));
@@ -316,16 +316,19 @@ int pc_mlp_create(pc_ctx *c, pc_mlp **out, const float *const *W, const float *c
   }
   *out = mm;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-void pc_mlp_destroy(pc_mlp *mm) {
+void pc_mlp_destroy(pc_mlp *mm) try {
   if (!mm) return;
   cudaSetDevice(mm->ctx->device);
   cudaStreamSynchronize(mm->ctx->stream);
   delete mm;
+} catch (...) {
 }
 
-int pc_mlp_forward(pc_mlp *mm, int batch, const float *X, float *beta) {
+int pc_mlp_forward(pc_mlp *mm, int batch, const float *X, float *beta) try {
   if (!mm || !X || !beta || batch < 1) return fail(PC_EINVAL, "bad arguments");
   PC_CUDA_TRY(cudaSetDevice(mm->ctx->device));
   cudaStream_t st = mm->ctx->stream;
@@ -336,10 +339,12 @@ int pc_mlp_forward(pc_mlp *mm, int batch, const float *X, float *beta) {
   PC_CUDA_TRY(cudaMemcpyAsync(beta, mm->beta.p, (size_t)batch * kOut * 4, cudaMemcpyDeviceToHost, st));
   PC_CUDA_TRY(cudaStreamSynchronize(st));
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_mlp_grads(pc_mlp *mm, int batch, const float *X, const float *Y, float *loss, float *const *gW,
-                 float *const *gb) {
+                 float *const *gb) try {
   if (!mm || !X || !Y || batch < 1) return fail(PC_EINVAL, "bad arguments");
   PC_CUDA_TRY(cudaSetDevice(mm->ctx->device));
   cudaStream_t st = mm->ctx->stream;
@@ -359,10 +364,12 @@ int pc_mlp_grads(pc_mlp *mm, int batch, const float *X, const float *Y, float *l
     if (gb && gb[k]) std::memcpy(gb[k], h.data() + mm->b_off[k], sizeof(float) * kDims[k + 1]);
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 int pc_mlp_train_step_dev(pc_mlp *mm, int batch, const float *X_dev, const float *Y_dev, float lr,
-                          float *loss_dev) {
+                          float *loss_dev) try {
   if (!mm || !X_dev || !Y_dev || batch < 1) return fail(PC_EINVAL, "bad arguments");
   PC_CUDA_TRY(cudaSetDevice(mm->ctx->device));
   int rc = ensure_batch(mm, batch);
@@ -371,9 +378,11 @@ int pc_mlp_train_step_dev(pc_mlp *mm, int batch, const float *X_dev, const float
   if (loss_dev)
     PC_CUDA_TRY(cudaMemcpyAsync(loss_dev, mm->loss.p, 4, cudaMemcpyDeviceToDevice, mm->ctx->stream));
   return adam(mm, lr);
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_mlp_train_step(pc_mlp *mm, int batch, const float *X, const float *Y, float lr, float *loss) {
+int pc_mlp_train_step(pc_mlp *mm, int batch, const float *X, const float *Y, float lr, float *loss) try {
   if (!mm || !X || !Y || batch < 1) return fail(PC_EINVAL, "bad arguments");
   PC_CUDA_TRY(cudaSetDevice(mm->ctx->device));
   cudaStream_t st = mm->ctx->stream;
@@ -389,9 +398,11 @@ int pc_mlp_train_step(pc_mlp *mm, int batch, const float *X, const float *Y, flo
     *loss = mm->host_loss.p[0];
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
-int pc_mlp_get_params(pc_mlp *mm, float *const *W, float *const *b) {
+int pc_mlp_get_params(pc_mlp *mm, float *const *W, float *const *b) try {
   if (!mm) return fail(PC_EINVAL, "NULL argument");
   PC_CUDA_TRY(cudaSetDevice(mm->ctx->device));
   std::vector<float> h(mm->n_params);
@@ -402,6 +413,8 @@ int pc_mlp_get_params(pc_mlp *mm, float *const *W, float *const *b) {
     if (b && b[k]) std::memcpy(b[k], h.data() + mm->b_off[k], sizeof(float) * kDims[k + 1]);
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
 }
 
 }  // extern "C"

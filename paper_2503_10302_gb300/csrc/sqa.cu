@@ -586,7 +586,7 @@ int noalloc_scratch(int device, unsigned char **out) {
 extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, const int32_t *dims,
                                      const int8_t *J, int P, double T, int n_sweeps,
                                      const double *gamma, int R, uint32_t run0, int32_t *E_dev,
-                                     int32_t *best_dev) {
+                                     int32_t *best_dev) try {
   using namespace pc;
   if (!dims || !J || (n_sweeps > 0 && !gamma) || (R > 0 && !E_dev))
     return fail(PC_EINVAL, "NULL argument");
@@ -673,4 +673,6 @@ extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, co
   a.first_item = 0;
   a.wait_ns = 0;
   return sqa_launch(a, R, st);
+} catch (...) {
+  return pc::fail_exception();
 }
