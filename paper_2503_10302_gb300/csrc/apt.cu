@@ -929,6 +929,9 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
   swap_words(k, sh, k.geo.H, 2 * k.geo.H, bmask, sh.stage + 256 * par);
 }
 
+// MODE (pc::APT_MODE_*) is a template argument, so that each mode's kernel
+// carries only its own code (the run-time MODE equals it).
+template <int MODE>
 __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int cta = blockIdx.x;
@@ -956,7 +959,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.Bc = min(8 * k.Gc, P.B - 8 * k.g0);
   k.split = a.split;
   k.rank = a.split ? (int)cooperative_groups::this_cluster().block_rank() : 0;
-  if (a.mode == pc::APT_MODE_APT || a.mode == pc::APT_MODE_ENERGY) {
+  if (MODE == pc::APT_MODE_APT || MODE == pc::APT_MODE_ENERGY) {
     k.Gu = k.Gc / k.A;   // A is 1, 2 or 4
     k.Glp = k.Tp >> 3;
   } else {
@@ -972,7 +975,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   // larger half), so that distributed-shared-memory addresses correspond
   const int Gcarve = a.split ? k.A * ((k.Glp + 1) >> 1) : k.Gc, G8 = 8 * Gcarve;
   const int64_t s0 = a.ctr[0], t0 = a.ctr[1];
-  const bool icm = a.mode == pc::APT_MODE_APT && a.icm;
+  const bool icm = MODE == pc::APT_MODE_APT && a.icm;
   // carve shared memory
   Shared sh;
   uint32_t *cur = smem;
@@ -990,7 +993,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.m64 = reinterpret_cast<int64_t *>(cur);      cur += 8;
   sh.sum1 = reinterpret_cast<int64_t *>(cur);     cur += 2 * G8;
   sh.sum2 = reinterpret_cast<int64_t *>(cur);     cur += 2 * G8;
-  sh.hist = reinterpret_cast<int32_t *>(cur);     cur += a.mode == pc::APT_MODE_PILOT ? k.T * a.n_bins : 0;
+  sh.hist = reinterpret_cast<int32_t *>(cur);     cur += MODE == pc::APT_MODE_PILOT ? k.T * a.n_bins : 0;
   sh.ikx = cur;                                   cur += 64;
   sh.ibit = reinterpret_cast<int32_t *>(cur);     cur += 64;
   sh.inm = reinterpret_cast<int32_t *>(cur);      cur += 64;
@@ -1030,7 +1033,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     sh.sacc[i] = 0;
   }
   if (threadIdx.x < 24) sh.xch[threadIdx.x] = 0;
-  if (a.mode == pc::APT_MODE_PILOT)
+  if (MODE == pc::APT_MODE_PILOT)
     for (int i = threadIdx.x; i < k.T * a.n_bins; i += blockDim.x) sh.hist[i] = 0;
   if (threadIdx.x == 0) {
     sh.m64[0] = a.best_E[p];
@@ -1044,7 +1047,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   }
   __syncthreads();
 
-  if (a.mode == pc::APT_MODE_ENERGY) {
+  if (MODE == pc::APT_MODE_ENERGY) {
     colour_phase<false, true>(a, k, sh, 1, 0u, k.Gc);
     __syncthreads();
     finish_energies(k, sh);
@@ -1063,14 +1066,14 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
         finish_energies(k, sh);
         __syncthreads();
         PROF_MARK(1, pt);
-        if (a.mode == pc::APT_MODE_LADDER) {
+        if (MODE == pc::APT_MODE_LADDER) {
           if ((int64_t)it * a.spp + qq >= a.window_from)
             for (int b = threadIdx.x; b < k.Bc; b += blockDim.x) {
               const int64_t e = sh.E[b];
               sh.sum1[b] += e;
               sh.sum2[b] += e * e;
             }
-        } else if (a.mode == pc::APT_MODE_PILOT) {
+        } else if (MODE == pc::APT_MODE_PILOT) {
           if ((int64_t)s >= a.window_from)
             for (int b = threadIdx.x; b < k.Bc; b += blockDim.x) {
               const int64_t span = 3 * (int64_t)N;
@@ -1081,7 +1084,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
             }
         }
       }
-      if (a.mode != pc::APT_MODE_APT) continue;
+      if (MODE != pc::APT_MODE_APT) continue;
       const int64_t sweeps = s0 + (int64_t)(it + 1) * a.spp;
       best_update(a, k, sh, p, sweeps);
       PROF_MARK(2, pt);
@@ -1100,7 +1103,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   // every thread's last histogram / sum update lands before the write-back,
   // and colour 0 takes the last attempt's swaps
   __syncthreads();
-  if (a.mode == pc::APT_MODE_APT && a.n_iter > 0) {
+  if (MODE == pc::APT_MODE_APT && a.n_iter > 0) {
     const int lpar = (int)((t0 + a.n_iter - 1) & 1);   // parity of the last attempt
     uint32_t bmask = 0;
     if (k.split) {
@@ -1158,16 +1161,16 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     a.temp_of[P.buf_off + gb] = sh.temp_of[b];
     a.buf_of[P.buf_off + gb] = sh.buf_of[b];
     a.E[P.buf_off + gb] = sh.E[b];
-    if (a.mode == pc::APT_MODE_LADDER) {
+    if (MODE == pc::APT_MODE_LADDER) {
       a.sum1[P.buf_off + gb] = sh.sum1[b];
       a.sum2[P.buf_off + gb] = sh.sum2[b];
     }
   }
-  if (a.mode == pc::APT_MODE_PILOT)
+  if (MODE == pc::APT_MODE_PILOT)
     for (int i = threadIdx.x; i < k.T * a.n_bins; i += blockDim.x)
       atomicAdd(reinterpret_cast<unsigned long long *>(&a.hist[P.hist_off + i]),
                 (unsigned long long)sh.hist[i]);
-  if (a.mode == pc::APT_MODE_APT) {
+  if (MODE == pc::APT_MODE_APT) {
     // statistics: both CTAs of a split problem add theirs
     unsigned long long *st = reinterpret_cast<unsigned long long *>(a.stats + P.stat_off);
     const int npair = (k.T - 1) * k.A;
@@ -1222,20 +1225,10 @@ size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n
   return words * 4 + (size_t)N * 2 + 16;
 }
 
-int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st) {
-  if (n_cta <= 0) return PC_OK;
-  // raise the dynamic shared-memory limit once per device (never inside a
-  // stream capture: the first launch on a device happens at load time)
-  static size_t set_for[64] = {0};
-  int dev = 0;
-  PC_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(PC_EINVAL, "device index out of range");
-  if (smem > set_for[dev]) {
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    set_for[dev] = smem;
-  }
+template <int MODE>
+int apt_launch_mode(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st) {
   if (!a.split) {
-    apt_kernel<<<n_cta, tpb, smem, st>>>(a);
+    apt_kernel<MODE><<<n_cta, tpb, smem, st>>>(a);
   } else {
     // split problems: consecutive CTA pairs form one cluster
     cudaLaunchConfig_t cfg = {};
@@ -1250,10 +1243,35 @@ int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t s
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, apt_kernel, a));
+    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, apt_kernel<MODE>, a));
   }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
+}
+
+int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st) {
+  if (n_cta <= 0) return PC_OK;
+  // raise the dynamic shared-memory limit of every mode's kernel once per
+  // device (never inside a stream capture: the first launch on a device
+  // happens at load time)
+  static size_t set_for[64] = {0};
+  int dev = 0;
+  PC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(PC_EINVAL, "device index out of range");
+  if (smem > set_for[dev]) {
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_LADDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_PILOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set_for[dev] = smem;
+  }
+  switch (a.mode) {
+    case pc::APT_MODE_APT: return apt_launch_mode<pc::APT_MODE_APT>(a, n_cta, tpb, smem, st);
+    case pc::APT_MODE_LADDER: return apt_launch_mode<pc::APT_MODE_LADDER>(a, n_cta, tpb, smem, st);
+    case pc::APT_MODE_PILOT: return apt_launch_mode<pc::APT_MODE_PILOT>(a, n_cta, tpb, smem, st);
+    case pc::APT_MODE_ENERGY: return apt_launch_mode<pc::APT_MODE_ENERGY>(a, n_cta, tpb, smem, st);
+    default: return fail(PC_EINVAL, "unknown kernel mode");
+  }
 }
 
 #if PC_APT_PROFILE
