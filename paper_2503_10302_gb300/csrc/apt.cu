@@ -931,7 +931,7 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
 
 // MODE (pc::APT_MODE_*) is a template argument, so that each mode's kernel
 // carries only its own code (the run-time MODE equals it).
-template <int MODE>
+template <int MODE, bool SPLIT>
 __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int cta = blockIdx.x;
@@ -957,8 +957,8 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.g0 = a.cta_g0[cta];
   k.Gc = a.cta_gc[cta];
   k.Bc = min(8 * k.Gc, P.B - 8 * k.g0);
-  k.split = a.split;
-  k.rank = a.split ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+  k.split = SPLIT;
+  k.rank = SPLIT ? (int)cooperative_groups::this_cluster().block_rank() : 0;
   if (MODE == pc::APT_MODE_APT || MODE == pc::APT_MODE_ENERGY) {
     k.Gu = k.Gc / k.A;   // A is 1, 2 or 4
     k.Glp = k.Tp >> 3;
@@ -973,7 +973,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   const int N = P.N;
   // both CTAs of a split problem carve shared memory alike (rank 0 holds the
   // larger half), so that distributed-shared-memory addresses correspond
-  const int Gcarve = a.split ? k.A * ((k.Glp + 1) >> 1) : k.Gc, G8 = 8 * Gcarve;
+  const int Gcarve = SPLIT ? k.A * ((k.Glp + 1) >> 1) : k.Gc, G8 = 8 * Gcarve;
   const int64_t s0 = a.ctr[0], t0 = a.ctr[1];
   const bool icm = MODE == pc::APT_MODE_APT && a.icm;
   // carve shared memory
@@ -1002,7 +1002,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.swm = cur;                                   cur += 24;
   sh.gmap = reinterpret_cast<int32_t *>(cur);     cur += 8;
   sh.xch = reinterpret_cast<int32_t *>(cur);      cur += 24;
-  sh.stage = cur;                                 cur += a.split ? 512 : 0;
+  sh.stage = cur;                                 cur += SPLIT ? 512 : 0;
   sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 : 0;   // V, X, Xt
   sh.jn = reinterpret_cast<uint16_t *>(cur);
 
@@ -1228,7 +1228,7 @@ size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n
 template <int MODE>
 int apt_launch_mode(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st) {
   if (!a.split) {
-    apt_kernel<MODE><<<n_cta, tpb, smem, st>>>(a);
+    apt_kernel<MODE, false><<<n_cta, tpb, smem, st>>>(a);
   } else {
     // split problems: consecutive CTA pairs form one cluster
     cudaLaunchConfig_t cfg = {};
@@ -1243,7 +1243,7 @@ int apt_launch_mode(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStrea
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, apt_kernel<MODE>, a));
+    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, apt_kernel<MODE, true>, a));
   }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
@@ -1259,10 +1259,14 @@ int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t s
   PC_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(PC_EINVAL, "device index out of range");
   if (smem > set_for[dev]) {
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_LADDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_PILOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_LADDER, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_LADDER, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_PILOT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_PILOT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_ENERGY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_ENERGY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     set_for[dev] = smem;
   }
   switch (a.mode) {
