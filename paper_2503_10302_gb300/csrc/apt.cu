@@ -929,8 +929,9 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
   swap_words(k, sh, k.geo.H, 2 * k.geo.H, bmask, sh.stage + 256 * par);
 }
 
-// MODE (pc::APT_MODE_*) is a template argument, so that each mode's kernel
-// carries only its own code (the run-time MODE equals it).
+// MODE (pc::APT_MODE_*) and SPLIT (a cluster of two CTAs per problem) are
+// template arguments, so that each kernel carries only its own code (the
+// launcher picks the instantiation from a.mode and a.split).
 template <int MODE, bool SPLIT>
 __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
