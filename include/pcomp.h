@@ -25,8 +25,12 @@
  * code): Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed;
  * every draw is a counter (c0, c1, c2, c3) whose 8 16-bit halves feed 8
  * spins of one "group" of 8 replicas (or 8 Trotter slices); a spin's
- * 32-bit uniform is (main half << 16) | (refine half).  See the oracle's
- * header and DESIGN notes for the exact counters.
+ * 32-bit uniform is (main half << 16) | (refine half).  A lattice spin
+ * update draws the counter (j, sweep, (colour << 16) | group,
+ * (entry << 8) | tag) with j = lin >> 1 the site's index within its
+ * checkerboard colour; a swap of pair (r, r+1), label a at attempt t draws
+ * (r, t, a, (entry << 8) | 4) and an ICM move of pair p at temperature r
+ * draws (r, t, p, (entry << 8) | 5).
  */
 #ifndef PCOMP_H
 #define PCOMP_H

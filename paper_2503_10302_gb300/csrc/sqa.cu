@@ -18,6 +18,8 @@
 // Philox4x32-10 call supplies the 8 16-bit uniforms.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -562,14 +564,40 @@ constexpr size_t kNoallocBytes = kNoallocJnegBytes + kNoallocTableBytes;
 
 static __device__ __align__(256) unsigned char g_sqa_noalloc_scratch[kNoallocBytes];
 
+// Host data reaches the scratch array as kernel parameters, which the
+// launch copies by value: no host buffer has to outlive the call and no
+// pageable copy is issued.  One chunk carries 12 KiB (a host stack buffer).
+constexpr int kStageWords = 3072;
+struct StageChunk {
+  uint32_t off;                 // destination offset in 32-bit words
+  uint32_t n;                   // words carried (<= kStageWords)
+  uint32_t w[kStageWords];
+};
+
+__global__ void noalloc_stage_kernel(uint32_t *dst, const __grid_constant__ StageChunk c) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n; i += gridDim.x * blockDim.x)
+    dst[c.off + i] = c.w[i];
+}
+
+int stage_words(uint32_t *dst, StageChunk &c, cudaStream_t st) {
+  if (c.n == 0) return PC_OK;
+  noalloc_stage_kernel<<<8, 512, 0, st>>>(dst, c);
+  PC_CUDA_TRY(cudaGetLastError());
+  return PC_OK;
+}
+
 // Device address of the scratch array, looked up once per device (with that
-// device current).  The symbol's name is a host-side stand-in, never a
-// device address, so only this pointer is handed to kernels.
+// device current) under a lock, so that host threads making their first
+// calls at the same time do not race.  The symbol's name is a host-side
+// stand-in, never a device address, so only this pointer is handed to
+// kernels.
 constexpr int kMaxDevices = 64;
-static unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_lock;
+unsigned char *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 int noalloc_scratch(int device, unsigned char **out) {
   if (device < 0 || device >= kMaxDevices) return pc::fail(PC_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_scratch_lock);
   if (!g_scratch_ptr[device]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_sqa_noalloc_scratch);
@@ -607,12 +635,15 @@ extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, co
   if ((rc = noalloc_scratch(device, &scratch))) return rc;
   if (R == 0) return PC_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  uint32_t *words = reinterpret_cast<uint32_t *>(scratch);
+  StageChunk chunk_buf;
+  StageChunk *chunk = &chunk_buf;
 
-  // couplings: one 16-bit word per site (periodic: no absent bonds), staged
-  // through a stack buffer
+  // couplings: one 16-bit word per site (periodic: no absent bonds), two
+  // per staged 32-bit word (N is even)
   {
-    uint16_t jn[kNoallocJnegBytes / 2];
     const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2];
+    uint16_t *jn = reinterpret_cast<uint16_t *>(chunk->w);
     for (int s = 0; s < lat.N; ++s) {
       const int x = s % Lx, y = (s / Lx) % Ly, z = s / (Lx * Ly);
       const int xm = (x + Lx - 1) % Lx + Lx * (y + Ly * z);
@@ -625,24 +656,27 @@ extern "C" int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, co
         if (j6[d] < 0) m |= (uint16_t)(1u << d);
       jn[s] = m;
     }
-    PC_CUDA_TRY(cudaMemcpyAsync(scratch, jn, (size_t)lat.N * 2, cudaMemcpyHostToDevice, st));
+    chunk->off = 0;
+    chunk->n = (uint32_t)lat.N / 2;
+    if ((rc = stage_words(words, *chunk, st))) return rc;
   }
-  // per-sweep threshold tables, 64 sweeps per staged copy
+  // per-sweep threshold tables, kStageWords / kSqaTab sweeps per chunk
   {
-    constexpr int kChunk = 64;
     constexpr int W = pc::kSqaTab;
-    uint32_t tab[kChunk * W];
+    constexpr int kSweepsPerChunk = kStageWords / W;
     const double beta_eff = 1.0 / ((double)P * T);
-    for (int s0 = 0; s0 < n_sweeps; s0 += kChunk) {
-      const int ns = (n_sweeps - s0 < kChunk) ? n_sweeps - s0 : kChunk;
+    for (int s0 = 0; s0 < n_sweeps; s0 += kSweepsPerChunk) {
+      const int ns = (n_sweeps - s0 < kSweepsPerChunk) ? n_sweeps - s0 : kSweepsPerChunk;
+      uint32_t *tab = chunk->w;
       for (int k = 0; k < ns; ++k) {
         const int32_t jq = pc_jperp_q(gamma[s0 + k], P, T);
         for (int e = 0; e < W; ++e) tab[W * k + e] = 0u;
         for (int m = 0; m < 3; ++m)
           for (int e = 0; e < 13; ++e) tab[W * k + e + 13 * m] = sqa_threshold(beta_eff, e - 6, jq, 2 * m - 2);
       }
-      PC_CUDA_TRY(cudaMemcpyAsync(scratch + kNoallocJnegBytes + (size_t)s0 * W * 4, tab,
-                                  (size_t)ns * W * 4, cudaMemcpyHostToDevice, st));
+      chunk->off = (uint32_t)(kNoallocJnegBytes / 4 + (size_t)s0 * W);
+      chunk->n = (uint32_t)(ns * W);
+      if ((rc = stage_words(words, *chunk, st))) return rc;
     }
   }
   SqaArgs a;

@@ -37,24 +37,62 @@ def _reference(pc, dims, J, P, T, gamma, R, seed, run0):
     return E
 
 
+def _device_memory():
+    import torch
+    free, _ = torch.cuda.mem_get_info(0)
+    return free, torch.cuda.memory_allocated(0)
+
+
 def test_noalloc_matches_allocating_entry_point_on_consecutive_calls(pc):
+    """Two consecutive calls that share the static scratch, compared with the
+    allocating entry point; device memory (free bytes and torch's count)
+    must not change across them."""
     import torch
     T = 0.05
+    cases = []
     for dims, P, R, S, seed, run0 in CALLS:
         J = W.ea_couplings(dims, W.SEED_INSTANCES, seed)
         gamma = W.linear_gamma_schedule(S)
         E_dev = torch.full((R, P), 12345, dtype=torch.int32, device="cuda:0")
         best_dev = torch.full((R, 2), -7, dtype=torch.int32, device="cuda:0")
-        torch.cuda.synchronize()
+        cases.append((dims, P, R, seed, run0, J, gamma, E_dev, best_dev))
+    # warm-up: the first call on the device looks up the scratch address and
+    # loads the kernels (lazy module loading may take device memory then)
+    for dims, P, R, seed, run0, J, gamma, E_dev, best_dev in cases:
         pc.pc_sqa_anneal_noalloc(0, 0, seed, dims, J, P, T, gamma, R, run0, E_dev.data_ptr(),
                                  best_dev.data_ptr())
-        torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    for _, _, _, _, _, _, _, E_dev, best_dev in cases:
+        E_dev.fill_(12345)
+        best_dev.fill_(-7)
+    torch.cuda.synchronize()
+    mem0 = _device_memory()
+    for dims, P, R, seed, run0, J, gamma, E_dev, best_dev in cases:
+        pc.pc_sqa_anneal_noalloc(0, 0, seed, dims, J, P, T, gamma, R, run0, E_dev.data_ptr(),
+                                 best_dev.data_ptr())
+    torch.cuda.synchronize()
+    assert _device_memory() == mem0
+    for dims, P, R, seed, run0, J, gamma, E_dev, best_dev in cases:
         E = E_dev.cpu().numpy().astype(np.int64)
         best = best_dev.cpu().numpy()
         E_ref = _reference(pc, dims, J, P, T, gamma, R, seed, run0)
         assert np.array_equal(E, E_ref)
         assert np.array_equal(best[:, 0], E_ref.min(axis=1))
         assert np.array_equal(best[:, 1], E_ref.argmin(axis=1))
+
+
+def test_noalloc_many_chunks_of_tables(pc):
+    """The longest schedule the scratch holds (10240 sweeps, staged in many
+    chunks) on a small lattice, against the allocating entry point."""
+    import torch
+    dims, P, R, S, seed = (4, 4, 4), 16, 3, 10240, 3
+    J = W.ea_couplings(dims, W.SEED_INSTANCES, 77)
+    gamma = W.linear_gamma_schedule(S)
+    E_dev = torch.zeros((R, P), dtype=torch.int32, device="cuda:0")
+    pc.pc_sqa_anneal_noalloc(0, 0, seed, dims, J, P, 0.05, gamma, R, 0, E_dev.data_ptr(), 0)
+    torch.cuda.synchronize()
+    E_ref = _reference(pc, dims, J, P, 0.05, gamma, R, seed, 0)
+    assert np.array_equal(E_dev.cpu().numpy().astype(np.int64), E_ref)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(pc):
