@@ -366,6 +366,24 @@ int pc_gsqa_anneal(pc_ctx *ctx, int n, const int32_t *row_ptr, const int32_t *co
                    int n_sweeps, const double *gamma, int R, uint32_t run0, int64_t *E_out,
                    int8_t *spins_out);
 
+/* Judge of beta ladders by their swap-acceptance profile.  For each of
+ * n_inst periodic lattices (dims [n][3], J concatenated) with the ladder
+ * betas [n][n_temps] (strictly increasing), runs the first probe_attempts
+ * APT attempts (one sweep, ICM when n_labels >= 2, the swaps; Algorithm S2)
+ * on a scratch batch whose problem i draws with entry entry0 + i, exactly as
+ * a pc_apt_load of that ladder followed by pc_apt_run would (the loaded APT
+ * batch is not touched).  acc_out [n][n_temps-1] (nullable) receives each
+ * pair's acceptance pooled over the labels, accepts / attempts (-1 for a
+ * pair the probe never attempted); pass_out [n] is 1 iff every attempted
+ * pair reaches acc_floor, i.e. accepts >= acc_floor * attempts in double.
+ * The adaptive procedure aims at a flat acceptance of erfc(alpha / 2)
+ * (about 0.38 at the paper's alpha = 1.25; Supplementary "Temperature
+ * profile and swap acceptance rate in APT"), so half of it is a natural
+ * floor. */
+int pc_ladder_judge(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+                    int n_temps, const double *betas, int n_labels, int probe_attempts, double acc_floor,
+                    double *acc_out, int32_t *pass_out);
+
 /* MLP 259 -> 256 -> 256 -> 256 -> 32 (ReLU hidden), head
  * beta_k = beta_min + sum_{m<=k} softplus(o_m), loss = mean (beta - y)^2,
  * fp32 on the GPU, Adam.  W[l] is [out][in] row-major, b[l] is [out]. */
@@ -386,6 +404,49 @@ int pc_mlp_train_step(pc_mlp *m, int batch, const float *X, const float *Y, floa
 int pc_mlp_train_step_dev(pc_mlp *m, int batch, const float *X_dev, const float *Y_dev,
                           float lr, float *loss_dev);
 int pc_mlp_get_params(pc_mlp *m, float *const *W, float *const *b);
+/* Weights file of the network: the bytes "PCMLP001", the five layer widths
+ * (int32), beta_min (fp32), then W[l] and b[l] of each layer (fp32,
+ * little-endian).  pc_mlp_load creates a network on ctx from such a file
+ * (PC_EINVAL if the file is missing, truncated or of another shape). */
+int pc_mlp_save(pc_mlp *m, const char *path);
+int pc_mlp_load(pc_ctx *ctx, const char *path, pc_mlp **out);
+
+/* Learned beta ladder: the network above in place of the adaptive
+ * procedure of Algorithm S2's preprocessing (Methods "APT details"), with
+ * that procedure kept as judge and fallback.  The paper has no learned
+ * component; it observes that ladders of one size are nearly identical
+ * across instances (Fig. S12), which makes them predictable from cheap
+ * features.  Options: */
+typedef struct {
+  const double *pilot_betas;  /* [4] pilot temperatures, those the network was trained with */
+  int pilot_chains;           /* chains per pilot temperature (4 * pilot_chains <= 64) */
+  int pilot_sweeps;           /* pilot sweeps; energies of sweeps >= pilot_burn are counted */
+  int pilot_burn;
+  int probe_attempts;         /* judge's APT attempts; 0: no judge and no fallback */
+  int probe_labels;           /* labels per temperature of the probe (1, 2 or 4) */
+  double acc_floor;           /* least pooled swap acceptance of every pair (pc_ladder_judge) */
+  double beta0, alpha;        /* fallback: pc_adaptive_ladder with these settings, */
+  int n_chains, sweeps, tail; /* resampled to 32 points (pc_resample_ladder) */
+  double tol;
+  int max_len;
+} pc_learned_opts;
+/* For each of n_inst periodic lattices (dims [n][3], J concatenated; the
+ * instance i draws with entry entry0 + i), all on the device:
+ *   1. pilot histograms as pc_pilot_hist (4 temperatures, 64 bins);
+ *   2. features: cbrt(N)/16, the fraction of J > 0, the fraction of
+ *      frustrated plaquettes, and each pilot temperature's histogram divided
+ *      by its total (fp32);
+ *   3. the network m (created on ctx) gives 32 betas;
+ *   4. ladder k becomes max(b_0, 0), then max(b_k, beta_{k-1} + 1e-6), in
+ *      double, so that it is strictly increasing;
+ *   5. with probe_attempts > 0, pc_ladder_judge of these ladders
+ *      (probe_labels, probe_attempts, acc_floor; acc_out [n][31] nullable);
+ *   6. every rejected instance falls back to pc_adaptive_ladder (same entry
+ *      id) resampled to 32 points, and fallback_out [n] (nullable) is 1.
+ * beta_out [n][32] receives the ladders (host). */
+int pc_learned_ladder(pc_ctx *ctx, pc_mlp *m, int n_inst, const int32_t *dims, const int8_t *J,
+                      uint32_t entry0, const pc_learned_opts *opt, double *beta_out, double *acc_out,
+                      int32_t *fallback_out);
 
 #ifdef __cplusplus
 }

@@ -882,16 +882,16 @@ int pc_apt_get_swap_table(pc_ctx *c, int inst, int pair, uint32_t *out, int max_
 }
 
 // ------------------------------------------------------------------ ladder
-int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
-                       double beta0, double alpha, int n_chains, int sweeps, int tail, double tol,
-                       int max_len, double *beta_out, double *sigma_out, int32_t *len_out,
-                       int32_t *converged_out) try {
-  if (!c || !dims || !J || !beta_out || !len_out) return fail(PC_EINVAL, "NULL argument");
-  if (n_inst < 1 || n_chains < 1 || n_chains > 4096 || sweeps < 1 || tail < 2 || tail > sweeps ||
-      max_len < 1 || !(beta0 > 0.0) || !(alpha > 0.0))
-    return fail(PC_EINVAL, "bad ladder parameters");
-  if ((uint64_t)entry0 + (uint64_t)n_inst > (1ull << 24)) return fail(PC_EINVAL, "entry ids must be < 2^24");
-  if ((int64_t)sweeps * max_len > 0xFFFFFFFFll) return fail(PC_EINVAL, "sweep counter would exceed 2^32");
+}  // extern "C"
+
+namespace {
+
+// The adaptive beta ladder of Algorithm S2's preprocessing for n_inst
+// lattices, instance i drawing with Philox entry ents[i]; outputs as
+// pc_adaptive_ladder.  Arguments are checked by the callers.
+int adaptive_impl(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, const uint32_t *ents,
+                  double beta0, double alpha, int n_chains, int sweeps, int tail, double tol, int max_len,
+                  double *beta_out, double *sigma_out, int32_t *len_out, int32_t *converged_out) {
   PC_CUDA_TRY(cudaSetDevice(c->device));
   std::vector<ProbSpec> specs((size_t)n_inst);
   size_t joff = 0;
@@ -906,7 +906,7 @@ int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t 
     s.Tp = 1;
     s.A = 1;
     s.B = n_chains;
-    s.ent = entry0 + (uint32_t)i;
+    s.ent = ents[i];
     s.beta.assign(1, beta0);
     s.temp_of.assign((size_t)n_chains, 0);
     s.swaps = false;
@@ -977,6 +977,33 @@ int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t 
     if (converged_out) converged_out[i] = conv[(size_t)i];
   }
   return PC_OK;
+}
+
+int check_ladder_params(int n_chains, int sweeps, int tail, int max_len, double beta0, double alpha) {
+  if (n_chains < 1 || n_chains > 4096 || sweeps < 1 || tail < 2 || tail > sweeps || max_len < 1 ||
+      !(beta0 > 0.0) || !(alpha > 0.0))
+    return fail(PC_EINVAL, "bad ladder parameters");
+  if ((int64_t)sweeps * max_len > 0xFFFFFFFFll) return fail(PC_EINVAL, "sweep counter would exceed 2^32");
+  return PC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pc_adaptive_ladder(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+                       double beta0, double alpha, int n_chains, int sweeps, int tail, double tol,
+                       int max_len, double *beta_out, double *sigma_out, int32_t *len_out,
+                       int32_t *converged_out) try {
+  if (!c || !dims || !J || !beta_out || !len_out) return fail(PC_EINVAL, "NULL argument");
+  if (n_inst < 1) return fail(PC_EINVAL, "bad ladder parameters");
+  int rc = check_ladder_params(n_chains, sweeps, tail, max_len, beta0, alpha);
+  if (rc) return rc;
+  if ((uint64_t)entry0 + (uint64_t)n_inst > (1ull << 24)) return fail(PC_EINVAL, "entry ids must be < 2^24");
+  std::vector<uint32_t> ents((size_t)n_inst);
+  for (int i = 0; i < n_inst; ++i) ents[(size_t)i] = entry0 + (uint32_t)i;
+  return adaptive_impl(c, n_inst, dims, J, ents.data(), beta0, alpha, n_chains, sweeps, tail, tol, max_len,
+                       beta_out, sigma_out, len_out, converged_out);
 } catch (...) {
   return pc::fail_exception();
 }
@@ -1000,16 +1027,25 @@ int pc_resample_ladder(const double *beta, int len, int n, double *out) try {
 }
 
 // ------------------------------------------------------------------ pilot
-int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
-                  int n_beta, const double *betas, int chains_per_beta, int sweeps, int burn, int n_bins,
-                  int64_t *counts) try {
-  if (!c || !dims || !J || !betas || !counts) return fail(PC_EINVAL, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+int check_pilot_params(int n_inst, uint32_t entry0, int n_beta, const double *betas, int chains_per_beta,
+                       int sweeps, int burn, int n_bins) {
   if (n_inst < 1 || n_beta < 1 || chains_per_beta < 1 || n_beta * chains_per_beta > 64 || sweeps < 1 ||
       burn < 0 || burn >= sweeps || n_bins < 1 || n_bins > 256 || n_beta * n_bins > 2048)
     return fail(PC_EINVAL, "bad pilot parameters (n_beta * chains_per_beta <= 64)");
   if ((uint64_t)entry0 + (uint64_t)n_inst > (1ull << 24)) return fail(PC_EINVAL, "entry ids must be < 2^24");
   for (int t = 0; t < n_beta; ++t)
     if (!(betas[t] >= 0.0) || !std::isfinite(betas[t])) return fail(PC_EINVAL, "betas must be finite and >= 0");
+  return PC_OK;
+}
+
+// Runs the pilot chains of every instance on the device; the histograms stay
+// in bt.d_hist ([n][n_beta][n_bins] at each problem's hist_off).
+int pilot_run(pc_ctx *c, Batch &bt, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+              int n_beta, const double *betas, int chains_per_beta, int sweeps, int burn, int n_bins) {
   PC_CUDA_TRY(cudaSetDevice(c->device));
   std::vector<ProbSpec> specs((size_t)n_inst);
   size_t joff = 0;
@@ -1029,7 +1065,6 @@ int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, u
     s.swaps = false;
     joff += (size_t)s.lat.N;
   }
-  Batch bt;
   int rc = build_batch(c, bt, specs, n_bins);
   if (rc) return rc;
   if ((rc = schedule(c, bt, {}, APT_MODE_PILOT, 0, n_bins))) return rc;
@@ -1044,7 +1079,22 @@ int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, u
   a.n_bins = n_bins;
   a.tag_main = 10;   // TAG_PIL_SWEEP
   a.tag_ref = 11;    // TAG_PIL_REFINE
-  if ((rc = apt_launch(a, bt.n_cta, bt.tpb, bt.smem, c->stream))) return rc;
+  return apt_launch(a, bt.n_cta, bt.tpb, bt.smem, c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pc_pilot_hist(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+                  int n_beta, const double *betas, int chains_per_beta, int sweeps, int burn, int n_bins,
+                  int64_t *counts) try {
+  if (!c || !dims || !J || !betas || !counts) return fail(PC_EINVAL, "NULL argument");
+  int rc = check_pilot_params(n_inst, entry0, n_beta, betas, chains_per_beta, sweeps, burn, n_bins);
+  if (rc) return rc;
+  Batch bt;
+  if ((rc = pilot_run(c, bt, n_inst, dims, J, entry0, n_beta, betas, chains_per_beta, sweeps, burn, n_bins)))
+    return rc;
   PC_CUDA_TRY(cudaMemcpyAsync(counts, bt.d_hist.p, (size_t)n_inst * n_beta * n_bins * 8,
                               cudaMemcpyDeviceToHost, c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1077,6 +1127,215 @@ int pc_instance_features(const int32_t *dims, const int8_t *J, double *out3) try
   out3[0] = std::cbrt((double)N) / 16.0;
   out3[1] = (double)pos / (3.0 * N);
   out3[2] = (double)frust / (3.0 * N);
+  return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
+}
+
+// ------------------------------------------------------- learned ladder
+}  // extern "C"
+
+namespace {
+
+constexpr int kLearnedLen = 32;        // ladder length of the network's head
+constexpr int kLearnedBins = 64;       // pilot histogram bins of its input
+constexpr int kLearnedBetas = 4;       // pilot temperatures of its input
+constexpr double kLadderGap = 1e-6;    // least gap of a predicted ladder
+
+// Probe of given ladders: the first `attempts` APT attempts of one sweep,
+// ICM (n_labels >= 2) and the swaps, on a scratch batch whose problem i
+// draws with entry entry0 + i (the loaded APT batch is not touched).
+// att / acc [n][T-1]: swap attempts and accepts of each pair summed over the
+// labels.
+int probe_impl(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0, int T,
+               const double *betas, int n_labels, int attempts, std::vector<int64_t> &att,
+               std::vector<int64_t> &acc) {
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  std::vector<ProbSpec> specs((size_t)n_inst);
+  size_t joff = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    ProbSpec &s = specs[(size_t)i];
+    int rc = check_lattice(dims + 3 * i, J + 3 * joff, &s.lat);
+    if (rc) return rc;
+    s.J = J + 3 * joff;
+    s.T = T;
+    s.A = n_labels;
+    s.Tp = 8 * ((T + 7) / 8);
+    s.B = s.Tp * n_labels;
+    s.ent = entry0 + (uint32_t)i;
+    s.beta.assign(betas + (size_t)i * T, betas + (size_t)(i + 1) * T);
+    for (int t = 0; t < T; ++t) {
+      if (!(s.beta[(size_t)t] >= 0.0) || !std::isfinite(s.beta[(size_t)t]))
+        return fail(PC_EINVAL, "betas must be finite and >= 0");
+      if (t > 0 && !(s.beta[(size_t)t] > s.beta[(size_t)t - 1]))
+        return fail(PC_EINVAL, "betas must be strictly increasing");
+    }
+    s.temp_of.resize((size_t)s.B);
+    for (int b = 0; b < s.B; ++b) s.temp_of[(size_t)b] = (b % s.Tp < s.T) ? b % s.Tp : 0;
+    s.swaps = true;
+    joff += (size_t)s.lat.N;
+  }
+  Batch bt;
+  const int icm = n_labels >= 2 ? 1 : 0;
+  int rc = build_batch(c, bt, specs, 0);
+  if (rc) return rc;
+  if ((rc = schedule(c, bt, {}, APT_MODE_APT, icm, 0))) return rc;
+  AptArgs a = base_args(c, bt);
+  a.tag_init = 1;   // TAG_APT_INIT
+  if ((rc = apt_init_launch(a, n_inst, max_words(bt), c->stream))) return rc;
+  a.mode = APT_MODE_ENERGY;
+  if ((rc = apt_launch(a, bt.n_cta, bt.tpb, bt.smem, c->stream))) return rc;
+  for (int done = 0; done < attempts;) {
+    const int n = std::min(kChunkAttempts, attempts - done);
+    a = base_args(c, bt);
+    a.mode = APT_MODE_APT;
+    a.n_iter = n;
+    a.spp = 1;
+    a.icm = icm;
+    a.tag_main = 2;   // TAG_APT_SWEEP
+    a.tag_ref = 3;    // TAG_APT_REFINE
+    if ((rc = apt_launch(a, bt.n_cta, bt.tpb, bt.smem, c->stream))) return rc;
+    if ((rc = apt_advance_launch(bt.d_ctr.p, n, n, c->stream))) return rc;
+    done += n;
+  }
+  std::vector<int64_t> st(bt.d_stats.n);
+  PC_CUDA_TRY(cudaMemcpyAsync(st.data(), bt.d_stats.p, st.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  att.assign((size_t)n_inst * (T - 1), 0);
+  acc.assign((size_t)n_inst * (T - 1), 0);
+  for (int i = 0; i < n_inst; ++i) {
+    const AptProbDev &P = bt.prob[(size_t)i];
+    const int np = (T - 1) * n_labels;
+    for (int r = 0; r + 1 < T; ++r)
+      for (int l = 0; l < n_labels; ++l) {
+        att[(size_t)i * (T - 1) + r] += st[P.stat_off + (size_t)r * n_labels + l];
+        acc[(size_t)i * (T - 1) + r] += st[P.stat_off + (size_t)np + (size_t)r * n_labels + l];
+      }
+  }
+  return PC_OK;
+}
+
+// Judge of a ladder by its swap-acceptance profile: the pooled acceptance
+// acc/att of every pair that the probe attempted must reach acc_floor.
+// acc_out [T-1] receives acc/att (-1 for a pair never attempted).
+bool judge_pass(const int64_t *att, const int64_t *acc, int T, double acc_floor, double *acc_out) {
+  bool pass = true;
+  for (int r = 0; r + 1 < T; ++r) {
+    if (att[r] <= 0) {
+      if (acc_out) acc_out[r] = -1.0;
+      continue;
+    }
+    if (acc_out) acc_out[r] = (double)acc[r] / (double)att[r];
+    if ((double)acc[r] < acc_floor * (double)att[r]) pass = false;
+  }
+  return pass;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pc_ladder_judge(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0, int n_temps,
+                    const double *betas, int n_labels, int probe_attempts, double acc_floor, double *acc_out,
+                    int32_t *pass_out) try {
+  if (!c || !dims || !J || !betas || !pass_out) return fail(PC_EINVAL, "NULL argument");
+  if (n_inst < 1 || n_temps < 2 || n_temps > 32 || probe_attempts < 1 ||
+      !(n_labels == 1 || n_labels == 2 || n_labels == 4) || 8 * ((n_temps + 7) / 8) * n_labels > 128 ||
+      !std::isfinite(acc_floor))
+    return fail(PC_EINVAL, "bad judge parameters");
+  if ((uint64_t)entry0 + (uint64_t)n_inst > (1ull << 24)) return fail(PC_EINVAL, "entry ids must be < 2^24");
+  std::vector<int64_t> att, acc;
+  int rc = probe_impl(c, n_inst, dims, J, entry0, n_temps, betas, n_labels, probe_attempts, att, acc);
+  if (rc) return rc;
+  for (int i = 0; i < n_inst; ++i)
+    pass_out[i] = judge_pass(att.data() + (size_t)i * (n_temps - 1), acc.data() + (size_t)i * (n_temps - 1),
+                             n_temps, acc_floor, acc_out ? acc_out + (size_t)i * (n_temps - 1) : nullptr)
+                      ? 1
+                      : 0;
+  return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
+}
+
+int pc_learned_ladder(pc_ctx *c, pc_mlp *m, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+                      const pc_learned_opts *o, double *beta_out, double *acc_out, int32_t *fallback_out) try {
+  if (!c || !m || !dims || !J || !o || !o->pilot_betas || !beta_out) return fail(PC_EINVAL, "NULL argument");
+  if (mlp_context(m) != c) return fail(PC_EINVAL, "the network must belong to this context");
+  if (n_inst < 1) return fail(PC_EINVAL, "n_inst must be >= 1");
+  int rc = check_pilot_params(n_inst, entry0, kLearnedBetas, o->pilot_betas, o->pilot_chains, o->pilot_sweeps,
+                              o->pilot_burn, kLearnedBins);
+  if (rc) return rc;
+  const bool judge = o->probe_attempts > 0;
+  if (judge) {
+    if (!(o->probe_labels == 1 || o->probe_labels == 2 || o->probe_labels == 4) || !std::isfinite(o->acc_floor))
+      return fail(PC_EINVAL, "bad probe parameters");
+    if ((rc = check_ladder_params(o->n_chains, o->sweeps, o->tail, o->max_len, o->beta0, o->alpha))) return rc;
+  }
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  // (1) pilot histograms, (2) features, (3) the network, (4) monotone ladders
+  {
+    Batch bt;
+    if ((rc = pilot_run(c, bt, n_inst, dims, J, entry0, kLearnedBetas, o->pilot_betas, o->pilot_chains,
+                        o->pilot_sweeps, o->pilot_burn, kLearnedBins)))
+      return rc;
+    float *X = nullptr;
+    if ((rc = mlp_input(m, n_inst, &X))) return rc;
+    if ((rc = learned_features_launch(bt.d_prob.p, n_inst, bt.d_jneg.p, bt.d_hist.p, kLearnedBetas, kLearnedBins,
+                                      X, 3 + kLearnedBetas * kLearnedBins, st)))
+      return rc;
+    const float *bf = nullptr;
+    if ((rc = mlp_forward_input(m, n_inst, &bf))) return rc;
+    DevBuf<double> d_beta;
+    if ((rc = d_beta.alloc((size_t)n_inst * kLearnedLen))) return rc;
+    if ((rc = ladder_monotone_launch(n_inst, kLearnedLen, bf, kLadderGap, d_beta.p, st))) return rc;
+    PC_CUDA_TRY(cudaMemcpyAsync(beta_out, d_beta.p, (size_t)n_inst * kLearnedLen * 8, cudaMemcpyDeviceToHost, st));
+    PC_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (fallback_out)
+    for (int i = 0; i < n_inst; ++i) fallback_out[i] = 0;
+  if (!judge) {
+    if (acc_out)
+      for (size_t k = 0; k < (size_t)n_inst * (kLearnedLen - 1); ++k) acc_out[k] = -1.0;
+    return PC_OK;
+  }
+  // (5) the judge: a short probe of every predicted ladder
+  std::vector<int64_t> att, acc;
+  if ((rc = probe_impl(c, n_inst, dims, J, entry0, kLearnedLen, beta_out, o->probe_labels, o->probe_attempts, att,
+                       acc)))
+    return rc;
+  std::vector<int> fail_idx;
+  for (int i = 0; i < n_inst; ++i) {
+    const size_t off = (size_t)i * (kLearnedLen - 1);
+    if (!judge_pass(att.data() + off, acc.data() + off, kLearnedLen, o->acc_floor, acc_out ? acc_out + off : nullptr))
+      fail_idx.push_back(i);
+  }
+  if (fail_idx.empty()) return PC_OK;
+  // (6) fallback: the adaptive procedure for the instances the judge
+  // rejected (entry ids unchanged), resampled to the network's length
+  std::vector<size_t> joff((size_t)n_inst + 1, 0);
+  for (int i = 0; i < n_inst; ++i) joff[(size_t)i + 1] = joff[(size_t)i] + (size_t)dims[3 * i] * dims[3 * i + 1] * dims[3 * i + 2];
+  const int nf = (int)fail_idx.size();
+  std::vector<int32_t> fd;
+  std::vector<int8_t> fJ;
+  std::vector<uint32_t> fe;
+  for (int i : fail_idx) {
+    fd.insert(fd.end(), dims + 3 * i, dims + 3 * i + 3);
+    fJ.insert(fJ.end(), J + 3 * joff[(size_t)i], J + 3 * joff[(size_t)i + 1]);
+    fe.push_back(entry0 + (uint32_t)i);
+  }
+  std::vector<double> lad((size_t)nf * o->max_len);
+  std::vector<int32_t> len((size_t)nf);
+  if ((rc = adaptive_impl(c, nf, fd.data(), fJ.data(), fe.data(), o->beta0, o->alpha, o->n_chains, o->sweeps,
+                          o->tail, o->tol, o->max_len, lad.data(), nullptr, len.data(), nullptr)))
+    return rc;
+  for (int k = 0; k < nf; ++k) {
+    const int i = fail_idx[(size_t)k];
+    if ((rc = pc_resample_ladder(lad.data() + (size_t)k * o->max_len, len[(size_t)k], kLearnedLen,
+                                 beta_out + (size_t)i * kLearnedLen)))
+      return rc;
+    if (fallback_out) fallback_out[i] = 1;
+  }
   return PC_OK;
 } catch (...) {
   return pc::fail_exception();

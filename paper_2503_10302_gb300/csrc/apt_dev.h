@@ -61,4 +61,11 @@ int apt_init_launch(const AptArgs &a, int n_prob, int max_words, cudaStream_t st
 // ctr[0] += sweeps, ctr[1] += swaps (stream-ordered after a launch).
 int apt_advance_launch(int64_t *ctr, int64_t sweeps, int64_t swaps, cudaStream_t st);
 
+// Learned-ladder steps (learned.cu): features [n_inst][ldx] fp32 of a pilot
+// batch (instance features, then the normalised histograms of its n_beta
+// temperatures), and strictly increasing double ladders from fp32 ones.
+int learned_features_launch(const AptProbDev *prob, int n_inst, const uint16_t *jneg, const int64_t *hist,
+                            int n_beta, int n_bins, float *X, int ldx, cudaStream_t st);
+int ladder_monotone_launch(int n, int len, const float *b, double gap, double *out, cudaStream_t st);
+
 }  // namespace pc

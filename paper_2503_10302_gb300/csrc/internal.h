@@ -67,6 +67,14 @@ struct SqaArgs {
 size_t sqa_smem_bytes(int N, int P);
 int sqa_launch(const SqaArgs &a, int R, cudaStream_t st);
 
+// ---------------------------------------------------------------- MLP (mlp.cu)
+pc_ctx *mlp_context(pc_mlp *m);
+// The network's device input buffer [batch][259], grown as needed.
+int mlp_input(pc_mlp *m, int batch, float **X_dev);
+// Forward pass of the input buffer; *beta_dev receives [batch][32] fp32
+// ladders on the device, valid until the next call on m.
+int mlp_forward_input(pc_mlp *m, int batch, const float **beta_dev);
+
 // ---------------------------------------------------------------- Philox check
 int philox_launch(const uint32_t *ctr, uint32_t *out, int64_t n, uint32_t k0, uint32_t k1,
                   cudaStream_t st);

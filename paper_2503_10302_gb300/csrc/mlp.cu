@@ -10,7 +10,9 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "ctx.h"
@@ -276,6 +278,35 @@ int adam(pc_mlp *mm, float lr) {
 
 }  // namespace
 
+namespace pc {
+
+pc_ctx *mlp_context(pc_mlp *mm) { return mm->ctx; }
+
+int mlp_input(pc_mlp *mm, int batch, float **X_dev) {
+  int rc = ensure_batch(mm, batch);
+  if (rc) return rc;
+  *X_dev = mm->X.p;
+  return PC_OK;
+}
+
+int mlp_forward_input(pc_mlp *mm, int batch, const float **beta_dev) {
+  int rc = ensure_batch(mm, batch);
+  if (rc) return rc;
+  if ((rc = forward(mm, batch, mm->X.p, mm->beta.p))) return rc;
+  *beta_dev = mm->beta.p;
+  return PC_OK;
+}
+
+}  // namespace pc
+
+namespace {
+
+// Weights file: magic, the five layer widths, beta_min, then W[l] ([out][in]
+// row-major) and b[l] of every layer as little-endian fp32.
+constexpr char kMlpMagic[8] = {'P', 'C', 'M', 'L', 'P', '0', '0', '1'};
+
+}  // namespace
+
 extern "C" {
 
 int pc_mlp_create(pc_ctx *c, pc_mlp **out, const float *const *W, const float *const *b, float beta_min) try {
@@ -413,6 +444,57 @@ int pc_mlp_get_params(pc_mlp *mm, float *const *W, float *const *b) try {
     if (b && b[k]) std::memcpy(b[k], h.data() + mm->b_off[k], sizeof(float) * kDims[k + 1]);
   }
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
+}
+
+int pc_mlp_save(pc_mlp *mm, const char *path) try {
+  if (!mm || !path) return fail(PC_EINVAL, "NULL argument");
+  PC_CUDA_TRY(cudaSetDevice(mm->ctx->device));
+  std::vector<float> h(mm->n_params);
+  PC_CUDA_TRY(cudaMemcpyAsync(h.data(), mm->params.p, h.size() * 4, cudaMemcpyDeviceToHost, mm->ctx->stream));
+  PC_CUDA_TRY(cudaStreamSynchronize(mm->ctx->stream));
+  FILE *f = fopen(path, "wb");
+  if (!f) return fail(PC_EINVAL, std::string("cannot open ") + path);
+  int32_t dims[kLayers + 1];
+  for (int l = 0; l <= kLayers; ++l) dims[l] = kDims[l];
+  bool ok = fwrite(kMlpMagic, 1, 8, f) == 8 && fwrite(dims, 4, kLayers + 1, f) == (size_t)kLayers + 1 &&
+            fwrite(&mm->beta_min, 4, 1, f) == 1;
+  for (int l = 0; ok && l < kLayers; ++l) {
+    const size_t nw = (size_t)kDims[l + 1] * kDims[l], nb = (size_t)kDims[l + 1];
+    ok = fwrite(h.data() + mm->w_off[l], 4, nw, f) == nw && fwrite(h.data() + mm->b_off[l], 4, nb, f) == nb;
+  }
+  if (fclose(f) != 0) ok = false;
+  return ok ? PC_OK : fail(PC_EINVAL, std::string("write failed: ") + path);
+} catch (...) {
+  return pc::fail_exception();
+}
+
+int pc_mlp_load(pc_ctx *c, const char *path, pc_mlp **out) try {
+  if (!c || !path || !out) return fail(PC_EINVAL, "NULL argument");
+  *out = nullptr;
+  FILE *f = fopen(path, "rb");
+  if (!f) return fail(PC_EINVAL, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t dims[kLayers + 1];
+  float beta_min = 0.f;
+  bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMlpMagic, 8) == 0 &&
+            fread(dims, 4, kLayers + 1, f) == (size_t)kLayers + 1 && fread(&beta_min, 4, 1, f) == 1;
+  for (int l = 0; ok && l <= kLayers; ++l) ok = dims[l] == kDims[l];
+  std::vector<std::vector<float>> W(kLayers), b(kLayers);
+  for (int l = 0; ok && l < kLayers; ++l) {
+    W[l].resize((size_t)kDims[l + 1] * kDims[l]);
+    b[l].resize((size_t)kDims[l + 1]);
+    ok = fread(W[l].data(), 4, W[l].size(), f) == W[l].size() && fread(b[l].data(), 4, b[l].size(), f) == b[l].size();
+  }
+  fclose(f);
+  if (!ok) return fail(PC_EINVAL, std::string("not a ladder-MLP weights file of this network: ") + path);
+  const float *Wp[kLayers], *bp[kLayers];
+  for (int l = 0; l < kLayers; ++l) {
+    Wp[l] = W[l].data();
+    bp[l] = b[l].data();
+  }
+  return pc_mlp_create(c, out, Wp, bp, beta_min);
 } catch (...) {
   return pc::fail_exception();
 }

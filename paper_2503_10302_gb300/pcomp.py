@@ -98,6 +98,11 @@ SIGNATURES = {
     "pc_mlp_train_step": (c_int, [c_vp, c_int, c_f32p, c_f32p, c_flt, c_f32p]),
     "pc_mlp_train_step_dev": (c_int, [c_vp, c_int, c_vp, c_vp, c_flt, c_vp]),
     "pc_mlp_get_params": (c_int, [c_vp, c_f32pp, c_f32pp]),
+    "pc_mlp_save": (c_int, [c_vp, ctypes.c_char_p]),
+    "pc_mlp_load": (c_int, [c_vp, ctypes.c_char_p, ctypes.POINTER(c_vp)]),
+    "pc_ladder_judge": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_u32, c_int, c_f64p, c_int, c_int, c_dbl, c_f64p,
+                                c_i32p]),
+    "pc_learned_ladder": (c_int, [c_vp, c_vp, c_int, c_i32p, c_i8p, c_u32, c_vp, c_f64p, c_f64p, c_i32p]),
 }
 
 _lib = None
@@ -436,6 +441,51 @@ def pc_instance_features(dims, J) -> np.ndarray:
     return out
 
 
+def pc_ladder_judge(ctx, dims, J_list, betas, entry0=0, n_labels=2, probe_attempts=200, acc_floor=0.19):
+    """Swap-acceptance judge of ladders [n][T]: (acceptance [n][T-1], pass [n])."""
+    n = len(J_list)
+    d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(n, 3))
+    J = _concat_J(J_list)
+    b = np.ascontiguousarray(np.asarray(betas, np.float64).reshape(n, -1))
+    T = b.shape[1]
+    acc = np.zeros((n, T - 1), np.float64)
+    ok = np.zeros(n, np.int32)
+    _call("pc_ladder_judge", ctx, n, ptr(d, ctypes.c_int32), ptr(J, ctypes.c_int8), c_u32(entry0), T,
+          ptr(b, ctypes.c_double), n_labels, probe_attempts, acc_floor, ptr(acc, ctypes.c_double),
+          ptr(ok, ctypes.c_int32))
+    return acc, ok.astype(bool)
+
+
+class LearnedOpts(ctypes.Structure):
+    """pc_learned_opts."""
+    _fields_ = [("pilot_betas", c_f64p), ("pilot_chains", c_int), ("pilot_sweeps", c_int),
+                ("pilot_burn", c_int), ("probe_attempts", c_int), ("probe_labels", c_int),
+                ("acc_floor", c_dbl), ("beta0", c_dbl), ("alpha", c_dbl), ("n_chains", c_int),
+                ("sweeps", c_int), ("tail", c_int), ("tol", c_dbl), ("max_len", c_int)]
+
+
+def pc_learned_ladder(ctx, mlp, dims, J_list, pilot_betas, entry0=0, pilot_chains=8, pilot_sweeps=256,
+                      pilot_burn=128, probe_attempts=200, probe_labels=2, acc_floor=0.19, beta0=0.5,
+                      alpha=1.25, n_chains=32, sweeps=2000, tail=500, tol=1.0, max_len=64):
+    """Learned ladders [n][32] with the judge's acceptances [n][31] and the
+    fallback flags [n] (pc_learned_ladder)."""
+    n = len(J_list)
+    d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(n, 3))
+    J = _concat_J(J_list)
+    pb = np.ascontiguousarray(np.asarray(pilot_betas, np.float64))
+    if pb.shape != (4,):
+        raise ValueError("pilot_betas must hold 4 temperatures")
+    o = LearnedOpts(ptr(pb, ctypes.c_double), pilot_chains, pilot_sweeps, pilot_burn, probe_attempts,
+                    probe_labels, acc_floor, beta0, alpha, n_chains, sweeps, tail, tol, max_len)
+    beta = np.zeros((n, 32), np.float64)
+    acc = np.zeros((n, 31), np.float64)
+    fb = np.zeros(n, np.int32)
+    _call("pc_learned_ladder", ctx, mlp.h if isinstance(mlp, Mlp) else mlp, n, ptr(d, ctypes.c_int32),
+          ptr(J, ctypes.c_int8), c_u32(entry0), ctypes.byref(o), ptr(beta, ctypes.c_double),
+          ptr(acc, ctypes.c_double), ptr(fb, ctypes.c_int32))
+    return beta, acc, fb.astype(bool)
+
+
 MLP_SIZES = (259, 256, 256, 256, 32)
 
 
@@ -447,13 +497,19 @@ def _fpp(arrs):
 class Mlp:
     """The ladder predictor on the GPU (pc_mlp_*): params [(W [out,in], b [out])] x 4."""
 
-    def __init__(self, ctx, params, beta_min: float = 0.0):
+    def __init__(self, ctx, params=None, beta_min: float = 0.0, path: Optional[str] = None):
         self.ctx = ctx
-        Ws = [np.ascontiguousarray(W, np.float32) for W, _ in params]
-        bs = [np.ascontiguousarray(b, np.float32) for _, b in params]
         h = c_vp()
-        _call("pc_mlp_create", ctx, ctypes.byref(h), _fpp(Ws), _fpp(bs), c_flt(beta_min))
+        if path is not None:
+            _call("pc_mlp_load", ctx, os.fsencode(path), ctypes.byref(h))
+        else:
+            Ws = [np.ascontiguousarray(W, np.float32) for W, _ in params]
+            bs = [np.ascontiguousarray(b, np.float32) for _, b in params]
+            _call("pc_mlp_create", ctx, ctypes.byref(h), _fpp(Ws), _fpp(bs), c_flt(beta_min))
         self.h = h
+
+    def save(self, path: str) -> None:
+        _call("pc_mlp_save", self.h, os.fsencode(path))
 
     def close(self):
         if getattr(self, "h", None) is not None:

@@ -233,7 +233,8 @@ def test_split_placement_is_bit_identical_and_matches_oracle(pc, orc, labels, jo
 
 def test_four_labels_thirty_two_temperatures(pc, orc):
     """The paper's APT shape: 32 temperatures x 4 ICM labels = 128 replicas
-    per problem (two CTAs per problem), with open x, y boundaries."""
+    per problem (two CTAs per problem), with open x, y boundaries; 260
+    attempts (two graph replays and a remainder)."""
     shapes = [(8, 8, 8), (6, 6, 4)]
     per = [(0, 0, 1), (1, 1, 1)]
     dims = np.array(shapes, np.int32)
@@ -246,6 +247,9 @@ def test_four_labels_thirty_two_temperatures(pc, orc):
     apt = orc.Apt(dims, J, betas, 4, seed=41, periodic=np.array(per, np.uint8))
     pc.pc_apt_run(ctx.h, 60, 1, True)
     apt.run(60, threads=8)
+    _compare(pc, apt, ctx, b)
+    pc.pc_apt_run(ctx.h, 200, 1, True)
+    apt.run(200, threads=8)
     _compare(pc, apt, ctx, b)
     ctx.close()
 
@@ -314,32 +318,57 @@ def test_target_hit_sweep(pc, orc):
     ctx.close()
 
 
-def test_c3_shape_sampled(pc, orc):
+@pytest.mark.parametrize("pref", [0, 1])
+def test_c3_shape_sampled(pc, orc, pref):
     """64 instances of L = 12 with 32 x 2 replicas (the APT+ICM batch
-    shape); instances 0, 31 and 63 re-computed by the oracle."""
+    shape), in its default placement (two-CTA clusters: the batch fills at
+    most half the SMs) and in one CTA per problem; 260 attempts = two
+    replays of the 128-attempt CUDA graph and a remainder.  Instances 0, 31
+    and 63 re-computed by the oracle."""
     b = W.apt_uniform_batch(64, 12, 32)
     ctx = pc.Context(0, 9)
     pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
-    pc.pc_apt_run(ctx.h, 40, 1, True)
+    pc.pc_apt_set_split(ctx.h, pref)
+    pc.pc_apt_run(ctx.h, 260, 1, True)
     for i in (0, 31, 63):
         apt = orc.Apt(b.dims[i:i + 1], b.J[i:i + 1], b.betas[i:i + 1], 2, seed=9, entry0=i)
-        apt.run(40)
+        apt.run(260)
         _compare(pc, apt, ctx, b, [(i, 0)])
     ctx.close()
 
 
+def test_sweep_to_swap_ratio_ten(pc, orc):
+    """Ten sweeps per swap attempt (the ratio the paper uses to find the
+    best energies, Methods "Instances"), 130 attempts (a graph replay and a
+    remainder), with ICM, against the oracle."""
+    shapes = [(6, 6, 6), (4, 4, 8), (8, 8, 8)]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 14, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in (12, 7, 20)]
+    b = W.AptBatch(dims, J, betas, 2)
+    ctx = pc.Context(0, 47)
+    pc.pc_apt_load(ctx.h, dims, J, betas, 2, 11)
+    apt = orc.Apt(dims, J, betas, 2, seed=47, entry0=11)
+    pc.pc_apt_run(ctx.h, 130, 10, True)
+    apt.run(130, 10, True, threads=8)
+    _compare(pc, apt, ctx, b)
+    assert pc.pc_apt_progress(ctx.h) == (1300, 130)
+    ctx.close()
+
+
 def test_c4_mixed_batch_sampled(pc, orc):
-    """256 instances, L uniform over {6..16}, 24-32 temperatures x 2; the
-    smallest, the largest and a middle instance re-computed by the oracle."""
+    """256 instances, L uniform over {6..16}, 24-32 temperatures x 2, 140
+    attempts (a graph replay and a remainder); the smallest, the largest and
+    a middle instance re-computed by the oracle."""
     b = W.apt_mixed_batch()
     ctx = pc.Context(0, 17)
     pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
-    pc.pc_apt_run(ctx.h, 12, 1, True)
+    pc.pc_apt_run(ctx.h, 140, 1, True)
     work = [int(np.prod(d)) * len(t) for d, t in zip(b.dims, b.betas)]
     picks = {int(np.argmin(work)), int(np.argmax(work)), 128}
     for i in picks:
         apt = orc.Apt(b.dims[i:i + 1], b.J[i:i + 1], b.betas[i:i + 1], 2, seed=17, entry0=i)
-        apt.run(12)
+        apt.run(140)
         _compare(pc, apt, ctx, b, [(i, 0)])
     ctx.close()
 
