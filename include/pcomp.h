@@ -127,6 +127,17 @@ int pc_apt_run(pc_ctx *ctx, int64_t n_swaps, int sweeps_per_swap, int icm);
  * moves all labels, accepted with min(1, exp(dbeta sum_a dE_a)) from word 0
  * of the label-0 swap draw. */
 int pc_apt_set_joint_swap(pc_ctx *ctx, int joint);
+/* ICMop rules of later pc_apt_run calls (Algorithm S2 ICMop).
+ * big_cluster_rule 1 (default): a cluster holding more than half of the
+ * spins present flips one whole replica instead ("greater than half");
+ * 0: every cluster flips in both replicas, which makes the move an exact
+ * symmetric proposal on pairs of states.  cluster_seed 0 (default): the
+ * cluster grows from a uniformly chosen mismatch site (the Houdayer
+ * choice); 1: one of the mismatch clusters is chosen uniformly ("randomly
+ * pick one cluster"), the k-th in the order of their first sites (colour 0
+ * by lin, then colour 1), k = floor(x0 n_clusters / 2^32) with x0 word 0 of
+ * the pair's ICM draw. */
+int pc_apt_set_icm_rules(pc_ctx *ctx, int big_cluster_rule, int cluster_seed);
 /* Placement of each problem: one CTA, or a cluster of two CTAs that split
  * its temperatures (rank 0 the colder half).  The two CTAs exchange the
  * boundary swap and the best-energy candidates through distributed shared
@@ -196,6 +207,10 @@ int pc_sqa_setup(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, doubl
  * sum the present bonds. */
 int pc_sqa_setup_bc(pc_ctx *ctx, const int32_t *dims, const uint8_t *periodic, const uint8_t *present,
                     const int8_t *J, int P, double T, int n_sweeps, const double *gamma);
+/* Bytes pc_sqa_setup copies host -> device for N sites and n_sweeps sweeps:
+ * the 16-bit coupling word of every site and the 40 threshold words of every
+ * sweep (host function). */
+int64_t pc_sqa_upload_bytes(int N, int n_sweeps);
 /* Threshold table of sweep s: out[3][7] for n = s_{k-1} + s_{k+1} in
  * {-2, 0, 2} and intra-slice field I = 2c - 6; *jq = J_perp in Q16.16. */
 int pc_sqa_get_table(pc_ctx *ctx, int sweep, uint32_t *out, int32_t *jq);
@@ -390,6 +405,8 @@ int pc_ladder_judge(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *
 typedef struct pc_mlp pc_mlp;
 int pc_mlp_create(pc_ctx *ctx, pc_mlp **out, const float *const *W, const float *const *b,
                   float beta_min);
+/* Frees the network; it may be called after its context was destroyed
+ * (every other pc_mlp_* call needs the context alive). */
 void pc_mlp_destroy(pc_mlp *m);
 /* X [batch][259] -> beta [batch][32] (host). */
 int pc_mlp_forward(pc_mlp *m, int batch, const float *X, float *beta);
@@ -444,6 +461,11 @@ typedef struct {
  *   6. every rejected instance falls back to pc_adaptive_ladder (same entry
  *      id) resampled to 32 points, and fallback_out [n] (nullable) is 1.
  * beta_out [n][32] receives the ladders (host). */
+/* Steps 1 and 2 alone (the pilot fields of opt): the network's inputs
+ * X_out [n][259] fp32 (host), as pc_learned_ladder computes them; used to
+ * build training sets. */
+int pc_learned_features(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+                        const pc_learned_opts *opt, float *X_out);
 int pc_learned_ladder(pc_ctx *ctx, pc_mlp *m, int n_inst, const int32_t *dims, const int8_t *J,
                       uint32_t entry0, const pc_learned_opts *opt, double *beta_out, double *acc_out,
                       int32_t *fallback_out);

@@ -66,6 +66,11 @@ def lib():
         L.or_apt_run.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.or_apt_set_target.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]
         L.or_apt_set_joint_swap.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_apt_set_icm_rules.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+        L.or_icm_apply_rules.argtypes = [i32p, u8p, i8p, i8p, u64, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, i64p]
+        L.or_icm_choice.argtypes = [i32p, u8p, i8p, i8p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, i64p, i64p]
         L.or_apt_state.argtypes = [ctypes.c_void_p, ctypes.c_int, i8p, i64p, i32p]
         L.or_apt_best.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p, i32p, i64p, i8p]
         L.or_apt_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p, i64p]
@@ -212,6 +217,10 @@ class Apt:
     def set_joint_swap(self, joint: bool):
         _check(lib().or_apt_set_joint_swap(self.h, int(bool(joint))), "set_joint_swap")
 
+    def set_icm_rules(self, big_cluster_rule: bool = True, cluster_seed: bool = False):
+        _check(lib().or_apt_set_icm_rules(self.h, int(bool(big_cluster_rule)), int(bool(cluster_seed))),
+               "set_icm_rules")
+
     def set_target(self, inst: int, e_target: int):
         _check(lib().or_apt_set_target(self.h, inst, e_target), "set_target")
 
@@ -256,6 +265,37 @@ def icm_apply(dims, sa, sb, seed=0, entry=0, r=0, t=0, p=0, periodic=None):
                                    ctypes.c_uint32(entry), ctypes.c_uint32(r), ctypes.c_uint32(t),
                                    ctypes.c_uint32(p), _ptr(size, ctypes.c_int64)), "icm_apply")
     return br, int(size[0]), a, b
+
+
+def icm_apply_rules(dims, sa, sb, seed=0, entry=0, r=0, t=0, p=0, big_cluster_rule=True, cluster_seed=False,
+                    periodic=None):
+    """One ICMop under the given rules on copies of (sa, sb); returns
+    (branch, cluster_size, sa', sb')."""
+    d, per = _dims(dims), _per(periodic)
+    a = np.ascontiguousarray(sa, dtype=np.int8).copy()
+    b = np.ascontiguousarray(sb, dtype=np.int8).copy()
+    size = np.zeros(1, np.int64)
+    br = _check(lib().or_icm_apply_rules(_ptr(d, ctypes.c_int32), _ptr(per, ctypes.c_uint8),
+                                         _ptr(a, ctypes.c_int8), _ptr(b, ctypes.c_int8), ctypes.c_uint64(seed),
+                                         ctypes.c_uint32(entry), ctypes.c_uint32(r), ctypes.c_uint32(t),
+                                         ctypes.c_uint32(p), int(bool(big_cluster_rule)), int(bool(cluster_seed)),
+                                         _ptr(size, ctypes.c_int64)), "icm_apply_rules")
+    return br, int(size[0]), a, b
+
+
+def icm_choice(dims, sa, sb, k, flip_b=False, big_cluster_rule=True, cluster_seed=False, periodic=None):
+    """ICMop with its choices given: (branch, n_choices, cluster_size, sa', sb')."""
+    d, per = _dims(dims), _per(periodic)
+    a = np.ascontiguousarray(sa, dtype=np.int8).copy()
+    b = np.ascontiguousarray(sb, dtype=np.int8).copy()
+    n = np.zeros(1, np.int64)
+    size = np.zeros(1, np.int64)
+    br = lib().or_icm_choice(_ptr(d, ctypes.c_int32), _ptr(per, ctypes.c_uint8), _ptr(a, ctypes.c_int8),
+                             _ptr(b, ctypes.c_int8), k, int(bool(flip_b)), int(bool(big_cluster_rule)),
+                             int(bool(cluster_seed)), _ptr(n, ctypes.c_int64), _ptr(size, ctypes.c_int64))
+    if br < 0 and n[0] > 0 and not (0 <= k < n[0]):
+        raise ValueError("choice out of range")
+    return br, int(n[0]), int(size[0]), a, b
 
 
 def icm_pairing(seed, entry, r, t, n_labels=4):

@@ -99,6 +99,8 @@ struct or_apt {
   apt_entry *e;
   uint64_t seed;
   int joint;   /* 1: one swap decision per temperature pair for all labels */
+  int icm_big;  /* 1 (default): the big-cluster branch of ICMop is on */
+  int icm_seed; /* 0 (default): uniform mismatch site; 1: uniform cluster */
   int64_t sweeps_done, swaps_done;
 };
 
@@ -128,6 +130,8 @@ int or_apt_create(or_apt **out, int n_inst, const int32_t *dims, const uint8_t *
   if (!a) return -2;
   a->n = n_inst;
   a->seed = seed;
+  a->icm_big = 1;
+  a->icm_seed = 0;
   a->e = (apt_entry *)calloc((size_t)n_inst, sizeof(apt_entry));
   if (!a->e) { free(a); return -2; }
   size_t joff = 0, boff = 0;
@@ -201,27 +205,10 @@ static void best_update(apt_entry *e, int64_t sweeps) {
   if (e->hit_sweep < 0 && e->best_E <= e->target) e->hit_sweep = sweeps;
 }
 
-/* Core of ICMop on two configurations; x = the pair's Philox block.
- * Returns 0 (no mismatch), 1 (cluster flipped in both) or 2 (one whole
- * replica flipped); *size = cluster size. */
-static int icm_core(const or_lat *L, int8_t *sa, int8_t *sb, const uint32_t x[4],
-                    int32_t *queue, uint8_t *inC, int64_t *size_out) {
-  int N = L->N;
-  const uint8_t *vac = L->vac;
-  int64_t nminus = 0;
-  for (int lin = 0; lin < N; ++lin) nminus += (sa[lin] != sb[lin]) && !(vac && vac[lin]);
-  *size_out = 0;
-  if (nminus == 0) return 0;
-  int64_t k = (int64_t)(((uint64_t)x[0] * (uint64_t)nminus) >> 32);
-  int seed_site = -1;
-  int64_t cnt = 0;
-  for (int c = 0; c < 2 && seed_site < 0; ++c)
-    for (int lin = 0; lin < N; ++lin) {
-      if (or_colour(L, lin) != c || sa[lin] == sb[lin] || (vac && vac[lin])) continue;
-      if (cnt == k) { seed_site = lin; break; }
-      ++cnt;
-    }
-  memset(inC, 0, (size_t)N);
+/* Flood of the mismatch component of `seed_site` into queue[0 .. size-1]
+ * (breadth first over lattice adjacency); marks inC. */
+static int64_t icm_component(const or_lat *L, const int8_t *sa, const int8_t *sb, int seed_site,
+                             int32_t *queue, uint8_t *inC) {
   int head = 0, tail = 0;
   queue[tail++] = seed_site;
   inC[seed_site] = 1;
@@ -234,13 +221,67 @@ static int icm_core(const or_lat *L, int8_t *sa, int8_t *sb, const uint32_t x[4]
       queue[tail++] = n;
     }
   }
-  *size_out = tail;
-  if (2 * (int64_t)tail > (int64_t)L->nreal) {   /* more than half of the spins present */
-    int8_t *sf = (x[1] & 1u) ? sb : sa;
+  return tail;
+}
+
+static int icm_mismatch(const or_lat *L, const int8_t *sa, const int8_t *sb, int lin) {
+  return sa[lin] != sb[lin] && !(L->vac && L->vac[lin]);
+}
+
+/* Number of choices of the seed rule: the mismatch sites (seed_rule 0) or
+ * the mismatch clusters (seed_rule 1). */
+static int64_t icm_choices(const or_lat *L, const int8_t *sa, const int8_t *sb, int seed_rule,
+                           int32_t *queue, uint8_t *inC) {
+  const int N = L->N;
+  int64_t n = 0;
+  if (seed_rule == 0) {
+    for (int lin = 0; lin < N; ++lin) n += icm_mismatch(L, sa, sb, lin);
+    return n;
+  }
+  memset(inC, 0, (size_t)N);
+  for (int lin = 0; lin < N; ++lin)
+    if (icm_mismatch(L, sa, sb, lin) && !inC[lin]) {
+      icm_component(L, sa, sb, lin, queue, inC);
+      ++n;
+    }
+  return n;
+}
+
+/* ICMop with the seed choice k in [0, n_choices) given: the seed is the
+ * k-th mismatch site in canonical order (colour 0 by increasing lin, then
+ * colour 1) under seed_rule 0, or the first site, in that order, of the
+ * k-th cluster met in that order under seed_rule 1.  The seed's cluster C
+ * is flipped in both replicas; with big_rule set and 2|C| larger than the
+ * spins present, one whole replica (flip_b: the second, else the first)
+ * is flipped instead.  Returns 1 (cluster) or 2 (whole replica). */
+static int icm_apply_choice(const or_lat *L, int8_t *sa, int8_t *sb, int64_t k, int flip_b, int big_rule,
+                            int seed_rule, int32_t *queue, uint8_t *inC, int64_t *size_out) {
+  const int N = L->N;
+  int seed_site = -1;
+  int64_t cnt = 0;
+  memset(inC, 0, (size_t)N);
+  for (int c = 0; c < 2 && seed_site < 0; ++c)
+    for (int lin = 0; lin < N; ++lin) {
+      if (or_colour(L, lin) != c || !icm_mismatch(L, sa, sb, lin)) continue;
+      if (seed_rule == 1) {
+        if (inC[lin]) continue;               /* a cluster met before */
+        if (cnt == k) { seed_site = lin; break; }
+        icm_component(L, sa, sb, lin, queue, inC);
+      } else if (cnt == k) {
+        seed_site = lin;
+        break;
+      }
+      ++cnt;
+    }
+  memset(inC, 0, (size_t)N);
+  const int64_t size = icm_component(L, sa, sb, seed_site, queue, inC);
+  *size_out = size;
+  if (big_rule && 2 * size > (int64_t)L->nreal) {   /* more than half of the spins present */
+    int8_t *sf = flip_b ? sb : sa;
     for (int lin = 0; lin < N; ++lin) sf[lin] = (int8_t)-sf[lin];
     return 2;
   }
-  for (int q = 0; q < tail; ++q) {
+  for (int64_t q = 0; q < size; ++q) {
     int v = queue[q];
     sa[v] = (int8_t)-sa[v];
     sb[v] = (int8_t)-sb[v];
@@ -248,21 +289,34 @@ static int icm_core(const or_lat *L, int8_t *sa, int8_t *sb, const uint32_t x[4]
   return 1;
 }
 
+/* Core of ICMop on two configurations; x = the pair's Philox block.
+ * The choice is k = floor(x0 n / 2^32) of the n choices of the seed rule,
+ * and bit 0 of x1 picks the replica of a whole-replica flip.  Returns 0 (no
+ * mismatch), 1 (cluster flipped in both) or 2 (one whole replica flipped);
+ * *size = cluster size. */
+static int icm_core(const or_lat *L, int8_t *sa, int8_t *sb, const uint32_t x[4], int big_rule, int seed_rule,
+                    int32_t *queue, uint8_t *inC, int64_t *size_out) {
+  *size_out = 0;
+  const int64_t n = icm_choices(L, sa, sb, seed_rule, queue, inC);
+  if (n == 0) return 0;
+  const int64_t k = (int64_t)(((uint64_t)x[0] * (uint64_t)n) >> 32);
+  return icm_apply_choice(L, sa, sb, k, (int)(x[1] & 1u), big_rule, seed_rule, queue, inC, size_out);
+}
+
 /* ICMop of Algorithm S2 on buffers (ba, bb) at attempt t, temperature r:
- * overlap q_i = s_i^a s_i^b; a uniformly chosen site with q = -1 (the k-th
- * in canonical order: colour 0 by increasing lin, then colour 1, with
- * k = floor(x0 n_minus / 2^32)) seeds the cluster = its connected component
- * of {q = -1} on the lattice graph.  If the cluster holds more than half of
- * all spins, one of the two replicas (x1 bit 0: 0 -> a, 1 -> b) is flipped
- * entirely; otherwise the cluster is flipped in both. */
-static void icm_op(apt_entry *e, uint64_t seed, int ba, int bb, uint32_t r, uint32_t t,
-                   uint32_t p) {
+ * overlap q_i = s_i^a s_i^b; the seed (a uniform mismatch site, or the
+ * first site of a uniform mismatch cluster) starts the cluster = its
+ * connected component of {q = -1} on the lattice graph, flipped in both
+ * replicas, or, when it holds more than half of all spins and the
+ * big-cluster rule is on, one whole replica is flipped instead. */
+static void icm_op(apt_entry *e, uint64_t seed, int ba, int bb, uint32_t r, uint32_t t, uint32_t p,
+                   int big_rule, int seed_rule) {
   int N = e->L.N;
   int8_t *sa = e->spin + (size_t)ba * N, *sb = e->spin + (size_t)bb * N;
   uint32_t ctr[4] = {r, t, p, (e->ent << 8) | OR_TAG_ICM}, x[4];
   or_philox(ctr, seed, x);
   int64_t size;
-  int br = icm_core(&e->L, sa, sb, x, e->queue, e->inC, &size);
+  int br = icm_core(&e->L, sa, sb, x, big_rule, seed_rule, e->queue, e->inC, &size);
   e->icm[br]++;
   if (br == 0) return;
   e->E[ba] = or_energy_lat(&e->L, e->J, e->h, sa);
@@ -272,6 +326,12 @@ static void icm_op(apt_entry *e, uint64_t seed, int ba, int bb, uint32_t r, uint
 int or_icm_apply(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb,
                  uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p,
                  int64_t *cluster_size) {
+  return or_icm_apply_rules(dims, periodic, sa, sb, seed, entry, r, t, p, 1, 0, cluster_size);
+}
+
+int or_icm_apply_rules(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb,
+                       uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p, int big_rule,
+                       int seed_rule, int64_t *cluster_size) {
   or_lat L;
   int rc = or_lat_init(&L, dims, periodic);
   if (rc) return rc;
@@ -279,7 +339,27 @@ int or_icm_apply(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, i
   uint8_t *inC = (uint8_t *)malloc((size_t)L.N);
   uint32_t ctr[4] = {r, t, p, (entry << 8) | OR_TAG_ICM}, x[4];
   or_philox(ctr, seed, x);
-  int br = icm_core(&L, sa, sb, x, queue, inC, cluster_size);
+  int br = icm_core(&L, sa, sb, x, big_rule != 0, seed_rule != 0, queue, inC, cluster_size);
+  free(queue); free(inC);
+  or_lat_free(&L);
+  return br;
+}
+
+int or_icm_choice(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb, int64_t k,
+                  int flip_b, int big_rule, int seed_rule, int64_t *n_choices, int64_t *cluster_size) {
+  or_lat L;
+  int rc = or_lat_init(&L, dims, periodic);
+  if (rc) return rc;
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * L.N);
+  uint8_t *inC = (uint8_t *)malloc((size_t)L.N);
+  const int64_t n = icm_choices(&L, sa, sb, seed_rule != 0, queue, inC);
+  *n_choices = n;
+  *cluster_size = 0;
+  int br = 0;
+  if (n > 0 && k >= 0 && k < n)
+    br = icm_apply_choice(&L, sa, sb, k, flip_b != 0, big_rule != 0, seed_rule != 0, queue, inC, cluster_size);
+  else if (n > 0)
+    br = -1;
   free(queue); free(inC);
   or_lat_free(&L);
   return br;
@@ -390,7 +470,8 @@ int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int thr
           int q[4];
           icm_matching(a->seed, e->ent, (uint32_t)r, t, e->A, q);
           for (int p = 0; p < e->A / 2; ++p)
-            icm_op(e, a->seed, r * e->A + q[2 * p], r * e->A + q[2 * p + 1], (uint32_t)r, t, (uint32_t)p);
+            icm_op(e, a->seed, r * e->A + q[2 * p], r * e->A + q[2 * p + 1], (uint32_t)r, t, (uint32_t)p,
+                   a->icm_big, a->icm_seed);
         }
         best_update(e, s);
       }
@@ -406,6 +487,13 @@ int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int thr
 int or_apt_set_joint_swap(or_apt *a, int joint) {
   if (!a) return -1;
   a->joint = joint != 0;
+  return 0;
+}
+
+int or_apt_set_icm_rules(or_apt *a, int big_cluster_rule, int cluster_seed) {
+  if (!a) return -1;
+  a->icm_big = big_cluster_rule != 0;
+  a->icm_seed = cluster_seed != 0;
   return 0;
 }
 

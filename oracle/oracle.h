@@ -81,6 +81,14 @@ int or_apt_run(or_apt *a, int64_t n_swaps, int sweeps_per_swap, int icm, int thr
  * decision per temperature pair swaps all labels, accepted with
  * min(1, exp(dbeta sum_a dE_a)) (Algorithm S2 read literally). */
 int or_apt_set_joint_swap(or_apt *a, int joint);
+/* ICMop rules of later runs (Algorithm S2 ICMop): big_cluster_rule 1
+ * (default) flips one whole replica when the cluster holds more than half
+ * of the spins present, 0 always flips the cluster in both replicas;
+ * cluster_seed 0 (default) seeds the cluster at a uniformly chosen mismatch
+ * site, 1 picks one of the mismatch clusters uniformly ("randomly pick one
+ * cluster"), k = floor(x0 n_clusters / 2^32), clusters ordered by their first
+ * site in canonical order. */
+int or_apt_set_icm_rules(or_apt *a, int big_cluster_rule, int cluster_seed);
 int or_apt_set_target(or_apt *a, int inst, int64_t e_target);
 /* spins [B][N] in slot order (slot r*A + a: temperature r, label a);
    energies [B]; temperature index of each slot [B] (= slot / A). */
@@ -103,6 +111,17 @@ int or_icm_pairing(uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, int n_
 int or_icm_apply(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb,
                  uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p,
                  int64_t *cluster_size);
+/* As or_icm_apply under the rules of or_apt_set_icm_rules. */
+int or_icm_apply_rules(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb,
+                       uint64_t seed, uint32_t entry, uint32_t r, uint32_t t, uint32_t p, int big_rule,
+                       int seed_rule, int64_t *cluster_size);
+/* ICMop with its random choices given: seed choice k in [0, n_choices)
+ * (mismatch site or cluster, by seed_rule) and flip_b (whole-replica flip
+ * of the second replica).  *n_choices receives the number of choices
+ * (0: nothing moves).  Returns 0 (no mismatch), 1 (cluster), 2 (whole
+ * replica) or -1 (k out of range).  Used to enumerate transition matrices. */
+int or_icm_choice(const int32_t dims[3], const uint8_t periodic[3], int8_t *sa, int8_t *sb, int64_t k,
+                  int flip_b, int big_rule, int seed_rule, int64_t *n_choices, int64_t *cluster_size);
 
 /* ---------------- adaptive beta ladder (Algorithm S2 preprocessing) --------- */
 /* beta_out/sigma_out have room for max_len; *len_out = ladder length;

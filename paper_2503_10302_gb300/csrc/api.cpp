@@ -321,6 +321,8 @@ int pc_sqa_setup_bc(pc_ctx *c, const int32_t *dims, const uint8_t *periodic, con
   if ((rc = q.stage.reserve(jb + tb))) return rc;
   std::memcpy(q.stage.p, jn.data(), jn.size() * 2);
   std::memcpy(q.stage.p + jb, q.table.data(), tb);
+  if ((int64_t)(jn.size() * 2 + tb) != pc_sqa_upload_bytes(lat.N, n_sweeps))
+    return fail(PC_EINVAL, "internal: upload size disagrees with pc_sqa_upload_bytes");
   PC_CUDA_TRY(cudaMemcpyAsync(q.d_jneg.p, q.stage.p, jn.size() * 2, cudaMemcpyHostToDevice, c->stream));
   PC_CUDA_TRY(cudaMemcpyAsync(q.d_table.p, q.stage.p + jb, tb, cudaMemcpyHostToDevice, c->stream));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -480,6 +482,11 @@ int pc_sqa_anneal(pc_ctx *c, const int32_t *dims, const int8_t *J, int P, double
   return pc_sqa_run(c, R, run0, E_out, nullptr);
 } catch (...) {
   return pc::fail_exception();
+}
+
+int64_t pc_sqa_upload_bytes(int N, int n_sweeps) {
+  if (N < 0) return 0;
+  return (int64_t)N * 2 + (int64_t)kSqaTab * 4 * (n_sweeps > 0 ? n_sweeps : 1);
 }
 
 }  // extern "C"

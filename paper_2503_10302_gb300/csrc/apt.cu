@@ -386,6 +386,113 @@ __device__ __forceinline__ uint32_t byte_to_nib(uint32_t b) {
   return (t | (t << 3)) & 0x11111111u;
 }
 
+// Union-find over 32-bit parent words in shared memory, every parent no
+// larger than its child, so a root is the smallest index of its set.  A
+// failed atomicMin means the word decreased meanwhile, which bounds the
+// retries; the cap only guards the loop.
+__device__ __forceinline__ uint32_t uf_find(volatile uint32_t *L, uint32_t x) {
+  uint32_t p = L[x];
+  for (int it = 0; p != x && it < 8192; ++it) {
+    x = p;
+    p = L[x];
+  }
+  return x;
+}
+
+__device__ __forceinline__ void uf_union(uint32_t *L, uint32_t a, uint32_t b) {
+  volatile uint32_t *Lv = L;
+  for (int it = 0; it < 1 << 16; ++it) {
+    a = uf_find(Lv, a);
+    b = uf_find(Lv, b);
+    if (a == b) return;
+    if (a < b) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    const uint32_t old = atomicMin(&L[a], b);   // link the larger root under the smaller
+    if (old == a) return;
+    a = old;
+  }
+}
+
+// Seeds of the cluster-seed rule ("randomly pick one cluster" read as a
+// uniform choice among the mismatch clusters): for each pair in turn, a
+// union-find over the lattice bonds between its mismatch sites labels the
+// clusters by their first site in canonical order (c*H + j); with n
+// clusters, the k-th root, k = floor(x0 n / 2^32), seeds the pair's flood
+// fill.  The labels use the transposed-overlap words, which this rule does
+// not need; R holds one root bit per site.
+__device__ __forceinline__ void icm_cluster_seeds(const Cta &k, const Shared &sh, int nbits, int r0, int P) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int N = k.geo.N, H = k.geo.H, nchunk = (N + 31) >> 5;
+  uint32_t *V = sh.V, *X = sh.V + N, *Lb = sh.V + 2 * N, *R = sh.V + 2 * N + 32 * nchunk;
+  volatile uint32_t *Lv = Lb;
+  for (int pb = 0; pb < nbits; ++pb) {
+    if (r0 + 8 * ((pb >> 3) >> (P - 1)) + (pb & 7) >= k.T || sh.inm[pb] == 0) continue;
+    for (int kk = tid; kk < N; kk += nt) Lb[kk] = ((X[kk] >> pb) & 1u) ? (uint32_t)kk : 0xFFFFFFFFu;
+    __syncthreads();
+    // every bond has one colour-0 end: unite each colour-0 mismatch site
+    // with its mismatched neighbours over the bonds present
+    for (int j = tid; j < H; j += nt) {
+      if (!((X[j] >> pb) & 1u)) continue;
+      int nb[6];
+      neighbours(k.geo, 0, j, nb);
+      const uint32_t miss = ((uint32_t)sh.jn[j] >> 8) & 0x3Fu;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        const int kk2 = H + nb[d];
+        if (((miss >> d) & 1u) == 0u && ((X[kk2] >> pb) & 1u)) uf_union(Lb, (uint32_t)j, (uint32_t)kk2);
+      }
+    }
+    __syncthreads();
+    for (int ch = warp; ch < nchunk; ch += (nt >> 5)) {
+      const int kk = ch * 32 + lane;
+      const bool root = kk < N && ((X[kk] >> pb) & 1u) && uf_find(Lv, (uint32_t)kk) == (uint32_t)kk;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, root);
+      if (lane == 0) R[ch] = m;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int tot = 0;
+      for (int ch = lane; ch < nchunk; ch += 32) tot += __popc(R[ch]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+      const int kth = (int)(((uint64_t)sh.ikx[pb] * (uint64_t)tot) >> 32);
+      int base = 0;
+      for (int ch0 = 0; ch0 < nchunk; ch0 += 32) {
+        const int ch = ch0 + lane;
+        uint32_t w = ch < nchunk ? R[ch] : 0u;
+        const int cn = __popc(w);
+        int inc = cn;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+          if (lane >= o) inc += y;
+        }
+        const int ex = base + inc - cn;
+        const bool hit = kth >= ex && kth < ex + cn;
+        if (hit) {
+          int q = kth - ex, pos = 0;
+#pragma unroll
+          for (int h = 16; h >= 1; h >>= 1) {
+            const int cl = __popc(w & ((1u << h) - 1u));
+            if (q >= cl) {
+              q -= cl;
+              w >>= h;
+              pos += h;
+            }
+          }
+          V[ch * 32 + pos] |= 1u << pb;
+        }
+        if (__any_sync(0xFFFFFFFFu, hit)) break;
+        base += __shfl_sync(0xFFFFFFFFu, inc, 31);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ICMop of Algorithm S2 for every temperature at once.  With A labels per
 // temperature (2 or 4) the labels of temperature r = 8h + i sit in nibble i
 // of groups l*Gl + h, and pair p of the temperature's random matching owns
@@ -396,6 +503,7 @@ __device__ __forceinline__ uint32_t byte_to_nib(uint32_t b) {
 // V <- V | (X & OR_nbr V) until no cluster changes.  Clusters larger than
 // N/2 flip one whole replica (x1 bit 0: the pair's first or second label),
 // smaller ones flip in both replicas; then the energies are updated.
+template <bool CSEED>
 __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32_t t) {
   long long pt = clock64();
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -484,8 +592,9 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   PROF_MARK(4, pt);
   // seeds: warp w finds the k-th mismatch of pairs w, w + nw, ...: chunk
   // counts by popcount, a warp scan over chunks, then the set bit inside
-  // the chunk
-  for (int r = warp; r < nbits; r += nw) {   // r: pair bit
+  // the chunk (the cluster-seed rule finds the k-th cluster instead)
+  if (CSEED) icm_cluster_seeds(k, sh, nbits, r0, P);
+  for (int r = warp; r < nbits && !CSEED; r += nw) {   // r: pair bit
     if (r0 + 8 * ((r >> 3) >> (P - 1)) + (r & 7) >= k.T) continue;
     const int nm = sh.inm[r];
     if (nm == 0) continue;
@@ -680,7 +789,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
       const uint32_t bit = 1u << (4 * i);
       if (sh.inm[pb] == 0) {
         atomicAdd(&sh.m32[2], 1);
-      } else if (2 * size > k.nreal) {   // more than half of the spins present
+      } else if (a.icm_big && 2 * size > k.nreal) {   // more than half of the spins present
         atomicOr(&sh.imask[16 + (sh.ibit[pb] ? lb : la) * Gl + h], bit);   // one whole replica
         atomicAdd(&sh.m32[4], 1);
       } else {
@@ -932,7 +1041,7 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
 // MODE (pc::APT_MODE_*) and SPLIT (a cluster of two CTAs per problem) are
 // template arguments, so that each kernel carries only its own code (the
 // launcher picks the instantiation from a.mode and a.split).
-template <int MODE, bool SPLIT>
+template <int MODE, bool SPLIT, bool CSEED>
 __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   extern __shared__ __align__(16) uint32_t smem[];
   const int cta = blockIdx.x;
@@ -1004,7 +1113,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.gmap = reinterpret_cast<int32_t *>(cur);     cur += 8;
   sh.xch = reinterpret_cast<int32_t *>(cur);      cur += 24;
   sh.stage = cur;                                 cur += SPLIT ? 512 : 0;
-  sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 : 0;   // V, X, Xt
+  sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 + ((N + 31) >> 5) : 0;   // V, X, Xt, R
   sh.jn = reinterpret_cast<uint16_t *>(cur);
 
   // load state: local group u is global group gmap[u]
@@ -1090,7 +1199,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
       best_update(a, k, sh, p, sweeps);
       PROF_MARK(2, pt);
       if (icm) {
-        icm_all(a, k, sh, t);
+        icm_all<CSEED>(a, k, sh, t);
         pt = clock64();
         best_update(a, k, sh, p, sweeps);
         PROF_MARK(10, pt);
@@ -1222,14 +1331,15 @@ size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n
   size_t words = (size_t)Gc * N + 32 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
   words += 4 * 64 + 24 + 24 + 128 + 8 + 24 + 512;   // + larger swap stats, group map, exchange, stage
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
-  if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31;   // V, X and the transposed X
+  // V, X, the transposed X (or the cluster labels) and the root masks
+  if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31 + (size_t)((N + 31) >> 5);
   return words * 4 + (size_t)N * 2 + 16;
 }
 
-template <int MODE>
+template <int MODE, bool CSEED>
 int apt_launch_mode(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st) {
   if (!a.split) {
-    apt_kernel<MODE, false><<<n_cta, tpb, smem, st>>>(a);
+    apt_kernel<MODE, false, CSEED><<<n_cta, tpb, smem, st>>>(a);
   } else {
     // split problems: consecutive CTA pairs form one cluster
     cudaLaunchConfig_t cfg = {};
@@ -1244,7 +1354,7 @@ int apt_launch_mode(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStrea
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, apt_kernel<MODE, true>, a));
+    PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, apt_kernel<MODE, true, CSEED>, a));
   }
   PC_CUDA_TRY(cudaGetLastError());
   return PC_OK;
@@ -1260,21 +1370,27 @@ int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t s
   PC_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(PC_EINVAL, "device index out of range");
   if (smem > set_for[dev]) {
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_LADDER, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_LADDER, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_PILOT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_PILOT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_ENERGY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_ENERGY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_APT, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_LADDER, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_LADDER, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_PILOT, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_PILOT, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_ENERGY, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PC_CUDA_TRY(cudaFuncSetAttribute(apt_kernel<pc::APT_MODE_ENERGY, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     set_for[dev] = smem;
   }
   switch (a.mode) {
-    case pc::APT_MODE_APT: return apt_launch_mode<pc::APT_MODE_APT>(a, n_cta, tpb, smem, st);
-    case pc::APT_MODE_LADDER: return apt_launch_mode<pc::APT_MODE_LADDER>(a, n_cta, tpb, smem, st);
-    case pc::APT_MODE_PILOT: return apt_launch_mode<pc::APT_MODE_PILOT>(a, n_cta, tpb, smem, st);
-    case pc::APT_MODE_ENERGY: return apt_launch_mode<pc::APT_MODE_ENERGY>(a, n_cta, tpb, smem, st);
+    case pc::APT_MODE_APT:
+      // the cluster-seed ICM rule has an instantiation of its own, so the
+      // default rule's code is compiled without it
+      return a.icm_seed ? apt_launch_mode<pc::APT_MODE_APT, true>(a, n_cta, tpb, smem, st)
+                        : apt_launch_mode<pc::APT_MODE_APT, false>(a, n_cta, tpb, smem, st);
+    case pc::APT_MODE_LADDER: return apt_launch_mode<pc::APT_MODE_LADDER, false>(a, n_cta, tpb, smem, st);
+    case pc::APT_MODE_PILOT: return apt_launch_mode<pc::APT_MODE_PILOT, false>(a, n_cta, tpb, smem, st);
+    case pc::APT_MODE_ENERGY: return apt_launch_mode<pc::APT_MODE_ENERGY, false>(a, n_cta, tpb, smem, st);
     default: return fail(PC_EINVAL, "unknown kernel mode");
   }
 }

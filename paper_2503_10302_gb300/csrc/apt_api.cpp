@@ -253,6 +253,8 @@ AptArgs base_args(pc_ctx *c, Batch &bt) {
   a.k0 = (uint32_t)(c->seed & 0xFFFFFFFFu);
   a.k1 = (uint32_t)(c->seed >> 32);
   a.spp = 1;
+  a.icm_big = 1;
+  a.icm_seed = 0;
   return a;
 }
 
@@ -364,6 +366,7 @@ struct AptImpl {
   cudaGraph_t graph = nullptr;
   int g_spp = -1, g_icm = -1;
   int joint = 0;                      // joint-label swap rule
+  int icm_big = 1, icm_seed = 0;      // ICMop rules (pc_apt_set_icm_rules)
   ~AptImpl() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -549,6 +552,8 @@ static int apt_enqueue(pc_ctx *c, AptImpl *im, int n_iter, int spp, int icm) {
   a.spp = spp;
   a.icm = icm;
   a.joint_swap = im->joint;
+  a.icm_big = im->icm_big;
+  a.icm_seed = im->icm_seed;
   a.tag_main = 2;    // TAG_APT_SWEEP
   a.tag_ref = 3;     // TAG_APT_REFINE
   int rc = apt_launch(a, im->bt.n_cta, im->bt.tpb, im->bt.smem, c->stream);
@@ -561,6 +566,17 @@ int pc_apt_set_joint_swap(pc_ctx *c, int joint) try {
   AptImpl *im = apt_impl(c);
   im->joint = joint ? 1 : 0;
   im->g_spp = -1;   // the captured chunk bakes the rule in: capture again
+  return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
+}
+
+int pc_apt_set_icm_rules(pc_ctx *c, int big_cluster_rule, int cluster_seed) try {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  AptImpl *im = apt_impl(c);
+  im->icm_big = big_cluster_rule ? 1 : 0;
+  im->icm_seed = cluster_seed ? 1 : 0;
+  im->g_spp = -1;   // the captured chunk bakes the rules in: capture again
   return PC_OK;
 } catch (...) {
   return pc::fail_exception();
@@ -1252,6 +1268,30 @@ int pc_ladder_judge(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J,
                              n_temps, acc_floor, acc_out ? acc_out + (size_t)i * (n_temps - 1) : nullptr)
                       ? 1
                       : 0;
+  return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
+}
+
+int pc_learned_features(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
+                        const pc_learned_opts *o, float *X_out) try {
+  if (!c || !dims || !J || !o || !o->pilot_betas || !X_out) return fail(PC_EINVAL, "NULL argument");
+  int rc = check_pilot_params(n_inst, entry0, kLearnedBetas, o->pilot_betas, o->pilot_chains, o->pilot_sweeps,
+                              o->pilot_burn, kLearnedBins);
+  if (rc) return rc;
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  Batch bt;
+  if ((rc = pilot_run(c, bt, n_inst, dims, J, entry0, kLearnedBetas, o->pilot_betas, o->pilot_chains,
+                      o->pilot_sweeps, o->pilot_burn, kLearnedBins)))
+    return rc;
+  constexpr int kIn = 3 + kLearnedBetas * kLearnedBins;
+  DevBuf<float> X;
+  if ((rc = X.alloc((size_t)n_inst * kIn))) return rc;
+  if ((rc = learned_features_launch(bt.d_prob.p, n_inst, bt.d_jneg.p, bt.d_hist.p, kLearnedBetas, kLearnedBins,
+                                    X.p, kIn, c->stream)))
+    return rc;
+  PC_CUDA_TRY(cudaMemcpyAsync(X_out, X.p, (size_t)n_inst * kIn * 4, cudaMemcpyDeviceToHost, c->stream));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PC_OK;
 } catch (...) {
   return pc::fail_exception();

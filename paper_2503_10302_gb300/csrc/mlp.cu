@@ -169,6 +169,7 @@ size_t mlp_param_count() {
 
 struct pc_mlp {
   pc_ctx *ctx = nullptr;
+  int device = 0;    // the context's device, kept for pc_mlp_destroy
   float beta_min = 0.f;
   int64_t t = 0;
   size_t n_params = 0;
@@ -315,6 +316,7 @@ int pc_mlp_create(pc_ctx *c, pc_mlp **out, const float *const *W, const float *c
   PC_CUDA_TRY(cudaSetDevice(c->device));
   pc_mlp *mm = new pc_mlp();
   mm->ctx = c;
+  mm->device = c->device;
   mm->beta_min = beta_min;
   size_t off = 0;
   for (int l = 0; l < kLayers; ++l) {
@@ -353,8 +355,9 @@ int pc_mlp_create(pc_ctx *c, pc_mlp **out, const float *const *W, const float *c
 
 void pc_mlp_destroy(pc_mlp *mm) try {
   if (!mm) return;
-  cudaSetDevice(mm->ctx->device);
-  cudaStreamSynchronize(mm->ctx->stream);
+  // the context may already be gone: use only the device recorded at
+  // creation (cudaFree waits for the device's work on these buffers)
+  cudaSetDevice(mm->device);
   delete mm;
 } catch (...) {
 }

@@ -45,6 +45,7 @@ SIGNATURES = {
     "pc_apt_load_bc": (c_int, [c_vp, c_int, c_i32p, c_vp, c_vp, c_i8p, c_i32p, c_f64p, c_int, c_u32]),
     "pc_apt_run": (c_int, [c_vp, c_i64, c_int, c_int]),
     "pc_apt_set_joint_swap": (c_int, [c_vp, c_int]),
+    "pc_apt_set_icm_rules": (c_int, [c_vp, c_int, c_int]),
     "pc_apt_set_split": (c_int, [c_vp, c_int]),
     "pc_apt_is_split": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "pc_apt_autotune": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_int)]),
@@ -61,6 +62,7 @@ SIGNATURES = {
     "pc_apt_get_swap_table": (c_int, [c_vp, c_int, c_int, c_u32p, c_int, ctypes.POINTER(c_int)]),
     "pc_sqa_setup": (c_int, [c_vp, c_i32p, c_i8p, c_int, c_dbl, c_int, c_f64p]),
     "pc_sqa_setup_bc": (c_int, [c_vp, c_i32p, c_vp, c_vp, c_i8p, c_int, c_dbl, c_int, c_f64p]),
+    "pc_sqa_upload_bytes": (c_i64, [c_int, c_int]),
     "pc_sqa_get_table": (c_int, [c_vp, c_int, c_u32p, ctypes.POINTER(ctypes.c_int32)]),
     "pc_sqa_run": (c_int, [c_vp, c_int, c_u32, c_i64p, c_i8p]),
     "pc_sqa_run_dev": (c_int, [c_vp, c_int, c_u32, c_vp, c_vp]),
@@ -102,6 +104,7 @@ SIGNATURES = {
     "pc_mlp_load": (c_int, [c_vp, ctypes.c_char_p, ctypes.POINTER(c_vp)]),
     "pc_ladder_judge": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_u32, c_int, c_f64p, c_int, c_int, c_dbl, c_f64p,
                                 c_i32p]),
+    "pc_learned_features": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_u32, c_vp, c_f32p]),
     "pc_learned_ladder": (c_int, [c_vp, c_vp, c_int, c_i32p, c_i8p, c_u32, c_vp, c_f64p, c_f64p, c_i32p]),
 }
 
@@ -226,6 +229,10 @@ def pc_sqa_setup_bc(ctx, dims, periodic, J, P: int, T: float, gamma, present=Non
           ptr(g, ctypes.c_double))
 
 
+def pc_sqa_upload_bytes(N: int, n_sweeps: int) -> int:
+    return int(lib().pc_sqa_upload_bytes(N, n_sweeps))
+
+
 def pc_sqa_get_table(ctx, sweep: int):
     out = np.zeros((3, 7), np.uint32)
     jq = ctypes.c_int32()
@@ -307,6 +314,10 @@ def pc_apt_load_bc(ctx, dims, periodic, J_list, betas_list, n_labels: int = 2, e
 
 def pc_apt_set_joint_swap(ctx, joint: bool) -> None:
     _call("pc_apt_set_joint_swap", ctx, int(bool(joint)))
+
+
+def pc_apt_set_icm_rules(ctx, big_cluster_rule: bool = True, cluster_seed: bool = False) -> None:
+    _call("pc_apt_set_icm_rules", ctx, int(bool(big_cluster_rule)), int(bool(cluster_seed)))
 
 
 def pc_apt_set_split(ctx, pref: int) -> None:
@@ -464,6 +475,33 @@ class LearnedOpts(ctypes.Structure):
                 ("sweeps", c_int), ("tail", c_int), ("tol", c_dbl), ("max_len", c_int)]
 
 
+def _learned_opts(pb, pilot_chains, pilot_sweeps, pilot_burn, probe_attempts=0, probe_labels=2, acc_floor=0.0,
+                  beta0=0.5, alpha=1.25, n_chains=32, sweeps=2000, tail=500, tol=1.0, max_len=64):
+    return LearnedOpts(ptr(pb, ctypes.c_double), pilot_chains, pilot_sweeps, pilot_burn, probe_attempts,
+                       probe_labels, acc_floor, beta0, alpha, n_chains, sweeps, tail, tol, max_len)
+
+
+def _pilot_betas(pilot_betas) -> np.ndarray:
+    pb = np.ascontiguousarray(np.asarray(pilot_betas, np.float64))
+    if pb.shape != (4,):
+        raise ValueError("pilot_betas must hold 4 temperatures")
+    return pb
+
+
+def pc_learned_features(ctx, dims, J_list, pilot_betas, entry0=0, pilot_chains=8, pilot_sweeps=256,
+                        pilot_burn=128) -> np.ndarray:
+    """The network's inputs [n][259] (pc_learned_features)."""
+    n = len(J_list)
+    d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(n, 3))
+    J = _concat_J(J_list)
+    pb = _pilot_betas(pilot_betas)
+    o = _learned_opts(pb, pilot_chains, pilot_sweeps, pilot_burn)
+    X = np.zeros((n, MLP_SIZES[0]), np.float32)
+    _call("pc_learned_features", ctx, n, ptr(d, ctypes.c_int32), ptr(J, ctypes.c_int8), c_u32(entry0),
+          ctypes.byref(o), ptr(X, ctypes.c_float))
+    return X
+
+
 def pc_learned_ladder(ctx, mlp, dims, J_list, pilot_betas, entry0=0, pilot_chains=8, pilot_sweeps=256,
                       pilot_burn=128, probe_attempts=200, probe_labels=2, acc_floor=0.19, beta0=0.5,
                       alpha=1.25, n_chains=32, sweeps=2000, tail=500, tol=1.0, max_len=64):
@@ -472,11 +510,9 @@ def pc_learned_ladder(ctx, mlp, dims, J_list, pilot_betas, entry0=0, pilot_chain
     n = len(J_list)
     d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(n, 3))
     J = _concat_J(J_list)
-    pb = np.ascontiguousarray(np.asarray(pilot_betas, np.float64))
-    if pb.shape != (4,):
-        raise ValueError("pilot_betas must hold 4 temperatures")
-    o = LearnedOpts(ptr(pb, ctypes.c_double), pilot_chains, pilot_sweeps, pilot_burn, probe_attempts,
-                    probe_labels, acc_floor, beta0, alpha, n_chains, sweeps, tail, tol, max_len)
+    pb = _pilot_betas(pilot_betas)
+    o = _learned_opts(pb, pilot_chains, pilot_sweeps, pilot_burn, probe_attempts, probe_labels, acc_floor,
+                      beta0, alpha, n_chains, sweeps, tail, tol, max_len)
     beta = np.zeros((n, 32), np.float64)
     acc = np.zeros((n, 31), np.float64)
     fb = np.zeros(n, np.int32)
@@ -498,6 +534,9 @@ class Mlp:
     """The ladder predictor on the GPU (pc_mlp_*): params [(W [out,in], b [out])] x 4."""
 
     def __init__(self, ctx, params=None, beta_min: float = 0.0, path: Optional[str] = None):
+        # ctx: a Context (kept alive as long as the network) or a raw handle
+        self._owner = ctx if isinstance(ctx, Context) else None
+        ctx = ctx.h if isinstance(ctx, Context) else ctx
         self.ctx = ctx
         h = c_vp()
         if path is not None:

@@ -5,9 +5,8 @@
 * Time to a target residual energy rho_E = (E - E_best)/N (Eq. rho_E_f)
   with E_best the best energy over independent long runs (Methods
   "Instances": best over an APT+ICM run with sweep-to-swap ratio 10).
-* The learned-ladder pipeline: adaptive ladders for generated instances,
-  pilot histograms, MLP training on the GPU, and learned vs adaptive
-  ladders compared by wall time to the target.
+* The learned-ladder pipeline lives in ``ladder.py`` (training, weights,
+  learned vs adaptive ladders by wall time to the target).
 
 Run ``python -m paper_2503_10302_gb300.ttt --help``.
 """
@@ -22,9 +21,6 @@ import numpy as np
 
 from . import pcomp
 from . import workloads as W
-
-PILOT_BETAS = W.geometric_ladder(4, 0.2, 3.0)
-
 
 class DeviceTimer:
     """CUDA-event timing of work enqueued on the context's torch stream."""
@@ -105,22 +101,6 @@ def adaptive_ladders(dims, J_list, n_chains=32, sweeps=2000, tail=500, seed=11, 
     dt = time.perf_counter() - t0
     ctx.close()
     return [b for b, _, _ in res], dt
-
-
-def features(dims, J_list, seed=13, entry0=0, chains_per_beta=8, sweeps=256, burn=128) -> Tuple[np.ndarray, float]:
-    """MLP inputs: instance features + normalised pilot histograms."""
-    ctx = pcomp.Context(0, seed)
-    t0 = time.perf_counter()
-    hist = pcomp.pc_pilot_hist(ctx.h, dims, J_list, PILOT_BETAS, entry0=entry0,
-                               chains_per_beta=chains_per_beta, sweeps=sweeps, burn=burn, n_bins=64)
-    X = np.zeros((len(J_list), 259), np.float32)
-    for i, (d, J) in enumerate(zip(dims, J_list)):
-        X[i, :3] = pcomp.pc_instance_features(d, J)
-        h = hist[i].astype(np.float64)
-        X[i, 3:] = (h / np.maximum(h.sum(axis=1, keepdims=True), 1)).reshape(-1)
-    dt = time.perf_counter() - t0
-    ctx.close()
-    return X, dt
 
 
 def c3_time_to_target(n_inst=64, L=12, rho=1e-3, best_runs=10, best_sweeps=100000,
@@ -223,111 +203,6 @@ def c4_mixed_time_to_target(rho=1e-3, best_runs=10, best_sweeps=20000, max_sweep
                           "median_time_s": float(np.median(h) * t_sweep) if h.size else None}
     return {"flips_per_ns_icm": tp["flips_per_ns"], "apt_seconds_per_sweep": t_sweep,
             "hit_fraction": float(ok.mean()), "per_L": per_L}
-
-
-def training_set(n: int, sizes=(6, 8, 10, 12, 14, 16), seed: int = W.SEED_TRAIN, ladder_kw=None,
-                 chunk: int = 4096):
-    """n generated instances (even L drawn from `sizes`), their adaptive
-    ladders resampled to 32, and their MLP input features."""
-    ladder_kw = ladder_kw or {}
-    rng = np.random.Generator(np.random.Philox(key=[seed, 0xEEEE]))
-    Ls = rng.choice(np.asarray(sizes), size=n)
-    X = np.zeros((n, 259), np.float32)
-    Y = np.zeros((n, 32), np.float32)
-    lens = np.zeros(n, np.int32)
-    t_lad = t_feat = 0.0
-    for s0 in range(0, n, chunk):
-        idx = range(s0, min(n, s0 + chunk))
-        dims = np.array([[Ls[i]] * 3 for i in idx], np.int32)
-        J = [W.ea_couplings((int(Ls[i]),) * 3, seed, i) for i in idx]
-        lad, dt = adaptive_ladders(dims, J, entry0=s0, **ladder_kw)
-        t_lad += dt
-        f, dt = features(dims, J, entry0=s0)
-        t_feat += dt
-        X[s0:s0 + len(J)] = f
-        for k, b in enumerate(lad):
-            Y[s0 + k] = pcomp.pc_resample_ladder(b, 32)
-            lens[s0 + k] = len(b)
-    return X, Y, Ls, lens, t_lad, t_feat
-
-
-def train(X: np.ndarray, Y: np.ndarray, epochs: int = 60, batch: int = 256, lr: float = 1e-3,
-          seed: int = 21):
-    """Trains the ladder MLP on the GPU (pc_mlp_train_step_dev)."""
-    import torch
-    from .pcomp import MLP_SIZES
-    params = W.mlp_init(MLP_SIZES, seed)
-    ctx = pcomp.Context(0, seed)
-    stream = torch.cuda.Stream()
-    pcomp.pc_set_stream(ctx.h, stream.cuda_stream)
-    m = pcomp.Mlp(ctx.h, params)
-    Xd = torch.from_numpy(X).cuda()
-    Yd = torch.from_numpy(Y).cuda()
-    loss = torch.zeros(1, device="cuda")
-    rng = np.random.default_rng(seed)
-    n = X.shape[0]
-    hist = []
-    t0 = time.perf_counter()
-    for ep in range(epochs):
-        perm = torch.from_numpy(rng.permutation(n)).cuda()
-        Xp, Yp = Xd[perm].contiguous(), Yd[perm].contiguous()
-        torch.cuda.synchronize()
-        lr_ep = lr * (0.1 ** (ep / max(1, epochs - 1)))     # decays tenfold over training
-        for b0 in range(0, n - batch + 1, batch):
-            m.train_step_dev(batch, Xp[b0:].data_ptr(), Yp[b0:].data_ptr(), lr_ep, loss.data_ptr())
-        torch.cuda.synchronize()
-        hist.append(float(loss.item()))
-    t_train = time.perf_counter() - t0
-    return m, ctx, hist, t_train
-
-
-def c5_learned_vs_adaptive(n_train=20000, n_eval=128, L=16, rho=1e-3, best_runs=10,
-                           best_sweeps=20000, max_sweeps=100000, epochs=60, ladder_kw=None) -> Dict:
-    """Learned ladder (pilot run + MLP) vs the adaptive procedure on held-out
-    L = 16 instances: wall time to rho_E <= rho, ladder construction included."""
-    ladder_kw = ladder_kw or dict(n_chains=32, sweeps=2000, tail=500)
-    X, Y, Ls, lens, t_lad_train, t_feat_train = training_set(n_train, ladder_kw=ladder_kw)
-    m, mctx, hist, t_train = train(X, Y, epochs=epochs)
-    N = L ** 3
-    dims = np.tile(np.array([L, L, L], np.int32), (n_eval, 1))
-    J = [W.ea_couplings((L, L, L), W.SEED_EVAL, i) for i in range(n_eval)]
-    # adaptive arm: the preprocessing of Algorithm S2, resampled to 32
-    lad, t_adapt = adaptive_ladders(dims, J, entry0=1 << 20, **ladder_kw)
-    betas_a = [pcomp.pc_resample_ladder(b, 32) for b in lad]
-    # learned arm: pilot histograms + MLP forward
-    t0 = time.perf_counter()
-    f, _ = features(dims, J, entry0=1 << 21)
-    pred = m.forward(f).astype(np.float64)
-    t_learn = time.perf_counter() - t0
-    betas_l = [np.maximum.accumulate(np.maximum(p, 1e-3)) + 1e-9 * np.arange(32) for p in pred]
-    # per-L mean training ladder (no instance information) for context
-    mean_lad = Y[Ls == L].mean(axis=0).astype(np.float64) if (Ls == L).any() else Y.mean(axis=0)
-    betas_m = [mean_lad + 1e-9 * np.arange(32) for _ in range(n_eval)]
-    Ya = np.stack(betas_a)
-    ladder_rmse = {"learned": float(np.sqrt(((np.stack(betas_l) - Ya) ** 2).mean())),
-                   "mean_ladder": float(np.sqrt(((mean_lad[None, :] - Ya) ** 2).mean()))}
-    ref = W.AptBatch(dims, J, betas_a, 2)
-    e_best = best_energies(ref, best_runs, best_sweeps)
-    targets = np.floor(e_best + rho * N).astype(np.int64)
-    out = {"n_train": n_train, "n_eval": n_eval, "L": L, "rho_target": rho,
-           "train_ladder_seconds": t_lad_train, "train_feature_seconds": t_feat_train,
-           "train_seconds": t_train, "train_loss_first_last": [hist[0], hist[-1]],
-           "ladder_settings": ladder_kw, "mean_ladder_len_L16": float(lens[Ls == L].mean()) if (Ls == L).any() else None,
-           "ladder_rmse_vs_adaptive": ladder_rmse}
-    for name, betas, t_pre in (("adaptive", betas_a, t_adapt), ("learned", betas_l, t_learn),
-                               ("mean_ladder", betas_m, 0.0)):
-        hit, t_sweep, total = run_to_target(W.AptBatch(dims, J, betas, 2), targets, max_sweeps)
-        ok = hit >= 0
-        tt = t_pre + np.where(ok, hit, max_sweeps) * t_sweep
-        out[name] = {"ladder_seconds": t_pre, "apt_seconds_per_sweep": t_sweep,
-                     "hit_fraction": float(ok.mean()),
-                     "median_hit_sweep": float(np.median(hit[ok])) if ok.any() else None,
-                     "median_time_to_target_s": float(np.median(tt)),
-                     "mean_time_to_target_s": float(tt.mean()),
-                     "time_to_90pct_s": float(np.quantile(tt, 0.9))}
-    m.close()
-    mctx.close()
-    return out
 
 
 def graph_apt_throughput(graphs: Sequence[W.Graph], n_temps: int = 32, labels: int = 2, sweeps: int = 200,
@@ -484,7 +359,7 @@ def graph_time_to_target(name: str = "dimer_64xL8", labels: int = 2, rho: float 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("what", choices=["throughput", "graph", "graph-ttt", "gsqa-embedded", "c2", "c3", "c4", "c5",
+    ap.add_argument("what", choices=["throughput", "graph", "graph-ttt", "gsqa-embedded", "c2", "c3", "c4",
                                      "all"])
     ap.add_argument("--graph", choices=["dimer_64xL8", "lattice15x15x12_64", "lattice12_64", "random4096_152"])
     ap.add_argument("--graph-labels", type=int, choices=[2, 4], help="graph: one label count only")
@@ -494,9 +369,6 @@ def main():
     ap.add_argument("--sweeps", type=int, default=200)
     ap.add_argument("--batch", choices=["apt_plain_L4", "apt_icm_64xL12", "apt_icm_mixed256"])
     ap.add_argument("--icm", type=int, choices=[0, 1])
-    ap.add_argument("--n-train", type=int, default=20000)
-    ap.add_argument("--n-eval", type=int, default=128)
-    ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--best-runs", type=int, default=10)
     ap.add_argument("--best-sweeps", type=int, default=20000)
     ap.add_argument("--max-sweeps", type=int, default=100000)
@@ -546,10 +418,6 @@ def main():
         out["c3"] = c3_time_to_target(labels=args.labels)
     if args.what in ("c4", "all"):
         out["c4"] = c4_mixed_time_to_target()
-    if args.what in ("c5", "all"):
-        out["c5"] = c5_learned_vs_adaptive(n_train=args.n_train, n_eval=args.n_eval, epochs=args.epochs,
-                                           best_runs=args.best_runs, best_sweeps=args.best_sweeps,
-                                           max_sweeps=args.max_sweeps)
     print(json.dumps(out, indent=1))
 
 

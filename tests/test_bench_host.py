@@ -32,3 +32,21 @@ def test_clock_summary_without_samples_is_none():
     S = _bench().ClockSampler.summarize
     assert S([]) is None
     assert S(["not, enough, fields"]) is None
+
+
+def test_e2e_upload_bytes_match_what_setup_stages():
+    """The e2e line declares what pc_sqa_setup copies host -> device: one
+    16-bit coupling word per site and the 40 threshold words of every sweep
+    (the anneal kernel's table row, [3 time counts][13 fields] + 1 pad)."""
+    from paper_2503_10302_gb300 import build, pcomp
+    build.build()
+    for N, S in ((512, 10000), (64, 1), (4096, 30), (8, 0)):
+        assert pcomp.pc_sqa_upload_bytes(N, S) == 2 * N + 40 * 4 * max(S, 1)
+    assert pcomp.pc_sqa_upload_bytes(512, 10000) == 1601024
+
+
+def test_alu_roofline_uses_twenty_ops_per_update():
+    b = _bench()
+    r = b._alu_roofline(1000.0, 40.0, "k")
+    assert b.ALG_OPS_PER_FLIP == 20.0
+    assert abs(r["achieved"] - 20.0) < 1e-12 and abs(r["frac"] - 0.5) < 1e-12

@@ -196,6 +196,35 @@ def test_joint_label_swaps(pc, orc, labels, icm):
     ctx.close()
 
 
+@pytest.mark.parametrize("big,cseed,labels,pref", [(False, False, 2, 1), (True, True, 2, 1), (False, True, 4, 2),
+                                                    (True, True, 2, 2), (False, False, 4, 1)])
+def test_icm_rules_match_oracle(pc, orc, big, cseed, labels, pref):
+    """The ICMop switches (big-cluster branch on or off; seed at a uniform
+    mismatch site or at a uniform cluster) against the oracle with the same
+    switches, with open boundaries and vacancies, one-CTA and two-CTA
+    placements, across a graph-replayed chunk (140 attempts)."""
+    shapes = [(8, 8, 8), (6, 6, 6), (4, 4, 8), (12, 12, 4)]
+    per = [(1, 1, 1), (0, 0, 1), (1, 1, 1), (0, 1, 1)]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 15, i) for i, s in enumerate(shapes)]
+    present = [W.random_vacancies(s, 0.05, i) if i == 2 else None for i, s in enumerate(shapes)]
+    present = [np.ones(int(np.prod(s)), np.uint8) if p_ is None else p_ for s, p_ in zip(shapes, present)]
+    temps = [16, 12, 9, 16] if labels == 4 else [24, 12, 9, 20]
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, labels)
+    ctx = pc.Context(0, 53)
+    pc.pc_apt_load_bc(ctx.h, dims, per, J, betas, labels, 6, present_list=present)
+    pc.pc_apt_set_split(ctx.h, pref)
+    pc.pc_apt_set_icm_rules(ctx.h, big, cseed)
+    apt = orc.Apt(dims, J, betas, labels, seed=53, entry0=6, periodic=np.array(per, np.uint8),
+                  present_list=present)
+    apt.set_icm_rules(big, cseed)
+    pc.pc_apt_run(ctx.h, 140, 1, True)
+    apt.run(140, threads=8)
+    _compare(pc, apt, ctx, b)
+    ctx.close()
+
+
 @pytest.mark.parametrize("labels,joint", [(2, False), (4, False), (2, True), (1, False)])
 def test_split_placement_is_bit_identical_and_matches_oracle(pc, orc, labels, joint):
     """The same batch as one CTA per problem and as two-CTA clusters that

@@ -491,6 +491,91 @@ def test_icm_seed_is_uniform_over_mismatch_sites(orc):
     assert stats.chisquare(obs, exp).pvalue > 1e-6
 
 
+def test_icm_cluster_seed_is_uniform_over_clusters(orc):
+    """Under the cluster-seed rule ("randomly pick one cluster" read as a
+    uniform cluster) each of the three mismatch clusters is chosen with
+    probability 1/3 whatever its size, and the number of choices is the
+    number of networkx components of the mismatch set."""
+    dims = (4, 4, 4)
+    N = 64
+    sa = np.ones(N, np.int8)
+    sb = sa.copy()
+    for c in [[0, 1, 2, 3], [42], [23, 39]]:
+        sb[c] = -1
+    comps = _components(dims, sa != sb)
+    assert orc.icm_choice(dims, sa, sb, 0, cluster_seed=True)[1] == len(comps) == 3
+    counts = {tuple(c): 0 for c in comps}
+    n = 6000
+    for t in range(n):
+        br, size, a2, b2 = orc.icm_apply_rules(dims, sa, sb, seed=77, t=t, cluster_seed=True)
+        counts[tuple(np.nonzero(a2 != sa)[0].tolist())] += 1
+    obs = np.array([counts[tuple(c)] for c in comps], np.float64)
+    assert stats.chisquare(obs, np.full(3, n / 3)).pvalue > 1e-6
+    rng = np.random.default_rng(5)
+    for t in range(40):     # random overlaps: choices = components, chosen set = a component
+        sa = W.random_spins(N, 3000 + t)
+        sb = np.where(rng.random(N) < 0.1 + 0.02 * t, -sa, sa).astype(np.int8)
+        comps = _components(dims, sa != sb)
+        br, nc, size, a2, b2 = orc.icm_choice(dims, sa, sb, 0, big_cluster_rule=False, cluster_seed=True)
+        assert nc == len(comps)
+        if nc:
+            k = int(rng.integers(nc))
+            br, _, size, a2, b2 = orc.icm_choice(dims, sa, sb, k, big_cluster_rule=False, cluster_seed=True)
+            assert br == 1 and np.nonzero(a2 != sa)[0].tolist() in comps
+
+
+def _icm_moves(orc, dims, sa, sb, big, seed_rule):
+    """{y: T[x -> y]} of one ICMop from x = (s^a, s^b), from the oracle's
+    move with each of its random choices (seed choice k, replica bit)
+    weighted uniformly; y = (index of s^a', index of s^b')."""
+    _, n, _, _, _ = orc.icm_choice(dims, sa, sb, 0, False, big, seed_rule)
+    if n == 0:
+        return {(int(X.state_index(sa)), int(X.state_index(sb))): 1.0}
+    out = {}
+    for k in range(n):
+        for fb in (0, 1):
+            _, _, _, a2, b2 = orc.icm_choice(dims, sa, sb, k, fb, big, seed_rule)
+            y = (int(X.state_index(a2)), int(X.state_index(b2)))
+            out[y] = out.get(y, 0.0) + 0.5 / n
+    return out
+
+
+@pytest.mark.parametrize("seed_rule", [False, True])
+def test_icm_transition_matrix_is_symmetric_without_big_cluster_rule(orc, seed_rule):
+    """With the big-cluster branch off, ICMop is an exact symmetric move
+    on pairs of states (a cluster flip keeps the overlap, hence the set of
+    choices): T[x -> y] = T[y -> x] on a 2 x 2 x 2 lattice for every one of
+    the 256 overlaps, with 16 seeded s^a each, for the site seed and the
+    cluster seed; rows sum to 1 and every move keeps E_a + E_b, so the
+    product Boltzmann law at one temperature is stationary.  With the
+    branch on, T is not symmetric: a cluster of 7 of the 8 spins flips one
+    whole replica, and no move leads back."""
+    dims = (2, 2, 2)
+    states = X.all_states(8)
+    J = W.ea_couplings(dims, 62, 0)
+    E = X.energies(X.lattice_edges(dims), J, None, states)
+    rng = np.random.default_rng(9)
+    for iq in range(256):
+        q = states[iq]
+        for ia in rng.choice(256, size=16, replace=False):
+            sa = states[ia]
+            sb = (sa * q).astype(np.int8)
+            x = (int(ia), int(X.state_index(sb)))
+            fwd = _icm_moves(orc, dims, sa, sb, False, seed_rule)
+            assert abs(sum(fwd.values()) - 1.0) < 1e-12
+            for y, p in fwd.items():
+                back = _icm_moves(orc, dims, states[y[0]], states[y[1]], False, seed_rule)
+                assert abs(back.get(x, 0.0) - p) < 1e-12, (x, y)
+                assert E[x[0]] + E[x[1]] == E[y[0]] + E[y[1]]
+    sa = states[0]
+    sb = sa.copy()
+    sb[:7] = -sb[:7]                    # one mismatch cluster of 7 sites
+    x = (0, int(X.state_index(sb)))
+    fwd = _icm_moves(orc, dims, sa, sb, True, False)
+    assert any(_icm_moves(orc, dims, states[y[0]], states[y[1]], True, False).get(x, 0.0) != p
+               for y, p in fwd.items())
+
+
 def test_joint_label_swaps_keep_product_boltzmann(orc):
     """Joint swaps (one decision moves both labels of a temperature pair):
     each temperature's marginal stays exp(-beta_r E), and the acceptance
