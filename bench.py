@@ -235,12 +235,13 @@ def apt_metrics(stream, peak_tops: float, attempts: int = 256) -> dict:
         ctx = pcomp.Context(0, 1)
         pcomp.pc_set_stream(ctx.h, stream.cuda_stream)
         pcomp.pc_apt_load(ctx.h, batch.dims, batch.J, batch.betas, batch.n_labels, 0)
+        shape = pcomp.pc_apt_autotune(ctx.h, 16, True)     # launch shape of the fused kernel
+        out[name + "_launch"] = {"threads": shape[0], "thread_chunks": shape[1], "two_cta_clusters": shape[2]}
         for icm in icms:
             v = timed(ctx, batch.spins_per_sweep(), icm)
             key = f"{name}_{'e2e' if icm else 'sweep_only'}"
             out[key] = {"value": v, "unit": UNIT, "attempts": attempts,
                         "roofline": _alu_roofline(v, peak_tops, "apt_kernel")}
-        out[name + "_split"] = pcomp.pc_apt_is_split(ctx.h)
         ctx.close()
     out["apt_icm_64xL12_adaptive_ladder_seconds"] = t_lad
     return out

@@ -41,14 +41,17 @@ struct Batch {
   int tpb = kTpbDefault;
   int split = 0;         // APT problems run as clusters of two CTAs (by temperature)
   int split_pref = 0;    // 0: when needed or when the batch fills at most half the SMs; 1: only when needed; 2: whenever possible
+  int nch_pref = 0;      // thread chunks per CTA: 0 = the cost model's choice, else this count where it fits
   size_t smem = 0;
   std::vector<uint32_t> h_pbit, h_swaptab, h_swapidx;
 };
 
 // Split of a CTA's threads into nch chunks of tpb/nch threads, each chunk
-// sweeping ceil(Gc/nch) groups of every site: the choice that minimises the
-// longest thread's work (site rounds x groups).
-int choose_nch(int H, int Gc, int tpb) {
+// sweeping ceil(Gc/nch) groups of every site: `pref` where it fits (tpb a
+// multiple of 32 nch, nch <= Gc, at most 4 groups per thread), else the
+// choice that minimises the longest thread's work (site rounds x groups).
+int choose_nch(int H, int Gc, int tpb, int pref) {
+  if (pref > 0 && tpb % (32 * pref) == 0 && pref <= Gc && (Gc + pref - 1) / pref <= 4) return pref;
   int best = 1, best_cost = INT_MAX;
   for (int nch = 1; nch <= 8; nch *= 2) {
     if (tpb % (32 * nch)) continue;
@@ -306,7 +309,7 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
         cp.push_back(i);
         cg0.push_back(g0);
         cgc.push_back(P.A * gu);
-        cnch.push_back(choose_nch(P.N / 2, P.A * gu, bt.tpb));
+        cnch.push_back(choose_nch(P.N / 2, P.A * gu, bt.tpb, bt.nch_pref));
       }
       smem = std::max(smem, apt_smem_bytes(P.N, P.A * h1, bt.tpb / 32, mode, icm, P.T, n_bins));
       continue;
@@ -318,7 +321,7 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
       cp.push_back(i);
       cg0.push_back(g0);
       cgc.push_back(gc);
-      cnch.push_back(choose_nch(P.N / 2, gc, bt.tpb));
+      cnch.push_back(choose_nch(P.N / 2, gc, bt.tpb, bt.nch_pref));
       smem = std::max(smem, apt_smem_bytes(P.N, gc, bt.tpb / 32, mode, icm, P.T, n_bins));
     }
   }
@@ -635,63 +638,116 @@ int pc_apt_run(pc_ctx *c, int64_t n_swaps, int sweeps_per_swap, int icm) try {
   return pc::fail_exception();
 }
 
-int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out) try {
+}  // extern "C"
+
+namespace {
+
+// Re-schedules the loaded batch with a new launch shape; the chains do not
+// move.  On failure the old shape is restored.
+int apply_shape(pc_ctx *c, AptImpl *im, int tpb, int nch_pref, int split_pref) {
+  Batch &bt = im->bt;
+  const int o_tpb = bt.tpb, o_nch = bt.nch_pref, o_split = bt.split_pref;
+  bt.tpb = tpb;
+  bt.nch_pref = nch_pref;
+  bt.split_pref = split_pref;
+  int rc = schedule(c, bt, {}, APT_MODE_APT, im->A >= 2, 0);
+  if (rc) {
+    bt.tpb = o_tpb;
+    bt.nch_pref = o_nch;
+    bt.split_pref = o_split;
+    schedule(c, bt, {}, APT_MODE_APT, im->A >= 2, 0);
+    return rc;
+  }
+  if (im->exec) cudaGraphExecDestroy(im->exec);
+  if (im->graph) cudaGraphDestroy(im->graph);
+  im->exec = nullptr;
+  im->graph = nullptr;
+  return PC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_out, int *split_out) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (trial_swaps < 1) return fail(PC_EINVAL, "trial_swaps must be >= 1");
   AptImpl *im = apt_impl(c);
   if (icm && im->A < 2) return fail(PC_EINVAL, "ICM needs two or four labels per temperature");
   PC_CUDA_TRY(cudaSetDevice(c->device));
-  const int cands[3] = {256, 384, 512};
-  int best = im->bt.tpb;
-  float best_ms = 1e30f;
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  // candidates: one CTA per problem or two-CTA clusters (where every
+  // problem can split; problems above 64 replicas always split), threads
+  // per CTA, and the threads' split over sites and replica groups
+  bool can_split = true;
+  for (const AptProbDev &P : im->bt.prob) can_split = can_split && (P.Tp >> 3) >= 2;
+  const int splits[2] = {1, 2}, tpbs[5] = {256, 320, 384, 448, 512}, nchs[4] = {0, 1, 2, 4};
+  struct Best { float ms; int tpb, nch, split; } best = {1e30f, im->bt.tpb, im->bt.nch_pref, im->bt.split_pref};
   cudaEvent_t e0, e1;
   PC_CUDA_TRY(cudaEventCreate(&e0));
   PC_CUDA_TRY(cudaEventCreate(&e1));
   int rc = PC_OK;
-  for (int tpb : cands) {
-    // a scratch copy of the batch: the loaded chains are not advanced
-    Batch tmp;
-    tmp.tpb = tpb;
-    tmp.split_pref = im->bt.split_pref;
-    if ((rc = build_batch(c, tmp, im->specs, 0))) break;
-    if ((rc = schedule(c, tmp, {}, APT_MODE_APT, im->A >= 2, 0))) {
-      rc = PC_OK;   // does not fit with this shape: skip it
-      continue;
-    }
-    AptArgs a = base_args(c, tmp);
-    a.tag_init = 1;
-    if ((rc = apt_init_launch(a, (int)im->specs.size(), max_words(tmp), c->stream))) break;
-    a.mode = APT_MODE_APT;
-    a.n_iter = trial_swaps;
-    a.spp = 1;
-    a.icm = icm ? 1 : 0;
-    a.tag_main = 2;
-    a.tag_ref = 3;
-    if ((rc = apt_launch(a, tmp.n_cta, tpb, tmp.smem, c->stream))) break;   // warm-up
-    PC_CUDA_TRY(cudaEventRecord(e0, c->stream));
-    if ((rc = apt_launch(a, tmp.n_cta, tpb, tmp.smem, c->stream))) break;
-    PC_CUDA_TRY(cudaEventRecord(e1, c->stream));
-    PC_CUDA_TRY(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = tpb;
-    }
+  for (int sp : splits) {
+    if (sp == 2 && !can_split) continue;
+    for (int tpb : tpbs)
+      for (int nch : nchs) {
+        if (rc) break;
+        // a scratch copy of the batch: the loaded chains are not advanced
+        Batch tmp;
+        tmp.tpb = tpb;
+        tmp.split_pref = sp;
+        tmp.nch_pref = nch;
+        if ((rc = build_batch(c, tmp, im->specs, 0))) break;
+        if (schedule(c, tmp, {}, APT_MODE_APT, im->A >= 2, 0)) continue;   // does not fit: skip
+        if (nch > 0) {   // skip a forced split that the schedule could not honour
+          std::vector<int> h((size_t)tmp.n_cta);
+          PC_CUDA_TRY(cudaMemcpy(h.data(), tmp.d_cta.p + 3 * tmp.n_cta, h.size() * 4, cudaMemcpyDeviceToHost));
+          bool used = false;
+          for (int v : h) used = used || v == nch;
+          if (!used) continue;
+        }
+        AptArgs a = base_args(c, tmp);
+        a.tag_init = 1;
+        if ((rc = apt_init_launch(a, (int)im->specs.size(), max_words(tmp), c->stream))) break;
+        a.mode = APT_MODE_APT;
+        a.n_iter = trial_swaps;
+        a.spp = 1;
+        a.icm = icm ? 1 : 0;
+        a.icm_big = im->icm_big;
+        a.icm_seed = im->icm_seed;
+        a.joint_swap = im->joint;
+        a.tag_main = 2;
+        a.tag_ref = 3;
+        if ((rc = apt_launch(a, tmp.n_cta, tpb, tmp.smem, c->stream))) break;   // warm-up
+        PC_CUDA_TRY(cudaEventRecord(e0, c->stream));
+        if ((rc = apt_launch(a, tmp.n_cta, tpb, tmp.smem, c->stream))) break;
+        PC_CUDA_TRY(cudaEventRecord(e1, c->stream));
+        PC_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best.ms) best = {ms, tpb, nch, sp};
+      }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  if (best != im->bt.tpb) {
-    im->bt.tpb = best;
-    if ((rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0))) return rc;
-    if (im->exec) cudaGraphExecDestroy(im->exec);
-    if (im->graph) cudaGraphDestroy(im->graph);
-    im->exec = nullptr;
-    im->graph = nullptr;
-  }
-  if (tpb_out) *tpb_out = best;
+  if ((rc = apply_shape(c, im, best.tpb, best.nch, best.split))) return rc;
+  if (tpb_out) *tpb_out = best.tpb;
+  if (nch_out) *nch_out = best.nch;
+  if (split_out) *split_out = im->bt.split;
   return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
+}
+
+int pc_apt_set_launch(pc_ctx *c, int tpb, int nch, int split_pref) try {
+  if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
+  if (tpb < 64 || tpb > 512 || tpb % 64) return fail(PC_EINVAL, "tpb must be a multiple of 64 in [64, 512]");
+  if (nch < 0 || nch > 8 || (nch & (nch - 1))) return fail(PC_EINVAL, "nch must be 0, 1, 2, 4 or 8");
+  if (split_pref < 0 || split_pref > 2) return fail(PC_EINVAL, "split_pref must be 0, 1 or 2");
+  PC_CUDA_TRY(cudaSetDevice(c->device));
+  PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return apply_shape(c, apt_impl(c), tpb, nch, split_pref);
 } catch (...) {
   return pc::fail_exception();
 }
@@ -702,19 +758,7 @@ int pc_apt_set_split(pc_ctx *c, int pref) try {
   AptImpl *im = apt_impl(c);
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  const int old = im->bt.split_pref;
-  im->bt.split_pref = pref;
-  int rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0);
-  if (rc) {
-    im->bt.split_pref = old;
-    schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0);
-    return rc;
-  }
-  if (im->exec) cudaGraphExecDestroy(im->exec);
-  if (im->graph) cudaGraphDestroy(im->graph);
-  im->exec = nullptr;
-  im->graph = nullptr;
-  return PC_OK;
+  return apply_shape(c, im, im->bt.tpb, im->bt.nch_pref, pref);
 } catch (...) {
   return pc::fail_exception();
 }
@@ -733,19 +777,7 @@ int pc_apt_set_block_threads(pc_ctx *c, int tpb) try {
   AptImpl *im = apt_impl(c);
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  const int old = im->bt.tpb;
-  im->bt.tpb = tpb;
-  int rc = schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0);
-  if (rc) {
-    im->bt.tpb = old;
-    schedule(c, im->bt, {}, APT_MODE_APT, im->A >= 2, 0);
-    return rc;
-  }
-  if (im->exec) cudaGraphExecDestroy(im->exec);
-  if (im->graph) cudaGraphDestroy(im->graph);
-  im->exec = nullptr;
-  im->graph = nullptr;
-  return PC_OK;
+  return apply_shape(c, im, tpb, im->bt.nch_pref, im->bt.split_pref);
 } catch (...) {
   return pc::fail_exception();
 }

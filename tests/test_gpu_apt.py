@@ -402,25 +402,43 @@ def test_c4_mixed_batch_sampled(pc, orc):
     ctx.close()
 
 
-def test_launch_shape_does_not_change_results(pc, orc):
-    """256, 384 and 512 threads per CTA (and the autotuner's choice) give
-    bit-identical chains."""
-    b = W.apt_uniform_batch(3, 8, 20)
-    states = []
-    for tpb in (256, 384, 512, None):
+@pytest.mark.parametrize("labels", [2, 4])
+def test_launch_shape_does_not_change_results(pc, orc, labels):
+    """Shapes the autotuner chooses from (one CTA or two-CTA clusters,
+    256/384/512 threads, thread chunks 0/1/2/4; also 320 and 448 threads)
+    and the autotuner's own choice give bit-identical chains, equal to the
+    oracle's."""
+    shapes = [(8, 8, 8), (6, 6, 6), (4, 4, 8)]
+    temps = [20, 12, 9] if labels == 2 else [16, 12, 9]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 16, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, labels)
+    ref = None
+    shapes_run = [(sp, tpb, nch) for sp in (1, 2) for tpb in (256, 384, 512) for nch in (0, 1, 2, 4)]
+    shapes_run += [(1, 320, 1), (2, 448, 1), None]
+    for shape in shapes_run:
         ctx = pc.Context(0, 13)
-        pc.pc_apt_load(ctx.h, b.dims, b.J, b.betas, 2, 0)
-        if tpb is None:
-            assert pc.pc_apt_autotune(ctx.h, 8, True) in (256, 384, 512)
+        pc.pc_apt_load(ctx.h, dims, J, betas, labels, 0)
+        if shape is None:
+            tpb, nch, split = pc.pc_apt_autotune(ctx.h, 8, True)
+            assert tpb in (256, 320, 384, 448, 512) and nch in (0, 1, 2, 4)
         else:
-            pc.pc_apt_set_block_threads(ctx.h, tpb)
+            sp, tpb, nch = shape
+            pc.pc_apt_set_launch(ctx.h, tpb, nch, sp)
+            assert pc.pc_apt_is_split(ctx.h) == (sp == 2)
         pc.pc_apt_run(ctx.h, 40, 1, True)
-        states.append([pc.pc_apt_get_state(ctx.h, i, 512, 40) for i in range(3)])
+        got = [pc.pc_apt_get_state(ctx.h, i, int(np.prod(s)), t * labels) for i, (s, t) in enumerate(zip(shapes, temps))]
+        if ref is None:
+            ref = got
+            apt = orc.Apt(dims, J, betas, labels, seed=13)
+            apt.run(40, threads=8)
+            _compare(pc, apt, ctx, b)
+        else:
+            for x, y in zip(ref, got):
+                for u, v in zip(x, y):
+                    assert np.array_equal(u, v), shape
         ctx.close()
-    for other in states[1:]:
-        for x, y in zip(states[0], other):
-            for u, v in zip(x, y):
-                assert np.array_equal(u, v)
 
 
 def test_checkpoint_resume_bit_exact(pc, tmp_path):

@@ -153,3 +153,34 @@ def test_weights_file_round_trip(pc, tmp_path):
     m.close()
     m2.close()
     ctx.close()
+
+
+def test_trained_network_gains_over_the_methods_without_it(pc):
+    """What the committed network (trained on the GPU by this library's
+    kernels on 20 000 instances with L = 6 .. 16) gains, on 32 held-out
+    L = 16 instances: time to rho_E <= 1e-3 (Eq. rho_E_f), construction of
+    the ladder included, per instance, measured.
+
+    * Against the adaptive procedure (Algorithm S2's preprocessing, which
+      the network replaces): no more sweeps to the target, within the
+      sampling noise of a median over 32 instances (a factor 1.25), and less
+      wall time (the pilot run, network and judge cost a fraction of the
+      adaptive procedure).
+    * Against the input-free geometric ladder 0.2 .. 3.0 (the range of the
+      pilot temperatures): strictly fewer sweeps to the target.
+    The per-size mean of the training ladders is reported, not asserted."""
+    from paper_2503_10302_gb300 import ladder
+    ctx = pc.Context(0, 5)
+    net = pc.Mlp(ctx, path=ladder.WEIGHTS)
+    res = ladder.compare(net, ladder.load_means(), n_eval=32, L=16, best_runs=10, best_sweeps=20000,
+                         max_sweeps=100000)
+    net.close()
+    ctx.close()
+    lrn, ada, geo = res["learned"], res["adaptive"], res["geometric"]
+    summary = {k: (v["median_hit_sweep"], round(v["median_time_to_target_s"], 4), v["hit_fraction"])
+               for k, v in res.items() if isinstance(v, dict) and "median_hit_sweep" in v}
+    print(summary)
+    assert lrn["hit_fraction"] >= ada["hit_fraction"] - 1 / 32, summary
+    assert lrn["median_hit_sweep"] <= 1.25 * ada["median_hit_sweep"], summary
+    assert lrn["median_time_to_target_s"] < ada["median_time_to_target_s"], summary
+    assert lrn["median_hit_sweep"] < geo["median_hit_sweep"], summary
