@@ -60,8 +60,8 @@ NCU_INSTR_PER_FLIP = 15.5
 # capture of the anneal kernel (mean of 3 timed launches), valid while the
 # kernel sources hash to TRAFFIC_SRC_SHA256; otherwise the bench reports
 # null.
-TRAFFIC_BYTES = 2359808          # mean of 3 timed launches: 2.34, 2.36, 2.38 MB
-TRAFFIC_SRC_SHA256 = "976abb0409016844245ab7e7ace6cc3f9b2f6339f07b5d5ec1382bde29689850"
+TRAFFIC_BYTES = 2218837          # mean of 3 timed launches: 1.68, 2.59, 2.39 MB
+TRAFFIC_SRC_SHA256 = "3bd5699b4935d0d8c167ac12c4ffe6ed4250f6acb66f74492ec0c50f32983131"
 TRAFFIC_SOURCES = ("paper_2503_10302_gb300/csrc/sqa.cu", "paper_2503_10302_gb300/csrc/device.cuh",
                    "paper_2503_10302_gb300/csrc/internal.h")
 WORKLOAD = f"DT-SQA 3D +-J L={L} periodic, P={P} slices, R={R} runs, T={T}, Gamma 3.0->1e-3 over {SWEEPS} sweeps"

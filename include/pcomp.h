@@ -402,10 +402,12 @@ int pc_gsqa_anneal(pc_ctx *ctx, int n, const int32_t *row_ptr, const int32_t *co
  * pair's acceptance pooled over the labels, accepts / attempts (-1 for a
  * pair the probe never attempted); pass_out [n] is 1 iff every attempted
  * pair reaches acc_floor, i.e. accepts >= acc_floor * attempts in double.
- * The adaptive procedure aims at a flat acceptance of erfc(alpha / 2)
- * (about 0.38 at the paper's alpha = 1.25; Supplementary "Temperature
- * profile and swap acceptance rate in APT"), so half of it is a natural
- * floor. */
+ * The adaptive procedure spaces temperatures so that dbeta sigma_E = alpha,
+ * a flat acceptance of erfc(alpha / 2) for Gaussian energies (about 0.38 at
+ * the paper's alpha = 1.25; Supplementary "Temperature profile and swap
+ * acceptance rate in APT": flat except the last pairs); erfc(1.25 alpha) =
+ * 0.027, the acceptance of a gap 2.5 times the adaptive one, is the floor
+ * the library's tools use. */
 int pc_ladder_judge(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
                     int n_temps, const double *betas, int n_labels, int probe_attempts, double acc_floor,
                     double *acc_out, int32_t *pass_out);
@@ -471,15 +473,18 @@ typedef struct {
  *      (probe_labels, probe_attempts, acc_floor; acc_out [n][31] nullable);
  *   6. every rejected instance falls back to pc_adaptive_ladder (same entry
  *      id) resampled to 32 points, and fallback_out [n] (nullable) is 1.
- * beta_out [n][32] receives the ladders (host). */
+ * beta_out [n][32] receives the ladders (host); ready_s [n] (nullable) the
+ * seconds (host clock) from the call's start until each instance's ladder
+ * was final: after the judge, or after its fallback. */
+int pc_learned_ladder(pc_ctx *ctx, pc_mlp *m, int n_inst, const int32_t *dims, const int8_t *J,
+                      uint32_t entry0, const pc_learned_opts *opt, double *beta_out, double *acc_out,
+                      int32_t *fallback_out, double *ready_s);
 /* Steps 1 and 2 alone (the pilot fields of opt): the network's inputs
  * X_out [n][259] fp32 (host), as pc_learned_ladder computes them; used to
  * build training sets. */
 int pc_learned_features(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
                         const pc_learned_opts *opt, float *X_out);
-int pc_learned_ladder(pc_ctx *ctx, pc_mlp *m, int n_inst, const int32_t *dims, const int8_t *J,
-                      uint32_t entry0, const pc_learned_opts *opt, double *beta_out, double *acc_out,
-                      int32_t *fallback_out);
+
 
 #ifdef __cplusplus
 }

@@ -168,7 +168,13 @@ struct Shared {
   int32_t *xch;      // split problems: [2][4] boundary energies by attempt parity;
                      // [8] accepted boundary labels; [12..17] the peer's best at launch end
   uint32_t *stage;   // [2][4][64] peer boundary spins by attempt parity, one bit per site
+  uint32_t *swt;     // split problems: [T-1][kSwtLen] first entries of each pair's swap table
 };
+
+// Entries of each pair's swap table (|dE| = 0, 2, .., 2 (kSwtLen - 1)) that a
+// split problem's CTAs keep in shared memory; larger |dE| read the table in
+// global memory.
+constexpr int kSwtLen = 64;
 
 struct Cta {
   Geo geo;
@@ -932,6 +938,7 @@ __device__ void push_boundary(const Cta &k, const Shared &sh, int kb, int par) {
 // pair from the same energies and random word, and take the peer's spins
 // for the accepted labels.  Buffers alternate with the attempt's parity, so
 // one barrier per attempt orders every exchange.
+template <bool SPLIT>
 __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int p, uint32_t t) {
   const AptProbDev &P = a.prob[p];
   const int A = k.A, q = (int)(t & 1u);
@@ -940,6 +947,7 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
   const int lb = 8 * k.Gu;
   auto swap_table = [&](int r, int dE) {
     const int kk = (-dE) >> 1;
+    if (SPLIT && kk < kSwtLen) return sh.swt[r * kSwtLen + kk];   // staged at launch
     const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
     return ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
   };
@@ -1113,6 +1121,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.gmap = reinterpret_cast<int32_t *>(cur);     cur += 8;
   sh.xch = reinterpret_cast<int32_t *>(cur);      cur += 24;
   sh.stage = cur;                                 cur += SPLIT ? 512 : 0;
+  sh.swt = cur;                                   cur += (SPLIT && MODE == pc::APT_MODE_APT) ? (size_t)max(k.T - 1, 0) * kSwtLen : 0;
   sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 + ((N + 31) >> 5) : 0;   // V, X, Xt, R
   sh.jn = reinterpret_cast<uint16_t *>(cur);
 
@@ -1143,6 +1152,12 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     sh.sacc[i] = 0;
   }
   if (threadIdx.x < 24) sh.xch[threadIdx.x] = 0;
+  if (SPLIT && MODE == pc::APT_MODE_APT)
+    for (int i = threadIdx.x; i < (k.T - 1) * kSwtLen; i += blockDim.x) {
+      const int r = i / kSwtLen, kk = i - r * kSwtLen;
+      const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
+      sh.swt[i] = ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
+    }
   if (MODE == pc::APT_MODE_PILOT)
     for (int i = threadIdx.x; i < k.T * a.n_bins; i += blockDim.x) sh.hist[i] = 0;
   if (threadIdx.x == 0) {
@@ -1204,7 +1219,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
         best_update(a, k, sh, p, sweeps);
         PROF_MARK(10, pt);
       }
-      swap_step(a, k, sh, p, t);
+      swap_step<SPLIT>(a, k, sh, p, t);
       __syncthreads();
       PROF_MARK(3, pt);
     }
@@ -1331,6 +1346,7 @@ size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n
   size_t words = (size_t)Gc * N + 32 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
   words += 4 * 64 + 24 + 24 + 128 + 8 + 24 + 512;   // + larger swap stats, group map, exchange, stage
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
+  if (mode == APT_MODE_APT) words += (size_t)(T > 1 ? T - 1 : 0) * kSwtLen;   // staged swap tables (split)
   // V, X, the transposed X (or the cluster labels) and the root masks
   if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31 + (size_t)((N + 31) >> 5);
   return words * 4 + (size_t)N * 2 + 16;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -1330,7 +1331,12 @@ int pc_learned_features(pc_ctx *c, int n_inst, const int32_t *dims, const int8_t
 }
 
 int pc_learned_ladder(pc_ctx *c, pc_mlp *m, int n_inst, const int32_t *dims, const int8_t *J, uint32_t entry0,
-                      const pc_learned_opts *o, double *beta_out, double *acc_out, int32_t *fallback_out) try {
+                      const pc_learned_opts *o, double *beta_out, double *acc_out, int32_t *fallback_out,
+                      double *ready_s) try {
+  const auto t_start = std::chrono::steady_clock::now();
+  auto seconds = [&]() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  };
   if (!c || !m || !dims || !J || !o || !o->pilot_betas || !beta_out) return fail(PC_EINVAL, "NULL argument");
   if (mlp_context(m) != c) return fail(PC_EINVAL, "the network must belong to this context");
   if (n_inst < 1) return fail(PC_EINVAL, "n_inst must be >= 1");
@@ -1369,6 +1375,8 @@ int pc_learned_ladder(pc_ctx *c, pc_mlp *m, int n_inst, const int32_t *dims, con
   if (!judge) {
     if (acc_out)
       for (size_t k = 0; k < (size_t)n_inst * (kLearnedLen - 1); ++k) acc_out[k] = -1.0;
+    if (ready_s)
+      for (int i = 0; i < n_inst; ++i) ready_s[i] = seconds();
     return PC_OK;
   }
   // (5) the judge: a short probe of every predicted ladder
@@ -1382,6 +1390,9 @@ int pc_learned_ladder(pc_ctx *c, pc_mlp *m, int n_inst, const int32_t *dims, con
     if (!judge_pass(att.data() + off, acc.data() + off, kLearnedLen, o->acc_floor, acc_out ? acc_out + off : nullptr))
       fail_idx.push_back(i);
   }
+  const double t_judged = seconds();
+  if (ready_s)
+    for (int i = 0; i < n_inst; ++i) ready_s[i] = t_judged;
   if (fail_idx.empty()) return PC_OK;
   // (6) fallback: the adaptive procedure for the instances the judge
   // rejected (entry ids unchanged), resampled to the network's length
@@ -1408,6 +1419,8 @@ int pc_learned_ladder(pc_ctx *c, pc_mlp *m, int n_inst, const int32_t *dims, con
       return rc;
     if (fallback_out) fallback_out[i] = 1;
   }
+  if (ready_s)
+    for (int i : fail_idx) ready_s[i] = seconds();
   return PC_OK;
 } catch (...) {
   return pc::fail_exception();

@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import time
 from typing import Dict, List, Sequence, Tuple
@@ -36,9 +37,14 @@ PILOT_KW = dict(pilot_chains=8, pilot_sweeps=256, pilot_burn=128)
 # the paper uses 100 chains, 10^4 sweeps and a tail of 10^3; these reduced
 # settings are used for the training labels and for the adaptive arm alike).
 LADDER_KW = dict(beta0=0.5, alpha=1.25, n_chains=32, sweeps=2000, tail=500, tol=1.0, max_len=64)
-# Judge: 200 probe attempts with 2 labels; a pair must accept at least half
-# of the adaptive procedure's design acceptance erfc(alpha/2) = 0.377.
-JUDGE_KW = dict(probe_attempts=200, probe_labels=2, acc_floor=0.19)
+# Judge: 500 probe attempts with 2 labels.  The adaptive procedure spaces
+# temperatures so that dbeta sigma_E = alpha, whose acceptance for Gaussian
+# energies is erfc(alpha / 2) = 0.377 at alpha = 1.25; a pair fails when its
+# acceptance is below erfc(1.25 alpha) = 0.027, that of a gap 2.5 times the
+# adaptive one.  (The adaptive ladders themselves, resampled to 32 points,
+# accept 0.07-0.13 at their coldest pair at L = 16, so a floor of half the
+# design acceptance would reject them too.)
+JUDGE_KW = dict(probe_attempts=500, probe_labels=2, acc_floor=math.erfc(1.25 * 1.25))
 SIZES = (6, 8, 10, 12, 14, 16)
 
 
@@ -172,26 +178,31 @@ def eval_set(n: int, L: int, seed: int = W.SEED_EVAL):
 
 
 def construct(arm: str, dims, J, net=None, means=None, entry0: int = 1 << 20, seed: int = 11,
-              judge_kw=None) -> Tuple[List[np.ndarray], float, Dict]:
-    """Ladders of one arm and the wall time to construct them (one batch)."""
+              judge_kw=None) -> Tuple[List[np.ndarray], float, Dict, np.ndarray]:
+    """Ladders of one arm, the wall time to construct them (one batch) and
+    the time at which each instance's ladder was ready: the learned arm
+    reports it per instance (after the judge, or after a fallback); the
+    adaptive arm's instances all wait for the batch."""
     info: Dict = {}
     n = len(J)
     if arm == "geometric":
-        return [W.geometric_ladder(32, 0.2, 3.0)] * n, 0.0, info
+        return [W.geometric_ladder(32, 0.2, 3.0)] * n, 0.0, info, np.zeros(n)
     if arm == "mean":
         L = int(dims[0][0])
-        return [means[L] + 0.0] * n, 0.0, info
+        return [means[L] + 0.0] * n, 0.0, info, np.zeros(n)
     owner = None if arm == "learned" else _ctx(seed)
     h = net.ctx if owner is None else owner.h
     pcomp.pc_synchronize(h)
     t0 = time.perf_counter()
+    ready = None
     if arm == "adaptive":
         lad = pcomp.pc_adaptive_ladder(h, dims, J, entry0=entry0, **LADDER_KW)
         betas = [pcomp.pc_resample_ladder(b, 32) for b, _, _ in lad]
         info["ladder_lengths"] = [len(b) for b, _, _ in lad]
     elif arm == "learned":
-        beta, acc, fb = pcomp.pc_learned_ladder(h, net, dims, J, PILOT_BETAS, entry0=entry0, **PILOT_KW,
-                                                **dict(JUDGE_KW, **(judge_kw or {})), **LADDER_KW)
+        beta, acc, fb, ready = pcomp.pc_learned_ladder(h, net, dims, J, PILOT_BETAS, entry0=entry0, **PILOT_KW,
+                                                       **dict(JUDGE_KW, **(judge_kw or {})), **LADDER_KW,
+                                                       with_ready=True)
         betas = list(beta)
         info["fallback"] = int(fb.sum())
         info["min_pair_acceptance"] = float(np.where(acc >= 0, acc, 1.0).min())
@@ -201,17 +212,17 @@ def construct(arm: str, dims, J, net=None, means=None, entry0: int = 1 << 20, se
     dt = time.perf_counter() - t0
     if owner is not None:
         owner.close()
-    return betas, dt, info
+    return betas, dt, info, (np.full(n, dt) if ready is None else ready)
 
 
 def compare(net, means, n_eval: int = 128, L: int = 16, rho: float = 1e-3, best_runs: int = 10,
             best_sweeps: int = 20000, max_sweeps: int = 100000,
             arms: Sequence[str] = ("learned", "adaptive", "geometric", "mean")) -> Dict:
     """Time to rho_E <= rho (Eq. rho_E_f) on n_eval held-out L^3 instances,
-    one APT+ICM batch per arm.  An instance's time is the arm's ladder
-    construction time plus the measured run time up to the chunk in which
-    it reached the target.  E_best is the best over best_runs runs on the
-    adaptive ladders (sweep-to-swap ratio 10) and every arm's runs."""
+    one APT+ICM batch per arm.  An instance's time is the time its ladder
+    was ready plus the measured run time up to the chunk in which it
+    reached the target.  E_best is the best over best_runs runs on the
+    adaptive ladders (sweep-to-swap ratio 10)."""
     dims, J = eval_set(n_eval, L)
     N = L ** 3
     ladders = {}
@@ -226,10 +237,10 @@ def compare(net, means, n_eval: int = 128, L: int = 16, rho: float = 1e-3, best_
            "e_best_seconds": t_best, "max_sweeps": max_sweeps, "adaptive_settings": LADDER_KW,
            "judge": JUDGE_KW, "pilot": PILOT_KW}
     for arm in arms:
-        betas, t_lad, info = ladders[arm]
+        betas, t_lad, info, ready = ladders[arm]
         hit, t_hit, t_sweep = run_to_target(dims, J, betas, targets, max_sweeps)
         ok = hit >= 0
-        tt = t_lad + t_hit
+        tt = ready + t_hit
         out[arm] = dict(info, ladder_seconds=t_lad, apt_seconds_per_sweep=t_sweep, hit_fraction=float(ok.mean()),
                         median_hit_sweep=float(np.median(np.where(ok, hit, max_sweeps))),
                         median_time_to_target_s=float(np.median(tt)),

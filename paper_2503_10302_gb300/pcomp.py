@@ -107,7 +107,8 @@ SIGNATURES = {
     "pc_ladder_judge": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_u32, c_int, c_f64p, c_int, c_int, c_dbl, c_f64p,
                                 c_i32p]),
     "pc_learned_features": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_u32, c_vp, c_f32p]),
-    "pc_learned_ladder": (c_int, [c_vp, c_vp, c_int, c_i32p, c_i8p, c_u32, c_vp, c_f64p, c_f64p, c_i32p]),
+    "pc_learned_ladder": (c_int, [c_vp, c_vp, c_int, c_i32p, c_i8p, c_u32, c_vp, c_f64p, c_f64p, c_i32p,
+                                  c_f64p]),
 }
 
 _lib = None
@@ -459,7 +460,7 @@ def pc_instance_features(dims, J) -> np.ndarray:
     return out
 
 
-def pc_ladder_judge(ctx, dims, J_list, betas, entry0=0, n_labels=2, probe_attempts=200, acc_floor=0.19):
+def pc_ladder_judge(ctx, dims, J_list, betas, entry0=0, n_labels=2, probe_attempts=500, acc_floor=0.0271):
     """Swap-acceptance judge of ladders [n][T]: (acceptance [n][T-1], pass [n])."""
     n = len(J_list)
     d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(n, 3))
@@ -510,10 +511,11 @@ def pc_learned_features(ctx, dims, J_list, pilot_betas, entry0=0, pilot_chains=8
 
 
 def pc_learned_ladder(ctx, mlp, dims, J_list, pilot_betas, entry0=0, pilot_chains=8, pilot_sweeps=256,
-                      pilot_burn=128, probe_attempts=200, probe_labels=2, acc_floor=0.19, beta0=0.5,
-                      alpha=1.25, n_chains=32, sweeps=2000, tail=500, tol=1.0, max_len=64):
+                      pilot_burn=128, probe_attempts=500, probe_labels=2, acc_floor=0.0271, beta0=0.5,
+                      alpha=1.25, n_chains=32, sweeps=2000, tail=500, tol=1.0, max_len=64, with_ready=False):
     """Learned ladders [n][32] with the judge's acceptances [n][31] and the
-    fallback flags [n] (pc_learned_ladder)."""
+    fallback flags [n] (pc_learned_ladder); with_ready adds each instance's
+    ready time [n] in seconds."""
     n = len(J_list)
     d = np.ascontiguousarray(np.asarray(dims, np.int32).reshape(n, 3))
     J = _concat_J(J_list)
@@ -523,9 +525,12 @@ def pc_learned_ladder(ctx, mlp, dims, J_list, pilot_betas, entry0=0, pilot_chain
     beta = np.zeros((n, 32), np.float64)
     acc = np.zeros((n, 31), np.float64)
     fb = np.zeros(n, np.int32)
+    ready = np.zeros(n, np.float64)
     _call("pc_learned_ladder", ctx, mlp.h if isinstance(mlp, Mlp) else mlp, n, ptr(d, ctypes.c_int32),
           ptr(J, ctypes.c_int8), c_u32(entry0), ctypes.byref(o), ptr(beta, ctypes.c_double),
-          ptr(acc, ctypes.c_double), ptr(fb, ctypes.c_int32))
+          ptr(acc, ctypes.c_double), ptr(fb, ctypes.c_int32), ptr(ready, ctypes.c_double))
+    if with_ready:
+        return beta, acc, fb.astype(bool), ready
     return beta, acc, fb.astype(bool)
 
 
