@@ -33,6 +33,15 @@
 #ifndef PC_APT_PROFILE
 #define PC_APT_PROFILE 0
 #endif
+// Relaxations of a flood-fill block between two barriers (build-time knob).
+#ifndef PC_APT_FILL_RELAX
+#define PC_APT_FILL_RELAX 1
+#endif
+// Split problems keep the first entries of their swap tables in shared
+// memory (build-time knob).
+#ifndef PC_APT_STAGE_SWT
+#define PC_APT_STAGE_SWT 1
+#endif
 #if PC_APT_PROFILE
 __device__ unsigned long long g_apt_prof[16];
 #define PROF_MARK(slot, t0)                                                     \
@@ -741,6 +750,11 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
 #pragma unroll
           for (int i = 0; i < 8; ++i) x[i] = X[B.kk[i]];
           changed = relax(B, x, v);
+#if PC_APT_FILL_RELAX > 1
+          // a second relaxation before the barrier reads whatever the
+          // neighbours have written meanwhile (monotone: still exact)
+          if (changed) relax(B, x, v);
+#endif
 #pragma unroll
           for (int i = 0; i < 8; ++i) o |= x[i] & ~v[i];
           open = o != 0;
@@ -947,7 +961,7 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
   const int lb = 8 * k.Gu;
   auto swap_table = [&](int r, int dE) {
     const int kk = (-dE) >> 1;
-    if (SPLIT && kk < kSwtLen) return sh.swt[r * kSwtLen + kk];   // staged at launch
+    if (PC_APT_STAGE_SWT && SPLIT && kk < kSwtLen) return sh.swt[r * kSwtLen + kk];   // staged at launch
     const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
     return ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
   };
@@ -1152,7 +1166,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     sh.sacc[i] = 0;
   }
   if (threadIdx.x < 24) sh.xch[threadIdx.x] = 0;
-  if (SPLIT && MODE == pc::APT_MODE_APT)
+  if (PC_APT_STAGE_SWT && SPLIT && MODE == pc::APT_MODE_APT)
     for (int i = threadIdx.x; i < (k.T - 1) * kSwtLen; i += blockDim.x) {
       const int r = i / kSwtLen, kk = i - r * kSwtLen;
       const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];

@@ -260,9 +260,12 @@ def main():
     ap.add_argument("--best-runs", type=int, default=10)
     ap.add_argument("--best-sweeps", type=int, default=20000)
     ap.add_argument("--max-sweeps", type=int, default=100000)
+    ap.add_argument("--dump", help="train: also save the training set (X, Y, L) to this .npz")
     args = ap.parse_args()
     if args.what == "train":
         ts = training_set(args.n_train)
+        if args.dump:
+            np.savez_compressed(args.dump, X=ts["X"], Y=ts["Y"], L=ts["L"], len=ts["len"])
         m, ctx, hist, t_train = train(ts["X"], ts["Y"], epochs=args.epochs)
         os.makedirs(os.path.dirname(args.out), exist_ok=True)
         m.save(args.out)
