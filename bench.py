@@ -236,7 +236,8 @@ def apt_metrics(stream, peak_tops: float, attempts: int = 256) -> dict:
         pcomp.pc_set_stream(ctx.h, stream.cuda_stream)
         pcomp.pc_apt_load(ctx.h, batch.dims, batch.J, batch.betas, batch.n_labels, 0)
         shape = pcomp.pc_apt_autotune(ctx.h, 16, True)     # launch shape of the fused kernel
-        out[name + "_launch"] = {"threads": shape[0], "thread_chunks": shape[1], "two_cta_clusters": shape[2]}
+        out[name + "_launch"] = {"threads": shape[0], "thread_chunks": shape[1], "two_cta_clusters": shape[2],
+                                 "split_groups": shape[3]}
         for icm in icms:
             v = timed(ctx, batch.spins_per_sweep(), icm)
             key = f"{name}_{'e2e' if icm else 'sweep_only'}"

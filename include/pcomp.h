@@ -155,18 +155,23 @@ int pc_apt_is_split(pc_ctx *ctx, int *split);
  * of every candidate on a scratch copy of the loaded batch (the loaded
  * chains do not move) and keeps the fastest for later pc_apt_run calls.
  * Candidates: the placement (one CTA per problem, or two-CTA clusters that
- * split the temperatures, where every problem has at least 9), threads per
- * CTA (256, 320, 384, 448, 512), and the split of those threads over sites and
- * replica groups (nch chunks of threads, each sweeping ceil(groups / nch)
- * groups of its sites; 0 = a cost model's choice, or 1, 2, 4).  Returns the
- * choice in *tpb, *nch and *split (1 = two-CTA clusters); any may be NULL.
- * Results do not depend on the shape: randomness is keyed by slot and
- * site. */
-int pc_apt_autotune(pc_ctx *ctx, int trial_swaps, int icm, int *tpb, int *nch, int *split);
+ * split the temperatures, where every problem has at least 9), for two-CTA
+ * clusters the split point (the colder CTA takes the groups of 8
+ * temperatures above the first split_groups of each label; 0 = half), threads
+ * per CTA (256, 320, 384, 448, 512), and the split of those threads over
+ * sites and replica groups (nch chunks of threads, each sweeping
+ * ceil(groups / nch) groups of its sites; 0 = a cost model's choice, or 1, 2,
+ * 4).  Returns the choice in *tpb, *nch, *split (1 = two-CTA clusters) and
+ * *split_groups; any may be NULL.  Results do not depend on the shape:
+ * randomness is keyed by slot and site. */
+int pc_apt_autotune(pc_ctx *ctx, int trial_swaps, int icm, int *tpb, int *nch, int *split,
+                    int *split_groups);
 /* Set the launch shape directly: tpb threads per CTA (a multiple of 64 in
  * [64, 512]), nch thread chunks (0, 1, 2, 4 or 8; applied where it fits,
- * else the cost model decides), split_pref as pc_apt_set_split. */
-int pc_apt_set_launch(pc_ctx *ctx, int tpb, int nch, int split_pref);
+ * else the cost model decides), split_pref as pc_apt_set_split, and
+ * split_groups (0 .. 3) the temperature groups per label of the hotter CTA of
+ * a split problem (0: half; clamped to leave the colder CTA one). */
+int pc_apt_set_launch(pc_ctx *ctx, int tpb, int nch, int split_pref, int split_groups);
 /* Set the threads per CTA directly (multiple of 64 in [64, 512]). */
 int pc_apt_set_block_threads(pc_ctx *ctx, int tpb);
 /* Checkpoint / resume: pc_apt_save writes the batch's dynamic state

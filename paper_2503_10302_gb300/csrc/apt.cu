@@ -33,10 +33,6 @@
 #ifndef PC_APT_PROFILE
 #define PC_APT_PROFILE 0
 #endif
-// Relaxations of a flood-fill block between two barriers (build-time knob).
-#ifndef PC_APT_FILL_RELAX
-#define PC_APT_FILL_RELAX 1
-#endif
 // Split problems keep the first entries of their swap tables in shared
 // memory (build-time knob).
 #ifndef PC_APT_STAGE_SWT
@@ -750,11 +746,6 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
 #pragma unroll
           for (int i = 0; i < 8; ++i) x[i] = X[B.kk[i]];
           changed = relax(B, x, v);
-#if PC_APT_FILL_RELAX > 1
-          // a second relaxation before the barrier reads whatever the
-          // neighbours have written meanwhile (monotone: still exact)
-          if (changed) relax(B, x, v);
-#endif
 #pragma unroll
           for (int i = 0; i < 8; ++i) o |= x[i] & ~v[i];
           open = o != 0;
@@ -1103,9 +1094,9 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   k.tpc = blockDim.x / k.nch;
   k.gc = (k.Gc + k.nch - 1) / k.nch;
   const int N = P.N;
-  // both CTAs of a split problem carve shared memory alike (rank 0 holds the
-  // larger half), so that distributed-shared-memory addresses correspond
-  const int Gcarve = SPLIT ? k.A * ((k.Glp + 1) >> 1) : k.Gc, G8 = 8 * Gcarve;
+  // both CTAs of a split problem carve shared memory alike (for the larger
+  // of the two parts), so that distributed-shared-memory addresses correspond
+  const int Gcarve = SPLIT ? k.A * max(k.Gu, k.Glp - k.Gu) : k.Gc, G8 = 8 * Gcarve;
   const int64_t s0 = a.ctr[0], t0 = a.ctr[1];
   const bool icm = MODE == pc::APT_MODE_APT && a.icm;
   // carve shared memory

@@ -43,6 +43,7 @@ struct Batch {
   int split = 0;         // APT problems run as clusters of two CTAs (by temperature)
   int split_pref = 0;    // 0: when needed or when the batch fills at most half the SMs; 1: only when needed; 2: whenever possible
   int nch_pref = 0;      // thread chunks per CTA: 0 = the cost model's choice, else this count where it fits
+  int split_h = 0;       // split problems: temperature groups per label on rank 0 (0: half)
   size_t smem = 0;
   std::vector<uint32_t> h_pbit, h_swaptab, h_swapidx;
 };
@@ -304,7 +305,8 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
     const int G = bt.G[(size_t)i];
     if (bt.split) {
       // rank 0: temperature groups [0, h1) of every label, rank 1: [h1, Glp)
-      const int Glp = P.Tp >> 3, h1 = (Glp + 1) / 2;
+      const int Glp = P.Tp >> 3;
+      const int h1 = bt.split_h > 0 ? std::min(bt.split_h, Glp - 1) : (Glp + 1) / 2;
       for (int rank = 0; rank < 2; ++rank) {
         const int g0 = rank ? h1 : 0, gu = rank ? Glp - h1 : h1;
         cp.push_back(i);
@@ -312,7 +314,7 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
         cgc.push_back(P.A * gu);
         cnch.push_back(choose_nch(P.N / 2, P.A * gu, bt.tpb, bt.nch_pref));
       }
-      smem = std::max(smem, apt_smem_bytes(P.N, P.A * h1, bt.tpb / 32, mode, icm, P.T, n_bins));
+      smem = std::max(smem, apt_smem_bytes(P.N, P.A * std::max(h1, Glp - h1), bt.tpb / 32, mode, icm, P.T, n_bins));
       continue;
     }
     // equal chunks of at most gmax groups
@@ -645,17 +647,19 @@ namespace {
 
 // Re-schedules the loaded batch with a new launch shape; the chains do not
 // move.  On failure the old shape is restored.
-int apply_shape(pc_ctx *c, AptImpl *im, int tpb, int nch_pref, int split_pref) {
+int apply_shape(pc_ctx *c, AptImpl *im, int tpb, int nch_pref, int split_pref, int split_h) {
   Batch &bt = im->bt;
-  const int o_tpb = bt.tpb, o_nch = bt.nch_pref, o_split = bt.split_pref;
+  const int o_tpb = bt.tpb, o_nch = bt.nch_pref, o_split = bt.split_pref, o_h = bt.split_h;
   bt.tpb = tpb;
   bt.nch_pref = nch_pref;
   bt.split_pref = split_pref;
+  bt.split_h = split_h;
   int rc = schedule(c, bt, {}, APT_MODE_APT, im->A >= 2, 0);
   if (rc) {
     bt.tpb = o_tpb;
     bt.nch_pref = o_nch;
     bt.split_pref = o_split;
+    bt.split_h = o_h;
     schedule(c, bt, {}, APT_MODE_APT, im->A >= 2, 0);
     return rc;
   }
@@ -670,7 +674,8 @@ int apply_shape(pc_ctx *c, AptImpl *im, int tpb, int nch_pref, int split_pref) {
 
 extern "C" {
 
-int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_out, int *split_out) try {
+int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_out, int *split_out,
+                    int *groups_out) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (trial_swaps < 1) return fail(PC_EINVAL, "trial_swaps must be >= 1");
   AptImpl *im = apt_impl(c);
@@ -682,14 +687,19 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_
   // per CTA, and the threads' split over sites and replica groups
   bool can_split = true;
   for (const AptProbDev &P : im->bt.prob) can_split = can_split && (P.Tp >> 3) >= 2;
+  int glp_max = 0;
+  for (const AptProbDev &P : im->bt.prob) glp_max = std::max(glp_max, P.Tp >> 3);
   const int splits[2] = {1, 2}, tpbs[5] = {256, 320, 384, 448, 512}, nchs[4] = {0, 1, 2, 4};
-  struct Best { float ms; int tpb, nch, split; } best = {1e30f, im->bt.tpb, im->bt.nch_pref, im->bt.split_pref};
+  struct Best { float ms; int tpb, nch, split, h; } best = {1e30f, im->bt.tpb, im->bt.nch_pref, im->bt.split_pref,
+                                                            im->bt.split_h};
   cudaEvent_t e0, e1;
   PC_CUDA_TRY(cudaEventCreate(&e0));
   PC_CUDA_TRY(cudaEventCreate(&e1));
   int rc = PC_OK;
-  for (int sp : splits) {
+  for (int sp : splits)
+   for (int h = 0; h <= (sp == 2 ? std::min(3, glp_max - 1) : 0); ++h) {
     if (sp == 2 && !can_split) continue;
+    if (sp == 2 && h > 0 && 2 * h == glp_max) continue;   // the even split is h = 0
     for (int tpb : tpbs)
       for (int nch : nchs) {
         if (rc) break;
@@ -698,6 +708,7 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_
         tmp.tpb = tpb;
         tmp.split_pref = sp;
         tmp.nch_pref = nch;
+        tmp.split_h = h;
         if ((rc = build_batch(c, tmp, im->specs, 0))) break;
         if (schedule(c, tmp, {}, APT_MODE_APT, im->A >= 2, 0)) continue;   // does not fit: skip
         if (nch > 0) {   // skip a forced split that the schedule could not honour
@@ -726,29 +737,31 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_
         PC_CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;
         PC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best.ms) best = {ms, tpb, nch, sp};
+        if (ms < best.ms) best = {ms, tpb, nch, sp, h};
       }
-  }
+   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  if ((rc = apply_shape(c, im, best.tpb, best.nch, best.split))) return rc;
+  if ((rc = apply_shape(c, im, best.tpb, best.nch, best.split, best.h))) return rc;
   if (tpb_out) *tpb_out = best.tpb;
   if (nch_out) *nch_out = best.nch;
   if (split_out) *split_out = im->bt.split;
+  if (groups_out) *groups_out = im->bt.split ? best.h : 0;
   return PC_OK;
 } catch (...) {
   return pc::fail_exception();
 }
 
-int pc_apt_set_launch(pc_ctx *c, int tpb, int nch, int split_pref) try {
+int pc_apt_set_launch(pc_ctx *c, int tpb, int nch, int split_pref, int split_groups) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (tpb < 64 || tpb > 512 || tpb % 64) return fail(PC_EINVAL, "tpb must be a multiple of 64 in [64, 512]");
   if (nch < 0 || nch > 8 || (nch & (nch - 1))) return fail(PC_EINVAL, "nch must be 0, 1, 2, 4 or 8");
   if (split_pref < 0 || split_pref > 2) return fail(PC_EINVAL, "split_pref must be 0, 1 or 2");
+  if (split_groups < 0 || split_groups > 3) return fail(PC_EINVAL, "split_groups must be 0 .. 3");
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  return apply_shape(c, apt_impl(c), tpb, nch, split_pref);
+  return apply_shape(c, apt_impl(c), tpb, nch, split_pref, split_groups);
 } catch (...) {
   return pc::fail_exception();
 }
@@ -759,7 +772,7 @@ int pc_apt_set_split(pc_ctx *c, int pref) try {
   AptImpl *im = apt_impl(c);
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  return apply_shape(c, im, im->bt.tpb, im->bt.nch_pref, pref);
+  return apply_shape(c, im, im->bt.tpb, im->bt.nch_pref, pref, im->bt.split_h);
 } catch (...) {
   return pc::fail_exception();
 }
@@ -778,7 +791,7 @@ int pc_apt_set_block_threads(pc_ctx *c, int tpb) try {
   AptImpl *im = apt_impl(c);
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
-  return apply_shape(c, im, tpb, im->bt.nch_pref, im->bt.split_pref);
+  return apply_shape(c, im, tpb, im->bt.nch_pref, im->bt.split_pref, im->bt.split_h);
 } catch (...) {
   return pc::fail_exception();
 }

@@ -49,8 +49,8 @@ SIGNATURES = {
     "pc_apt_set_split": (c_int, [c_vp, c_int]),
     "pc_apt_is_split": (c_int, [c_vp, ctypes.POINTER(c_int)]),
     "pc_apt_autotune": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
-                                ctypes.POINTER(c_int)]),
-    "pc_apt_set_launch": (c_int, [c_vp, c_int, c_int, c_int]),
+                                ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "pc_apt_set_launch": (c_int, [c_vp, c_int, c_int, c_int, c_int]),
     "pc_apt_set_block_threads": (c_int, [c_vp, c_int]),
     "pc_apt_save": (c_int, [c_vp, ctypes.c_char_p]),
     "pc_apt_restore": (c_int, [c_vp, ctypes.c_char_p]),
@@ -339,14 +339,16 @@ def pc_apt_run(ctx, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True) ->
 
 
 def pc_apt_autotune(ctx, trial_swaps: int = 16, icm: bool = True):
-    """Returns the chosen (threads per CTA, thread chunks, two-CTA clusters)."""
-    tpb, nch, split = c_int(), c_int(), c_int()
-    _call("pc_apt_autotune", ctx, trial_swaps, int(icm), ctypes.byref(tpb), ctypes.byref(nch), ctypes.byref(split))
-    return tpb.value, nch.value, bool(split.value)
+    """Returns the chosen (threads per CTA, thread chunks, two-CTA clusters,
+    split groups)."""
+    tpb, nch, split, grp = c_int(), c_int(), c_int(), c_int()
+    _call("pc_apt_autotune", ctx, trial_swaps, int(icm), ctypes.byref(tpb), ctypes.byref(nch), ctypes.byref(split),
+          ctypes.byref(grp))
+    return tpb.value, nch.value, bool(split.value), grp.value
 
 
-def pc_apt_set_launch(ctx, tpb: int, nch: int = 0, split_pref: int = 0) -> None:
-    _call("pc_apt_set_launch", ctx, tpb, nch, split_pref)
+def pc_apt_set_launch(ctx, tpb: int, nch: int = 0, split_pref: int = 0, split_groups: int = 0) -> None:
+    _call("pc_apt_set_launch", ctx, tpb, nch, split_pref, split_groups)
 
 
 def pc_apt_set_block_threads(ctx, tpb: int) -> None:

@@ -404,10 +404,10 @@ def test_c4_mixed_batch_sampled(pc, orc):
 
 @pytest.mark.parametrize("labels", [2, 4])
 def test_launch_shape_does_not_change_results(pc, orc, labels):
-    """Shapes the autotuner chooses from (one CTA or two-CTA clusters,
-    256/384/512 threads, thread chunks 0/1/2/4; also 320 and 448 threads)
-    and the autotuner's own choice give bit-identical chains, equal to the
-    oracle's."""
+    """Shapes the autotuner chooses from (one CTA or two-CTA clusters split
+    evenly or unevenly, 256/384/512 threads, thread chunks 0/1/2/4; also 320
+    and 448 threads) and the autotuner's own choice give bit-identical
+    chains, equal to the oracle's."""
     shapes = [(8, 8, 8), (6, 6, 6), (4, 4, 8)]
     temps = [20, 12, 9] if labels == 2 else [16, 12, 9]
     dims = np.array(shapes, np.int32)
@@ -415,17 +415,17 @@ def test_launch_shape_does_not_change_results(pc, orc, labels):
     betas = [W.geometric_ladder(t) for t in temps]
     b = W.AptBatch(dims, J, betas, labels)
     ref = None
-    shapes_run = [(sp, tpb, nch) for sp in (1, 2) for tpb in (256, 384, 512) for nch in (0, 1, 2, 4)]
-    shapes_run += [(1, 320, 1), (2, 448, 1), None]
+    shapes_run = [(sp, tpb, nch, 0) for sp in (1, 2) for tpb in (256, 384, 512) for nch in (0, 1, 2, 4)]
+    shapes_run += [(1, 320, 1, 0), (2, 448, 1, 0), (2, 512, 0, 1), (2, 256, 2, 3), None]
     for shape in shapes_run:
         ctx = pc.Context(0, 13)
         pc.pc_apt_load(ctx.h, dims, J, betas, labels, 0)
         if shape is None:
-            tpb, nch, split = pc.pc_apt_autotune(ctx.h, 8, True)
-            assert tpb in (256, 320, 384, 448, 512) and nch in (0, 1, 2, 4)
+            tpb, nch, split, grp = pc.pc_apt_autotune(ctx.h, 8, True)
+            assert tpb in (256, 320, 384, 448, 512) and nch in (0, 1, 2, 4) and grp in (0, 1, 2, 3)
         else:
-            sp, tpb, nch = shape
-            pc.pc_apt_set_launch(ctx.h, tpb, nch, sp)
+            sp, tpb, nch, grp = shape
+            pc.pc_apt_set_launch(ctx.h, tpb, nch, sp, grp)
             assert pc.pc_apt_is_split(ctx.h) == (sp == 2)
         pc.pc_apt_run(ctx.h, 40, 1, True)
         got = [pc.pc_apt_get_state(ctx.h, i, int(np.prod(s)), t * labels) for i, (s, t) in enumerate(zip(shapes, temps))]
