@@ -418,8 +418,10 @@ int pc_ladder_judge(pc_ctx *ctx, int n_inst, const int32_t *dims, const int8_t *
                     double *acc_out, int32_t *pass_out);
 
 /* MLP 259 -> 256 -> 256 -> 256 -> 32 (ReLU hidden), head
- * beta_k = beta_min + sum_{m<=k} softplus(o_m), loss = mean (beta - y)^2,
- * fp32 on the GPU, Adam.  W[l] is [out][in] row-major, b[l] is [out]. */
+ * beta_k = beta_min + sum_{m<=k} softplus(o_m), loss = mean (beta - y)^2
+ * + gap_weight * mean_{k>=1} ((softplus(o_k) - d_k) / d_k)^2 with d_k =
+ * y_k - y_{k-1} the target's gaps (gap_weight 0 unless set), fp32 on the
+ * GPU, Adam.  W[l] is [out][in] row-major, b[l] is [out]. */
 typedef struct pc_mlp pc_mlp;
 int pc_mlp_create(pc_ctx *ctx, pc_mlp **out, const float *const *W, const float *const *b,
                   float beta_min);
@@ -439,6 +441,11 @@ int pc_mlp_train_step(pc_mlp *m, int batch, const float *X, const float *Y, floa
 int pc_mlp_train_step_dev(pc_mlp *m, int batch, const float *X_dev, const float *Y_dev,
                           float lr, float *loss_dev);
 int pc_mlp_get_params(pc_mlp *m, float *const *W, float *const *b);
+/* Weight of the relative-gap term of later training steps and gradients
+ * (>= 0).  A pair's swap acceptance depends on its gap, and the squared
+ * error of the cumulative ladder alone barely penalises gap errors that
+ * cancel between neighbours. */
+int pc_mlp_set_gap_weight(pc_mlp *m, float w);
 /* Weights file of the network: the bytes "PCMLP001", the five layer widths
  * (int32), beta_min (fp32), then W[l] and b[l] of each layer (fp32,
  * little-endian).  pc_mlp_load creates a network on ctx from such a file

@@ -9,7 +9,12 @@ instances of one size, which makes them learnable from cheap features.
 
 Network: x (259) -> 256 -> 256 -> 256 (ReLU each) -> o (32).
 Monotone head: beta_k = beta_min + sum_{m<=k} softplus(o_m).
-Loss: mean over batch and the 32 outputs of (beta_k - y_k)^2.
+Loss: mean over batch and the 32 outputs of (beta_k - y_k)^2, plus
+gap_weight times the mean over batch and the 31 gaps k >= 1 of
+((g_k - d_k) / d_k)^2, with g_k = softplus(o_k) = beta_k - beta_{k-1} and
+d_k = y_k - y_{k-1} the target's gap (the swap acceptance of a pair depends
+on its gap; the squared error of the cumulative ladder alone barely
+constrains gap errors that cancel between neighbours).
 
 Features of an instance (also restated here): [L/16, fraction of J > 0,
 fraction of frustrated plaquettes, 4 x 64 normalised pilot histograms].
@@ -49,14 +54,23 @@ def forward(params: Sequence[Tuple[np.ndarray, np.ndarray]], X: np.ndarray, beta
     return beta, (acts, pre)
 
 
-def loss_and_grads(params, X, Y, beta_min: float = 0.0):
-    """MSE loss and gradients w.r.t. every W and b."""
+def loss_and_grads(params, X, Y, beta_min: float = 0.0, gap_weight: float = 0.0):
+    """Loss (squared ladder error plus gap_weight times the squared relative
+    gap error) and gradients w.r.t. every W and b."""
     beta, (acts, pre) = forward(params, X, beta_min)
-    diff = beta - np.asarray(Y, np.float64)
+    Y = np.asarray(Y, np.float64)
+    diff = beta - Y
     loss = float((diff ** 2).mean())
     g_beta = 2.0 * diff / diff.size
     # beta_k = sum_{m<=k} softplus(o_m)  =>  dL/do_m = sigmoid(o_m) sum_{k>=m} dL/dbeta_k
     g = sigmoid(pre[-1]) * np.cumsum(g_beta[:, ::-1], axis=1)[:, ::-1]
+    if gap_weight:
+        o = pre[-1][:, 1:]
+        d = np.diff(Y, axis=1)
+        r = (softplus(o) - d) / d
+        loss += gap_weight * float((r ** 2).mean())
+        # d softplus(o) / do = sigmoid(o)
+        g[:, 1:] += gap_weight * 2.0 * r / d * sigmoid(o) / r.size
     grads: List[Tuple[np.ndarray, np.ndarray]] = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         W = np.asarray(params[li][0], np.float64)

@@ -306,7 +306,10 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
     if (bt.split) {
       // rank 0: temperature groups [0, h1) of every label, rank 1: [h1, Glp)
       const int Glp = P.Tp >> 3;
-      const int h1 = bt.split_h > 0 ? std::min(bt.split_h, Glp - 1) : (Glp + 1) / 2;
+      int h1 = bt.split_h > 0 ? std::min(bt.split_h, Glp - 1) : (Glp + 1) / 2;
+      // each CTA holds at most kMaxGcCta groups (64 replicas, and 32 ICM
+      // pair bits): an uneven split that breaks this falls back to the even one
+      if (P.A * h1 > kMaxGcCta || P.A * (Glp - h1) > kMaxGcCta) h1 = (Glp + 1) / 2;
       for (int rank = 0; rank < 2; ++rank) {
         const int g0 = rank ? h1 : 0, gu = rank ? Glp - h1 : h1;
         cp.push_back(i);
@@ -329,6 +332,8 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
     }
   }
   bt.n_cta = (int)cp.size();
+  for (int g : cgc)
+    if (g < 1 || g > kMaxGcCta) return fail(PC_EINVAL, "internal: a CTA would hold more than 64 replicas");
   if (smem > (size_t)c->smem_optin) return fail(PC_EINVAL, "problem does not fit in shared memory");
   bt.smem = smem;
   std::vector<int> all;

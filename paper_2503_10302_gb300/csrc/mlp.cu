@@ -1,5 +1,6 @@
 // Learned beta-ladder predictor: an fp32 MLP 259 -> 256 -> 256 -> 256 -> 32
-// with a monotone head, trained with Adam.  The paper has no learned
+// with a monotone head, trained with Adam on the squared ladder error plus an
+// optional relative-gap term.  The paper has no learned
 // component; the predictor replaces the adaptive-ladder preprocessing of
 // Algorithm S2 by a network reading cheap instance features and short pilot
 // histograms, on the grounds that ladders of one size are nearly identical
@@ -86,14 +87,19 @@ __device__ __forceinline__ float softplus_f(float x) {
 }
 
 // One warp per sample: beta_k = beta_min + sum_{m<=k} softplus(o_m);
-// loss_s = sum_k (beta_k - y_k)^2; dO_m = sigmoid(o_m) sum_{k>=m} dL/dbeta_k
-// with dL/dbeta_k = 2 (beta_k - y_k) / (B * 32).
-__global__ void head_kernel(int B, const float *O, const float *Y, float beta_min, float *beta_out,
+// loss_s = sum_k (beta_k - y_k)^2 + gw (32/31) sum_{k>=1} r_k^2 with the
+// relative gap error r_k = (softplus(o_k) - d_k) / d_k, d_k = y_k - y_{k-1},
+// so that sum_s loss_s / (B * 32) is the mean squared ladder error plus gw
+// times the mean squared relative gap error; dO_m = sigmoid(o_m) (sum_{k>=m}
+// dL/dbeta_k + [m >= 1] 2 gw r_m / (d_m B * 31)) with dL/dbeta_k =
+// 2 (beta_k - y_k) / (B * 32).
+__global__ void head_kernel(int B, const float *O, const float *Y, float beta_min, float gw, float *beta_out,
                             float *dO, float *loss_s) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= B) return;
   const float o = O[(size_t)warp * kOut + lane];
-  float c = softplus_f(o);
+  const float sp = softplus_f(o);
+  float c = sp;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const float v = __shfl_up_sync(0xFFFFFFFFu, c, d);
@@ -102,8 +108,16 @@ __global__ void head_kernel(int B, const float *O, const float *Y, float beta_mi
   const float beta = beta_min + c;
   if (beta_out) beta_out[(size_t)warp * kOut + lane] = beta;
   if (!Y) return;
-  const float diff = beta - Y[(size_t)warp * kOut + lane];
+  const float y = Y[(size_t)warp * kOut + lane];
+  const float yprev = __shfl_up_sync(0xFFFFFFFFu, y, 1);
+  const float diff = beta - y;
   float l = diff * diff;
+  float r = 0.f, dgap = 1.f;
+  if (gw != 0.f && lane >= 1) {
+    dgap = y - yprev;
+    r = (sp - dgap) / dgap;
+    l += gw * (32.f / 31.f) * r * r;
+  }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) l += __shfl_xor_sync(0xFFFFFFFFu, l, d);
   if (lane == 0) loss_s[warp] = l;
@@ -115,7 +129,9 @@ __global__ void head_kernel(int B, const float *O, const float *Y, float beta_mi
     if (lane + d < 32) g += v;
   }
   const float sig = 1.f / (1.f + expf(-o));
-  dO[(size_t)warp * kOut + lane] = sig * g;
+  float dov = sig * g;
+  if (gw != 0.f && lane >= 1) dov += sig * (2.f * gw * r / dgap / (float)(B * (kOut - 1)));
+  dO[(size_t)warp * kOut + lane] = dov;
 }
 
 // out[n] = sum_m X[m][n] (bias gradients), one thread per column.
@@ -171,6 +187,7 @@ struct pc_mlp {
   pc_ctx *ctx = nullptr;
   int device = 0;    // the context's device, kept for pc_mlp_destroy
   float beta_min = 0.f;
+  float gap_weight = 0.f;   // weight of the relative-gap term of the loss
   int64_t t = 0;
   size_t n_params = 0;
   size_t w_off[kLayers], b_off[kLayers];
@@ -225,7 +242,7 @@ int forward(pc_mlp *mm, int batch, const float *X, float *beta_dev) {
                                      kOut, p + mm->b_off[3], nullptr, 0)))
     return rc;
   if (beta_dev) {
-    head_kernel<<<(batch * 32 + 255) / 256, 256, 0, st>>>(batch, mm->O.p, nullptr, mm->beta_min, beta_dev,
+    head_kernel<<<(batch * 32 + 255) / 256, 256, 0, st>>>(batch, mm->O.p, nullptr, mm->beta_min, 0.f, beta_dev,
                                                           nullptr, nullptr);
     PC_CUDA_TRY(cudaGetLastError());
   }
@@ -237,8 +254,8 @@ int backward(pc_mlp *mm, int batch, const float *X, const float *Y) {
   cudaStream_t st = mm->ctx->stream;
   int rc = forward(mm, batch, X, nullptr);
   if (rc) return rc;
-  head_kernel<<<(batch * 32 + 255) / 256, 256, 0, st>>>(batch, mm->O.p, Y, mm->beta_min, mm->beta.p,
-                                                        mm->dO.p, mm->loss_s.p);
+  head_kernel<<<(batch * 32 + 255) / 256, 256, 0, st>>>(batch, mm->O.p, Y, mm->beta_min, mm->gap_weight,
+                                                        mm->beta.p, mm->dO.p, mm->loss_s.p);
   PC_CUDA_TRY(cudaGetLastError());
   loss_kernel<<<1, 256, 0, st>>>(batch, mm->loss_s.p, mm->loss.p);
   PC_CUDA_TRY(cudaGetLastError());
@@ -446,6 +463,14 @@ int pc_mlp_get_params(pc_mlp *mm, float *const *W, float *const *b) try {
     if (W && W[k]) std::memcpy(W[k], h.data() + mm->w_off[k], sizeof(float) * kDims[k + 1] * kDims[k]);
     if (b && b[k]) std::memcpy(b[k], h.data() + mm->b_off[k], sizeof(float) * kDims[k + 1]);
   }
+  return PC_OK;
+} catch (...) {
+  return pc::fail_exception();
+}
+
+int pc_mlp_set_gap_weight(pc_mlp *mm, float w) try {
+  if (!mm || !std::isfinite(w) || w < 0.f) return fail(PC_EINVAL, "gap weight must be finite and >= 0");
+  mm->gap_weight = w;
   return PC_OK;
 } catch (...) {
   return pc::fail_exception();

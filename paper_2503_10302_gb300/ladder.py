@@ -46,6 +46,11 @@ LADDER_KW = dict(beta0=0.5, alpha=1.25, n_chains=32, sweeps=2000, tail=500, tol=
 # design acceptance would reject them too.)
 JUDGE_KW = dict(probe_attempts=500, probe_labels=2, acc_floor=math.erfc(1.25 * 1.25))
 SIZES = (6, 8, 10, 12, 14, 16)
+# Weight of the relative-gap term of the training loss (pc_mlp_set_gap_weight):
+# without it the network's hottest gaps ripple (pairs accepting alternately
+# about 0.13 and 0.8 at L = 16) because the squared error of the cumulative
+# ladder barely constrains gap errors that cancel between neighbours.
+GAP_WEIGHT = 0.05
 
 
 def _ctx(seed: int) -> pcomp.Context:
@@ -84,7 +89,8 @@ def training_set(n: int, sizes: Sequence[int] = SIZES, seed: int = W.SEED_TRAIN,
             "ladder_kw": ladder_kw}
 
 
-def train(X: np.ndarray, Y: np.ndarray, epochs: int = 60, batch: int = 256, lr: float = 1e-3, seed: int = 21):
+def train(X: np.ndarray, Y: np.ndarray, epochs: int = 60, batch: int = 256, lr: float = 1e-3, seed: int = 21,
+          gap_weight: float = GAP_WEIGHT):
     """Adam on the GPU kernels over shuffled minibatches, the learning rate
     decaying tenfold over the epochs.  Returns (network, context, loss of
     the last minibatch of each epoch, seconds)."""
@@ -94,6 +100,7 @@ def train(X: np.ndarray, Y: np.ndarray, epochs: int = 60, batch: int = 256, lr: 
     stream = torch.cuda.Stream()
     pcomp.pc_set_stream(ctx.h, stream.cuda_stream)
     m = pcomp.Mlp(ctx, params)
+    m.set_gap_weight(gap_weight)
     Xd = torch.from_numpy(X).cuda()
     Yd = torch.from_numpy(Y).cuda()
     loss = torch.zeros(1, device="cuda")
@@ -270,6 +277,7 @@ def main():
         os.makedirs(os.path.dirname(args.out), exist_ok=True)
         m.save(args.out)
         meta = {"n_train": args.n_train, "sizes": list(SIZES), "epochs": args.epochs, "seed": W.SEED_TRAIN,
+                "gap_weight": GAP_WEIGHT,
                 "ladder_kw": ts["ladder_kw"], "pilot_betas": [float(b) for b in PILOT_BETAS], "pilot": PILOT_KW,
                 "ladder_seconds": ts["ladder_seconds"], "feature_seconds": ts["feature_seconds"],
                 "train_seconds": t_train, "loss_first_last": [hist[0], hist[-1]],

@@ -102,6 +102,7 @@ SIGNATURES = {
     "pc_mlp_train_step": (c_int, [c_vp, c_int, c_f32p, c_f32p, c_flt, c_f32p]),
     "pc_mlp_train_step_dev": (c_int, [c_vp, c_int, c_vp, c_vp, c_flt, c_vp]),
     "pc_mlp_get_params": (c_int, [c_vp, c_f32pp, c_f32pp]),
+    "pc_mlp_set_gap_weight": (c_int, [c_vp, c_flt]),
     "pc_mlp_save": (c_int, [c_vp, ctypes.c_char_p]),
     "pc_mlp_load": (c_int, [c_vp, ctypes.c_char_p, ctypes.POINTER(c_vp)]),
     "pc_ladder_judge": (c_int, [c_vp, c_int, c_i32p, c_i8p, c_u32, c_int, c_f64p, c_int, c_int, c_dbl, c_f64p,
@@ -563,6 +564,9 @@ class Mlp:
 
     def save(self, path: str) -> None:
         _call("pc_mlp_save", self.h, os.fsencode(path))
+
+    def set_gap_weight(self, w: float) -> None:
+        _call("pc_mlp_set_gap_weight", self.h, c_flt(w))
 
     def close(self):
         if getattr(self, "h", None) is not None:

@@ -283,6 +283,26 @@ def test_four_labels_thirty_two_temperatures(pc, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("groups", [1, 3])
+def test_uneven_split_requests_respect_the_cta_limit(pc, orc, groups):
+    """32 temperatures x 4 labels: an uneven split would put 12 groups (96
+    replicas) in one CTA, so it falls back to the even split (8 groups
+    each); results equal the oracle's."""
+    shapes = [(6, 6, 6), (4, 4, 8)]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 17, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(32), W.geometric_ladder(30)]
+    b = W.AptBatch(dims, J, betas, 4)
+    ctx = pc.Context(0, 59)
+    pc.pc_apt_load(ctx.h, dims, J, betas, 4, 0)
+    pc.pc_apt_set_launch(ctx.h, 512, 0, 2, groups)
+    apt = orc.Apt(dims, J, betas, 4, seed=59)
+    pc.pc_apt_run(ctx.h, 30, 1, True)
+    apt.run(30, threads=8)
+    _compare(pc, apt, ctx, b)
+    ctx.close()
+
+
 @pytest.mark.parametrize("labels,pref", [(2, 1), (2, 2), (4, 2)])
 def test_vacancies_and_odd_open_lattices(pc, orc, labels, pref):
     """Missing spins (random vacancies) and odd open lengths padded with a

@@ -64,16 +64,19 @@ def test_forward_matches_oracle(pc, B):
     ctx.close()
 
 
-@pytest.mark.parametrize("B", [64, 300])
-def test_gradients_match_oracle(pc, B):
+@pytest.mark.parametrize("B,gw", [(64, 0.0), (300, 0.0), (64, 0.05), (300, 0.3)])
+def test_gradients_match_oracle(pc, B, gw):
+    """Gradients of the squared ladder error, and with the relative-gap
+    term (its gap_weight gw)."""
     from oracle import mlp
     params = W.mlp_init(mlp.SIZES, 2)
     params = [(w, b + 0.01) for w, b in params]
     X, Y = _data(B, 3)
     ctx = pc.Context(0, 0)
     m = pc.Mlp(ctx, params)
+    m.set_gap_weight(gw)
     loss, grads = m.grads(X, Y)
-    loss_ref, grads_ref = mlp.loss_and_grads(params, X.astype(np.float64), Y.astype(np.float64))
+    loss_ref, grads_ref = mlp.loss_and_grads(params, X.astype(np.float64), Y.astype(np.float64), gap_weight=gw)
     assert abs(loss - loss_ref) <= RTOL * loss_ref
     K = max(259, B)
     for l, ((gW, gb), (rW, rb)) in enumerate(zip(grads, grads_ref)):

@@ -18,13 +18,14 @@ def W_init(sizes, seed):
     return W.mlp_init(sizes, seed)
 
 
-def test_gradients_match_finite_differences():
+@pytest.mark.parametrize("gw", [0.0, 0.3])
+def test_gradients_match_finite_differences(gw):
     sizes = (7, 6, 5, 4, 3)
     params = _params(sizes, 1)
     rng = np.random.default_rng(0)
     X = rng.normal(size=(4, 7))
     Y = np.cumsum(np.abs(rng.normal(size=(4, 3))), axis=1)
-    loss, grads = mlp.loss_and_grads(params, X, Y, beta_min=0.1)
+    loss, grads = mlp.loss_and_grads(params, X, Y, beta_min=0.1, gap_weight=gw)
     eps = 1e-6
     for li in range(4):
         for k in range(2):
@@ -33,21 +34,22 @@ def test_gradients_match_finite_differences():
             for idx in itertools.islice(np.ndindex(p.shape), 0, None, 3):
                 old = p[idx]
                 p[idx] = old + eps
-                lp, _ = mlp.loss_and_grads(params, X, Y, 0.1)
+                lp, _ = mlp.loss_and_grads(params, X, Y, 0.1, gw)
                 p[idx] = old - eps
-                lm, _ = mlp.loss_and_grads(params, X, Y, 0.1)
+                lm, _ = mlp.loss_and_grads(params, X, Y, 0.1, gw)
                 p[idx] = old
                 fd = (lp - lm) / (2 * eps)
                 assert abs(fd - g[idx]) < 1e-6 * max(1.0, abs(fd)), (li, k, idx)
 
 
-def test_gradients_match_autograd_full_size():
+@pytest.mark.parametrize("gw", [0.0, 0.05])
+def test_gradients_match_autograd_full_size(gw):
     torch = pytest.importorskip("torch")
     params = _params(mlp.SIZES, 2)
     rng = np.random.default_rng(1)
     X = rng.random(size=(8, mlp.N_IN))
     Y = np.cumsum(rng.random(size=(8, 32)) * 0.1, axis=1) + 0.5
-    loss, grads = mlp.loss_and_grads(params, X, Y)
+    loss, grads = mlp.loss_and_grads(params, X, Y, gap_weight=gw)
     tp = [(torch.tensor(W, requires_grad=True), torch.tensor(b, requires_grad=True)) for W, b in params]
     h = torch.tensor(X)
     for i, (Wt, bt) in enumerate(tp):
@@ -55,7 +57,11 @@ def test_gradients_match_autograd_full_size():
         if i < 3:
             h = torch.relu(h)
     beta = torch.cumsum(torch.nn.functional.softplus(h), dim=1)
-    tl = ((beta - torch.tensor(Y)) ** 2).mean()
+    Yt = torch.tensor(Y)
+    tl = ((beta - Yt) ** 2).mean()
+    if gw:   # the gap term written with torch's own ops: differences of the ladders
+        gaps, d = torch.diff(beta, dim=1), torch.diff(Yt, dim=1)
+        tl = tl + gw * (((gaps - d) / d) ** 2).mean()
     tl.backward()
     assert abs(tl.item() - loss) < 1e-12 * max(1, loss)
     for (Wt, bt), (gW, gb) in zip(tp, grads):
