@@ -268,6 +268,7 @@ def main():
     ap.add_argument("--best-sweeps", type=int, default=20000)
     ap.add_argument("--max-sweeps", type=int, default=100000)
     ap.add_argument("--dump", help="train: also save the training set (X, Y, L) to this .npz")
+    ap.add_argument("--json", help="compare: also write the full results (per-instance hit sweeps) here")
     args = ap.parse_args()
     if args.what == "train":
         ts = training_set(args.n_train)
@@ -294,6 +295,9 @@ def main():
         out = compare(net, load_means(os.path.join(os.path.dirname(args.out), "ladder_means.json")),
                       args.n_eval, args.L, best_runs=args.best_runs, best_sweeps=args.best_sweeps,
                       max_sweeps=args.max_sweeps)
+        if args.json:
+            with open(args.json, "w") as f:
+                json.dump(out, f)
         print(json.dumps({k: ({kk: vv for kk, vv in v.items() if kk != "hit_sweeps"} if isinstance(v, dict)
                               else v) for k, v in out.items()}, indent=1))
         net.close()
