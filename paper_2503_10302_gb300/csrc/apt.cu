@@ -28,8 +28,9 @@
 #include "device.cuh"
 #include "internal.h"
 
-// Optional per-phase cycle counters of CTA 0 (build with -DPC_APT_PROFILE=1;
-// read with pc_apt_profile_read).  Off by default.
+// Optional per-phase cycle counters of CTAs 0 and 1 (the two ranks of the
+// first problem when problems split; build with -DPC_APT_PROFILE=1; read the
+// 2 x 16 counters with pc_apt_profile_read).  Off by default.
 #ifndef PC_APT_PROFILE
 #define PC_APT_PROFILE 0
 #endif
@@ -39,12 +40,12 @@
 #define PC_APT_STAGE_SWT 1
 #endif
 #if PC_APT_PROFILE
-__device__ unsigned long long g_apt_prof[16];
+__device__ unsigned long long g_apt_prof[32];
 #define PROF_MARK(slot, t0)                                                     \
   do {                                                                          \
-    if (blockIdx.x == 0 && threadIdx.x == 0) {                                  \
+    if (blockIdx.x < 2 && threadIdx.x == 0) {                                   \
       const long long t1_ = clock64();                                          \
-      atomicAdd(&g_apt_prof[slot], (unsigned long long)(t1_ - (t0)));           \
+      atomicAdd(&g_apt_prof[16 * blockIdx.x + (slot)], (unsigned long long)(t1_ - (t0))); \
       (t0) = t1_;                                                               \
     }                                                                           \
   } while (0)
@@ -752,7 +753,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
         }
         if (!__syncthreads_or(changed)) {
 #if PC_APT_PROFILE
-          if (blockIdx.x == 0 && tid == 0) atomicAdd(&g_apt_prof[11], (unsigned long long)(it + 1));
+          if (blockIdx.x < 2 && tid == 0) atomicAdd(&g_apt_prof[16 * blockIdx.x + 11], (unsigned long long)(it + 1));
 #endif
           break;
         }
@@ -1418,9 +1419,9 @@ int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t s
 
 #if PC_APT_PROFILE
 extern "C" int pc_apt_profile_read(unsigned long long *out, int reset) {
-  PC_CUDA_TRY(cudaMemcpyFromSymbol(out, g_apt_prof, sizeof(unsigned long long) * 16));
+  PC_CUDA_TRY(cudaMemcpyFromSymbol(out, g_apt_prof, sizeof(unsigned long long) * 32));
   if (reset) {
-    unsigned long long z[16] = {0};
+    unsigned long long z[32] = {0};
     PC_CUDA_TRY(cudaMemcpyToSymbol(g_apt_prof, z, sizeof(z)));
   }
   return PC_OK;
