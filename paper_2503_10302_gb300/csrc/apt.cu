@@ -34,6 +34,11 @@
 #ifndef PC_APT_PROFILE
 #define PC_APT_PROFILE 0
 #endif
+// Sites a thread's colour-phase loop unrolls (build-time knob).
+#ifndef PC_APT_SITE_UNROLL
+#define PC_APT_SITE_UNROLL 1
+#endif
+constexpr int kSiteUnroll = PC_APT_SITE_UNROLL;
 // Split problems keep the first entries of their swap tables in shared
 // memory (build-time knob).
 #ifndef PC_APT_STAGE_SWT
@@ -222,6 +227,7 @@ __device__ __forceinline__ void colour_phase_t(const AptArgs &a, const Cta &k, c
     for (int m = 0; m < 4; ++m) acc[u][m] = 0;
   const uint32_t c2 = (uint32_t)c << 16;
   if (gcnt > 0) {
+#pragma unroll kSiteUnroll
     for (int j = lt; j < H; j += k.tpc) {
       int n[6];
       neighbours(k.geo, c, j, n);
@@ -946,6 +952,9 @@ __device__ void push_boundary(const Cta &k, const Shared &sh, int kb, int par) {
 // one barrier per attempt orders every exchange.
 template <bool SPLIT>
 __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int p, uint32_t t) {
+#if PC_APT_PROFILE
+  long long pt = clock64();
+#endif
   const AptProbDev &P = a.prob[p];
   const int A = k.A, q = (int)(t & 1u);
   const int r0 = 8 * k.g0, r1 = min(8 * (k.g0 + k.Gu), k.T);   // temperatures held here
@@ -965,6 +974,7 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
     if (threadIdx.x < A) pe[threadIdx.x] = sh.E[threadIdx.x * lb + rb_own - r0];
     push_boundary(k, sh, k.geo.H, par);
   }
+  PROF_MARK(12, pt);
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     if (lane < 16) sh.swm[lane] = 0;
@@ -1003,6 +1013,7 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
     any = __any_sync(0xFFFFFFFFu, any);
     if (lane == 0) sh.m32[5] = any;
   }
+  PROF_MARK(13, pt);
   uint32_t bmask = 0;
   if (k.split) {
     cooperative_groups::this_cluster().sync();   // the peer's energies and spins have landed
@@ -1045,11 +1056,13 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
   } else {
     __syncthreads();
   }
+  PROF_MARK(14, pt);
   if (!sh.m32[5] && !bmask) return;
   // colour 0 is rewritten by the next sweep without being read (a Gibbs
   // update depends on the neighbours only), so only colour 1 moves now; the
   // kernel applies the last attempt's swaps to colour 0 before it stores
   swap_words(k, sh, k.geo.H, 2 * k.geo.H, bmask, sh.stage + 256 * par);
+  PROF_MARK(15, pt);
 }
 
 // MODE (pc::APT_MODE_*) and SPLIT (a cluster of two CTAs per problem) are
