@@ -34,11 +34,11 @@
 #ifndef PC_APT_PROFILE
 #define PC_APT_PROFILE 0
 #endif
-// Sites a thread's colour-phase loop unrolls (build-time knob).
-#ifndef PC_APT_SITE_UNROLL
-#define PC_APT_SITE_UNROLL 1
+// The flood fill keeps a block's overlap words in registers across passes
+// (build-time knob; 0 reloads them every pass).
+#ifndef PC_APT_FILL_XREG
+#define PC_APT_FILL_XREG 1
 #endif
-constexpr int kSiteUnroll = PC_APT_SITE_UNROLL;
 // Split problems keep the first entries of their swap tables in shared
 // memory (build-time knob).
 #ifndef PC_APT_STAGE_SWT
@@ -227,7 +227,6 @@ __device__ __forceinline__ void colour_phase_t(const AptArgs &a, const Cta &k, c
     for (int m = 0; m < 4; ++m) acc[u][m] = 0;
   const uint32_t c2 = (uint32_t)c << 16;
   if (gcnt > 0) {
-#pragma unroll kSiteUnroll
     for (int j = lt; j < H; j += k.tpc) {
       int n[6];
       neighbours(k.geo, c, j, n);
@@ -735,6 +734,9 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
       // registers across passes (the thread is their only writer)
       Blk B;
       uint32_t v[8];
+#if PC_APT_FILL_XREG
+      uint32_t x[8];   // the block's overlap words do not change during the fill
+#endif
       bool open = false;
       if (tid < nblk) {
         B = make_blk(tid);
@@ -742,16 +744,24 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           v[i] = V[B.kk[i]];
+#if PC_APT_FILL_XREG
+          x[i] = X[B.kk[i]];
+          o |= x[i] & ~v[i];
+#else
           o |= X[B.kk[i]] & ~v[i];
+#endif
         }
         open = o != 0;
       }
       for (int it = 0; it < N; ++it) {
         int changed = 0;
         if (open) {
-          uint32_t x[8], o = 0;
+          uint32_t o = 0;
+#if !PC_APT_FILL_XREG
+          uint32_t x[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) x[i] = X[B.kk[i]];
+#endif
           changed = relax(B, x, v);
 #pragma unroll
           for (int i = 0; i < 8; ++i) o |= x[i] & ~v[i];
@@ -924,13 +934,14 @@ __device__ void swap_words(const Cta &k, const Shared &sh, int kb, int ke, uint3
 // CTA's stage[par] (distributed shared memory).  Rank 0 sends its hottest
 // temperature (nibble 7 of each label's last group), rank 1 its coldest
 // (nibble 0 of each label's first group).
-__device__ void push_boundary(const Cta &k, const Shared &sh, int kb, int par) {
+__device__ void push_boundary(const Cta &k, const Shared &sh, int kb, int par, int w0 = 0) {
   namespace cg = cooperative_groups;
   const int H = k.geo.H;
   uint32_t *pstage = cg::this_cluster().map_shared_rank(sh.stage, k.rank ^ 1) + 256 * par;
   const int sh_own = k.rank == 0 ? 28 : 0, goff = k.rank == 0 ? k.Gu - 1 : 0;
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int base = (threadIdx.x >> 5) * 32; base < H; base += nw * 32) {
+  // warps w0 .. take part
+  const int lane = threadIdx.x & 31, nw = (blockDim.x >> 5) - w0;
+  for (int base = ((int)(threadIdx.x >> 5) - w0) * 32; base < H; base += nw * 32) {
     const int e = base + lane;
     for (int l = 0; l < k.A; ++l) {
       uint32_t bit = 0;
@@ -967,12 +978,21 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
     return ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
   };
   const int par = (int)(t & 1u);
+  const int warp = threadIdx.x >> 5;
   if (k.split) {
     // energies of this side of the boundary pair, and its colour-1 spins
+    // (warps 1 ..; warp 0 starts on the decisions meanwhile)
     const int rb_own = k.rank == 0 ? r1 - 1 : r0;
     int *pe = cooperative_groups::this_cluster().map_shared_rank(sh.xch, k.rank ^ 1) + 4 * par;
     if (threadIdx.x < A) pe[threadIdx.x] = sh.E[threadIdx.x * lb + rb_own - r0];
-    push_boundary(k, sh, k.geo.H, par);
+    if (warp >= 1) push_boundary(k, sh, k.geo.H, par, 1);
+    // the boundary pair's draws do not depend on the energies: warp 1 takes
+    // them now, before the cluster barrier
+    const int rb = k.rank == 0 ? r1 : r0;
+    const int lane1 = threadIdx.x - 32;
+    if (warp == 1 && lane1 < A && rb < k.T && ((rb - 1) & 1) == q)
+      sh.xch[18 + lane1] =
+          (int)philox((uint32_t)(rb - 1), t, (uint32_t)lane1, (k.ent << 8) | TAG_SWAP, a.k0, a.k1).x;
   }
   PROF_MARK(12, pt);
   if (threadIdx.x < 32) {
@@ -987,15 +1007,13 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
     const int nd = a.joint_swap ? np : np * A;
     for (int idx = lane; idx < nd; idx += 32) {
       const int r = first + 2 * (a.joint_swap ? idx : idx / A), al = a.joint_swap ? 0 : idx % A;
+      // the draw first: it does not depend on the energies
+      const uint32_t x0 = philox((uint32_t)r, t, (uint32_t)al, (k.ent << 8) | TAG_SWAP, a.k0, a.k1).x;
       const int bA = al * lb + r - r0, bB = bA + 1;
       int dE = sh.E[bB] - sh.E[bA];
       if (a.joint_swap)
         for (int l = 1; l < A; ++l) dE += sh.E[l * lb + r - r0 + 1] - sh.E[l * lb + r - r0];
-      bool acc = dE >= 0;
-      if (!acc) {
-        const uint4 x = philox((uint32_t)r, t, (uint32_t)al, (k.ent << 8) | TAG_SWAP, a.k0, a.k1);
-        acc = x.x < swap_table(r, dE);
-      }
+      const bool acc = dE >= 0 || x0 < swap_table(r, dE);
       for (int l = al; l < (a.joint_swap ? A : al + 1); ++l) {
         const int lA = l * lb + r - r0, lB = lA + 1;
         sh.satt[r * A + l] += 1;
@@ -1034,11 +1052,8 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
           int dE = e_hi[l] - e_lo[l];
           if (a.joint_swap)
             for (int m = 1; m < A; ++m) dE += e_hi[m] - e_lo[m];
-          bool acc = dE >= 0;
-          if (!acc) {
-            const uint4 x = philox((uint32_t)(rb - 1), t, (uint32_t)l, (k.ent << 8) | TAG_SWAP, a.k0, a.k1);
-            acc = x.x < swap_table(rb - 1, dE);
-          }
+          // the draw taken by warp 1 before the barrier
+          const bool acc = dE >= 0 || (uint32_t)sh.xch[18 + l] < swap_table(rb - 1, dE);
           if (acc) accm |= a.joint_swap ? (1u << A) - 1u : 1u << l;
         }
         for (int l = 0; l < A; ++l) {
