@@ -775,8 +775,10 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
         uint32_t o = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) o |= x[q] & ~v[q];
-        // a pair relaxes while either of its layers can still grow
-        const bool pair_open = valid && (o | __shfl_xor_sync(0xFFFFFFFFu, o, 1)) != 0u;
+        // a pair relaxes while either of its layers can still grow (every
+        // lane takes part in the shuffle, valid or not)
+        const uint32_t po = __shfl_xor_sync(0xFFFFFFFFu, o, 1);
+        const bool pair_open = valid && (o | po) != 0u;
         const uint32_t am = __ballot_sync(0xFFFFFFFFu, pair_open);
         int changed = 0;
         if (pair_open) {
