@@ -34,11 +34,6 @@
 #ifndef PC_APT_PROFILE
 #define PC_APT_PROFILE 0
 #endif
-// The flood fill runs two threads per 2 x 2 x 2 block when they fit
-// (build-time knob; 0: one thread per block).
-#ifndef PC_APT_FILL_HALF
-#define PC_APT_FILL_HALF 1
-#endif
 // The flood fill keeps a block's overlap words in registers across passes
 // (build-time knob; 0 reloads them every pass).
 #ifndef PC_APT_FILL_XREG
@@ -734,94 +729,7 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
       }
       return ch;
     };
-    if (PC_APT_FILL_HALF && 2 * nblk <= nt) {
-      // two threads per block, one per z-layer (dz = tid & 1): a thread reads
-      // the outside neighbours of its four sites, closes its 2 x 2 layer and
-      // takes the other layer's words by a lane shuffle (the pair sits in
-      // adjacent lanes), which halves each pass's dependent chain and uses
-      // twice the warps.  Each site word keeps a single writer.
-      const int hz = tid & 1, blk = tid >> 1;
-      const bool valid = blk < nblk;
-      // the layer's four site words (kh) and the other layer's (ko), selected
-      // with compile-time indices so that they stay in registers
-      int kh[4] = {0, 0, 0, 0}, ko[4] = {0, 0, 0, 0};
-      uint32_t v[4], x[4], okm = 0;
-      int dxm = 0, dxp = 0, dym = 0, dyp = 0, dzo = 0;
-      uint32_t mz = 0;
-      if (valid) {
-        const Blk B = make_blk(blk);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          kh[q] = hz ? B.kk[q + 4] : B.kk[q];
-          ko[q] = hz ? B.kk[q] : B.kk[q + 4];
-        }
-        okm = B.ok;
-        dxm = (int16_t)(B.dx2 & 0xFFFFu);
-        dxp = (int16_t)(B.dx2 >> 16);
-        dym = (int16_t)(B.dy2 & 0xFFFFu);
-        dyp = (int16_t)(B.dy2 >> 16);
-        dzo = hz ? (int)(int16_t)(B.dz2 >> 16) : (int)(int16_t)(B.dz2 & 0xFFFFu);
-        mz = ((B.ok >> (4 + hz)) & 1u) ? ~0u : 0u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          x[q] = X[kh[q]];
-          v[q] = V[kh[q]];
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] = v[q] = 0u;
-      }
-      for (int it = 0; it < N; ++it) {
-        uint32_t o = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) o |= x[q] & ~v[q];
-        // a pair relaxes while either of its layers can still grow (every
-        // lane takes part in the shuffle, valid or not)
-        const uint32_t po = __shfl_xor_sync(0xFFFFFFFFu, o, 1);
-        const bool pair_open = valid && (o | po) != 0u;
-        const uint32_t am = __ballot_sync(0xFFFFFFFFu, pair_open);
-        int changed = 0;
-        if (pair_open) {
-          uint32_t nv[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int dx = q & 1, dy = q >> 1;
-            const uint32_t mx = ((okm >> dx) & 1u) ? ~0u : 0u;
-            const uint32_t my = ((okm >> (2 + dy)) & 1u) ? ~0u : 0u;
-            const uint32_t ox = Vv[kh[q ^ 1] + (dx ? dxp : dxm)] & mx;
-            const uint32_t oy = Vv[kh[q ^ 2] + (dy ? dyp : dym)] & my;
-            const uint32_t oz = Vv[ko[q] + dzo] & mz;
-            nv[q] = v[q] | (x[q] & (ox | oy | oz));
-          }
-#pragma unroll
-          for (int round = 0; round < 2; ++round) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) nv[q] |= x[q] & (nv[q ^ 1] | nv[q ^ 2]);
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) nv[q] |= x[q] & __shfl_xor_sync(am, nv[q], 1);
-#pragma unroll
-          for (int round = 0; round < 2; ++round) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) nv[q] |= x[q] & (nv[q ^ 1] | nv[q ^ 2]);
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (nv[q] != v[q]) {
-              V[kh[q]] = nv[q];
-              v[q] = nv[q];
-              changed = 1;
-            }
-          }
-        }
-        if (!__syncthreads_or(changed)) {
-#if PC_APT_PROFILE
-          if (blockIdx.x < 2 && tid == 0) atomicAdd(&g_apt_prof[16 * blockIdx.x + 11], (unsigned long long)(it + 1));
-#endif
-          break;
-        }
-      }
-    } else if (nblk <= nt) {
+    if (nblk <= nt) {
       // one block per thread: its geometry and cluster words stay in
       // registers across passes (the thread is their only writer)
       Blk B;
