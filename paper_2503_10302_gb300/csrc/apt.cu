@@ -209,13 +209,93 @@ struct Cta {
 // A site missing k of its six bonds (open boundaries) counts its satisfied
 // present bonds C, so I = 2C - (6 - k); the threshold row is indexed by
 // I + 6 = 2C + k, formed for eight spins at once as 2C + k * 0x11111111.
+// The NG groups [gbeg, gbeg + NG) of site (c, j): every neighbour word is
+// loaded first, then the NG decisions run as one branch-free block whose
+// Philox chains are independent, ties (a zero product of a word's eight
+// differences, about 2^-13 per word) are settled after it, and the stores
+// come last.
+template <int NG, bool UPDATE, bool ENERGY, bool OPEN>
+__device__ __forceinline__ void site_groups(const AptArgs &a, const Cta &k, const Shared &sh, int c, int j,
+                                            uint32_t sweep, int gbeg, uint32_t (&acc)[MAXGC][4]) {
+  const int H = k.geo.H;
+  int n[6];
+  neighbours(k.geo, c, j, n);
+  const uint32_t jb = sh.jn[c * H + j];
+  const uint32_t miss = OPEN ? (jb >> 8) & 0x3Fu : 0u;
+  const uint32_t K = OPEN ? (uint32_t)__popc(miss) * 0x11111111u : 0u;
+  uint32_t jm[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    jm[d] = nib_mask((jb >> d) & 1u);
+  }
+  uint32_t C[NG], w[NG];
+#pragma unroll
+  for (int u = 0; u < NG; ++u) {
+    const uint32_t *Wo = sh.S + (size_t)(2 * (gbeg + u) + (1 - c)) * H;
+    uint32_t s = 0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      // an absent bond (open axis) adds nothing
+      const uint32_t keep = OPEN ? ((miss >> d) & 1u) - 1u : 0xFFFFFFFFu;
+      s += (Wo[n[d]] ^ jm[d]) & keep;
+    }
+    C[u] = s;
+  }
+  if (UPDATE) {
+    const uint32_t c2 = (uint32_t)c << 16, tag = (k.ent << 8) | a.tag_main;
+    uint32_t tmask = 0u;
+#pragma unroll
+    for (int u = 0; u < NG; ++u) {
+      const uint32_t g = (uint32_t)sh.gmap[gbeg + u];
+      const uint4 x = philox((uint32_t)j, sweep, c2 | g, tag, a.k0, a.k1);
+      bool tie = false;
+      // threshold index I + 6 = 2C + k per nibble (2C with every bond)
+      const uint32_t D = OPEN ? 2u * C[u] + K : C[u];
+      w[u] = decide8_grp<OPEN ? 1 : 2>(x, D, sh.thrh + 128 * (gbeg + u), tie);
+      tmask |= tie ? (1u << u) : 0u;
+    }
+    if (tmask) {
+#pragma unroll
+      for (int u = 0; u < NG; ++u) {
+        if (!((tmask >> u) & 1u)) continue;
+        const uint32_t g = (uint32_t)sh.gmap[gbeg + u];
+        const uint4 x = philox((uint32_t)j, sweep, c2 | g, tag, a.k0, a.k1);
+        const uint4 y = philox((uint32_t)j, sweep, c2 | g, (k.ent << 8) | a.tag_ref, a.k0, a.k1);
+        const uint32_t D = OPEN ? 2u * C[u] + K : C[u];
+        w[u] = refine8_grp<OPEN ? 1 : 2>(w[u], x, y, D, sh.thr + 128 * (gbeg + u));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NG; ++u) sh.S[(size_t)(2 * (gbeg + u) + c) * H + j] = w[u];
+  } else {
+#pragma unroll
+    for (int u = 0; u < NG; ++u) w[u] = sh.S[(size_t)(2 * (gbeg + u) + c) * H + j];
+  }
+  if (ENERGY) {
+#pragma unroll
+    for (int u = 0; u < NG; ++u) {
+      const uint32_t full = w[u] * 0xFu;    // nibble of all ones where the spin is +1
+      const uint32_t sat = (C[u] & full) | ((0x66666666u - K - C[u]) & ~full);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[u][m] += (sat >> (4 * m)) & 0x000F000Fu;
+    }
+  }
+}
+
+// One colour phase of a sweep over the CTA's groups.  UPDATE: Eq. synapse +
+// Eq. neuron for every site of colour c.  ENERGY: accumulate, per buffer,
+// the satisfied bonds of the colour-c sites (every bond has exactly one
+// colour-1 endpoint, so the colour-1 pass gives E = nbonds - 2 * satisfied).
+// A site missing k of its six bonds (open boundaries) counts its satisfied
+// present bonds C, so I = 2C - (6 - k); the threshold row is indexed by
+// I + 6 = 2C + k, formed for eight spins at once as 2C + k * 0x11111111.
 template <bool UPDATE, bool ENERGY, bool OPEN>
 __device__ __forceinline__ void colour_phase_t(const AptArgs &a, const Cta &k, const Shared &sh,
                                                int c, uint32_t sweep, int gtot) {
   const int tid = threadIdx.x;
   const int q = tid / k.tpc, lt = tid - q * k.tpc;
   const int H = k.geo.H;
-  // groups [0, gtot) over the nch thread chunks
+  // groups [0, gtot) over the nch thread chunks (at most MAXGC per chunk)
   const int gper = gtot == k.Gc ? k.gc : (gtot + k.nch - 1) / k.nch;
   const int gbeg = q * gper;
   int gcnt = gtot - gbeg;
@@ -225,55 +305,14 @@ __device__ __forceinline__ void colour_phase_t(const AptArgs &a, const Cta &k, c
   for (int u = 0; u < MAXGC; ++u)
 #pragma unroll
     for (int m = 0; m < 4; ++m) acc[u][m] = 0;
-  const uint32_t c2 = (uint32_t)c << 16;
-  if (gcnt > 0) {
-    for (int j = lt; j < H; j += k.tpc) {
-      int n[6];
-      neighbours(k.geo, c, j, n);
-      const uint32_t jb = sh.jn[c * H + j];
-      const uint32_t miss = OPEN ? (jb >> 8) & 0x3Fu : 0u;
-      const uint32_t K = OPEN ? (uint32_t)__popc(miss) * 0x11111111u : 0u;
-      uint32_t jm[6];
-#pragma unroll
-      for (int d = 0; d < 6; ++d) jm[d] = nib_mask((jb >> d) & 1u);
-#pragma unroll
-      for (int u = 0; u < MAXGC; ++u) {
-        if (u >= gcnt) break;
-        const int gl = gbeg + u;
-        const uint32_t *Wo = sh.S + (size_t)(2 * gl + (1 - c)) * H;
-        uint32_t C = 0;
-#pragma unroll
-        for (int d = 0; d < 6; ++d) C += Wo[n[d]] ^ jm[d];
-        if (OPEN && miss) {   // boundary site of an open axis: drop the absent bonds
-#pragma unroll
-          for (int d = 0; d < 6; ++d)
-            if ((miss >> d) & 1u) C -= Wo[n[d]] ^ jm[d];
-        }
-        uint32_t w;
-        uint32_t *dst = sh.S + (size_t)(2 * gl + c) * H + j;
-        if (UPDATE) {
-          const uint32_t g = (uint32_t)sh.gmap[gl];
-          const uint4 x = philox((uint32_t)j, sweep, c2 | g, (k.ent << 8) | a.tag_main, a.k0, a.k1);
-          bool tie = false;
-          // threshold index I + 6 = 2C + k per nibble (2C with every bond)
-          const uint32_t D = OPEN ? 2u * C + K : C;
-          w = decide8_grp<OPEN ? 1 : 2>(x, D, sh.thrh + 128 * gl, tie);
-          if (tie) {
-            const uint4 y = philox((uint32_t)j, sweep, c2 | g, (k.ent << 8) | a.tag_ref, a.k0, a.k1);
-            w = refine8_grp<OPEN ? 1 : 2>(w, x, y, D, sh.thr + 128 * gl);
-          }
-          *dst = w;
-        } else {
-          w = *dst;
-        }
-        if (ENERGY) {
-          const uint32_t full = w * 0xFu;    // nibble of all ones where the spin is +1
-          const uint32_t sat = (C & full) | ((0x66666666u - K - C) & ~full);
-#pragma unroll
-          for (int m = 0; m < 4; ++m) acc[u][m] += (sat >> (4 * m)) & 0x000F000Fu;
-        }
-      }
-    }
+  if (gcnt >= 4) {
+    for (int j = lt; j < H; j += k.tpc) site_groups<4, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, acc);
+  } else if (gcnt == 3) {
+    for (int j = lt; j < H; j += k.tpc) site_groups<3, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, acc);
+  } else if (gcnt == 2) {
+    for (int j = lt; j < H; j += k.tpc) site_groups<2, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, acc);
+  } else if (gcnt == 1) {
+    for (int j = lt; j < H; j += k.tpc) site_groups<1, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, acc);
   }
   if (ENERGY) {
     // lanes of a warp share the chunk q; reduce 16-bit lanes across the warp
