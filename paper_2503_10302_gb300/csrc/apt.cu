@@ -112,25 +112,28 @@ __device__ __forceinline__ int lin_of(const Geo &g, int c, int j) {
 // SCALE 2: C holds the satisfied count of a site with all six bonds, whose
 // entry is 2C.
 // thrh holds the thresholds' top halves t as 16-bit entries in the same
-// [buffer][16] order, so the entry of nibble i sits at byte offset
-// 32 i + 2 SCALE c_i <= 248: the offsets of 4 nibbles are formed in one word
-// and each is taken out with one byte extract.  The sign of d = v - t for
-// the main half v is the decision, and the top 4 bits of each d are shifted
-// into w so that bit 3 of nibble i carries half i's sign.  A zero product
-// of the differences (mod 2^32) flags a possible tie, which refine8_grp
-// settles exactly (a product that only wraps to 0 costs a needless refine).
+// [buffer][16] order, each group's 256 bytes starting on a 256-byte
+// boundary of shared memory (tb, a shared-window address), so the entry of
+// nibble i sits at tb | (32 i + 2 SCALE c_i), 32 i + 2 SCALE c_i <= 248:
+// the offsets of 4 nibbles are formed in one word and each address is one
+// byte permute of that word with tb.  The sign of d = v - t for the main
+// half v is the decision, and the top 4 bits of each d are shifted into w
+// so that bit 3 of nibble i carries half i's sign.  A zero product of the
+// differences (mod 2^32) flags a possible tie, which refine8_grp settles
+// exactly (a product that only wraps to 0 costs a needless refine).
 template <int SCALE>
-__device__ __forceinline__ uint32_t decide8_grp(const uint4 &x, uint32_t C, const uint16_t *thrh,
-                                                bool &tie) {
-  const char *base = reinterpret_cast<const char *>(thrh);
+__device__ __forceinline__ uint32_t decide8_grp(const uint4 &x, uint32_t C, uint32_t tb, bool &tie) {
   // byte k of Dlo: offset of nibble 2k (64 k + 2 SCALE c); of Dhi: nibble 2k+1
   const uint32_t Dlo = (C & 0x0F0F0F0Fu) * (2u * SCALE) + 0xC0804000u;
   const uint32_t Dhi = ((C >> 4) & 0x0F0F0F0Fu) * (2u * SCALE) + 0xE0A06020u;
   uint32_t w = 0, tp = 1u;
 #pragma unroll
   for (int i = 7; i >= 0; --i) {
-    const uint32_t off = __byte_perm((i & 1) ? Dhi : Dlo, 0u, 0x4440u + (uint32_t)(i >> 1));
-    const uint32_t d = half_lo(x, i) - *reinterpret_cast<const uint16_t *>(base + off);
+    // byte 0 from the offsets, bytes 1-3 from tb
+    const uint32_t addr = __byte_perm((i & 1) ? Dhi : Dlo, tb, 0x7650u + (uint32_t)(i >> 1));
+    uint32_t th;
+    asm("ld.shared.u16 %0, [%1];" : "=r"(th) : "r"(addr));
+    const uint32_t d = half_lo(x, i) - th;
     w = __funnelshift_l(d, w, 4);
     tp *= d;
   }
@@ -202,43 +205,43 @@ struct Cta {
   int nch, tpc, gc;
 };
 
-// One colour phase of a sweep over the CTA's groups.  UPDATE: Eq. synapse +
-// Eq. neuron for every site of colour c.  ENERGY: accumulate, per buffer,
-// the satisfied bonds of the colour-c sites (every bond has exactly one
-// colour-1 endpoint, so the colour-1 pass gives E = nbonds - 2 * satisfied).
-// A site missing k of its six bonds (open boundaries) counts its satisfied
-// present bonds C, so I = 2C - (6 - k); the threshold row is indexed by
-// I + 6 = 2C + k, formed for eight spins at once as 2C + k * 0x11111111.
+// Satisfied-bond counts of NG groups in byte lanes: e8[u][0] byte k counts
+// nibble 2k, e8[u][1] byte k nibble 2k + 1.  A site adds at most 6 to a
+// lane, so a thread reduces them after at most kFlushSites sites.
+constexpr int kFlushSites = 32;
+
 // The NG groups [gbeg, gbeg + NG) of site (c, j): every neighbour word is
 // loaded first, then the NG decisions run as one branch-free block whose
 // Philox chains are independent, ties (a zero product of a word's eight
 // differences, about 2^-13 per word) are settled after it, and the stores
-// come last.
+// come last.  The field of 8 spins is C = n_neg 0x11111111 + sum_d eps_d W_d
+// with eps_d = +1 (J > 0), -1 (J < 0) or 0 (absent bond): per nibble the
+// count of satisfied present bonds (W ^ 1 for a negative bond is 1 - W),
+// exact mod 2^32 because every final nibble lies in 0..6.
 template <int NG, bool UPDATE, bool ENERGY, bool OPEN>
 __device__ __forceinline__ void site_groups(const AptArgs &a, const Cta &k, const Shared &sh, int c, int j,
-                                            uint32_t sweep, int gbeg, uint32_t (&acc)[MAXGC][4]) {
+                                            uint32_t sweep, int gbeg, uint32_t (&e8)[NG][2]) {
   const int H = k.geo.H;
+  const uint32_t tb0 = (uint32_t)__cvta_generic_to_shared(sh.thrh) + 256u * (uint32_t)gbeg;
   int n[6];
   neighbours(k.geo, c, j, n);
   const uint32_t jb = sh.jn[c * H + j];
   const uint32_t miss = OPEN ? (jb >> 8) & 0x3Fu : 0u;
   const uint32_t K = OPEN ? (uint32_t)__popc(miss) * 0x11111111u : 0u;
-  uint32_t jm[6];
+  uint32_t eps[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
-    jm[d] = nib_mask((jb >> d) & 1u);
+    const uint32_t e = 1u - 2u * ((jb >> d) & 1u);
+    eps[d] = (OPEN && ((miss >> d) & 1u)) ? 0u : e;
   }
+  const uint32_t K0 = (uint32_t)__popc(jb & 0x3Fu & ~miss) * 0x11111111u;
   uint32_t C[NG], w[NG];
 #pragma unroll
   for (int u = 0; u < NG; ++u) {
     const uint32_t *Wo = sh.S + (size_t)(2 * (gbeg + u) + (1 - c)) * H;
-    uint32_t s = 0;
+    uint32_t s = K0;
 #pragma unroll
-    for (int d = 0; d < 6; ++d) {
-      // an absent bond (open axis) adds nothing
-      const uint32_t keep = OPEN ? ((miss >> d) & 1u) - 1u : 0xFFFFFFFFu;
-      s += (Wo[n[d]] ^ jm[d]) & keep;
-    }
+    for (int d = 0; d < 6; ++d) s += eps[d] * Wo[n[d]];
     C[u] = s;
   }
   if (UPDATE) {
@@ -246,12 +249,11 @@ __device__ __forceinline__ void site_groups(const AptArgs &a, const Cta &k, cons
     uint32_t tmask = 0u;
 #pragma unroll
     for (int u = 0; u < NG; ++u) {
-      const uint32_t g = (uint32_t)sh.gmap[gbeg + u];
-      const uint4 x = philox((uint32_t)j, sweep, c2 | g, tag, a.k0, a.k1);
+      const uint4 x = philox((uint32_t)j, sweep, c2 | (uint32_t)sh.gmap[gbeg + u], tag, a.k0, a.k1);
       bool tie = false;
       // threshold index I + 6 = 2C + k per nibble (2C with every bond)
       const uint32_t D = OPEN ? 2u * C[u] + K : C[u];
-      w[u] = decide8_grp<OPEN ? 1 : 2>(x, D, sh.thrh + 128 * (gbeg + u), tie);
+      w[u] = decide8_grp<OPEN ? 1 : 2>(x, D, tb0 + 256u * (uint32_t)u, tie);
       tmask |= tie ? (1u << u) : 0u;
     }
     if (tmask) {
@@ -276,10 +278,56 @@ __device__ __forceinline__ void site_groups(const AptArgs &a, const Cta &k, cons
     for (int u = 0; u < NG; ++u) {
       const uint32_t full = w[u] * 0xFu;    // nibble of all ones where the spin is +1
       const uint32_t sat = (C[u] & full) | ((0x66666666u - K - C[u]) & ~full);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) acc[u][m] += (sat >> (4 * m)) & 0x000F000Fu;
+      e8[u][0] += sat & 0x0F0F0F0Fu;
+      e8[u][1] += (sat >> 4) & 0x0F0F0F0Fu;
     }
   }
+}
+
+// The sites j = j0, j0 + tpc, .. below j1 of colour c for the NG groups
+// from gbeg; at most kFlushSites sites per thread, so that the byte lanes
+// of the energy counts cannot overflow.  Every lane of a warp calls it
+// (the warp reduction at the end).
+template <int NG, bool UPDATE, bool ENERGY, bool OPEN>
+__device__ __forceinline__ void site_loop(const AptArgs &a, const Cta &k, const Shared &sh, int c,
+                                          uint32_t sweep, int j0, int j1, int gbeg) {
+  uint32_t e8[NG][2];
+#pragma unroll
+  for (int u = 0; u < NG; ++u) e8[u][0] = e8[u][1] = 0u;
+  for (int j = j0; j < j1; j += k.tpc) site_groups<NG, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, e8);
+  if (ENERGY) {
+    // lanes of a warp share the chunk (and NG); reduce 16-bit lanes across
+    // the warp: word m of a group holds nibbles m (low) and m + 4 (high)
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < NG; ++u) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        uint32_t v = (e8[u][m & 1] >> (8 * (m >> 1))) & 0x00FF00FFu;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        if (lane == 0) {
+          const int b = 8 * (gbeg + u) + m;
+          atomicAdd(&sh.Eacc[b], (int)(v & 0xFFFFu));
+          atomicAdd(&sh.Eacc[b + 4], (int)(v >> 16));
+        }
+      }
+    }
+  }
+}
+
+// Sites of colour c in blocks of kFlushSites per thread (one block unless
+// H > kFlushSites * tpc).
+template <int NG, bool UPDATE, bool ENERGY, bool OPEN>
+__device__ __forceinline__ void site_blocks(const AptArgs &a, const Cta &k, const Shared &sh, int c,
+                                            uint32_t sweep, int lt, int gbeg) {
+  const int H = k.geo.H, span = kFlushSites * k.tpc;
+  if (!ENERGY || H <= span) {
+    site_loop<NG, UPDATE, ENERGY, OPEN>(a, k, sh, c, sweep, lt, H, gbeg);
+    return;
+  }
+  for (int b0 = 0; b0 < H; b0 += span)
+    site_loop<NG, UPDATE, ENERGY, OPEN>(a, k, sh, c, sweep, b0 + lt, min(H, b0 + span), gbeg);
 }
 
 // One colour phase of a sweep over the CTA's groups.  UPDATE: Eq. synapse +
@@ -294,45 +342,19 @@ __device__ __forceinline__ void colour_phase_t(const AptArgs &a, const Cta &k, c
                                                int c, uint32_t sweep, int gtot) {
   const int tid = threadIdx.x;
   const int q = tid / k.tpc, lt = tid - q * k.tpc;
-  const int H = k.geo.H;
   // groups [0, gtot) over the nch thread chunks (at most MAXGC per chunk)
   const int gper = gtot == k.Gc ? k.gc : (gtot + k.nch - 1) / k.nch;
   const int gbeg = q * gper;
   int gcnt = gtot - gbeg;
   if (gcnt > gper) gcnt = gper;
-  uint32_t acc[MAXGC][4];
-#pragma unroll
-  for (int u = 0; u < MAXGC; ++u)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) acc[u][m] = 0;
-  if (gcnt >= 4) {
-    for (int j = lt; j < H; j += k.tpc) site_groups<4, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, acc);
-  } else if (gcnt == 3) {
-    for (int j = lt; j < H; j += k.tpc) site_groups<3, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, acc);
-  } else if (gcnt == 2) {
-    for (int j = lt; j < H; j += k.tpc) site_groups<2, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, acc);
-  } else if (gcnt == 1) {
-    for (int j = lt; j < H; j += k.tpc) site_groups<1, UPDATE, ENERGY, OPEN>(a, k, sh, c, j, sweep, gbeg, acc);
-  }
-  if (ENERGY) {
-    // lanes of a warp share the chunk q; reduce 16-bit lanes across the warp
-    const int lane = tid & 31;
-#pragma unroll
-    for (int u = 0; u < MAXGC; ++u) {
-      if (u >= gcnt) break;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        uint32_t v = acc[u][m];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        if (lane == 0) {
-          const int b = 8 * (gbeg + u) + m;
-          atomicAdd(&sh.Eacc[b], (int)(v & 0xFFFFu));
-          atomicAdd(&sh.Eacc[b + 4], (int)(v >> 16));
-        }
-      }
-    }
-  }
+  if (gcnt >= 4)
+    site_blocks<4, UPDATE, ENERGY, OPEN>(a, k, sh, c, sweep, lt, gbeg);
+  else if (gcnt == 3)
+    site_blocks<3, UPDATE, ENERGY, OPEN>(a, k, sh, c, sweep, lt, gbeg);
+  else if (gcnt == 2)
+    site_blocks<2, UPDATE, ENERGY, OPEN>(a, k, sh, c, sweep, lt, gbeg);
+  else if (gcnt == 1)
+    site_blocks<1, UPDATE, ENERGY, OPEN>(a, k, sh, c, sweep, lt, gbeg);
 }
 
 // Periodic problems take the path without absent-bond handling.
@@ -1172,6 +1194,9 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   uint32_t *cur = smem;
   sh.S = cur;            cur += (size_t)Gcarve * N;
   sh.thr = cur;          cur += 16 * G8;
+  // each group's 256-byte block of thrh on a 256-byte boundary of the
+  // shared window (the same padding in both CTAs of a cluster)
+  cur += ((256u - ((uint32_t)__cvta_generic_to_shared(cur) & 255u)) & 255u) >> 2;
   sh.thrh = reinterpret_cast<uint16_t *>(cur);   cur += 16 * G8;   // uses half of its carve
   sh.temp_of = reinterpret_cast<int32_t *>(cur);  cur += G8;
   sh.buf_of = reinterpret_cast<int32_t *>(cur);   cur += G8;
@@ -1259,6 +1284,13 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
         colour_phase<true, false>(a, k, sh, 0, s, k.Gc);
         __syncthreads();
         PROF_MARK(0, pt);
+        if (MODE == pc::APT_MODE_APT && qq + 1 < a.spp) {
+          // the APT mode reads energies only after the attempt's last sweep
+          colour_phase<true, false>(a, k, sh, 1, s, k.Gc);
+          __syncthreads();
+          PROF_MARK(1, pt);
+          continue;
+        }
         colour_phase<true, true>(a, k, sh, 1, s, k.Gc);
         __syncthreads();
         finish_energies(k, sh);
@@ -1422,7 +1454,7 @@ size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n
   if (mode == APT_MODE_APT) words += (size_t)(T > 1 ? T - 1 : 0) * kSwtLen;   // staged swap tables (split)
   // V, X, the transposed X (or the cluster labels) and the root masks
   if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31 + (size_t)((N + 31) >> 5);
-  return words * 4 + (size_t)N * 2 + 16;
+  return words * 4 + (size_t)N * 2 + 16 + 256;   // + the threshold table's alignment
 }
 
 template <int MODE, bool CSEED>
