@@ -206,21 +206,22 @@ def apt_metrics(stream, peak_tops: float, attempts: int = 256) -> dict:
     stream, after a warm-up that also captures the CUDA graph): the 64 x
     L = 12 batch with adaptive ladders resampled to 32 temperatures x 2
     labels, sweep-only (ICM off, the paper's flip counters exclude swap and
-    ICM time) and end to end; the 256-instance mixed batch end to end."""
+    ICM time) and end to end, with one sweep per attempt and with 10 and
+    516; the 256-instance mixed batch end to end."""
     import torch
     from paper_2503_10302_gb300 import ladder, pcomp
     from paper_2503_10302_gb300 import workloads as W
     out = {}
 
-    def timed(ctx, spins_per_sweep, icm):
-        pcomp.pc_apt_run(ctx.h, 128, 1, icm)            # warm-up and graph capture
+    def timed(ctx, spins_per_sweep, icm, spp=1, n=attempts):
+        pcomp.pc_apt_run(ctx.h, min(n, 128), spp, icm)  # warm-up and graph capture
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        pcomp.pc_apt_run(ctx.h, attempts, 1, icm)
+        pcomp.pc_apt_run(ctx.h, n, spp, icm)
         b.record(stream)
         torch.cuda.synchronize()
-        return spins_per_sweep * attempts / (a.elapsed_time(b) * 1e6)
+        return spins_per_sweep * n * spp / (a.elapsed_time(b) * 1e6)
 
     dims, J = ladder.eval_set(64, 12, seed=W.SEED_INSTANCES)
     lctx = pcomp.Context(0, 11)
@@ -243,6 +244,13 @@ def apt_metrics(stream, peak_tops: float, attempts: int = 256) -> dict:
             key = f"{name}_{'e2e' if icm else 'sweep_only'}"
             out[key] = {"value": v, "unit": UNIT, "attempts": attempts,
                         "roofline": _alu_roofline(v, peak_tops, "apt_kernel")}
+        if name == "apt_icm_64xL12":
+            # the paper's larger sweep-to-swap ratios (Supplementary "APT
+            # Algorithm with ICM"): ICM and a swap attempt every 10 / 516 sweeps
+            for spp, n in ((10, 64), (516, 4)):
+                v = timed(ctx, batch.spins_per_sweep(), True, spp, n)
+                out[f"{name}_e2e_spp{spp}"] = {"value": v, "unit": UNIT, "attempts": n, "sweeps_per_swap": spp,
+                                               "roofline": _alu_roofline(v, peak_tops, "apt_kernel")}
         ctx.close()
     out["apt_icm_64xL12_adaptive_ladder_seconds"] = t_lad
     return out

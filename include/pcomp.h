@@ -139,7 +139,8 @@ int pc_apt_set_joint_swap(pc_ctx *ctx, int joint);
  * the pair's ICM draw. */
 int pc_apt_set_icm_rules(pc_ctx *ctx, int big_cluster_rule, int cluster_seed);
 /* Placement of each problem: one CTA, or a cluster of two CTAs that split
- * its temperatures (rank 0 the colder half).  The two CTAs exchange the
+ * its temperatures (rank 0 the hotter half: the ladder's first, lowest-beta
+ * temperatures).  The two CTAs exchange the
  * boundary swap and the best-energy candidates through distributed shared
  * memory; results are identical either way.  A problem with more than 64
  * replicas (e.g. 32 temperatures x 4 labels) always splits and needs at

@@ -195,7 +195,8 @@ struct Cta {
   int T, Tp, A, B, Bc, Gc, g0;
   // this CTA holds, for every label, the temperature groups [g0, g0 + Gu) of
   // the Glp groups per label (APT; ladder / pilot: A = 1, groups g0 ..);
-  // split problems run as a cluster of two CTAs, rank 0 holding the colder half
+  // split problems run as a cluster of two CTAs, rank 0 holding the hotter
+  // (lower-beta, first) half
   int Gu, Glp, split, rank;
   int nbonds;        // bonds present (3N with periodic axes)
   int nreal;         // spins present (N without vacancies)

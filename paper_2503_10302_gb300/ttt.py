@@ -15,7 +15,7 @@ from __future__ import annotations
 import argparse
 import json
 import time
-from typing import Dict, List, Sequence, Tuple
+from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -42,10 +42,15 @@ class DeviceTimer:
         return a.elapsed_time(b) * 1e-3
 
 
-def apt_throughput(batch: W.AptBatch, sweeps: int = 200, icm: bool = True, seed: int = 1) -> Dict:
+def apt_throughput(batch: W.AptBatch, sweeps: int = 200, icm: bool = True, seed: int = 1,
+                   shape: Optional[Tuple[int, int, int, int]] = None) -> Dict:
+    """shape: (threads, thread chunks, split preference, split groups) as
+    pc_apt_set_launch takes them; None keeps the default placement."""
     ctx = pcomp.Context(0, seed)
     timer = DeviceTimer(ctx)
     pcomp.pc_apt_load(ctx.h, batch.dims, batch.J, batch.betas, batch.n_labels, 0)
+    if shape is not None:
+        pcomp.pc_apt_set_launch(ctx.h, *shape)
     pcomp.pc_apt_run(ctx.h, 20, 1, icm)            # warm (also builds the graph)
     dt = timer.time(lambda: pcomp.pc_apt_run(ctx.h, sweeps, 1, icm))
     flips = batch.spins_per_sweep() * sweeps
@@ -369,6 +374,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=200)
     ap.add_argument("--batch", choices=["apt_plain_L4", "apt_icm_64xL12", "apt_icm_mixed256"])
     ap.add_argument("--icm", type=int, choices=[0, 1])
+    ap.add_argument("--shape", help="throughput: threads,chunks,split_pref,split_groups (pc_apt_set_launch)")
     ap.add_argument("--best-runs", type=int, default=10)
     ap.add_argument("--best-sweeps", type=int, default=20000)
     ap.add_argument("--max-sweeps", type=int, default=100000)
@@ -383,7 +389,8 @@ def main():
         for name in names:
             batch = batches[name]()
             for icm in ((True, False) if args.icm is None else (bool(args.icm),)):
-                out[f"{name}_icm{int(icm)}"] = apt_throughput(batch, args.sweeps, icm)
+                shape = tuple(int(v) for v in args.shape.split(",")) if args.shape else None
+                out[f"{name}_icm{int(icm)}"] = apt_throughput(batch, args.sweeps, icm, shape=shape)
     if args.what in ("graph", "all") and not args.sqa_only:
         names = [args.graph] if args.graph else ["dimer_64xL8", "lattice15x15x12_64", "lattice12_64",
                                                  "random4096_152"]

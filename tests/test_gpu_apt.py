@@ -405,6 +405,33 @@ def test_sweep_to_swap_ratio_ten(pc, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("pref", [1, 2])
+def test_sweep_to_swap_ratio_516(pc, orc, pref):
+    """516 sweeps per swap attempt (the largest ratio of the paper's
+    sweep-to-swap study, Supplementary "APT Algorithm with ICM"), 5 attempts
+    in one call and 2 more in a second (2580 + 1032 sweeps), with ICM,
+    against the oracle; one CTA per problem (pref 1) and two-CTA clusters
+    (pref 2)."""
+    shapes = [(6, 6, 6), (4, 4, 8), (8, 8, 8)]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 15, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in (12, 10, 16)]   # >= 9 each, so that pref 2 splits
+    b = W.AptBatch(dims, J, betas, 2)
+    ctx = pc.Context(0, 48)
+    pc.pc_apt_load(ctx.h, dims, J, betas, 2, 5)
+    pc.pc_apt_set_split(ctx.h, pref)
+    assert pc.pc_apt_is_split(ctx.h) == (pref == 2)
+    apt = orc.Apt(dims, J, betas, 2, seed=48, entry0=5)
+    pc.pc_apt_run(ctx.h, 5, 516, True)
+    apt.run(5, 516, True, threads=8)
+    _compare(pc, apt, ctx, b)
+    pc.pc_apt_run(ctx.h, 2, 516, True)
+    apt.run(2, 516, True, threads=8)
+    _compare(pc, apt, ctx, b)
+    assert pc.pc_apt_progress(ctx.h) == (7 * 516, 7)
+    ctx.close()
+
+
 def test_c4_mixed_batch_sampled(pc, orc):
     """256 instances, L uniform over {6..16}, 24-32 temperatures x 2, 140
     attempts (a graph replay and a remainder); the smallest, the largest and
