@@ -385,31 +385,26 @@ __device__ __forceinline__ void finish_energies(const Cta &k, const Shared &sh) 
 __device__ void best_update(const AptArgs &a, const Cta &k, const Shared &sh, int p,
                             int64_t sweeps) {
   if (threadIdx.x < 32) {
+    // the lowest energy, ties to the lowest slot r A + label: one warp
+    // minimum of the key (E + 2^18) 2^8 + slot (|E| <= 3N < 2^18, slot < 2^8)
     const int lane = threadIdx.x;
-    int bestE = 0x7FFFFFFF, bests = 0x7FFFFFFF, bestb = 0;
+    uint32_t key = 0xFFFFFFFFu;
+    int bestb = 0;
     for (int b = lane; b < 8 * k.Gc; b += 32) {
       const int gb = 8 * sh.gmap[b >> 3] + (b & 7);
       const int r = gb % k.Tp, lab = gb / k.Tp;
       if (r >= k.T) continue;
-      const int e = sh.E[b], slot = r * k.A + lab;
-      if (e < bestE || (e == bestE && slot < bests)) {
-        bestE = e;
-        bests = slot;
+      const uint32_t kb = ((uint32_t)(sh.E[b] + (1 << 18)) << 8) | (uint32_t)(r * k.A + lab);
+      if (kb < key) {
+        key = kb;
         bestb = b;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const int oe = __shfl_xor_sync(0xFFFFFFFFu, bestE, o);
-      const int os = __shfl_xor_sync(0xFFFFFFFFu, bests, o);
-      const int ob = __shfl_xor_sync(0xFFFFFFFFu, bestb, o);
-      if (oe < bestE || (oe == bestE && os < bests)) {
-        bestE = oe;
-        bests = os;
-        bestb = ob;
-      }
-    }
-    if (lane == 0) {
+    const uint32_t mn = __reduce_min_sync(0xFFFFFFFFu, key);
+    // the lane holding the minimum (keys are distinct), or lane 0 if no
+    // buffer holds a temperature
+    if (mn != 0xFFFFFFFFu ? key == mn : lane == 0) {
+      const int bestE = mn != 0xFFFFFFFFu ? (int)(mn >> 8) - (1 << 18) : 0x7FFFFFFF;
       int flag = 0;
       if ((int64_t)bestE < sh.m64[0]) {
         sh.m64[0] = bestE;
@@ -993,9 +988,10 @@ __device__ void swap_words(const Cta &k, const Shared &sh, int kb, int ke, uint3
 
 // Split problems: writes this CTA's boundary spins of the words
 // [kb, kb + H) (one colour), every label, one bit per site, into the peer
-// CTA's stage[par] (distributed shared memory).  Rank 0 sends its hottest
-// temperature (nibble 7 of each label's last group), rank 1 its coldest
-// (nibble 0 of each label's first group).
+// CTA's stage[par] (distributed shared memory).  Rank 0 sends the last
+// (coldest) temperature of its half (nibble 7 of each label's last group),
+// rank 1 the first (hottest) of its half (nibble 0 of each label's first
+// group).
 __device__ void push_boundary(const Cta &k, const Shared &sh, int kb, int par, int w0 = 0) {
   namespace cg = cooperative_groups;
   const int H = k.geo.H;
