@@ -272,8 +272,10 @@ int pc_sqa_anneal(pc_ctx *ctx, const int32_t *dims, const int8_t *J, int P, doub
  *   E_dev [R][P], best_dev [R][2] (nullable)   caller-owned device buffers.
  * Limits: n_sweeps <= 10240, N <= 4096 (else PC_EINVAL with a message).
  * No cudaMalloc, cudaFree or other allocating call is made.  The first call
- * on a device looks up the array's device address; make that first call
- * before any stream capture.  All calls share the one array and leave it
+ * on a device looks up the array's device address (under a host lock, so
+ * concurrent first calls are safe).  Host data reaches the device as kernel
+ * parameters of staging launches on `stream`, not as copies from host
+ * memory.  All calls share the one array and leave it
  * holding the last call's tables, so calls that overlap on the GPU (e.g. on
  * two streams) race; issue them in one stream or serialise them. */
 int pc_sqa_anneal_noalloc(int device, void *stream, uint64_t seed, const int32_t *dims,
