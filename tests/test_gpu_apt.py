@@ -432,6 +432,28 @@ def test_sweep_to_swap_ratio_516(pc, orc, pref):
     ctx.close()
 
 
+@pytest.mark.parametrize("spp", [1, 10])
+def test_more_than_32_sites_per_thread(pc, orc, spp):
+    """64 threads per CTA in two chunks of 32 on a 16^3 lattice (2048 sites
+    per colour): each thread sweeps 64 sites, so its byte-lane energy counts
+    are reduced in two blocks of 32 sites, and the flood fill runs several
+    2x2x2 blocks per thread; with ICM, against the oracle."""
+    shapes = [(16, 16, 16), (6, 6, 6)]
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s, 16, i) for i, s in enumerate(shapes)]
+    betas = [W.geometric_ladder(16), W.geometric_ladder(12)]
+    b = W.AptBatch(dims, J, betas, 2)
+    ctx = pc.Context(0, 49)
+    pc.pc_apt_load(ctx.h, dims, J, betas, 2, 2)
+    pc.pc_apt_set_launch(ctx.h, 64, 2, 1, 0)
+    apt = orc.Apt(dims, J, betas, 2, seed=49, entry0=2)
+    n = 24 if spp == 1 else 4
+    pc.pc_apt_run(ctx.h, n, spp, True)
+    apt.run(n, spp, True, threads=8)
+    _compare(pc, apt, ctx, b)
+    ctx.close()
+
+
 def test_c4_mixed_batch_sampled(pc, orc):
     """256 instances, L uniform over {6..16}, 24-32 temperatures x 2, 140
     attempts (a graph replay and a remainder); the smallest, the largest and
