@@ -237,7 +237,9 @@ def apt_metrics(stream, peak_tops: float, attempts: int = 256) -> dict:
         pcomp.pc_set_stream(ctx.h, stream.cuda_stream)
         pcomp.pc_apt_load(ctx.h, batch.dims, batch.J, batch.betas, batch.n_labels, 0)
         shape = pcomp.pc_apt_autotune(ctx.h, 16, True)     # launch shape of the fused kernel
-        out[name + "_launch"] = {"threads": shape[0], "thread_chunks": shape[1], "two_cta_clusters": shape[2],
+        placement = ("one CTA per problem", "two-CTA clusters",
+                     "two-CTA clusters for the largest problems, one CTA for the rest")[shape[2]]
+        out[name + "_launch"] = {"threads": shape[0], "thread_chunks": shape[1], "placement": placement,
                                  "split_groups": shape[3]}
         for icm in icms:
             v = timed(ctx, batch.spins_per_sweep(), icm)

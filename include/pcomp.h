@@ -146,8 +146,13 @@ int pc_apt_set_icm_rules(pc_ctx *ctx, int big_cluster_rule, int cluster_seed);
  * replicas (e.g. 32 temperatures x 4 labels) always splits and needs at
  * least 9 temperatures in every problem of the batch.  pref: 0 (default)
  * also splits when the batch fills at most half the SMs; 1 splits only when
- * needed; 2 splits whenever every problem has at least 9 temperatures.
- * pc_apt_is_split reports the current placement. */
+ * needed; 2 splits whenever every problem has at least 9 temperatures; 3
+ * splits, problem by problem, those that need it and those (with at least 9
+ * temperatures) whose work N x replicas exceeds the batch's mean work per
+ * SM, and runs the others as one CTA each, in a second launch on a second
+ * stream beside the first (for a batch whose largest problems would
+ * otherwise set its time).  pc_apt_is_split reports the current placement:
+ * 0 one CTA per problem, 1 every problem split, 2 some problems split. */
 int pc_apt_set_split(pc_ctx *ctx, int pref);
 int pc_apt_is_split(pc_ctx *ctx, int *split);
 /* Autotuner of the fused kernel's launch shape (the paper batches many
@@ -162,14 +167,16 @@ int pc_apt_is_split(pc_ctx *ctx, int *split);
  * per CTA (256, 320, 384, 448, 512), and the split of those threads over
  * sites and replica groups (nch chunks of threads, each sweeping
  * ceil(groups / nch) groups of its sites; 0 = a cost model's choice, or 1, 2,
- * 4).  Returns the choice in *tpb, *nch, *split (1 = two-CTA clusters) and
+ * 4), and the per-problem placement of preference 3 where it differs from
+ * both others.  Returns the choice in *tpb, *nch, *split (0 = one CTA per
+ * problem, 1 = two-CTA clusters, 2 = clusters for some problems) and
  * *split_groups; any may be NULL.  Results do not depend on the shape:
  * randomness is keyed by slot and site. */
 int pc_apt_autotune(pc_ctx *ctx, int trial_swaps, int icm, int *tpb, int *nch, int *split,
                     int *split_groups);
 /* Set the launch shape directly: tpb threads per CTA (a multiple of 64 in
  * [64, 512]), nch thread chunks (0, 1, 2, 4 or 8; applied where it fits,
- * else the cost model decides), split_pref as pc_apt_set_split, and
+ * else the cost model decides), split_pref (0 .. 3) as pc_apt_set_split, and
  * split_groups (0 .. 3) the temperature groups per label of the hotter CTA of
  * a split problem (0: half; clamped to leave the colder CTA one). */
 int pc_apt_set_launch(pc_ctx *ctx, int tpb, int nch, int split_pref, int split_groups);

@@ -1465,13 +1465,18 @@ int apt_launch_mode(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStrea
     cfg.blockDim = dim3((unsigned)tpb);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (a.prio) {   // a mixed placement starts its clusters (the largest problems) first
+      attr[1].id = cudaLaunchAttributePriority;
+      attr[1].val.priority = a.prio;
+      cfg.numAttrs = 2;
+    }
     PC_CUDA_TRY(cudaLaunchKernelEx(&cfg, apt_kernel<MODE, true, CSEED>, a));
   }
   PC_CUDA_TRY(cudaGetLastError());

@@ -37,14 +37,20 @@ struct Batch {
   DevBuf<int32_t> d_temp, d_buf, d_E, d_bestbuf;
   DevBuf<int64_t> d_bestE, d_bestsweep, d_hit, d_target, d_stats, d_sum1, d_sum2, d_hist, d_ctr;
   DevBuf<int8_t> d_bestspins, d_bestspins2;   // best states; rank-1 candidates of split problems
-  DevBuf<int> d_cta;             // [4][n_cta]: prob, g0, gc, nch
-  int n_cta = 0;
+  // CTA tables: the one-CTA part [4][n_u] (prob, g0, gc, nch), then the
+  // two-CTA-cluster part [4][n_s]
+  DevBuf<int> d_cta;
+  int n_cta = 0;         // n_u + n_s
+  int n_u = 0, n_s = 0;
   int tpb = kTpbDefault;
-  int split = 0;         // APT problems run as clusters of two CTAs (by temperature)
-  int split_pref = 0;    // 0: when needed or when the batch fills at most half the SMs; 1: only when needed; 2: whenever possible
+  int split = 0;         // every APT problem runs as a cluster of two CTAs (by temperature)
+  int hybrid = 0;        // some problems run as clusters, the others as one CTA (two launches)
+  int split_pref = 0;    // 0: when needed or when the batch fills at most half the SMs; 1: only when needed;
+                         // 2: whenever possible; 3: the problems needing it or above the mean work per SM
   int nch_pref = 0;      // thread chunks per CTA: 0 = the cost model's choice, else this count where it fits
   int split_h = 0;       // split problems: temperature groups per label on rank 0 (0: half)
-  size_t smem = 0;
+  size_t smem = 0;       // max of the two parts
+  size_t smem_u = 0, smem_s = 0;
   std::vector<uint32_t> h_pbit, h_swaptab, h_swapidx;
 };
 
@@ -276,20 +282,39 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
   });
   // APT keeps a problem in one CTA (swaps and ICM couple all its groups), or
   // in a cluster of two CTAs that split its temperatures: needed above 64
-  // replicas, and chosen for speed when the batch fills at most half the SMs.
-  // Ladder and pilot chains are independent, so their groups spread over
-  // about one CTA per SM when the batch is small.
+  // replicas, and chosen for speed when the batch fills at most half the SMs
+  // (pref 0), always (pref 2), or for the problems whose work alone exceeds
+  // the batch's mean work per SM (pref 3: the rest run as one CTA each, in a
+  // second, concurrent launch).  Ladder and pilot chains are independent, so
+  // their groups spread over about one CTA per SM when the batch is small.
   bt.split = 0;
+  bt.hybrid = 0;
+  std::vector<char> ps((size_t)n, 0);
   if (mode == APT_MODE_APT && !order.empty()) {
     bool need = false, can = true;
+    int64_t total = 0;
     for (int i : order) {
-      need = need || bt.prob[(size_t)i].B > 64;
-      can = can && (bt.prob[(size_t)i].Tp >> 3) >= 2;
+      const AptProbDev &P = bt.prob[(size_t)i];
+      need = need || P.B > 64;
+      can = can && (P.Tp >> 3) >= 2;
+      total += (int64_t)P.N * P.B;
     }
-    if (need && !can)
-      return fail(PC_EINVAL, "a batch with more than 64 replicas in a problem needs >= 9 temperatures everywhere");
-    const bool small = 2 * (int64_t)order.size() <= c->sms;
-    bt.split = need || (can && (bt.split_pref == 2 || (bt.split_pref == 0 && small)));
+    if (bt.split_pref == 3) {
+      const int64_t per_sm = total / std::max(1, c->sms);
+      for (int i : order) {
+        const AptProbDev &P = bt.prob[(size_t)i];
+        const bool need_i = P.B > 64, can_i = (P.Tp >> 3) >= 2;
+        if (need_i && !can_i)
+          return fail(PC_EINVAL, "a problem with more than 64 replicas needs >= 9 temperatures");
+        ps[(size_t)i] = need_i || (can_i && (int64_t)P.N * P.B > per_sm);
+      }
+    } else {
+      if (need && !can)
+        return fail(PC_EINVAL, "a batch with more than 64 replicas in a problem needs >= 9 temperatures everywhere");
+      const bool small = 2 * (int64_t)order.size() <= c->sms;
+      const bool all = need || (can && (bt.split_pref == 2 || (bt.split_pref == 0 && small)));
+      for (int i : order) ps[(size_t)i] = all;
+    }
   }
   int gmax = kMaxGcCta;
   if (mode == APT_MODE_LADDER || mode == APT_MODE_PILOT) {
@@ -298,12 +323,13 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
     const int sms = c->sms > 0 ? c->sms : 1;
     gmax = (int)std::min<int64_t>(kMaxGcCta, std::max<int64_t>(1, (total + sms - 1) / sms));
   }
-  std::vector<int> cp, cg0, cgc, cnch;
-  size_t smem = 0;
+  // [0]: one-CTA part, [1]: two-CTA-cluster part
+  std::vector<int> cp[2], cg0[2], cgc[2], cnch[2];
+  size_t smem[2] = {0, 0};
   for (int i : order) {
     const AptProbDev &P = bt.prob[(size_t)i];
     const int G = bt.G[(size_t)i];
-    if (bt.split) {
+    if (ps[(size_t)i]) {
       // rank 0: temperature groups [0, h1) of every label, rank 1: [h1, Glp)
       const int Glp = P.Tp >> 3;
       int h1 = bt.split_h > 0 ? std::min(bt.split_h, Glp - 1) : (Glp + 1) / 2;
@@ -312,35 +338,46 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
       if (P.A * h1 > kMaxGcCta || P.A * (Glp - h1) > kMaxGcCta) h1 = (Glp + 1) / 2;
       for (int rank = 0; rank < 2; ++rank) {
         const int g0 = rank ? h1 : 0, gu = rank ? Glp - h1 : h1;
-        cp.push_back(i);
-        cg0.push_back(g0);
-        cgc.push_back(P.A * gu);
-        cnch.push_back(choose_nch(P.N / 2, P.A * gu, bt.tpb, bt.nch_pref));
+        cp[1].push_back(i);
+        cg0[1].push_back(g0);
+        cgc[1].push_back(P.A * gu);
+        cnch[1].push_back(choose_nch(P.N / 2, P.A * gu, bt.tpb, bt.nch_pref));
       }
-      smem = std::max(smem, apt_smem_bytes(P.N, P.A * std::max(h1, Glp - h1), bt.tpb / 32, mode, icm, P.T, n_bins));
+      smem[1] = std::max(smem[1], apt_smem_bytes(P.N, P.A * std::max(h1, Glp - h1), bt.tpb / 32, mode, icm, P.T,
+                                                 n_bins));
       continue;
     }
     // equal chunks of at most gmax groups
     const int nchunk = (G + gmax - 1) / gmax, per = (G + nchunk - 1) / nchunk;
     for (int g0 = 0; g0 < G; g0 += per) {
       const int gc = std::min(per, G - g0);
-      cp.push_back(i);
-      cg0.push_back(g0);
-      cgc.push_back(gc);
-      cnch.push_back(choose_nch(P.N / 2, gc, bt.tpb, bt.nch_pref));
-      smem = std::max(smem, apt_smem_bytes(P.N, gc, bt.tpb / 32, mode, icm, P.T, n_bins));
+      cp[0].push_back(i);
+      cg0[0].push_back(g0);
+      cgc[0].push_back(gc);
+      cnch[0].push_back(choose_nch(P.N / 2, gc, bt.tpb, bt.nch_pref));
+      smem[0] = std::max(smem[0], apt_smem_bytes(P.N, gc, bt.tpb / 32, mode, icm, P.T, n_bins));
     }
   }
-  bt.n_cta = (int)cp.size();
-  for (int g : cgc)
-    if (g < 1 || g > kMaxGcCta) return fail(PC_EINVAL, "internal: a CTA would hold more than 64 replicas");
-  if (smem > (size_t)c->smem_optin) return fail(PC_EINVAL, "problem does not fit in shared memory");
-  bt.smem = smem;
+  bt.n_u = (int)cp[0].size();
+  bt.n_s = (int)cp[1].size();
+  bt.split = bt.n_s > 0 && bt.n_u == 0;
+  bt.hybrid = bt.n_s > 0 && bt.n_u > 0;
+  bt.smem_u = smem[0];
+  bt.smem_s = smem[1];
+  const size_t smem_max = std::max(smem[0], smem[1]);
+  bt.n_cta = bt.n_u + bt.n_s;
+  for (int part = 0; part < 2; ++part)
+    for (int g : cgc[part])
+      if (g < 1 || g > kMaxGcCta) return fail(PC_EINVAL, "internal: a CTA would hold more than 64 replicas");
+  if (smem_max > (size_t)c->smem_optin) return fail(PC_EINVAL, "problem does not fit in shared memory");
+  bt.smem = smem_max;
   std::vector<int> all;
-  all.insert(all.end(), cp.begin(), cp.end());
-  all.insert(all.end(), cg0.begin(), cg0.end());
-  all.insert(all.end(), cgc.begin(), cgc.end());
-  all.insert(all.end(), cnch.begin(), cnch.end());
+  for (int part = 0; part < 2; ++part) {
+    all.insert(all.end(), cp[part].begin(), cp[part].end());
+    all.insert(all.end(), cg0[part].begin(), cg0[part].end());
+    all.insert(all.end(), cgc[part].begin(), cgc[part].end());
+    all.insert(all.end(), cnch[part].begin(), cnch[part].end());
+  }
   int rc;
   if (bt.d_cta.n < all.size() && (rc = bt.d_cta.alloc(all.size()))) return rc;
   if (!all.empty())
@@ -362,6 +399,63 @@ int max_words(const Batch &bt) {
   return m;
 }
 
+// A second stream and two events for the two launches of a mixed batch.
+struct Fork {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  Fork() = default;
+  Fork(const Fork &) = delete;
+  Fork &operator=(const Fork &) = delete;
+  ~Fork() {
+    if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  int ensure() {
+    if (!st) PC_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : ev)
+      if (!e) PC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return PC_OK;
+  }
+};
+
+// The APT kernel over a scheduled batch: one launch, or, when some problems
+// run as two-CTA clusters and the others as one CTA (split preference 3),
+// the cluster part on a second stream beside the one-CTA part, forked from
+// and joined back into `st` with events (under stream capture the two become
+// parallel nodes of the graph).  The parts hold disjoint problems, so their
+// order does not matter.
+int launch_parts(Batch &bt, AptArgs a, cudaStream_t st, Fork &f) {
+  if (!bt.hybrid) {
+    a.split = bt.split;
+    return apt_launch(a, bt.n_cta, bt.tpb, bt.smem, st);
+  }
+  int rc;
+  if ((rc = f.ensure())) return rc;
+  AptArgs as = a, au = a;
+  int *ts = bt.d_cta.p + 4 * bt.n_u;
+  int least = 0, greatest = 0;
+  PC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  as.split = 1;
+  as.prio = greatest;
+  as.cta_prob = ts;
+  as.cta_g0 = ts + bt.n_s;
+  as.cta_gc = ts + 2 * bt.n_s;
+  as.cta_nch = ts + 3 * bt.n_s;
+  au.split = 0;
+  au.cta_prob = bt.d_cta.p;
+  au.cta_g0 = bt.d_cta.p + bt.n_u;
+  au.cta_gc = bt.d_cta.p + 2 * bt.n_u;
+  au.cta_nch = bt.d_cta.p + 3 * bt.n_u;
+  PC_CUDA_TRY(cudaEventRecord(f.ev[0], st));
+  PC_CUDA_TRY(cudaStreamWaitEvent(f.st, f.ev[0], 0));
+  if ((rc = apt_launch(as, bt.n_s, bt.tpb, bt.smem_s, f.st))) return rc;
+  if ((rc = apt_launch(au, bt.n_u, bt.tpb, bt.smem_u, st))) return rc;
+  PC_CUDA_TRY(cudaEventRecord(f.ev[1], f.st));
+  PC_CUDA_TRY(cudaStreamWaitEvent(st, f.ev[1], 0));
+  return PC_OK;
+}
+
 }  // namespace
 
 // -------------------------------------------------------------------- APT
@@ -378,6 +472,7 @@ struct AptImpl {
   int g_spp = -1, g_icm = -1;
   int joint = 0;                      // joint-label swap rule
   int icm_big = 1, icm_seed = 0;      // ICMop rules (pc_apt_set_icm_rules)
+  Fork fork;                          // the second launch of a mixed placement
   ~AptImpl() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -544,7 +639,7 @@ int pc_apt_load_bc(pc_ctx *c, int n_inst, const int32_t *dims, const uint8_t *pe
   a.tag_init = 1;   // TAG_APT_INIT
   if ((rc = apt_init_launch(a, n_inst, max_words(im->bt), c->stream))) return rc;
   a.mode = APT_MODE_ENERGY;
-  if ((rc = apt_launch(a, im->bt.n_cta, im->bt.tpb, im->bt.smem, c->stream))) return rc;
+  if ((rc = launch_parts(im->bt, a, c->stream, im->fork))) return rc;
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->apt.ready = true;
   c->apt.n = n_inst;
@@ -567,7 +662,7 @@ static int apt_enqueue(pc_ctx *c, AptImpl *im, int n_iter, int spp, int icm) {
   a.icm_seed = im->icm_seed;
   a.tag_main = 2;    // TAG_APT_SWEEP
   a.tag_ref = 3;     // TAG_APT_REFINE
-  int rc = apt_launch(a, im->bt.n_cta, im->bt.tpb, im->bt.smem, c->stream);
+  int rc = launch_parts(im->bt, a, c->stream, im->fork);
   if (rc) return rc;
   return apt_advance_launch(im->bt.d_ctr.p, (int64_t)n_iter * spp, n_iter, c->stream);
 }
@@ -694,7 +789,7 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_
   for (const AptProbDev &P : im->bt.prob) can_split = can_split && (P.Tp >> 3) >= 2;
   int glp_max = 0;
   for (const AptProbDev &P : im->bt.prob) glp_max = std::max(glp_max, P.Tp >> 3);
-  const int splits[2] = {1, 2}, tpbs[5] = {256, 320, 384, 448, 512}, nchs[4] = {0, 1, 2, 4};
+  const int splits[3] = {1, 2, 3}, tpbs[5] = {256, 320, 384, 448, 512}, nchs[4] = {0, 1, 2, 4};
   struct Best { float ms; int tpb, nch, split, h; } best = {1e30f, im->bt.tpb, im->bt.nch_pref, im->bt.split_pref,
                                                             im->bt.split_h};
   cudaEvent_t e0, e1;
@@ -702,9 +797,9 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_
   PC_CUDA_TRY(cudaEventCreate(&e1));
   int rc = PC_OK;
   for (int sp : splits)
-   for (int h = 0; h <= (sp == 2 ? std::min(3, glp_max - 1) : 0); ++h) {
+   for (int h = 0; h <= (sp >= 2 ? std::min(3, glp_max - 1) : 0); ++h) {
     if (sp == 2 && !can_split) continue;
-    if (sp == 2 && h > 0 && 2 * h == glp_max) continue;   // the even split is h = 0
+    if (sp >= 2 && h > 0 && 2 * h == glp_max) continue;   // the even split is h = 0
     for (int tpb : tpbs)
       for (int nch : nchs) {
         if (rc) break;
@@ -716,6 +811,7 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_
         tmp.split_h = h;
         if ((rc = build_batch(c, tmp, im->specs, 0))) break;
         if (schedule(c, tmp, {}, APT_MODE_APT, im->A >= 2, 0)) continue;   // does not fit: skip
+        if (sp == 3 && !tmp.hybrid) continue;   // the same placement as preference 1 or 2
         if (nch > 0) {   // skip a forced split that the schedule could not honour
           std::vector<int> h((size_t)tmp.n_cta);
           PC_CUDA_TRY(cudaMemcpy(h.data(), tmp.d_cta.p + 3 * tmp.n_cta, h.size() * 4, cudaMemcpyDeviceToHost));
@@ -735,9 +831,9 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_
         a.joint_swap = im->joint;
         a.tag_main = 2;
         a.tag_ref = 3;
-        if ((rc = apt_launch(a, tmp.n_cta, tpb, tmp.smem, c->stream))) break;   // warm-up
+        if ((rc = launch_parts(tmp, a, c->stream, im->fork))) break;   // warm-up
         PC_CUDA_TRY(cudaEventRecord(e0, c->stream));
-        if ((rc = apt_launch(a, tmp.n_cta, tpb, tmp.smem, c->stream))) break;
+        if ((rc = launch_parts(tmp, a, c->stream, im->fork))) break;
         PC_CUDA_TRY(cudaEventRecord(e1, c->stream));
         PC_CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -751,8 +847,8 @@ int pc_apt_autotune(pc_ctx *c, int trial_swaps, int icm, int *tpb_out, int *nch_
   if ((rc = apply_shape(c, im, best.tpb, best.nch, best.split, best.h))) return rc;
   if (tpb_out) *tpb_out = best.tpb;
   if (nch_out) *nch_out = best.nch;
-  if (split_out) *split_out = im->bt.split;
-  if (groups_out) *groups_out = im->bt.split ? best.h : 0;
+  if (split_out) *split_out = im->bt.hybrid ? 2 : im->bt.split;
+  if (groups_out) *groups_out = (im->bt.split || im->bt.hybrid) ? best.h : 0;
   return PC_OK;
 } catch (...) {
   return pc::fail_exception();
@@ -762,7 +858,7 @@ int pc_apt_set_launch(pc_ctx *c, int tpb, int nch, int split_pref, int split_gro
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
   if (tpb < 64 || tpb > 512 || tpb % 64) return fail(PC_EINVAL, "tpb must be a multiple of 64 in [64, 512]");
   if (nch < 0 || nch > 8 || (nch & (nch - 1))) return fail(PC_EINVAL, "nch must be 0, 1, 2, 4 or 8");
-  if (split_pref < 0 || split_pref > 2) return fail(PC_EINVAL, "split_pref must be 0, 1 or 2");
+  if (split_pref < 0 || split_pref > 3) return fail(PC_EINVAL, "split_pref must be 0, 1, 2 or 3");
   if (split_groups < 0 || split_groups > 3) return fail(PC_EINVAL, "split_groups must be 0 .. 3");
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -773,7 +869,7 @@ int pc_apt_set_launch(pc_ctx *c, int tpb, int nch, int split_pref, int split_gro
 
 int pc_apt_set_split(pc_ctx *c, int pref) try {
   if (!c || !c->apt.ready || !apt_impl(c)) return fail(PC_ESTATE, "pc_apt_load first");
-  if (pref < 0 || pref > 2) return fail(PC_EINVAL, "pref must be 0, 1 or 2");
+  if (pref < 0 || pref > 3) return fail(PC_EINVAL, "pref must be 0, 1, 2 or 3");
   AptImpl *im = apt_impl(c);
   PC_CUDA_TRY(cudaSetDevice(c->device));
   PC_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -784,7 +880,7 @@ int pc_apt_set_split(pc_ctx *c, int pref) try {
 
 int pc_apt_is_split(pc_ctx *c, int *split) try {
   if (!c || !c->apt.ready || !apt_impl(c) || !split) return fail(PC_ESTATE, "pc_apt_load first");
-  *split = apt_impl(c)->bt.split;
+  *split = apt_impl(c)->bt.hybrid ? 2 : apt_impl(c)->bt.split;
   return PC_OK;
 } catch (...) {
   return pc::fail_exception();

@@ -50,6 +50,7 @@ struct AptArgs {
   int joint_swap;         // 1: one swap decision per temperature pair for all labels
   int icm_big;            // 1: ICM flips one whole replica when the cluster holds more than half
   int icm_seed;           // 0: ICM seeds at a uniform mismatch site; 1: at a uniform cluster
+  int prio;               // host side only: launch priority of a cluster launch (0: default)
   int split;              // 1: every problem runs as a cluster of two CTAs (by temperature)
   int64_t *ctr;           // [2]: sweeps and swap attempts done before this launch
   int64_t window_from;

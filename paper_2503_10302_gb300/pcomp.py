@@ -325,14 +325,16 @@ def pc_apt_set_icm_rules(ctx, big_cluster_rule: bool = True, cluster_seed: bool 
 
 
 def pc_apt_set_split(ctx, pref: int) -> None:
-    """0: split when needed or when the batch is small; 1: only when needed; 2: whenever possible."""
+    """0: split when needed or when the batch is small; 1: only when needed; 2: whenever possible;
+    3: problem by problem, those that need it or whose work exceeds the mean per SM."""
     _call("pc_apt_set_split", ctx, int(pref))
 
 
-def pc_apt_is_split(ctx) -> bool:
+def pc_apt_is_split(ctx) -> int:
+    """0: one CTA per problem, 1: every problem a two-CTA cluster, 2: some."""
     v = c_int()
     _call("pc_apt_is_split", ctx, ctypes.byref(v))
-    return bool(v.value)
+    return v.value
 
 
 def pc_apt_run(ctx, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True) -> None:
@@ -340,12 +342,13 @@ def pc_apt_run(ctx, n_swaps: int, sweeps_per_swap: int = 1, icm: bool = True) ->
 
 
 def pc_apt_autotune(ctx, trial_swaps: int = 16, icm: bool = True):
-    """Returns the chosen (threads per CTA, thread chunks, two-CTA clusters,
+    """Returns the chosen (threads per CTA, thread chunks, placement (0: one
+    CTA per problem, 1: two-CTA clusters, 2: clusters for some problems),
     split groups)."""
     tpb, nch, split, grp = c_int(), c_int(), c_int(), c_int()
     _call("pc_apt_autotune", ctx, trial_swaps, int(icm), ctypes.byref(tpb), ctypes.byref(nch), ctypes.byref(split),
           ctypes.byref(grp))
-    return tpb.value, nch.value, bool(split.value), grp.value
+    return tpb.value, nch.value, split.value, grp.value
 
 
 def pc_apt_set_launch(ctx, tpb: int, nch: int = 0, split_pref: int = 0, split_groups: int = 0) -> None:

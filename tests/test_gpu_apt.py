@@ -510,6 +510,33 @@ def test_launch_shape_does_not_change_results(pc, orc, labels):
         ctx.close()
 
 
+@pytest.mark.parametrize("labels", [2, 4])
+def test_mixed_placement_matches_oracle(pc, orc, labels):
+    """Split preference 3: the two 8^3 problems (20 temperatures) run as
+    two-CTA clusters in one launch, the 150 problems of 4^3 (9 temperatures,
+    below the batch's mean work per SM) as one CTA each in a second launch
+    on a second stream; 40 attempts, then 130 (a captured graph with both
+    launches, and a remainder), with ICM, against the oracle."""
+    shapes = [(8, 8, 8)] * 2 + [(4, 4, 4)] * 150
+    temps = [20, 20] + [9] * 150
+    dims = np.array(shapes, np.int32)
+    J = [W.ea_couplings(s_, 17, i) for i, s_ in enumerate(shapes)]
+    betas = [W.geometric_ladder(t) for t in temps]
+    b = W.AptBatch(dims, J, betas, labels)
+    ctx = pc.Context(0, 51)
+    pc.pc_apt_load(ctx.h, dims, J, betas, labels, 4)
+    pc.pc_apt_set_split(ctx.h, 3)
+    assert pc.pc_apt_is_split(ctx.h) == 2
+    apt = orc.Apt(dims, J, betas, labels, seed=51, entry0=4)
+    pc.pc_apt_run(ctx.h, 40, 1, True)
+    apt.run(40, 1, True, threads=8)
+    _compare(pc, apt, ctx, b, [(i, i) for i in (0, 1, 2, 77, 151)])
+    pc.pc_apt_run(ctx.h, 130, 1, True)
+    apt.run(130, 1, True, threads=8)
+    _compare(pc, apt, ctx, b)
+    ctx.close()
+
+
 def test_checkpoint_resume_bit_exact(pc, tmp_path):
     """200 attempts == 90, save, restore into a fresh context, 110 more."""
     b = W.apt_uniform_batch(2, 6, 12)
