@@ -64,13 +64,23 @@ TRAFFIC_BYTES = 2218837          # mean of 3 timed launches: 1.68, 2.59, 2.39 MB
 TRAFFIC_SRC_SHA256 = "3bd5699b4935d0d8c167ac12c4ffe6ed4250f6acb66f74492ec0c50f32983131"
 TRAFFIC_SOURCES = ("paper_2503_10302_gb300/csrc/sqa.cu", "paper_2503_10302_gb300/csrc/device.cuh",
                    "paper_2503_10302_gb300/csrc/internal.h")
+# Shared-memory (LSU data pipe) throughput as a fraction of its peak, from the
+# same ncu captures (elapsed cycles, mean over SMs): the memory ceiling the
+# integer-issue bound sits under.  The anneal kernel's is valid under
+# TRAFFIC_SRC_SHA256; the APT kernel's two, from the 20-attempt launches of
+# the 64 x L = 12 and mixed batches, under APT_SRC_SHA256.
+SMEM_FRAC_SQA = 0.294
+SMEM_FRAC_APT = {"apt_icm_64xL12": 0.240, "apt_icm_mixed256": 0.286}
+APT_SRC_SHA256 = "94ed48c737b8a5542e2698d0284ffbb70386080a14b5755b99121e3f382eef13"
+APT_SOURCES = ("paper_2503_10302_gb300/csrc/apt.cu", "paper_2503_10302_gb300/csrc/apt_dev.h",
+               "paper_2503_10302_gb300/csrc/device.cuh")
 WORKLOAD = f"DT-SQA 3D +-J L={L} periodic, P={P} slices, R={R} runs, T={T}, Gamma 3.0->1e-3 over {SWEEPS} sweeps"
 
 
-def kernel_sources_sha256() -> str:
+def kernel_sources_sha256(sources=TRAFFIC_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for rel in TRAFFIC_SOURCES:
+    for rel in sources:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -195,10 +205,11 @@ def cpu_oracle_apt_sample(target_s: float = 6.0):
                                 f"({flips:.3g} sweep updates), OpenMP over instances")
 
 
-def _alu_roofline(flips_per_ns: float, peak_tops: float, kernel: str) -> dict:
+def _alu_roofline(flips_per_ns: float, peak_tops: float, kernel: str, smem_frac=None) -> dict:
     achieved = ALG_OPS_PER_FLIP * flips_per_ns * 1e9 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-            "frac": achieved / peak_tops, "traffic": None, "kernel": kernel, "ops_per_flip": ALG_OPS_PER_FLIP}
+            "frac": achieved / peak_tops, "traffic": None, "kernel": kernel, "ops_per_flip": ALG_OPS_PER_FLIP,
+            "smem_frac_ncu": smem_frac}
 
 
 def apt_metrics(stream, peak_tops: float, attempts: int = 256) -> dict:
@@ -244,8 +255,9 @@ def apt_metrics(stream, peak_tops: float, attempts: int = 256) -> dict:
         for icm in icms:
             v = timed(ctx, batch.spins_per_sweep(), icm)
             key = f"{name}_{'e2e' if icm else 'sweep_only'}"
+            smem = SMEM_FRAC_APT.get(name) if icm and kernel_sources_sha256(APT_SOURCES) == APT_SRC_SHA256 else None
             out[key] = {"value": v, "unit": UNIT, "attempts": attempts,
-                        "roofline": _alu_roofline(v, peak_tops, "apt_kernel")}
+                        "roofline": _alu_roofline(v, peak_tops, "apt_kernel", smem)}
         if name == "apt_icm_64xL12":
             # the paper's larger sweep-to-swap ratios (Supplementary "APT
             # Algorithm with ICM"): ICM and a swap attempt every 10 / 516 sweeps
@@ -420,6 +432,7 @@ def main() -> int:
         "roofline": {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
                      "frac": achieved_tops / peak_tops,
                      "traffic": TRAFFIC_BYTES if kernel_sources_sha256() == TRAFFIC_SRC_SHA256 else None,
+                     "smem_frac_ncu": SMEM_FRAC_SQA if kernel_sources_sha256() == TRAFFIC_SRC_SHA256 else None,
                      "kernel": "sqa_kernel",
                      "peak_note": f"{sms} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (issue bound)",
                      "ops_per_flip": ALG_OPS_PER_FLIP,
