@@ -767,6 +767,8 @@ int apply_shape(pc_ctx *c, AptImpl *im, int tpb, int nch_pref, int split_pref, i
   if (im->graph) cudaGraphDestroy(im->graph);
   im->exec = nullptr;
   im->graph = nullptr;
+  // a mixed placement's second stream and events exist before any capture
+  if (bt.hybrid) return im->fork.ensure();
   return PC_OK;
 }
 

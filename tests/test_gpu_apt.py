@@ -515,8 +515,9 @@ def test_mixed_placement_matches_oracle(pc, orc, labels):
     """Split preference 3: the two 8^3 problems (20 temperatures) run as
     two-CTA clusters in one launch, the 150 problems of 4^3 (9 temperatures,
     below the batch's mean work per SM) as one CTA each in a second launch
-    on a second stream; 40 attempts, then 130 (a captured graph with both
-    launches, and a remainder), with ICM, against the oracle."""
+    on a second stream; 40 and 130 attempts in both orders (130 = a captured
+    graph with both launches, and a remainder), with ICM, against the
+    oracle."""
     shapes = [(8, 8, 8)] * 2 + [(4, 4, 4)] * 150
     temps = [20, 20] + [9] * 150
     dims = np.array(shapes, np.int32)
@@ -528,11 +529,14 @@ def test_mixed_placement_matches_oracle(pc, orc, labels):
     pc.pc_apt_set_split(ctx.h, 3)
     assert pc.pc_apt_is_split(ctx.h) == 2
     apt = orc.Apt(dims, J, betas, labels, seed=51, entry0=4)
-    pc.pc_apt_run(ctx.h, 40, 1, True)
-    apt.run(40, 1, True, threads=8)
+    # with 2 labels the first launch after the placement change is the
+    # captured graph
+    first, second = (130, 40) if labels == 2 else (40, 130)
+    pc.pc_apt_run(ctx.h, first, 1, True)
+    apt.run(first, 1, True, threads=8)
     _compare(pc, apt, ctx, b, [(i, i) for i in (0, 1, 2, 77, 151)])
-    pc.pc_apt_run(ctx.h, 130, 1, True)
-    apt.run(130, 1, True, threads=8)
+    pc.pc_apt_run(ctx.h, second, 1, True)
+    apt.run(second, 1, True, threads=8)
     _compare(pc, apt, ctx, b)
     ctx.close()
 
