@@ -718,7 +718,10 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   {
     const Geo &g = k.geo;
     const int hx = g.hx, hy = g.Ly >> 1, nblk = N >> 3;
-    volatile const uint32_t *Vv = V;
+    // plain loads: a pass reads each neighbour word once, after the barrier
+    // that ended the previous pass (a compiler fence as well), and a value
+    // another thread writes during the pass is only seen one pass later
+    const uint32_t *Vv = V;
     // block geometry: site i = dx + 2 dy + 4 dz of block (bx, by, bz) has
     // colour (dx+dy+dz)&1 and index bx + hx (y0 + dy + Ly (z0 + dz)) inside
     // its colour; an outside neighbour is the opposite corner's word of the
