@@ -889,7 +889,17 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
   }
   __syncthreads();
   PROF_MARK(7, pt);
-  // (E) flips
+  // (E) flips.  With two labels the masks are read once into registers (a
+  // store to S could alias them, so they would be reloaded after every one)
+  uint32_t fm[4][4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const bool on = A == 2 && h < Gl;
+    fm[h][0] = on ? sh.imask[h] : 0u;
+    fm[h][1] = on ? sh.imask[16 + h] : 0u;
+    fm[h][2] = on ? sh.imask[Gl + h] : 0u;
+    fm[h][3] = on ? sh.imask[16 + Gl + h] : 0u;
+  }
   for (int kk = tid; kk < N; kk += nt) {
     const int c = kk >= H ? 1 : 0, j = kk - c * H;
     const uint32_t v = V[kk];
@@ -898,8 +908,10 @@ __device__ void icm_all(const AptArgs &a, const Cta &k, const Shared &sh, uint32
       for (int h = 0; h < 4; ++h) {
         if (h >= Gl) break;
         const uint32_t vv = byte_to_nib((v >> (8 * h)) & 0xFFu);
-        sh.S[(2 * h + c) * H + j] ^= (vv & sh.imask[h]) | sh.imask[16 + h];
-        sh.S[(2 * (Gl + h) + c) * H + j] ^= (vv & sh.imask[Gl + h]) | sh.imask[16 + Gl + h];
+        uint32_t *p0 = sh.S + (size_t)(2 * h + c) * H + j, *p1 = sh.S + (size_t)(2 * (Gl + h) + c) * H + j;
+        const uint32_t a0 = *p0, a1 = *p1;
+        *p0 = a0 ^ ((vv & fm[h][0]) | fm[h][1]);
+        *p1 = a1 ^ ((vv & fm[h][2]) | fm[h][3]);
       }
     } else {
 #pragma unroll
