@@ -70,8 +70,8 @@ TRAFFIC_SOURCES = ("paper_2503_10302_gb300/csrc/sqa.cu", "paper_2503_10302_gb300
 # TRAFFIC_SRC_SHA256; the APT kernel's two, from the 20-attempt launches of
 # the 64 x L = 12 and mixed batches, under APT_SRC_SHA256.
 SMEM_FRAC_SQA = 0.294
-SMEM_FRAC_APT = {"apt_icm_64xL12": 0.242, "apt_icm_mixed256": 0.287}
-APT_SRC_SHA256 = "26bafc955a8e81232846479646364f7029cfe76cb36665dc92c39a23cd41aa8a"
+SMEM_FRAC_APT = {"apt_icm_64xL12": 0.241, "apt_icm_mixed256": 0.286}
+APT_SRC_SHA256 = "da1d4fa3befadf0894521ce817063c78fb9689620ff9340fe71a22b742537960"
 APT_SOURCES = ("paper_2503_10302_gb300/csrc/apt.cu", "paper_2503_10302_gb300/csrc/apt_dev.h",
                "paper_2503_10302_gb300/csrc/device.cuh")
 WORKLOAD = f"DT-SQA 3D +-J L={L} periodic, P={P} slices, R={R} runs, T={T}, Gamma 3.0->1e-3 over {SWEEPS} sweeps"
