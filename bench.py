@@ -70,8 +70,8 @@ TRAFFIC_SOURCES = ("paper_2503_10302_gb300/csrc/sqa.cu", "paper_2503_10302_gb300
 # TRAFFIC_SRC_SHA256; the APT kernel's two, from the 20-attempt launches of
 # the 64 x L = 12 and mixed batches, under APT_SRC_SHA256.
 SMEM_FRAC_SQA = 0.294
-SMEM_FRAC_APT = {"apt_icm_64xL12": 0.241, "apt_icm_mixed256": 0.286}
-APT_SRC_SHA256 = "da1d4fa3befadf0894521ce817063c78fb9689620ff9340fe71a22b742537960"
+SMEM_FRAC_APT = {"apt_icm_64xL12": 0.247, "apt_icm_mixed256": 0.286}
+APT_SRC_SHA256 = "0e52ceec74429d7da634e643c1347d1e6caa8e972f7294bef1046754e4f30b92"
 APT_SOURCES = ("paper_2503_10302_gb300/csrc/apt.cu", "paper_2503_10302_gb300/csrc/apt_dev.h",
                "paper_2503_10302_gb300/csrc/device.cuh")
 WORKLOAD = f"DT-SQA 3D +-J L={L} periodic, P={P} slices, R={R} runs, T={T}, Gamma 3.0->1e-3 over {SWEEPS} sweeps"

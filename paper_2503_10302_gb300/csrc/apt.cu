@@ -188,7 +188,7 @@ struct Shared {
 // Entries of each pair's swap table (|dE| = 0, 2, .., 2 (kSwtLen - 1)) that a
 // split problem's CTAs keep in shared memory; larger |dE| read the table in
 // global memory.
-constexpr int kSwtLen = 64;
+constexpr int kSwtLen = 256;
 
 struct Cta {
   Geo geo;
@@ -1458,12 +1458,12 @@ __global__ void apt_init_kernel(const AptArgs a, int n_prob) {
 
 namespace pc {
 
-size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins) {
+size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins, int split) {
   const size_t G8 = 8 * (size_t)Gc;
   size_t words = (size_t)Gc * N + 32 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
   words += 4 * 64 + 24 + 24 + 128 + 8 + 24 + 512;   // + larger swap stats, group map, exchange, stage
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
-  if (mode == APT_MODE_APT) words += (size_t)(T > 1 ? T - 1 : 0) * kSwtLen;   // staged swap tables (split)
+  if (mode == APT_MODE_APT && split) words += (size_t)(T > 1 ? T - 1 : 0) * kSwtLen;   // staged swap tables
   // V, X, the transposed X (or the cluster labels) and the root masks
   if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31 + (size_t)((N + 31) >> 5);
   return words * 4 + (size_t)N * 2 + 16 + 256;   // + the threshold table's alignment

@@ -344,7 +344,7 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
         cnch[1].push_back(choose_nch(P.N / 2, P.A * gu, bt.tpb, bt.nch_pref));
       }
       smem[1] = std::max(smem[1], apt_smem_bytes(P.N, P.A * std::max(h1, Glp - h1), bt.tpb / 32, mode, icm, P.T,
-                                                 n_bins));
+                                                 n_bins, 1));
       continue;
     }
     // equal chunks of at most gmax groups
@@ -355,7 +355,7 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
       cg0[0].push_back(g0);
       cgc[0].push_back(gc);
       cnch[0].push_back(choose_nch(P.N / 2, gc, bt.tpb, bt.nch_pref));
-      smem[0] = std::max(smem[0], apt_smem_bytes(P.N, gc, bt.tpb / 32, mode, icm, P.T, n_bins));
+      smem[0] = std::max(smem[0], apt_smem_bytes(P.N, gc, bt.tpb / 32, mode, icm, P.T, n_bins, 0));
     }
   }
   bt.n_u = (int)cp[0].size();

@@ -58,7 +58,7 @@ struct AptArgs {
   uint32_t k0, k1;
 };
 
-size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins);
+size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins, int split);
 int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st);
 int apt_init_launch(const AptArgs &a, int n_prob, int max_words, cudaStream_t st);
 // ctr[0] += sweeps, ctr[1] += swaps (stream-ordered after a launch).
