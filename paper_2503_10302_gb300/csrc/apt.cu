@@ -1046,7 +1046,7 @@ __device__ void swap_step(const AptArgs &a, const Cta &k, const Shared &sh, int 
   const int lb = 8 * k.Gu;
   auto swap_table = [&](int r, int dE) {
     const int kk = (-dE) >> 1;
-    if (PC_APT_STAGE_SWT && SPLIT && kk < kSwtLen) return sh.swt[r * kSwtLen + kk];   // staged at launch
+    if (PC_APT_STAGE_SWT && SPLIT && a.stage_swt && kk < kSwtLen) return sh.swt[r * kSwtLen + kk];   // staged at launch
     const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
     return ((uint32_t)kk < len) ? a.swaptab[off + kk] : 0u;
   };
@@ -1231,7 +1231,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
   sh.gmap = reinterpret_cast<int32_t *>(cur);     cur += 8;
   sh.xch = reinterpret_cast<int32_t *>(cur);      cur += 24;
   sh.stage = cur;                                 cur += SPLIT ? 512 : 0;
-  sh.swt = cur;                                   cur += (SPLIT && MODE == pc::APT_MODE_APT) ? (size_t)max(k.T - 1, 0) * kSwtLen : 0;
+  sh.swt = cur;                                   cur += (SPLIT && MODE == pc::APT_MODE_APT && a.stage_swt) ? (size_t)max(k.T - 1, 0) * kSwtLen : 0;
   sh.V = cur;                                     cur += icm ? (size_t)3 * N + 31 + ((N + 31) >> 5) : 0;   // V, X, Xt, R
   sh.jn = reinterpret_cast<uint16_t *>(cur);
 
@@ -1262,7 +1262,7 @@ __global__ void __launch_bounds__(512) apt_kernel(const AptArgs a) {
     sh.sacc[i] = 0;
   }
   if (threadIdx.x < 24) sh.xch[threadIdx.x] = 0;
-  if (PC_APT_STAGE_SWT && SPLIT && MODE == pc::APT_MODE_APT)
+  if (PC_APT_STAGE_SWT && SPLIT && MODE == pc::APT_MODE_APT && a.stage_swt)
     for (int i = threadIdx.x; i < (k.T - 1) * kSwtLen; i += blockDim.x) {
       const int r = i / kSwtLen, kk = i - r * kSwtLen;
       const uint32_t off = a.swapidx[P.swapidx_off + 2 * r], len = a.swapidx[P.swapidx_off + 2 * r + 1];
@@ -1458,12 +1458,12 @@ __global__ void apt_init_kernel(const AptArgs a, int n_prob) {
 
 namespace pc {
 
-size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins, int split) {
+size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins, int stage_swt) {
   const size_t G8 = 8 * (size_t)Gc;
   size_t words = (size_t)Gc * N + 32 * G8 + 4 * G8 + 128 + 8 + 1 + 16 + 8 * G8;
   words += 4 * 64 + 24 + 24 + 128 + 8 + 24 + 512;   // + larger swap stats, group map, exchange, stage
   if (mode == APT_MODE_PILOT) words += (size_t)T * n_bins;
-  if (mode == APT_MODE_APT && split) words += (size_t)(T > 1 ? T - 1 : 0) * kSwtLen;   // staged swap tables
+  if (mode == APT_MODE_APT && stage_swt) words += (size_t)(T > 1 ? T - 1 : 0) * kSwtLen;   // staged swap tables
   // V, X, the transposed X (or the cluster labels) and the root masks
   if (mode == APT_MODE_APT && icm) words += (size_t)3 * N + 31 + (size_t)((N + 31) >> 5);
   return words * 4 + (size_t)N * 2 + 16 + 256;   // + the threshold table's alignment

@@ -51,6 +51,7 @@ struct Batch {
   int split_h = 0;       // split problems: temperature groups per label on rank 0 (0: half)
   size_t smem = 0;       // max of the two parts
   size_t smem_u = 0, smem_s = 0;
+  int stage_swt = 1;     // the split part stages swap tables (when its CTAs still fit)
   std::vector<uint32_t> h_pbit, h_swaptab, h_swapidx;
 };
 
@@ -266,6 +267,7 @@ AptArgs base_args(pc_ctx *c, Batch &bt) {
   a.spp = 1;
   a.icm_big = 1;
   a.icm_seed = 0;
+  a.stage_swt = bt.stage_swt;
   return a;
 }
 
@@ -325,7 +327,7 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
   }
   // [0]: one-CTA part, [1]: two-CTA-cluster part
   std::vector<int> cp[2], cg0[2], cgc[2], cnch[2];
-  size_t smem[2] = {0, 0};
+  size_t smem[2] = {0, 0}, smem_ns = 0;   // smem_ns: the split part without staged swap tables
   for (int i : order) {
     const AptProbDev &P = bt.prob[(size_t)i];
     const int G = bt.G[(size_t)i];
@@ -343,8 +345,9 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
         cgc[1].push_back(P.A * gu);
         cnch[1].push_back(choose_nch(P.N / 2, P.A * gu, bt.tpb, bt.nch_pref));
       }
-      smem[1] = std::max(smem[1], apt_smem_bytes(P.N, P.A * std::max(h1, Glp - h1), bt.tpb / 32, mode, icm, P.T,
-                                                 n_bins, 1));
+      const int gmx = P.A * std::max(h1, Glp - h1);
+      smem[1] = std::max(smem[1], apt_smem_bytes(P.N, gmx, bt.tpb / 32, mode, icm, P.T, n_bins, 1));
+      smem_ns = std::max(smem_ns, apt_smem_bytes(P.N, gmx, bt.tpb / 32, mode, icm, P.T, n_bins, 0));
       continue;
     }
     // equal chunks of at most gmax groups
@@ -358,6 +361,9 @@ int schedule(pc_ctx *c, Batch &bt, const std::vector<char> &active, int mode, in
       smem[0] = std::max(smem[0], apt_smem_bytes(P.N, gc, bt.tpb / 32, mode, icm, P.T, n_bins, 0));
     }
   }
+  // the split part stages its swap tables only where its CTAs still fit
+  bt.stage_swt = smem[1] <= (size_t)c->smem_optin;
+  if (!bt.stage_swt) smem[1] = smem_ns;
   bt.n_u = (int)cp[0].size();
   bt.n_s = (int)cp[1].size();
   bt.split = bt.n_s > 0 && bt.n_u == 0;

@@ -51,6 +51,7 @@ struct AptArgs {
   int icm_big;            // 1: ICM flips one whole replica when the cluster holds more than half
   int icm_seed;           // 0: ICM seeds at a uniform mismatch site; 1: at a uniform cluster
   int prio;               // host side only: launch priority of a cluster launch (0: default)
+  int stage_swt;          // split problems keep the first swap-table entries in shared memory
   int split;              // 1: every problem runs as a cluster of two CTAs (by temperature)
   int64_t *ctr;           // [2]: sweeps and swap attempts done before this launch
   int64_t window_from;
@@ -58,7 +59,7 @@ struct AptArgs {
   uint32_t k0, k1;
 };
 
-size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins, int split);
+size_t apt_smem_bytes(int N, int Gc, int nwarps, int mode, int icm, int T, int n_bins, int stage_swt);
 int apt_launch(const AptArgs &a, int n_cta, int tpb, size_t smem, cudaStream_t st);
 int apt_init_launch(const AptArgs &a, int n_prob, int max_words, cudaStream_t st);
 // ctr[0] += sweeps, ctr[1] += swaps (stream-ordered after a launch).

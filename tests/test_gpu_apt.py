@@ -541,6 +541,25 @@ def test_mixed_placement_matches_oracle(pc, orc, labels):
     ctx.close()
 
 
+def test_swap_tables_unstaged_where_they_do_not_fit(pc, orc):
+    """32 temperatures x 4 labels on a 16^3 lattice (the paper's label
+    count): a two-CTA cluster with staged swap tables would exceed shared
+    memory, so this batch reads them from global memory; with ICM, against
+    the oracle."""
+    dims = np.array([(16, 16, 16)], np.int32)
+    J = [W.ea_couplings((16, 16, 16), 18, 0)]
+    betas = [W.geometric_ladder(32)]
+    b = W.AptBatch(dims, J, betas, 4)
+    ctx = pc.Context(0, 53)
+    pc.pc_apt_load(ctx.h, dims, J, betas, 4, 1)
+    assert pc.pc_apt_is_split(ctx.h) == 1
+    apt = orc.Apt(dims, J, betas, 4, seed=53, entry0=1)
+    pc.pc_apt_run(ctx.h, 12, 1, True)
+    apt.run(12, 1, True, threads=8)
+    _compare(pc, apt, ctx, b)
+    ctx.close()
+
+
 def test_checkpoint_resume_bit_exact(pc, tmp_path):
     """200 attempts == 90, save, restore into a fresh context, 110 more."""
     b = W.apt_uniform_batch(2, 6, 12)
