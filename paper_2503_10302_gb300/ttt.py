@@ -137,13 +137,20 @@ def c3_time_to_target(n_inst=64, L=12, rho=1e-3, best_runs=10, best_sweeps=10000
             "e_best_per_spin_mean": float((e_best / N).mean())}
 
 
+def evt_median_gaussian(mu: float, sd: float, r: int) -> float:
+    """Median of the minimum of r independent N(mu, sd^2) draws (Eq.
+    EVTmedianFinal): F_min(x) = 1 - (1 - Phi((x - mu)/sd))^r = 1/2 gives
+    x = mu + sqrt(2) sd erfc^-1(2^((r - 1)/r))."""
+    from scipy.special import erfcinv
+    return mu + np.sqrt(2.0) * sd * float(erfcinv(2.0 ** ((r - 1) / r)))
+
+
 def c2_residual_vs_R(L=8, P=64, R=256, T=0.05, sweeps=10000, best_runs=10, best_sweeps=100000,
                      Rs=(1, 4, 16, 64, 256)) -> Dict:
     """DT-SQA on one L = 8 instance: residual energy of the best slice of a
     run, and of the best of R independent runs as R grows.  E_best: best of
     APT+ICM runs on the same instance.  The Gaussian extreme-value median of
     the best of R (Eq. EVTmedianFinal) is reported beside the measurement."""
-    from scipy.special import erfcinv
     wl = W.sqa_workload(L, P, R, T, sweeps)
     N = L ** 3
     ctx = pcomp.Context(0, 31)
@@ -189,7 +196,7 @@ def c2_residual_vs_R(L=8, P=64, R=256, T=0.05, sweeps=10000, best_runs=10, best_
            "C_r_length_1_over_e": int(np.argmax(C_r[: P // 2 + 1] < np.exp(-1.0))) or None}
     for r in Rs:
         g = rho_run[: (R // r) * r].reshape(-1, r).min(axis=1)
-        pred = mu + np.sqrt(2.0) * sd * float(erfcinv(2.0 ** ((r - 1) / r)))
+        pred = evt_median_gaussian(mu, sd, r)
         out["best_of_R"][str(r)] = {"groups": int(g.size), "mean": float(g.mean()),
                                     "median": float(np.median(g)), "evt_median_gaussian": pred,
                                     "hit_fraction_rho_le_1e-3": float((g <= 1e-3).mean())}
